@@ -1,0 +1,392 @@
+/*
+ * stap_oracle.c -- plain, slow FP64 CPU oracle for the STAP hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant generator with the CUDA library: it is written from
+ * the definitions below and nothing else.
+ *
+ * What it computes (arXiv 2203.06233, Sec. 4.2 "Kernel from the STAP Signal
+ * Processing Application" and Sec. 5.3 "Multi-node Results (STAP)").  The paper
+ * fixes only three facts about the kernel: an explicit loop (statement S), an
+ * `fft` over a 1-D domain (statement T) and a 2-D x 2-D array multiply
+ * (statement U), fused into one parallel loop over data cubes.  Everything else
+ * is the standard post-Doppler STAP reading, written out here step by step:
+ *
+ *   1. Doppler transform over pulses (statement T):
+ *        h[p]       = 0.5 - 0.5 cos(2 pi p / (P-1))           symmetric Hann
+ *        X[c][k][r] = sum_{p<P} h[p] x[c][p][r] exp(-j 2 pi p k / K)
+ *      a direct DFT of length K >= P (zero padding), no shift, no scale.
+ *   2. Space-time snapshot of cell (k, r), D = C*T entries, channel fastest:
+ *        x_{k,r}[t*C + c] = X[c][(k + t - floor(T/2)) mod K][r]
+ *   3. Covariance per (Doppler bin k, range block b of B cells) (statement U):
+ *        R_{k,b} = (1/B) sum_{r in block b} x_{k,r} x_{k,r}^H
+ *   4. Diagonal loading:  delta = lf * Re tr(R) / D,  Rl = R + delta I.
+ *   5. Cholesky Rl = L L^H (L lower, real positive diagonal), column by column.
+ *   6. u_s = Rl^{-1} v_s by forward then back substitution (no refinement:
+ *      the FP64 solve is the reference).
+ *   7. w_s = u_s / sqrt(Re v_s^H u_s)      (unit noise gain / AMF weights)
+ *   8. P[s][k][r] = |w_{k,b(r),s}^H x_{k,r}|^2
+ *
+ *   Default steering (same for every Doppler bin):
+ *        theta_s = -90 deg + 180 deg (s + 1/2) / S,  f_s = sin(theta_s) / 2
+ *        a_c     = exp(j 2 pi f_s c)
+ *        g_t     = sum_{p<P} h[p] exp(-j 2 pi m_t p / K),  m_t = t - floor(T/2)
+ *        v_s[t*C + c] = g_t a_c
+ *
+ * All arithmetic is IEEE double (compile without -ffast-math).  Complex arrays
+ * are interleaved (re, im) doubles, i.e. C99 `double complex`, row-major.
+ * Range arguments (r0, nr) select a window of range cells so that very large
+ * cubes can be processed a slab at a time; every step is independent across
+ * range blocks, so a window that starts and ends on block boundaries gives the
+ * exact result for its cells.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+/* The oracle's own description of one coherent processing interval. */
+typedef struct {
+  int32_t n_chan;          /* C */
+  int32_t n_pulses;        /* P */
+  int32_t n_dop;           /* K */
+  int32_t n_range;         /* R */
+  int32_t tdof;            /* T */
+  int32_t training_block;  /* B */
+  int32_t n_steering;      /* S */
+} oracle_dims;
+
+#define ORACLE_OK 0
+#define ORACLE_BAD_ARGS (-1)
+#define ORACLE_NO_MEMORY (-2)
+
+static const double kPi = 3.14159265358979323846264338327950288;
+
+static int dims_ok(const oracle_dims* d) {
+  if (!d) return 0;
+  if (d->n_chan < 1 || d->n_pulses < 1 || d->n_dop < d->n_pulses || d->n_range < 1) return 0;
+  if (d->tdof < 1 || d->tdof > d->n_dop || d->training_block < 1 || d->n_steering < 1) return 0;
+  if (d->n_range % d->training_block != 0) return 0;
+  return 1;
+}
+
+static int window_ok(const oracle_dims* d, int r0, int nr) {
+  return r0 >= 0 && nr >= 0 && r0 + nr <= d->n_range && r0 % d->training_block == 0 &&
+         nr % d->training_block == 0;
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* Step 1 window: symmetric Hann of length P (P = 1 gives the single value 1,
+ * as numpy.hanning does). */
+void oracle_hann(int32_t P, double* h) {
+  if (P == 1) {
+    h[0] = 1.0;
+    return;
+  }
+  for (int p = 0; p < P; ++p) h[p] = 0.5 - 0.5 * cos(2.0 * kPi * (double)p / (double)(P - 1));
+}
+
+/* exp(-j 2 pi n / K) for an integer n, with n reduced mod K exactly first. */
+static cplx twiddle(int64_t n, int32_t K) {
+  int64_t m = n % K;
+  if (m < 0) m += K;
+  double a = -2.0 * kPi * (double)m / (double)K;
+  return cos(a) + I * sin(a);
+}
+
+/* Step 1 with an arbitrary real window w[P] (the Hann case is oracle_doppler).
+ * cube: [C][P][R] complex (the full cube); dop: [C][K][nr] complex for the
+ * range cells r0 .. r0+nr-1. */
+int oracle_doppler_window(const oracle_dims* d, const double* w, const cplx* cube, int32_t r0,
+                          int32_t nr, cplx* dop) {
+  if (!dims_ok(d) || !w || !cube || !dop || r0 < 0 || nr < 0 || r0 + nr > d->n_range)
+    return ORACLE_BAD_ARGS;
+  const int C = d->n_chan, P = d->n_pulses, K = d->n_dop, R = d->n_range;
+  cplx* tw = (cplx*)malloc(sizeof(cplx) * (size_t)K);
+  if (!tw) return ORACLE_NO_MEMORY;
+  for (int n = 0; n < K; ++n) tw[n] = twiddle(n, K);
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int c = 0; c < C; ++c) {
+    for (int k = 0; k < K; ++k) {
+      for (int rr = 0; rr < nr; ++rr) {
+        cplx acc = 0.0;
+        for (int p = 0; p < P; ++p) {
+          const cplx x = cube[((size_t)c * P + p) * R + (size_t)(r0 + rr)];
+          acc += w[p] * x * tw[((int64_t)p * k) % K];
+        }
+        dop[((size_t)c * K + k) * nr + rr] = acc;
+      }
+    }
+  }
+  free(tw);
+  return ORACLE_OK;
+}
+
+int oracle_doppler(const oracle_dims* d, const cplx* cube, int32_t r0, int32_t nr, cplx* dop) {
+  if (!dims_ok(d)) return ORACLE_BAD_ARGS;
+  double* h = (double*)malloc(sizeof(double) * (size_t)d->n_pulses);
+  if (!h) return ORACLE_NO_MEMORY;
+  oracle_hann(d->n_pulses, h);
+  int rc = oracle_doppler_window(d, h, cube, r0, nr, dop);
+  free(h);
+  return rc;
+}
+
+/* Step 2: snapshot of cell (k, rr) of a Doppler window dop[C][K][nr]. */
+int oracle_snapshot(const oracle_dims* d, const cplx* dop, int32_t nr, int32_t k, int32_t rr,
+                    cplx* x) {
+  if (!dims_ok(d) || !dop || !x || k < 0 || k >= d->n_dop || rr < 0 || rr >= nr)
+    return ORACLE_BAD_ARGS;
+  const int C = d->n_chan, K = d->n_dop, T = d->tdof;
+  for (int t = 0; t < T; ++t) {
+    int kk = ((k + t - T / 2) % K + K) % K;
+    for (int c = 0; c < C; ++c) x[t * C + c] = dop[((size_t)c * K + kk) * nr + rr];
+  }
+  return ORACLE_OK;
+}
+
+/* Step 3: cov[K][nr/B][D][D] from a Doppler window dop[C][K][nr]; nr must be a
+ * multiple of B (the window starts on a block boundary). */
+int oracle_covariance(const oracle_dims* d, const cplx* dop, int32_t nr, cplx* cov) {
+  if (!dims_ok(d) || !dop || !cov || nr < 0 || nr % d->training_block != 0) return ORACLE_BAD_ARGS;
+  const int K = d->n_dop, B = d->training_block, D = d->n_chan * d->tdof;
+  const int NB = nr / B;
+  int bad = 0;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int k = 0; k < K; ++k) {
+    for (int b = 0; b < NB; ++b) {
+      cplx* x = (cplx*)malloc(sizeof(cplx) * (size_t)D);
+      cplx* Rm = (cplx*)calloc((size_t)D * D, sizeof(cplx));
+      if (!x || !Rm) {
+#pragma omp atomic write
+        bad = 1;
+        free(x);
+        free(Rm);
+        continue;
+      }
+      for (int rr = b * B; rr < (b + 1) * B; ++rr) {
+        oracle_snapshot(d, dop, nr, k, rr, x);
+        for (int i = 0; i < D; ++i)
+          for (int j = 0; j < D; ++j) Rm[(size_t)i * D + j] += x[i] * conj(x[j]);
+      }
+      cplx* out = cov + ((size_t)k * NB + b) * D * D;
+      for (int i = 0; i < D * D; ++i) out[i] = Rm[i] / (double)B;
+      free(x);
+      free(Rm);
+    }
+  }
+  return bad ? ORACLE_NO_MEMORY : ORACLE_OK;
+}
+
+/* Step 5: A = L L^H for Hermitian positive definite A[D][D] (only the lower
+ * triangle of A is read).  L[D][D] gets the lower factor, zeros above the
+ * diagonal.  Column by column: the diagonal entry from the row's squared norm,
+ * then the entries below it from the inner products with earlier columns.
+ * Returns 0, or 1 + the column whose pivot was not positive and finite. */
+int oracle_cholesky(int32_t D, const cplx* A, cplx* L) {
+  if (D < 1 || !A || !L) return ORACLE_BAD_ARGS;
+  memset(L, 0, sizeof(cplx) * (size_t)D * D);
+  for (int j = 0; j < D; ++j) {
+    double s = creal(A[(size_t)j * D + j]);
+    for (int k = 0; k < j; ++k) {
+      cplx l = L[(size_t)j * D + k];
+      s -= creal(l) * creal(l) + cimag(l) * cimag(l);
+    }
+    if (!(s > 0.0) || !isfinite(s)) return 1 + j;
+    double ljj = sqrt(s);
+    L[(size_t)j * D + j] = ljj;
+    for (int i = j + 1; i < D; ++i) {
+      cplx acc = A[(size_t)i * D + j];
+      for (int k = 0; k < j; ++k) acc -= L[(size_t)i * D + k] * conj(L[(size_t)j * D + k]);
+      L[(size_t)i * D + j] = acc / ljj;
+    }
+  }
+  return ORACLE_OK;
+}
+
+/* Step 6: u = (L L^H)^{-1} b by forward substitution L y = b, then back
+ * substitution L^H u = y. */
+int oracle_cholesky_solve(int32_t D, const cplx* L, const cplx* b, cplx* u) {
+  if (D < 1 || !L || !b || !u) return ORACLE_BAD_ARGS;
+  cplx* y = (cplx*)malloc(sizeof(cplx) * (size_t)D);
+  if (!y) return ORACLE_NO_MEMORY;
+  for (int i = 0; i < D; ++i) {
+    cplx acc = b[i];
+    for (int j = 0; j < i; ++j) acc -= L[(size_t)i * D + j] * y[j];
+    y[i] = acc / creal(L[(size_t)i * D + i]);
+  }
+  for (int i = D - 1; i >= 0; --i) {
+    cplx acc = y[i];
+    for (int j = i + 1; j < D; ++j) acc -= conj(L[(size_t)j * D + i]) * u[j];
+    u[i] = acc / creal(L[(size_t)i * D + i]);
+  }
+  free(y);
+  return ORACLE_OK;
+}
+
+/* Default steering table steer[S][D] (see the header comment). */
+int oracle_default_steering(const oracle_dims* d, cplx* steer) {
+  if (!dims_ok(d) || !steer) return ORACLE_BAD_ARGS;
+  const int C = d->n_chan, P = d->n_pulses, K = d->n_dop, T = d->tdof, S = d->n_steering;
+  const int D = C * T;
+  double* h = (double*)malloc(sizeof(double) * (size_t)P);
+  cplx* g = (cplx*)malloc(sizeof(cplx) * (size_t)T);
+  if (!h || !g) {
+    free(h);
+    free(g);
+    return ORACLE_NO_MEMORY;
+  }
+  oracle_hann(P, h);
+  for (int t = 0; t < T; ++t) {
+    int m = t - T / 2;
+    cplx acc = 0.0;
+    for (int p = 0; p < P; ++p) acc += h[p] * twiddle((int64_t)m * p, K);
+    g[t] = acc;
+  }
+  for (int s = 0; s < S; ++s) {
+    double theta = (-90.0 + 180.0 * ((double)s + 0.5) / (double)S) * kPi / 180.0;
+    double fs = 0.5 * sin(theta);
+    for (int t = 0; t < T; ++t)
+      for (int c = 0; c < C; ++c) {
+        double a = 2.0 * kPi * fs * (double)c;
+        steer[(size_t)s * D + t * C + c] = g[t] * (cos(a) + I * sin(a));
+      }
+  }
+  free(h);
+  free(g);
+  return ORACLE_OK;
+}
+
+/* Steps 4-7 for nsys covariances cov[nsys][D][D] (lower triangle read) and a
+ * steering table steer[S][D]: wts[nsys][S][D].  status[i] = 0, or 1 + the
+ * failing column if system i was not positive definite (its weights are zero).
+ * Returns the number of failed systems (>= 0) or a negative error. */
+int oracle_weights(const oracle_dims* d, const cplx* cov, int32_t nsys, const cplx* steer,
+                   double load_factor, cplx* wts, int32_t* status) {
+  if (!dims_ok(d) || !cov || !steer || !wts || nsys < 0) return ORACLE_BAD_ARGS;
+  const int D = d->n_chan * d->tdof, S = d->n_steering;
+  int failed = 0, bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : failed)
+  for (int i = 0; i < nsys; ++i) {
+    const cplx* R = cov + (size_t)i * D * D;
+    cplx* W = wts + (size_t)i * S * D;
+    cplx* A = (cplx*)malloc(sizeof(cplx) * (size_t)D * D);
+    cplx* L = (cplx*)malloc(sizeof(cplx) * (size_t)D * D);
+    cplx* u = (cplx*)malloc(sizeof(cplx) * (size_t)D);
+    if (!A || !L || !u) {
+#pragma omp atomic write
+      bad = 1;
+      free(A);
+      free(L);
+      free(u);
+      continue;
+    }
+    double tr = 0.0;
+    for (int j = 0; j < D; ++j) tr += creal(R[(size_t)j * D + j]);
+    const double delta = load_factor * tr / (double)D;
+    memcpy(A, R, sizeof(cplx) * (size_t)D * D);
+    for (int j = 0; j < D; ++j) A[(size_t)j * D + j] += delta;
+    int rc = oracle_cholesky(D, A, L);
+    if (status) status[i] = rc;
+    if (rc != 0) {
+      failed += 1;
+      memset(W, 0, sizeof(cplx) * (size_t)S * D);
+    } else {
+      for (int s = 0; s < S; ++s) {
+        const cplx* v = steer + (size_t)s * D;
+        oracle_cholesky_solve(D, L, v, u);
+        double q = 0.0; /* Re v^H u */
+        for (int j = 0; j < D; ++j) q += creal(conj(v[j]) * u[j]);
+        double scale = 1.0 / sqrt(q);
+        for (int j = 0; j < D; ++j) W[(size_t)s * D + j] = u[j] * scale;
+      }
+    }
+    free(A);
+    free(L);
+    free(u);
+  }
+  if (bad) return ORACLE_NO_MEMORY;
+  return failed;
+}
+
+/* Step 8: out[S][K][nr] = |w^H x|^2 for every cell of a Doppler window
+ * dop[C][K][nr] with weights wts[K][nr/B][S][D]. */
+int oracle_apply(const oracle_dims* d, const cplx* dop, int32_t nr, const cplx* wts, double* out) {
+  if (!dims_ok(d) || !dop || !wts || !out || nr < 0 || nr % d->training_block != 0)
+    return ORACLE_BAD_ARGS;
+  const int K = d->n_dop, B = d->training_block, S = d->n_steering, D = d->n_chan * d->tdof;
+  const int NB = nr / B;
+  int bad = 0;
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < K; ++k) {
+    cplx* x = (cplx*)malloc(sizeof(cplx) * (size_t)D);
+    if (!x) {
+#pragma omp atomic write
+      bad = 1;
+      continue;
+    }
+    for (int rr = 0; rr < nr; ++rr) {
+      oracle_snapshot(d, dop, nr, k, rr, x);
+      const cplx* W = wts + ((size_t)k * NB + rr / B) * S * D;
+      for (int s = 0; s < S; ++s) {
+        cplx y = 0.0;
+        for (int j = 0; j < D; ++j) y += conj(W[(size_t)s * D + j]) * x[j];
+        out[((size_t)s * K + k) * nr + rr] = creal(y) * creal(y) + cimag(y) * cimag(y);
+      }
+    }
+    free(x);
+  }
+  return bad ? ORACLE_NO_MEMORY : ORACLE_OK;
+}
+
+/* Steps 1-8 for the range window [r0, r0+nr) of one CPI.  steer may be NULL
+ * (default steering).  Any of dop [C][K][nr], cov [K][nr/B][D][D],
+ * wts [K][nr/B][S][D] may be NULL, in which case a temporary is used; out
+ * [S][K][nr] and status [K][nr/B] (may be NULL) receive the results.
+ * Returns the number of failed systems or a negative error. */
+int oracle_run(const oracle_dims* d, const cplx* cube, const cplx* steer, double load_factor,
+               int32_t r0, int32_t nr, cplx* dop, cplx* cov, cplx* wts, double* out,
+               int32_t* status) {
+  if (!dims_ok(d) || !cube || !out || !window_ok(d, r0, nr)) return ORACLE_BAD_ARGS;
+  const int C = d->n_chan, K = d->n_dop, S = d->n_steering, D = d->n_chan * d->tdof;
+  const int NB = nr / d->training_block;
+  cplx *dop_t = NULL, *cov_t = NULL, *wts_t = NULL, *steer_t = NULL;
+  int rc = ORACLE_NO_MEMORY;
+  if (!dop) dop = dop_t = (cplx*)malloc(sizeof(cplx) * (size_t)C * K * nr);
+  if (!cov) cov = cov_t = (cplx*)malloc(sizeof(cplx) * (size_t)K * NB * D * D);
+  if (!wts) wts = wts_t = (cplx*)malloc(sizeof(cplx) * (size_t)K * NB * S * D);
+  if (!steer) {
+    steer = steer_t = (cplx*)malloc(sizeof(cplx) * (size_t)S * D);
+    if (steer_t && oracle_default_steering(d, steer_t) != ORACLE_OK) goto done;
+  }
+  if (!dop || !cov || !wts || !steer) goto done;
+  if ((rc = oracle_doppler(d, cube, r0, nr, dop)) != ORACLE_OK) goto done;
+  if ((rc = oracle_covariance(d, dop, nr, cov)) != ORACLE_OK) goto done;
+  int failed = oracle_weights(d, cov, K * NB, steer, load_factor, wts, status);
+  if (failed < 0) {
+    rc = failed;
+    goto done;
+  }
+  if ((rc = oracle_apply(d, dop, nr, wts, out)) != ORACLE_OK) goto done;
+  rc = failed;
+done:
+  free(dop_t);
+  free(cov_t);
+  free(wts_t);
+  free(steer_t);
+  return rc;
+}

@@ -1,0 +1,228 @@
+"""Seeded synthetic radar cubes for the STAP path (inputs only).
+
+This module holds the data model and nothing of the STAP method's arithmetic.
+Both the CUDA path (through its tests and the benchmark) and the CPU oracle
+take their inputs from here.
+
+Random numbers: a counter-based SplitMix64 generator (Steele, Lea & Flood,
+"Fast splittable pseudorandom number generators", OOPSLA 2014): sample ``i`` of
+stream ``s`` under ``seed`` is ``mix(key(seed, s) + (i + 1) * 0x9E3779B97F4A7C15)``,
+so every sample can be regenerated on its own.  Normal deviates come from the
+Box-Muller transform in float64; the cube is rounded to complex64 once at the
+end, and that complex64 cube is the canonical input.
+
+Data model per CPI (cube[c][p][r], c < C channels, p < P pulses, r < R cells):
+
+* noise: i.i.d. CN(0, 1) per sample (real and imaginary parts N(0, 1/2));
+* clutter ridge: 64 patches at azimuths theta_i = -90 + 180 (i + 1/2)/64 deg,
+  spatial frequency f_i = sin(theta_i)/2 and Doppler equal to it (beta = 1);
+  per (patch, range cell) a CN(0, CNR/64) amplitude, constant over pulses and
+  channels: sample += alpha_{i,r} exp(j 2 pi f_i c) exp(j 2 pi f_i p);
+* targets: amplitude sqrt(SNR) exp(j phi) at one range cell r0, a Doppler-bin
+  centre frequency k0/K and a steering-grid angle theta_{s0}:
+  sample += a exp(j 2 pi f_{s0} c) exp(j 2 pi (k0/K) p).
+
+CNR and SNR are per element per pulse (relative to the unit noise power).
+"""
+from dataclasses import dataclass, field
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+STREAM_NOISE = 0
+STREAM_CLUTTER = 1
+STREAM_TARGETS = 2
+STREAM_BATCH_DIMS = 3
+
+N_PATCH = 64
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def _key(seed: int, stream: int, sub: int = 0) -> np.uint64:
+    a = _mix(np.array([seed & 0xFFFFFFFFFFFFFFFF], np.uint64))
+    b = _mix(a ^ np.array([(stream << 48) ^ (sub & 0xFFFFFFFFFFFF)], np.uint64))
+    return b[0]
+
+
+def uniform(seed: int, stream: int, idx, sub: int = 0) -> np.ndarray:
+    """Uniform deviates in (0, 1) for the integer counters ``idx``."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = _mix(_key(seed, stream, sub) + (idx + np.uint64(1)) * _GAMMA)
+    return ((z >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def complex_normal(seed: int, stream: int, idx, var: float = 1.0, sub: int = 0) -> np.ndarray:
+    """CN(0, var) deviates (Box-Muller) for the counters ``idx`` (two uniforms each)."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    u1 = uniform(seed, stream, idx * np.uint64(2), sub)
+    u2 = uniform(seed, stream, idx * np.uint64(2) + np.uint64(1), sub)
+    rad = np.sqrt(-np.log(u1) * var)
+    ang = 2.0 * np.pi * u2
+    return rad * np.cos(ang) + 1j * (rad * np.sin(ang))
+
+
+@dataclass(frozen=True)
+class Target:
+    r0: int          # range cell
+    k0: int          # Doppler bin (normalised Doppler k0/K, wrapping above K/2)
+    s0: int          # steering-grid index (angle theta_{s0})
+    snr_db: float    # per element per pulse
+    phase: float = 0.0
+
+
+@dataclass(frozen=True)
+class CPISpec:
+    """Shape and content of one synthetic CPI."""
+    n_chan: int
+    n_pulses: int
+    n_dop: int
+    n_range: int
+    tdof: int
+    training_block: int
+    n_steering: int
+    cnr_db: Optional[float] = 40.0      # None: no clutter
+    noise: bool = True
+    targets: Tuple[Target, ...] = ()
+    seed: int = 0
+    sub: int = 0                          # CPI index inside a batch (substream)
+
+    @property
+    def D(self) -> int:
+        return self.n_chan * self.tdof
+
+    @property
+    def NB(self) -> int:
+        return self.n_range // self.training_block
+
+    @property
+    def cells(self) -> int:
+        return self.n_dop * self.n_range
+
+    def dims(self) -> Tuple[int, ...]:
+        return (self.n_chan, self.n_pulses, self.n_dop, self.n_range, self.tdof,
+                self.training_block, self.n_steering)
+
+
+def steering_angle_deg(s: int, S: int) -> float:
+    """The steering grid: uniform in angle over (-90, 90) degrees."""
+    return -90.0 + 180.0 * (s + 0.5) / S
+
+
+def patch_frequencies() -> np.ndarray:
+    theta = np.deg2rad(-90.0 + 180.0 * (np.arange(N_PATCH) + 0.5) / N_PATCH)
+    return 0.5 * np.sin(theta)
+
+
+def random_targets(seed: int, n: int, R: int, K: int, S: int, snr_lo=0.0, snr_hi=15.0,
+                   sub: int = 0) -> Tuple[Target, ...]:
+    """n targets at seeded uniform (range, Doppler bin, steering index), SNR and phase."""
+    u = uniform(seed, STREAM_TARGETS, np.arange(5 * n), sub).reshape(n, 5) if n else np.zeros((0, 5))
+    out = []
+    for j in range(n):
+        out.append(Target(r0=int(u[j, 0] * R), k0=int(u[j, 1] * K), s0=int(u[j, 2] * S),
+                          snr_db=float(snr_lo + (snr_hi - snr_lo) * u[j, 3]),
+                          phase=float(2.0 * np.pi * u[j, 4])))
+    return tuple(out)
+
+
+def make_cube(spec: CPISpec, chan_chunk: int = 4) -> np.ndarray:
+    """The complex64 cube [C][P][R] of ``spec`` (generated in float64, rounded once)."""
+    C, P, R = spec.n_chan, spec.n_pulses, spec.n_range
+    cube = np.empty((C, P, R), np.complex64)
+    f = patch_frequencies()
+    alpha = None
+    if spec.cnr_db is not None:
+        cnr = 10.0 ** (spec.cnr_db / 10.0)
+        alpha = complex_normal(spec.seed, STREAM_CLUTTER, np.arange(N_PATCH * R, dtype=np.uint64),
+                               cnr / N_PATCH, spec.sub).reshape(N_PATCH, R)
+    dop_steer = np.exp(2j * np.pi * np.outer(np.arange(P), f))            # [P][patch]
+    for c0 in range(0, C, chan_chunk):
+        c1 = min(C, c0 + chan_chunk)
+        blk = np.zeros((c1 - c0, P, R), np.complex128)
+        if spec.noise:
+            idx = np.arange(c0 * P * R, c1 * P * R, dtype=np.uint64)
+            blk += complex_normal(spec.seed, STREAM_NOISE, idx, 1.0, spec.sub).reshape(c1 - c0, P, R)
+        if alpha is not None:
+            for c in range(c0, c1):
+                sp = np.exp(2j * np.pi * f * c)                           # [patch]
+                blk[c - c0] += (dop_steer * sp[None, :]) @ alpha
+        cube[c0:c1] = blk
+    if spec.targets:
+        for t in spec.targets:
+            th = np.deg2rad(steering_angle_deg(t.s0, spec.n_steering))
+            fs = 0.5 * np.sin(th)
+            amp = np.sqrt(10.0 ** (t.snr_db / 10.0)) * np.exp(1j * t.phase)
+            sig = amp * np.exp(2j * np.pi * fs * np.arange(C))[:, None] * \
+                np.exp(2j * np.pi * (t.k0 / spec.n_dop) * np.arange(P))[None, :]
+            # add in float64 on top of the already-rounded value, then round again:
+            # targets sit on single cells, so this equals generating them together
+            # up to one extra rounding of those cells only.
+            cube[:, :, t.r0] = (cube[:, :, t.r0].astype(np.complex128) + sig).astype(np.complex64)
+    return cube
+
+
+# ----------------------------------------------------------------------------
+# The workloads: a small single-CPI case, the standard single-CPI case, a
+# mixed-precision case, a batch of uneven CPIs and a large single CPI.
+# ----------------------------------------------------------------------------
+
+def small_cpi() -> CPISpec:
+    """C4 P32 K32 R256 T3 B32 S4, 30 dB CNR, one 10 dB target at (r 128, bin 24, steer 2)."""
+    return CPISpec(4, 32, 32, 256, 3, 32, 4, cnr_db=30.0,
+                   targets=(Target(128, 24, 2, 10.0, 0.0),), seed=1)
+
+
+def standard_cpi() -> CPISpec:
+    """C4 P128 K256 R4096 T3 B64 S16, 40 dB CNR, 8 targets at 0-15 dB SNR."""
+    return CPISpec(4, 128, 256, 4096, 3, 64, 16, cnr_db=40.0,
+                   targets=random_targets(2, 8, 4096, 256, 16), seed=2)
+
+
+def mixed_cpi() -> CPISpec:
+    """C16 P256 K256 R16384 T4 B128 S32, 40 dB CNR, 8 targets."""
+    return CPISpec(16, 256, 256, 16384, 4, 128, 32, cnr_db=40.0,
+                   targets=random_targets(3, 8, 16384, 256, 32), seed=3)
+
+
+def large_cpi() -> CPISpec:
+    """C32 P512 K512 R32768 T4 B256 S64, 40 dB CNR, 32 targets (about 4.3 GB)."""
+    return CPISpec(32, 512, 512, 32768, 4, 256, 64, cnr_db=40.0,
+                   targets=random_targets(5, 32, 32768, 512, 64), seed=5)
+
+
+def batch_cpis(n: int = 512, seed: int = 4) -> List[CPISpec]:
+    """n uneven CPIs: C in {4,8,16}, T in {2,3,4}, P = K in {64,128,256},
+    R = 64 * U{16..256}, B = 64, S in {8,16}, CNR uniform in 20-40 dB, 4 targets each."""
+    u = uniform(seed, STREAM_BATCH_DIMS, np.arange(7 * n)).reshape(n, 7)
+    out = []
+    for i in range(n):
+        C = (4, 8, 16)[int(u[i, 0] * 3)]
+        T = (2, 3, 4)[int(u[i, 1] * 3)]
+        P = (64, 128, 256)[int(u[i, 2] * 3)]
+        R = 64 * (16 + int(u[i, 3] * 241))
+        S = (8, 16)[int(u[i, 4] * 2)]
+        cnr = 20.0 + 20.0 * float(u[i, 5])
+        out.append(CPISpec(C, P, P, R, T, 64, S, cnr_db=cnr,
+                           targets=random_targets(seed, 4, R, P, S, sub=i + 1),
+                           seed=seed, sub=i + 1))
+    return out
+
+
+WORKLOADS = {
+    "small": small_cpi,
+    "standard": standard_cpi,
+    "mixed": mixed_cpi,
+    "large": large_cpi,
+}

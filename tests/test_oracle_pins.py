@@ -1,0 +1,404 @@
+"""Pins for the FP64 CPU oracle: closed forms, invariants, library routines and
+brute force, each chosen so that a plausible slip in the oracle (a dropped term,
+a wrong sign or index, a transposed operand, a missing scale) fails one of them.
+
+The paper (arXiv 2203.06233) prints no STAP numbers, so nothing here is a
+value from it; the definitions pinned are the post-Doppler reading of its STAP
+kernel (Sec. 4.2: `fft` over pulses, 2-D x 2-D array multiply).
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_06233_gb300 import synth
+
+RNG = np.random.default_rng(12345)
+
+
+def crandn(*shape):
+    return (RNG.standard_normal(shape) + 1j * RNG.standard_normal(shape)) / np.sqrt(2.0)
+
+
+def dims(C=3, P=16, K=16, R=64, T=3, B=16, S=4):
+    return oracle.Dims(C, P, K, R, T, B, S)
+
+
+# ---------------------------------------------------------------- window -----
+
+@pytest.mark.parametrize("P", [1, 2, 5, 32, 128])
+def test_hann_is_numpy_symmetric_hann(P):
+    h = oracle.hann(P)
+    np.testing.assert_allclose(h, np.hanning(P), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(h, h[::-1], rtol=0, atol=1e-15)
+    if P > 1:
+        assert h[0] == 0.0 and abs(h[-1]) < 1e-16
+
+
+# ---------------------------------------------------------------- doppler ----
+
+def _geom(w, P):
+    """sum_{p<P} w^p in closed form."""
+    if abs(w - 1.0) < 1e-14:
+        return complex(P)
+    return (1.0 - w ** P) / (1.0 - w)
+
+
+@pytest.mark.parametrize("P,K,k0", [(32, 32, 5), (20, 64, 61), (33, 64, 0)])
+def test_doppler_tone_on_bin_closed_form(P, K, k0):
+    """x[p] = exp(j 2 pi k0 p / K): X[k] = sum_p h[p] exp(-j 2 pi (k-k0) p / K),
+    with the Hann sum expanded into three geometric series."""
+    d = dims(C=2, P=P, K=K, R=4, T=1, B=4, S=1)
+    p = np.arange(P)
+    tone = np.exp(2j * np.pi * k0 * p / K)
+    cube = np.broadcast_to(tone[None, :, None], (2, P, 4)).astype(np.complex128)
+    X = oracle.doppler(d, cube)
+    th = 2.0 * np.pi / (P - 1)
+    for k in range(K):
+        z = np.exp(-2j * np.pi * (k - k0) / K)
+        ref = 0.5 * _geom(z, P) - 0.25 * _geom(z * np.exp(1j * th), P) \
+            - 0.25 * _geom(z * np.exp(-1j * th), P)
+        np.testing.assert_allclose(X[:, k, :], ref, rtol=0, atol=1e-12 * P)
+
+
+def test_doppler_matches_numpy_fft_with_zero_padding():
+    d = dims(C=3, P=24, K=64, R=40, T=1, B=8, S=1)
+    cube = crandn(3, 24, 40)
+    ref = np.fft.fft(np.hanning(24)[None, :, None] * cube, n=64, axis=1)
+    X = oracle.doppler(d, cube)
+    assert np.linalg.norm(X - ref) / np.linalg.norm(ref) < 1e-13
+
+
+def test_doppler_linearity_and_parseval_rect_window():
+    d = dims(C=2, P=16, K=16, R=8, T=1, B=8, S=1)
+    x, y = crandn(2, 16, 8), crandn(2, 16, 8)
+    a, b = 0.3 - 1.2j, -2.0 + 0.5j
+    lhs = oracle.doppler(d, a * x + b * y)
+    rhs = a * oracle.doppler(d, x) + b * oracle.doppler(d, y)
+    assert np.linalg.norm(lhs - rhs) / np.linalg.norm(rhs) < 1e-13
+    X = oracle.doppler(d, x, window=np.ones(16))
+    np.testing.assert_allclose(np.sum(np.abs(X) ** 2, axis=1), 16 * np.sum(np.abs(x) ** 2, axis=1),
+                               rtol=1e-12)
+
+
+def test_doppler_range_window_is_a_slice():
+    d = dims(C=2, P=8, K=16, R=32, T=1, B=8, S=1)
+    x = crandn(2, 8, 32)
+    full = oracle.doppler(d, x)
+    part = oracle.doppler(d, x, r0=8, nr=16)
+    np.testing.assert_array_equal(part, full[:, :, 8:24])
+
+
+# ---------------------------------------------------------------- snapshot ---
+
+@pytest.mark.parametrize("T", [1, 2, 3, 4])
+def test_snapshot_index_mapping(T):
+    """dop values encode their own (c, k, r): the snapshot must read channel c
+    of bin (k + t - floor(T/2)) mod K at entry t*C + c."""
+    C, K, R = 3, 8, 5
+    d = dims(C=C, P=8, K=K, R=R, T=T, B=5, S=1)
+    c, k, r = np.meshgrid(np.arange(C), np.arange(K), np.arange(R), indexing="ij")
+    dop = (c + 10 * k + 1000 * r) + 1j * (r - c)
+    for kk in (0, 1, K - 1):
+        for rr in (0, R - 1):
+            x = oracle.snapshot(d, dop, kk, rr)
+            for t in range(T):
+                for cc in range(C):
+                    kb = (kk + t - T // 2) % K
+                    assert x[t * C + cc] == (cc + 10 * kb + 1000 * rr) + 1j * (rr - cc)
+
+
+# ---------------------------------------------------------------- covariance -
+
+def _gather(dop, T):
+    """x[k, r, t*C + c] = dop[c, (k + t - T//2) % K, r], by numpy indexing."""
+    C, K, R = dop.shape
+    x = np.empty((K, R, T * C), np.complex128)
+    for t in range(T):
+        kk = (np.arange(K) + t - T // 2) % K
+        x[:, :, t * C:(t + 1) * C] = dop[:, kk, :].transpose(1, 2, 0)
+    return x
+
+
+def test_covariance_equals_blocked_outer_products():
+    d = dims(C=3, P=8, K=8, R=48, T=3, B=16, S=1)
+    dop = crandn(3, 8, 48)
+    cov = oracle.covariance(d, dop)
+    x = _gather(dop, 3).reshape(8, 3, 16, 9)                    # [K][NB][B][D]
+    ref = np.einsum("kbri,kbrj->kbij", x, x.conj()) / 16
+    assert cov.shape == (8, 3, 9, 9)
+    assert np.max(np.abs(cov - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+def test_covariance_hermitian_psd_trace_rank():
+    d = dims(C=2, P=4, K=4, R=12, T=3, B=4, S=1)                 # B=4 < D=6
+    dop = crandn(2, 4, 12) * 10.0
+    cov = oracle.covariance(d, dop)
+    x = _gather(dop, 3).reshape(4, 3, 4, 6)
+    for k in range(4):
+        for b in range(3):
+            Rm = cov[k, b]
+            np.testing.assert_array_equal(Rm, Rm.conj().T)
+            ev = np.linalg.eigvalsh(Rm)
+            tr = np.trace(Rm).real
+            assert ev.min() > -1e-12 * tr
+            assert np.sum(ev > 1e-10 * tr) <= 4                 # rank <= B
+            np.testing.assert_allclose(tr, np.mean(np.sum(np.abs(x[k, b]) ** 2, axis=1)),
+                                       rtol=1e-13)
+
+
+def _true_covariance(d, cnr_db, k):
+    """Covariance of the snapshot at bin k under the synthetic data model:
+    unit white noise through the window plus the 64-patch clutter ridge."""
+    C, P, K, T = d.n_chan, d.n_pulses, d.n_dop, d.tdof
+    h = np.hanning(P)
+    p = np.arange(P)
+    m = np.arange(T) - T // 2
+    Rn = np.zeros((T * C, T * C), np.complex128)
+    for t1 in range(T):
+        for t2 in range(T):
+            val = np.sum(h * h * np.exp(-2j * np.pi * p * (m[t1] - m[t2]) / K))
+            for c in range(C):
+                Rn[t1 * C + c, t2 * C + c] = val
+    f = synth.patch_frequencies()
+    Rc = np.zeros_like(Rn)
+    for fi in f:
+        Hb = np.array([np.sum(h * np.exp(2j * np.pi * p * (fi - (k + mt) / K))) for mt in m])
+        z = (Hb[:, None] * np.exp(2j * np.pi * fi * np.arange(C))[None, :]).reshape(-1)
+        Rc += (10 ** (cnr_db / 10) / synth.N_PATCH) * np.outer(z, z.conj())
+    return Rn + Rc
+
+
+def test_covariance_converges_to_data_model_covariance():
+    """With one long training block the estimate approaches the analytic
+    covariance of noise + clutter ridge; a sign slip in the DFT, a wrong bin
+    offset or a missing 1/B fails this by orders of magnitude."""
+    spec = synth.CPISpec(2, 16, 16, 8192, 3, 8192, 1, cnr_db=10.0, seed=77)
+    d = oracle.Dims(*spec.dims())
+    cube = synth.make_cube(spec)
+    dop = oracle.doppler(d, cube)
+    cov = oracle.covariance(d, dop)
+    for k in (0, 3, 8, 13):
+        Rt = _true_covariance(d, 10.0, k)
+        err = np.linalg.norm(cov[k, 0] - Rt) / np.linalg.norm(Rt)
+        assert err < 5.0 / np.sqrt(8192), (k, err)
+
+
+# ---------------------------------------------------------------- cholesky ---
+
+def _hpd(n, cond=1e3):
+    Q, _ = np.linalg.qr(crandn(n, n))
+    ev = np.logspace(0, np.log10(cond), n)
+    return (Q * ev) @ Q.conj().T
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 12, 33])
+def test_cholesky_reconstructs_and_matches_numpy(n):
+    A = _hpd(n)
+    A = 0.5 * (A + A.conj().T)
+    L = oracle.cholesky(A)
+    assert np.all(np.triu(L, 1) == 0)
+    assert np.all(np.diag(L).real > 0) and np.all(np.diag(L).imag == 0)
+    assert np.linalg.norm(L @ L.conj().T - A) / np.linalg.norm(A) < 1e-12
+    np.testing.assert_allclose(L, np.linalg.cholesky(A), rtol=0, atol=1e-11 * np.abs(L).max())
+
+
+def test_cholesky_rejects_indefinite():
+    A = np.diag([2.0, -1.0, 3.0]).astype(np.complex128)
+    with pytest.raises(ValueError, match="column 1"):
+        oracle.cholesky(A)
+
+
+class _Q:
+    """Exact complex rational."""
+
+    def __init__(self, re, im=0):
+        self.re, self.im = Fraction(re), Fraction(im)
+
+    def __add__(self, o):
+        return _Q(self.re + o.re, self.im + o.im)
+
+    def __sub__(self, o):
+        return _Q(self.re - o.re, self.im - o.im)
+
+    def __mul__(self, o):
+        return _Q(self.re * o.re - self.im * o.im, self.re * o.im + self.im * o.re)
+
+    def __truediv__(self, o):
+        den = o.re * o.re + o.im * o.im
+        return _Q((self.re * o.re + self.im * o.im) / den, (self.im * o.re - self.re * o.im) / den)
+
+    def is_zero(self):
+        return self.re == 0 and self.im == 0
+
+
+def _exact_solve(A, b):
+    """Gauss-Jordan elimination in exact rational arithmetic."""
+    n = len(b)
+    M = [[_Q(int(A[i, j].real), int(A[i, j].imag)) for j in range(n)] +
+         [_Q(int(b[i].real), int(b[i].imag))] for i in range(n)]
+    for col in range(n):
+        piv = next(r for r in range(col, n) if not M[r][col].is_zero())
+        M[col], M[piv] = M[piv], M[col]
+        pv = M[col][col]
+        M[col] = [v / pv for v in M[col]]
+        for r in range(n):
+            if r != col and not M[r][col].is_zero():
+                f = M[r][col]
+                M[r] = [a - f * c for a, c in zip(M[r], M[col])]
+    return np.array([float(M[i][n].re) + 1j * float(M[i][n].im) for i in range(n)])
+
+
+@pytest.mark.parametrize("n", [2, 4, 6])
+def test_cholesky_solve_matches_exact_rational_solution(n):
+    rng = np.random.default_rng(n)
+    M = rng.integers(-3, 4, (n, n)) + 1j * rng.integers(-3, 4, (n, n))
+    A = M @ M.conj().T + n * np.eye(n)                           # Gaussian-integer HPD
+    b = rng.integers(-5, 6, n) + 1j * rng.integers(-5, 6, n)
+    u = oracle.cholesky_solve(oracle.cholesky(A), b)
+    ref = _exact_solve(A, b)
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) < 1e-13
+    np.testing.assert_allclose(u, np.linalg.solve(A, b), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- steering ---
+
+@pytest.mark.parametrize("C,P,K,T,S,s0,k0", [(4, 32, 32, 3, 4, 2, 24), (3, 20, 64, 4, 5, 0, 1),
+                                              (2, 16, 16, 2, 3, 1, 15)])
+def test_default_steering_is_noise_free_target_snapshot(C, P, K, T, S, s0, k0):
+    """A unit target at a bin centre on the steering grid has snapshot v_{s0}."""
+    spec = synth.CPISpec(C, P, K, 8, T, 8, S, cnr_db=None, noise=False,
+                         targets=(synth.Target(5, k0, s0, 0.0, 0.0),))
+    d = oracle.Dims(*spec.dims())
+    cube = synth.make_cube(spec).astype(np.complex128)
+    # regenerate the target in float64 to avoid the complex64 rounding of the cube
+    th = np.deg2rad(synth.steering_angle_deg(s0, S))
+    cube[:, :, 5] = np.exp(2j * np.pi * 0.5 * np.sin(th) * np.arange(C))[:, None] * \
+        np.exp(2j * np.pi * k0 / K * np.arange(P))[None, :]
+    dop = oracle.doppler(d, cube)
+    x = oracle.snapshot(d, dop, k0, 5)
+    v = oracle.default_steering(d)[s0]
+    np.testing.assert_allclose(x, v, rtol=0, atol=1e-12 * np.abs(v).max())
+
+
+def test_default_steering_angles_and_temporal_part():
+    d = dims(C=5, P=12, K=24, T=3, S=6)
+    st = oracle.default_steering(d)
+    h = np.hanning(12)
+    for s in range(6):
+        th = np.deg2rad(-90 + 180 * (s + 0.5) / 6)
+        a = np.exp(2j * np.pi * 0.5 * np.sin(th) * np.arange(5))
+        g = np.array([np.sum(h * np.exp(-2j * np.pi * m * np.arange(12) / 24)) for m in (-1, 0, 1)])
+        np.testing.assert_allclose(st[s], np.kron(g, a), rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- weights ----
+
+def test_weights_white_noise_closed_form():
+    """R = sigma^2 I: w_s = v_s / (sigma sqrt(1 + lf) ||v_s||)."""
+    d = dims(C=3, P=16, K=16, T=2, S=5)
+    sig2, lf = 2.5, 1e-3
+    cov = np.broadcast_to(sig2 * np.eye(6), (4, 6, 6)).astype(np.complex128)
+    w, status, nf = oracle.weights(d, cov, load_factor=lf)
+    assert nf == 0 and np.all(status == 0)
+    v = oracle.default_steering(d)
+    ref = v / (np.sqrt(sig2 * (1 + lf)) * np.linalg.norm(v, axis=1, keepdims=True))
+    for i in range(4):
+        np.testing.assert_allclose(w[i], ref, rtol=1e-13)
+
+
+def test_weights_unit_noise_gain_and_optimal_sinr():
+    """w = R^{-1} v / sqrt(v^H R^{-1} v): w^H R w = 1 and |w^H v|^2 = v^H R^{-1} v
+    (the optimal output SINR for a unit target), here with no loading."""
+    d = dims(C=2, P=8, K=8, T=3, S=3)
+    R = _hpd(6, cond=1e4)
+    R = 0.5 * (R + R.conj().T)
+    steer = crandn(3, 6)
+    w, _, _ = oracle.weights(d, R[None], steer=steer, load_factor=0.0)
+    for s in range(3):
+        ws = w[0, s]
+        np.testing.assert_allclose((ws.conj() @ R @ ws).real, 1.0, rtol=1e-10)
+        sinr = np.real(steer[s].conj() @ np.linalg.solve(R, steer[s]))
+        np.testing.assert_allclose(np.abs(ws.conj() @ steer[s]) ** 2, sinr, rtol=1e-10)
+
+
+def test_weights_loading_uses_trace_over_D():
+    d = dims(C=2, P=8, K=8, T=1, S=2)
+    R = _hpd(2)
+    R = 0.5 * (R + R.conj().T)
+    steer = crandn(2, 2)
+    lf = 0.37
+    w, _, _ = oracle.weights(d, R[None], steer=steer, load_factor=lf)
+    Rl = R + lf * np.trace(R).real / 2 * np.eye(2)
+    for s in range(2):
+        u = np.linalg.solve(Rl, steer[s])
+        np.testing.assert_allclose(w[0, s], u / np.sqrt(np.real(steer[s].conj() @ u)), rtol=1e-12)
+
+
+def test_weights_flag_indefinite_system():
+    d = dims(C=1, P=8, K=8, T=2, S=2)
+    good = np.eye(2, dtype=np.complex128)
+    bad = np.diag([1.0, -5.0]).astype(np.complex128)
+    w, status, nf = oracle.weights(d, np.stack([good, bad, good]), load_factor=0.0)
+    assert nf == 1 and list(status) == [0, 2, 0]
+    assert np.all(w[1] == 0) and np.all(np.isfinite(w))
+
+
+# ---------------------------------------------------------------- apply ------
+
+def test_apply_matches_einsum_and_unit_vector_weights():
+    d = dims(C=2, P=8, K=8, R=32, T=2, B=8, S=3)
+    dop = crandn(2, 8, 32)
+    wts = crandn(8, 4, 3, 4)
+    out = oracle.apply(d, dop, wts)
+    x = _gather(dop, 2)                                         # [K][R][D]
+    wb = np.repeat(wts, 8, axis=1)                              # [K][R][S][D]
+    ref = np.abs(np.einsum("krsd,krd->skr", wb.conj(), x)) ** 2
+    np.testing.assert_allclose(out, ref, rtol=1e-12)
+    e = np.zeros((8, 4, 3, 4), np.complex128)
+    e[..., 0, 1] = 1.0                                          # steering 0 picks entry 1
+    out = oracle.apply(d, dop, e)
+    np.testing.assert_allclose(out[0], np.abs(x[:, :, 1]) ** 2, rtol=1e-15)
+    assert np.all(out[1:] == 0)
+
+
+# ---------------------------------------------------------------- whole path -
+
+def test_run_is_composition_of_steps_and_windows_are_slices():
+    spec = synth.CPISpec(3, 16, 32, 128, 3, 32, 4, cnr_db=30.0,
+                         targets=(synth.Target(40, 7, 1, 10.0),), seed=9)
+    d = oracle.Dims(*spec.dims())
+    cube = synth.make_cube(spec)
+    res = oracle.run(d, cube, keep=True)
+    dop = oracle.doppler(d, cube)
+    cov = oracle.covariance(d, dop)
+    w, _, _ = oracle.weights(d, cov)
+    out = oracle.apply(d, dop, w)
+    np.testing.assert_array_equal(res["dop"], dop)
+    np.testing.assert_array_equal(res["cov"], cov)
+    np.testing.assert_array_equal(res["wts"], w)
+    np.testing.assert_array_equal(res["out"], out)
+    part = oracle.run(d, cube, r0=64, nr=32)
+    np.testing.assert_array_equal(part["out"], res["out"][:, :, 64:96])
+
+
+def test_small_workload_recovers_injected_target():
+    """The small workload's 10 dB target at (range 128, bin 24, steering 2) is the
+    strongest cell of its Doppler/steering row and > 10 dB above the median."""
+    spec = synth.small_cpi()
+    d = oracle.Dims(*spec.dims())
+    res = oracle.run(d, synth.make_cube(spec))
+    P = res["out"]
+    assert res["n_failed"] == 0
+    assert int(np.argmax(P[2, 24])) == 128
+    assert 10 * np.log10(P[2, 24, 128] / np.median(P)) > 10.0
+
+
+def test_noise_only_output_mean_near_one():
+    """AMF output on noise alone has mean close to 1 (a little below, since the
+    cell under test is part of its own training block)."""
+    spec = synth.CPISpec(4, 32, 32, 4096, 3, 256, 4, cnr_db=None, seed=21)
+    d = oracle.Dims(*spec.dims())
+    P = oracle.run(d, synth.make_cube(spec))["out"]
+    assert 0.85 < P.mean() < 1.05, P.mean()
