@@ -1,0 +1,161 @@
+/*
+ * stap.h -- C ABI of libstap, a GB300 (sm_103a) implementation of the
+ * Space-Time Adaptive Processing (STAP) radar kernel.
+ *
+ * The operation is the STAP kernel of arXiv 2203.06233, Sec. 4.2 (the kernel
+ * figure: an explicit loop, statement S; an `fft` over a 1-D domain, statement
+ * T; a 2-D x 2-D array multiply, statement U; all fused into one parallel loop
+ * over data cubes) and Sec. 5.3 (the STAP workload: data cubes of pulses x
+ * channels x range samples, throughput in cubes per second).  The paper gives
+ * no formulas; each call below states the post-Doppler reading it implements.
+ *
+ * Notation: C channels, P pulses, K Doppler bins (K >= P), R range cells,
+ * T adjacent-bin degrees of freedom, D = C*T snapshot length, B cells per
+ * training block, NB = R/B blocks, S steering vectors.
+ *
+ * Conventions shared by every call:
+ *  - Buffers are DEVICE pointers owned by the caller, 16-byte aligned, dense
+ *    row-major in the layout given.  Complex values are interleaved (re, im):
+ *    "c64" = 2 x float, "c128" = 2 x double.
+ *  - Calls are asynchronous on the plan's CUDA stream.  Argument, shape and
+ *    alignment errors are returned synchronously and launch nothing.  Errors
+ *    found on the device (a covariance that is not positive definite) are
+ *    counted in the workspace and read back by stap_get_status.
+ *  - No call allocates device memory.  Scratch comes from the caller through
+ *    stap_plan_set_workspace; its contents between calls belong to the plan.
+ *  - No exception crosses the ABI.  A plan is not thread-safe: one host thread
+ *    at a time per plan.
+ */
+#ifndef STAP_H_
+#define STAP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STAP_ABI_VERSION 1
+
+typedef enum {
+  STAP_OK = 0,
+  STAP_ERR_INVALID_ARG = 1,  /* NULL pointer, bad option value, wrong CPI index */
+  STAP_ERR_SHAPE = 2,        /* dims violate K >= P, R % B == 0, 1 <= T <= K, ... */
+  STAP_ERR_UNSUPPORTED = 3,  /* valid STAP shape outside what the kernels handle */
+  STAP_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed */
+  STAP_ERR_NOT_POSDEF = 5,   /* some loaded covariances were not positive definite */
+  STAP_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+  STAP_ERR_NO_WORKSPACE = 7, /* workspace missing or smaller than the call needs */
+  STAP_ERR_MISALIGNED = 8    /* a buffer is not 16-byte aligned */
+} stap_status;
+
+/* Arithmetic of the contraction steps (Doppler, covariance, apply).  The
+ * diagonal loading, Cholesky factorisation and triangular solves are FP64 in
+ * every mode. */
+typedef enum {
+  STAP_PREC_FP32 = 0 /* FP32 FFT; covariance accumulated error-free in FP32
+                        pairs (two-product / compensated sum); FP32 apply */
+} stap_precision;
+
+typedef struct {
+  int32_t n_chan;         /* C >= 1 */
+  int32_t n_pulses;       /* P >= 1 */
+  int32_t n_dop;          /* K >= P, a power of two, K <= 1024 */
+  int32_t n_range;        /* R >= 1, a multiple of B */
+  int32_t tdof;           /* 1 <= T <= K */
+  int32_t training_block; /* B >= 1 */
+  int32_t n_steering;     /* S >= 1 */
+} stap_dims;
+
+typedef struct {
+  double load_factor;   /* diagonal load delta = load_factor * Re tr(R) / D; >= 0 (default 1e-3) */
+  int32_t refine_steps; /* iterative-refinement steps after the FP64 solve, 0..4 (default 1) */
+  int32_t precision;    /* a stap_precision value (default STAP_PREC_FP32) */
+} stap_options;
+
+typedef struct stap_plan_s* stap_plan;
+
+/* Fill *opt with the defaults (load_factor 1e-3, refine_steps 1, FP32). */
+void stap_options_default(stap_options* opt);
+
+/* Create a plan for n_cpi CPIs whose shapes are dims[0 .. n_cpi-1].
+ * opt may be NULL (defaults).  cuda_stream is a cudaStream_t (NULL = legacy
+ * default stream).  On success *out is the plan and, if workspace_bytes is not
+ * NULL, *workspace_bytes the device workspace stap_run_cpi needs (the
+ * step-by-step calls need less, see stap_plan_workspace_sizes).  Host-only:
+ * makes no CUDA call.  Sets the default steering table of every CPI:
+ *   theta_s = -90 + 180 (s + 1/2)/S degrees, f_s = sin(theta_s)/2,
+ *   a_c = exp(j 2 pi f_s c),  g_t = sum_p h[p] exp(-j 2 pi (t - floor(T/2)) p / K),
+ *   v_s[t*C + c] = g_t a_c   (h = symmetric Hann of length P). */
+stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_options* opt,
+                             void* cuda_stream, stap_plan* out, size_t* workspace_bytes);
+
+/* step_bytes: workspace needed by the step-by-step calls (tables and status);
+ * run_bytes: workspace needed by stap_run_cpi (adds the intermediates of the
+ * largest CPI).  Either pointer may be NULL. */
+stap_status stap_plan_workspace_sizes(stap_plan plan, size_t* step_bytes, size_t* run_bytes);
+
+/* Hand the plan a device workspace of `bytes` bytes (16-byte aligned, caller-
+ * owned, kept until destroy or the next call of this function).  Uploads the
+ * plan's tables on the plan's stream and clears the device status. */
+stap_status stap_plan_set_workspace(stap_plan plan, void* dev_ptr, size_t bytes);
+
+/* Change the stream later calls are issued on. */
+stap_status stap_plan_set_stream(stap_plan plan, void* cuda_stream);
+
+/* Replace the steering table of CPI `cpi` with host_c128[S][D] (copied).
+ * Needs the workspace to be set (the table is uploaded on the plan's stream). */
+stap_status stap_plan_set_steering(stap_plan plan, int32_t cpi, const double* host_c128);
+
+stap_status stap_plan_destroy(stap_plan plan);
+
+/* Statement T (Sec. 4.2): Hann-windowed DFT over pulses, zero-padded to K.
+ *   dop[c][k][r] = sum_{p<P} h[p] cube[c][p][r] exp(-j 2 pi p k / K)
+ * cube: c64 [C][P][R]; dop: c64 [C][K][R].  Single-CPI plans only. */
+stap_status stap_doppler(stap_plan plan, const void* cube_c64, void* dop_c64);
+
+/* Statement U (Sec. 4.2), one covariance per (Doppler bin k, range block b):
+ *   x_{k,r}[t*C + c] = dop[c][(k + t - floor(T/2)) mod K][r]
+ *   cov[k][b] = (1/B) sum_{r = bB}^{bB+B-1} x_{k,r} x_{k,r}^H
+ * dop: c64 [C][K][R]; cov: c128 [K][NB][D][D], full Hermitian. */
+stap_status stap_covariance(stap_plan plan, const void* dop_c64, void* cov_c128);
+
+/* Adaptive weights per (k, b) and steering vector v_s, all in FP64:
+ *   delta = load_factor * Re tr(cov) / D,  Rl = cov + delta I = L L^H,
+ *   u_s = Rl^{-1} v_s by forward/back substitution, refine_steps refinement
+ *   steps u_s += Rl^{-1} (v_s - Rl u_s),  w_s = u_s / sqrt(Re v_s^H u_s).
+ * Only the lower triangle and the real part of the diagonal of each cov are
+ * read.  A system whose pivot is not positive and finite gets zero weights
+ * and is counted (stap_get_status).  cov: c128 [K][NB][D][D];
+ * wts: c64 [K][NB][S][D]. */
+stap_status stap_solve_weights(stap_plan plan, const void* cov_c128, void* wts_c64);
+
+/* Output power of every range-Doppler cell:
+ *   out[s][k][r] = | w_{k, r/B, s}^H x_{k,r} |^2
+ * dop: c64 [C][K][R]; wts: c64 [K][NB][S][D]; out: float [S][K][R]. */
+stap_status stap_apply(stap_plan plan, const void* dop_c64, const void* wts_c64, float* out);
+
+/* The whole chain (Doppler, covariance, weights, apply) for every CPI of the
+ * plan, with the intermediates in the workspace and no host round trip.
+ * cubes[i]: c64 [C_i][P_i][R_i]; outs[i]: float [S_i][K_i][R_i]; both arrays
+ * are HOST arrays of n_cpi device pointers. */
+stap_status stap_run_cpi(stap_plan plan, const void* const* cubes, float* const* outs);
+
+/* Wait for the plan's stream, then report and clear the device status.
+ * *n_failed_systems (if not NULL) = covariances found not positive definite
+ * since the last call; returns STAP_ERR_NOT_POSDEF if that is > 0,
+ * STAP_ERR_TIMEOUT if a bounded device wait gave up, else STAP_OK. */
+stap_status stap_get_status(stap_plan plan, int64_t* n_failed_systems);
+
+/* Static description of a status code. */
+const char* stap_status_string(stap_status status);
+
+/* STAP_ABI_VERSION of the loaded library. */
+int32_t stap_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STAP_H_ */

@@ -1,0 +1,158 @@
+// Doppler transform (statement T of the STAP kernel, arXiv 2203.06233 Sec. 4.2):
+//   dop[c][k][r] = sum_{p<P} h[p] cube[c][p][r] exp(-2 pi i p k / K),  K >= P,
+// computed as a zero-padded length-K FFT over the pulse axis.
+//
+// Layout: the pulse axis has stride R, the range axis is contiguous.  A CTA
+// owns one channel and TR consecutive range cells and does TR independent
+// length-K FFTs by the four-step split K = N1 * N2:
+//   input  index n = n1 + N1 n2,   output index k = k2 + N2 k1,
+//   Y[n1][k2] = W_K^{n1 k2} * sum_{n2} x[n1 + N1 n2] W_{N2}^{n2 k2}     (pass A)
+//   X[k2 + N2 k1] = sum_{n1} Y[n1][k2] W_{N1}^{n1 k1}                    (pass B)
+// Each thread does one short FFT in registers per pass; the only shared-memory
+// traffic is the Y transpose between the passes.  Global loads (pass A) and
+// stores (pass B) are coalesced along range: a warp touches 32 (or 16)
+// consecutive complex samples of one pulse/bin row.  The window and the zero
+// padding are applied while loading.  HBM traffic is the algorithmic minimum:
+// 8*C*P*R bytes read + 8*C*K*R bytes written.
+#include "snapshots.cuh"
+
+namespace stap {
+namespace {
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+
+__host__ __device__ constexpr int bitrev(int x, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+  return r;
+}
+
+// In-register radix-2 FFT of length N (forward, natural order in and out).
+// tw[m] = W_K^m; W_N^j = tw[j * (K / N)].
+template <int N, int K>
+__device__ __forceinline__ void fft_reg(float2 (&v)[N], const float2* __restrict__ tw) {
+  constexpr int LOGN = ilog2c(N);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int j = bitrev(i, LOGN);
+    if (i < j) {
+      float2 t = v[i];
+      v[i] = v[j];
+      v[j] = t;
+    }
+  }
+#pragma unroll
+  for (int len = 2; len <= N; len <<= 1) {
+    const int half = len >> 1;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const float2 w = tw[j * (K / len)];
+#pragma unroll
+      for (int st = 0; st < N; st += len) {
+        const float2 a = v[st + j];
+        const float2 b = (j == 0) ? v[st + j + half] : cmulf(v[st + j + half], w);
+        v[st + j] = make_float2(a.x + b.x, a.y + b.y);
+        v[st + j + half] = make_float2(a.x - b.x, a.y - b.y);
+      }
+    }
+  }
+}
+
+template <int LOGK, int TR>
+__global__ void __launch_bounds__(TR * (1 << ((LOGK + 1) / 2)))
+doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
+                   const float* __restrict__ win, const float2* __restrict__ twg, int P, int R) {
+  constexpr int K = 1 << LOGK;
+  constexpr int N1 = 1 << ((LOGK + 1) / 2);
+  constexpr int N2 = 1 << (LOGK / 2);
+  extern __shared__ float2 smem[];
+  float2* tw = smem;        // [K]
+  float2* Y = smem + K;     // [N1][N2][TR]
+
+  const int tid = threadIdx.x;
+  const int c = blockIdx.y;
+  const int r0 = blockIdx.x * TR;
+  for (int m = tid; m < K; m += blockDim.x) tw[m] = twg[m];
+
+  // ---- pass A: thread (col, n1), N2-point FFT over n2 ----
+  {
+    const int col = tid % TR, n1 = tid / TR;
+    const int r = r0 + col;
+    const bool in_range = r < R;
+    const float2* src = cube + (size_t)c * P * R + r;
+    float2 v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+      const int n = n1 + N1 * n2;
+      float2 x = make_float2(0.f, 0.f);
+      if (in_range && n < P) {
+        x = __ldg(src + (size_t)n * R);
+        const float h = __ldg(win + n);
+        x.x *= h;
+        x.y *= h;
+      }
+      v[n2] = x;
+    }
+    __syncthreads();  // twiddle table ready
+    fft_reg<N2, K>(v, tw);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const float2 y = (k2 == 0) ? v[k2] : cmulf(v[k2], tw[n1 * k2]);
+      Y[(n1 * N2 + k2) * TR + col] = y;
+    }
+  }
+  __syncthreads();
+
+  // ---- pass B: thread (col, k2), N1-point FFT over n1 ----
+  if (tid < TR * N2) {
+    const int col = tid % TR, k2 = tid / TR;
+    const int r = r0 + col;
+    float2 u[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) u[n1] = Y[(n1 * N2 + k2) * TR + col];
+    fft_reg<N1, K>(u, tw);
+    if (r < R) {
+      float2* dst = dop + (size_t)c * K * R + r;
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) dst[(size_t)(k2 + N2 * k1) * R] = u[k1];
+    }
+  }
+}
+
+template <int LOGK>
+cudaError_t launch_logk(const float2* cube, float2* dop, const float* win, const float2* tw, int C,
+                        int P, int R, cudaStream_t s) {
+  constexpr int K = 1 << LOGK;
+  constexpr int N1 = 1 << ((LOGK + 1) / 2);
+  constexpr int TR = (N1 >= 32) ? 16 : 32;
+  const size_t smem = (size_t)K * sizeof(float2) * (1 + TR);
+  auto kern = doppler_fft_kernel<LOGK, TR>;
+  static int set_bytes[64] = {0};
+  cudaError_t e = ensure_smem(kern, smem, set_bytes);
+  if (e != cudaSuccess) return e;
+  dim3 grid((R + TR - 1) / TR, C);
+  kern<<<grid, TR * N1, smem, s>>>(cube, dop, win, tw, P, R);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_doppler(const float2* cube, float2* dop, const float* win, const float2* tw,
+                           int C, int P, int K, int R, cudaStream_t s) {
+  switch (ilog2c(K)) {
+    case 0: return launch_logk<0>(cube, dop, win, tw, C, P, R, s);
+    case 1: return launch_logk<1>(cube, dop, win, tw, C, P, R, s);
+    case 2: return launch_logk<2>(cube, dop, win, tw, C, P, R, s);
+    case 3: return launch_logk<3>(cube, dop, win, tw, C, P, R, s);
+    case 4: return launch_logk<4>(cube, dop, win, tw, C, P, R, s);
+    case 5: return launch_logk<5>(cube, dop, win, tw, C, P, R, s);
+    case 6: return launch_logk<6>(cube, dop, win, tw, C, P, R, s);
+    case 7: return launch_logk<7>(cube, dop, win, tw, C, P, R, s);
+    case 8: return launch_logk<8>(cube, dop, win, tw, C, P, R, s);
+    case 9: return launch_logk<9>(cube, dop, win, tw, C, P, R, s);
+    case 10: return launch_logk<10>(cube, dop, win, tw, C, P, R, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace stap

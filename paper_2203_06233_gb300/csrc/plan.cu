@@ -1,0 +1,375 @@
+// Host side of libstap: plan creation and validation, workspace layout,
+// host-computed tables (window, twiddles, default steering) and the C entry
+// points that launch the kernels.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "stap_internal.cuh"
+
+using stap::DeviceStatus;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Cpi {
+  stap_dims d{};
+  int D = 0, NB = 0;
+  // offsets of this CPI's tables inside the workspace
+  size_t win_off = 0, tw_off = 0, steer_off = 0;
+  std::vector<float> win;       // [P]
+  std::vector<float> tw;        // [K][2]
+  std::vector<double> steer;    // [S][D][2]
+  size_t dop_elems() const { return (size_t)d.n_chan * d.n_dop * d.n_range; }
+  size_t cov_elems() const { return (size_t)d.n_dop * NB * D * D; }
+  size_t wts_elems() const { return (size_t)d.n_dop * NB * d.n_steering * D; }
+};
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+stap_status validate(const stap_dims& d) {
+  if (d.n_chan < 1 || d.n_pulses < 1 || d.n_dop < 1 || d.n_range < 1 || d.tdof < 1 ||
+      d.training_block < 1 || d.n_steering < 1)
+    return STAP_ERR_SHAPE;
+  if (d.n_dop < d.n_pulses || d.tdof > d.n_dop || d.n_range % d.training_block != 0)
+    return STAP_ERR_SHAPE;
+  const long long D = (long long)d.n_chan * d.tdof;
+  if (!is_pow2(d.n_dop) || d.n_dop > (1 << stap::kMaxLogK) || D > stap::kMaxD)
+    return STAP_ERR_UNSUPPORTED;
+  // keep every tensor below 2^40 elements and every grid dimension in range
+  const long long NB = d.n_range / d.training_block;
+  if ((long long)d.n_chan * d.n_dop * d.n_range > (1LL << 40) ||
+      (long long)d.n_dop * NB * D * D > (1LL << 40) ||
+      (long long)d.n_dop * NB * d.n_steering * D > (1LL << 40) || d.n_steering > 4096 ||
+      d.training_block > 4096 || d.n_chan > 65535)
+    return STAP_ERR_UNSUPPORTED;
+  return STAP_OK;
+}
+
+void make_tables(Cpi& c) {
+  const stap_dims& d = c.d;
+  const int P = d.n_pulses, K = d.n_dop, T = d.tdof, C = d.n_chan, S = d.n_steering;
+  std::vector<double> h(P);
+  for (int p = 0; p < P; ++p)
+    h[p] = (P == 1) ? 1.0 : 0.5 - 0.5 * std::cos(2.0 * kPi * p / (double)(P - 1));
+  c.win.resize(P);
+  for (int p = 0; p < P; ++p) c.win[p] = (float)h[p];
+  c.tw.resize(2 * (size_t)K);
+  for (int m = 0; m < K; ++m) {
+    const double a = -2.0 * kPi * m / (double)K;
+    c.tw[2 * m] = (float)std::cos(a);
+    c.tw[2 * m + 1] = (float)std::sin(a);
+  }
+  // temporal part: the window's response at the T bin offsets around the bin
+  std::vector<double> gr(T), gi(T);
+  for (int t = 0; t < T; ++t) {
+    const long long m = t - T / 2;
+    double sr = 0, si = 0;
+    for (int p = 0; p < P; ++p) {
+      long long n = (m * p) % K;
+      if (n < 0) n += K;
+      const double a = -2.0 * kPi * (double)n / (double)K;
+      sr += h[p] * std::cos(a);
+      si += h[p] * std::sin(a);
+    }
+    gr[t] = sr;
+    gi[t] = si;
+  }
+  const int D = c.D;
+  c.steer.assign(2 * (size_t)S * D, 0.0);
+  for (int s = 0; s < S; ++s) {
+    const double th = (-90.0 + 180.0 * (s + 0.5) / S) * kPi / 180.0;
+    const double fs = 0.5 * std::sin(th);
+    for (int t = 0; t < T; ++t)
+      for (int ch = 0; ch < C; ++ch) {
+        const double a = 2.0 * kPi * fs * ch;
+        const double ar = std::cos(a), ai = std::sin(a);
+        double* v = &c.steer[2 * ((size_t)s * D + t * C + ch)];
+        v[0] = gr[t] * ar - gi[t] * ai;
+        v[1] = gr[t] * ai + gi[t] * ar;
+      }
+  }
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+struct stap_plan_s {
+  std::vector<Cpi> cpis;
+  stap_options opt{};
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  size_t step_bytes = 0, run_bytes = 0;
+  size_t dop_off = 0, cov_off = 0, wts_off = 0;   // run intermediates (sized for the largest CPI)
+  bool tables_ready = false;
+
+  DeviceStatus* status() const { return reinterpret_cast<DeviceStatus*>(ws); }
+  template <typename Tp>
+  Tp* at(size_t off) const { return reinterpret_cast<Tp*>(ws + off); }
+};
+
+namespace {
+
+stap_status upload_tables(stap_plan p, int only_cpi = -1) {
+  for (size_t i = 0; i < p->cpis.size(); ++i) {
+    if (only_cpi >= 0 && (int)i != only_cpi) continue;
+    const Cpi& c = p->cpis[i];
+    if (cudaMemcpyAsync(p->ws + c.win_off, c.win.data(), c.win.size() * sizeof(float),
+                        cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(p->ws + c.tw_off, c.tw.data(), c.tw.size() * sizeof(float),
+                        cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(p->ws + c.steer_off, c.steer.data(), c.steer.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+      return STAP_ERR_CUDA;
+  }
+  return STAP_OK;
+}
+
+stap_status check_launch(cudaError_t e) { return e == cudaSuccess ? STAP_OK : STAP_ERR_CUDA; }
+
+stap_status ready(stap_plan p, size_t need) {
+  if (!p) return STAP_ERR_INVALID_ARG;
+  if (!p->ws || !p->tables_ready || p->ws_bytes < need) return STAP_ERR_NO_WORKSPACE;
+  return STAP_OK;
+}
+
+// ----- the four steps on one CPI (arguments already validated) --------------
+
+stap_status do_doppler(stap_plan p, const Cpi& c, const void* cube, void* dop) {
+  const stap_dims& d = c.d;
+  return check_launch(stap::launch_doppler(
+      static_cast<const float2*>(cube), static_cast<float2*>(dop), p->at<const float>(c.win_off),
+      p->at<const float2>(c.tw_off), d.n_chan, d.n_pulses, d.n_dop, d.n_range, p->stream));
+}
+
+stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov) {
+  const stap_dims& d = c.d;
+  return check_launch(stap::launch_covariance_fp32(static_cast<const float2*>(dop),
+                                                   static_cast<double2*>(cov), d.n_chan, d.n_dop,
+                                                   d.n_range, d.tdof, d.training_block, p->stream));
+}
+
+stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts) {
+  const stap_dims& d = c.d;
+  return check_launch(stap::launch_solve(
+      static_cast<const double2*>(cov), static_cast<float2*>(wts),
+      p->at<const double2>(c.steer_off), (long long)d.n_dop * c.NB, c.D, d.n_steering,
+      p->opt.load_factor, p->opt.refine_steps, p->status(), p->stream));
+}
+
+stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts, float* out) {
+  const stap_dims& d = c.d;
+  return check_launch(stap::launch_apply(static_cast<const float2*>(dop),
+                                         static_cast<const float2*>(wts), out, d.n_chan, d.n_dop,
+                                         d.n_range, d.tdof, d.training_block, d.n_steering,
+                                         p->stream));
+}
+
+stap_status single_cpi(stap_plan p) {
+  if (!p) return STAP_ERR_INVALID_ARG;
+  return p->cpis.size() == 1 ? STAP_OK : STAP_ERR_INVALID_ARG;
+}
+
+}  // namespace
+
+extern "C" {
+
+void stap_options_default(stap_options* opt) {
+  if (!opt) return;
+  opt->load_factor = 1e-3;
+  opt->refine_steps = 1;
+  opt->precision = STAP_PREC_FP32;
+}
+
+int32_t stap_abi_version(void) { return STAP_ABI_VERSION; }
+
+const char* stap_status_string(stap_status s) {
+  switch (s) {
+    case STAP_OK: return "ok";
+    case STAP_ERR_INVALID_ARG: return "invalid argument";
+    case STAP_ERR_SHAPE: return "invalid STAP shape";
+    case STAP_ERR_UNSUPPORTED: return "shape or option not supported by the kernels";
+    case STAP_ERR_CUDA: return "CUDA error";
+    case STAP_ERR_NOT_POSDEF: return "loaded covariance not positive definite";
+    case STAP_ERR_TIMEOUT: return "device-side wait timed out";
+    case STAP_ERR_NO_WORKSPACE: return "workspace missing or too small";
+    case STAP_ERR_MISALIGNED: return "buffer not 16-byte aligned";
+  }
+  return "unknown status";
+}
+
+stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_options* opt,
+                             void* cuda_stream, stap_plan* out, size_t* workspace_bytes) {
+  if (!dims || !out || n_cpi < 1) return STAP_ERR_INVALID_ARG;
+  *out = nullptr;
+  stap_options o;
+  stap_options_default(&o);
+  if (opt) o = *opt;
+  if (!(o.load_factor >= 0.0) || !std::isfinite(o.load_factor) || o.refine_steps < 0 ||
+      o.refine_steps > 4)
+    return STAP_ERR_INVALID_ARG;
+  if (o.precision != STAP_PREC_FP32) return STAP_ERR_UNSUPPORTED;
+  for (int i = 0; i < n_cpi; ++i) {
+    stap_status st = validate(dims[i]);
+    if (st != STAP_OK) return st;
+  }
+  stap_plan p = new (std::nothrow) stap_plan_s;
+  if (!p) return STAP_ERR_INVALID_ARG;
+  p->opt = o;
+  p->stream = static_cast<cudaStream_t>(cuda_stream);
+  p->cpis.resize(n_cpi);
+  size_t off = align_up(sizeof(DeviceStatus));
+  size_t max_dop = 0, max_cov = 0, max_wts = 0;
+  for (int i = 0; i < n_cpi; ++i) {
+    Cpi& c = p->cpis[i];
+    c.d = dims[i];
+    c.D = c.d.n_chan * c.d.tdof;
+    c.NB = c.d.n_range / c.d.training_block;
+    make_tables(c);
+    c.win_off = off;
+    off = align_up(off + c.win.size() * sizeof(float));
+    c.tw_off = off;
+    off = align_up(off + c.tw.size() * sizeof(float));
+    c.steer_off = off;
+    off = align_up(off + c.steer.size() * sizeof(double));
+    if (c.dop_elems() > max_dop) max_dop = c.dop_elems();
+    if (c.cov_elems() > max_cov) max_cov = c.cov_elems();
+    if (c.wts_elems() > max_wts) max_wts = c.wts_elems();
+  }
+  p->step_bytes = off;
+  p->dop_off = off;
+  off = align_up(off + max_dop * 8);
+  p->cov_off = off;
+  off = align_up(off + max_cov * 16);
+  p->wts_off = off;
+  off = align_up(off + max_wts * 8);
+  p->run_bytes = off;
+  *out = p;
+  if (workspace_bytes) *workspace_bytes = p->run_bytes;
+  return STAP_OK;
+}
+
+stap_status stap_plan_workspace_sizes(stap_plan p, size_t* step_bytes, size_t* run_bytes) {
+  if (!p) return STAP_ERR_INVALID_ARG;
+  if (step_bytes) *step_bytes = p->step_bytes;
+  if (run_bytes) *run_bytes = p->run_bytes;
+  return STAP_OK;
+}
+
+stap_status stap_plan_set_workspace(stap_plan p, void* dev_ptr, size_t bytes) {
+  if (!p || !dev_ptr) return STAP_ERR_INVALID_ARG;
+  if (!aligned16(dev_ptr)) return STAP_ERR_MISALIGNED;
+  if (bytes < p->step_bytes) return STAP_ERR_NO_WORKSPACE;
+  p->ws = static_cast<char*>(dev_ptr);
+  p->ws_bytes = bytes;
+  p->tables_ready = false;
+  if (cudaMemsetAsync(p->ws, 0, sizeof(DeviceStatus), p->stream) != cudaSuccess) return STAP_ERR_CUDA;
+  stap_status st = upload_tables(p);
+  if (st != STAP_OK) return st;
+  p->tables_ready = true;
+  return STAP_OK;
+}
+
+stap_status stap_plan_set_stream(stap_plan p, void* cuda_stream) {
+  if (!p) return STAP_ERR_INVALID_ARG;
+  p->stream = static_cast<cudaStream_t>(cuda_stream);
+  return STAP_OK;
+}
+
+stap_status stap_plan_set_steering(stap_plan p, int32_t cpi, const double* host_c128) {
+  if (!p || !host_c128 || cpi < 0 || cpi >= (int32_t)p->cpis.size()) return STAP_ERR_INVALID_ARG;
+  if (!p->ws || !p->tables_ready) return STAP_ERR_NO_WORKSPACE;
+  Cpi& c = p->cpis[cpi];
+  for (size_t i = 0; i < c.steer.size(); ++i)
+    if (!std::isfinite(host_c128[i])) return STAP_ERR_INVALID_ARG;
+  std::memcpy(c.steer.data(), host_c128, c.steer.size() * sizeof(double));
+  return upload_tables(p, cpi);
+}
+
+stap_status stap_plan_destroy(stap_plan p) {
+  if (!p) return STAP_ERR_INVALID_ARG;
+  // pageable-memory uploads were staged synchronously, so nothing on the
+  // device still reads the host tables
+  delete p;
+  return STAP_OK;
+}
+
+stap_status stap_doppler(stap_plan p, const void* cube, void* dop) {
+  stap_status st = single_cpi(p);
+  if (st != STAP_OK) return st;
+  if (!cube || !dop) return STAP_ERR_INVALID_ARG;
+  if (!aligned16(cube) || !aligned16(dop)) return STAP_ERR_MISALIGNED;
+  if ((st = ready(p, p->step_bytes)) != STAP_OK) return st;
+  return do_doppler(p, p->cpis[0], cube, dop);
+}
+
+stap_status stap_covariance(stap_plan p, const void* dop, void* cov) {
+  stap_status st = single_cpi(p);
+  if (st != STAP_OK) return st;
+  if (!dop || !cov) return STAP_ERR_INVALID_ARG;
+  if (!aligned16(dop) || !aligned16(cov)) return STAP_ERR_MISALIGNED;
+  if ((st = ready(p, p->step_bytes)) != STAP_OK) return st;
+  return do_covariance(p, p->cpis[0], dop, cov);
+}
+
+stap_status stap_solve_weights(stap_plan p, const void* cov, void* wts) {
+  stap_status st = single_cpi(p);
+  if (st != STAP_OK) return st;
+  if (!cov || !wts) return STAP_ERR_INVALID_ARG;
+  if (!aligned16(cov) || !aligned16(wts)) return STAP_ERR_MISALIGNED;
+  if ((st = ready(p, p->step_bytes)) != STAP_OK) return st;
+  return do_solve(p, p->cpis[0], cov, wts);
+}
+
+stap_status stap_apply(stap_plan p, const void* dop, const void* wts, float* out) {
+  stap_status st = single_cpi(p);
+  if (st != STAP_OK) return st;
+  if (!dop || !wts || !out) return STAP_ERR_INVALID_ARG;
+  if (!aligned16(dop) || !aligned16(wts) || !aligned16(out)) return STAP_ERR_MISALIGNED;
+  if ((st = ready(p, p->step_bytes)) != STAP_OK) return st;
+  return do_apply(p, p->cpis[0], dop, wts, out);
+}
+
+stap_status stap_run_cpi(stap_plan p, const void* const* cubes, float* const* outs) {
+  if (!p || !cubes || !outs) return STAP_ERR_INVALID_ARG;
+  for (size_t i = 0; i < p->cpis.size(); ++i) {
+    if (!cubes[i] || !outs[i]) return STAP_ERR_INVALID_ARG;
+    if (!aligned16(cubes[i]) || !aligned16(outs[i])) return STAP_ERR_MISALIGNED;
+  }
+  stap_status st = ready(p, p->run_bytes);
+  if (st != STAP_OK) return st;
+  void* dop = p->ws + p->dop_off;
+  void* cov = p->ws + p->cov_off;
+  void* wts = p->ws + p->wts_off;
+  for (size_t i = 0; i < p->cpis.size(); ++i) {
+    const Cpi& c = p->cpis[i];
+    if ((st = do_doppler(p, c, cubes[i], dop)) != STAP_OK) return st;
+    if ((st = do_covariance(p, c, dop, cov)) != STAP_OK) return st;
+    if ((st = do_solve(p, c, cov, wts)) != STAP_OK) return st;
+    if ((st = do_apply(p, c, dop, wts, outs[i])) != STAP_OK) return st;
+  }
+  return STAP_OK;
+}
+
+stap_status stap_get_status(stap_plan p, int64_t* n_failed) {
+  if (!p) return STAP_ERR_INVALID_ARG;
+  if (!p->ws) return STAP_ERR_NO_WORKSPACE;
+  DeviceStatus h{};
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return STAP_ERR_CUDA;
+  if (cudaMemcpyAsync(&h, p->ws, sizeof(h), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+      cudaMemsetAsync(p->ws, 0, sizeof(DeviceStatus), p->stream) != cudaSuccess ||
+      cudaStreamSynchronize(p->stream) != cudaSuccess)
+    return STAP_ERR_CUDA;
+  if (n_failed) *n_failed = (int64_t)h.n_failed;
+  if (h.timeout) return STAP_ERR_TIMEOUT;
+  return h.n_failed ? STAP_ERR_NOT_POSDEF : STAP_OK;
+}
+
+}  // extern "C"

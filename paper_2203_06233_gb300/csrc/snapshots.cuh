@@ -1,0 +1,42 @@
+// Space-time snapshot gather shared by the covariance and apply kernels.
+//   x_{k,r}[t*C + c] = dop[c][(k + t - floor(T/2)) mod K][r]
+// The snapshot tensor is never materialised in HBM: each CTA stages the
+// D x ncells tile it needs into shared memory, row d = t*C + c contiguous in
+// range, with leading dimension ld (padded so that reads of different rows at
+// the same cell fall in different banks).
+#pragma once
+
+#include "stap_internal.cuh"
+
+namespace stap {
+
+__device__ __forceinline__ void stage_snapshots(float2* __restrict__ xs, int ld,
+                                                const float2* __restrict__ dop, int C, int K, int R,
+                                                int T, int k, int r_begin, int ncells) {
+  const int D = C * T;
+  const int total = D * ncells;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int rr = idx % ncells;
+    const int d = idx / ncells;
+    const int t = d / C, c = d - t * C;
+    const int kk = wrap_bin(k + t - T / 2, K);
+    xs[d * ld + rr] = __ldg(dop + ((size_t)c * K + kk) * R + r_begin + rr);
+  }
+}
+
+// Raise a kernel's dynamic shared-memory limit above the 48 KB default, once
+// per device and size (set_bytes: per-device record of the limit already set).
+template <typename F>
+cudaError_t ensure_smem(F* kern, size_t bytes, int* set_bytes /* [64] */) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  dev &= 63;
+  if (set_bytes[dev] >= (int)bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) set_bytes[dev] = (int)bytes;
+  return e;
+}
+
+}  // namespace stap

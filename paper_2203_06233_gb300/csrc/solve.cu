@@ -1,0 +1,240 @@
+// Adaptive weights per (Doppler bin, range block), all in FP64:
+//   delta = lf * Re tr(R) / D,   Rl = R + delta I = L L^H      (diagonal load, Cholesky)
+//   u_s = Rl^{-1} v_s            (forward then back substitution)
+//   u_s += Rl^{-1} (v_s - Rl u_s)   refine_steps times (residual in FP64 from Rl itself)
+//   w_s = u_s / sqrt(Re v_s^H u_s)  (unit noise gain)
+// This is the solve half of the STAP kernel of arXiv 2203.06233 Sec. 4.2 (the
+// paper gives no formulas; this is the standard loaded-sample-matrix reading).
+//
+// Cost model on GB300: FP64 FMA runs at 1/62 of the FP32 rate (1.2 TFLOP/s per
+// GPU measured), and a warp-wide DFMA costs the same whether 1 or 32 lanes are
+// active.  So the kernel is designed around the count of warp-level FP64
+// instructions: every lane of every DFMA does useful work, and everything else
+// (shared-memory traffic, index arithmetic) is free by comparison.
+//
+// Mapping: a warp handles G systems at once, TS = 32/G lanes ("a team") per
+// system.  The team factors its system right-looking in shared memory (packed
+// lower triangle), spreading each trailing update over its lanes, then each
+// lane solves for its own right-hand sides (one steering vector per lane and
+// pass), reading L as a broadcast and keeping its two work vectors in shared
+// memory.  Teams of one warp share all control flow (same D and S), so the
+// warp never diverges except where S is not a multiple of TS.
+#include "snapshots.cuh"
+
+namespace stap {
+namespace {
+
+__device__ __forceinline__ int pidx(int i, int l) { return i * (i + 1) / 2 + l; }
+
+__device__ __forceinline__ void unpack_lower(int q, int& i, int& l) {
+  int r = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+  while (r * (r + 1) / 2 > q) --r;
+  while ((r + 1) * (r + 2) / 2 <= q) ++r;
+  i = r;
+  l = q - r * (r + 1) / 2;
+}
+
+// acc -= a * b
+__device__ __forceinline__ void cfms(double2& acc, double2 a, double2 b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
+// acc -= conj(a) * b
+__device__ __forceinline__ void cfms_conj(double2& acc, double2 a, double2 b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+// Lower-triangle element (i, l) of the loaded matrix Rl, i >= l, from the
+// full input (only the lower triangle and the real diagonal are read).
+__device__ __forceinline__ double2 loaded(const double2* __restrict__ A, int D, int i, int l,
+                                          double delta) {
+  double2 a = __ldg(A + (size_t)i * D + l);
+  if (i == l) {
+    a.x += delta;
+    a.y = 0.0;
+  }
+  return a;
+}
+
+// x <- (L L^H)^{-1} x in place, x[d] at vec[d * 32] (this lane's column).
+__device__ __forceinline__ void chol_solve_inplace(const double2* __restrict__ L,
+                                                   const double* __restrict__ invd, double2* vec,
+                                                   int D) {
+  for (int i = 0; i < D; ++i) {
+    double2 acc = vec[i * 32];
+    const double2* Li = L + pidx(i, 0);
+    for (int l = 0; l < i; ++l) cfms(acc, Li[l], vec[l * 32]);
+    const double s = invd[i];
+    vec[i * 32] = make_double2(acc.x * s, acc.y * s);
+  }
+  for (int i = D - 1; i >= 0; --i) {
+    double2 acc = vec[i * 32];
+    for (int l = i + 1; l < D; ++l) cfms_conj(acc, L[pidx(l, i)], vec[l * 32]);
+    const double s = invd[i];
+    vec[i * 32] = make_double2(acc.x * s, acc.y * s);
+  }
+}
+
+__global__ void __launch_bounds__(128)
+solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
+             const double2* __restrict__ steer, long long nsys, int D, int S, int TS,
+             double load_factor, int refine_steps, DeviceStatus* __restrict__ status) {
+  extern __shared__ double2 sm[];
+  const int nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = 32 / TS, team = lane / TS, tl = lane - team * TS;
+  const int Dp = D * (D + 1) / 2;
+  const size_t warp_elems = (size_t)G * Dp + 2 * (size_t)D * 32;
+  double2* wbase = sm + warp * warp_elems;
+  double2* L = wbase + (size_t)team * Dp;          // packed lower factor of this team's system
+  double2* U = wbase + (size_t)G * Dp + lane;      // u (this lane's column), stride 32
+  double2* W = U + (size_t)D * 32;                 // work vector, stride 32
+  double* invd = reinterpret_cast<double*>(sm + nw * warp_elems) + ((size_t)warp * G + team) * D;
+  const double invD = 1.0 / (double)D;
+
+  for (long long base = ((long long)blockIdx.x * nw + warp) * G; base < nsys;
+       base += (long long)gridDim.x * nw * G) {
+    const long long sys = base + team;
+    const bool valid = sys < nsys;
+    const double2* A = cov + (size_t)(valid ? sys : nsys - 1) * D * D;
+
+    // ---- diagonal load and packed copy of Rl (lower triangle) ----
+    double tr = 0.0;
+    for (int j = 0; j < D; ++j) tr += __ldg(&A[(size_t)j * D + j].x);
+    const double delta = load_factor * tr * invD;
+    for (int q = tl; q < Dp; q += TS) {
+      int i, l;
+      unpack_lower(q, i, l);
+      L[q] = loaded(A, D, i, l, delta);
+    }
+    __syncwarp();
+
+    // ---- right-looking Cholesky, trailing updates spread over the team ----
+    bool ok = true;
+    for (int j = 0; j < D; ++j) {
+      double djj = L[pidx(j, j)].x;
+      if (!(djj > 0.0) || !isfinite(djj)) {
+        ok = false;
+        djj = 1.0;  // keep the control flow uniform; this system's weights become zero
+      }
+      const double ljj = sqrt(djj);
+      const double inv = 1.0 / ljj;
+      for (int i = j + 1 + tl; i < D; i += TS) {
+        const double2 v = L[pidx(i, j)];
+        L[pidx(i, j)] = make_double2(v.x * inv, v.y * inv);
+      }
+      __syncwarp();
+      const int m = D - j - 1;
+      const int np = m * (m + 1) / 2;
+      for (int q = tl; q < np; q += TS) {
+        int a, b;
+        unpack_lower(q, a, b);
+        const int i = j + 1 + a, l = j + 1 + b;
+        double2 acc = L[pidx(i, l)];
+        const double2 lij = L[pidx(i, j)], llj = L[pidx(l, j)];
+        // acc -= lij * conj(llj)
+        acc.x = fma(-lij.x, llj.x, acc.x);
+        acc.x = fma(-lij.y, llj.y, acc.x);
+        acc.y = fma(-lij.y, llj.x, acc.y);
+        acc.y = fma(lij.x, llj.y, acc.y);
+        L[pidx(i, l)] = acc;
+      }
+      __syncwarp();
+      if (tl == 0) {
+        L[pidx(j, j)] = make_double2(ljj, 0.0);
+        invd[j] = inv;
+      }
+      __syncwarp();
+    }
+
+    // ---- per-lane solves, one steering vector per lane and pass ----
+    for (int s0 = 0; s0 < S; s0 += TS) {
+      const int s = s0 + tl;
+      if (s < S) {
+        const double2* v = steer + (size_t)s * D;
+        for (int i = 0; i < D; ++i) W[i * 32] = __ldg(v + i);
+        chol_solve_inplace(L, invd, W, D);
+        for (int i = 0; i < D; ++i) U[i * 32] = W[i * 32];
+        for (int it = 0; it < refine_steps; ++it) {
+          // W = v - Rl u  (Rl Hermitian: lower part direct, upper part mirrored)
+          for (int i = 0; i < D; ++i) {
+            double2 acc = __ldg(v + i);
+            for (int l = 0; l <= i; ++l) cfms(acc, loaded(A, D, i, l, delta), U[l * 32]);
+            for (int l = i + 1; l < D; ++l) cfms_conj(acc, loaded(A, D, l, i, delta), U[l * 32]);
+            W[i * 32] = acc;
+          }
+          chol_solve_inplace(L, invd, W, D);
+          for (int i = 0; i < D; ++i) {
+            const double2 u = U[i * 32], c = W[i * 32];
+            U[i * 32] = make_double2(u.x + c.x, u.y + c.y);
+          }
+        }
+        double q = 0.0;  // Re v^H u
+        for (int i = 0; i < D; ++i) {
+          const double2 vi = __ldg(v + i), ui = U[i * 32];
+          q = fma(vi.x, ui.x, q);
+          q = fma(vi.y, ui.y, q);
+        }
+        const bool good = ok && q > 0.0 && isfinite(q);
+        const double scale = good ? 1.0 / sqrt(q) : 0.0;
+        if (valid) {
+          float2* w = wts + ((size_t)sys * S + s) * D;
+          for (int i = 0; i < D; ++i) {
+            const double2 u = U[i * 32];
+            w[i] = good ? make_float2((float)(u.x * scale), (float)(u.y * scale))
+                        : make_float2(0.f, 0.f);
+          }
+        }
+      }
+    }
+    if (valid && !ok && tl == 0) atomicAdd(&status->n_failed, 1ULL);
+    __syncwarp();  // the next batch reuses L, U, W
+  }
+}
+
+int pow2ceil(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer, long long nsys,
+                         int D, int S, double load_factor, int refine_steps, DeviceStatus* status,
+                         cudaStream_t s) {
+  if (nsys <= 0) return cudaSuccess;
+  if (D < 1 || D > kMaxD || S < 1) return cudaErrorInvalidValue;
+  constexpr size_t kBudget = 200 * 1024;
+  const int Dp = D * (D + 1) / 2;
+  // lanes per system: enough for one steering vector per lane, more if the
+  // packed factors of 32/TS systems would not fit in shared memory
+  int TS = pow2ceil(S < 32 ? S : 32);
+  auto warp_bytes = [&](int ts) {
+    const int G = 32 / ts;
+    return ((size_t)G * Dp + 2 * (size_t)D * 32) * sizeof(double2) + (size_t)G * D * sizeof(double);
+  };
+  while (TS < 32 && warp_bytes(TS) * 4 > kBudget) TS <<= 1;
+  int nw = 4;
+  while (nw > 1 && warp_bytes(TS) * nw > kBudget) --nw;
+  const size_t smem = warp_bytes(TS) * nw;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  static int set_bytes[64] = {0};
+  cudaError_t e = ensure_smem(solve_kernel, smem, set_bytes);
+  if (e != cudaSuccess) return e;
+  const int G = 32 / TS;
+  const long long batches = (nsys + G - 1) / G;
+  long long blocks = (batches + nw - 1) / nw;
+  if (blocks > 152LL * 64) blocks = 152LL * 64;
+  solve_kernel<<<(unsigned)blocks, nw * 32, smem, s>>>(cov, wts, steer, nsys, D, S, TS, load_factor,
+                                                      refine_steps, status);
+  return cudaGetLastError();
+}
+
+}  // namespace stap

@@ -1,0 +1,58 @@
+// Internal declarations of libstap: kernel launchers, the device status block
+// and small complex helpers shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "stap.h"
+
+namespace stap {
+
+// Device-side status, at offset 0 of the workspace.
+struct DeviceStatus {
+  unsigned long long n_failed;   // systems whose loaded covariance was not positive definite
+  unsigned int timeout;          // a bounded wait gave up (1)
+  unsigned int pad[13];
+};
+static_assert(sizeof(DeviceStatus) <= 256, "status block must fit its slot");
+
+constexpr int kMaxD = 64;        // largest snapshot length the solve kernel handles
+constexpr int kMaxLogK = 10;     // K <= 1024
+
+// ---------------------------------------------------------------- launchers --
+// Each returns cudaGetLastError() after its launches.
+
+// Hann-windowed DFT over pulses via a two-pass in-register FFT.
+// cube [C][P][R] c64 -> dop [C][K][R] c64; win[P] float; tw[K] = exp(-2 pi i m/K).
+cudaError_t launch_doppler(const float2* cube, float2* dop, const float* win, const float2* tw,
+                           int C, int P, int K, int R, cudaStream_t s);
+
+// Covariance per (k, block) from the Doppler cube, accumulated error-free in
+// FP32 pairs; written as FP64 complex [K][NB][D][D] (full Hermitian).
+cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K, int R, int T,
+                                   int B, cudaStream_t s);
+
+// FP64 loading, Cholesky, solves, refinement and scaling for nsys systems.
+// cov [nsys][D][D] c128 -> wts [nsys][S][D] c64; steer [S][D] c128.
+cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer, long long nsys,
+                         int D, int S, double load_factor, int refine_steps, DeviceStatus* status,
+                         cudaStream_t s);
+
+// out[s][k][r] = |w^H x|^2; dop [C][K][R] c64, wts [K][NB][S][D] c64, out [S][K][R] f32.
+cudaError_t launch_apply(const float2* dop, const float2* wts, float* out, int C, int K, int R,
+                         int T, int B, int S, cudaStream_t s);
+
+// ------------------------------------------------------------ device helpers --
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ int wrap_bin(int k, int K) {
+  int m = k % K;
+  return m < 0 ? m + K : m;
+}
+
+}  // namespace stap

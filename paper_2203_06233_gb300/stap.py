@@ -1,0 +1,331 @@
+"""Thin Python binding of libstap (the C ABI in ``include/stap.h``).
+
+Argument marshalling only: every step of the STAP path runs in the CUDA
+kernels of ``libstap.so``.  PyTorch provides device memory and streams.  The
+functions carry the C names (``stap_plan_create``, ``stap_doppler``, ...) and
+take torch tensors; :class:`Plan` wraps a plan together with its workspace.
+
+If the compiled library is missing it is built with nvcc; if that fails an
+error is raised -- there is no other implementation to fall back to.
+"""
+import ctypes
+import os
+import threading
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import build as _build
+
+STAP_OK = 0
+STAP_ERR_INVALID_ARG = 1
+STAP_ERR_SHAPE = 2
+STAP_ERR_UNSUPPORTED = 3
+STAP_ERR_CUDA = 4
+STAP_ERR_NOT_POSDEF = 5
+STAP_ERR_TIMEOUT = 6
+STAP_ERR_NO_WORKSPACE = 7
+STAP_ERR_MISALIGNED = 8
+
+STAP_PREC_FP32 = 0
+
+# every symbol include/stap.h declares
+EXPORTED = (
+    "stap_options_default", "stap_plan_create", "stap_plan_workspace_sizes",
+    "stap_plan_set_workspace", "stap_plan_set_stream", "stap_plan_set_steering",
+    "stap_plan_destroy", "stap_doppler", "stap_covariance", "stap_solve_weights", "stap_apply",
+    "stap_run_cpi", "stap_get_status", "stap_status_string", "stap_abi_version",
+)
+
+
+class StapError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} (status {code})")
+
+
+class stap_dims(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("n_chan", "n_pulses", "n_dop", "n_range", "tdof", "training_block", "n_steering")]
+
+
+class stap_options(ctypes.Structure):
+    _fields_ = [("load_factor", ctypes.c_double), ("refine_steps", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libstap.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            vp, i32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+            L.stap_options_default.argtypes = [ctypes.POINTER(stap_options)]
+            L.stap_options_default.restype = None
+            L.stap_plan_create.argtypes = [ctypes.POINTER(stap_dims), i32, ctypes.POINTER(stap_options),
+                                           vp, ctypes.POINTER(vp), ctypes.POINTER(sz)]
+            L.stap_plan_workspace_sizes.argtypes = [vp, ctypes.POINTER(sz), ctypes.POINTER(sz)]
+            L.stap_plan_set_workspace.argtypes = [vp, vp, sz]
+            L.stap_plan_set_stream.argtypes = [vp, vp]
+            L.stap_plan_set_steering.argtypes = [vp, i32, vp]
+            L.stap_plan_destroy.argtypes = [vp]
+            L.stap_doppler.argtypes = [vp, vp, vp]
+            L.stap_covariance.argtypes = [vp, vp, vp]
+            L.stap_solve_weights.argtypes = [vp, vp, vp]
+            L.stap_apply.argtypes = [vp, vp, vp, vp]
+            L.stap_run_cpi.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+            L.stap_get_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+            L.stap_status_string.argtypes = [ctypes.c_int]
+            L.stap_status_string.restype = ctypes.c_char_p
+            L.stap_abi_version.argtypes = []
+            for f in EXPORTED:
+                if f not in ("stap_options_default", "stap_status_string"):
+                    getattr(L, f).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().stap_status_string(int(code)).decode()
+
+
+def _check(code: int, what: str, ok=(STAP_OK,)):
+    if code not in ok:
+        raise StapError(code, what)
+    return code
+
+
+def _dims(d) -> stap_dims:
+    if isinstance(d, stap_dims):
+        return d
+    if hasattr(d, "dims"):
+        d = d.dims()
+    return stap_dims(*[int(v) for v in d])
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(t: torch.Tensor, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------- C entry points --
+
+def stap_options_default() -> stap_options:
+    o = stap_options()
+    lib().stap_options_default(ctypes.byref(o))
+    return o
+
+
+def stap_plan_create(dims: Sequence, opts: Optional[stap_options] = None, stream=None):
+    """(plan handle, run workspace bytes) for a list of CPI shapes."""
+    arr = (stap_dims * len(dims))(*[_dims(d) for d in dims])
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    _check(lib().stap_plan_create(arr, len(dims), ctypes.byref(opts) if opts is not None else None,
+                                  _stream_ptr(stream) if torch.cuda.is_available() else None,
+                                  ctypes.byref(h), ctypes.byref(ws)), "stap_plan_create")
+    return h, ws.value
+
+
+def stap_plan_workspace_sizes(plan):
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().stap_plan_workspace_sizes(plan, ctypes.byref(a), ctypes.byref(b)),
+           "stap_plan_workspace_sizes")
+    return a.value, b.value
+
+
+def stap_plan_set_workspace(plan, workspace: torch.Tensor):
+    if not workspace.is_cuda or not workspace.is_contiguous():
+        raise ValueError("workspace must be a contiguous CUDA tensor")
+    nbytes = workspace.numel() * workspace.element_size()
+    _check(lib().stap_plan_set_workspace(plan, ctypes.c_void_p(workspace.data_ptr()), nbytes),
+           "stap_plan_set_workspace")
+
+
+def stap_plan_set_stream(plan, stream=None):
+    _check(lib().stap_plan_set_stream(plan, _stream_ptr(stream)), "stap_plan_set_stream")
+
+
+def stap_plan_set_steering(plan, cpi: int, steer):
+    import numpy as np
+    a = np.ascontiguousarray(steer, dtype=np.complex128)
+    _check(lib().stap_plan_set_steering(plan, int(cpi), a.ctypes.data_as(ctypes.c_void_p)),
+           "stap_plan_set_steering")
+
+
+def stap_plan_destroy(plan):
+    _check(lib().stap_plan_destroy(plan), "stap_plan_destroy")
+
+
+def stap_doppler(plan, cube: torch.Tensor, dop: torch.Tensor):
+    _check(lib().stap_doppler(plan, ctypes.c_void_p(cube.data_ptr()), ctypes.c_void_p(dop.data_ptr())),
+           "stap_doppler")
+
+
+def stap_covariance(plan, dop: torch.Tensor, cov: torch.Tensor):
+    _check(lib().stap_covariance(plan, ctypes.c_void_p(dop.data_ptr()), ctypes.c_void_p(cov.data_ptr())),
+           "stap_covariance")
+
+
+def stap_solve_weights(plan, cov: torch.Tensor, wts: torch.Tensor):
+    _check(lib().stap_solve_weights(plan, ctypes.c_void_p(cov.data_ptr()),
+                                    ctypes.c_void_p(wts.data_ptr())), "stap_solve_weights")
+
+
+def stap_apply(plan, dop: torch.Tensor, wts: torch.Tensor, out: torch.Tensor):
+    _check(lib().stap_apply(plan, ctypes.c_void_p(dop.data_ptr()), ctypes.c_void_p(wts.data_ptr()),
+                            ctypes.c_void_p(out.data_ptr())), "stap_apply")
+
+
+def stap_run_cpi(plan, cubes: Sequence[torch.Tensor], outs: Sequence[torch.Tensor]):
+    n = len(cubes)
+    ca = (ctypes.c_void_p * n)(*[t.data_ptr() for t in cubes])
+    oa = (ctypes.c_void_p * n)(*[t.data_ptr() for t in outs])
+    _check(lib().stap_run_cpi(plan, ca, oa), "stap_run_cpi")
+
+
+def stap_get_status(plan):
+    """(status code, failed systems) -- waits for the plan's stream."""
+    n = ctypes.c_int64()
+    code = lib().stap_get_status(plan, ctypes.byref(n))
+    _check(code, "stap_get_status", ok=(STAP_OK, STAP_ERR_NOT_POSDEF, STAP_ERR_TIMEOUT))
+    return code, n.value
+
+
+def stap_abi_version() -> int:
+    return lib().stap_abi_version()
+
+
+# --------------------------------------------------------------- convenience --
+
+class Plan:
+    """A libstap plan plus its torch-owned workspace, for tensors on one device.
+
+    ``dims`` is one CPI shape (7 ints or an object with ``dims()``) or a list of
+    them.  Calls are issued on torch's current stream.
+    """
+
+    def __init__(self, dims, load_factor: float = 1e-3, refine_steps: int = 1,
+                 precision: int = STAP_PREC_FP32, device=None, steps_only: bool = False):
+        dl = list(dims) if isinstance(dims, (list, tuple)) and dims and not isinstance(dims[0], int) \
+            else [dims]
+        self.dims = [_dims(d) for d in dl]
+        self.device = torch.device(device) if device is not None else torch.device("cuda")
+        opts = stap_options(float(load_factor), int(refine_steps), int(precision))
+        with torch.cuda.device(self.device):
+            self.handle, _ = stap_plan_create(self.dims, opts)
+            self.step_bytes, self.run_bytes = stap_plan_workspace_sizes(self.handle)
+            nbytes = self.step_bytes if steps_only else self.run_bytes
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            stap_plan_set_workspace(self.handle, self.workspace)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            torch.cuda.synchronize(self.device)
+            stap_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # shapes of CPI i
+    def shapes(self, i: int = 0):
+        d = self.dims[i]
+        C, P, K, R, T, B, S = (d.n_chan, d.n_pulses, d.n_dop, d.n_range, d.tdof,
+                               d.training_block, d.n_steering)
+        D, NB = C * T, R // B
+        return dict(cube=(C, P, R), dop=(C, K, R), cov=(K, NB, D, D), wts=(K, NB, S, D),
+                    out=(S, K, R))
+
+    def _sync_stream(self):
+        stap_plan_set_stream(self.handle, torch.cuda.current_stream(self.device))
+
+    def doppler(self, cube, dop=None):
+        sh = self.shapes()
+        dop = torch.empty(sh["dop"], dtype=torch.complex64, device=self.device) if dop is None else dop
+        _dev(cube, torch.complex64, sh["cube"], "cube")
+        _dev(dop, torch.complex64, sh["dop"], "dop")
+        self._sync_stream()
+        stap_doppler(self.handle, cube, dop)
+        return dop
+
+    def covariance(self, dop, cov=None):
+        sh = self.shapes()
+        cov = torch.empty(sh["cov"], dtype=torch.complex128, device=self.device) if cov is None else cov
+        _dev(dop, torch.complex64, sh["dop"], "dop")
+        _dev(cov, torch.complex128, sh["cov"], "cov")
+        self._sync_stream()
+        stap_covariance(self.handle, dop, cov)
+        return cov
+
+    def solve_weights(self, cov, wts=None):
+        sh = self.shapes()
+        wts = torch.empty(sh["wts"], dtype=torch.complex64, device=self.device) if wts is None else wts
+        _dev(cov, torch.complex128, sh["cov"], "cov")
+        _dev(wts, torch.complex64, sh["wts"], "wts")
+        self._sync_stream()
+        stap_solve_weights(self.handle, cov, wts)
+        return wts
+
+    def apply(self, dop, wts, out=None):
+        sh = self.shapes()
+        out = torch.empty(sh["out"], dtype=torch.float32, device=self.device) if out is None else out
+        _dev(dop, torch.complex64, sh["dop"], "dop")
+        _dev(wts, torch.complex64, sh["wts"], "wts")
+        _dev(out, torch.float32, sh["out"], "out")
+        self._sync_stream()
+        stap_apply(self.handle, dop, wts, out)
+        return out
+
+    def run_cpi(self, cubes, outs=None) -> List[torch.Tensor]:
+        single = isinstance(cubes, torch.Tensor)
+        cubes = [cubes] if single else list(cubes)
+        if len(cubes) != len(self.dims):
+            raise ValueError(f"plan has {len(self.dims)} CPIs, got {len(cubes)} cubes")
+        if outs is None:
+            outs = [torch.empty(self.shapes(i)["out"], dtype=torch.float32, device=self.device)
+                    for i in range(len(cubes))]
+        elif isinstance(outs, torch.Tensor):
+            outs = [outs]
+        for i, (c, o) in enumerate(zip(cubes, outs)):
+            sh = self.shapes(i)
+            _dev(c, torch.complex64, sh["cube"], f"cubes[{i}]")
+            _dev(o, torch.float32, sh["out"], f"outs[{i}]")
+        self._sync_stream()
+        stap_run_cpi(self.handle, cubes, outs)
+        return outs[0] if single else outs
+
+    def set_steering(self, steer, cpi: int = 0):
+        self._sync_stream()
+        stap_plan_set_steering(self.handle, cpi, steer)
+
+    def status(self):
+        return stap_get_status(self.handle)

@@ -1,0 +1,77 @@
+"""Shared helpers of the GPU parity tests: workloads, error metrics, bounds."""
+import numpy as np
+
+import oracle
+from paper_2203_06233_gb300 import synth
+
+EPS32 = 2.0 ** -24          # unit roundoff of FP32
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def power_errors(P, P_ref):
+    """(max over cells of |P - P_ref| / max(P_ref, median P_ref), ||P - P_ref||_2 / ||P_ref||_2).
+
+    The first normalises each cell by its own power but never by less than the
+    noise floor (the median), where a per-cell relative error means nothing."""
+    P = np.asarray(P, np.float64)
+    med = float(np.median(P_ref))
+    floor = np.maximum(P_ref, med)
+    return float(np.max(np.abs(P - P_ref) / floor)), \
+        float(np.linalg.norm(P - P_ref) / np.linalg.norm(P_ref))
+
+
+def gather(dop, T):
+    """x[k, r, t*C + c] = dop[c, (k + t - T//2) % K, r] (numpy indexing)."""
+    C, K, R = dop.shape
+    x = np.empty((K, R, T * C), np.complex128)
+    for t in range(T):
+        kk = (np.arange(K) + t - T // 2) % K
+        x[:, :, t * C:(t + 1) * C] = dop[:, kk, :].transpose(1, 2, 0)
+    return x
+
+
+def cell_bound(dop, wts, T, B):
+    """Per-cell bound on |P_fp32 - P| for the FP32 apply of FP32 inputs.
+
+    y = sum_d conj(w_d) x_d accumulated with fused multiply-adds in FP32 has
+    |dy| <= (D + 2) u sum_d |w_d| |x_d| (two real FMA chains of length D per
+    component, the complex magnitude folded into the constant); then
+    |dP| <= 2 |y| |dy| + |dy|^2 + 2 u P for the final |y|^2 in FP32."""
+    C, K, R = dop.shape
+    S, D = wts.shape[2], wts.shape[3]
+    x = gather(dop.astype(np.complex128), T)                          # [K][R][D]
+    wb = np.repeat(wts.astype(np.complex128), B, axis=1)              # [K][R][S][D]
+    y = np.einsum("krsd,krd->skr", wb.conj(), x)
+    mag = np.einsum("krsd,krd->skr", np.abs(wb), np.abs(x))
+    g = (D + 2) * EPS32 * mag
+    P = np.abs(y) ** 2
+    return 2.0 * np.abs(y) * g + g * g + 2.0 * EPS32 * P
+
+
+def spec_small():
+    return synth.small_cpi()
+
+
+def spec_standard():
+    return synth.standard_cpi()
+
+
+def oracle_dims(spec):
+    return oracle.Dims(*spec.dims())
+
+
+# Edge shapes: ragged range tiles, even/odd T, K = P, K = 1, S not a power of
+# two and S > 32, the largest D, B = 1, the largest K.
+EDGE_SPECS = [
+    synth.CPISpec(3, 20, 32, 96, 2, 32, 5, cnr_db=30.0, targets=(synth.Target(50, 3, 1, 12.0),), seed=11),
+    synth.CPISpec(2, 16, 16, 48, 1, 16, 3, cnr_db=20.0, seed=12),
+    synth.CPISpec(5, 7, 8, 40, 4, 8, 40, cnr_db=25.0, seed=13),
+    synth.CPISpec(16, 32, 64, 256, 4, 128, 8, cnr_db=40.0, seed=14),
+    synth.CPISpec(1, 1, 1, 8, 1, 1, 1, cnr_db=10.0, seed=15),
+    synth.CPISpec(4, 64, 1024, 64, 3, 64, 4, cnr_db=30.0, seed=16),
+    synth.CPISpec(2, 300, 512, 40, 3, 40, 4, cnr_db=30.0, seed=17),
+    synth.CPISpec(6, 24, 32, 160, 3, 160, 33, cnr_db=35.0, seed=18),
+]

@@ -1,0 +1,132 @@
+"""Host-side tests of the C ABI: the library loads without a GPU, exports every
+symbol ``include/stap.h`` declares, and validates shapes, options, pointers and
+workspace sizes before touching CUDA (none of these calls launches anything)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2203_06233_gb300 import stap
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+GOOD = (4, 128, 256, 4096, 3, 64, 16)
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "stap.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(stap_[a-z_]+)\s*\(", src)))
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    L = stap.lib()
+    declared = _declared()
+    assert len(declared) >= 14
+    for name in declared:
+        assert hasattr(L, name), f"{name} declared in stap.h but not exported"
+    assert set(declared) == set(stap.EXPORTED)
+    assert stap.stap_abi_version() == 1
+
+
+def _create(dims, opts=None):
+    L = stap.lib()
+    arr = (stap.stap_dims * 1)(stap.stap_dims(*dims))
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t()
+    code = L.stap_plan_create(arr, 1, ctypes.byref(opts) if opts else None, None, ctypes.byref(h),
+                              ctypes.byref(ws))
+    return code, h, ws.value
+
+
+def test_plan_create_default_options_and_workspace_layout():
+    o = stap.stap_options_default()
+    assert o.load_factor == 1e-3 and o.refine_steps == 1 and o.precision == 0
+    code, h, ws = _create(GOOD)
+    assert code == stap.STAP_OK and h.value
+    step, run = stap.stap_plan_workspace_sizes(h)
+    C, P, K, R, T, B, S = GOOD
+    D, NB = C * T, R // B
+    inter = C * K * R * 8 + K * NB * D * D * 16 + K * NB * S * D * 8
+    assert run == ws
+    assert run - step >= inter and run - step < inter + 4 * 256
+    assert step < 64 * 1024                                 # status + window + twiddles + steering
+    stap.stap_plan_destroy(h)
+
+
+@pytest.mark.parametrize("dims,code", [
+    ((0, 128, 256, 4096, 3, 64, 16), stap.STAP_ERR_SHAPE),      # no channels
+    ((4, 128, 64, 4096, 3, 64, 16), stap.STAP_ERR_SHAPE),       # K < P
+    ((4, 128, 256, 4000, 3, 64, 16), stap.STAP_ERR_SHAPE),      # R not a multiple of B
+    ((4, 8, 8, 64, 9, 8, 4), stap.STAP_ERR_SHAPE),              # T > K
+    ((4, 128, 256, 4096, 3, 64, 0), stap.STAP_ERR_SHAPE),       # no steering vectors
+    ((4, 128, 192, 4096, 3, 64, 16), stap.STAP_ERR_UNSUPPORTED),  # K not a power of two
+    ((4, 128, 2048, 4096, 3, 64, 16), stap.STAP_ERR_UNSUPPORTED),  # K > 1024
+    ((33, 16, 16, 64, 2, 8, 4), stap.STAP_ERR_UNSUPPORTED),     # D = 66 > 64
+])
+def test_plan_create_rejects_bad_shapes(dims, code):
+    got, h, _ = _create(dims)
+    assert got == code and not h.value
+
+
+@pytest.mark.parametrize("lf,refine,prec,code", [
+    (-1.0, 1, 0, stap.STAP_ERR_INVALID_ARG),
+    (float("nan"), 1, 0, stap.STAP_ERR_INVALID_ARG),
+    (1e-3, -1, 0, stap.STAP_ERR_INVALID_ARG),
+    (1e-3, 5, 0, stap.STAP_ERR_INVALID_ARG),
+    (1e-3, 1, 7, stap.STAP_ERR_UNSUPPORTED),
+    (0.0, 0, 0, stap.STAP_OK),
+])
+def test_plan_create_checks_options(lf, refine, prec, code):
+    got, h, _ = _create(GOOD, stap.stap_options(lf, refine, prec))
+    assert got == code
+    if h.value:
+        stap.stap_plan_destroy(h)
+
+
+def test_null_and_misaligned_pointers_and_missing_workspace_fail_before_cuda():
+    L = stap.lib()
+    h = ctypes.c_void_p()
+    assert L.stap_plan_create(None, 1, None, None, ctypes.byref(h), None) == stap.STAP_ERR_INVALID_ARG
+    code, h, ws = _create(GOOD)
+    assert code == 0
+    fake = ctypes.c_void_p(0x10000)                           # never dereferenced
+    odd = ctypes.c_void_p(0x10008)
+    step, run = stap.stap_plan_workspace_sizes(h)
+    assert L.stap_plan_set_workspace(h, None, run) == stap.STAP_ERR_INVALID_ARG
+    assert L.stap_plan_set_workspace(h, odd, run) == stap.STAP_ERR_MISALIGNED
+    assert L.stap_plan_set_workspace(h, fake, step - 1) == stap.STAP_ERR_NO_WORKSPACE
+    # step calls: NULL -> invalid, misaligned -> misaligned, otherwise no workspace yet
+    assert L.stap_doppler(h, None, fake) == stap.STAP_ERR_INVALID_ARG
+    assert L.stap_doppler(h, odd, fake) == stap.STAP_ERR_MISALIGNED
+    assert L.stap_doppler(h, fake, fake) == stap.STAP_ERR_NO_WORKSPACE
+    assert L.stap_covariance(h, fake, fake) == stap.STAP_ERR_NO_WORKSPACE
+    assert L.stap_solve_weights(h, fake, fake) == stap.STAP_ERR_NO_WORKSPACE
+    assert L.stap_apply(h, fake, fake, fake) == stap.STAP_ERR_NO_WORKSPACE
+    arr = (ctypes.c_void_p * 1)(fake)
+    assert L.stap_run_cpi(h, arr, arr) == stap.STAP_ERR_NO_WORKSPACE
+    assert L.stap_get_status(h, None) == stap.STAP_ERR_NO_WORKSPACE
+    assert L.stap_plan_set_steering(h, 0, fake) == stap.STAP_ERR_NO_WORKSPACE
+    assert L.stap_plan_set_steering(h, 1, fake) == stap.STAP_ERR_INVALID_ARG
+    assert L.stap_plan_destroy(None) == stap.STAP_ERR_INVALID_ARG
+    stap.stap_plan_destroy(h)
+
+
+def test_step_calls_need_a_single_cpi_plan():
+    L = stap.lib()
+    arr = (stap.stap_dims * 2)(stap.stap_dims(*GOOD), stap.stap_dims(4, 64, 64, 1024, 2, 64, 8))
+    h = ctypes.c_void_p()
+    assert L.stap_plan_create(arr, 2, None, None, ctypes.byref(h), None) == 0
+    fake = ctypes.c_void_p(0x10000)
+    assert L.stap_doppler(h, fake, fake) == stap.STAP_ERR_INVALID_ARG
+    step, run = stap.stap_plan_workspace_sizes(h)
+    assert run > step
+    stap.stap_plan_destroy(h)
+
+
+def test_status_strings():
+    for code in range(9):
+        s = stap.status_string(code)
+        assert s and s != "unknown status"
+    assert stap.status_string(99) == "unknown status"

@@ -1,0 +1,196 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Every comparison uses the same seeded complex64 input on both sides; the
+oracle never sees a value produced by the CUDA path.  Tolerances:
+
+* Doppler (FP32 FFT): normwise relative error per channel <= 2 u log2(K) + 4u
+  (FFT error bound with correctly rounded twiddles, u = 2^-24).
+* Covariance (error-free FP32-pair accumulation, FP64 result): relative
+  Frobenius error per system <= 1e-10 (Dot2 bound (2Bu)^2 plus FP64 rounding),
+  Hermitian bit-exact.
+* Weights (FP64 solve, complex64 result): relative 2-norm per vector <= 2u.
+* Apply (FP32): every cell within the forward-error bound of the FP32 dot
+  product (tests/_parity.cell_bound).
+* Whole path, plain FP32: ||P - P_ref||_2 / ||P_ref||_2 <= 1e-5, and every
+  cell within 1e-3 of max(P_ref, median P_ref).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2203_06233_gb300 import stap, synth
+
+from _parity import EDGE_SPECS, EPS32, cell_bound, power_errors, to_np
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _cube(spec):
+    return synth.make_cube(spec)
+
+
+def _plan(spec, **kw):
+    return stap.Plan(spec.dims(), device=DEV, **kw)
+
+
+def _dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+SPECS = [synth.small_cpi(), synth.standard_cpi()] + EDGE_SPECS
+IDS = ["small", "standard"] + [f"edge{i}" for i in range(len(EDGE_SPECS))]
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_doppler_parity(spec):
+    d = oracle.Dims(*spec.dims())
+    cube = _cube(spec)
+    ref = oracle.doppler(d, cube)
+    plan = _plan(spec)
+    dop = to_np(plan.doppler(_dev(cube, torch.complex64)))
+    K = spec.n_dop
+    tol = 2 * EPS32 * max(1, np.log2(K)) + 4 * EPS32
+    for c in range(spec.n_chan):
+        err = np.linalg.norm(dop[c] - ref[c]) / np.linalg.norm(ref[c])
+        assert err <= tol, (c, err, tol)
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_covariance_parity(spec):
+    d = oracle.Dims(*spec.dims())
+    dop64 = oracle.doppler(d, _cube(spec)).astype(np.complex64)     # same c64 input both sides
+    ref = oracle.covariance(d, dop64)
+    plan = _plan(spec)
+    cov = to_np(plan.covariance(_dev(dop64, torch.complex64)))
+    np.testing.assert_array_equal(cov, np.conj(np.swapaxes(cov, -1, -2)))
+    num = np.linalg.norm((cov - ref).reshape(spec.n_dop, spec.NB, -1), axis=-1)
+    den = np.linalg.norm(ref.reshape(spec.n_dop, spec.NB, -1), axis=-1)
+    assert np.max(num / den) <= 1e-10, np.max(num / den)
+
+
+@pytest.mark.parametrize("refine", [0, 1, 2])
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_solve_weights_parity(spec, refine):
+    d = oracle.Dims(*spec.dims())
+    cov = oracle.covariance(d, oracle.doppler(d, _cube(spec)))     # FP64 input both sides
+    ref, status, nf = oracle.weights(d, cov)
+    assert nf == 0
+    plan = _plan(spec, refine_steps=refine)
+    wts = to_np(plan.solve_weights(_dev(cov, torch.complex128)))
+    err = np.linalg.norm(wts - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+    assert np.max(err) <= 2 * EPS32 * np.sqrt(2), np.max(err)
+    assert plan.status() == (stap.STAP_OK, 0)
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_apply_parity(spec):
+    d = oracle.Dims(*spec.dims())
+    dop = oracle.doppler(d, _cube(spec))
+    w, _, _ = oracle.weights(d, oracle.covariance(d, dop))
+    dop64, w64 = dop.astype(np.complex64), w.astype(np.complex64)   # same c64 inputs both sides
+    ref = oracle.apply(d, dop64, w64)
+    plan = _plan(spec)
+    out = to_np(plan.apply(_dev(dop64, torch.complex64), _dev(w64, torch.complex64)))
+    bound = cell_bound(dop64, w64, spec.tdof, spec.training_block)
+    viol = np.abs(out - ref) > bound
+    assert not viol.any(), (int(viol.sum()), float(np.max(np.abs(out - ref) - bound)))
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_run_cpi_end_to_end(spec):
+    d = oracle.Dims(*spec.dims())
+    cube = _cube(spec)
+    ref = oracle.run(d, cube)["out"]
+    plan = _plan(spec)
+    out = to_np(plan.run_cpi(_dev(cube, torch.complex64)))
+    e_cell, e_norm = power_errors(out, ref)
+    print(f"dims={spec.dims()} max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
+    assert e_norm <= 1e-5, e_norm
+    assert e_cell <= 1e-3, e_cell
+    assert plan.status() == (stap.STAP_OK, 0)
+
+
+def test_run_cpi_equals_step_by_step_and_is_deterministic():
+    spec = synth.standard_cpi()
+    cube = _dev(_cube(spec), torch.complex64)
+    plan = _plan(spec)
+    a = plan.run_cpi(cube)
+    b = plan.run_cpi(cube)
+    dop = plan.doppler(cube)
+    steps = plan.apply(dop, plan.solve_weights(plan.covariance(dop)))
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert torch.equal(a, steps)
+
+
+def test_small_workload_target_recovered_on_gpu():
+    spec = synth.small_cpi()
+    out = to_np(_plan(spec).run_cpi(_dev(_cube(spec), torch.complex64)))
+    assert int(np.argmax(out[2, 24])) == 128
+    assert 10 * np.log10(out[2, 24, 128] / np.median(out)) > 10.0
+
+
+def test_user_steering_override():
+    spec = synth.CPISpec(3, 16, 32, 128, 2, 32, 6, cnr_db=30.0, seed=31)
+    d = oracle.Dims(*spec.dims())
+    rng = np.random.default_rng(3)
+    steer = rng.standard_normal((6, 6)) + 1j * rng.standard_normal((6, 6))
+    cube = _cube(spec)
+    ref = oracle.run(d, cube, steer=steer)["out"]
+    plan = _plan(spec)
+    plan.set_steering(steer)
+    out = to_np(plan.run_cpi(_dev(cube, torch.complex64)))
+    e_cell, e_norm = power_errors(out, ref)
+    assert e_norm <= 1e-5 and e_cell <= 1e-3, (e_cell, e_norm)
+
+
+@pytest.mark.parametrize("lf", [0.0, 1e-2, 0.3])
+def test_load_factor_parity(lf):
+    spec = synth.CPISpec(4, 32, 32, 256, 3, 64, 4, cnr_db=20.0, seed=41)
+    d = oracle.Dims(*spec.dims())
+    cube = _cube(spec)
+    ref = oracle.run(d, cube, load_factor=lf)["out"]
+    out = to_np(_plan(spec, load_factor=lf).run_cpi(_dev(cube, torch.complex64)))
+    e_cell, e_norm = power_errors(out, ref)
+    assert e_norm <= 1e-5 and e_cell <= 1e-3, (lf, e_cell, e_norm)
+
+
+def test_not_positive_definite_systems_are_flagged_and_zeroed():
+    spec = synth.CPISpec(1, 4, 4, 12, 2, 4, 2, cnr_db=None, seed=51)   # D=2, 4 x 3 systems
+    d = oracle.Dims(*spec.dims())
+    rng = np.random.default_rng(5)
+    cov = np.zeros((4, 3, 2, 2), np.complex128)
+    for k in range(4):
+        for b in range(3):
+            M = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+            cov[k, b] = M @ M.conj().T + np.eye(2)
+    cov[1, 2] = np.diag([1.0, -5.0])                 # indefinite, negative trace
+    cov[3, 0, 0, 0] = np.nan                         # non-finite input
+    ref, status, nf = oracle.weights(d, cov)
+    assert nf == 2
+    plan = _plan(spec)
+    wts = to_np(plan.solve_weights(_dev(cov, torch.complex128)))
+    code, failed = plan.status()
+    assert code == stap.STAP_ERR_NOT_POSDEF and failed == 2
+    assert np.all(wts[1, 2] == 0) and np.all(wts[3, 0] == 0)
+    good = status == 0
+    err = np.linalg.norm(wts[good] - ref[good], axis=-1) / np.linalg.norm(ref[good], axis=-1)
+    assert np.max(err) <= 2 * EPS32 * np.sqrt(2)
+    assert plan.status() == (stap.STAP_OK, 0)        # cleared by the previous read
+
+
+def test_standard_workload_full_size_parity_and_launch_configuration():
+    """The benchmark workload at full size, through the same run_cpi call the
+    benchmark times, against the oracle on every cell."""
+    spec = synth.standard_cpi()
+    d = oracle.Dims(*spec.dims())
+    cube = _cube(spec)
+    res = oracle.run(d, cube, keep=True)
+    plan = _plan(spec)
+    out = to_np(plan.run_cpi(_dev(cube, torch.complex64)))
+    e_cell, e_norm = power_errors(out, res["out"])
+    print(f"standard workload: max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
+    assert e_norm <= 1e-5 and e_cell <= 1e-3
