@@ -1,0 +1,365 @@
+"""Benchmark of the STAP path on GB300: range-Doppler cells per second.
+
+One step = one whole CPI through ``stap_run_cpi`` (Doppler transform,
+covariance, FP64 loading/Cholesky/solve/refinement, apply) on the standard
+workload: C=4 channels, P=128 pulses, K=256 Doppler bins, R=4096 range cells,
+T=3 (D=12), B=64-cell training blocks, S=16 steering vectors, seeded synthetic
+cube (unit noise, 40 dB CNR clutter ridge, 8 targets).
+
+Timing: inputs resident in HBM, L2 flushed (256 MiB write) between timed steps,
+each step bracketed by CUDA events on the launching stream; barrier and
+synchronize around the timed region; max over ranks.  Under torchrun every rank
+processes its own CPIs (weak scaling, no data-path collective).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (rank
+0 only), each step a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "STAP range-Doppler cells/s per GB300, mixed vs FP32 at ≤1e-3 err vs FP64"
+UNIT = "cells/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM bytes (read + write) per launch of the solve kernel on the standard CPI,
+# from one ncu capture (profiles/fp32_path_standard_cpi_full.md), keyed by a hash
+# of the kernel source so that a changed kernel reports null until re-measured.
+SOLVE_TRAFFIC = {"c7f1bac30e4d5176": 33.64e6}
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "src": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            m = json.load(f)
+        p = {"hbm_gbs": float(m["hbm_gbs"]), "src": "measured"}
+    # FP64 / FP32 ALU peaks from unit counts and the maximum SM clock:
+    # 152 SMs x 2 DFMA lanes/clk (x2 flops) and x 128 FFMA lanes/clk (x2 flops) at 2070 MHz.
+    p["fp64_tflops"] = 152 * 2 * 2 * 2.070e9 / 1e12
+    p["fp32_tflops"] = 152 * 128 * 2 * 2.070e9 / 1e12
+    return p
+
+
+def workload_spec(rank=0):
+    import dataclasses
+    from paper_2203_06233_gb300 import synth
+    return dataclasses.replace(synth.standard_cpi(), sub=rank)
+
+
+def workload_config(spec):
+    C, P, K, R, T, B, S = spec.dims()
+    return {"workload": f"standard CPI C{C} P{P} K{K} R{R} T{T} B{B} S{S} (D={C*T}), "
+                        f"{spec.cnr_db:.0f} dB CNR, {len(spec.targets)} targets",
+            "n_chan": C, "n_pulses": P, "n_dop": K, "n_range": R, "tdof": T,
+            "training_block": B, "n_steering": S, "cells_per_step": K * R,
+            "precision": "plain FP32 contractions, FP64 solve, 1 refinement step",
+            "l2": "flushed between timed steps (256 MiB write); inputs resident in HBM",
+            "parallelism": "one CPI per GPU per step"}
+
+
+def solve_flops(spec, refine=1):
+    """FP64 flops of loading/Cholesky/solve: 8 K NB (D^3/6 + (1 + 2 refine) S D^2)."""
+    C, P, K, R, T, B, S = spec.dims()
+    D, NB = C * T, R // B
+    return 8.0 * K * NB * (D ** 3 / 6.0 + (1 + 2 * refine) * S * D * D)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[3][1:]) if v.lower() == "active"})
+        loaded = [r[0] for r in rows if r[2] > 200.0] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def time_steps(fn, steps, flush, stream):
+    """Per-step device time (ms) with CUDA events, L2 flushed before each step."""
+    import torch
+    evs = []
+    for _ in range(steps):
+        flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def cpu_baseline_oracle(spec, budget_s=12.0):
+    """The oracle, as it stands, on the host cores: whole CPIs until ~budget_s."""
+    import oracle
+    from paper_2203_06233_gb300 import synth
+    d = oracle.Dims(*spec.dims())
+    cube = synth.make_cube(spec)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.run(d, cube)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= 50:
+            break
+    cells = n * spec.n_dop * spec.n_range
+    return {"value": cells / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} whole CPI(s) of the standard workload ({cells} cells) in {el:.1f} s"}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2203_06233_gb300 import stap, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = workload_spec(rank)
+    C, P, K, R, T, B, S = spec.dims()
+    cube_h = synth.make_cube(spec)
+    plan = stap.Plan(spec.dims(), device=dev)
+    cube = torch.from_numpy(cube_h).to(dev)
+    out = torch.empty((S, K, R), dtype=torch.float32, device=dev)
+    flushbuf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def flush():
+        flushbuf.zero_()
+
+    def step():
+        plan.run_cpi(cube, out)
+
+    for _ in range(args.warmup):
+        flush()
+        step()
+    torch.cuda.synchronize()
+    code, failed = plan.status()
+    if code != stap.STAP_OK:
+        raise RuntimeError(f"device status {code} ({failed} failed systems) after warm-up")
+
+    # ---- timed region ----
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        times = time_steps(step, args.steps, flush, stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    cells = K * R
+    value = world * cells * args.steps / (total_ms * 1e-3)
+
+    # ---- per-kernel breakdown (same kernels and launch configuration) ----
+    dop = plan.doppler(cube)
+    cov = plan.covariance(dop)
+    wts = plan.solve_weights(cov)
+    reps = max(20, min(200, args.steps))
+    kt = {
+        "doppler": statistics.mean(time_steps(lambda: plan.doppler(cube, dop), reps, flush, stream)),
+        "covariance": statistics.mean(time_steps(lambda: plan.covariance(dop, cov), reps, flush, stream)),
+        "solve": statistics.mean(time_steps(lambda: plan.solve_weights(cov, wts), reps, flush, stream)),
+        "apply": statistics.mean(time_steps(lambda: plan.apply(dop, wts, out), reps, flush, stream)),
+    }
+    pk = peaks()
+    D, NB = C * T, R // B
+    dop_bytes = 8.0 * C * R * (P + K)
+    cov_real_products = 4.0 * K * NB * B * D * (D + 1) / 2
+    apply_flops = 8.0 * K * R * S * D
+    apply_bytes = 8.0 * C * K * R + 8.0 * K * NB * S * D + 4.0 * S * K * R
+    sf = solve_flops(spec, refine=1)
+    kernels = {
+        "doppler": {"ms": kt["doppler"], "bound": "hbm", "bytes": dop_bytes,
+                    "achieved_gbs": dop_bytes / kt["doppler"] / 1e6,
+                    "frac": dop_bytes / kt["doppler"] / 1e6 / pk["hbm_gbs"]},
+        "covariance": {"ms": kt["covariance"], "bound": "alu",
+                       "fp32_instr": 10.0 * cov_real_products,
+                       "achieved_tops": 10.0 * cov_real_products / kt["covariance"] / 1e9,
+                       "frac": 10.0 * cov_real_products / kt["covariance"] / 1e9 / (pk["fp32_tflops"] / 2)},
+        "solve": {"ms": kt["solve"], "bound": "alu", "fp64_flops": sf,
+                  "achieved_tflops": sf / kt["solve"] / 1e9,
+                  "frac": sf / kt["solve"] / 1e9 / pk["fp64_tflops"]},
+        "apply": {"ms": kt["apply"], "bound": "alu", "fp32_flops": apply_flops, "bytes": apply_bytes,
+                  "achieved_tflops": apply_flops / kt["apply"] / 1e9,
+                  "frac": apply_flops / kt["apply"] / 1e9 / pk["fp32_tflops"],
+                  "hbm_frac": apply_bytes / kt["apply"] / 1e6 / pk["hbm_gbs"]},
+    }
+    roofline = {"kernel": "solve_kernel (FP64 loading, Cholesky, solves, refinement)",
+                "bound": "alu", "achieved": kernels["solve"]["achieved_tflops"],
+                "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                "frac": kernels["solve"]["frac"], "traffic": None,
+                "peak_src": "FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (unit count and max clock)"}
+    roofline["traffic"] = SOLVE_TRAFFIC.get(kernel_hash())
+
+    # ---- end to end through the public API from pinned host buffers ----
+    cube_pin = torch.from_numpy(cube_h).pin_memory()
+    out_pin = torch.empty((S, K, R), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        cube.copy_(cube_pin, non_blocking=True)
+        plan.run_cpi(cube, out)
+        out_pin.copy_(out, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = statistics.mean(time_steps(e2e_step, reps, flush, stream))
+    e2e_val = world * cells / (e2e_ms * 1e-3)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": workload_config(spec),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": cube_h.nbytes,
+                "d2h_bytes_per_step": S * K * R * 4, "ms_per_step": e2e_ms},
+        "gpu_launches": 4 * args.steps,
+        "roofline": roofline,
+        "kernels": kernels,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_oracle(spec)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2203_06233_gb300", "csrc", "solve.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2203_06233_gb300 import synth
+    spec = workload_spec(0)
+    d = oracle.Dims(*spec.dims())
+    cube = synth.make_cube(spec)
+    B, NB, K = spec.training_block, spec.NB, spec.n_dop
+    # size each step (a range window of whole blocks) so the run ends in ~3 minutes
+    t0 = time.perf_counter()
+    oracle.run(d, cube, r0=0, nr=B)
+    per_block = time.perf_counter() - t0
+    nblk = int(max(1, min(NB, 150.0 / max(1, args.steps + args.warmup) / max(per_block, 1e-6))))
+    nr = nblk * B
+
+    def one(i):
+        r0 = ((i * nblk) % NB) * B
+        r0 = min(r0, (NB - nblk) * B)
+        oracle.run(d, cube, r0=r0, nr=nr)
+
+    for i in range(args.warmup):
+        one(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        one(i)
+    el = time.perf_counter() - t0
+    value = args.steps * K * nr / el
+    sample = f"each step: range window of {nblk} block(s) x {B} cells x {K} bins of the standard CPI"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(spec), "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
