@@ -142,6 +142,42 @@ stap_status stap_apply(stap_plan plan, const void* dop_c64, const void* wts_c64,
  * are HOST arrays of n_cpi device pointers. */
 stap_status stap_run_cpi(stap_plan plan, const void* const* cubes, float* const* outs);
 
+/* Size of the device scratch array that libstap itself holds for
+ * stap_run_cpi_noalloc: 16 MiB on every GPU that loads the library, kept
+ * until the process exits. */
+#define STAP_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* No-allocation form of stap_run_cpi for one CPI.  The paper has no
+ * counterpart: this exists for callers that must not allocate device memory
+ * themselves -- for example a real-time radar loop that forbids cudaMalloc
+ * after start-up (it can synchronise the whole device and its latency is
+ * unbounded), or a host application whose own pool owns all device memory and
+ * gives none to libraries.  Such callers cannot provide the workspace that
+ * stap_run_cpi needs, so this call uses a fixed scratch array inside the
+ * library (STAP_NOALLOC_SCRATCH_BYTES) instead, and makes no cudaMalloc,
+ * cudaFree or other allocating call.
+ *
+ * dims/opt (opt may be NULL) describe the CPI as for stap_plan_create;
+ * cube_c64: device c64 [C][P][R]; out: device float [S][K][R]; cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream).  If n_failed_systems is not
+ * NULL the call waits for the stream and stores the number of covariances
+ * that were not positive definite (returning STAP_ERR_NOT_POSDEF if > 0);
+ * otherwise it returns as soon as the work is queued.
+ *
+ * Errors: the shape/option errors of stap_plan_create; STAP_ERR_NO_WORKSPACE
+ * if the CPI needs more scratch than STAP_NOALLOC_SCRATCH_BYTES (the
+ * stap_plan_workspace_sizes run_bytes of the same dims), rejected before any
+ * CUDA call; STAP_ERR_CUDA if a CUDA call fails.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current) and keeps it; make that first call before any stream
+ * capture begins.  Every call on a device shares the one array: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and give
+ * wrong results, so order them.  Each call clears the status it uses and
+ * rewrites the tables and intermediates before reading them. */
+stap_status stap_run_cpi_noalloc(const stap_dims* dims, const stap_options* opt, void* cuda_stream,
+                                 const void* cube_c64, float* out, int64_t* n_failed_systems);
+
 /* Wait for the plan's stream, then report and clear the device status.
  * *n_failed_systems (if not NULL) = covariances found not positive definite
  * since the last call; returns STAP_ERR_NOT_POSDEF if that is > 0,

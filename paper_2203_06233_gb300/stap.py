@@ -35,7 +35,11 @@ EXPORTED = (
     "stap_plan_set_workspace", "stap_plan_set_stream", "stap_plan_set_steering",
     "stap_plan_destroy", "stap_doppler", "stap_covariance", "stap_solve_weights", "stap_apply",
     "stap_run_cpi", "stap_get_status", "stap_status_string", "stap_abi_version",
+    "stap_run_cpi_noalloc",
 )
+
+# size of the library-owned scratch array used by stap_run_cpi_noalloc
+STAP_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class StapError(RuntimeError):
@@ -88,6 +92,8 @@ def lib():
             L.stap_status_string.argtypes = [ctypes.c_int]
             L.stap_status_string.restype = ctypes.c_char_p
             L.stap_abi_version.argtypes = []
+            L.stap_run_cpi_noalloc.argtypes = [ctypes.POINTER(stap_dims), ctypes.POINTER(stap_options),
+                                               vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
             for f in EXPORTED:
                 if f not in ("stap_options_default", "stap_status_string"):
                     getattr(L, f).restype = ctypes.c_int
@@ -215,6 +221,26 @@ def stap_get_status(plan):
     code = lib().stap_get_status(plan, ctypes.byref(n))
     _check(code, "stap_get_status", ok=(STAP_OK, STAP_ERR_NOT_POSDEF, STAP_ERR_TIMEOUT))
     return code, n.value
+
+
+def stap_run_cpi_noalloc(dims, cube: torch.Tensor, out: torch.Tensor, opts=None, stream=None,
+                         want_status: bool = False):
+    """Whole chain for one CPI using the library's own fixed scratch array.
+
+    For callers that must not allocate device memory: nothing is allocated
+    here or in the library (``cube`` and ``out`` are the caller's).  With
+    ``want_status`` the call waits for the stream and returns the number of
+    covariances that were not positive definite; otherwise it returns None
+    once the work is queued.
+    """
+    d = _dims(dims)
+    n = ctypes.c_int64(0)
+    code = lib().stap_run_cpi_noalloc(ctypes.byref(d), ctypes.byref(opts) if opts is not None else None,
+                                      _stream_ptr(stream), ctypes.c_void_p(cube.data_ptr()),
+                                      ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.byref(n) if want_status else None)
+    _check(code, "stap_run_cpi_noalloc", ok=(STAP_OK, STAP_ERR_NOT_POSDEF) if want_status else (STAP_OK,))
+    return n.value if want_status else None
 
 
 def stap_abi_version() -> int:
