@@ -3,69 +3,159 @@
 // the last step of the STAP kernel of arXiv 2203.06233 Sec. 4.2 (the adaptive
 // filter output |w^H x|^2).
 //
-// Mapping: a CTA owns one (Doppler bin k, block b) system.  Its S x D weights
-// go to shared memory transposed ([d][s]) and its D x B snapshot tile is
-// staged by the same gather as the covariance kernel.  A thread owns one range
-// cell and SB consecutive steering vectors: per snapshot entry it reads x once
-// and SB weights as broadcasts, so shared-memory traffic is one read per FMA
-// pair.  Output rows are written coalesced along range.
+// Mapping: a CTA owns NBB consecutive training blocks of one Doppler bin (up
+// to 256 range cells).  Their weights go to shared memory as [block][d][s]
+// and their D x cells snapshot tile is staged by the same gather as the
+// covariance kernel.  A thread owns one range cell and walks the steering
+// vectors in chunks of SC, keeping SC complex accumulators in registers: per
+// snapshot entry it reads x once and the chunk's weights as broadcast 16-byte
+// loads, i.e. 1 + SC/2 shared loads for 4*SC FMAs.  Each output row
+// out[s][k][cells] is written coalesced along range.
 #include "snapshots.cuh"
 
 namespace stap {
 namespace {
 
-constexpr int SB = 4;  // steering vectors per thread
+constexpr int SC = 8;       // steering vectors per register chunk
+constexpr int kThreads = 256;
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kThreads)
 apply_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts, float* __restrict__ out,
-             int C, int K, int R, int T, int B, int S, int BC) {
-  extern __shared__ float2 sm[];
+             int C, int K, int R, int T, int B, int S, int NBB, int CC) {
+  extern __shared__ float4 sm4[];
+  float2* sm = reinterpret_cast<float2*>(sm4);
   const int D = C * T;
   const int NB = R / B;
-  const int b = blockIdx.x, k = blockIdx.y;
-  const int ld = BC + 1;
-  float2* ws = sm;                     // [D][S]
-  float2* xs = sm + (size_t)D * S;     // [D][ld]
-  const float2* wsrc = wts + ((size_t)k * NB + b) * S * D;
-  for (int idx = threadIdx.x; idx < S * D; idx += blockDim.x) {
-    const int s = idx / D, d = idx - s * D;
-    ws[d * S + s] = __ldg(wsrc + idx);
+  const int k = blockIdx.y;
+  const int b0 = blockIdx.x * NBB;
+  const int nbb = min(NBB, NB - b0);
+  const int Sp = (S + SC - 1) / SC * SC;        // padded steering count (zero weights beyond S)
+  float2* ws = sm;                              // [nbb][D][Sp]
+  float2* xs = sm + (size_t)NBB * D * Sp;       // [D][CC + 1]
+  const int ld = CC + 1;
+
+  {  // weights of the nbb blocks, [j][d][s] in shared memory (zero for s >= S)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int row = warp; row < nbb * Sp; row += nw) {   // row = (block j, steering s)
+      const int j = row / Sp, s = row - j * Sp;
+      const float2* src = wts + (((size_t)k * NB + b0 + j) * S + s) * D;
+      for (int d = lane; d < D; d += 32)
+        ws[((size_t)j * D + d) * Sp + s] = (s < S) ? __ldg(src + d) : make_float2(0.f, 0.f);
+    }
   }
-  const int ngroups = (S + SB - 1) / SB;
-  for (int c0 = 0; c0 < B; c0 += BC) {
-    const int bc = min(BC, B - c0);
+  const int cells = nbb * B;
+  for (int c0 = 0; c0 < cells; c0 += CC) {
+    const int cc = min(CC, cells - c0);
     __syncthreads();
-    stage_snapshots(xs, ld, dop, C, K, R, T, k, b * B + c0, bc);
+    stage_snapshots(xs, ld, dop, C, K, R, T, k, b0 * B + c0, cc);
     __syncthreads();
-    for (int it = threadIdx.x; it < bc * ngroups; it += blockDim.x) {
-      const int g = it / bc, rr = it - g * bc;
-      const int s0 = g * SB;
-      float2 acc[SB];
+    for (int rr = threadIdx.x; rr < cc; rr += blockDim.x) {
+      const int j = (c0 + rr) / B;
+      const float2* wj = ws + (size_t)j * D * Sp;
+      const size_t r = (size_t)b0 * B + c0 + rr;
+      for (int s0 = 0; s0 < S; s0 += SC) {
+        float2 acc[SC];
 #pragma unroll
-      for (int q = 0; q < SB; ++q) acc[q] = make_float2(0.f, 0.f);
-      for (int d = 0; d < D; ++d) {
-        const float2 x = xs[d * ld + rr];
-        const float2* wd = ws + d * S + s0;
+        for (int q = 0; q < SC; ++q) acc[q] = make_float2(0.f, 0.f);
+        for (int d = 0; d < D; ++d) {
+          const float2 x = xs[d * ld + rr];
+          const float4* w4 = reinterpret_cast<const float4*>(wj + (size_t)d * Sp + s0);
 #pragma unroll
-        for (int q = 0; q < SB; ++q) {
-          if (s0 + q < S) {
-            const float2 w = wd[q];
+          for (int q = 0; q < SC / 2; ++q) {
+            const float4 w = w4[q];      // weights s0+2q and s0+2q+1
             // acc += conj(w) * x
-            acc[q].x = fmaf(w.x, x.x, acc[q].x);
-            acc[q].x = fmaf(w.y, x.y, acc[q].x);
-            acc[q].y = fmaf(w.x, x.y, acc[q].y);
-            acc[q].y = fmaf(-w.y, x.x, acc[q].y);
+            acc[2 * q].x = fmaf(w.x, x.x, acc[2 * q].x);
+            acc[2 * q].x = fmaf(w.y, x.y, acc[2 * q].x);
+            acc[2 * q].y = fmaf(w.x, x.y, acc[2 * q].y);
+            acc[2 * q].y = fmaf(-w.y, x.x, acc[2 * q].y);
+            acc[2 * q + 1].x = fmaf(w.z, x.x, acc[2 * q + 1].x);
+            acc[2 * q + 1].x = fmaf(w.w, x.y, acc[2 * q + 1].x);
+            acc[2 * q + 1].y = fmaf(w.z, x.y, acc[2 * q + 1].y);
+            acc[2 * q + 1].y = fmaf(-w.w, x.x, acc[2 * q + 1].y);
           }
         }
-      }
-      const size_t r = (size_t)b * B + c0 + rr;
 #pragma unroll
-      for (int q = 0; q < SB; ++q) {
-        if (s0 + q < S)
-          out[((size_t)(s0 + q) * K + k) * R + r] = fmaf(acc[q].x, acc[q].x, acc[q].y * acc[q].y);
+        for (int q = 0; q < SC; ++q)
+          if (s0 + q < S)
+            out[((size_t)(s0 + q) * K + k) * R + r] = fmaf(acc[q].x, acc[q].x, acc[q].y * acc[q].y);
       }
     }
   }
+}
+
+// Register-resident form for small even D (the common shapes).  A thread owns
+// two adjacent range cells: their 2 x D snapshot entries are loaded straight
+// from the Doppler cube with one 16-byte load per entry (coalesced along
+// range; T neighbouring bins are re-read through L2 by neighbouring CTAs) and
+// stay in registers, while the weights of the CTA's blocks sit in shared
+// memory as [block][s][d].  For each steering vector the thread reads its
+// weights as D/2 broadcast 16-byte loads and does 8 D FMAs: FMA-bound.
+constexpr int kRegCells = 2 * kThreads;     // range cells per CTA
+
+template <int D>
+__global__ void __launch_bounds__(kThreads)
+apply_reg_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
+                 float* __restrict__ out, int C, int K, int R, int T, int B, int S) {
+  extern __shared__ float4 sm4[];
+  float2* ws = reinterpret_cast<float2*>(sm4);    // [nblk][S][D]
+  const int NB = R / B;
+  const int k = blockIdx.y;
+  const int cta_r0 = blockIdx.x * kRegCells;
+  const int jb0 = cta_r0 / B;
+  const int jb1 = min(NB - 1, (min(cta_r0 + kRegCells, R) - 1) / B);
+  const int nblk = jb1 - jb0 + 1;
+  {
+    const float2* src = wts + ((size_t)k * NB + jb0) * S * D;
+    const int n = nblk * S * D;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ws[i] = __ldg(src + i);
+  }
+  const int r0 = cta_r0 + 2 * threadIdx.x;
+  float4 x[D];                                    // (cell r0, cell r0 + 1) per entry
+  if (r0 < R) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int t = d / C, c = d - t * C;
+      const int kk = wrap_bin(k + t - T / 2, K);
+      x[d] = __ldg(reinterpret_cast<const float4*>(dop + ((size_t)c * K + kk) * R + r0));
+    }
+  }
+  __syncthreads();
+  if (r0 >= R) return;
+  const int j = r0 / B - jb0;                      // B even: both cells in one block
+  const float4* wj = reinterpret_cast<const float4*>(ws + (size_t)j * S * D);
+  for (int s = 0; s < S; ++s) {
+    float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
+#pragma unroll
+    for (int d2 = 0; d2 < D / 2; ++d2) {
+      const float4 w = wj[s * (D / 2) + d2];        // w_d = (w.x, w.y), w_{d+1} = (w.z, w.w)
+      const float4 xa = x[2 * d2], xb = x[2 * d2 + 1];
+      // acc += conj(w) * x for both cells
+      a0r = fmaf(w.x, xa.x, a0r); a0r = fmaf(w.y, xa.y, a0r);
+      a0i = fmaf(w.x, xa.y, a0i); a0i = fmaf(-w.y, xa.x, a0i);
+      a1r = fmaf(w.x, xa.z, a1r); a1r = fmaf(w.y, xa.w, a1r);
+      a1i = fmaf(w.x, xa.w, a1i); a1i = fmaf(-w.y, xa.z, a1i);
+      a0r = fmaf(w.z, xb.x, a0r); a0r = fmaf(w.w, xb.y, a0r);
+      a0i = fmaf(w.z, xb.y, a0i); a0i = fmaf(-w.w, xb.x, a0i);
+      a1r = fmaf(w.z, xb.z, a1r); a1r = fmaf(w.w, xb.w, a1r);
+      a1i = fmaf(w.z, xb.w, a1i); a1i = fmaf(-w.w, xb.z, a1i);
+    }
+    *reinterpret_cast<float2*>(out + ((size_t)s * K + k) * R + r0) =
+        make_float2(fmaf(a0r, a0r, a0i * a0i), fmaf(a1r, a1r, a1i * a1i));
+  }
+}
+
+template <int D>
+cudaError_t launch_apply_reg(const float2* dop, const float2* wts, float* out, int C, int K, int R,
+                             int T, int B, int S, cudaStream_t s) {
+  const int NB = R / B;
+  const int max_blk = kRegCells / B + 2;
+  const size_t smem = (size_t)(max_blk < NB ? max_blk : NB) * S * D * sizeof(float2);
+  static int set_bytes[64] = {0};
+  cudaError_t e = ensure_smem(apply_reg_kernel<D>, smem, set_bytes);
+  if (e != cudaSuccess) return e;
+  dim3 grid((R + kRegCells - 1) / kRegCells, K);
+  apply_reg_kernel<D><<<grid, kThreads, smem, s>>>(dop, wts, out, C, K, R, T, B, S);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -75,18 +165,42 @@ cudaError_t launch_apply(const float2* dop, const float2* wts, float* out, int C
   const int D = C * T;
   const int NB = R / B;
   if (NB == 0) return cudaSuccess;
-  constexpr size_t kBudget = 96 * 1024;
-  const size_t wbytes = (size_t)D * S * sizeof(float2);
-  if (wbytes + (size_t)D * 2 * sizeof(float2) > kBudget) return cudaErrorInvalidValue;
-  int BC = B;
-  if (wbytes + (size_t)D * (BC + 1) * sizeof(float2) > kBudget)
-    BC = (int)((kBudget - wbytes) / ((size_t)D * sizeof(float2))) - 1;
-  const size_t smem = wbytes + (size_t)D * (BC + 1) * sizeof(float2);
+  // register-resident form: even D <= 24, even B (cell pairs never straddle a
+  // block and 16-byte loads stay aligned), weights of a CTA within 160 KB
+  if (D % 2 == 0 && D <= 24 && B % 2 == 0 &&
+      (size_t)(kRegCells / B + 2) * S * D * sizeof(float2) <= 160 * 1024) {
+    switch (D) {
+      case 2: return launch_apply_reg<2>(dop, wts, out, C, K, R, T, B, S, s);
+      case 4: return launch_apply_reg<4>(dop, wts, out, C, K, R, T, B, S, s);
+      case 6: return launch_apply_reg<6>(dop, wts, out, C, K, R, T, B, S, s);
+      case 8: return launch_apply_reg<8>(dop, wts, out, C, K, R, T, B, S, s);
+      case 10: return launch_apply_reg<10>(dop, wts, out, C, K, R, T, B, S, s);
+      case 12: return launch_apply_reg<12>(dop, wts, out, C, K, R, T, B, S, s);
+      case 14: return launch_apply_reg<14>(dop, wts, out, C, K, R, T, B, S, s);
+      case 16: return launch_apply_reg<16>(dop, wts, out, C, K, R, T, B, S, s);
+      case 18: return launch_apply_reg<18>(dop, wts, out, C, K, R, T, B, S, s);
+      case 20: return launch_apply_reg<20>(dop, wts, out, C, K, R, T, B, S, s);
+      case 22: return launch_apply_reg<22>(dop, wts, out, C, K, R, T, B, S, s);
+      case 24: return launch_apply_reg<24>(dop, wts, out, C, K, R, T, B, S, s);
+      default: break;
+    }
+  }
+  constexpr size_t kBudget = 160 * 1024;
+  const int Sp = (S + SC - 1) / SC * SC;
+  int NBB = B >= kThreads ? 1 : kThreads / B;   // up to 256 cells per CTA
+  if (NBB > NB) NBB = NB;
+  auto wbytes = [&](int nbb) { return (size_t)nbb * D * Sp * sizeof(float2); };
+  while (NBB > 1 && wbytes(NBB) > kBudget / 2) --NBB;
+  if (wbytes(NBB) + (size_t)D * 2 * sizeof(float2) > kBudget) return cudaErrorInvalidValue;
+  int CC = NBB * B;                              // cells staged per pass
+  if (wbytes(NBB) + (size_t)D * (CC + 1) * sizeof(float2) > kBudget)
+    CC = (int)((kBudget - wbytes(NBB)) / ((size_t)D * sizeof(float2))) - 1;
+  const size_t smem = wbytes(NBB) + (size_t)D * (CC + 1) * sizeof(float2);
   static int set_bytes[64] = {0};
   cudaError_t e = ensure_smem(apply_kernel, smem, set_bytes);
   if (e != cudaSuccess) return e;
-  dim3 grid(NB, K);
-  apply_kernel<<<grid, 256, smem, s>>>(dop, wts, out, C, K, R, T, B, S, BC);
+  dim3 grid((NB + NBB - 1) / NBB, K);
+  apply_kernel<<<grid, kThreads, smem, s>>>(dop, wts, out, C, K, R, T, B, S, NBB, CC);
   return cudaGetLastError();
 }
 

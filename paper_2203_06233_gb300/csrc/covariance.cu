@@ -94,6 +94,151 @@ covariance_ff_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Bin-pair form.  Block (t, t') of R_k is the cross-covariance of bins
+// k + m_t and k + m_t' (m_t = t - floor(T/2)):
+//   R_k[(t,c),(t',c')] = Q(k + m_t, k + m_t')[c][c'],
+//   Q(k1, k2)[c][c'] = (1/B) sum_r X_c(k1, r) conj(X_c'(k2, r)),
+// and Q(k2, k1) = Q(k1, k2)^H.  Neighbouring bins share these blocks, so a CTA
+// that owns KT consecutive bins of one range block computes every Q(k1, k1+d),
+// d < T, once (C(C+1)/2 entries for d = 0, C^2 otherwise) and assembles its KT
+// covariances from them: T C^2 - C(C-1)/2 products per bin instead of
+// D(D+1)/2.
+//
+// Accumulation on a fixed grid (error-free transformation in the manner of
+// Rump, Ogita & Oishi, "Accurate floating-point summation part I", SISC 2008,
+// ExtractScalar): for an entry whose row maxima are m1, m2 pick the power of
+// two sig >= 4 B m1 m2.  For each product, s = fma(a, b, sig) rounds a*b onto
+// the grid of sig, q = s - sig is exact, and the running sum of the q stays
+// exact because every q lies on that grid and |sum| <= sig/2.  The remainder
+// fma(a, b, -q) (|.| <= ulp(sig)/2) goes to a second FP32 accumulator.  Five
+// FP32 instructions per real product; the pair is combined in FP64 at the end.
+constexpr int kPairThreads = 256;
+
+__device__ __forceinline__ float pow2_ceil(float x) {  // smallest power of two >= x
+  if (!(x > 0.f)) return 1.0f;
+  unsigned u = __float_as_uint(x);
+  unsigned e = u >> 23;
+  if (u & 0x7fffffu) e += 1;
+  if (e < 1) e = 1;
+  if (e > 254) e = 254;
+  return __uint_as_float(e << 23);
+}
+
+__device__ __forceinline__ void grid_add(float& hi, float& lo, float a, float b, float sig) {
+  const float s = __fmaf_rn(a, b, sig);
+  const float q = __fsub_rn(s, sig);
+  const float r = __fmaf_rn(a, b, -q);
+  hi = __fadd_rn(hi, q);
+  lo = __fadd_rn(lo, r);
+}
+
+__global__ void __launch_bounds__(kPairThreads)
+covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K,
+                        int R, int T, int B, int NB, int KT) {
+  extern __shared__ double2 smd[];
+  const int b = blockIdx.x;
+  const int k0 = blockIdx.y * KT;
+  const int h = T / 2;
+  const int NBIN = KT + T - 1;                    // staged bins k0-h .. k0+KT-1+(T-1-h)
+  const int nrows = NBIN * C;
+  const int ld = B + 1;
+  const int Ediag = C * (C + 1) / 2, Eoff = C * C;
+  // items: d-major; d = 0 has NBIN * Ediag items, d > 0 has (NBIN - d) * Eoff
+  const int nitems = NBIN * Ediag + (T - 1) * (2 * NBIN - T) / 2 * Eoff;
+  double2* Q = smd;                                             // [nitems]
+  float* m = reinterpret_cast<float*>(Q + nitems);              // [nrows] row maxima
+  float2* X = reinterpret_cast<float2*>(m + ((nrows + 3) & ~3));  // [nrows][ld]
+
+  // stage rows (bin j, channel c) of this range block
+  for (int idx = threadIdx.x; idx < nrows * B; idx += blockDim.x) {
+    const int cell = idx % B, row = idx / B;
+    const int j = row / C, c = row - j * C;
+    const int kk = wrap_bin(k0 - h + j, K);
+    X[row * ld + cell] = __ldg(dop + ((size_t)c * K + kk) * R + (size_t)b * B + cell);
+  }
+  __syncthreads();
+  // row maxima of |re|, |im| (one warp per row)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int row = warp; row < nrows; row += nwarps) {
+    float mx = 0.f;
+    for (int cell = lane; cell < B; cell += 32) {
+      const float2 x = X[row * ld + cell];
+      mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) m[row] = mx;
+  }
+  __syncthreads();
+
+  const double invB = 1.0 / (double)B;
+  const float fourB = 4.0f * (float)B;
+  for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+    int d = 0, rem = it;
+    if (rem >= NBIN * Ediag) {
+      rem -= NBIN * Ediag;
+      d = 1;
+      while (rem >= (NBIN - d) * Eoff) {
+        rem -= (NBIN - d) * Eoff;
+        ++d;
+      }
+    }
+    int j1, c1, c2;
+    if (d == 0) {
+      j1 = rem / Ediag;
+      unpack_lower(rem - j1 * Ediag, c1, c2);
+    } else {
+      j1 = rem / Eoff;
+      const int e = rem - j1 * Eoff;
+      c1 = e / C;
+      c2 = e - c1 * C;
+    }
+    const int ra = j1 * C + c1, rb = (j1 + d) * C + c2;
+    const float2* xa = X + ra * ld;
+    const float2* xb = X + rb * ld;
+    const float sig = pow2_ceil(fourB * m[ra] * m[rb]);
+    float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
+    for (int cell = 0; cell < B; ++cell) {
+      const float2 a = xa[cell], bb = xb[cell];
+      // a * conj(bb) = (a.x bb.x + a.y bb.y) + i (a.y bb.x - a.x bb.y)
+      grid_add(hr, lr, a.x, bb.x, sig);
+      grid_add(hr, lr, a.y, bb.y, sig);
+      grid_add(hi, li, a.y, bb.x, sig);
+      grid_add(hi, li, -a.x, bb.y, sig);
+    }
+    Q[it] = make_double2(((double)hr + (double)lr) * invB, ((double)hi + (double)li) * invB);
+  }
+  __syncthreads();
+
+  // assemble R_k for the KT bins of this tile
+  const int D = C * T;
+  auto qat = [&](int j1, int d, int c1, int c2) -> double2 {  // Q(bin j1, bin j1+d)[c1][c2]
+    if (d == 0) {
+      if (c1 >= c2) return Q[j1 * Ediag + c1 * (c1 + 1) / 2 + c2];
+      const double2 v = Q[j1 * Ediag + c2 * (c2 + 1) / 2 + c1];
+      return make_double2(v.x, -v.y);
+    }
+    int off = NBIN * Ediag;
+    for (int e = 1; e < d; ++e) off += (NBIN - e) * Eoff;
+    return Q[off + j1 * Eoff + c1 * C + c2];
+  };
+  for (int idx = threadIdx.x; idx < KT * D * D; idx += blockDim.x) {
+    const int kl = idx / (D * D);
+    const int e = idx - kl * D * D;
+    const int i = e / D, l = e - i * D;
+    const int t1 = i / C, c1 = i - t1 * C, t2 = l / C, c2 = l - t2 * C;
+    double2 v;
+    if (t1 <= t2) {
+      v = qat(kl + t1, t2 - t1, c1, c2);
+    } else {
+      const double2 w = qat(kl + t2, t1 - t2, c2, c1);
+      v = make_double2(w.x, -w.y);
+    }
+    if (i == l) v.y = 0.0;
+    cov[(((size_t)(k0 + kl) * NB + b) * D + i) * D + l] = v;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K, int R, int T,
@@ -101,6 +246,31 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
   const int D = C * T;
   const int E = D * (D + 1) / 2;
   const int NB = R / B;
+  if (NB == 0) return cudaSuccess;
+  // bin-pair kernel: the whole B-cell tile of KT + T - 1 bins in shared memory
+  {
+    constexpr size_t kPairBudget = 200 * 1024;
+    auto pair_smem = [&](int kt) {
+      const int nbin = kt + T - 1;
+      const size_t nitems = (size_t)nbin * (C * (C + 1) / 2) +
+                            (size_t)(T - 1) * (2 * nbin - T) / 2 * C * C;
+      const size_t nrows = (size_t)nbin * C;
+      return nitems * sizeof(double2) + ((nrows + 3) & ~(size_t)3) * sizeof(float) +
+             nrows * (B + 1) * sizeof(float2);
+    };
+    int KT = K < 16 ? K : 16;  // K is a power of two, so KT divides it
+    while (KT > 1 && pair_smem(KT) > kPairBudget) KT >>= 1;
+    if (pair_smem(KT) <= kPairBudget) {
+      const size_t smem = pair_smem(KT);
+      static int set_bytes[64] = {0};
+      cudaError_t e = ensure_smem(covariance_pairs_kernel, smem, set_bytes);
+      if (e != cudaSuccess) return e;
+      dim3 grid(NB, K / KT);
+      covariance_pairs_kernel<<<grid, kPairThreads, smem, s>>>(dop, cov, C, K, R, T, B, NB, KT);
+      return cudaGetLastError();
+    }
+  }
+  // general form: one tile per system, cells in chunks
   constexpr size_t kSmemBudget = 96 * 1024;
   int BC = B;
   if ((size_t)D * (BC + 1) * sizeof(float2) > kSmemBudget)

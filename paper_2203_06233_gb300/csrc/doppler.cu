@@ -3,15 +3,15 @@
 // computed as a zero-padded length-K FFT over the pulse axis.
 //
 // Layout: the pulse axis has stride R, the range axis is contiguous.  A CTA
-// owns one channel and TR consecutive range cells and does TR independent
+// owns one channel and TR (8-32) consecutive range cells and does TR independent
 // length-K FFTs by the four-step split K = N1 * N2:
 //   input  index n = n1 + N1 n2,   output index k = k2 + N2 k1,
 //   Y[n1][k2] = W_K^{n1 k2} * sum_{n2} x[n1 + N1 n2] W_{N2}^{n2 k2}     (pass A)
 //   X[k2 + N2 k1] = sum_{n1} Y[n1][k2] W_{N1}^{n1 k1}                    (pass B)
 // Each thread does one short FFT in registers per pass; the only shared-memory
 // traffic is the Y transpose between the passes.  Global loads (pass A) and
-// stores (pass B) are coalesced along range: a warp touches 32 (or 16)
-// consecutive complex samples of one pulse/bin row.  The window and the zero
+// stores (pass B) are coalesced along range: a warp touches runs of TR
+// consecutive complex samples of pulse/bin rows.  The window and the zero
 // padding are applied while loading.  HBM traffic is the algorithmic minimum:
 // 8*C*P*R bytes read + 8*C*K*R bytes written.
 #include "snapshots.cuh"
@@ -124,7 +124,10 @@ cudaError_t launch_logk(const float2* cube, float2* dop, const float* win, const
                         int P, int R, cudaStream_t s) {
   constexpr int K = 1 << LOGK;
   constexpr int N1 = 1 << ((LOGK + 1) / 2);
-  constexpr int TR = (N1 >= 32) ? 16 : 32;
+  // range cells per CTA: 256-thread CTAs (TR * N1) of at most 32 columns, so
+  // that several CTAs fit per SM; a warp still covers >= 64 contiguous bytes
+  // of a row (two full 32-byte sectors)
+  constexpr int TR = (N1 >= 32) ? 8 : (N1 >= 16 ? 16 : 32);
   const size_t smem = (size_t)K * sizeof(float2) * (1 + TR);
   auto kern = doppler_fft_kernel<LOGK, TR>;
   static int set_bytes[64] = {0};

@@ -21,10 +21,14 @@ struct Cpi {
   stap_dims d{};
   int D = 0, NB = 0;
   // offsets of this CPI's tables inside the workspace
-  size_t win_off = 0, tw_off = 0, steer_off = 0;
+  size_t win_off = 0, tw_off = 0, steer_off = 0, g_off = 0, a_off = 0;
   std::vector<float> win;       // [P]
   std::vector<float> tw;        // [K][2]
   std::vector<double> steer;    // [S][D][2]
+  // steer[s] = g (x) a_s for the default table: temporal factor g [T][2] and
+  // spatial factors a [S][C][2]; cleared when the caller replaces the table
+  bool separable = false;
+  std::vector<double> sep_g, sep_a;
   size_t dop_elems() const { return (size_t)d.n_chan * d.n_dop * d.n_range; }
   size_t cov_elems() const { return (size_t)d.n_dop * NB * D * D; }
   size_t wts_elems() const { return (size_t)d.n_dop * NB * d.n_steering * D; }
@@ -82,18 +86,29 @@ void make_tables(Cpi& c) {
   }
   const int D = c.D;
   c.steer.assign(2 * (size_t)S * D, 0.0);
+  c.sep_g.assign(2 * (size_t)T, 0.0);
+  c.sep_a.assign(2 * (size_t)S * C, 0.0);
+  for (int t = 0; t < T; ++t) {
+    c.sep_g[2 * t] = gr[t];
+    c.sep_g[2 * t + 1] = gi[t];
+  }
   for (int s = 0; s < S; ++s) {
     const double th = (-90.0 + 180.0 * (s + 0.5) / S) * kPi / 180.0;
     const double fs = 0.5 * std::sin(th);
+    for (int ch = 0; ch < C; ++ch) {
+      const double a = 2.0 * kPi * fs * ch;
+      c.sep_a[2 * ((size_t)s * C + ch)] = std::cos(a);
+      c.sep_a[2 * ((size_t)s * C + ch) + 1] = std::sin(a);
+    }
     for (int t = 0; t < T; ++t)
       for (int ch = 0; ch < C; ++ch) {
-        const double a = 2.0 * kPi * fs * ch;
-        const double ar = std::cos(a), ai = std::sin(a);
+        const double ar = c.sep_a[2 * ((size_t)s * C + ch)], ai = c.sep_a[2 * ((size_t)s * C + ch) + 1];
         double* v = &c.steer[2 * ((size_t)s * D + t * C + ch)];
         v[0] = gr[t] * ar - gi[t] * ai;
         v[1] = gr[t] * ai + gi[t] * ar;
       }
   }
+  c.separable = true;
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -126,6 +141,10 @@ stap_status upload_tables(stap_plan p, int only_cpi = -1) {
         cudaMemcpyAsync(p->ws + c.tw_off, c.tw.data(), c.tw.size() * sizeof(float),
                         cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
         cudaMemcpyAsync(p->ws + c.steer_off, c.steer.data(), c.steer.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(p->ws + c.g_off, c.sep_g.data(), c.sep_g.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(p->ws + c.a_off, c.sep_a.data(), c.sep_a.size() * sizeof(double),
                         cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
       return STAP_ERR_CUDA;
   }
@@ -160,8 +179,9 @@ stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts) {
   const stap_dims& d = c.d;
   return check_launch(stap::launch_solve(
       static_cast<const double2*>(cov), static_cast<float2*>(wts),
-      p->at<const double2>(c.steer_off), (long long)d.n_dop * c.NB, c.D, d.n_steering,
-      p->opt.load_factor, p->opt.refine_steps, p->status(), p->stream));
+      p->at<const double2>(c.steer_off), c.separable ? p->at<const double2>(c.g_off) : nullptr,
+      c.separable ? p->at<const double2>(c.a_off) : nullptr, (long long)d.n_dop * c.NB, c.D,
+      d.n_steering, d.n_chan, p->opt.load_factor, p->opt.refine_steps, p->status(), p->stream));
 }
 
 stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts, float* out) {
@@ -239,6 +259,10 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
     off = align_up(off + c.tw.size() * sizeof(float));
     c.steer_off = off;
     off = align_up(off + c.steer.size() * sizeof(double));
+    c.g_off = off;
+    off = align_up(off + c.sep_g.size() * sizeof(double));
+    c.a_off = off;
+    off = align_up(off + c.sep_a.size() * sizeof(double));
     if (c.dop_elems() > max_dop) max_dop = c.dop_elems();
     if (c.cov_elems() > max_cov) max_cov = c.cov_elems();
     if (c.wts_elems() > max_wts) max_wts = c.wts_elems();
@@ -290,6 +314,7 @@ stap_status stap_plan_set_steering(stap_plan p, int32_t cpi, const double* host_
   for (size_t i = 0; i < c.steer.size(); ++i)
     if (!std::isfinite(host_c128[i])) return STAP_ERR_INVALID_ARG;
   std::memcpy(c.steer.data(), host_c128, c.steer.size() * sizeof(double));
+  c.separable = false;  // an arbitrary table: solve for every steering vector
   return upload_tables(p, cpi);
 }
 

@@ -13,14 +13,16 @@ namespace stap {
 __device__ __forceinline__ void stage_snapshots(float2* __restrict__ xs, int ld,
                                                 const float2* __restrict__ dop, int C, int K, int R,
                                                 int T, int k, int r_begin, int ncells) {
+  // one warp per snapshot row, lanes along range: coalesced, no divisions per element
   const int D = C * T;
-  const int total = D * ncells;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int rr = idx % ncells;
-    const int d = idx / ncells;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int d = warp; d < D; d += nw) {
     const int t = d / C, c = d - t * C;
     const int kk = wrap_bin(k + t - T / 2, K);
-    xs[d * ld + rr] = __ldg(dop + ((size_t)c * K + kk) * R + r_begin + rr);
+    const float2* src = dop + ((size_t)c * K + kk) * R + r_begin;
+    float2* dst = xs + (size_t)d * ld;
+#pragma unroll 4
+    for (int cell = lane; cell < ncells; cell += 32) dst[cell] = __ldg(src + cell);
   }
 }
 

@@ -19,6 +19,16 @@
 // pass), reading L as a broadcast and keeping its two work vectors in shared
 // memory.  Teams of one warp share all control flow (same D and S), so the
 // warp never diverges except where S is not a multiple of TS.
+//
+// Separable steering (SEP): when every steering vector is v_s = g (x) a_s
+// (one temporal factor g of length T shared by all s, a spatial factor a_s of
+// length C), Rl^{-1} v_s = sum_c a_s[c] Rl^{-1} (g (x) e_c).  The team then
+// solves (and refines) only the C basis right-hand sides g (x) e_c, one per
+// lane, and forms each u_s as that FP64 combination, followed by the same
+// normalisation.  Exact in exact arithmetic; it cuts the substitution work
+// from S to C right-hand sides.  The combination stays in FP64: u_s can be
+// two orders of magnitude smaller than the terms it sums (steering vectors
+// near the clutter ridge), so FP32 there costs ~1e-4 in the weights.
 #include "snapshots.cuh"
 
 namespace stap {
@@ -81,9 +91,11 @@ __device__ __forceinline__ void chol_solve_inplace(const double2* __restrict__ L
   }
 }
 
+template <bool SEP>
 __global__ void __launch_bounds__(128)
 solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
-             const double2* __restrict__ steer, long long nsys, int D, int S, int TS,
+             const double2* __restrict__ steer, const double2* __restrict__ sep_g,
+             const double2* __restrict__ sep_a, long long nsys, int D, int S, int C, int TS,
              double load_factor, int refine_steps, DeviceStatus* __restrict__ status) {
   extern __shared__ double2 sm[];
   const int nw = blockDim.x >> 5;
@@ -123,8 +135,8 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
         ok = false;
         djj = 1.0;  // keep the control flow uniform; this system's weights become zero
       }
-      const double ljj = sqrt(djj);
-      const double inv = 1.0 / ljj;
+      const double inv = rsqrt(djj);
+      const double ljj = djj * inv;
       for (int i = j + 1 + tl; i < D; i += TS) {
         const double2 v = L[pidx(i, j)];
         L[pidx(i, j)] = make_double2(v.x * inv, v.y * inv);
@@ -153,18 +165,50 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       __syncwarp();
     }
 
-    // ---- per-lane solves, one steering vector per lane and pass ----
-    for (int s0 = 0; s0 < S; s0 += TS) {
-      const int s = s0 + tl;
-      if (s < S) {
-        const double2* v = steer + (size_t)s * D;
-        for (int i = 0; i < D; ++i) W[i * 32] = __ldg(v + i);
+    // Weights of steering vector s from its solution u (stride 32): scale by
+    // 1/sqrt(Re v_s^H u) and store as complex64.
+    auto emit = [&](int s, const double2* u) {
+      const double2* v = steer + (size_t)s * D;
+      double q = 0.0;
+      for (int i = 0; i < D; ++i) {
+        const double2 vi = __ldg(v + i), ui = u[i * 32];
+        q = fma(vi.x, ui.x, q);
+        q = fma(vi.y, ui.y, q);
+      }
+      const bool good = ok && q > 0.0 && isfinite(q);
+      const double scale = good ? rsqrt(q) : 0.0;
+      if (valid) {
+        float2* w = wts + ((size_t)sys * S + s) * D;
+        for (int i = 0; i < D; ++i) {
+          const double2 ui = u[i * 32];
+          w[i] = good ? make_float2((float)(ui.x * scale), (float)(ui.y * scale))
+                      : make_float2(0.f, 0.f);
+        }
+      }
+    };
+
+    // ---- per-lane solves: one right-hand side per lane and pass ----
+    // generic: the S steering vectors, each written as soon as it is solved;
+    // SEP: the C <= TS basis vectors g (x) e_c, all in one pass
+    const int nrhs = SEP ? C : S;
+    for (int r0 = 0; r0 < nrhs; r0 += TS) {
+      const int rhs = r0 + tl;
+      if (rhs < nrhs) {
+        const double2* v = steer + (size_t)rhs * D;
+        auto rhs_at = [&](int i) -> double2 {
+          if (SEP) {
+            const int t = i / C;
+            return (i - t * C == rhs) ? __ldg(sep_g + t) : make_double2(0.0, 0.0);
+          }
+          return __ldg(v + i);
+        };
+        for (int i = 0; i < D; ++i) W[i * 32] = rhs_at(i);
         chol_solve_inplace(L, invd, W, D);
         for (int i = 0; i < D; ++i) U[i * 32] = W[i * 32];
         for (int it = 0; it < refine_steps; ++it) {
-          // W = v - Rl u  (Rl Hermitian: lower part direct, upper part mirrored)
+          // W = b - Rl u  (Rl Hermitian: lower part direct, upper part mirrored)
           for (int i = 0; i < D; ++i) {
-            double2 acc = __ldg(v + i);
+            double2 acc = rhs_at(i);
             for (int l = 0; l <= i; ++l) cfms(acc, loaded(A, D, i, l, delta), U[l * 32]);
             for (int l = i + 1; l < D; ++l) cfms_conj(acc, loaded(A, D, l, i, delta), U[l * 32]);
             W[i * 32] = acc;
@@ -175,21 +219,30 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
             U[i * 32] = make_double2(u.x + c.x, u.y + c.y);
           }
         }
-        double q = 0.0;  // Re v^H u
-        for (int i = 0; i < D; ++i) {
-          const double2 vi = __ldg(v + i), ui = U[i * 32];
-          q = fma(vi.x, ui.x, q);
-          q = fma(vi.y, ui.y, q);
-        }
-        const bool good = ok && q > 0.0 && isfinite(q);
-        const double scale = good ? 1.0 / sqrt(q) : 0.0;
-        if (valid) {
-          float2* w = wts + ((size_t)sys * S + s) * D;
+        if (!SEP) emit(rhs, U);
+      }
+    }
+
+    // ---- SEP: u_s = sum_c a_s[c] U_c (U_c = column of lane team*TS + c) ----
+    if (SEP) {
+      __syncwarp();  // the combination reads the other lanes' U columns
+      const double2* Ut = U - lane + team * TS;
+      for (int s0 = 0; s0 < S; s0 += TS) {
+        const int s = s0 + tl;
+        if (s < S) {
+          const double2* as = sep_a + (size_t)s * C;
           for (int i = 0; i < D; ++i) {
-            const double2 u = U[i * 32];
-            w[i] = good ? make_float2((float)(u.x * scale), (float)(u.y * scale))
-                        : make_float2(0.f, 0.f);
+            double2 acc = make_double2(0.0, 0.0);
+            for (int c = 0; c < C; ++c) {
+              const double2 a = __ldg(as + c), x = Ut[i * 32 + c];
+              acc.x = fma(a.x, x.x, acc.x);
+              acc.x = fma(-a.y, x.y, acc.x);
+              acc.y = fma(a.x, x.y, acc.y);
+              acc.y = fma(a.y, x.x, acc.y);
+            }
+            W[i * 32] = acc;
           }
+          emit(s, W);
         }
       }
     }
@@ -206,16 +259,20 @@ int pow2ceil(int x) {
 
 }  // namespace
 
-cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer, long long nsys,
-                         int D, int S, double load_factor, int refine_steps, DeviceStatus* status,
+cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
+                         const double2* sep_g, const double2* sep_a, long long nsys, int D, int S,
+                         int C, double load_factor, int refine_steps, DeviceStatus* status,
                          cudaStream_t s) {
   if (nsys <= 0) return cudaSuccess;
   if (D < 1 || D > kMaxD || S < 1) return cudaErrorInvalidValue;
+  const bool sep = sep_g != nullptr && sep_a != nullptr && C >= 1 && C <= 32 && D % C == 0;
   constexpr size_t kBudget = 200 * 1024;
   const int Dp = D * (D + 1) / 2;
-  // lanes per system: enough for one steering vector per lane, more if the
-  // packed factors of 32/TS systems would not fit in shared memory
-  int TS = pow2ceil(S < 32 ? S : 32);
+  // lanes per system: one right-hand side per lane (S steering vectors, or C
+  // basis vectors when separable), more if the packed factors of 32/TS
+  // systems would not fit in shared memory
+  const int nrhs = sep ? C : S;
+  int TS = pow2ceil(nrhs < 32 ? nrhs : 32);
   auto warp_bytes = [&](int ts) {
     const int G = 32 / ts;
     return ((size_t)G * Dp + 2 * (size_t)D * 32) * sizeof(double2) + (size_t)G * D * sizeof(double);
@@ -225,15 +282,22 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer, 
   while (nw > 1 && warp_bytes(TS) * nw > kBudget) --nw;
   const size_t smem = warp_bytes(TS) * nw;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  static int set_bytes[64] = {0};
-  cudaError_t e = ensure_smem(solve_kernel, smem, set_bytes);
-  if (e != cudaSuccess) return e;
   const int G = 32 / TS;
   const long long batches = (nsys + G - 1) / G;
   long long blocks = (batches + nw - 1) / nw;
   if (blocks > 152LL * 64) blocks = 152LL * 64;
-  solve_kernel<<<(unsigned)blocks, nw * 32, smem, s>>>(cov, wts, steer, nsys, D, S, TS, load_factor,
-                                                      refine_steps, status);
+  cudaError_t e;
+  if (sep) {
+    static int set_bytes[64] = {0};
+    if ((e = ensure_smem(solve_kernel<true>, smem, set_bytes)) != cudaSuccess) return e;
+    solve_kernel<true><<<(unsigned)blocks, nw * 32, smem, s>>>(
+        cov, wts, steer, sep_g, sep_a, nsys, D, S, C, TS, load_factor, refine_steps, status);
+  } else {
+    static int set_bytes[64] = {0};
+    if ((e = ensure_smem(solve_kernel<false>, smem, set_bytes)) != cudaSuccess) return e;
+    solve_kernel<false><<<(unsigned)blocks, nw * 32, smem, s>>>(
+        cov, wts, steer, nullptr, nullptr, nsys, D, S, C, TS, load_factor, refine_steps, status);
+  }
   return cudaGetLastError();
 }
 

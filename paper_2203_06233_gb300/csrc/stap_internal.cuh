@@ -35,9 +35,12 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
                                    int B, cudaStream_t s);
 
 // FP64 loading, Cholesky, solves, refinement and scaling for nsys systems.
-// cov [nsys][D][D] c128 -> wts [nsys][S][D] c64; steer [S][D] c128.
-cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer, long long nsys,
-                         int D, int S, double load_factor, int refine_steps, DeviceStatus* status,
+// cov [nsys][D][D] c128 -> wts [nsys][S][D] c64; steer [S][D] c128.  If
+// sep_g [T] and sep_a [S][C] are given, steer[s] = sep_g (x) sep_a[s] and the
+// solve runs on the C basis vectors instead of the S steering vectors.
+cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
+                         const double2* sep_g, const double2* sep_a, long long nsys, int D, int S,
+                         int C, double load_factor, int refine_steps, DeviceStatus* status,
                          cudaStream_t s);
 
 // out[s][k][r] = |w^H x|^2; dop [C][K][R] c64, wts [K][NB][S][D] c64, out [S][K][R] f32.
