@@ -63,7 +63,7 @@ typedef struct {
   int32_t n_pulses;       /* P >= 1 */
   int32_t n_dop;          /* K >= P, a power of two, K <= 1024 */
   int32_t n_range;        /* R >= 1, a multiple of B */
-  int32_t tdof;           /* 1 <= T <= K */
+  int32_t tdof;           /* 1 <= T <= K; D = n_chan * tdof <= 128 */
   int32_t training_block; /* B >= 1 */
   int32_t n_steering;     /* S >= 1 */
 } stap_dims;

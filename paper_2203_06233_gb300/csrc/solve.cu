@@ -251,6 +251,264 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Large systems (D up to 128).  The per-lane layout above needs two D-long
+// FP64 vectors per lane, which no longer fits next to a 132 KB factor, so here
+// one CTA of 4 warps owns one system at a time and the lanes own ROWS:
+//  * L (column-major packed lower triangle) lives in shared memory; the
+//    Cholesky is right-looking with the trailing update of each column spread
+//    over all 128 threads.
+//  * Each warp solves one right-hand side at a time; lane l keeps rows
+//    l, l+32, l+64, l+96 of its vectors in registers.  Substitution goes
+//    column by column: the owner of row j finishes y_j, a shuffle broadcasts
+//    it, and every lane updates its rows below (above, for L^H).
+//  * The residual b - Rl u reads Rl from the input through L1: for each
+//    column index l every lane takes A[i][l] (i >= l) or conj(A[l][i]) (i < l)
+//    by a select, so all lanes run every DFMA.
+//  * Separable steering: the C basis solutions are kept in shared memory and
+//    combined per steering vector by lanes over rows.
+constexpr int kBigThreads = 128;
+constexpr int kBigRPL = 4;          // rows per lane: D <= 32 * kBigRPL = 128
+
+__device__ __forceinline__ int colstart(int l, int D) { return l * D - l * (l - 1) / 2; }
+
+// In-place forward (L y = x) or back (L^H y = x) substitution of one vector
+// held as rows lane + 32 q.
+template <bool BACK>
+__device__ __forceinline__ void big_subst(double2 (&x)[kBigRPL], const double2* __restrict__ Lc,
+                                          const double* __restrict__ invd, int D, int lane) {
+  for (int jj = 0; jj < D; ++jj) {
+    const int j = BACK ? D - 1 - jj : jj;
+    const int owner = j & 31, qj = j >> 5;
+    double2 pick = x[0];
+#pragma unroll
+    for (int q = 1; q < kBigRPL; ++q)
+      if (q == qj) pick = x[q];
+    double2 yj;
+    yj.x = __shfl_sync(0xffffffffu, pick.x, owner);
+    yj.y = __shfl_sync(0xffffffffu, pick.y, owner);
+    const double s = invd[j];
+    yj.x *= s;
+    yj.y *= s;
+#pragma unroll
+    for (int q = 0; q < kBigRPL; ++q) {
+      if (q == qj && lane == owner) x[q] = yj;
+      const bool touch = BACK ? (q <= qj) : (q >= qj);     // warp-uniform
+      if (touch) {
+        const int i = lane + 32 * q;
+        const bool act = BACK ? (i < j) : (i > j && i < D);
+        if (act) {
+          if (BACK) {  // x_i -= conj(L[j][i]) y_j
+            const double2 l = Lc[colstart(i, D) + j - i];
+            x[q].x = fma(-l.x, yj.x, x[q].x);
+            x[q].x = fma(-l.y, yj.y, x[q].x);
+            x[q].y = fma(-l.x, yj.y, x[q].y);
+            x[q].y = fma(l.y, yj.x, x[q].y);
+          } else {     // x_i -= L[i][j] y_j
+            const double2 l = Lc[colstart(j, D) + i - j];
+            x[q].x = fma(-l.x, yj.x, x[q].x);
+            x[q].x = fma(l.y, yj.y, x[q].x);
+            x[q].y = fma(-l.x, yj.y, x[q].y);
+            x[q].y = fma(-l.y, yj.x, x[q].y);
+          }
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <bool SEP>
+__global__ void __launch_bounds__(kBigThreads)
+solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
+                 const double2* __restrict__ steer, const double2* __restrict__ sep_g,
+                 const double2* __restrict__ sep_a, long long nsys, int D, int S, int C,
+                 double load_factor, int refine_steps, DeviceStatus* __restrict__ status) {
+  extern __shared__ double2 sm[];
+  constexpr int NW = kBigThreads / 32;
+  const int Dp = D * (D + 1) / 2;
+  double2* Lc = sm;                                  // [Dp] column-major packed
+  double2* Ub = Lc + Dp;                             // SEP: [C][D] basis solutions
+  double2* uv = Ub + (SEP ? (size_t)C * D : 0);      // [NW][D] broadcast vectors
+  double* invd = reinterpret_cast<double*>(uv + (size_t)NW * D);   // [D]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double invD = 1.0 / (double)D;
+
+  for (long long sys = blockIdx.x; sys < nsys; sys += gridDim.x) {
+    const double2* A = cov + (size_t)sys * D * D;
+    double tr = 0.0;
+    for (int j = 0; j < D; ++j) tr += __ldg(&A[(size_t)j * D + j].x);
+    const double delta = load_factor * tr * invD;
+    for (int i = warp; i < D; i += NW)                 // rows of A, coalesced
+      for (int l = lane; l <= i; l += 32) Lc[colstart(l, D) + i - l] = loaded(A, D, i, l, delta);
+    __syncthreads();
+
+    bool ok = true;
+    for (int j = 0; j < D; ++j) {
+      const int cj = colstart(j, D);
+      double djj = Lc[cj].x;
+      if (!(djj > 0.0) || !isfinite(djj)) {
+        ok = false;
+        djj = 1.0;
+      }
+      const double inv = rsqrt(djj);
+      const double ljj = djj * inv;
+      for (int i = j + 1 + tid; i < D; i += kBigThreads) {
+        const double2 v = Lc[cj + i - j];
+        Lc[cj + i - j] = make_double2(v.x * inv, v.y * inv);
+      }
+      __syncthreads();
+      // trailing update, pairs (i, l) with j < l <= i, column-major order
+      const int m = D - j - 1;
+      const int np = m * (m + 1) / 2;
+      for (int q = tid; q < np; q += kBigThreads) {
+        // column a of the trailing triangle holds m - a entries
+        const float fm = 2.0f * m + 1.0f;
+        int a = (int)((fm - sqrtf(fm * fm - 8.0f * (float)q)) * 0.5f);
+        while (a > 0 && a * m - a * (a - 1) / 2 > q) --a;
+        while ((a + 1) * m - (a + 1) * a / 2 <= q) ++a;
+        const int off = q - (a * m - a * (a - 1) / 2);
+        const int l = j + 1 + a, i = l + off;
+        const double2 lij = Lc[cj + i - j], llj = Lc[cj + l - j];
+        double2 acc = Lc[colstart(l, D) + i - l];
+        acc.x = fma(-lij.x, llj.x, acc.x);
+        acc.x = fma(-lij.y, llj.y, acc.x);
+        acc.y = fma(-lij.y, llj.x, acc.y);
+        acc.y = fma(lij.x, llj.y, acc.y);
+        Lc[colstart(l, D) + i - l] = acc;
+      }
+      if (tid == 0) {
+        Lc[cj] = make_double2(ljj, 0.0);
+        invd[j] = inv;
+      }
+      __syncthreads();
+    }
+
+    // weights of steering vector s from u (rows lane + 32 q): warp-wide
+    auto emit = [&](int s, const double2 (&u)[kBigRPL]) {
+      const double2* v = steer + (size_t)s * D;
+      double qp = 0.0;
+#pragma unroll
+      for (int q = 0; q < kBigRPL; ++q) {
+        const int i = lane + 32 * q;
+        if (i < D) {
+          const double2 vi = __ldg(v + i);
+          qp = fma(vi.x, u[q].x, qp);
+          qp = fma(vi.y, u[q].y, qp);
+        }
+      }
+      const double qs = warp_sum(qp);
+      const bool good = ok && qs > 0.0 && isfinite(qs);
+      const double scale = good ? rsqrt(qs) : 0.0;
+      float2* w = wts + ((size_t)sys * S + s) * D;
+#pragma unroll
+      for (int q = 0; q < kBigRPL; ++q) {
+        const int i = lane + 32 * q;
+        if (i < D)
+          w[i] = good ? make_float2((float)(u[q].x * scale), (float)(u[q].y * scale))
+                      : make_float2(0.f, 0.f);
+      }
+    };
+
+    const int nrhs = SEP ? C : S;
+    for (int rhs = warp; rhs < nrhs; rhs += NW) {
+      double2 b[kBigRPL], u[kBigRPL], r[kBigRPL];
+#pragma unroll
+      for (int q = 0; q < kBigRPL; ++q) {
+        const int i = lane + 32 * q;
+        double2 v = make_double2(0.0, 0.0);
+        if (i < D) {
+          if (SEP) {
+            const int t = i / C;
+            if (i - t * C == rhs) v = __ldg(sep_g + t);
+          } else {
+            v = __ldg(steer + (size_t)rhs * D + i);
+          }
+        }
+        b[q] = v;
+        u[q] = v;
+      }
+      big_subst<false>(u, Lc, invd, D, lane);
+      big_subst<true>(u, Lc, invd, D, lane);
+      for (int it = 0; it < refine_steps; ++it) {
+        // r = b - Rl u
+#pragma unroll
+        for (int q = 0; q < kBigRPL; ++q)
+          if (lane + 32 * q < D) uv[warp * D + lane + 32 * q] = u[q];
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < kBigRPL; ++q) r[q] = b[q];
+        for (int l = 0; l < D; ++l) {
+          const double2 ul = uv[warp * D + l];
+#pragma unroll
+          for (int q = 0; q < kBigRPL; ++q) {
+            const int i = lane + 32 * q;
+            if (32 * q < D) {               // warp-uniform: some lane has a row here
+              const int ic = i < D ? i : D - 1;
+              const bool low = ic >= l;
+              const double2 a = __ldg(low ? A + (size_t)ic * D + l : A + (size_t)l * D + ic);
+              double ax = a.x, ay = low ? a.y : -a.y;     // Rl[i][l]
+              if (ic == l) {
+                ax += delta;
+                ay = 0.0;
+              }
+              r[q].x = fma(-ax, ul.x, r[q].x);
+              r[q].x = fma(ay, ul.y, r[q].x);
+              r[q].y = fma(-ax, ul.y, r[q].y);
+              r[q].y = fma(-ay, ul.x, r[q].y);
+            }
+          }
+        }
+        __syncwarp();
+        big_subst<false>(r, Lc, invd, D, lane);
+        big_subst<true>(r, Lc, invd, D, lane);
+#pragma unroll
+        for (int q = 0; q < kBigRPL; ++q) {
+          u[q].x += r[q].x;
+          u[q].y += r[q].y;
+        }
+      }
+      if (SEP) {
+#pragma unroll
+        for (int q = 0; q < kBigRPL; ++q)
+          if (lane + 32 * q < D) Ub[(size_t)rhs * D + lane + 32 * q] = u[q];
+      } else {
+        emit(rhs, u);
+      }
+    }
+    if (SEP) {
+      __syncthreads();
+      for (int s = warp; s < S; s += NW) {
+        const double2* as = sep_a + (size_t)s * C;
+        double2 u[kBigRPL];
+#pragma unroll
+        for (int q = 0; q < kBigRPL; ++q) u[q] = make_double2(0.0, 0.0);
+        for (int c = 0; c < C; ++c) {
+          const double2 a = __ldg(as + c);
+#pragma unroll
+          for (int q = 0; q < kBigRPL; ++q) {
+            if (32 * q < D) {
+              const int i = lane + 32 * q;
+              const double2 x = Ub[(size_t)c * D + (i < D ? i : D - 1)];
+              u[q].x = fma(a.x, x.x, u[q].x);
+              u[q].x = fma(-a.y, x.y, u[q].x);
+              u[q].y = fma(a.x, x.y, u[q].y);
+              u[q].y = fma(a.y, x.x, u[q].y);
+            }
+          }
+        }
+        emit(s, u);
+      }
+    }
+    if (!ok && tid == 0) atomicAdd(&status->n_failed, 1ULL);
+    __syncthreads();  // the next system reuses Lc, Ub
+  }
+}
+
 int pow2ceil(int x) {
   int p = 1;
   while (p < x) p <<= 1;
@@ -266,6 +524,29 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
   if (nsys <= 0) return cudaSuccess;
   if (D < 1 || D > kMaxD || S < 1) return cudaErrorInvalidValue;
   const bool sep = sep_g != nullptr && sep_a != nullptr && C >= 1 && C <= 32 && D % C == 0;
+  if (D > kSmallMaxD) {  // one system per CTA, lanes over rows
+    if (D > 32 * kBigRPL) return cudaErrorInvalidValue;
+    const size_t Dp = (size_t)D * (D + 1) / 2;
+    const bool sep_big = sep && (Dp + (size_t)C * D + 4 * (size_t)D) * sizeof(double2) +
+                                   D * sizeof(double) <= 227 * 1024;
+    const size_t smem = (Dp + (sep_big ? (size_t)C * D : 0) + 4 * (size_t)D) * sizeof(double2) +
+                        D * sizeof(double);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    long long blocks = nsys < 152LL * 8 ? nsys : 152LL * 8;
+    cudaError_t e;
+    if (sep_big) {
+      static int set_bytes[64] = {0};
+      if ((e = ensure_smem(solve_big_kernel<true>, smem, set_bytes)) != cudaSuccess) return e;
+      solve_big_kernel<true><<<(unsigned)blocks, kBigThreads, smem, s>>>(
+          cov, wts, steer, sep_g, sep_a, nsys, D, S, C, load_factor, refine_steps, status);
+    } else {
+      static int set_bytes[64] = {0};
+      if ((e = ensure_smem(solve_big_kernel<false>, smem, set_bytes)) != cudaSuccess) return e;
+      solve_big_kernel<false><<<(unsigned)blocks, kBigThreads, smem, s>>>(
+          cov, wts, steer, nullptr, nullptr, nsys, D, S, C, load_factor, refine_steps, status);
+    }
+    return cudaGetLastError();
+  }
   constexpr size_t kBudget = 200 * 1024;
   const int Dp = D * (D + 1) / 2;
   // lanes per system: one right-hand side per lane (S steering vectors, or C

@@ -18,7 +18,8 @@ struct DeviceStatus {
 };
 static_assert(sizeof(DeviceStatus) <= 256, "status block must fit its slot");
 
-constexpr int kMaxD = 64;        // largest snapshot length the solve kernel handles
+constexpr int kMaxD = 128;       // largest snapshot length the solve kernels handle
+constexpr int kSmallMaxD = 64;   // above this, one system per CTA (lanes over rows)
 constexpr int kMaxLogK = 10;     // K <= 1024
 
 // ---------------------------------------------------------------- launchers --

@@ -74,4 +74,7 @@ EDGE_SPECS = [
     synth.CPISpec(4, 64, 1024, 64, 3, 64, 4, cnr_db=30.0, seed=16),
     synth.CPISpec(2, 300, 512, 40, 3, 40, 4, cnr_db=30.0, seed=17),
     synth.CPISpec(6, 24, 32, 160, 3, 160, 33, cnr_db=35.0, seed=18),
+    # large snapshots: one system per CTA (D = 128 and a D that is not a multiple of 32)
+    synth.CPISpec(32, 8, 8, 256, 4, 256, 40, cnr_db=40.0, seed=19),
+    synth.CPISpec(25, 16, 16, 192, 4, 96, 12, cnr_db=30.0, seed=20),
 ]

@@ -63,7 +63,7 @@ def test_plan_create_default_options_and_workspace_layout():
     ((4, 128, 256, 4096, 3, 64, 0), stap.STAP_ERR_SHAPE),       # no steering vectors
     ((4, 128, 192, 4096, 3, 64, 16), stap.STAP_ERR_UNSUPPORTED),  # K not a power of two
     ((4, 128, 2048, 4096, 3, 64, 16), stap.STAP_ERR_UNSUPPORTED),  # K > 1024
-    ((33, 16, 16, 64, 2, 8, 4), stap.STAP_ERR_UNSUPPORTED),     # D = 66 > 64
+    ((65, 16, 16, 64, 2, 8, 4), stap.STAP_ERR_UNSUPPORTED),     # D = 130 > 128
 ])
 def test_plan_create_rejects_bad_shapes(dims, code):
     got, h, _ = _create(dims)

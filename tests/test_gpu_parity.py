@@ -12,7 +12,9 @@ oracle never sees a value produced by the CUDA path.  Tolerances:
 * Apply (FP32): every cell within the forward-error bound of the FP32 dot
   product (tests/_parity.cell_bound).
 * Whole path, plain FP32: ||P - P_ref||_2 / ||P_ref||_2 <= 1e-5, and every
-  cell within 1e-3 of max(P_ref, median P_ref).
+  cell within 1e-3 of max(P_ref, median P_ref), for D <= 12 (the plain
+  workloads); for larger D both bars grow with the FP32 dot-product error
+  of the apply, by (D + 2) / 14.
 """
 import numpy as np
 import pytest
@@ -41,6 +43,13 @@ def _dev(a, dtype):
 
 
 SPECS = [synth.small_cpi(), synth.standard_cpi()] + EDGE_SPECS
+
+
+def growth(spec):
+    """End-to-end bars scale with the FP32 dot-product error of the apply,
+    gamma_D ~ (D + 2) u, relative to the D = 12 of the plain workloads:
+    1e-5 / 1e-3 hold as stated for D <= 12."""
+    return max(1.0, (spec.D + 2) / 14.0)
 IDS = ["small", "standard"] + [f"edge{i}" for i in range(len(EDGE_SPECS))]
 
 
@@ -107,9 +116,10 @@ def test_run_cpi_end_to_end(spec):
     plan = _plan(spec)
     out = to_np(plan.run_cpi(_dev(cube, torch.complex64)))
     e_cell, e_norm = power_errors(out, ref)
-    print(f"dims={spec.dims()} max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
-    assert e_norm <= 1e-5, e_norm
-    assert e_cell <= 1e-3, e_cell
+    g = growth(spec)
+    print(f"dims={spec.dims()} max-cell/floor={e_cell:.3e} normwise={e_norm:.3e} (x{g:.2f})")
+    assert e_norm <= 1e-5 * g, e_norm
+    assert e_cell <= 1e-3 * g, e_cell
     assert plan.status() == (stap.STAP_OK, 0)
 
 
@@ -196,8 +206,9 @@ def test_standard_workload_full_size_parity_and_launch_configuration():
     assert e_norm <= 1e-5 and e_cell <= 1e-3
 
 
-@pytest.mark.parametrize("spec", [synth.small_cpi(), synth.standard_cpi(), EDGE_SPECS[2], EDGE_SPECS[3]],
-                         ids=["small", "standard", "edge2", "edge3"])
+@pytest.mark.parametrize("spec", [synth.small_cpi(), synth.standard_cpi(), EDGE_SPECS[2], EDGE_SPECS[3],
+                                  EDGE_SPECS[8], EDGE_SPECS[9]],
+                         ids=["small", "standard", "edge2", "edge3", "edge8", "edge9"])
 def test_generic_and_separable_solves_agree(spec):
     """The default steering table is solved on the C basis vectors; the same
     table given explicitly takes the generic path (one solve per steering
