@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "STAP range-Doppler cells/s per GB300, mixed vs FP32 at ≤1e-3 err vs FP64"
 UNIT = "cells/s"
+NAME = "standard"
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes (read + write) per launch of the solve kernel on the standard CPI,
@@ -51,15 +52,15 @@ def peaks():
     return p
 
 
-def workload_spec(rank=0):
+def workload_spec(rank=0, name="standard"):
     import dataclasses
     from paper_2203_06233_gb300 import synth
-    return dataclasses.replace(synth.standard_cpi(), sub=rank)
+    return dataclasses.replace(synth.WORKLOADS[name](), sub=rank)
 
 
 def workload_config(spec):
     C, P, K, R, T, B, S = spec.dims()
-    return {"workload": f"standard CPI C{C} P{P} K{K} R{R} T{T} B{B} S{S} (D={C*T}), "
+    return {"workload": f"{NAME} CPI C{C} P{P} K{K} R{R} T{T} B{B} S{S} (D={C*T}), "
                         f"{spec.cnr_db:.0f} dB CNR, {len(spec.targets)} targets",
             "n_chan": C, "n_pulses": P, "n_dop": K, "n_range": R, "tdof": T,
             "training_block": B, "n_steering": S, "cells_per_step": K * R,
@@ -185,11 +186,15 @@ def run_gpu(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    spec = workload_spec(rank)
+    spec = workload_spec(rank, NAME)
     C, P, K, R, T, B, S = spec.dims()
-    cube_h = synth.make_cube(spec)
+    if NAME == "standard":
+        cube_h = synth.make_cube(spec)
+        cube = torch.from_numpy(cube_h).to(dev)
+    else:  # several GB: generate on the device, keep a host copy for the e2e leg
+        cube = synth.make_cube_torch(spec, dev)
+        cube_h = cube.cpu().numpy()
     plan = stap.Plan(spec.dims(), device=dev)
-    cube = torch.from_numpy(cube_h).to(dev)
     out = torch.empty((S, K, R), dtype=torch.float32, device=dev)
     flushbuf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -230,7 +235,7 @@ def run_gpu(args):
     dop = plan.doppler(cube)
     cov = plan.covariance(dop)
     wts = plan.solve_weights(cov)
-    reps = max(20, min(200, args.steps))
+    reps = max(20, min(200, args.steps)) if NAME == "standard" else max(3, args.steps)
     kt = {
         "doppler": statistics.mean(time_steps(lambda: plan.doppler(cube, dop), reps, flush, stream)),
         "covariance": statistics.mean(time_steps(lambda: plan.covariance(dop, cov), reps, flush, stream)),
@@ -296,7 +301,7 @@ def run_gpu(args):
         "kernels": kernels,
         "clocks": clk.summary(),
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and NAME == "standard":
         line["cpu_baseline"] = cpu_baseline_oracle(spec)
     plan.close()
     if world > 1:
@@ -320,7 +325,7 @@ def run_reference(args):
         return
     import oracle
     from paper_2203_06233_gb300 import synth
-    spec = workload_spec(0)
+    spec = workload_spec(0, NAME)
     d = oracle.Dims(*spec.dims())
     cube = synth.make_cube(spec)
     B, NB, K = spec.training_block, spec.NB, spec.n_dop
@@ -364,7 +369,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["standard", "mixed", "large"], default="standard",
+                    help="standard is the benchmark workload; the others are for inspection")
     args = ap.parse_args()
+    global NAME
+    NAME = args.workload
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -139,8 +139,22 @@ stap_status stap_apply(stap_plan plan, const void* dop_c64, const void* wts_c64,
 /* The whole chain (Doppler, covariance, weights, apply) for every CPI of the
  * plan, with the intermediates in the workspace and no host round trip.
  * cubes[i]: c64 [C_i][P_i][R_i]; outs[i]: float [S_i][K_i][R_i]; both arrays
- * are HOST arrays of n_cpi device pointers. */
+ * are HOST arrays of n_cpi device pointers.
+ *
+ * With n_cpi > 1 the CPIs are packed, in order, into waves whose
+ * intermediates fit in the workspace beyond step_bytes (any workspace of at
+ * least run_bytes works; stap_plan_batch_bytes gives the size at which all
+ * CPIs run in one wave).  Within a wave each CPI's chain runs on one of
+ * several internal streams forked from the plan's stream, so CPIs overlap on
+ * the GPU.  The launch sequence is captured into a CUDA graph on the first
+ * call and replayed by later calls that pass the same cubes, outs, workspace
+ * and stream; any change re-captures it.  The first batched call also creates
+ * the plan's internal streams and events. */
 stap_status stap_run_cpi(stap_plan plan, const void* const* cubes, float* const* outs);
+
+/* Workspace size at which every CPI of the plan has its own intermediates,
+ * i.e. stap_run_cpi runs the whole batch as one wave. */
+stap_status stap_plan_batch_bytes(stap_plan plan, size_t* all_concurrent_bytes);
 
 /* Size of the device scratch array that libstap itself holds for
  * stap_run_cpi_noalloc: 16 MiB on every GPU that loads the library, kept

@@ -135,78 +135,87 @@ __device__ __forceinline__ void grid_add(float& hi, float& lo, float a, float b,
 
 __global__ void __launch_bounds__(kPairThreads)
 covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K,
-                        int R, int T, int B, int NB, int KT) {
+                        int R, int T, int B, int NB, int KT, int CB) {
   extern __shared__ double2 smd[];
   const int b = blockIdx.x;
   const int k0 = blockIdx.y * KT;
   const int h = T / 2;
   const int NBIN = KT + T - 1;                    // staged bins k0-h .. k0+KT-1+(T-1-h)
   const int nrows = NBIN * C;
-  const int ld = B + 1;
+  const int ld = CB + 1;
   const int Ediag = C * (C + 1) / 2, Eoff = C * C;
   // items: d-major; d = 0 has NBIN * Ediag items, d > 0 has (NBIN - d) * Eoff
   const int nitems = NBIN * Ediag + (T - 1) * (2 * NBIN - T) / 2 * Eoff;
   double2* Q = smd;                                             // [nitems]
   float* m = reinterpret_cast<float*>(Q + nitems);              // [nrows] row maxima
   float2* X = reinterpret_cast<float2*>(m + ((nrows + 3) & ~3));  // [nrows][ld]
-
-  // stage rows (bin j, channel c) of this range block
-  for (int idx = threadIdx.x; idx < nrows * B; idx += blockDim.x) {
-    const int cell = idx % B, row = idx / B;
-    const int j = row / C, c = row - j * C;
-    const int kk = wrap_bin(k0 - h + j, K);
-    X[row * ld + cell] = __ldg(dop + ((size_t)c * K + kk) * R + (size_t)b * B + cell);
-  }
-  __syncthreads();
-  // row maxima of |re|, |im| (one warp per row)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int row = warp; row < nrows; row += nwarps) {
-    float mx = 0.f;
-    for (int cell = lane; cell < B; cell += 32) {
-      const float2 x = X[row * ld + cell];
-      mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
-    }
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) m[row] = mx;
-  }
-  __syncthreads();
-
   const double invB = 1.0 / (double)B;
-  const float fourB = 4.0f * (float)B;
-  for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
-    int d = 0, rem = it;
-    if (rem >= NBIN * Ediag) {
-      rem -= NBIN * Ediag;
-      d = 1;
-      while (rem >= (NBIN - d) * Eoff) {
-        rem -= (NBIN - d) * Eoff;
-        ++d;
+
+  // the B cells in chunks of CB: each chunk is summed error-free on its own
+  // grid and added to Q in FP64
+  for (int c0 = 0; c0 < B; c0 += CB) {
+    const int cc = min(CB, B - c0);
+    __syncthreads();
+    for (int row = warp; row < nrows; row += nwarps) {   // rows (bin j, channel c)
+      const int j = row / C, c = row - j * C;
+      const int kk = wrap_bin(k0 - h + j, K);
+      const float2* src = dop + ((size_t)c * K + kk) * R + (size_t)b * B + c0;
+      float2* dst = X + row * ld;
+      float mx = 0.f;
+      for (int cell = lane; cell < cc; cell += 32) {
+        const float2 x = __ldg(src + cell);
+        dst[cell] = x;
+        mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
       }
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) m[row] = mx;
     }
-    int j1, c1, c2;
-    if (d == 0) {
-      j1 = rem / Ediag;
-      unpack_lower(rem - j1 * Ediag, c1, c2);
-    } else {
-      j1 = rem / Eoff;
-      const int e = rem - j1 * Eoff;
-      c1 = e / C;
-      c2 = e - c1 * C;
+    __syncthreads();
+
+    const float fourB = 4.0f * (float)cc;
+    for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+      int d = 0, rem = it;
+      if (rem >= NBIN * Ediag) {
+        rem -= NBIN * Ediag;
+        d = 1;
+        while (rem >= (NBIN - d) * Eoff) {
+          rem -= (NBIN - d) * Eoff;
+          ++d;
+        }
+      }
+      int j1, c1, c2;
+      if (d == 0) {
+        j1 = rem / Ediag;
+        unpack_lower(rem - j1 * Ediag, c1, c2);
+      } else {
+        j1 = rem / Eoff;
+        const int e = rem - j1 * Eoff;
+        c1 = e / C;
+        c2 = e - c1 * C;
+      }
+      const int ra = j1 * C + c1, rb = (j1 + d) * C + c2;
+      const float2* xa = X + ra * ld;
+      const float2* xb = X + rb * ld;
+      const float sig = pow2_ceil(fourB * m[ra] * m[rb]);
+      float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
+#pragma unroll 4
+      for (int cell = 0; cell < cc; ++cell) {
+        const float2 a = xa[cell], bb = xb[cell];
+        // a * conj(bb) = (a.x bb.x + a.y bb.y) + i (a.y bb.x - a.x bb.y)
+        grid_add(hr, lr, a.x, bb.x, sig);
+        grid_add(hr, lr, a.y, bb.y, sig);
+        grid_add(hi, li, a.y, bb.x, sig);
+        grid_add(hi, li, -a.x, bb.y, sig);
+      }
+      double2 v = make_double2(((double)hr + (double)lr) * invB, ((double)hi + (double)li) * invB);
+      if (c0 > 0) {
+        const double2 p = Q[it];
+        v.x += p.x;
+        v.y += p.y;
+      }
+      Q[it] = v;
     }
-    const int ra = j1 * C + c1, rb = (j1 + d) * C + c2;
-    const float2* xa = X + ra * ld;
-    const float2* xb = X + rb * ld;
-    const float sig = pow2_ceil(fourB * m[ra] * m[rb]);
-    float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
-    for (int cell = 0; cell < B; ++cell) {
-      const float2 a = xa[cell], bb = xb[cell];
-      // a * conj(bb) = (a.x bb.x + a.y bb.y) + i (a.y bb.x - a.x bb.y)
-      grid_add(hr, lr, a.x, bb.x, sig);
-      grid_add(hr, lr, a.y, bb.y, sig);
-      grid_add(hi, li, a.y, bb.x, sig);
-      grid_add(hi, li, -a.x, bb.y, sig);
-    }
-    Q[it] = make_double2(((double)hr + (double)lr) * invB, ((double)hi + (double)li) * invB);
   }
   __syncthreads();
 
@@ -247,26 +256,29 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
   const int E = D * (D + 1) / 2;
   const int NB = R / B;
   if (NB == 0) return cudaSuccess;
-  // bin-pair kernel: the whole B-cell tile of KT + T - 1 bins in shared memory
+  // bin-pair kernel: the B cells of KT + T - 1 bins in shared memory, in
+  // chunks of CB cells when the whole block does not fit
   {
     constexpr size_t kPairBudget = 200 * 1024;
-    auto pair_smem = [&](int kt) {
+    auto pair_smem = [&](int kt, int cb) {
       const int nbin = kt + T - 1;
       const size_t nitems = (size_t)nbin * (C * (C + 1) / 2) +
                             (size_t)(T - 1) * (2 * nbin - T) / 2 * C * C;
       const size_t nrows = (size_t)nbin * C;
       return nitems * sizeof(double2) + ((nrows + 3) & ~(size_t)3) * sizeof(float) +
-             nrows * (B + 1) * sizeof(float2);
+             nrows * (cb + 1) * sizeof(float2);
     };
     int KT = K < 16 ? K : 16;  // K is a power of two, so KT divides it
-    while (KT > 1 && pair_smem(KT) > kPairBudget) KT >>= 1;
-    if (pair_smem(KT) <= kPairBudget) {
-      const size_t smem = pair_smem(KT);
+    while (KT > 1 && pair_smem(KT, B) > kPairBudget) KT >>= 1;
+    int CB = B;
+    while (CB > 32 && pair_smem(KT, CB) > kPairBudget) CB = (CB + 1) / 2;
+    if (pair_smem(KT, CB) <= kPairBudget) {
+      const size_t smem = pair_smem(KT, CB);
       static int set_bytes[64] = {0};
       cudaError_t e = ensure_smem(covariance_pairs_kernel, smem, set_bytes);
       if (e != cudaSuccess) return e;
       dim3 grid(NB, K / KT);
-      covariance_pairs_kernel<<<grid, kPairThreads, smem, s>>>(dop, cov, C, K, R, T, B, NB, KT);
+      covariance_pairs_kernel<<<grid, kPairThreads, smem, s>>>(dop, cov, C, K, R, T, B, NB, KT, CB);
       return cudaGetLastError();
     }
   }

@@ -121,9 +121,22 @@ struct stap_plan_s {
   cudaStream_t stream = nullptr;
   char* ws = nullptr;
   size_t ws_bytes = 0;
-  size_t step_bytes = 0, run_bytes = 0;
+  size_t step_bytes = 0, run_bytes = 0, batch_bytes = 0;
   size_t dop_off = 0, cov_off = 0, wts_off = 0;   // run intermediates (sized for the largest CPI)
   bool tables_ready = false;
+
+  // batched runs (n_cpi > 1): forked streams and the captured launch graph
+  static constexpr int kSideStreams = 8;
+  cudaStream_t side[kSideStreams] = {};
+  cudaStream_t cap = nullptr;     // capture origin (the caller's stream may be the legacy one)
+  cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<const void*> graph_cubes;   // buffers the graph was captured with
+  std::vector<float*> graph_outs;
+  char* graph_ws = nullptr;
+  size_t graph_ws_bytes = 0;
+  cudaStream_t graph_stream = nullptr;
+  int graph_waves = 0;
 
   DeviceStatus* status() const { return reinterpret_cast<DeviceStatus*>(ws); }
   template <typename Tp>
@@ -161,35 +174,134 @@ stap_status ready(stap_plan p, size_t need) {
 
 // ----- the four steps on one CPI (arguments already validated) --------------
 
-stap_status do_doppler(stap_plan p, const Cpi& c, const void* cube, void* dop) {
+stap_status do_doppler(stap_plan p, const Cpi& c, const void* cube, void* dop, cudaStream_t st) {
   const stap_dims& d = c.d;
   return check_launch(stap::launch_doppler(
       static_cast<const float2*>(cube), static_cast<float2*>(dop), p->at<const float>(c.win_off),
-      p->at<const float2>(c.tw_off), d.n_chan, d.n_pulses, d.n_dop, d.n_range, p->stream));
+      p->at<const float2>(c.tw_off), d.n_chan, d.n_pulses, d.n_dop, d.n_range, st));
 }
 
-stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov) {
+stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov, cudaStream_t st) {
   const stap_dims& d = c.d;
+  (void)p;
   return check_launch(stap::launch_covariance_fp32(static_cast<const float2*>(dop),
                                                    static_cast<double2*>(cov), d.n_chan, d.n_dop,
-                                                   d.n_range, d.tdof, d.training_block, p->stream));
+                                                   d.n_range, d.tdof, d.training_block, st));
 }
 
-stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts) {
+stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts, cudaStream_t st) {
   const stap_dims& d = c.d;
   return check_launch(stap::launch_solve(
       static_cast<const double2*>(cov), static_cast<float2*>(wts),
       p->at<const double2>(c.steer_off), c.separable ? p->at<const double2>(c.g_off) : nullptr,
       c.separable ? p->at<const double2>(c.a_off) : nullptr, (long long)d.n_dop * c.NB, c.D,
-      d.n_steering, d.n_chan, p->opt.load_factor, p->opt.refine_steps, p->status(), p->stream));
+      d.n_steering, d.n_chan, p->opt.load_factor, p->opt.refine_steps, p->status(), st));
 }
 
-stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts, float* out) {
+stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts, float* out,
+                     cudaStream_t st) {
   const stap_dims& d = c.d;
+  (void)p;
   return check_launch(stap::launch_apply(static_cast<const float2*>(dop),
                                          static_cast<const float2*>(wts), out, d.n_chan, d.n_dop,
-                                         d.n_range, d.tdof, d.training_block, d.n_steering,
-                                         p->stream));
+                                         d.n_range, d.tdof, d.training_block, d.n_steering, st));
+}
+
+stap_status do_chain(stap_plan p, const Cpi& c, const void* cube, float* out, char* dop, char* cov,
+                     char* wts, cudaStream_t st) {
+  stap_status r;
+  if ((r = do_doppler(p, c, cube, dop, st)) != STAP_OK) return r;
+  if ((r = do_covariance(p, c, dop, cov, st)) != STAP_OK) return r;
+  if ((r = do_solve(p, c, cov, wts, st)) != STAP_OK) return r;
+  return do_apply(p, c, dop, wts, out, st);
+}
+
+size_t inter_bytes(const Cpi& c) {
+  return align_up(c.dop_elems() * 8) + align_up(c.cov_elems() * 16) + align_up(c.wts_elems() * 8);
+}
+
+void drop_graph(stap_plan p) {
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  p->graph_exec = nullptr;
+  p->graph_cubes.clear();
+  p->graph_outs.clear();
+}
+
+// Batched run: CPIs packed into waves whose intermediates fit the workspace
+// beyond the tables; inside a wave every CPI's four-kernel chain runs on one
+// of kSideStreams forked streams, so small CPIs overlap.  The whole sequence
+// is captured once into a CUDA graph and replayed while the same buffers,
+// workspace and stream are passed.
+stap_status run_batched(stap_plan p, const void* const* cubes, float* const* outs) {
+  const size_t n = p->cpis.size();
+  bool same = p->graph_exec && p->graph_ws == p->ws && p->graph_ws_bytes == p->ws_bytes &&
+              p->graph_stream == p->stream;
+  for (size_t i = 0; same && i < n; ++i)
+    same = p->graph_cubes[i] == cubes[i] && p->graph_outs[i] == outs[i];
+  if (same)
+    return cudaGraphLaunch(p->graph_exec, p->stream) == cudaSuccess ? STAP_OK : STAP_ERR_CUDA;
+
+  drop_graph(p);
+  if (!p->fork_ev) {
+    if (cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess)
+      return STAP_ERR_CUDA;
+    for (int i = 0; i < stap_plan_s::kSideStreams; ++i)
+      if (cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming) != cudaSuccess)
+        return STAP_ERR_CUDA;
+  }
+  const size_t arena = p->ws_bytes - p->step_bytes;
+  char* base = p->ws + p->step_bytes;
+  cudaStream_t cs = p->cap;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return STAP_ERR_CUDA;
+  stap_status st = STAP_OK;
+  int waves = 0;
+  size_t i = 0;
+  while (st == STAP_OK && i < n) {
+    // fork
+    if (cudaEventRecord(p->fork_ev, cs) != cudaSuccess) { st = STAP_ERR_CUDA; break; }
+    for (int k = 0; k < stap_plan_s::kSideStreams; ++k)
+      if (cudaStreamWaitEvent(p->side[k], p->fork_ev, 0) != cudaSuccess) st = STAP_ERR_CUDA;
+    size_t used = 0;
+    int slot = 0;
+    while (st == STAP_OK && i < n && (slot == 0 || used + inter_bytes(p->cpis[i]) <= arena)) {
+      const Cpi& c = p->cpis[i];
+      char* dop = base + used;
+      char* cov = dop + align_up(c.dop_elems() * 8);
+      char* wts = cov + align_up(c.cov_elems() * 16);
+      used += inter_bytes(c);
+      st = do_chain(p, c, cubes[i], outs[i], dop, cov, wts, p->side[slot % stap_plan_s::kSideStreams]);
+      ++slot;
+      ++i;
+    }
+    // join
+    for (int k = 0; k < stap_plan_s::kSideStreams && st == STAP_OK; ++k)
+      if (cudaEventRecord(p->join_ev[k], p->side[k]) != cudaSuccess ||
+          cudaStreamWaitEvent(cs, p->join_ev[k], 0) != cudaSuccess)
+        st = STAP_ERR_CUDA;
+    ++waves;
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t end = cudaStreamEndCapture(cs, &graph);
+  if (st != STAP_OK || end != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return st != STAP_OK ? st : STAP_ERR_CUDA;
+  }
+  const cudaError_t inst = cudaGraphInstantiate(&p->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (inst != cudaSuccess) {
+    p->graph_exec = nullptr;
+    return STAP_ERR_CUDA;
+  }
+  p->graph_cubes.assign(cubes, cubes + n);
+  p->graph_outs.assign(outs, outs + n);
+  p->graph_ws = p->ws;
+  p->graph_ws_bytes = p->ws_bytes;
+  p->graph_stream = p->stream;
+  p->graph_waves = waves;
+  return cudaGraphLaunch(p->graph_exec, p->stream) == cudaSuccess ? STAP_OK : STAP_ERR_CUDA;
 }
 
 stap_status single_cpi(stap_plan p) {
@@ -275,6 +387,9 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
   p->wts_off = off;
   off = align_up(off + max_wts * 8);
   p->run_bytes = off;
+  size_t all = p->step_bytes;
+  for (const Cpi& c : p->cpis) all += inter_bytes(c);
+  p->batch_bytes = all > p->run_bytes ? all : p->run_bytes;
   *out = p;
   if (workspace_bytes) *workspace_bytes = p->run_bytes;
   return STAP_OK;
@@ -294,6 +409,7 @@ stap_status stap_plan_set_workspace(stap_plan p, void* dev_ptr, size_t bytes) {
   p->ws = static_cast<char*>(dev_ptr);
   p->ws_bytes = bytes;
   p->tables_ready = false;
+  drop_graph(p);
   if (cudaMemsetAsync(p->ws, 0, sizeof(DeviceStatus), p->stream) != cudaSuccess) return STAP_ERR_CUDA;
   stap_status st = upload_tables(p);
   if (st != STAP_OK) return st;
@@ -315,11 +431,24 @@ stap_status stap_plan_set_steering(stap_plan p, int32_t cpi, const double* host_
     if (!std::isfinite(host_c128[i])) return STAP_ERR_INVALID_ARG;
   std::memcpy(c.steer.data(), host_c128, c.steer.size() * sizeof(double));
   c.separable = false;  // an arbitrary table: solve for every steering vector
+  drop_graph(p);        // the captured launches chose the solve variant
   return upload_tables(p, cpi);
 }
 
 stap_status stap_plan_destroy(stap_plan p) {
   if (!p) return STAP_ERR_INVALID_ARG;
+  drop_graph(p);
+  if (p->fork_ev) {
+    for (int i = 0; i < stap_plan_s::kSideStreams; ++i) {
+      if (p->side[i]) {
+        cudaStreamSynchronize(p->side[i]);
+        cudaStreamDestroy(p->side[i]);
+      }
+      if (p->join_ev[i]) cudaEventDestroy(p->join_ev[i]);
+    }
+    cudaEventDestroy(p->fork_ev);
+    if (p->cap) cudaStreamDestroy(p->cap);
+  }
   // pageable-memory uploads were staged synchronously, so nothing on the
   // device still reads the host tables
   delete p;
@@ -332,7 +461,7 @@ stap_status stap_doppler(stap_plan p, const void* cube, void* dop) {
   if (!cube || !dop) return STAP_ERR_INVALID_ARG;
   if (!aligned16(cube) || !aligned16(dop)) return STAP_ERR_MISALIGNED;
   if ((st = ready(p, p->step_bytes)) != STAP_OK) return st;
-  return do_doppler(p, p->cpis[0], cube, dop);
+  return do_doppler(p, p->cpis[0], cube, dop, p->stream);
 }
 
 stap_status stap_covariance(stap_plan p, const void* dop, void* cov) {
@@ -341,7 +470,7 @@ stap_status stap_covariance(stap_plan p, const void* dop, void* cov) {
   if (!dop || !cov) return STAP_ERR_INVALID_ARG;
   if (!aligned16(dop) || !aligned16(cov)) return STAP_ERR_MISALIGNED;
   if ((st = ready(p, p->step_bytes)) != STAP_OK) return st;
-  return do_covariance(p, p->cpis[0], dop, cov);
+  return do_covariance(p, p->cpis[0], dop, cov, p->stream);
 }
 
 stap_status stap_solve_weights(stap_plan p, const void* cov, void* wts) {
@@ -350,7 +479,7 @@ stap_status stap_solve_weights(stap_plan p, const void* cov, void* wts) {
   if (!cov || !wts) return STAP_ERR_INVALID_ARG;
   if (!aligned16(cov) || !aligned16(wts)) return STAP_ERR_MISALIGNED;
   if ((st = ready(p, p->step_bytes)) != STAP_OK) return st;
-  return do_solve(p, p->cpis[0], cov, wts);
+  return do_solve(p, p->cpis[0], cov, wts, p->stream);
 }
 
 stap_status stap_apply(stap_plan p, const void* dop, const void* wts, float* out) {
@@ -359,7 +488,7 @@ stap_status stap_apply(stap_plan p, const void* dop, const void* wts, float* out
   if (!dop || !wts || !out) return STAP_ERR_INVALID_ARG;
   if (!aligned16(dop) || !aligned16(wts) || !aligned16(out)) return STAP_ERR_MISALIGNED;
   if ((st = ready(p, p->step_bytes)) != STAP_OK) return st;
-  return do_apply(p, p->cpis[0], dop, wts, out);
+  return do_apply(p, p->cpis[0], dop, wts, out, p->stream);
 }
 
 stap_status stap_run_cpi(stap_plan p, const void* const* cubes, float* const* outs) {
@@ -370,16 +499,14 @@ stap_status stap_run_cpi(stap_plan p, const void* const* cubes, float* const* ou
   }
   stap_status st = ready(p, p->run_bytes);
   if (st != STAP_OK) return st;
-  void* dop = p->ws + p->dop_off;
-  void* cov = p->ws + p->cov_off;
-  void* wts = p->ws + p->wts_off;
-  for (size_t i = 0; i < p->cpis.size(); ++i) {
-    const Cpi& c = p->cpis[i];
-    if ((st = do_doppler(p, c, cubes[i], dop)) != STAP_OK) return st;
-    if ((st = do_covariance(p, c, dop, cov)) != STAP_OK) return st;
-    if ((st = do_solve(p, c, cov, wts)) != STAP_OK) return st;
-    if ((st = do_apply(p, c, dop, wts, outs[i])) != STAP_OK) return st;
-  }
+  if (p->cpis.size() > 1) return run_batched(p, cubes, outs);
+  return do_chain(p, p->cpis[0], cubes[0], outs[0], p->ws + p->dop_off, p->ws + p->cov_off,
+                  p->ws + p->wts_off, p->stream);
+}
+
+stap_status stap_plan_batch_bytes(stap_plan p, size_t* all_concurrent_bytes) {
+  if (!p || !all_concurrent_bytes) return STAP_ERR_INVALID_ARG;
+  *all_concurrent_bytes = p->batch_bytes;
   return STAP_OK;
 }
 

@@ -252,34 +252,35 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
 }
 
 // ---------------------------------------------------------------------------
-// Large systems (D up to 128).  The per-lane layout above needs two D-long
-// FP64 vectors per lane, which no longer fits next to a 132 KB factor, so here
-// one CTA of 4 warps owns one system at a time and the lanes own ROWS:
+// Larger systems (32 < D <= 128).  The per-lane layout above needs two D-long
+// FP64 vectors per lane, which stops fitting next to the factor, so here one
+// CTA of 4 warps owns one system at a time and the lanes own ROWS:
 //  * L (column-major packed lower triangle) lives in shared memory; the
 //    Cholesky is right-looking with the trailing update of each column spread
 //    over all 128 threads.
-//  * Each warp solves one right-hand side at a time; lane l keeps rows
-//    l, l+32, l+64, l+96 of its vectors in registers.  Substitution goes
-//    column by column: the owner of row j finishes y_j, a shuffle broadcasts
-//    it, and every lane updates its rows below (above, for L^H).
+//  * A group of LR lanes (LR = 32, or 16 for D <= 64 so that a warp carries
+//    two right-hand sides) solves one right-hand side at a time; lane l of
+//    the group keeps rows l, l + LR, l + 2 LR, l + 3 LR of its vectors in
+//    registers.  Substitution goes column by column: the owner of row j
+//    finishes y_j, a shuffle broadcasts it, and the group updates its rows
+//    below (above, for L^H).
 //  * The residual b - Rl u reads Rl from the input through L1: for each
 //    column index l every lane takes A[i][l] (i >= l) or conj(A[l][i]) (i < l)
 //    by a select, so all lanes run every DFMA.
 //  * Separable steering: the C basis solutions are kept in shared memory and
 //    combined per steering vector by lanes over rows.
-constexpr int kBigThreads = 128;
-constexpr int kBigRPL = 4;          // rows per lane: D <= 32 * kBigRPL = 128
+constexpr int kBigRPL = 4;          // rows per lane: D <= LR * kBigRPL
 
 __device__ __forceinline__ int colstart(int l, int D) { return l * D - l * (l - 1) / 2; }
 
 // In-place forward (L y = x) or back (L^H y = x) substitution of one vector
-// held as rows lane + 32 q.
-template <bool BACK>
+// held as rows li + LR q by the LR lanes of group `grp` (li = lane % LR).
+template <int LR, bool BACK>
 __device__ __forceinline__ void big_subst(double2 (&x)[kBigRPL], const double2* __restrict__ Lc,
-                                          const double* __restrict__ invd, int D, int lane) {
+                                          const double* __restrict__ invd, int D, int li, int grp) {
   for (int jj = 0; jj < D; ++jj) {
     const int j = BACK ? D - 1 - jj : jj;
-    const int owner = j & 31, qj = j >> 5;
+    const int owner = (j % LR) + grp * LR, qj = j / LR;
     double2 pick = x[0];
 #pragma unroll
     for (int q = 1; q < kBigRPL; ++q)
@@ -292,10 +293,10 @@ __device__ __forceinline__ void big_subst(double2 (&x)[kBigRPL], const double2* 
     yj.y *= s;
 #pragma unroll
     for (int q = 0; q < kBigRPL; ++q) {
-      if (q == qj && lane == owner) x[q] = yj;
-      const bool touch = BACK ? (q <= qj) : (q >= qj);     // warp-uniform
+      if (q == qj && li == j % LR) x[q] = yj;
+      const bool touch = (BACK ? (q <= qj) : (q >= qj)) && LR * q < D;   // warp-uniform
       if (touch) {
-        const int i = lane + 32 * q;
+        const int i = li + LR * q;
         const bool act = BACK ? (i < j) : (i > j && i < D);
         if (act) {
           if (BACK) {  // x_i -= conj(L[j][i]) y_j
@@ -317,25 +318,29 @@ __device__ __forceinline__ void big_subst(double2 (&x)[kBigRPL], const double2* 
   }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+template <int LR>
+__device__ __forceinline__ double group_sum(double v) {
+  for (int o = LR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-template <bool SEP>
-__global__ void __launch_bounds__(kBigThreads)
+template <bool SEP, int LR, int NT>
+__global__ void __launch_bounds__(NT)
 solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
                  const double2* __restrict__ steer, const double2* __restrict__ sep_g,
                  const double2* __restrict__ sep_a, long long nsys, int D, int S, int C,
                  double load_factor, int refine_steps, DeviceStatus* __restrict__ status) {
   extern __shared__ double2 sm[];
-  constexpr int NW = kBigThreads / 32;
+  constexpr int NW = NT / 32;
+  constexpr int NG = NT / LR;                      // right-hand sides in flight per CTA
   const int Dp = D * (D + 1) / 2;
   double2* Lc = sm;                                  // [Dp] column-major packed
   double2* Ub = Lc + Dp;                             // SEP: [C][D] basis solutions
-  double2* uv = Ub + (SEP ? (size_t)C * D : 0);      // [NW][D] broadcast vectors
-  double* invd = reinterpret_cast<double*>(uv + (size_t)NW * D);   // [D]
+  double2* uv = Ub + (SEP ? (size_t)C * D : 0);      // [NG][D] broadcast vectors
+  double* invd = reinterpret_cast<double*>(uv + (size_t)NG * D);   // [D]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int li = lane % LR, grp = lane / LR;         // lane in group, group in warp
+  const int g = warp * (32 / LR) + grp;              // group in CTA
   const double invD = 1.0 / (double)D;
 
   for (long long sys = blockIdx.x; sys < nsys; sys += gridDim.x) {
@@ -357,7 +362,7 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       }
       const double inv = rsqrt(djj);
       const double ljj = djj * inv;
-      for (int i = j + 1 + tid; i < D; i += kBigThreads) {
+      for (int i = j + 1 + tid; i < D; i += NT) {
         const double2 v = Lc[cj + i - j];
         Lc[cj + i - j] = make_double2(v.x * inv, v.y * inv);
       }
@@ -365,7 +370,7 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       // trailing update, pairs (i, l) with j < l <= i, column-major order
       const int m = D - j - 1;
       const int np = m * (m + 1) / 2;
-      for (int q = tid; q < np; q += kBigThreads) {
+      for (int q = tid; q < np; q += NT) {
         // column a of the trailing triangle holds m - a entries
         const float fm = 2.0f * m + 1.0f;
         int a = (int)((fm - sqrtf(fm * fm - 8.0f * (float)q)) * 0.5f);
@@ -388,66 +393,70 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       __syncthreads();
     }
 
-    // weights of steering vector s from u (rows lane + 32 q): warp-wide
+    // weights of steering vector s from u (rows li + LR q): group-wide
     auto emit = [&](int s, const double2 (&u)[kBigRPL]) {
       const double2* v = steer + (size_t)s * D;
       double qp = 0.0;
 #pragma unroll
       for (int q = 0; q < kBigRPL; ++q) {
-        const int i = lane + 32 * q;
+        const int i = li + LR * q;
         if (i < D) {
           const double2 vi = __ldg(v + i);
           qp = fma(vi.x, u[q].x, qp);
           qp = fma(vi.y, u[q].y, qp);
         }
       }
-      const double qs = warp_sum(qp);
+      const double qs = group_sum<LR>(qp);
       const bool good = ok && qs > 0.0 && isfinite(qs);
       const double scale = good ? rsqrt(qs) : 0.0;
       float2* w = wts + ((size_t)sys * S + s) * D;
 #pragma unroll
       for (int q = 0; q < kBigRPL; ++q) {
-        const int i = lane + 32 * q;
+        const int i = li + LR * q;
         if (i < D)
           w[i] = good ? make_float2((float)(u[q].x * scale), (float)(u[q].y * scale))
                       : make_float2(0.f, 0.f);
       }
     };
 
+    // every group runs the same number of passes (shuffles need the whole warp)
     const int nrhs = SEP ? C : S;
-    for (int rhs = warp; rhs < nrhs; rhs += NW) {
+    for (int r0 = 0; r0 < nrhs; r0 += NG) {
+      const int rhs = r0 + g;
+      const bool live = rhs < nrhs;
+      const int rsafe = live ? rhs : 0;
       double2 b[kBigRPL], u[kBigRPL], r[kBigRPL];
 #pragma unroll
       for (int q = 0; q < kBigRPL; ++q) {
-        const int i = lane + 32 * q;
+        const int i = li + LR * q;
         double2 v = make_double2(0.0, 0.0);
         if (i < D) {
           if (SEP) {
             const int t = i / C;
-            if (i - t * C == rhs) v = __ldg(sep_g + t);
+            if (i - t * C == rsafe) v = __ldg(sep_g + t);
           } else {
-            v = __ldg(steer + (size_t)rhs * D + i);
+            v = __ldg(steer + (size_t)rsafe * D + i);
           }
         }
         b[q] = v;
         u[q] = v;
       }
-      big_subst<false>(u, Lc, invd, D, lane);
-      big_subst<true>(u, Lc, invd, D, lane);
+      big_subst<LR, false>(u, Lc, invd, D, li, grp);
+      big_subst<LR, true>(u, Lc, invd, D, li, grp);
       for (int it = 0; it < refine_steps; ++it) {
         // r = b - Rl u
 #pragma unroll
         for (int q = 0; q < kBigRPL; ++q)
-          if (lane + 32 * q < D) uv[warp * D + lane + 32 * q] = u[q];
+          if (li + LR * q < D) uv[g * D + li + LR * q] = u[q];
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < kBigRPL; ++q) r[q] = b[q];
         for (int l = 0; l < D; ++l) {
-          const double2 ul = uv[warp * D + l];
+          const double2 ul = uv[g * D + l];
 #pragma unroll
           for (int q = 0; q < kBigRPL; ++q) {
-            const int i = lane + 32 * q;
-            if (32 * q < D) {               // warp-uniform: some lane has a row here
+            if (LR * q < D) {               // warp-uniform: some lane has a row here
+              const int i = li + LR * q;
               const int ic = i < D ? i : D - 1;
               const bool low = ic >= l;
               const double2 a = __ldg(low ? A + (size_t)ic * D + l : A + (size_t)l * D + ic);
@@ -464,26 +473,30 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
           }
         }
         __syncwarp();
-        big_subst<false>(r, Lc, invd, D, lane);
-        big_subst<true>(r, Lc, invd, D, lane);
+        big_subst<LR, false>(r, Lc, invd, D, li, grp);
+        big_subst<LR, true>(r, Lc, invd, D, li, grp);
 #pragma unroll
         for (int q = 0; q < kBigRPL; ++q) {
           u[q].x += r[q].x;
           u[q].y += r[q].y;
         }
       }
-      if (SEP) {
+      if (live) {
+        if (SEP) {
 #pragma unroll
-        for (int q = 0; q < kBigRPL; ++q)
-          if (lane + 32 * q < D) Ub[(size_t)rhs * D + lane + 32 * q] = u[q];
-      } else {
-        emit(rhs, u);
+          for (int q = 0; q < kBigRPL; ++q)
+            if (li + LR * q < D) Ub[(size_t)rhs * D + li + LR * q] = u[q];
+        } else {
+          emit(rhs, u);
+        }
       }
     }
     if (SEP) {
       __syncthreads();
-      for (int s = warp; s < S; s += NW) {
-        const double2* as = sep_a + (size_t)s * C;
+      for (int s0 = 0; s0 < S; s0 += NG) {
+        const int s = s0 + g;
+        const int ssafe = s < S ? s : 0;
+        const double2* as = sep_a + (size_t)ssafe * C;
         double2 u[kBigRPL];
 #pragma unroll
         for (int q = 0; q < kBigRPL; ++q) u[q] = make_double2(0.0, 0.0);
@@ -491,8 +504,8 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
           const double2 a = __ldg(as + c);
 #pragma unroll
           for (int q = 0; q < kBigRPL; ++q) {
-            if (32 * q < D) {
-              const int i = lane + 32 * q;
+            if (LR * q < D) {
+              const int i = li + LR * q;
               const double2 x = Ub[(size_t)c * D + (i < D ? i : D - 1)];
               u[q].x = fma(a.x, x.x, u[q].x);
               u[q].x = fma(-a.y, x.y, u[q].x);
@@ -501,12 +514,27 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
             }
           }
         }
-        emit(s, u);
+        if (s < S) emit(s, u);
       }
     }
     if (!ok && tid == 0) atomicAdd(&status->n_failed, 1ULL);
     __syncthreads();  // the next system reuses Lc, Ub
   }
+}
+
+template <bool SEP, int LR, int NT>
+cudaError_t launch_big(const double2* cov, float2* wts, const double2* steer, const double2* sep_g,
+                       const double2* sep_a, long long nsys, int D, int S, int C, double lf,
+                       int refine, DeviceStatus* status, size_t smem, cudaStream_t s) {
+  static int set_bytes[64] = {0};
+  cudaError_t e = ensure_smem(solve_big_kernel<SEP, LR, NT>, smem, set_bytes);
+  if (e != cudaSuccess) return e;
+  const int per_sm = (int)(228 * 1024 / (smem + 1024));
+  long long blocks = 152LL * (per_sm < 1 ? 1 : per_sm) * 2;
+  if (blocks > nsys) blocks = nsys;
+  solve_big_kernel<SEP, LR, NT><<<(unsigned)blocks, NT, smem, s>>>(
+      cov, wts, steer, sep_g, sep_a, nsys, D, S, C, lf, refine, status);
+  return cudaGetLastError();
 }
 
 int pow2ceil(int x) {
@@ -526,26 +554,27 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
   const bool sep = sep_g != nullptr && sep_a != nullptr && C >= 1 && C <= 32 && D % C == 0;
   if (D > kSmallMaxD) {  // one system per CTA, lanes over rows
     if (D > 32 * kBigRPL) return cudaErrorInvalidValue;
+    // 16 lanes per right-hand side (two per warp) up to D = 64 with 4 warps
+    // (several CTAs per SM); above that 32 lanes and 8 warps sharing one factor
+    const int LR = D <= 16 * kBigRPL ? 16 : 32;
+    const int NT = LR == 16 ? 128 : 256;
     const size_t Dp = (size_t)D * (D + 1) / 2;
-    const bool sep_big = sep && (Dp + (size_t)C * D + 4 * (size_t)D) * sizeof(double2) +
-                                   D * sizeof(double) <= 227 * 1024;
-    const size_t smem = (Dp + (sep_big ? (size_t)C * D : 0) + 4 * (size_t)D) * sizeof(double2) +
-                        D * sizeof(double);
+    const size_t ng = NT / LR;
+    auto bytes = [&](bool with_u) {
+      return (Dp + (with_u ? (size_t)C * D : 0) + ng * D) * sizeof(double2) + D * sizeof(double);
+    };
+    const bool sep_big = sep && bytes(true) <= 227 * 1024;
+    const size_t smem = bytes(sep_big);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    long long blocks = nsys < 152LL * 8 ? nsys : 152LL * 8;
-    cudaError_t e;
-    if (sep_big) {
-      static int set_bytes[64] = {0};
-      if ((e = ensure_smem(solve_big_kernel<true>, smem, set_bytes)) != cudaSuccess) return e;
-      solve_big_kernel<true><<<(unsigned)blocks, kBigThreads, smem, s>>>(
-          cov, wts, steer, sep_g, sep_a, nsys, D, S, C, load_factor, refine_steps, status);
-    } else {
-      static int set_bytes[64] = {0};
-      if ((e = ensure_smem(solve_big_kernel<false>, smem, set_bytes)) != cudaSuccess) return e;
-      solve_big_kernel<false><<<(unsigned)blocks, kBigThreads, smem, s>>>(
-          cov, wts, steer, nullptr, nullptr, nsys, D, S, C, load_factor, refine_steps, status);
-    }
-    return cudaGetLastError();
+    if (LR == 16)
+      return sep_big ? launch_big<true, 16, 128>(cov, wts, steer, sep_g, sep_a, nsys, D, S, C,
+                                                 load_factor, refine_steps, status, smem, s)
+                     : launch_big<false, 16, 128>(cov, wts, steer, nullptr, nullptr, nsys, D, S, C,
+                                                  load_factor, refine_steps, status, smem, s);
+    return sep_big ? launch_big<true, 32, 256>(cov, wts, steer, sep_g, sep_a, nsys, D, S, C,
+                                               load_factor, refine_steps, status, smem, s)
+                   : launch_big<false, 32, 256>(cov, wts, steer, nullptr, nullptr, nsys, D, S, C,
+                                                load_factor, refine_steps, status, smem, s);
   }
   constexpr size_t kBudget = 200 * 1024;
   const int Dp = D * (D + 1) / 2;

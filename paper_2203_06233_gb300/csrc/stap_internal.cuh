@@ -19,7 +19,7 @@ struct DeviceStatus {
 static_assert(sizeof(DeviceStatus) <= 256, "status block must fit its slot");
 
 constexpr int kMaxD = 128;       // largest snapshot length the solve kernels handle
-constexpr int kSmallMaxD = 64;   // above this, one system per CTA (lanes over rows)
+constexpr int kSmallMaxD = 32;   // above this, one system per CTA (lanes over rows)
 constexpr int kMaxLogK = 10;     // K <= 1024
 
 // ---------------------------------------------------------------- launchers --

@@ -35,7 +35,7 @@ EXPORTED = (
     "stap_plan_set_workspace", "stap_plan_set_stream", "stap_plan_set_steering",
     "stap_plan_destroy", "stap_doppler", "stap_covariance", "stap_solve_weights", "stap_apply",
     "stap_run_cpi", "stap_get_status", "stap_status_string", "stap_abi_version",
-    "stap_run_cpi_noalloc",
+    "stap_run_cpi_noalloc", "stap_plan_batch_bytes",
 )
 
 # size of the library-owned scratch array used by stap_run_cpi_noalloc
@@ -92,6 +92,7 @@ def lib():
             L.stap_status_string.argtypes = [ctypes.c_int]
             L.stap_status_string.restype = ctypes.c_char_p
             L.stap_abi_version.argtypes = []
+            L.stap_plan_batch_bytes.argtypes = [vp, ctypes.POINTER(sz)]
             L.stap_run_cpi_noalloc.argtypes = [ctypes.POINTER(stap_dims), ctypes.POINTER(stap_options),
                                                vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
             for f in EXPORTED:
@@ -163,6 +164,12 @@ def stap_plan_workspace_sizes(plan):
     _check(lib().stap_plan_workspace_sizes(plan, ctypes.byref(a), ctypes.byref(b)),
            "stap_plan_workspace_sizes")
     return a.value, b.value
+
+
+def stap_plan_batch_bytes(plan) -> int:
+    a = ctypes.c_size_t()
+    _check(lib().stap_plan_batch_bytes(plan, ctypes.byref(a)), "stap_plan_batch_bytes")
+    return a.value
 
 
 def stap_plan_set_workspace(plan, workspace: torch.Tensor):
@@ -257,7 +264,8 @@ class Plan:
     """
 
     def __init__(self, dims, load_factor: float = 1e-3, refine_steps: int = 1,
-                 precision: int = STAP_PREC_FP32, device=None, steps_only: bool = False):
+                 precision: int = STAP_PREC_FP32, device=None, steps_only: bool = False,
+                 max_workspace_bytes: Optional[int] = None):
         dl = list(dims) if isinstance(dims, (list, tuple)) and dims and not isinstance(dims[0], int) \
             else [dims]
         self.dims = [_dims(d) for d in dl]
@@ -266,7 +274,12 @@ class Plan:
         with torch.cuda.device(self.device):
             self.handle, _ = stap_plan_create(self.dims, opts)
             self.step_bytes, self.run_bytes = stap_plan_workspace_sizes(self.handle)
+            self.batch_bytes = stap_plan_batch_bytes(self.handle)
             nbytes = self.step_bytes if steps_only else self.run_bytes
+            if not steps_only and len(self.dims) > 1:
+                # a batch: as much of the all-concurrent size as the cap allows
+                cap = max_workspace_bytes if max_workspace_bytes is not None else 16 << 30
+                nbytes = max(self.run_bytes, min(self.batch_bytes, cap))
             self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
             stap_plan_set_workspace(self.handle, self.workspace)
 

@@ -226,3 +226,75 @@ WORKLOADS = {
     "mixed": mixed_cpi,
     "large": large_cpi,
 }
+
+
+# ----------------------------------------------------------------------------
+# The same recipe evaluated on a CUDA device (for cubes of several GB).  The
+# counters and SplitMix64 mixing are bit-identical to the numpy version; the
+# Box-Muller transcendentals and the clutter matrix product may differ in the
+# last bits, so tests always hand the oracle the device cube copied back.
+# ----------------------------------------------------------------------------
+
+def _signed(x: int) -> int:
+    x &= 0xFFFFFFFFFFFFFFFF
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+def _mix_t(z):
+    z = z ^ ((z >> 30) & ((1 << 34) - 1))          # logical shifts on int64 bit patterns
+    z = z * _signed(0xBF58476D1CE4E5B9)
+    z = z ^ ((z >> 27) & ((1 << 37) - 1))
+    z = z * _signed(0x94D049BB133111EB)
+    return z ^ ((z >> 31) & ((1 << 33) - 1))
+
+
+def _uniform_t(seed, stream, idx, sub=0):
+    import torch
+    key = _signed(int(_key(seed, stream, sub)))
+    z = _mix_t(key + (idx + 1) * _signed(0x9E3779B97F4A7C15))
+    return (((z >> 11) & ((1 << 53) - 1)).to(torch.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def _complex_normal_t(seed, stream, idx, var, sub=0):
+    import torch
+    u1 = _uniform_t(seed, stream, idx * 2, sub)
+    u2 = _uniform_t(seed, stream, idx * 2 + 1, sub)
+    rad = torch.sqrt(-torch.log(u1) * var)
+    ang = (2.0 * np.pi) * u2
+    return torch.complex(rad * torch.cos(ang), rad * torch.sin(ang))
+
+
+def make_cube_torch(spec: CPISpec, device="cuda"):
+    """The complex64 cube of ``spec`` computed on ``device`` (torch tensor)."""
+    import torch
+    C, P, R = spec.n_chan, spec.n_pulses, spec.n_range
+    dev = torch.device(device)
+    cube = torch.empty((C, P, R), dtype=torch.complex64, device=dev)
+    f = torch.from_numpy(patch_frequencies()).to(dev)
+    alpha = None
+    if spec.cnr_db is not None:
+        cnr = 10.0 ** (spec.cnr_db / 10.0)
+        idx = torch.arange(N_PATCH * R, dtype=torch.int64, device=dev)
+        alpha = _complex_normal_t(spec.seed, STREAM_CLUTTER, idx, cnr / N_PATCH, spec.sub).reshape(N_PATCH, R)
+    p = torch.arange(P, dtype=torch.float64, device=dev)
+    dop_steer = torch.exp(torch.complex(torch.zeros_like(p[:, None] * f[None, :]),
+                                        2.0 * np.pi * p[:, None] * f[None, :]))   # [P][patch]
+    base = torch.arange(P * R, dtype=torch.int64, device=dev)
+    for c in range(C):
+        blk = torch.zeros((P, R), dtype=torch.complex128, device=dev)
+        if spec.noise:
+            blk += _complex_normal_t(spec.seed, STREAM_NOISE, base + c * P * R, 1.0, spec.sub).reshape(P, R)
+        if alpha is not None:
+            ph = 2.0 * np.pi * f * c
+            sp = torch.complex(torch.cos(ph), torch.sin(ph))
+            blk += (dop_steer * sp[None, :]) @ alpha
+        cube[c] = blk.to(torch.complex64)
+    for t in spec.targets:
+        th = np.deg2rad(steering_angle_deg(t.s0, spec.n_steering))
+        fs = 0.5 * np.sin(th)
+        amp = np.sqrt(10.0 ** (t.snr_db / 10.0)) * np.exp(1j * t.phase)
+        sig = amp * np.exp(2j * np.pi * fs * np.arange(C))[:, None] * \
+            np.exp(2j * np.pi * (t.k0 / spec.n_dop) * np.arange(P))[None, :]
+        col = cube[:, :, t.r0].to(torch.complex128) + torch.from_numpy(sig).to(dev)
+        cube[:, :, t.r0] = col.to(torch.complex64)
+    return cube

@@ -1,0 +1,91 @@
+"""Batched stap_run_cpi: uneven CPIs packed into waves, forked streams,
+captured in a CUDA graph and replayed."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2203_06233_gb300 import stap, synth
+
+from _parity import power_errors
+
+pytestmark = pytest.mark.gpu
+
+
+def growth(spec):
+    return max(1.0, (spec.D + 2) / 14.0)
+
+
+def _uneven(n=12, seed=7):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        C = int(rng.choice([4, 8, 16]))
+        T = int(rng.choice([2, 3, 4]))
+        K = int(rng.choice([64, 128]))
+        R = 64 * int(rng.integers(2, 17))
+        S = int(rng.choice([8, 16]))
+        out.append(synth.CPISpec(C, K, K, R, T, 64, S, cnr_db=float(rng.uniform(20, 40)),
+                                 targets=synth.random_targets(seed, 2, R, K, S, sub=i + 1),
+                                 seed=seed, sub=i + 1))
+    return out
+
+
+def test_batch_equals_single_cpi_runs_across_waves_and_replays():
+    specs = _uneven()
+    cubes = [torch.from_numpy(synth.make_cube(s)).cuda() for s in specs]
+    singles = []
+    for s, c in zip(specs, cubes):
+        p = stap.Plan(s.dims())
+        singles.append(p.run_cpi(c).clone())
+        p.close()
+    full = stap.Plan([s.dims() for s in specs])                    # one wave
+    tight = stap.Plan([s.dims() for s in specs], max_workspace_bytes=0)   # one CPI per wave
+    for plan in (full, tight):
+        outs = plan.run_cpi(cubes)                                 # capture + launch
+        again = plan.run_cpi(cubes, outs)                          # graph replay
+        torch.cuda.synchronize()
+        for o, ref in zip(again, singles):
+            assert torch.equal(o, ref)
+        fresh = [torch.zeros_like(o) for o in outs]                # new buffers: recapture
+        plan.run_cpi(cubes, fresh)
+        torch.cuda.synchronize()
+        for o, ref in zip(fresh, singles):
+            assert torch.equal(o, ref)
+        assert plan.status() == (stap.STAP_OK, 0)
+    full.close()
+    tight.close()
+
+
+def test_full_batch_workload_on_sampled_cpis():
+    """512 uneven CPIs (C in {4,8,16}, T in {2,3,4}, P = K in {64,128,256},
+    R in 1024..16384, B 64, S in {8,16}) in one call; the oracle checks one
+    seeded block of 8 seeded CPIs."""
+    specs = synth.batch_cpis(512)
+    cubes = [synth.make_cube_torch(s, "cuda") for s in specs]
+    plan = stap.Plan([s.dims() for s in specs])
+    outs = plan.run_cpi(cubes)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan.run_cpi(cubes, outs)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    cells = sum(s.cells for s in specs)
+    print(f"batch of {len(specs)} CPIs: {el * 1e3:.1f} ms, {cells / el:.3e} cells/s, "
+          f"workspace {plan.workspace.numel() / 2**30:.1f} GiB of {plan.batch_bytes / 2**30:.1f}")
+    assert plan.status() == (stap.STAP_OK, 0)
+    rng = np.random.default_rng(4)
+    for i in sorted(int(x) for x in rng.choice(len(specs), 8, replace=False)):
+        s = specs[i]
+        b = int(rng.integers(s.NB))
+        B = s.training_block
+        d = oracle.Dims(*s.dims())
+        ref = oracle.run(d, cubes[i].cpu().numpy(), r0=b * B, nr=B)["out"]
+        got = outs[i][:, :, b * B:(b + 1) * B].cpu().numpy()
+        e_cell, e_norm = power_errors(got, ref)
+        print(f"  cpi {i} {s.dims()} block {b}: max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
+        g = growth(s)
+        assert e_norm <= 1e-5 * g and e_cell <= 1e-3 * g, (i, e_cell, e_norm)
+    plan.close()
