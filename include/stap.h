@@ -54,8 +54,10 @@ typedef enum {
  * diagonal loading, Cholesky factorisation and triangular solves are FP64 in
  * every mode. */
 typedef enum {
-  STAP_PREC_FP32 = 0 /* FP32 FFT; covariance accumulated error-free in FP32
-                        pairs (two-product / compensated sum); FP32 apply */
+  STAP_PREC_FP32 = 0,  /* FP32 FFT; covariance accumulated error-free in FP32
+                          pairs (two-product / compensated sum); FP32 apply */
+  STAP_PREC_TF32X3 = 2 /* mixed: covariance from 3xTF32 tensor-core products
+                          (hi*hi + hi*lo + lo*hi) with FP32 accumulation */
 } stap_precision;
 
 typedef struct {

@@ -1,0 +1,207 @@
+// Mixed-precision contractions on the tensor cores (tcgen05, kind::tf32).
+//
+// Covariance per (Doppler bin, range block), R = (1/B) X X^H with X the D x B
+// snapshot tile, as three real accumulators in TMEM:
+//   Re R = Xr Xr^T + Xi Xi^T,   Im R = Xi Xr^T - Xr Xi^T
+// (accumulators A = Xr Xr^T + Xi Xi^T, Bm = Xi Xr^T, Cm = Xr Xi^T; Im R =
+// Bm - Cm in the epilogue).  Every product is a 3xTF32 split, hi*hi + hi*lo +
+// lo*hi with hi = tf32(v), lo = tf32(v - hi), accumulated in FP32 by the
+// tensor core: about 2^-21 relative per product instead of TF32's 2^-11.
+// The M = N = 128 tile holds floor(128 / D) systems on its diagonal (rows and
+// columns g*D .. g*D + D - 1 belong to system g; off-diagonal blocks are
+// never read), so D up to 128 needs no second tile.  Thread i of the CTA owns
+// TMEM lane i, i.e. row i of all three accumulators, so the epilogue forms
+// its row of R without any exchange.
+//
+// Pipeline per CTA (128 threads): the B cells are staged in chunks of 32 into
+// one of two shared-memory stages (four 128 x 32 TF32 tiles: Xr hi/lo, Xi
+// hi/lo, in the K-major core-matrix layout), thread 0 issues the 48 MMAs of
+// the chunk and commits them to that stage's mbarrier, and the next chunk is
+// staged into the other stage meanwhile.  All waits are bounded: on expiry
+// the CTA records a timeout in the device status and stops.
+#include "snapshots.cuh"
+#include "tcgen05.cuh"
+
+namespace stap {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kKC = 32;                       // cells per chunk (K of one stage)
+constexpr int kTile = 128 * kKC * 4;          // one 128 x 32 TF32 operand tile (16 KB)
+constexpr int kStage = 4 * kTile;             // Xr hi, Xr lo, Xi hi, Xi lo (64 KB)
+constexpr int kWaitIter = 1 << 22;
+constexpr int kTmemCols = 512;                // 3 x 128 accumulators, rounded up
+
+__global__ void __launch_bounds__(kTcThreads)
+covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K,
+                     int R, int T, int B, int NB, int G, long long ntiles,
+                     DeviceStatus* __restrict__ status) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int D = C * T;
+  const int rows = G * D;
+  const long long nsys = (long long)K * NB;
+  const int nchunks = (B + kKC - 1) / kKC;
+
+  for (int i = tid; i < 2 * kStage / 4; i += kTcThreads) reinterpret_cast<uint32_t*>(sm)[i] = 0u;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t accA = tmem, accB = tmem + 128, accC = tmem + 256;
+  const uint32_t idesc = tc::idesc_tf32(128, 128);
+  uint32_t parity[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  bool ok = true;
+  long long gch = 0;                          // chunks issued by this CTA (stage = gch & 1)
+
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const long long sys0 = tile * G;
+    for (int ch = 0; ch < nchunks && ok; ++ch, ++gch) {
+      const int st = (int)(gch & 1);
+      uint8_t* stage = sm + st * kStage;
+      if (pending[st]) {  // the MMAs that last read this stage must be done
+        ok = tc::mbar_wait(&mbar[st], parity[st], kWaitIter);
+        parity[st] ^= 1u;
+        pending[st] = false;
+      }
+      ok = __syncthreads_and(ok);
+      if (!ok) break;
+      // stage cells c0 .. c0+31: one core matrix (8 rows x 4 cells) per warp pass
+      const int c0 = ch * kKC;
+      for (int cmi = warp; cmi < (rows + 7) / 8 * (kKC / 4); cmi += kTcThreads / 32) {
+        const int pg = cmi / (kKC / 4), jg = cmi - pg * (kKC / 4);
+        const int p = pg * 8 + (lane >> 2), j = jg * 4 + (lane & 3);
+        float2 x = make_float2(0.f, 0.f);
+        if (p < rows && c0 + j < B) {
+          const int g = p / D, i = p - g * D;
+          const long long sys = sys0 + g;
+          if (sys < nsys) {
+            const int k = (int)(sys / NB), b = (int)(sys - (long long)k * NB);
+            const int t = i / C, c = i - t * C;
+            const int kk = wrap_bin(k + t - T / 2, K);
+            x = __ldg(dop + ((size_t)c * K + kk) * R + (size_t)b * B + c0 + j);
+          }
+        }
+        const uint32_t rh = tc::to_tf32(x.x), ih = tc::to_tf32(x.y);
+        const uint32_t rl = tc::to_tf32(x.x - __uint_as_float(rh));
+        const uint32_t il = tc::to_tf32(x.y - __uint_as_float(ih));
+        const int off = tc::cm_offset(p, j, kKC);
+        *reinterpret_cast<uint32_t*>(stage + 0 * kTile + off) = rh;
+        *reinterpret_cast<uint32_t*>(stage + 1 * kTile + off) = rl;
+        *reinterpret_cast<uint32_t*>(stage + 2 * kTile + off) = ih;
+        *reinterpret_cast<uint32_t*>(stage + 3 * kTile + off) = il;
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (tid == 0) {
+        const uint32_t base = tc::smem_u32(stage);
+        const uint32_t rh = base, rl = base + kTile, ih = base + 2 * kTile, il = base + 3 * kTile;
+        constexpr uint32_t LBO = 128, SBO = 128 * (kKC / 4);
+        for (int ks = 0; ks < kKC / 8; ++ks) {
+          const uint32_t o = ks * 256;
+          const bool first = (ch == 0 && ks == 0);
+          const uint64_t drh = tc::smem_desc(rh + o, LBO, SBO), drl = tc::smem_desc(rl + o, LBO, SBO);
+          const uint64_t dih = tc::smem_desc(ih + o, LBO, SBO), dil = tc::smem_desc(il + o, LBO, SBO);
+          // A += Xr Xr^T + Xi Xi^T
+          tc::mma_tf32(accA, drh, drh, idesc, !first);
+          tc::mma_tf32(accA, drh, drl, idesc, true);
+          tc::mma_tf32(accA, drl, drh, idesc, true);
+          tc::mma_tf32(accA, dih, dih, idesc, true);
+          tc::mma_tf32(accA, dih, dil, idesc, true);
+          tc::mma_tf32(accA, dil, dih, idesc, true);
+          // Bm += Xi Xr^T
+          tc::mma_tf32(accB, dih, drh, idesc, !first);
+          tc::mma_tf32(accB, dih, drl, idesc, true);
+          tc::mma_tf32(accB, dil, drh, idesc, true);
+          // Cm += Xr Xi^T
+          tc::mma_tf32(accC, drh, dih, idesc, !first);
+          tc::mma_tf32(accC, drh, dil, idesc, true);
+          tc::mma_tf32(accC, drl, dih, idesc, true);
+        }
+        tc::mma_commit(&mbar[st]);
+      }
+      pending[st] = true;
+    }
+    // all MMAs of this tile done (commits complete in order; drain both stages)
+    for (int s2 = 0; s2 < 2; ++s2) {
+      if (pending[s2] && ok) ok = tc::mbar_wait(&mbar[s2], parity[s2], kWaitIter);
+      if (pending[s2]) {
+        parity[s2] ^= 1u;
+        pending[s2] = false;
+      }
+    }
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    tc::fence_after_sync();
+    // epilogue: thread tid owns row tid of the tile = row i of system g
+    const int g = tid / D, i = tid - g * D;
+    const long long sys = sys0 + g;
+    const bool mine = tid < rows && sys < nsys;
+    const double invB = 1.0 / (double)B;
+    double2* out = cov + (size_t)(mine ? sys : 0) * D * D;
+    const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
+    for (int cb = 0; cb < rows; cb += 8) {        // columns in blocks of 8 (warp-collective)
+      float a[8], bm[8], cm[8];
+      tc::tmem_ld8(accA + lanebase + cb, a);
+      tc::tmem_ld8(accB + lanebase + cb, bm);
+      tc::tmem_ld8(accC + lanebase + cb, cm);
+      if (mine) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int col = cb + u;
+          const int l = col - g * D;
+          if (l >= 0 && l <= i && l < D) {        // lower triangle of this system, mirrored
+            const double re = (double)a[u] * invB;
+            const double im = (l == i) ? 0.0 : ((double)bm[u] - (double)cm[u]) * invB;
+            out[(size_t)i * D + l] = make_double2(re, im);
+            if (l != i) out[(size_t)l * D + i] = make_double2(re, -im);
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // TMEM reads done before the next tile's MMAs overwrite it
+    tc::fence_after_sync();
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(&status->timeout, 1u);
+    for (int s2 = 0; s2 < 2; ++s2)      // let MMAs still in flight finish (bounded)
+      if (pending[s2]) tc::mbar_wait(&mbar[s2], parity[s2], kWaitIter);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int T, int B,
+                                 DeviceStatus* status, cudaStream_t s) {
+  const int D = C * T;
+  const int NB = R / B;
+  if (NB == 0) return cudaSuccess;
+  if (D > 128) return cudaErrorInvalidValue;
+  const int G = 128 / D;
+  const long long nsys = (long long)K * NB;
+  const long long ntiles = (nsys + G - 1) / G;
+  const size_t smem = 2 * (size_t)kStage;
+  static int set_bytes[64] = {0};
+  cudaError_t e = ensure_smem(covariance_tc_kernel, smem, set_bytes);
+  if (e != cudaSuccess) return e;
+  long long blocks = ntiles < 152 ? ntiles : 152;   // one CTA per SM (TMEM and shared memory)
+  covariance_tc_kernel<<<(unsigned)blocks, kTcThreads, smem, s>>>(dop, cov, C, K, R, T, B, NB, G,
+                                                                    ntiles, status);
+  return cudaGetLastError();
+}
+
+}  // namespace stap

@@ -183,7 +183,10 @@ stap_status do_doppler(stap_plan p, const Cpi& c, const void* cube, void* dop, c
 
 stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov, cudaStream_t st) {
   const stap_dims& d = c.d;
-  (void)p;
+  if (p->opt.precision == STAP_PREC_TF32X3)
+    return check_launch(stap::launch_covariance_tc(static_cast<const float2*>(dop),
+                                                   static_cast<double2*>(cov), d.n_chan, d.n_dop,
+                                                   d.n_range, d.tdof, d.training_block, p->status(), st));
   return check_launch(stap::launch_covariance_fp32(static_cast<const float2*>(dop),
                                                    static_cast<double2*>(cov), d.n_chan, d.n_dop,
                                                    d.n_range, d.tdof, d.training_block, st));
@@ -347,7 +350,7 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
   if (!(o.load_factor >= 0.0) || !std::isfinite(o.load_factor) || o.refine_steps < 0 ||
       o.refine_steps > 4)
     return STAP_ERR_INVALID_ARG;
-  if (o.precision != STAP_PREC_FP32) return STAP_ERR_UNSUPPORTED;
+  if (o.precision != STAP_PREC_FP32 && o.precision != STAP_PREC_TF32X3) return STAP_ERR_UNSUPPORTED;
   for (int i = 0; i < n_cpi; ++i) {
     stap_status st = validate(dims[i]);
     if (st != STAP_OK) return st;

@@ -35,6 +35,10 @@ cudaError_t launch_doppler(const float2* cube, float2* dop, const float* win, co
 cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K, int R, int T,
                                    int B, cudaStream_t s);
 
+// Same covariance from 3xTF32 tensor-core products (tcgen05), FP32 accumulation.
+cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int T, int B,
+                                 DeviceStatus* status, cudaStream_t s);
+
 // FP64 loading, Cholesky, solves, refinement and scaling for nsys systems.
 // cov [nsys][D][D] c128 -> wts [nsys][S][D] c64; steer [S][D] c128.  If
 // sep_g [T] and sep_a [S][C] are given, steer[s] = sep_g (x) sep_a[s] and the

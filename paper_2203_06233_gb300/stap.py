@@ -28,6 +28,7 @@ STAP_ERR_NO_WORKSPACE = 7
 STAP_ERR_MISALIGNED = 8
 
 STAP_PREC_FP32 = 0
+STAP_PREC_TF32X3 = 2
 
 # every symbol include/stap.h declares
 EXPORTED = (

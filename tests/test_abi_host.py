@@ -76,6 +76,8 @@ def test_plan_create_rejects_bad_shapes(dims, code):
     (1e-3, -1, 0, stap.STAP_ERR_INVALID_ARG),
     (1e-3, 5, 0, stap.STAP_ERR_INVALID_ARG),
     (1e-3, 1, 7, stap.STAP_ERR_UNSUPPORTED),
+    (1e-3, 1, 1, stap.STAP_ERR_UNSUPPORTED),
+    (1e-3, 1, 2, stap.STAP_OK),
     (0.0, 0, 0, stap.STAP_OK),
 ])
 def test_plan_create_checks_options(lf, refine, prec, code):

@@ -1,0 +1,58 @@
+"""Parity of the mixed-precision path (STAP_PREC_TF32X3: tcgen05 3xTF32
+tensor-core products with FP32 accumulation; FP64 solve unchanged) with the
+FP64 oracle.
+
+Tolerances: covariance per system (relative Frobenius) <= max(1e-5, 2 B u)
+(about 2^-21 per product from the 3xTF32 split plus FP32 accumulation of B
+terms, u = 2^-24), Hermitian bit-exact; whole path normwise <= 1e-3 (the
+mixed bar), grown by (D + 2)/14 for D > 12 as for the plain path."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2203_06233_gb300 import stap, synth
+
+from _parity import EDGE_SPECS, EPS32, power_errors, to_np
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [synth.small_cpi(), synth.standard_cpi()] + EDGE_SPECS
+IDS = ["small", "standard"] + [f"edge{i}" for i in range(len(EDGE_SPECS))]
+
+
+def growth(spec):
+    return max(1.0, (spec.D + 2) / 14.0)
+
+
+def _plan(spec):
+    return stap.Plan(spec.dims(), precision=stap.STAP_PREC_TF32X3)
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_mixed_covariance_parity(spec):
+    d = oracle.Dims(*spec.dims())
+    dop64 = oracle.doppler(d, synth.make_cube(spec)).astype(np.complex64)
+    ref = oracle.covariance(d, dop64)
+    plan = _plan(spec)
+    cov = to_np(plan.covariance(torch.from_numpy(dop64).cuda()))
+    assert plan.status() == (stap.STAP_OK, 0)
+    np.testing.assert_array_equal(cov, np.conj(np.swapaxes(cov, -1, -2)))
+    num = np.linalg.norm((cov - ref).reshape(spec.n_dop, spec.NB, -1), axis=-1)
+    den = np.linalg.norm(ref.reshape(spec.n_dop, spec.NB, -1), axis=-1)
+    tol = max(1e-5, 2 * spec.training_block * EPS32)
+    print(f"{spec.dims()}: max per-system rel err {np.max(num / den):.3e} (tol {tol:.1e})")
+    assert np.max(num / den) <= tol
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_mixed_run_cpi_end_to_end(spec):
+    d = oracle.Dims(*spec.dims())
+    cube = synth.make_cube(spec)
+    ref = oracle.run(d, cube)["out"]
+    plan = _plan(spec)
+    out = to_np(plan.run_cpi(torch.from_numpy(cube).cuda()))
+    assert plan.status() == (stap.STAP_OK, 0)
+    e_cell, e_norm = power_errors(out, ref)
+    print(f"{spec.dims()}: mixed max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
+    assert e_norm <= 1e-3 * growth(spec), e_norm
