@@ -56,8 +56,11 @@ typedef enum {
 typedef enum {
   STAP_PREC_FP32 = 0,  /* FP32 FFT; covariance accumulated error-free in FP32
                           pairs (two-product / compensated sum); FP32 apply */
-  STAP_PREC_TF32X3 = 2 /* mixed: covariance from 3xTF32 tensor-core products
-                          (hi*hi + hi*lo + lo*hi) with FP32 accumulation */
+  STAP_PREC_TF32X3 = 2 /* mixed: covariance and apply from 3xTF32 tensor-core
+                          products (hi*hi + hi*lo + lo*hi) with FP32
+                          accumulation; the apply falls back to FP32 when
+                          neither B divides 128 nor 128 divides B, or a 128-cell
+                          tile needs more than 128 steering columns */
 } stap_precision;
 
 typedef struct {

@@ -183,6 +183,187 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
+// ---------------------------------------------------------------------------
+// Apply, out[s][k][r] = |w_{k,b(r),s}^H x_{k,r}|^2, as a real GEMM per tile of
+// 128 range cells of one Doppler bin (M = cells, N = steering vectors of the
+// nbt blocks the tile covers, K = D):
+//   Re y = Xr Wr^T + Xi Wi^T,   Im y = Xi Wr^T - Xr Wi^T
+// with accumulators A = Xr Wr^T + Xi Wi^T, Bm = Xi Wr^T, Cm = Xr Wi^T, each a
+// 3xTF32 product.  Column j*S + s of the tile holds steering vector s of the
+// tile's block j; a cell only reads its own block's columns.  K = D goes in
+// double-buffered chunks of 16.  Thread m owns TMEM lane m (cell r0 + m), so
+// the epilogue writes each output row out[s][k][r0 .. r0+127] coalesced.
+constexpr int kAKC = 16;                      // snapshot entries per chunk
+constexpr int kAX = 128 * kAKC * 4;           // one 128 x 16 TF32 tile (8 KB)
+constexpr int kAStage = 8 * kAX;              // X: re/im x hi/lo, W: re/im x hi/lo (64 KB)
+
+__global__ void __launch_bounds__(kTcThreads)
+apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
+                float* __restrict__ out, int C, int K, int R, int T, int B, int S, int NB,
+                int NP, long long ntiles, DeviceStatus* __restrict__ status) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int D = C * T;
+  const int tiles_per_k = (R + 127) / 128;
+  const int nbt_max = B < 128 ? 128 / B : 1;
+  const int N = nbt_max * S;
+  const int nchunks = (D + kAKC - 1) / kAKC;
+
+  for (int i = tid; i < 2 * kAStage / 4; i += kTcThreads) reinterpret_cast<uint32_t*>(sm)[i] = 0u;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t accA = tmem, accB = tmem + 128, accC = tmem + 256;
+  const uint32_t idesc = tc::idesc_tf32(128, NP);
+  uint32_t parity[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  bool ok = true;
+  long long gch = 0;
+
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int k = (int)(tile / tiles_per_k);
+    const int r0 = (int)(tile - (long long)k * tiles_per_k) * 128;
+    const int b0 = r0 / B;
+    for (int ch = 0; ch < nchunks && ok; ++ch, ++gch) {
+      const int st = (int)(gch & 1);
+      uint8_t* stage = sm + st * kAStage;
+      if (pending[st]) {
+        ok = tc::mbar_wait(&mbar[st], parity[st], kWaitIter);
+        parity[st] ^= 1u;
+        pending[st] = false;
+      }
+      ok = __syncthreads_and(ok);
+      if (!ok) break;
+      const int d0 = ch * kAKC;
+      // X tile: rows = cells, K = snapshot entries d0 .. d0+15
+      for (int cmi = warp; cmi < 16 * (kAKC / 4); cmi += kTcThreads / 32) {
+        const int pg = cmi / (kAKC / 4), jg = cmi - pg * (kAKC / 4);
+        const int m = pg * 8 + (lane >> 2), dd = jg * 4 + (lane & 3);
+        const int d = d0 + dd, r = r0 + m;
+        float2 x = make_float2(0.f, 0.f);
+        if (d < D && r < R) {
+          const int t = d / C, c = d - t * C;
+          const int kk = wrap_bin(k + t - T / 2, K);
+          x = __ldg(dop + ((size_t)c * K + kk) * R + r);
+        }
+        const uint32_t rh = tc::to_tf32(x.x), ih = tc::to_tf32(x.y);
+        const uint32_t rl = tc::to_tf32(x.x - __uint_as_float(rh));
+        const uint32_t il = tc::to_tf32(x.y - __uint_as_float(ih));
+        const int off = tc::cm_offset(m, dd, kAKC);
+        *reinterpret_cast<uint32_t*>(stage + 0 * kAX + off) = rh;
+        *reinterpret_cast<uint32_t*>(stage + 1 * kAX + off) = rl;
+        *reinterpret_cast<uint32_t*>(stage + 2 * kAX + off) = ih;
+        *reinterpret_cast<uint32_t*>(stage + 3 * kAX + off) = il;
+      }
+      // W tile: rows n = j*S + s (block b0 + j), K = snapshot entries
+      for (int cmi = warp; cmi < (NP / 8) * (kAKC / 4); cmi += kTcThreads / 32) {
+        const int pg = cmi / (kAKC / 4), jg = cmi - pg * (kAKC / 4);
+        const int n = pg * 8 + (lane >> 2), dd = jg * 4 + (lane & 3);
+        const int d = d0 + dd;
+        const int j = n / S, s = n - j * S;
+        float2 w = make_float2(0.f, 0.f);
+        if (n < N && d < D && b0 + j < NB)
+          w = __ldg(wts + ((((size_t)k * NB + b0 + j) * S + s) * D + d));
+        const uint32_t rh = tc::to_tf32(w.x), ih = tc::to_tf32(w.y);
+        const uint32_t rl = tc::to_tf32(w.x - __uint_as_float(rh));
+        const uint32_t il = tc::to_tf32(w.y - __uint_as_float(ih));
+        const int off = tc::cm_offset(n, dd, kAKC);
+        *reinterpret_cast<uint32_t*>(stage + 4 * kAX + off) = rh;
+        *reinterpret_cast<uint32_t*>(stage + 5 * kAX + off) = rl;
+        *reinterpret_cast<uint32_t*>(stage + 6 * kAX + off) = ih;
+        *reinterpret_cast<uint32_t*>(stage + 7 * kAX + off) = il;
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (tid == 0) {
+        const uint32_t base = tc::smem_u32(stage);
+        constexpr uint32_t LBO = 128, SBO = 128 * (kAKC / 4);
+        for (int ks = 0; ks < kAKC / 8; ++ks) {
+          const uint32_t o = ks * 256;
+          const bool first = (ch == 0 && ks == 0);
+          const uint64_t xrh = tc::smem_desc(base + 0 * kAX + o, LBO, SBO);
+          const uint64_t xrl = tc::smem_desc(base + 1 * kAX + o, LBO, SBO);
+          const uint64_t xih = tc::smem_desc(base + 2 * kAX + o, LBO, SBO);
+          const uint64_t xil = tc::smem_desc(base + 3 * kAX + o, LBO, SBO);
+          const uint64_t wrh = tc::smem_desc(base + 4 * kAX + o, LBO, SBO);
+          const uint64_t wrl = tc::smem_desc(base + 5 * kAX + o, LBO, SBO);
+          const uint64_t wih = tc::smem_desc(base + 6 * kAX + o, LBO, SBO);
+          const uint64_t wil = tc::smem_desc(base + 7 * kAX + o, LBO, SBO);
+          // A += Xr Wr^T + Xi Wi^T
+          tc::mma_tf32(accA, xrh, wrh, idesc, !first);
+          tc::mma_tf32(accA, xrh, wrl, idesc, true);
+          tc::mma_tf32(accA, xrl, wrh, idesc, true);
+          tc::mma_tf32(accA, xih, wih, idesc, true);
+          tc::mma_tf32(accA, xih, wil, idesc, true);
+          tc::mma_tf32(accA, xil, wih, idesc, true);
+          // Bm += Xi Wr^T
+          tc::mma_tf32(accB, xih, wrh, idesc, !first);
+          tc::mma_tf32(accB, xih, wrl, idesc, true);
+          tc::mma_tf32(accB, xil, wrh, idesc, true);
+          // Cm += Xr Wi^T
+          tc::mma_tf32(accC, xrh, wih, idesc, !first);
+          tc::mma_tf32(accC, xrh, wil, idesc, true);
+          tc::mma_tf32(accC, xrl, wih, idesc, true);
+        }
+        tc::mma_commit(&mbar[st]);
+      }
+      pending[st] = true;
+    }
+    for (int s2 = 0; s2 < 2; ++s2) {
+      if (pending[s2] && ok) ok = tc::mbar_wait(&mbar[s2], parity[s2], kWaitIter);
+      if (pending[s2]) {
+        parity[s2] ^= 1u;
+        pending[s2] = false;
+      }
+    }
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    tc::fence_after_sync();
+    // epilogue: cell r0 + tid, block b0 + j, columns j*S .. j*S + S - 1
+    const int r = r0 + tid;
+    const int j = (r / B) - b0;
+    const bool mine = r < R;
+    const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
+    for (int cb = 0; cb < NP; cb += 8) {
+      float a[8], bm[8], cm[8];
+      tc::tmem_ld8(accA + lanebase + cb, a);
+      tc::tmem_ld8(accB + lanebase + cb, bm);
+      tc::tmem_ld8(accC + lanebase + cb, cm);
+      if (mine) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int s = cb + u - j * S;
+          if (s >= 0 && s < S) {
+            const float re = a[u], im = bm[u] - cm[u];
+            out[((size_t)s * K + k) * R + r] = fmaf(re, re, im * im);
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(&status->timeout, 1u);
+    for (int s2 = 0; s2 < 2; ++s2)
+      if (pending[s2]) tc::mbar_wait(&mbar[s2], parity[s2], kWaitIter);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
 }  // namespace
 
 cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int T, int B,
@@ -201,6 +382,31 @@ cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, 
   long long blocks = ntiles < 152 ? ntiles : 152;   // one CTA per SM (TMEM and shared memory)
   covariance_tc_kernel<<<(unsigned)blocks, kTcThreads, smem, s>>>(dop, cov, C, K, R, T, B, NB, G,
                                                                     ntiles, status);
+  return cudaGetLastError();
+}
+
+bool apply_tc_supported(int B, int S) {
+  const bool tiles = (B <= 128 && 128 % B == 0) || (B % 128 == 0);
+  if (!tiles) return false;
+  const int N = (B < 128 ? 128 / B : 1) * S;
+  return (N + 15) / 16 * 16 <= 128;
+}
+
+cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, int C, int K, int R,
+                            int T, int B, int S, DeviceStatus* status, cudaStream_t s) {
+  const int NB = R / B;
+  if (NB == 0) return cudaSuccess;
+  if (!apply_tc_supported(B, S) || C * T > 128) return cudaErrorInvalidValue;
+  const int N = (B < 128 ? 128 / B : 1) * S;
+  const int NP = (N + 15) / 16 * 16;
+  const long long ntiles = (long long)K * ((R + 127) / 128);
+  const size_t smem = 2 * (size_t)kAStage;
+  static int set_bytes[64] = {0};
+  cudaError_t e = ensure_smem(apply_tc_kernel, smem, set_bytes);
+  if (e != cudaSuccess) return e;
+  long long blocks = ntiles < 152 ? ntiles : 152;
+  apply_tc_kernel<<<(unsigned)blocks, kTcThreads, smem, s>>>(dop, wts, out, C, K, R, T, B, S, NB, NP,
+                                                               ntiles, status);
   return cudaGetLastError();
 }
 

@@ -204,7 +204,11 @@ stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts, cuda
 stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts, float* out,
                      cudaStream_t st) {
   const stap_dims& d = c.d;
-  (void)p;
+  if (p->opt.precision == STAP_PREC_TF32X3 && stap::apply_tc_supported(d.training_block, d.n_steering))
+    return check_launch(stap::launch_apply_tc(static_cast<const float2*>(dop),
+                                              static_cast<const float2*>(wts), out, d.n_chan,
+                                              d.n_dop, d.n_range, d.tdof, d.training_block,
+                                              d.n_steering, p->status(), st));
   return check_launch(stap::launch_apply(static_cast<const float2*>(dop),
                                          static_cast<const float2*>(wts), out, d.n_chan, d.n_dop,
                                          d.n_range, d.tdof, d.training_block, d.n_steering, st));

@@ -39,6 +39,12 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
 cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int T, int B,
                                  DeviceStatus* status, cudaStream_t s);
 
+// Apply from 3xTF32 tensor-core products; needs B | 128 or 128 | B and at most
+// 128 steering columns per 128-cell tile (apply_tc_supported).
+bool apply_tc_supported(int B, int S);
+cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, int C, int K, int R,
+                            int T, int B, int S, DeviceStatus* status, cudaStream_t s);
+
 // FP64 loading, Cholesky, solves, refinement and scaling for nsys systems.
 // cov [nsys][D][D] c128 -> wts [nsys][S][D] c64; steer [S][D] c128.  If
 // sep_g [T] and sep_a [S][C] are given, steer[s] = sep_g (x) sep_a[s] and the

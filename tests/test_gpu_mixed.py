@@ -56,3 +56,28 @@ def test_mixed_run_cpi_end_to_end(spec):
     e_cell, e_norm = power_errors(out, ref)
     print(f"{spec.dims()}: mixed max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
     assert e_norm <= 1e-3 * growth(spec), e_norm
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=IDS)
+def test_mixed_apply_parity(spec):
+    """Tensor-core apply (where the tile shape allows it; the FP32 apply
+    otherwise) against the oracle on the same complex64 inputs: every cell
+    within 2|y| g + g^2 + 2 u P with g = (2 D + 8) u sum |w||x| (3xTF32
+    products, about 3 * 2^-22 each, plus FP32 accumulation of 2 D terms)."""
+    from _parity import gather
+    d = oracle.Dims(*spec.dims())
+    dop = oracle.doppler(d, synth.make_cube(spec))
+    w, _, _ = oracle.weights(d, oracle.covariance(d, dop))
+    dop64, w64 = dop.astype(np.complex64), w.astype(np.complex64)
+    ref = oracle.apply(d, dop64, w64)
+    plan = _plan(spec)
+    out = to_np(plan.apply(torch.from_numpy(dop64).cuda(), torch.from_numpy(w64).cuda()))
+    assert plan.status() == (stap.STAP_OK, 0)
+    x = gather(dop64.astype(np.complex128), spec.tdof)
+    wb = np.repeat(w64.astype(np.complex128), spec.training_block, axis=1)
+    y = np.einsum("krsd,krd->skr", wb.conj(), x)
+    mag = np.einsum("krsd,krd->skr", np.abs(wb), np.abs(x))
+    g = (2 * spec.D + 8) * EPS32 * mag
+    bound = 2 * np.abs(y) * g + g * g + 2 * EPS32 * np.abs(y) ** 2
+    viol = np.abs(out - ref) > bound
+    assert not viol.any(), (int(viol.sum()), float(np.max(np.abs(out - ref) - bound)))
