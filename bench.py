@@ -140,6 +140,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def aggregate(local_ms, local_cells, world, device):
+    """Whole-job throughput: every rank processed ``local_cells`` (weak scaling)
+    in ``local_ms``; the job took the slowest rank's time.  Returns
+    (max time over ranks in ms, all ranks' cells per second)."""
+    import torch
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * local_cells / (total_ms * 1e-3)
+
+
 def time_steps(fn, steps, flush, stream):
     """Per-step device time (ms) with CUDA events, L2 flushed before each step."""
     import torch
@@ -196,6 +210,7 @@ def run_gpu(args):
         cube_h = cube.cpu().numpy()
     plan = stap.Plan(spec.dims(), device=dev)
     out = torch.empty((S, K, R), dtype=torch.float32, device=dev)
+    tuning = plan.autotune(cube, out)          # launch shapes picked on the device, untimed
     flushbuf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -222,14 +237,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
     cells = K * R
-    value = world * cells * args.steps / (total_ms * 1e-3)
+    total_ms, value = aggregate(sum(times), cells * args.steps, world, dev)
+    ms_per_step = total_ms / args.steps
 
     # ---- per-kernel breakdown (same kernels and launch configuration) ----
     dop = plan.doppler(cube)
@@ -274,6 +284,35 @@ def run_gpu(args):
                 "peak_src": "FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (unit count and max clock)"}
     roofline["traffic"] = SOLVE_TRAFFIC.get(kernel_hash())
 
+    # ---- the mixed-precision path (tensor-core contractions) on the same CPI ----
+    mplan = stap.Plan(spec.dims(), device=dev, precision=stap.STAP_PREC_TF32X3)
+    mout = torch.empty_like(out)
+    mtuning = mplan.autotune(cube, mout)
+    for _ in range(args.warmup):
+        flush()
+        mplan.run_cpi(cube, mout)
+    torch.cuda.synchronize()
+    mtimes = time_steps(lambda: mplan.run_cpi(cube, mout), args.steps, flush, stream)
+    mdop = mplan.doppler(cube)
+    mcov = mplan.covariance(mdop)
+    mwts = mplan.solve_weights(mcov)
+    mixed = {
+        "value": world * cells * args.steps / (sum(mtimes) * 1e-3),
+        "ms_per_step": sum(mtimes) / args.steps,
+        "precision": "3xTF32 tensor-core covariance and apply (tcgen05), FP64 solve",
+        "tuning": mtuning,
+        "kernels_ms": {
+            "doppler": statistics.mean(time_steps(lambda: mplan.doppler(cube, mdop), reps, flush, stream)),
+            "covariance": statistics.mean(time_steps(lambda: mplan.covariance(mdop, mcov), reps, flush, stream)),
+            "solve": statistics.mean(time_steps(lambda: mplan.solve_weights(mcov, mwts), reps, flush, stream)),
+            "apply": statistics.mean(time_steps(lambda: mplan.apply(mdop, mwts, mout), reps, flush, stream)),
+        },
+    }
+    code, failed = mplan.status()
+    if code != stap.STAP_OK:
+        raise RuntimeError(f"mixed path: device status {code} ({failed} failed systems)")
+    mplan.close()
+
     # ---- end to end through the public API from pinned host buffers ----
     cube_pin = torch.from_numpy(cube_h).pin_memory()
     out_pin = torch.empty((S, K, R), dtype=torch.float32).pin_memory()
@@ -289,14 +328,17 @@ def run_gpu(args):
     e2e_ms = statistics.mean(time_steps(e2e_step, reps, flush, stream))
     e2e_val = world * cells / (e2e_ms * 1e-3)
 
+    cfg = workload_config(spec)
+    cfg["tuning"] = tuning
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": workload_config(spec),
+        "config": cfg,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": cube_h.nbytes,
                 "d2h_bytes_per_step": S * K * R * 4, "ms_per_step": e2e_ms},
         "gpu_launches": 4 * args.steps,
+        "mixed": mixed,
         "roofline": roofline,
         "kernels": kernels,
         "clocks": clk.summary(),
@@ -369,7 +411,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["standard", "mixed", "large"], default="standard",
+    ap.add_argument("--workload", choices=["standard", "mixed", "mixed_small", "large"], default="standard",
                     help="standard is the benchmark workload; the others are for inspection")
     args = ap.parse_args()
     global NAME

@@ -197,6 +197,32 @@ stap_status stap_plan_batch_bytes(stap_plan plan, size_t* all_concurrent_bytes);
 stap_status stap_run_cpi_noalloc(const stap_dims* dims, const stap_options* opt, void* cuda_stream,
                                  const void* cube_c64, float* out, int64_t* n_failed_systems);
 
+/* Number of launch choices per CPI kept by the autotuner. */
+#define STAP_TUNING_LEN 6
+
+/* Autotune the launch configuration of every distinct CPI shape of the plan
+ * (C, P, K, T, B, S; CPIs that differ only in R share one tuning): for each
+ * step in turn it times candidate tile shapes and schedules on the device, on
+ * the caller's cubes and output buffers, `reps` runs each (reps < 1 means 3),
+ * and keeps the fastest.  Candidates: range cells per Doppler CTA (8/16/32);
+ * Doppler bins per covariance CTA (plain precision); lanes per system and
+ * warps per CTA of the D <= 32 solve, lanes per right-hand side of the larger
+ * solve; register-resident or general FP32 apply.  Every candidate computes
+ * the same result except that the two FP32 apply kernels sum in a different
+ * order.  Needs the run workspace; synchronises the plan's stream; overwrites
+ * outs; clears the device status; drops a captured batch graph. */
+stap_status stap_plan_autotune(stap_plan plan, const void* const* cubes, float* const* outs,
+                               int32_t reps);
+
+/* The launch choices of CPI `cpi` as STAP_TUNING_LEN integers (0 = built-in
+ * heuristic): Doppler cells per CTA, covariance bins per CTA, solve lanes per
+ * system, solve warps per CTA, large-solve lanes per right-hand side, apply
+ * kernel (1 register-resident, 2 general).  set_tuning installs saved choices
+ * (values 0..64; a choice that does not fit a launch falls back to the
+ * heuristic). */
+stap_status stap_plan_get_tuning(stap_plan plan, int32_t cpi, int32_t* choices);
+stap_status stap_plan_set_tuning(stap_plan plan, int32_t cpi, const int32_t* choices);
+
 /* Wait for the plan's stream, then report and clear the device status.
  * *n_failed_systems (if not NULL) = covariances found not positive definite
  * since the last call; returns STAP_ERR_NOT_POSDEF if that is > 0,

@@ -161,13 +161,13 @@ cudaError_t launch_apply_reg(const float2* dop, const float2* wts, float* out, i
 }  // namespace
 
 cudaError_t launch_apply(const float2* dop, const float2* wts, float* out, int C, int K, int R,
-                         int T, int B, int S, cudaStream_t s) {
+                         int T, int B, int S, cudaStream_t s, const Tune& tn) {
   const int D = C * T;
   const int NB = R / B;
   if (NB == 0) return cudaSuccess;
   // register-resident form: even D <= 24, even B (cell pairs never straddle a
   // block and 16-byte loads stay aligned), weights of a CTA within 160 KB
-  if (D % 2 == 0 && D <= 24 && B % 2 == 0 &&
+  if (tn.apply_kind != 2 && D % 2 == 0 && D <= 24 && B % 2 == 0 &&
       (size_t)(kRegCells / B + 2) * S * D * sizeof(float2) <= 160 * 1024) {
     switch (D) {
       case 2: return launch_apply_reg<2>(dop, wts, out, C, K, R, T, B, S, s);

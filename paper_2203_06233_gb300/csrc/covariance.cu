@@ -251,7 +251,7 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
 }  // namespace
 
 cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K, int R, int T,
-                                   int B, cudaStream_t s) {
+                                   int B, cudaStream_t s, const Tune& tn) {
   const int D = C * T;
   const int E = D * (D + 1) / 2;
   const int NB = R / B;
@@ -270,6 +270,8 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
     };
     int KT = K < 16 ? K : 16;  // K is a power of two, so KT divides it
     while (KT > 1 && pair_smem(KT, B) > kPairBudget) KT >>= 1;
+    if (tn.cov_kt > 0 && tn.cov_kt <= K && K % tn.cov_kt == 0 && pair_smem(tn.cov_kt, B) <= kPairBudget)
+      KT = tn.cov_kt;
     int CB = B;
     while (CB > 32 && pair_smem(KT, CB) > kPairBudget) CB = (CB + 1) / 2;
     if (pair_smem(KT, CB) <= kPairBudget) {

@@ -119,16 +119,13 @@ doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
   }
 }
 
-template <int LOGK>
-cudaError_t launch_logk(const float2* cube, float2* dop, const float* win, const float2* tw, int C,
-                        int P, int R, cudaStream_t s) {
+template <int LOGK, int TR>
+cudaError_t launch_logk_tr(const float2* cube, float2* dop, const float* win, const float2* tw, int C,
+                           int P, int R, cudaStream_t s) {
   constexpr int K = 1 << LOGK;
   constexpr int N1 = 1 << ((LOGK + 1) / 2);
-  // range cells per CTA: 256-thread CTAs (TR * N1) of at most 32 columns, so
-  // that several CTAs fit per SM; a warp still covers >= 64 contiguous bytes
-  // of a row (two full 32-byte sectors)
-  constexpr int TR = (N1 >= 32) ? 8 : (N1 >= 16 ? 16 : 32);
   const size_t smem = (size_t)K * sizeof(float2) * (1 + TR);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
   auto kern = doppler_fft_kernel<LOGK, TR>;
   static int set_bytes[64] = {0};
   cudaError_t e = ensure_smem(kern, smem, set_bytes);
@@ -138,22 +135,39 @@ cudaError_t launch_logk(const float2* cube, float2* dop, const float* win, const
   return cudaGetLastError();
 }
 
+// range cells per CTA: by default 256-thread CTAs (TR * N1) of at most 32
+// columns, so that several CTAs fit per SM; a warp still covers >= 64
+// contiguous bytes of a row (two full 32-byte sectors)
+template <int LOGK>
+cudaError_t launch_logk(const float2* cube, float2* dop, const float* win, const float2* tw, int C,
+                        int P, int R, cudaStream_t s, int tr) {
+  constexpr int N1 = 1 << ((LOGK + 1) / 2);
+  if (tr == 0) tr = (N1 >= 32) ? 8 : (N1 >= 16 ? 16 : 32);
+  switch (tr) {
+    case 8: return launch_logk_tr<LOGK, 8>(cube, dop, win, tw, C, P, R, s);
+    case 16: return launch_logk_tr<LOGK, 16>(cube, dop, win, tw, C, P, R, s);
+    case 32: return launch_logk_tr<LOGK, 32>(cube, dop, win, tw, C, P, R, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_doppler(const float2* cube, float2* dop, const float* win, const float2* tw,
-                           int C, int P, int K, int R, cudaStream_t s) {
+                           int C, int P, int K, int R, cudaStream_t s, const Tune& t) {
+  const int tr = t.dop_tr;
   switch (ilog2c(K)) {
-    case 0: return launch_logk<0>(cube, dop, win, tw, C, P, R, s);
-    case 1: return launch_logk<1>(cube, dop, win, tw, C, P, R, s);
-    case 2: return launch_logk<2>(cube, dop, win, tw, C, P, R, s);
-    case 3: return launch_logk<3>(cube, dop, win, tw, C, P, R, s);
-    case 4: return launch_logk<4>(cube, dop, win, tw, C, P, R, s);
-    case 5: return launch_logk<5>(cube, dop, win, tw, C, P, R, s);
-    case 6: return launch_logk<6>(cube, dop, win, tw, C, P, R, s);
-    case 7: return launch_logk<7>(cube, dop, win, tw, C, P, R, s);
-    case 8: return launch_logk<8>(cube, dop, win, tw, C, P, R, s);
-    case 9: return launch_logk<9>(cube, dop, win, tw, C, P, R, s);
-    case 10: return launch_logk<10>(cube, dop, win, tw, C, P, R, s);
+    case 0: return launch_logk<0>(cube, dop, win, tw, C, P, R, s, tr);
+    case 1: return launch_logk<1>(cube, dop, win, tw, C, P, R, s, tr);
+    case 2: return launch_logk<2>(cube, dop, win, tw, C, P, R, s, tr);
+    case 3: return launch_logk<3>(cube, dop, win, tw, C, P, R, s, tr);
+    case 4: return launch_logk<4>(cube, dop, win, tw, C, P, R, s, tr);
+    case 5: return launch_logk<5>(cube, dop, win, tw, C, P, R, s, tr);
+    case 6: return launch_logk<6>(cube, dop, win, tw, C, P, R, s, tr);
+    case 7: return launch_logk<7>(cube, dop, win, tw, C, P, R, s, tr);
+    case 8: return launch_logk<8>(cube, dop, win, tw, C, P, R, s, tr);
+    case 9: return launch_logk<9>(cube, dop, win, tw, C, P, R, s, tr);
+    case 10: return launch_logk<10>(cube, dop, win, tw, C, P, R, s, tr);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -25,7 +25,8 @@
 namespace stap {
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;              // 8 warps stage; warps 0-3 own the TMEM lanes
+constexpr int kUnroll = 8;                    // staging loads in flight per lane
 constexpr int kKC = 32;                       // cells per chunk (K of one stage)
 constexpr int kTile = 128 * kKC * 4;          // one 128 x 32 TF32 operand tile (16 KB)
 constexpr int kStage = 4 * kTile;             // Xr hi, Xr lo, Xi hi, Xi lo (64 KB)
@@ -74,30 +75,49 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
       }
       ok = __syncthreads_and(ok);
       if (!ok) break;
-      // stage cells c0 .. c0+31: one core matrix (8 rows x 4 cells) per warp pass
+      // stage cells c0 .. c0+31: one core matrix (8 rows x 4 cells) per warp
+      // pass, kUnroll loads in flight per lane before the conversions
       const int c0 = ch * kKC;
-      for (int cmi = warp; cmi < (rows + 7) / 8 * (kKC / 4); cmi += kTcThreads / 32) {
-        const int pg = cmi / (kKC / 4), jg = cmi - pg * (kKC / 4);
-        const int p = pg * 8 + (lane >> 2), j = jg * 4 + (lane & 3);
-        float2 x = make_float2(0.f, 0.f);
-        if (p < rows && c0 + j < B) {
-          const int g = p / D, i = p - g * D;
-          const long long sys = sys0 + g;
-          if (sys < nsys) {
-            const int k = (int)(sys / NB), b = (int)(sys - (long long)k * NB);
-            const int t = i / C, c = i - t * C;
-            const int kk = wrap_bin(k + t - T / 2, K);
-            x = __ldg(dop + ((size_t)c * K + kk) * R + (size_t)b * B + c0 + j);
+      const int ncm = (rows + 7) / 8 * (kKC / 4);
+      constexpr int NWS = kTcThreads / 32;
+      for (int cb0 = warp; cb0 < ncm; cb0 += NWS * kUnroll) {
+        float2 xv[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int cmi = cb0 + u * NWS;
+          xv[u] = make_float2(0.f, 0.f);
+          if (cmi < ncm) {
+            const int pg = cmi / (kKC / 4), jg = cmi - pg * (kKC / 4);
+            const int p = pg * 8 + (lane >> 2), j = jg * 4 + (lane & 3);
+            if (p < rows && c0 + j < B) {
+              const int g = p / D, i = p - g * D;
+              const long long sys = sys0 + g;
+              if (sys < nsys) {
+                const int k = (int)(sys / NB), b = (int)(sys - (long long)k * NB);
+                const int t = i / C, c = i - t * C;
+                const int kk = wrap_bin(k + t - T / 2, K);
+                xv[u] = __ldg(dop + ((size_t)c * K + kk) * R + (size_t)b * B + c0 + j);
+              }
+            }
           }
         }
-        const uint32_t rh = tc::to_tf32(x.x), ih = tc::to_tf32(x.y);
-        const uint32_t rl = tc::to_tf32(x.x - __uint_as_float(rh));
-        const uint32_t il = tc::to_tf32(x.y - __uint_as_float(ih));
-        const int off = tc::cm_offset(p, j, kKC);
-        *reinterpret_cast<uint32_t*>(stage + 0 * kTile + off) = rh;
-        *reinterpret_cast<uint32_t*>(stage + 1 * kTile + off) = rl;
-        *reinterpret_cast<uint32_t*>(stage + 2 * kTile + off) = ih;
-        *reinterpret_cast<uint32_t*>(stage + 3 * kTile + off) = il;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int cmi = cb0 + u * NWS;
+          if (cmi < ncm) {
+            const int pg = cmi / (kKC / 4), jg = cmi - pg * (kKC / 4);
+            const int p = pg * 8 + (lane >> 2), j = jg * 4 + (lane & 3);
+            const float2 x = xv[u];
+            const uint32_t rh = tc::to_tf32(x.x), ih = tc::to_tf32(x.y);
+            const uint32_t rl = tc::to_tf32(x.x - __uint_as_float(rh));
+            const uint32_t il = tc::to_tf32(x.y - __uint_as_float(ih));
+            const int off = tc::cm_offset(p, j, kKC);
+            *reinterpret_cast<uint32_t*>(stage + 0 * kTile + off) = rh;
+            *reinterpret_cast<uint32_t*>(stage + 1 * kTile + off) = rl;
+            *reinterpret_cast<uint32_t*>(stage + 2 * kTile + off) = ih;
+            *reinterpret_cast<uint32_t*>(stage + 3 * kTile + off) = il;
+          }
+        }
       }
       tc::fence_proxy_async();
       tc::fence_before_sync();
@@ -143,14 +163,14 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
     ok = __syncthreads_and(ok);
     if (!ok) break;
     tc::fence_after_sync();
-    // epilogue: thread tid owns row tid of the tile = row i of system g
+    // epilogue (warps 0-3): thread tid owns row tid of the tile = row i of system g
     const int g = tid / D, i = tid - g * D;
     const long long sys = sys0 + g;
-    const bool mine = tid < rows && sys < nsys;
+    const bool mine = tid < 128 && tid < rows && sys < nsys;
     const double invB = 1.0 / (double)B;
     double2* out = cov + (size_t)(mine ? sys : 0) * D * D;
     const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
-    for (int cb = 0; cb < rows; cb += 8) {        // columns in blocks of 8 (warp-collective)
+    for (int cb = 0; cb < rows && warp < 4; cb += 8) {   // columns in blocks of 8 (warp-collective)
       float a[8], bm[8], cm[8];
       tc::tmem_ld8(accA + lanebase + cb, a);
       tc::tmem_ld8(accB + lanebase + cb, bm);
@@ -243,43 +263,52 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
       ok = __syncthreads_and(ok);
       if (!ok) break;
       const int d0 = ch * kAKC;
-      // X tile: rows = cells, K = snapshot entries d0 .. d0+15
-      for (int cmi = warp; cmi < 16 * (kAKC / 4); cmi += kTcThreads / 32) {
-        const int pg = cmi / (kAKC / 4), jg = cmi - pg * (kAKC / 4);
-        const int m = pg * 8 + (lane >> 2), dd = jg * 4 + (lane & 3);
-        const int d = d0 + dd, r = r0 + m;
-        float2 x = make_float2(0.f, 0.f);
-        if (d < D && r < R) {
-          const int t = d / C, c = d - t * C;
-          const int kk = wrap_bin(k + t - T / 2, K);
-          x = __ldg(dop + ((size_t)c * K + kk) * R + r);
+      // X tile (rows = cells) and W tile (rows n = j*S + s of block b0 + j),
+      // K = snapshot entries d0 .. d0+15; kUnroll loads in flight per lane
+      constexpr int NWS = kTcThreads / 32;
+      const int ncx = 16 * (kAKC / 4), ncw = (NP / 8) * (kAKC / 4), ncm = ncx + ncw;
+      for (int cb0 = warp; cb0 < ncm; cb0 += NWS * kUnroll) {
+        float2 xv[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int cmi = cb0 + u * NWS;
+          xv[u] = make_float2(0.f, 0.f);
+          if (cmi < ncx) {
+            const int pg = cmi / (kAKC / 4), jg = cmi - pg * (kAKC / 4);
+            const int m = pg * 8 + (lane >> 2), d = d0 + jg * 4 + (lane & 3), r = r0 + m;
+            if (d < D && r < R) {
+              const int t = d / C, c = d - t * C;
+              const int kk = wrap_bin(k + t - T / 2, K);
+              xv[u] = __ldg(dop + ((size_t)c * K + kk) * R + r);
+            }
+          } else if (cmi < ncm) {
+            const int cw = cmi - ncx;
+            const int pg = cw / (kAKC / 4), jg = cw - pg * (kAKC / 4);
+            const int n = pg * 8 + (lane >> 2), d = d0 + jg * 4 + (lane & 3);
+            const int j = n / S, s = n - j * S;
+            if (n < N && d < D && b0 + j < NB)
+              xv[u] = __ldg(wts + ((((size_t)k * NB + b0 + j) * S + s) * D + d));
+          }
         }
-        const uint32_t rh = tc::to_tf32(x.x), ih = tc::to_tf32(x.y);
-        const uint32_t rl = tc::to_tf32(x.x - __uint_as_float(rh));
-        const uint32_t il = tc::to_tf32(x.y - __uint_as_float(ih));
-        const int off = tc::cm_offset(m, dd, kAKC);
-        *reinterpret_cast<uint32_t*>(stage + 0 * kAX + off) = rh;
-        *reinterpret_cast<uint32_t*>(stage + 1 * kAX + off) = rl;
-        *reinterpret_cast<uint32_t*>(stage + 2 * kAX + off) = ih;
-        *reinterpret_cast<uint32_t*>(stage + 3 * kAX + off) = il;
-      }
-      // W tile: rows n = j*S + s (block b0 + j), K = snapshot entries
-      for (int cmi = warp; cmi < (NP / 8) * (kAKC / 4); cmi += kTcThreads / 32) {
-        const int pg = cmi / (kAKC / 4), jg = cmi - pg * (kAKC / 4);
-        const int n = pg * 8 + (lane >> 2), dd = jg * 4 + (lane & 3);
-        const int d = d0 + dd;
-        const int j = n / S, s = n - j * S;
-        float2 w = make_float2(0.f, 0.f);
-        if (n < N && d < D && b0 + j < NB)
-          w = __ldg(wts + ((((size_t)k * NB + b0 + j) * S + s) * D + d));
-        const uint32_t rh = tc::to_tf32(w.x), ih = tc::to_tf32(w.y);
-        const uint32_t rl = tc::to_tf32(w.x - __uint_as_float(rh));
-        const uint32_t il = tc::to_tf32(w.y - __uint_as_float(ih));
-        const int off = tc::cm_offset(n, dd, kAKC);
-        *reinterpret_cast<uint32_t*>(stage + 4 * kAX + off) = rh;
-        *reinterpret_cast<uint32_t*>(stage + 5 * kAX + off) = rl;
-        *reinterpret_cast<uint32_t*>(stage + 6 * kAX + off) = ih;
-        *reinterpret_cast<uint32_t*>(stage + 7 * kAX + off) = il;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int cmi = cb0 + u * NWS;
+          if (cmi < ncm) {
+            const bool isx = cmi < ncx;
+            const int cl = isx ? cmi : cmi - ncx;
+            const int pg = cl / (kAKC / 4), jg = cl - pg * (kAKC / 4);
+            const int row = pg * 8 + (lane >> 2), dd = jg * 4 + (lane & 3);
+            const float2 x = xv[u];
+            const uint32_t rh = tc::to_tf32(x.x), ih = tc::to_tf32(x.y);
+            const uint32_t rl = tc::to_tf32(x.x - __uint_as_float(rh));
+            const uint32_t il = tc::to_tf32(x.y - __uint_as_float(ih));
+            uint8_t* t0 = stage + (isx ? 0 : 4 * kAX) + tc::cm_offset(row, dd, kAKC);
+            *reinterpret_cast<uint32_t*>(t0 + 0 * kAX) = rh;
+            *reinterpret_cast<uint32_t*>(t0 + 1 * kAX) = rl;
+            *reinterpret_cast<uint32_t*>(t0 + 2 * kAX) = ih;
+            *reinterpret_cast<uint32_t*>(t0 + 3 * kAX) = il;
+          }
+        }
       }
       tc::fence_proxy_async();
       tc::fence_before_sync();
@@ -329,12 +358,12 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
     ok = __syncthreads_and(ok);
     if (!ok) break;
     tc::fence_after_sync();
-    // epilogue: cell r0 + tid, block b0 + j, columns j*S .. j*S + S - 1
+    // epilogue (warps 0-3): cell r0 + tid, block b0 + j, columns j*S .. j*S + S - 1
     const int r = r0 + tid;
     const int j = (r / B) - b0;
-    const bool mine = r < R;
+    const bool mine = tid < 128 && r < R;
     const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
-    for (int cb = 0; cb < NP; cb += 8) {
+    for (int cb = 0; cb < NP && warp < 4; cb += 8) {
       float a[8], bm[8], cm[8];
       tc::tmem_ld8(accA + lanebase + cb, a);
       tc::tmem_ld8(accB + lanebase + cb, bm);

@@ -29,6 +29,7 @@ struct Cpi {
   // spatial factors a [S][C][2]; cleared when the caller replaces the table
   bool separable = false;
   std::vector<double> sep_g, sep_a;
+  stap::Tune tune;              // launch choices (autotuner or defaults)
   size_t dop_elems() const { return (size_t)d.n_chan * d.n_dop * d.n_range; }
   size_t cov_elems() const { return (size_t)d.n_dop * NB * D * D; }
   size_t wts_elems() const { return (size_t)d.n_dop * NB * d.n_steering * D; }
@@ -178,7 +179,7 @@ stap_status do_doppler(stap_plan p, const Cpi& c, const void* cube, void* dop, c
   const stap_dims& d = c.d;
   return check_launch(stap::launch_doppler(
       static_cast<const float2*>(cube), static_cast<float2*>(dop), p->at<const float>(c.win_off),
-      p->at<const float2>(c.tw_off), d.n_chan, d.n_pulses, d.n_dop, d.n_range, st));
+      p->at<const float2>(c.tw_off), d.n_chan, d.n_pulses, d.n_dop, d.n_range, st, c.tune));
 }
 
 stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov, cudaStream_t st) {
@@ -189,7 +190,7 @@ stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov,
                                                    d.n_range, d.tdof, d.training_block, p->status(), st));
   return check_launch(stap::launch_covariance_fp32(static_cast<const float2*>(dop),
                                                    static_cast<double2*>(cov), d.n_chan, d.n_dop,
-                                                   d.n_range, d.tdof, d.training_block, st));
+                                                   d.n_range, d.tdof, d.training_block, st, c.tune));
 }
 
 stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts, cudaStream_t st) {
@@ -198,7 +199,7 @@ stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts, cuda
       static_cast<const double2*>(cov), static_cast<float2*>(wts),
       p->at<const double2>(c.steer_off), c.separable ? p->at<const double2>(c.g_off) : nullptr,
       c.separable ? p->at<const double2>(c.a_off) : nullptr, (long long)d.n_dop * c.NB, c.D,
-      d.n_steering, d.n_chan, p->opt.load_factor, p->opt.refine_steps, p->status(), st));
+      d.n_steering, d.n_chan, p->opt.load_factor, p->opt.refine_steps, p->status(), st, c.tune));
 }
 
 stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts, float* out,
@@ -211,7 +212,8 @@ stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts
                                               d.n_steering, p->status(), st));
   return check_launch(stap::launch_apply(static_cast<const float2*>(dop),
                                          static_cast<const float2*>(wts), out, d.n_chan, d.n_dop,
-                                         d.n_range, d.tdof, d.training_block, d.n_steering, st));
+                                         d.n_range, d.tdof, d.training_block, d.n_steering, st,
+                                         c.tune));
 }
 
 stap_status do_chain(stap_plan p, const Cpi& c, const void* cube, float* out, char* dop, char* cov,
@@ -514,6 +516,136 @@ stap_status stap_run_cpi(stap_plan p, const void* const* cubes, float* const* ou
 stap_status stap_plan_batch_bytes(stap_plan p, size_t* all_concurrent_bytes) {
   if (!p || !all_concurrent_bytes) return STAP_ERR_INVALID_ARG;
   *all_concurrent_bytes = p->batch_bytes;
+  return STAP_OK;
+}
+
+stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* const* outs,
+                               int32_t reps) {
+  if (!p || !cubes || !outs) return STAP_ERR_INVALID_ARG;
+  for (size_t i = 0; i < p->cpis.size(); ++i) {
+    if (!cubes[i] || !outs[i]) return STAP_ERR_INVALID_ARG;
+    if (!aligned16(cubes[i]) || !aligned16(outs[i])) return STAP_ERR_MISALIGNED;
+  }
+  stap_status st = ready(p, p->run_bytes);
+  if (st != STAP_OK) return st;
+  if (reps < 1) reps = 3;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return STAP_ERR_CUDA;
+  const float kNever = 3.0e38f;
+  // time `launch` (one untimed run first); kNever if it fails
+  auto timeit = [&](auto&& launch) -> float {
+    if (launch() != STAP_OK) return kNever;
+    cudaEventRecord(e0, p->stream);
+    for (int r = 0; r < reps; ++r)
+      if (launch() != STAP_OK) return kNever;
+    cudaEventRecord(e1, p->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return kNever;
+    float ms = kNever;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  auto same_key = [](const stap_dims& a, const stap_dims& b) {
+    return a.n_chan == b.n_chan && a.n_pulses == b.n_pulses && a.n_dop == b.n_dop &&
+           a.tdof == b.tdof && a.training_block == b.training_block && a.n_steering == b.n_steering;
+  };
+  std::vector<char> tuned(p->cpis.size(), 0);
+  char* dop = p->ws + p->dop_off;
+  char* cov = p->ws + p->cov_off;
+  char* wts = p->ws + p->wts_off;
+  for (size_t i = 0; i < p->cpis.size() && st == STAP_OK; ++i) {
+    if (tuned[i]) continue;
+    Cpi& c = p->cpis[i];
+    const stap_dims& d = c.d;
+    const void* cube = cubes[i];
+    float* out = outs[i];
+    stap::Tune best = c.tune;
+    auto pick = [&](auto&& set, const std::vector<int>& values, auto&& run) {
+      float bt = kNever;
+      int bv = 0;
+      for (int v : values) {
+        set(c.tune, v);
+        const float ms = timeit(run);
+        if (ms < bt) {
+          bt = ms;
+          bv = v;
+        }
+      }
+      set(c.tune, bv);
+    };
+    c.tune = best;
+    pick([](stap::Tune& t, int v) { t.dop_tr = v; }, {8, 16, 32},
+         [&] { return do_doppler(p, c, cube, dop, p->stream); });
+    if (p->opt.precision == STAP_PREC_FP32) {
+      std::vector<int> kts;
+      for (int kt = 1; kt <= 32 && kt <= d.n_dop; kt *= 2) kts.push_back(kt);
+      pick([](stap::Tune& t, int v) { t.cov_kt = v; }, kts,
+           [&] { return do_covariance(p, c, dop, cov, p->stream); });
+    }
+    if ((st = do_covariance(p, c, dop, cov, p->stream)) != STAP_OK) break;
+    if (c.D <= stap::kSmallMaxD) {
+      const int nrhs = c.separable ? d.n_chan : d.n_steering;
+      int base = 1;
+      while (base < nrhs && base < 32) base <<= 1;
+      float bt = kNever;
+      int bts = 0, bnw = 0;
+      for (int ts = base; ts <= 32; ts <<= 1)
+        for (int nw = 1; nw <= 4; ++nw) {
+          c.tune.solve_ts = ts;
+          c.tune.solve_nw = nw;
+          const float ms = timeit([&] { return do_solve(p, c, cov, wts, p->stream); });
+          if (ms < bt) {
+            bt = ms;
+            bts = ts;
+            bnw = nw;
+          }
+        }
+      c.tune.solve_ts = bts;
+      c.tune.solve_nw = bnw;
+    } else {
+      std::vector<int> lrs = {32};
+      if (c.D <= 64) lrs.insert(lrs.begin(), 16);
+      pick([](stap::Tune& t, int v) { t.solve_lr = v; }, lrs,
+           [&] { return do_solve(p, c, cov, wts, p->stream); });
+    }
+    if ((st = do_solve(p, c, cov, wts, p->stream)) != STAP_OK) break;
+    if (p->opt.precision == STAP_PREC_FP32)
+      pick([](stap::Tune& t, int v) { t.apply_kind = v; }, {1, 2},
+           [&] { return do_apply(p, c, dop, wts, out, p->stream); });
+    for (size_t j = i; j < p->cpis.size(); ++j)
+      if (!tuned[j] && same_key(p->cpis[j].d, d)) {
+        p->cpis[j].tune = c.tune;
+        tuned[j] = 1;
+      }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  drop_graph(p);
+  // the timing runs may have counted failures: start clean
+  if (cudaMemsetAsync(p->ws, 0, sizeof(DeviceStatus), p->stream) != cudaSuccess) return STAP_ERR_CUDA;
+  return st;
+}
+
+stap_status stap_plan_get_tuning(stap_plan p, int32_t cpi, int32_t* choices) {
+  if (!p || !choices || cpi < 0 || cpi >= (int32_t)p->cpis.size()) return STAP_ERR_INVALID_ARG;
+  const stap::Tune& t = p->cpis[cpi].tune;
+  const int32_t v[STAP_TUNING_LEN] = {t.dop_tr, t.cov_kt, t.solve_ts, t.solve_nw, t.solve_lr,
+                                      t.apply_kind};
+  for (int i = 0; i < STAP_TUNING_LEN; ++i) choices[i] = v[i];
+  return STAP_OK;
+}
+
+stap_status stap_plan_set_tuning(stap_plan p, int32_t cpi, const int32_t* choices) {
+  if (!p || !choices || cpi < 0 || cpi >= (int32_t)p->cpis.size()) return STAP_ERR_INVALID_ARG;
+  for (int i = 0; i < STAP_TUNING_LEN; ++i)
+    if (choices[i] < 0 || choices[i] > 64) return STAP_ERR_INVALID_ARG;
+  stap::Tune& t = p->cpis[cpi].tune;
+  t.dop_tr = choices[0];
+  t.cov_kt = choices[1];
+  t.solve_ts = choices[2];
+  t.solve_nw = choices[3];
+  t.solve_lr = choices[4];
+  t.apply_kind = choices[5];
+  drop_graph(p);
   return STAP_OK;
 }
 

@@ -548,7 +548,7 @@ int pow2ceil(int x) {
 cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
                          const double2* sep_g, const double2* sep_a, long long nsys, int D, int S,
                          int C, double load_factor, int refine_steps, DeviceStatus* status,
-                         cudaStream_t s) {
+                         cudaStream_t s, const Tune& tn) {
   if (nsys <= 0) return cudaSuccess;
   if (D < 1 || D > kMaxD || S < 1) return cudaErrorInvalidValue;
   const bool sep = sep_g != nullptr && sep_a != nullptr && C >= 1 && C <= 32 && D % C == 0;
@@ -556,7 +556,8 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
     if (D > 32 * kBigRPL) return cudaErrorInvalidValue;
     // 16 lanes per right-hand side (two per warp) up to D = 64 with 4 warps
     // (several CTAs per SM); above that 32 lanes and 8 warps sharing one factor
-    const int LR = D <= 16 * kBigRPL ? 16 : 32;
+    int LR = D <= 16 * kBigRPL ? 16 : 32;
+    if (tn.solve_lr == 32 || (tn.solve_lr == 16 && D <= 16 * kBigRPL)) LR = tn.solve_lr;
     const int NT = LR == 16 ? 128 : 256;
     const size_t Dp = (size_t)D * (D + 1) / 2;
     const size_t ng = NT / LR;
@@ -588,8 +589,11 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
     return ((size_t)G * Dp + 2 * (size_t)D * 32) * sizeof(double2) + (size_t)G * D * sizeof(double);
   };
   while (TS < 32 && warp_bytes(TS) * 4 > kBudget) TS <<= 1;
+  if (tn.solve_ts >= TS && tn.solve_ts <= 32 && (tn.solve_ts & (tn.solve_ts - 1)) == 0)
+    TS = tn.solve_ts;
   int nw = 4;
   while (nw > 1 && warp_bytes(TS) * nw > kBudget) --nw;
+  if (tn.solve_nw >= 1 && tn.solve_nw <= nw) nw = tn.solve_nw;
   const size_t smem = warp_bytes(TS) * nw;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   const int G = 32 / TS;

@@ -22,18 +22,30 @@ constexpr int kMaxD = 128;       // largest snapshot length the solve kernels ha
 constexpr int kSmallMaxD = 32;   // above this, one system per CTA (lanes over rows)
 constexpr int kMaxLogK = 10;     // K <= 1024
 
+// Launch choices the autotuner can make for one CPI shape (0 = the built-in
+// heuristic).  Every choice computes the same result, except that the two FP32
+// apply kernels accumulate in a different order.
+struct Tune {
+  int dop_tr = 0;      // range cells per Doppler CTA: 8, 16 or 32
+  int cov_kt = 0;      // Doppler bins per covariance CTA (bin-pair kernel), a divisor of K
+  int solve_ts = 0;    // D <= 32 solve: lanes per system (power of two, >= one per RHS)
+  int solve_nw = 0;    // D <= 32 solve: warps per CTA, 1..4
+  int solve_lr = 0;    // D > 32 solve: lanes per right-hand side, 16 (D <= 64) or 32
+  int apply_kind = 0;  // FP32 apply: 1 register-resident, 2 general
+};
+
 // ---------------------------------------------------------------- launchers --
 // Each returns cudaGetLastError() after its launches.
 
 // Hann-windowed DFT over pulses via a two-pass in-register FFT.
 // cube [C][P][R] c64 -> dop [C][K][R] c64; win[P] float; tw[K] = exp(-2 pi i m/K).
 cudaError_t launch_doppler(const float2* cube, float2* dop, const float* win, const float2* tw,
-                           int C, int P, int K, int R, cudaStream_t s);
+                           int C, int P, int K, int R, cudaStream_t s, const Tune& t = Tune());
 
 // Covariance per (k, block) from the Doppler cube, accumulated error-free in
 // FP32 pairs; written as FP64 complex [K][NB][D][D] (full Hermitian).
 cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K, int R, int T,
-                                   int B, cudaStream_t s);
+                                   int B, cudaStream_t s, const Tune& t = Tune());
 
 // Same covariance from 3xTF32 tensor-core products (tcgen05), FP32 accumulation.
 cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int T, int B,
@@ -52,11 +64,11 @@ cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, in
 cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
                          const double2* sep_g, const double2* sep_a, long long nsys, int D, int S,
                          int C, double load_factor, int refine_steps, DeviceStatus* status,
-                         cudaStream_t s);
+                         cudaStream_t s, const Tune& t = Tune());
 
 // out[s][k][r] = |w^H x|^2; dop [C][K][R] c64, wts [K][NB][S][D] c64, out [S][K][R] f32.
 cudaError_t launch_apply(const float2* dop, const float2* wts, float* out, int C, int K, int R,
-                         int T, int B, int S, cudaStream_t s);
+                         int T, int B, int S, cudaStream_t s, const Tune& t = Tune());
 
 // ------------------------------------------------------------ device helpers --
 

@@ -36,8 +36,11 @@ EXPORTED = (
     "stap_plan_set_workspace", "stap_plan_set_stream", "stap_plan_set_steering",
     "stap_plan_destroy", "stap_doppler", "stap_covariance", "stap_solve_weights", "stap_apply",
     "stap_run_cpi", "stap_get_status", "stap_status_string", "stap_abi_version",
-    "stap_run_cpi_noalloc", "stap_plan_batch_bytes",
+    "stap_run_cpi_noalloc", "stap_plan_batch_bytes", "stap_plan_autotune", "stap_plan_get_tuning",
+    "stap_plan_set_tuning",
 )
+
+STAP_TUNING_LEN = 6
 
 # size of the library-owned scratch array used by stap_run_cpi_noalloc
 STAP_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -94,6 +97,9 @@ def lib():
             L.stap_status_string.restype = ctypes.c_char_p
             L.stap_abi_version.argtypes = []
             L.stap_plan_batch_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+            L.stap_plan_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32]
+            L.stap_plan_get_tuning.argtypes = [vp, i32, ctypes.POINTER(i32)]
+            L.stap_plan_set_tuning.argtypes = [vp, i32, ctypes.POINTER(i32)]
             L.stap_run_cpi_noalloc.argtypes = [ctypes.POINTER(stap_dims), ctypes.POINTER(stap_options),
                                                vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
             for f in EXPORTED:
@@ -251,6 +257,29 @@ def stap_run_cpi_noalloc(dims, cube: torch.Tensor, out: torch.Tensor, opts=None,
     return n.value if want_status else None
 
 
+def stap_plan_autotune(plan, cubes: Sequence[torch.Tensor], outs: Sequence[torch.Tensor], reps: int = 3):
+    n = len(cubes)
+    ca = (ctypes.c_void_p * n)(*[t.data_ptr() for t in cubes])
+    oa = (ctypes.c_void_p * n)(*[t.data_ptr() for t in outs])
+    _check(lib().stap_plan_autotune(plan, ca, oa, int(reps)), "stap_plan_autotune")
+
+
+def stap_plan_get_tuning(plan, cpi: int) -> List[int]:
+    a = (ctypes.c_int32 * STAP_TUNING_LEN)()
+    _check(lib().stap_plan_get_tuning(plan, int(cpi), a), "stap_plan_get_tuning")
+    return list(a)
+
+
+def stap_plan_set_tuning(plan, cpi: int, choices: Sequence[int]):
+    a = (ctypes.c_int32 * STAP_TUNING_LEN)(*[int(v) for v in choices])
+    _check(lib().stap_plan_set_tuning(plan, int(cpi), a), "stap_plan_set_tuning")
+
+
+def default_tune_cache() -> str:
+    return os.environ.get("STAP_TUNE_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "stap_gb300", "tune.json")
+
+
 def stap_abi_version() -> int:
     return lib().stap_abi_version()
 
@@ -272,6 +301,7 @@ class Plan:
         self.dims = [_dims(d) for d in dl]
         self.device = torch.device(device) if device is not None else torch.device("cuda")
         opts = stap_options(float(load_factor), int(refine_steps), int(precision))
+        self.precision, self.refine_steps = int(precision), int(refine_steps)
         with torch.cuda.device(self.device):
             self.handle, _ = stap_plan_create(self.dims, opts)
             self.step_bytes, self.run_bytes = stap_plan_workspace_sizes(self.handle)
@@ -362,6 +392,53 @@ class Plan:
         self._sync_stream()
         stap_run_cpi(self.handle, cubes, outs)
         return outs[0] if single else outs
+
+    def _tune_key(self, i: int) -> str:
+        d = self.dims[i]
+        return "C%d P%d K%d T%d B%d S%d prec%d ref%d" % (d.n_chan, d.n_pulses, d.n_dop, d.tdof,
+                                                       d.training_block, d.n_steering,
+                                                       self.precision, self.refine_steps)
+
+    def autotune(self, cubes, outs=None, cache_path: Optional[str] = None, reps: int = 3,
+                 force: bool = False) -> dict:
+        """Pick launch choices per CPI shape: from the JSON cache at ``cache_path``
+        (default ``$STAP_TUNE_CACHE`` or ``~/.cache/stap_gb300/tune.json``) when every
+        shape is there, else by timing candidates on the device
+        (``stap_plan_autotune``) and adding them to the cache.  Returns {key: choices}."""
+        import json
+        cubes = [cubes] if isinstance(cubes, torch.Tensor) else list(cubes)
+        path = cache_path or default_tune_cache()
+        cache = {}
+        if os.path.exists(path):
+            try:
+                with open(path) as f:
+                    cache = json.load(f)
+            except (OSError, ValueError):
+                cache = {}
+        keys = [self._tune_key(i) for i in range(len(self.dims))]
+        if not force and all(k in cache for k in keys):
+            for i, k in enumerate(keys):
+                stap_plan_set_tuning(self.handle, i, cache[k])
+            return {k: cache[k] for k in keys}
+        if outs is None:
+            outs = [torch.empty(self.shapes(i)["out"], dtype=torch.float32, device=self.device)
+                    for i in range(len(cubes))]
+        elif isinstance(outs, torch.Tensor):
+            outs = [outs]
+        self._sync_stream()
+        stap_plan_autotune(self.handle, cubes, outs, reps)
+        result = {}
+        for i, k in enumerate(keys):
+            result[k] = cache[k] = stap_plan_get_tuning(self.handle, i)
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + ".tmp.%d" % os.getpid()
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1, sort_keys=True)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+        return result
 
     def set_steering(self, steer, cpi: int = 0):
         self._sync_stream()

@@ -196,6 +196,12 @@ def mixed_cpi() -> CPISpec:
                    targets=random_targets(3, 8, 16384, 256, 32), seed=3)
 
 
+def mixed_small_cpi() -> CPISpec:
+    """A quarter of the mixed workload (R = 4096) for profiling: C16 P256 K256 R4096 T4 B128 S32."""
+    return CPISpec(16, 256, 256, 4096, 4, 128, 32, cnr_db=40.0,
+                   targets=random_targets(3, 8, 4096, 256, 32), seed=3)
+
+
 def large_cpi() -> CPISpec:
     """C32 P512 K512 R32768 T4 B256 S64, 40 dB CNR, 32 targets (about 4.3 GB)."""
     return CPISpec(32, 512, 512, 32768, 4, 256, 64, cnr_db=40.0,
@@ -224,6 +230,7 @@ WORKLOADS = {
     "small": small_cpi,
     "standard": standard_cpi,
     "mixed": mixed_cpi,
+    "mixed_small": mixed_small_cpi,
     "large": large_cpi,
 }
 

@@ -89,3 +89,30 @@ def test_full_batch_workload_on_sampled_cpis():
         g = growth(s)
         assert e_norm <= 1e-5 * g and e_cell <= 1e-3 * g, (i, e_cell, e_norm)
     plan.close()
+
+
+def test_autotune_keeps_results_and_round_trips_through_the_cache(tmp_path):
+    """Autotuning changes launch shapes only: the tuned plan reproduces the
+    default plan's output bit for bit (up to the apply kernel's summation
+    order, checked against the parity bar), and the JSON cache restores the
+    same choices into a fresh plan."""
+    specs = _uneven(6, seed=9) + [synth.standard_cpi()]
+    cubes = [torch.from_numpy(synth.make_cube(s)).cuda() for s in specs]
+    base = stap.Plan([s.dims() for s in specs])
+    ref = [o.clone() for o in base.run_cpi(cubes)]
+    cache = str(tmp_path / "tune.json")
+    tuned = stap.Plan([s.dims() for s in specs])
+    choices = tuned.autotune(cubes, cache_path=cache)
+    assert len(choices) == len({tuned._tune_key(i) for i in range(len(specs))})
+    outs = tuned.run_cpi(cubes)
+    torch.cuda.synchronize()
+    for s, o, r in zip(specs, outs, ref):
+        e_cell, e_norm = power_errors(o.cpu().numpy(), r.cpu().numpy().astype(np.float64))
+        assert e_norm <= 1e-5 and e_cell <= 1e-4, (s.dims(), e_cell, e_norm)
+    again = stap.Plan([s.dims() for s in specs])
+    again.autotune(cubes, cache_path=cache)             # from the cache, no timing
+    for i in range(len(specs)):
+        assert stap.stap_plan_get_tuning(again.handle, i) == stap.stap_plan_get_tuning(tuned.handle, i)
+    assert tuned.status() == (stap.STAP_OK, 0)
+    for p in (base, tuned, again):
+        p.close()
