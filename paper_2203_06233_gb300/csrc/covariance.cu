@@ -151,6 +151,8 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
   float2* X = reinterpret_cast<float2*>(m + ((nrows + 3) & ~3));  // [nrows][ld]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const double invB = 1.0 / (double)B;
+  const bool pow2B = (B & (B - 1)) == 0;
+  const float invBf = 1.0f / (float)B;
 
   // the B cells in chunks of CB: each chunk is summed error-free on its own
   // grid and added to Q in FP64
@@ -208,7 +210,13 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
         grid_add(hi, li, a.y, bb.x, sig);
         grid_add(hi, li, -a.x, bb.y, sig);
       }
-      double2 v = make_double2(((double)hr + (double)lr) * invB, ((double)hi + (double)li) * invB);
+      double2 v;
+      if (pow2B) {  // 1/B is a power of two: scaling the pair in FP32 is exact
+        v = make_double2((double)(hr * invBf) + (double)(lr * invBf),
+                         (double)(hi * invBf) + (double)(li * invBf));
+      } else {
+        v = make_double2(((double)hr + (double)lr) * invB, ((double)hi + (double)li) * invB);
+      }
       if (c0 > 0) {
         const double2 p = Q[it];
         v.x += p.x;

@@ -40,6 +40,7 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
+  __shared__ long long rowbase[128];          // dop offset of each tile row's range block, or -1
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int D = C * T;
   const int rows = G * D;
@@ -65,6 +66,20 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
 
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const long long sys0 = tile * G;
+    if (tid < 128) {  // row p = g*D + i: snapshot entry i of system sys0 + g
+      long long base = -1;
+      if (tid < rows) {
+        const int g = tid / D, i = tid - g * D;
+        const long long sys = sys0 + g;
+        if (sys < nsys) {
+          const int k = (int)(sys / NB), b = (int)(sys - (long long)k * NB);
+          const int t = i / C, c = i - t * C;
+          const int kk = wrap_bin(k + t - T / 2, K);
+          base = ((long long)c * K + kk) * R + (long long)b * B;
+        }
+      }
+      rowbase[tid] = base;
+    }
     for (int ch = 0; ch < nchunks && ok; ++ch, ++gch) {
       const int st = (int)(gch & 1);
       uint8_t* stage = sm + st * kStage;
@@ -87,26 +102,16 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
           const int cmi = cb0 + u * NWS;
           xv[u] = make_float2(0.f, 0.f);
           if (cmi < ncm) {
-            const int pg = cmi / (kKC / 4), jg = cmi - pg * (kKC / 4);
-            const int p = pg * 8 + (lane >> 2), j = jg * 4 + (lane & 3);
-            if (p < rows && c0 + j < B) {
-              const int g = p / D, i = p - g * D;
-              const long long sys = sys0 + g;
-              if (sys < nsys) {
-                const int k = (int)(sys / NB), b = (int)(sys - (long long)k * NB);
-                const int t = i / C, c = i - t * C;
-                const int kk = wrap_bin(k + t - T / 2, K);
-                xv[u] = __ldg(dop + ((size_t)c * K + kk) * R + (size_t)b * B + c0 + j);
-              }
-            }
+            const int p = (cmi >> 3) * 8 + (lane >> 2), j = (cmi & 7) * 4 + (lane & 3);
+            const long long base = rowbase[p];
+            if (base >= 0 && c0 + j < B) xv[u] = __ldg(dop + base + c0 + j);
           }
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
           const int cmi = cb0 + u * NWS;
           if (cmi < ncm) {
-            const int pg = cmi / (kKC / 4), jg = cmi - pg * (kKC / 4);
-            const int p = pg * 8 + (lane >> 2), j = jg * 4 + (lane & 3);
+            const int p = (cmi >> 3) * 8 + (lane >> 2), j = (cmi & 7) * 4 + (lane & 3);
             const float2 x = xv[u];
             const uint32_t rh = tc::to_tf32(x.x), ih = tc::to_tf32(x.y);
             const uint32_t rl = tc::to_tf32(x.x - __uint_as_float(rh));
@@ -167,7 +172,7 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
     const int g = tid / D, i = tid - g * D;
     const long long sys = sys0 + g;
     const bool mine = tid < 128 && tid < rows && sys < nsys;
-    const double invB = 1.0 / (double)B;
+    const float invBf = 1.0f / (float)B;
     double2* out = cov + (size_t)(mine ? sys : 0) * D * D;
     const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
     for (int cb = 0; cb < rows && warp < 4; cb += 8) {   // columns in blocks of 8 (warp-collective)
@@ -181,8 +186,8 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
           const int col = cb + u;
           const int l = col - g * D;
           if (l >= 0 && l <= i && l < D) {        // lower triangle of this system, mirrored
-            const double re = (double)a[u] * invB;
-            const double im = (l == i) ? 0.0 : ((double)bm[u] - (double)cm[u]) * invB;
+            const double re = (double)(a[u] * invBf);
+            const double im = (l == i) ? 0.0 : (double)((bm[u] - cm[u]) * invBf);
             out[(size_t)i * D + l] = make_double2(re, im);
             if (l != i) out[(size_t)l * D + i] = make_double2(re, -im);
           }
@@ -224,6 +229,8 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
+  __shared__ long long colbase[128];          // dop offset of snapshot entry d's row (bin k)
+  __shared__ long long wbase[128];            // wts offset of weight row n, or -1
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int D = C * T;
   const int tiles_per_k = (R + 127) / 128;
@@ -252,6 +259,14 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
     const int k = (int)(tile / tiles_per_k);
     const int r0 = (int)(tile - (long long)k * tiles_per_k) * 128;
     const int b0 = r0 / B;
+    if (tid < 128) {
+      if (tid < D) {
+        const int t = tid / C, c = tid - t * C;
+        colbase[tid] = ((long long)c * K + wrap_bin(k + t - T / 2, K)) * R;
+      }
+      const int j = tid / S, s = tid - j * S;
+      wbase[tid] = (tid < N && b0 + j < NB) ? ((((long long)k * NB + b0 + j) * S + s) * D) : -1;
+    }
     for (int ch = 0; ch < nchunks && ok; ++ch, ++gch) {
       const int st = (int)(gch & 1);
       uint8_t* stage = sm + st * kAStage;
@@ -274,20 +289,14 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
           const int cmi = cb0 + u * NWS;
           xv[u] = make_float2(0.f, 0.f);
           if (cmi < ncx) {
-            const int pg = cmi / (kAKC / 4), jg = cmi - pg * (kAKC / 4);
-            const int m = pg * 8 + (lane >> 2), d = d0 + jg * 4 + (lane & 3), r = r0 + m;
-            if (d < D && r < R) {
-              const int t = d / C, c = d - t * C;
-              const int kk = wrap_bin(k + t - T / 2, K);
-              xv[u] = __ldg(dop + ((size_t)c * K + kk) * R + r);
-            }
+            const int m = (cmi >> 2) * 8 + (lane >> 2), d = d0 + (cmi & 3) * 4 + (lane & 3);
+            const int r = r0 + m;
+            if (d < D && r < R) xv[u] = __ldg(dop + colbase[d] + r);
           } else if (cmi < ncm) {
             const int cw = cmi - ncx;
-            const int pg = cw / (kAKC / 4), jg = cw - pg * (kAKC / 4);
-            const int n = pg * 8 + (lane >> 2), d = d0 + jg * 4 + (lane & 3);
-            const int j = n / S, s = n - j * S;
-            if (n < N && d < D && b0 + j < NB)
-              xv[u] = __ldg(wts + ((((size_t)k * NB + b0 + j) * S + s) * D + d));
+            const int n = (cw >> 2) * 8 + (lane >> 2), d = d0 + (cw & 3) * 4 + (lane & 3);
+            const long long wb = wbase[n];
+            if (wb >= 0 && d < D) xv[u] = __ldg(wts + wb + d);
           }
         }
 #pragma unroll
@@ -296,8 +305,7 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
           if (cmi < ncm) {
             const bool isx = cmi < ncx;
             const int cl = isx ? cmi : cmi - ncx;
-            const int pg = cl / (kAKC / 4), jg = cl - pg * (kAKC / 4);
-            const int row = pg * 8 + (lane >> 2), dd = jg * 4 + (lane & 3);
+            const int row = (cl >> 2) * 8 + (lane >> 2), dd = (cl & 3) * 4 + (lane & 3);
             const float2 x = xv[u];
             const uint32_t rh = tc::to_tf32(x.x), ih = tc::to_tf32(x.y);
             const uint32_t rl = tc::to_tf32(x.x - __uint_as_float(rh));

@@ -29,6 +29,8 @@ struct Cpi {
   // spatial factors a [S][C][2]; cleared when the caller replaces the table
   bool separable = false;
   std::vector<double> sep_g, sep_a;
+  std::vector<float> steer_ff, sep_a_ff;   // the tables as double-floats [..][4]
+  size_t steer_ff_off = 0, a_ff_off = 0;
   stap::Tune tune;              // launch choices (autotuner or defaults)
   size_t dop_elems() const { return (size_t)d.n_chan * d.n_dop * d.n_range; }
   size_t cov_elems() const { return (size_t)d.n_dop * NB * D * D; }
@@ -54,6 +56,16 @@ stap_status validate(const stap_dims& d) {
       d.training_block > 4096 || d.n_chan > 65535)
     return STAP_ERR_UNSUPPORTED;
   return STAP_OK;
+}
+
+// (re, im) double pairs -> (re_hi, re_lo, im_hi, im_lo) floats
+void to_ff(const std::vector<double>& src, std::vector<float>& dst) {
+  dst.resize(src.size() * 2);
+  for (size_t i = 0; i < src.size(); ++i) {
+    const float hi = (float)src[i];
+    dst[2 * i] = hi;
+    dst[2 * i + 1] = (float)(src[i] - (double)hi);
+  }
 }
 
 void make_tables(Cpi& c) {
@@ -110,6 +122,8 @@ void make_tables(Cpi& c) {
       }
   }
   c.separable = true;
+  to_ff(c.steer, c.steer_ff);
+  to_ff(c.sep_a, c.sep_a_ff);
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -159,6 +173,10 @@ stap_status upload_tables(stap_plan p, int only_cpi = -1) {
         cudaMemcpyAsync(p->ws + c.g_off, c.sep_g.data(), c.sep_g.size() * sizeof(double),
                         cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
         cudaMemcpyAsync(p->ws + c.a_off, c.sep_a.data(), c.sep_a.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(p->ws + c.steer_ff_off, c.steer_ff.data(), c.steer_ff.size() * sizeof(float),
+                        cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(p->ws + c.a_ff_off, c.sep_a_ff.data(), c.sep_a_ff.size() * sizeof(float),
                         cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
       return STAP_ERR_CUDA;
   }
@@ -198,7 +216,8 @@ stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts, cuda
   return check_launch(stap::launch_solve(
       static_cast<const double2*>(cov), static_cast<float2*>(wts),
       p->at<const double2>(c.steer_off), c.separable ? p->at<const double2>(c.g_off) : nullptr,
-      c.separable ? p->at<const double2>(c.a_off) : nullptr, (long long)d.n_dop * c.NB, c.D,
+      c.separable ? p->at<const double2>(c.a_off) : nullptr, p->at<const float4>(c.steer_ff_off),
+      c.separable ? p->at<const float4>(c.a_ff_off) : nullptr, (long long)d.n_dop * c.NB, c.D,
       d.n_steering, d.n_chan, p->opt.load_factor, p->opt.refine_steps, p->status(), st, c.tune));
 }
 
@@ -384,6 +403,10 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
     off = align_up(off + c.sep_g.size() * sizeof(double));
     c.a_off = off;
     off = align_up(off + c.sep_a.size() * sizeof(double));
+    c.steer_ff_off = off;
+    off = align_up(off + c.steer_ff.size() * sizeof(float));
+    c.a_ff_off = off;
+    off = align_up(off + c.sep_a_ff.size() * sizeof(float));
     if (c.dop_elems() > max_dop) max_dop = c.dop_elems();
     if (c.cov_elems() > max_cov) max_cov = c.cov_elems();
     if (c.wts_elems() > max_wts) max_wts = c.wts_elems();
@@ -439,6 +462,7 @@ stap_status stap_plan_set_steering(stap_plan p, int32_t cpi, const double* host_
   for (size_t i = 0; i < c.steer.size(); ++i)
     if (!std::isfinite(host_c128[i])) return STAP_ERR_INVALID_ARG;
   std::memcpy(c.steer.data(), host_c128, c.steer.size() * sizeof(double));
+  to_ff(c.steer, c.steer_ff);
   c.separable = false;  // an arbitrary table: solve for every steering vector
   drop_graph(p);        // the captured launches chose the solve variant
   return upload_tables(p, cpi);

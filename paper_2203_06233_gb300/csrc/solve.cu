@@ -29,6 +29,7 @@
 // from S to C right-hand sides.  The combination stays in FP64: u_s can be
 // two orders of magnitude smaller than the terms it sums (steering vectors
 // near the clutter ridge), so FP32 there costs ~1e-4 in the weights.
+#include "df64.cuh"
 #include "snapshots.cuh"
 
 namespace stap {
@@ -95,7 +96,8 @@ template <bool SEP>
 __global__ void __launch_bounds__(128)
 solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
              const double2* __restrict__ steer, const double2* __restrict__ sep_g,
-             const double2* __restrict__ sep_a, long long nsys, int D, int S, int C, int TS,
+             const double2* __restrict__ sep_a, const float4* __restrict__ steer_ff,
+             const float4* __restrict__ sep_a_ff, long long nsys, int D, int S, int C, int TS,
              double load_factor, int refine_steps, DeviceStatus* __restrict__ status) {
   extern __shared__ double2 sm[];
   const int nw = blockDim.x >> 5;
@@ -176,13 +178,12 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
         q = fma(vi.y, ui.y, q);
       }
       const bool good = ok && q > 0.0 && isfinite(q);
-      const double scale = good ? rsqrt(q) : 0.0;
+      const float sf = good ? (float)rsqrt(q) : 0.f;
       if (valid) {
         float2* w = wts + ((size_t)sys * S + s) * D;
         for (int i = 0; i < D; ++i) {
           const double2 ui = u[i * 32];
-          w[i] = good ? make_float2((float)(ui.x * scale), (float)(ui.y * scale))
-                      : make_float2(0.f, 0.f);
+          w[i] = good ? make_float2((float)ui.x * sf, (float)ui.y * sf) : make_float2(0.f, 0.f);
         }
       }
     };
@@ -224,25 +225,55 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
     }
 
     // ---- SEP: u_s = sum_c a_s[c] U_c (U_c = column of lane team*TS + c) ----
+    // The combination and the normalisation are not triangular solves; they
+    // run in double-float on the FP32 pipe (about 2^-48 relative) from the
+    // FP64 basis solutions: each basis lane first writes its column as
+    // (re_hi, re_lo, im_hi, im_lo) into its W column.
     if (SEP) {
-      __syncwarp();  // the combination reads the other lanes' U columns
-      const double2* Ut = U - lane + team * TS;
+      __syncwarp();
+      float4* Wf = reinterpret_cast<float4*>(W);
+      if (tl < C)
+        for (int i = 0; i < D; ++i) {
+          const double2 u = U[i * 32];
+          const ff::F2 re = ff::from_double(u.x), im = ff::from_double(u.y);
+          Wf[i * 32] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+      __syncwarp();
+      const float4* Wt = Wf - lane + team * TS;
+      auto combine = [&](int s, int i, ff::F2& ur, ff::F2& ui) {
+        const float4* as = sep_a_ff + (size_t)s * C;
+        ur = {0.f, 0.f};
+        ui = {0.f, 0.f};
+        for (int c = 0; c < C; ++c) {
+          const float4 a = __ldg(as + c), x = Wt[i * 32 + c];
+          const ff::F2 ar{a.x, a.y}, ai{a.z, a.w}, xr{x.x, x.y}, xi{x.z, x.w};
+          ur = ff::fms(ff::fma(ur, ar, xr), ai, xi);
+          ui = ff::fma(ff::fma(ui, ar, xi), ai, xr);
+        }
+      };
       for (int s0 = 0; s0 < S; s0 += TS) {
         const int s = s0 + tl;
         if (s < S) {
-          const double2* as = sep_a + (size_t)s * C;
+          const float4* v = steer_ff + (size_t)s * D;
+          ff::F2 q{0.f, 0.f};                   // Re v^H u
           for (int i = 0; i < D; ++i) {
-            double2 acc = make_double2(0.0, 0.0);
-            for (int c = 0; c < C; ++c) {
-              const double2 a = __ldg(as + c), x = Ut[i * 32 + c];
-              acc.x = fma(a.x, x.x, acc.x);
-              acc.x = fma(-a.y, x.y, acc.x);
-              acc.y = fma(a.x, x.y, acc.y);
-              acc.y = fma(a.y, x.x, acc.y);
-            }
-            W[i * 32] = acc;
+            ff::F2 ur, ui;
+            combine(s, i, ur, ui);
+            const float4 vi = __ldg(v + i);
+            q = ff::fma(ff::fma(q, {vi.x, vi.y}, ur), {vi.z, vi.w}, ui);
           }
-          emit(s, W);
+          const double qd = ff::to_double(q);
+          const bool good = ok && qd > 0.0 && isfinite(qd);
+          const float sf = good ? (float)rsqrt(qd) : 0.f;
+          if (valid) {
+            float2* w = wts + ((size_t)sys * S + s) * D;
+            for (int i = 0; i < D; ++i) {
+              ff::F2 ur, ui;
+              combine(s, i, ur, ui);
+              w[i] = good ? make_float2(__fadd_rn(ur.hi, ur.lo) * sf, __fadd_rn(ui.hi, ui.lo) * sf)
+                          : make_float2(0.f, 0.f);
+            }
+          }
         }
       }
     }
@@ -546,12 +577,14 @@ int pow2ceil(int x) {
 }  // namespace
 
 cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
-                         const double2* sep_g, const double2* sep_a, long long nsys, int D, int S,
-                         int C, double load_factor, int refine_steps, DeviceStatus* status,
+                         const double2* sep_g, const double2* sep_a, const float4* steer_ff,
+                         const float4* sep_a_ff, long long nsys, int D, int S, int C,
+                         double load_factor, int refine_steps, DeviceStatus* status,
                          cudaStream_t s, const Tune& tn) {
   if (nsys <= 0) return cudaSuccess;
   if (D < 1 || D > kMaxD || S < 1) return cudaErrorInvalidValue;
-  const bool sep = sep_g != nullptr && sep_a != nullptr && C >= 1 && C <= 32 && D % C == 0;
+  const bool sep = sep_g != nullptr && sep_a != nullptr && steer_ff != nullptr && sep_a_ff != nullptr &&
+                   C >= 1 && C <= 32 && D % C == 0;
   if (D > kSmallMaxD) {  // one system per CTA, lanes over rows
     if (D > 32 * kBigRPL) return cudaErrorInvalidValue;
     // 16 lanes per right-hand side (two per warp) up to D = 64 with 4 warps
@@ -604,13 +637,15 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
   if (sep) {
     static int set_bytes[64] = {0};
     if ((e = ensure_smem(solve_kernel<true>, smem, set_bytes)) != cudaSuccess) return e;
-    solve_kernel<true><<<(unsigned)blocks, nw * 32, smem, s>>>(
-        cov, wts, steer, sep_g, sep_a, nsys, D, S, C, TS, load_factor, refine_steps, status);
+    solve_kernel<true><<<(unsigned)blocks, nw * 32, smem, s>>>(cov, wts, steer, sep_g, sep_a,
+                                                               steer_ff, sep_a_ff, nsys, D, S, C,
+                                                               TS, load_factor, refine_steps, status);
   } else {
     static int set_bytes[64] = {0};
     if ((e = ensure_smem(solve_kernel<false>, smem, set_bytes)) != cudaSuccess) return e;
-    solve_kernel<false><<<(unsigned)blocks, nw * 32, smem, s>>>(
-        cov, wts, steer, nullptr, nullptr, nsys, D, S, C, TS, load_factor, refine_steps, status);
+    solve_kernel<false><<<(unsigned)blocks, nw * 32, smem, s>>>(cov, wts, steer, nullptr, nullptr,
+                                                                nullptr, nullptr, nsys, D, S, C, TS,
+                                                                load_factor, refine_steps, status);
   }
   return cudaGetLastError();
 }

@@ -61,9 +61,12 @@ cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, in
 // cov [nsys][D][D] c128 -> wts [nsys][S][D] c64; steer [S][D] c128.  If
 // sep_g [T] and sep_a [S][C] are given, steer[s] = sep_g (x) sep_a[s] and the
 // solve runs on the C basis vectors instead of the S steering vectors.
+// steer_ff [S][D] and sep_a_ff [S][C] are the same tables as double-floats
+// (re_hi, re_lo, im_hi, im_lo) for the combination on the FP32 pipe.
 cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
-                         const double2* sep_g, const double2* sep_a, long long nsys, int D, int S,
-                         int C, double load_factor, int refine_steps, DeviceStatus* status,
+                         const double2* sep_g, const double2* sep_a, const float4* steer_ff,
+                         const float4* sep_a_ff, long long nsys, int D, int S, int C,
+                         double load_factor, int refine_steps, DeviceStatus* status,
                          cudaStream_t s, const Tune& t = Tune());
 
 // out[s][k][r] = |w^H x|^2; dop [C][K][R] c64, wts [K][NB][S][D] c64, out [S][K][R] f32.
