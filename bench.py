@@ -154,6 +154,12 @@ def aggregate(local_ms, local_cells, world, device):
     return total_ms, world * local_cells / (total_ms * 1e-3)
 
 
+def slab_count(tuning, nb):
+    """Range slabs the tuned one-CPI run uses (four kernel launches each)."""
+    (choices,) = tuning.values()
+    return max(1, min(choices[6], 8, nb))
+
+
 def time_steps(fn, steps, flush, stream):
     """Per-step device time (ms) with CUDA events, L2 flushed before each step."""
     import torch
@@ -337,7 +343,7 @@ def run_gpu(args):
         "config": cfg,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": cube_h.nbytes,
                 "d2h_bytes_per_step": S * K * R * 4, "ms_per_step": e2e_ms},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 4 * slab_count(tuning, NB) * args.steps,
         "mixed": mixed,
         "roofline": roofline,
         "kernels": kernels,

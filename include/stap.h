@@ -146,6 +146,14 @@ stap_status stap_apply(stap_plan plan, const void* dop_c64, const void* wts_c64,
  * cubes[i]: c64 [C_i][P_i][R_i]; outs[i]: float [S_i][K_i][R_i]; both arrays
  * are HOST arrays of n_cpi device pointers.
  *
+ * With n_cpi == 1 and a tuned slab count above 1 (stap_plan_autotune or
+ * stap_plan_set_tuning), the range axis is cut into that many slabs of whole
+ * training blocks and each slab's chain runs on its own internal stream,
+ * earlier slabs at higher priority, so that the FP64 solve of one slab
+ * overlaps the other steps of the next; the result is the same.  Those
+ * streams are created by the first such call and joined back into the plan's
+ * stream before the call returns.
+ *
  * With n_cpi > 1 the CPIs are packed, in order, into waves whose
  * intermediates fit in the workspace beyond step_bytes (any workspace of at
  * least run_bytes works; stap_plan_batch_bytes gives the size at which all
@@ -198,7 +206,7 @@ stap_status stap_run_cpi_noalloc(const stap_dims* dims, const stap_options* opt,
                                  const void* cube_c64, float* out, int64_t* n_failed_systems);
 
 /* Number of launch choices per CPI kept by the autotuner. */
-#define STAP_TUNING_LEN 6
+#define STAP_TUNING_LEN 7
 
 /* Autotune the launch configuration of every distinct CPI shape of the plan
  * (C, P, K, T, B, S; CPIs that differ only in R share one tuning): for each
@@ -207,7 +215,8 @@ stap_status stap_run_cpi_noalloc(const stap_dims* dims, const stap_options* opt,
  * and keeps the fastest.  Candidates: range cells per Doppler CTA (8/16/32);
  * Doppler bins per covariance CTA (plain precision); lanes per system and
  * warps per CTA of the D <= 32 solve, lanes per right-hand side of the larger
- * solve; register-resident or general FP32 apply.  Every candidate computes
+ * solve; register-resident or general FP32 apply; for a one-CPI plan, 1, 2, 4
+ * or 8 pipelined range slabs of the whole run.  Every candidate computes
  * the same result except that the two FP32 apply kernels sum in a different
  * order.  Needs the run workspace; synchronises the plan's stream; overwrites
  * outs; clears the device status; drops a captured batch graph. */
@@ -217,7 +226,8 @@ stap_status stap_plan_autotune(stap_plan plan, const void* const* cubes, float* 
 /* The launch choices of CPI `cpi` as STAP_TUNING_LEN integers (0 = built-in
  * heuristic): Doppler cells per CTA, covariance bins per CTA, solve lanes per
  * system, solve warps per CTA, large-solve lanes per right-hand side, apply
- * kernel (1 register-resident, 2 general).  set_tuning installs saved choices
+ * kernel (1 register-resident, 2 general), range slabs of a one-CPI
+ * stap_run_cpi (at most 8 and NB are used).  set_tuning installs saved choices
  * (values 0..64; a choice that does not fit a launch falls back to the
  * heuristic). */
 stap_status stap_plan_get_tuning(stap_plan plan, int32_t cpi, int32_t* choices);

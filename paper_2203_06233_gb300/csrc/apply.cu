@@ -21,7 +21,7 @@ constexpr int kThreads = 256;
 
 __global__ void __launch_bounds__(kThreads)
 apply_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts, float* __restrict__ out,
-             int C, int K, int R, int T, int B, int S, int NBB, int CC) {
+             int C, int K, int R, int ldr, int T, int B, int S, int NBB, int CC) {
   extern __shared__ float4 sm4[];
   float2* sm = reinterpret_cast<float2*>(sm4);
   const int D = C * T;
@@ -47,7 +47,7 @@ apply_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts, flo
   for (int c0 = 0; c0 < cells; c0 += CC) {
     const int cc = min(CC, cells - c0);
     __syncthreads();
-    stage_snapshots(xs, ld, dop, C, K, R, T, k, b0 * B + c0, cc);
+    stage_snapshots(xs, ld, dop, C, K, ldr, T, k, b0 * B + c0, cc);
     __syncthreads();
     for (int rr = threadIdx.x; rr < cc; rr += blockDim.x) {
       const int j = (c0 + rr) / B;
@@ -77,7 +77,7 @@ apply_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts, flo
 #pragma unroll
         for (int q = 0; q < SC; ++q)
           if (s0 + q < S)
-            out[((size_t)(s0 + q) * K + k) * R + r] = fmaf(acc[q].x, acc[q].x, acc[q].y * acc[q].y);
+            out[((size_t)(s0 + q) * K + k) * ldr + r] = fmaf(acc[q].x, acc[q].x, acc[q].y * acc[q].y);
       }
     }
   }
@@ -95,7 +95,7 @@ constexpr int kRegCells = 2 * kThreads;     // range cells per CTA
 template <int D>
 __global__ void __launch_bounds__(kThreads)
 apply_reg_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
-                 float* __restrict__ out, int C, int K, int R, int T, int B, int S) {
+                 float* __restrict__ out, int C, int K, int R, int ldr, int T, int B, int S) {
   extern __shared__ float4 sm4[];
   float2* ws = reinterpret_cast<float2*>(sm4);    // [nblk][S][D]
   const int NB = R / B;
@@ -116,7 +116,7 @@ apply_reg_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
     for (int d = 0; d < D; ++d) {
       const int t = d / C, c = d - t * C;
       const int kk = wrap_bin(k + t - T / 2, K);
-      x[d] = __ldg(reinterpret_cast<const float4*>(dop + ((size_t)c * K + kk) * R + r0));
+      x[d] = __ldg(reinterpret_cast<const float4*>(dop + ((size_t)c * K + kk) * ldr + r0));
     }
   }
   __syncthreads();
@@ -139,14 +139,14 @@ apply_reg_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
       a1r = fmaf(w.z, xb.z, a1r); a1r = fmaf(w.w, xb.w, a1r);
       a1i = fmaf(w.z, xb.w, a1i); a1i = fmaf(-w.w, xb.z, a1i);
     }
-    *reinterpret_cast<float2*>(out + ((size_t)s * K + k) * R + r0) =
+    *reinterpret_cast<float2*>(out + ((size_t)s * K + k) * ldr + r0) =
         make_float2(fmaf(a0r, a0r, a0i * a0i), fmaf(a1r, a1r, a1i * a1i));
   }
 }
 
 template <int D>
 cudaError_t launch_apply_reg(const float2* dop, const float2* wts, float* out, int C, int K, int R,
-                             int T, int B, int S, cudaStream_t s) {
+                             int ldr, int T, int B, int S, cudaStream_t s) {
   const int NB = R / B;
   const int max_blk = kRegCells / B + 2;
   const size_t smem = (size_t)(max_blk < NB ? max_blk : NB) * S * D * sizeof(float2);
@@ -154,34 +154,37 @@ cudaError_t launch_apply_reg(const float2* dop, const float2* wts, float* out, i
   cudaError_t e = ensure_smem(apply_reg_kernel<D>, smem, set_bytes);
   if (e != cudaSuccess) return e;
   dim3 grid((R + kRegCells - 1) / kRegCells, K);
-  apply_reg_kernel<D><<<grid, kThreads, smem, s>>>(dop, wts, out, C, K, R, T, B, S);
+  apply_reg_kernel<D><<<grid, kThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_apply(const float2* dop, const float2* wts, float* out, int C, int K, int R,
-                         int T, int B, int S, cudaStream_t s, const Tune& tn) {
+                         int ldr, int T, int B, int S, cudaStream_t s, const Tune& tn) {
   const int D = C * T;
   const int NB = R / B;
   if (NB == 0) return cudaSuccess;
-  // register-resident form: even D <= 24, even B (cell pairs never straddle a
-  // block and 16-byte loads stay aligned), weights of a CTA within 160 KB
-  if (tn.apply_kind != 2 && D % 2 == 0 && D <= 24 && B % 2 == 0 &&
+  // register-resident form: even D <= 24, even B and row stride (cell pairs
+  // never straddle a block and 16-byte loads stay aligned), weights of a CTA
+  // within 160 KB
+  const bool aligned = (reinterpret_cast<uintptr_t>(dop) & 15) == 0 &&
+                       (reinterpret_cast<uintptr_t>(out) & 7) == 0 && ldr % 2 == 0;
+  if (tn.apply_kind != 2 && aligned && D % 2 == 0 && D <= 24 && B % 2 == 0 &&
       (size_t)(kRegCells / B + 2) * S * D * sizeof(float2) <= 160 * 1024) {
     switch (D) {
-      case 2: return launch_apply_reg<2>(dop, wts, out, C, K, R, T, B, S, s);
-      case 4: return launch_apply_reg<4>(dop, wts, out, C, K, R, T, B, S, s);
-      case 6: return launch_apply_reg<6>(dop, wts, out, C, K, R, T, B, S, s);
-      case 8: return launch_apply_reg<8>(dop, wts, out, C, K, R, T, B, S, s);
-      case 10: return launch_apply_reg<10>(dop, wts, out, C, K, R, T, B, S, s);
-      case 12: return launch_apply_reg<12>(dop, wts, out, C, K, R, T, B, S, s);
-      case 14: return launch_apply_reg<14>(dop, wts, out, C, K, R, T, B, S, s);
-      case 16: return launch_apply_reg<16>(dop, wts, out, C, K, R, T, B, S, s);
-      case 18: return launch_apply_reg<18>(dop, wts, out, C, K, R, T, B, S, s);
-      case 20: return launch_apply_reg<20>(dop, wts, out, C, K, R, T, B, S, s);
-      case 22: return launch_apply_reg<22>(dop, wts, out, C, K, R, T, B, S, s);
-      case 24: return launch_apply_reg<24>(dop, wts, out, C, K, R, T, B, S, s);
+      case 2: return launch_apply_reg<2>(dop, wts, out, C, K, R, ldr, T, B, S, s);
+      case 4: return launch_apply_reg<4>(dop, wts, out, C, K, R, ldr, T, B, S, s);
+      case 6: return launch_apply_reg<6>(dop, wts, out, C, K, R, ldr, T, B, S, s);
+      case 8: return launch_apply_reg<8>(dop, wts, out, C, K, R, ldr, T, B, S, s);
+      case 10: return launch_apply_reg<10>(dop, wts, out, C, K, R, ldr, T, B, S, s);
+      case 12: return launch_apply_reg<12>(dop, wts, out, C, K, R, ldr, T, B, S, s);
+      case 14: return launch_apply_reg<14>(dop, wts, out, C, K, R, ldr, T, B, S, s);
+      case 16: return launch_apply_reg<16>(dop, wts, out, C, K, R, ldr, T, B, S, s);
+      case 18: return launch_apply_reg<18>(dop, wts, out, C, K, R, ldr, T, B, S, s);
+      case 20: return launch_apply_reg<20>(dop, wts, out, C, K, R, ldr, T, B, S, s);
+      case 22: return launch_apply_reg<22>(dop, wts, out, C, K, R, ldr, T, B, S, s);
+      case 24: return launch_apply_reg<24>(dop, wts, out, C, K, R, ldr, T, B, S, s);
       default: break;
     }
   }
@@ -200,7 +203,7 @@ cudaError_t launch_apply(const float2* dop, const float2* wts, float* out, int C
   cudaError_t e = ensure_smem(apply_kernel, smem, set_bytes);
   if (e != cudaSuccess) return e;
   dim3 grid((NB + NBB - 1) / NBB, K);
-  apply_kernel<<<grid, kThreads, smem, s>>>(dop, wts, out, C, K, R, T, B, S, NBB, CC);
+  apply_kernel<<<grid, kThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S, NBB, CC);
   return cudaGetLastError();
 }
 

@@ -47,7 +47,7 @@ __device__ __forceinline__ void unpack_lower(int q, int& i, int& l) {
 }
 
 __global__ void __launch_bounds__(256)
-covariance_ff_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K, int R,
+covariance_ff_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K, int ldr,
                      int T, int B, int NB, int NS, int BC) {
   extern __shared__ float2 xs[];  // [NS][D][BC + 1]
   const int k = blockIdx.y;
@@ -62,7 +62,7 @@ covariance_ff_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
     const int bc = min(BC, B - c0);
     __syncthreads();
     for (int j = 0; j < ns; ++j)
-      stage_snapshots(xs + (size_t)j * D * ld, ld, dop, C, K, R, T, k, (b0 + j) * B + c0, bc);
+      stage_snapshots(xs + (size_t)j * D * ld, ld, dop, C, K, ldr, T, k, (b0 + j) * B + c0, bc);
     __syncthreads();
     for (int it = threadIdx.x; it < ns * E; it += blockDim.x) {
       const int j = it / E;
@@ -135,7 +135,7 @@ __device__ __forceinline__ void grid_add(float& hi, float& lo, float a, float b,
 
 __global__ void __launch_bounds__(kPairThreads)
 covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K,
-                        int R, int T, int B, int NB, int KT, int CB) {
+                        int ldr, int T, int B, int NB, int KT, int CB) {
   extern __shared__ double2 smd[];
   const int b = blockIdx.x;
   const int k0 = blockIdx.y * KT;
@@ -162,7 +162,7 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
     for (int row = warp; row < nrows; row += nwarps) {   // rows (bin j, channel c)
       const int j = row / C, c = row - j * C;
       const int kk = wrap_bin(k0 - h + j, K);
-      const float2* src = dop + ((size_t)c * K + kk) * R + (size_t)b * B + c0;
+      const float2* src = dop + ((size_t)c * K + kk) * ldr + (size_t)b * B + c0;
       float2* dst = X + row * ld;
       float mx = 0.f;
       for (int cell = lane; cell < cc; cell += 32) {
@@ -258,8 +258,8 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
 
 }  // namespace
 
-cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K, int R, int T,
-                                   int B, cudaStream_t s, const Tune& tn) {
+cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K, int R, int ldr,
+                                   int T, int B, cudaStream_t s, const Tune& tn) {
   const int D = C * T;
   const int E = D * (D + 1) / 2;
   const int NB = R / B;
@@ -288,7 +288,7 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
       cudaError_t e = ensure_smem(covariance_pairs_kernel, smem, set_bytes);
       if (e != cudaSuccess) return e;
       dim3 grid(NB, K / KT);
-      covariance_pairs_kernel<<<grid, kPairThreads, smem, s>>>(dop, cov, C, K, R, T, B, NB, KT, CB);
+      covariance_pairs_kernel<<<grid, kPairThreads, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, KT, CB);
       return cudaGetLastError();
     }
   }
@@ -306,7 +306,7 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
   cudaError_t e = ensure_smem(covariance_ff_kernel, smem, set_bytes);
   if (e != cudaSuccess) return e;
   dim3 grid((NB + NS - 1) / NS, K);
-  covariance_ff_kernel<<<grid, 256, smem, s>>>(dop, cov, C, K, R, T, B, NB, NS, BC);
+  covariance_ff_kernel<<<grid, 256, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, NS, BC);
   return cudaGetLastError();
 }
 

@@ -2,7 +2,8 @@
 //   dop[c][k][r] = sum_{p<P} h[p] cube[c][p][r] exp(-2 pi i p k / K),  K >= P,
 // computed as a zero-padded length-K FFT over the pulse axis.
 //
-// Layout: the pulse axis has stride R, the range axis is contiguous.  A CTA
+// Layout: the pulse axis has stride ldr (the full range extent; a launch may
+// cover R <= ldr cells of it), the range axis is contiguous.  A CTA
 // owns one channel and TR (8-32) consecutive range cells and does TR independent
 // length-K FFTs by the four-step split K = N1 * N2:
 //   input  index n = n1 + N1 n2,   output index k = k2 + N2 k1,
@@ -61,7 +62,8 @@ __device__ __forceinline__ void fft_reg(float2 (&v)[N], const float2* __restrict
 template <int LOGK, int TR>
 __global__ void __launch_bounds__(TR * (1 << ((LOGK + 1) / 2)))
 doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
-                   const float* __restrict__ win, const float2* __restrict__ twg, int P, int R) {
+                   const float* __restrict__ win, const float2* __restrict__ twg, int P, int R,
+                   int ldr) {
   constexpr int K = 1 << LOGK;
   constexpr int N1 = 1 << ((LOGK + 1) / 2);
   constexpr int N2 = 1 << (LOGK / 2);
@@ -79,14 +81,14 @@ doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
     const int col = tid % TR, n1 = tid / TR;
     const int r = r0 + col;
     const bool in_range = r < R;
-    const float2* src = cube + (size_t)c * P * R + r;
+    const float2* src = cube + (size_t)c * P * ldr + r;
     float2 v[N2];
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) {
       const int n = n1 + N1 * n2;
       float2 x = make_float2(0.f, 0.f);
       if (in_range && n < P) {
-        x = __ldg(src + (size_t)n * R);
+        x = __ldg(src + (size_t)n * ldr);
         const float h = __ldg(win + n);
         x.x *= h;
         x.y *= h;
@@ -112,16 +114,16 @@ doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
     for (int n1 = 0; n1 < N1; ++n1) u[n1] = Y[(n1 * N2 + k2) * TR + col];
     fft_reg<N1, K>(u, tw);
     if (r < R) {
-      float2* dst = dop + (size_t)c * K * R + r;
+      float2* dst = dop + (size_t)c * K * ldr + r;
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) dst[(size_t)(k2 + N2 * k1) * R] = u[k1];
+      for (int k1 = 0; k1 < N1; ++k1) dst[(size_t)(k2 + N2 * k1) * ldr] = u[k1];
     }
   }
 }
 
 template <int LOGK, int TR>
 cudaError_t launch_logk_tr(const float2* cube, float2* dop, const float* win, const float2* tw, int C,
-                           int P, int R, cudaStream_t s) {
+                           int P, int R, int ldr, cudaStream_t s) {
   constexpr int K = 1 << LOGK;
   constexpr int N1 = 1 << ((LOGK + 1) / 2);
   const size_t smem = (size_t)K * sizeof(float2) * (1 + TR);
@@ -131,7 +133,7 @@ cudaError_t launch_logk_tr(const float2* cube, float2* dop, const float* win, co
   cudaError_t e = ensure_smem(kern, smem, set_bytes);
   if (e != cudaSuccess) return e;
   dim3 grid((R + TR - 1) / TR, C);
-  kern<<<grid, TR * N1, smem, s>>>(cube, dop, win, tw, P, R);
+  kern<<<grid, TR * N1, smem, s>>>(cube, dop, win, tw, P, R, ldr);
   return cudaGetLastError();
 }
 
@@ -140,13 +142,13 @@ cudaError_t launch_logk_tr(const float2* cube, float2* dop, const float* win, co
 // contiguous bytes of a row (two full 32-byte sectors)
 template <int LOGK>
 cudaError_t launch_logk(const float2* cube, float2* dop, const float* win, const float2* tw, int C,
-                        int P, int R, cudaStream_t s, int tr) {
+                        int P, int R, int ldr, cudaStream_t s, int tr) {
   constexpr int N1 = 1 << ((LOGK + 1) / 2);
   if (tr == 0) tr = (N1 >= 32) ? 8 : (N1 >= 16 ? 16 : 32);
   switch (tr) {
-    case 8: return launch_logk_tr<LOGK, 8>(cube, dop, win, tw, C, P, R, s);
-    case 16: return launch_logk_tr<LOGK, 16>(cube, dop, win, tw, C, P, R, s);
-    case 32: return launch_logk_tr<LOGK, 32>(cube, dop, win, tw, C, P, R, s);
+    case 8: return launch_logk_tr<LOGK, 8>(cube, dop, win, tw, C, P, R, ldr, s);
+    case 16: return launch_logk_tr<LOGK, 16>(cube, dop, win, tw, C, P, R, ldr, s);
+    case 32: return launch_logk_tr<LOGK, 32>(cube, dop, win, tw, C, P, R, ldr, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -154,20 +156,20 @@ cudaError_t launch_logk(const float2* cube, float2* dop, const float* win, const
 }  // namespace
 
 cudaError_t launch_doppler(const float2* cube, float2* dop, const float* win, const float2* tw,
-                           int C, int P, int K, int R, cudaStream_t s, const Tune& t) {
+                           int C, int P, int K, int R, int ldr, cudaStream_t s, const Tune& t) {
   const int tr = t.dop_tr;
   switch (ilog2c(K)) {
-    case 0: return launch_logk<0>(cube, dop, win, tw, C, P, R, s, tr);
-    case 1: return launch_logk<1>(cube, dop, win, tw, C, P, R, s, tr);
-    case 2: return launch_logk<2>(cube, dop, win, tw, C, P, R, s, tr);
-    case 3: return launch_logk<3>(cube, dop, win, tw, C, P, R, s, tr);
-    case 4: return launch_logk<4>(cube, dop, win, tw, C, P, R, s, tr);
-    case 5: return launch_logk<5>(cube, dop, win, tw, C, P, R, s, tr);
-    case 6: return launch_logk<6>(cube, dop, win, tw, C, P, R, s, tr);
-    case 7: return launch_logk<7>(cube, dop, win, tw, C, P, R, s, tr);
-    case 8: return launch_logk<8>(cube, dop, win, tw, C, P, R, s, tr);
-    case 9: return launch_logk<9>(cube, dop, win, tw, C, P, R, s, tr);
-    case 10: return launch_logk<10>(cube, dop, win, tw, C, P, R, s, tr);
+    case 0: return launch_logk<0>(cube, dop, win, tw, C, P, R, ldr, s, tr);
+    case 1: return launch_logk<1>(cube, dop, win, tw, C, P, R, ldr, s, tr);
+    case 2: return launch_logk<2>(cube, dop, win, tw, C, P, R, ldr, s, tr);
+    case 3: return launch_logk<3>(cube, dop, win, tw, C, P, R, ldr, s, tr);
+    case 4: return launch_logk<4>(cube, dop, win, tw, C, P, R, ldr, s, tr);
+    case 5: return launch_logk<5>(cube, dop, win, tw, C, P, R, ldr, s, tr);
+    case 6: return launch_logk<6>(cube, dop, win, tw, C, P, R, ldr, s, tr);
+    case 7: return launch_logk<7>(cube, dop, win, tw, C, P, R, ldr, s, tr);
+    case 8: return launch_logk<8>(cube, dop, win, tw, C, P, R, ldr, s, tr);
+    case 9: return launch_logk<9>(cube, dop, win, tw, C, P, R, ldr, s, tr);
+    case 10: return launch_logk<10>(cube, dop, win, tw, C, P, R, ldr, s, tr);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -35,7 +35,7 @@ constexpr int kTmemCols = 512;                // 3 x 128 accumulators, rounded u
 
 __global__ void __launch_bounds__(kTcThreads)
 covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K,
-                     int R, int T, int B, int NB, int G, long long ntiles,
+                     int ldr, int T, int B, int NB, int G, long long ntiles,
                      DeviceStatus* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t mbar[2];
@@ -75,7 +75,7 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
           const int k = (int)(sys / NB), b = (int)(sys - (long long)k * NB);
           const int t = i / C, c = i - t * C;
           const int kk = wrap_bin(k + t - T / 2, K);
-          base = ((long long)c * K + kk) * R + (long long)b * B;
+          base = ((long long)c * K + kk) * ldr + (long long)b * B;
         }
       }
       rowbase[tid] = base;
@@ -224,7 +224,7 @@ constexpr int kAStage = 8 * kAX;              // X: re/im x hi/lo, W: re/im x hi
 
 __global__ void __launch_bounds__(kTcThreads)
 apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
-                float* __restrict__ out, int C, int K, int R, int T, int B, int S, int NB,
+                float* __restrict__ out, int C, int K, int R, int ldr, int T, int B, int S, int NB,
                 int NP, long long ntiles, DeviceStatus* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t mbar[2];
@@ -262,7 +262,7 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
     if (tid < 128) {
       if (tid < D) {
         const int t = tid / C, c = tid - t * C;
-        colbase[tid] = ((long long)c * K + wrap_bin(k + t - T / 2, K)) * R;
+        colbase[tid] = ((long long)c * K + wrap_bin(k + t - T / 2, K)) * ldr;
       }
       const int j = tid / S, s = tid - j * S;
       wbase[tid] = (tid < N && b0 + j < NB) ? ((((long long)k * NB + b0 + j) * S + s) * D) : -1;
@@ -382,7 +382,7 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
           const int s = cb + u - j * S;
           if (s >= 0 && s < S) {
             const float re = a[u], im = bm[u] - cm[u];
-            out[((size_t)s * K + k) * R + r] = fmaf(re, re, im * im);
+            out[((size_t)s * K + k) * ldr + r] = fmaf(re, re, im * im);
           }
         }
       }
@@ -403,8 +403,8 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
 
 }  // namespace
 
-cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int T, int B,
-                                 DeviceStatus* status, cudaStream_t s) {
+cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int ldr, int T,
+                                 int B, DeviceStatus* status, cudaStream_t s) {
   const int D = C * T;
   const int NB = R / B;
   if (NB == 0) return cudaSuccess;
@@ -417,7 +417,7 @@ cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, 
   cudaError_t e = ensure_smem(covariance_tc_kernel, smem, set_bytes);
   if (e != cudaSuccess) return e;
   long long blocks = ntiles < 152 ? ntiles : 152;   // one CTA per SM (TMEM and shared memory)
-  covariance_tc_kernel<<<(unsigned)blocks, kTcThreads, smem, s>>>(dop, cov, C, K, R, T, B, NB, G,
+  covariance_tc_kernel<<<(unsigned)blocks, kTcThreads, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, G,
                                                                     ntiles, status);
   return cudaGetLastError();
 }
@@ -430,7 +430,7 @@ bool apply_tc_supported(int B, int S) {
 }
 
 cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, int C, int K, int R,
-                            int T, int B, int S, DeviceStatus* status, cudaStream_t s) {
+                            int ldr, int T, int B, int S, DeviceStatus* status, cudaStream_t s) {
   const int NB = R / B;
   if (NB == 0) return cudaSuccess;
   if (!apply_tc_supported(B, S) || C * T > 128) return cudaErrorInvalidValue;
@@ -442,7 +442,7 @@ cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, in
   cudaError_t e = ensure_smem(apply_tc_kernel, smem, set_bytes);
   if (e != cudaSuccess) return e;
   long long blocks = ntiles < 152 ? ntiles : 152;
-  apply_tc_kernel<<<(unsigned)blocks, kTcThreads, smem, s>>>(dop, wts, out, C, K, R, T, B, S, NB, NP,
+  apply_tc_kernel<<<(unsigned)blocks, kTcThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S, NB, NP,
                                                                ntiles, status);
   return cudaGetLastError();
 }

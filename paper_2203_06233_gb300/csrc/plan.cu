@@ -13,6 +13,7 @@ using stap::DeviceStatus;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kMaxSlabs = 8;     // range slabs of a pipelined single-CPI run
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -146,6 +147,10 @@ struct stap_plan_s {
   cudaStream_t cap = nullptr;     // capture origin (the caller's stream may be the legacy one)
   cudaEvent_t fork_ev = nullptr, join_ev[kSideStreams] = {};
   cudaGraphExec_t graph_exec = nullptr;
+  // pipelined single-CPI runs: one stream per range slab, earlier slabs at
+  // higher priority
+  cudaStream_t slab[kMaxSlabs] = {};
+  cudaEvent_t slab_fork = nullptr, slab_join[kMaxSlabs] = {};
   std::vector<const void*> graph_cubes;   // buffers the graph was captured with
   std::vector<float*> graph_outs;
   char* graph_ws = nullptr;
@@ -193,55 +198,129 @@ stap_status ready(stap_plan p, size_t need) {
 
 // ----- the four steps on one CPI (arguments already validated) --------------
 
-stap_status do_doppler(stap_plan p, const Cpi& c, const void* cube, void* dop, cudaStream_t st) {
+// Each step covers nr range cells (whole training blocks; nr < 0: all of
+// them) starting at the given pointers; range-indexed tensors keep the CPI's
+// full row stride R, and cov/wts hold the nr / B blocks of each bin.
+
+stap_status do_doppler(stap_plan p, const Cpi& c, const void* cube, void* dop, cudaStream_t st,
+                       int nr = -1) {
   const stap_dims& d = c.d;
   return check_launch(stap::launch_doppler(
       static_cast<const float2*>(cube), static_cast<float2*>(dop), p->at<const float>(c.win_off),
-      p->at<const float2>(c.tw_off), d.n_chan, d.n_pulses, d.n_dop, d.n_range, st, c.tune));
+      p->at<const float2>(c.tw_off), d.n_chan, d.n_pulses, d.n_dop, nr < 0 ? d.n_range : nr,
+      d.n_range, st, c.tune));
 }
 
-stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov, cudaStream_t st) {
+stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov, cudaStream_t st,
+                          int nr = -1) {
   const stap_dims& d = c.d;
+  const int R = nr < 0 ? d.n_range : nr;
   if (p->opt.precision == STAP_PREC_TF32X3)
     return check_launch(stap::launch_covariance_tc(static_cast<const float2*>(dop),
                                                    static_cast<double2*>(cov), d.n_chan, d.n_dop,
-                                                   d.n_range, d.tdof, d.training_block, p->status(), st));
+                                                   R, d.n_range, d.tdof, d.training_block,
+                                                   p->status(), st));
   return check_launch(stap::launch_covariance_fp32(static_cast<const float2*>(dop),
                                                    static_cast<double2*>(cov), d.n_chan, d.n_dop,
-                                                   d.n_range, d.tdof, d.training_block, st, c.tune));
+                                                   R, d.n_range, d.tdof, d.training_block, st,
+                                                   c.tune));
 }
 
-stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts, cudaStream_t st) {
+stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts, cudaStream_t st,
+                     int nr = -1) {
   const stap_dims& d = c.d;
+  const long long nb = nr < 0 ? c.NB : nr / d.training_block;
   return check_launch(stap::launch_solve(
       static_cast<const double2*>(cov), static_cast<float2*>(wts),
       p->at<const double2>(c.steer_off), c.separable ? p->at<const double2>(c.g_off) : nullptr,
       c.separable ? p->at<const double2>(c.a_off) : nullptr, p->at<const float4>(c.steer_ff_off),
-      c.separable ? p->at<const float4>(c.a_ff_off) : nullptr, (long long)d.n_dop * c.NB, c.D,
+      c.separable ? p->at<const float4>(c.a_ff_off) : nullptr, (long long)d.n_dop * nb, c.D,
       d.n_steering, d.n_chan, p->opt.load_factor, p->opt.refine_steps, p->status(), st, c.tune));
 }
 
 stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts, float* out,
-                     cudaStream_t st) {
+                     cudaStream_t st, int nr = -1) {
   const stap_dims& d = c.d;
+  const int R = nr < 0 ? d.n_range : nr;
   if (p->opt.precision == STAP_PREC_TF32X3 && stap::apply_tc_supported(d.training_block, d.n_steering))
     return check_launch(stap::launch_apply_tc(static_cast<const float2*>(dop),
                                               static_cast<const float2*>(wts), out, d.n_chan,
-                                              d.n_dop, d.n_range, d.tdof, d.training_block,
+                                              d.n_dop, R, d.n_range, d.tdof, d.training_block,
                                               d.n_steering, p->status(), st));
   return check_launch(stap::launch_apply(static_cast<const float2*>(dop),
                                          static_cast<const float2*>(wts), out, d.n_chan, d.n_dop,
-                                         d.n_range, d.tdof, d.training_block, d.n_steering, st,
+                                         R, d.n_range, d.tdof, d.training_block, d.n_steering, st,
                                          c.tune));
 }
 
 stap_status do_chain(stap_plan p, const Cpi& c, const void* cube, float* out, char* dop, char* cov,
-                     char* wts, cudaStream_t st) {
+                     char* wts, cudaStream_t st, int nr = -1) {
   stap_status r;
-  if ((r = do_doppler(p, c, cube, dop, st)) != STAP_OK) return r;
-  if ((r = do_covariance(p, c, dop, cov, st)) != STAP_OK) return r;
-  if ((r = do_solve(p, c, cov, wts, st)) != STAP_OK) return r;
-  return do_apply(p, c, dop, wts, out, st);
+  if ((r = do_doppler(p, c, cube, dop, st, nr)) != STAP_OK) return r;
+  if ((r = do_covariance(p, c, dop, cov, st, nr)) != STAP_OK) return r;
+  if ((r = do_solve(p, c, cov, wts, st, nr)) != STAP_OK) return r;
+  return do_apply(p, c, dop, wts, out, st, nr);
+}
+
+int slab_count(const Cpi& c) {
+  int ns = c.tune.slabs < 1 ? 1 : c.tune.slabs;
+  if (ns > kMaxSlabs) ns = kMaxSlabs;
+  if (ns > c.NB) ns = c.NB;
+  return ns;
+}
+
+// One CPI in `slab_count` range slabs of whole training blocks.  Every slab's
+// four-step chain is independent (its snapshots, covariances and weights lie
+// inside the slab), so the chains run on their own streams: while the
+// FP64-bound solve of one slab runs, the memory- and FP32-bound Doppler,
+// covariance and apply kernels of the others fill the SMs.  Earlier slabs run
+// at higher stream priority, so the chains stagger into a pipeline instead of
+// advancing in lockstep.  Slab j's covariances and weights start at 256-byte
+// aligned offsets of the run buffers (the plan reserves the slack).
+stap_status run_single(stap_plan p, const void* cube, float* out) {
+  const Cpi& c = p->cpis[0];
+  char* dop = p->ws + p->dop_off;
+  char* cov = p->ws + p->cov_off;
+  char* wts = p->ws + p->wts_off;
+  const int ns = slab_count(c);
+  if (ns <= 1) return do_chain(p, c, cube, static_cast<float*>(out), dop, cov, wts, p->stream);
+  if (!p->slab_fork) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return STAP_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&p->slab_fork, cudaEventDisableTiming) != cudaSuccess)
+      return STAP_ERR_CUDA;
+    for (int j = 0; j < kMaxSlabs; ++j) {
+      int prio = greatest + j;            // numerically lower = higher priority
+      if (prio > least) prio = least;
+      if (cudaStreamCreateWithPriority(&p->slab[j], cudaStreamNonBlocking, prio) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p->slab_join[j], cudaEventDisableTiming) != cudaSuccess)
+        return STAP_ERR_CUDA;
+    }
+  }
+  const stap_dims& d = c.d;
+  const int B = d.training_block, K = d.n_dop;
+  if (cudaEventRecord(p->slab_fork, p->stream) != cudaSuccess) return STAP_ERR_CUDA;
+  stap_status st = STAP_OK;
+  size_t cov_at = 0, wts_at = 0;
+  int j = 0;
+  for (; j < ns && st == STAP_OK; ++j) {
+    const int nb0 = (int)((long long)c.NB * j / ns), nb1 = (int)((long long)c.NB * (j + 1) / ns);
+    const size_t rs = (size_t)nb0 * B;
+    const int nr = (nb1 - nb0) * B;
+    if (cudaStreamWaitEvent(p->slab[j], p->slab_fork, 0) != cudaSuccess) {
+      st = STAP_ERR_CUDA;
+      break;
+    }
+    st = do_chain(p, c, static_cast<const float2*>(cube) + rs, out + rs,
+                  dop + rs * sizeof(float2), cov + cov_at, wts + wts_at, p->slab[j], nr);
+    cov_at += align_up((size_t)K * (nb1 - nb0) * c.D * c.D * 16);
+    wts_at += align_up((size_t)K * (nb1 - nb0) * d.n_steering * c.D * 8);
+    if (cudaEventRecord(p->slab_join[j], p->slab[j]) != cudaSuccess) st = STAP_ERR_CUDA;
+  }
+  // join every stream that was forked, even after a failed launch
+  for (int i = 0; i < j; ++i)
+    if (cudaStreamWaitEvent(p->stream, p->slab_join[i], 0) != cudaSuccess) st = STAP_ERR_CUDA;
+  return st;
 }
 
 size_t inter_bytes(const Cpi& c) {
@@ -418,6 +497,7 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
   off = align_up(off + max_cov * 16);
   p->wts_off = off;
   off = align_up(off + max_wts * 8);
+  if (n_cpi == 1) off += 2 * kMaxSlabs * kAlign;   // per-slab alignment of cov and wts
   p->run_bytes = off;
   size_t all = p->step_bytes;
   for (const Cpi& c : p->cpis) all += inter_bytes(c);
@@ -482,6 +562,16 @@ stap_status stap_plan_destroy(stap_plan p) {
     cudaEventDestroy(p->fork_ev);
     if (p->cap) cudaStreamDestroy(p->cap);
   }
+  if (p->slab_fork) {
+    for (int i = 0; i < kMaxSlabs; ++i) {
+      if (p->slab[i]) {
+        cudaStreamSynchronize(p->slab[i]);
+        cudaStreamDestroy(p->slab[i]);
+      }
+      if (p->slab_join[i]) cudaEventDestroy(p->slab_join[i]);
+    }
+    cudaEventDestroy(p->slab_fork);
+  }
   // pageable-memory uploads were staged synchronously, so nothing on the
   // device still reads the host tables
   delete p;
@@ -533,8 +623,7 @@ stap_status stap_run_cpi(stap_plan p, const void* const* cubes, float* const* ou
   stap_status st = ready(p, p->run_bytes);
   if (st != STAP_OK) return st;
   if (p->cpis.size() > 1) return run_batched(p, cubes, outs);
-  return do_chain(p, p->cpis[0], cubes[0], outs[0], p->ws + p->dop_off, p->ws + p->cov_off,
-                  p->ws + p->wts_off, p->stream);
+  return run_single(p, cubes[0], outs[0]);
 }
 
 stap_status stap_plan_batch_bytes(stap_plan p, size_t* all_concurrent_bytes) {
@@ -635,6 +724,9 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
     if (p->opt.precision == STAP_PREC_FP32)
       pick([](stap::Tune& t, int v) { t.apply_kind = v; }, {1, 2},
            [&] { return do_apply(p, c, dop, wts, out, p->stream); });
+    if (p->cpis.size() == 1)   // the whole run, pipelined over range slabs or not
+      pick([](stap::Tune& t, int v) { t.slabs = v; }, {1, 2, 4, 8},
+           [&] { return run_single(p, cube, out); });
     for (size_t j = i; j < p->cpis.size(); ++j)
       if (!tuned[j] && same_key(p->cpis[j].d, d)) {
         p->cpis[j].tune = c.tune;
@@ -652,8 +744,8 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
 stap_status stap_plan_get_tuning(stap_plan p, int32_t cpi, int32_t* choices) {
   if (!p || !choices || cpi < 0 || cpi >= (int32_t)p->cpis.size()) return STAP_ERR_INVALID_ARG;
   const stap::Tune& t = p->cpis[cpi].tune;
-  const int32_t v[STAP_TUNING_LEN] = {t.dop_tr, t.cov_kt, t.solve_ts, t.solve_nw, t.solve_lr,
-                                      t.apply_kind};
+  const int32_t v[STAP_TUNING_LEN] = {t.dop_tr, t.cov_kt,   t.solve_ts, t.solve_nw,
+                                      t.solve_lr, t.apply_kind, t.slabs};
   for (int i = 0; i < STAP_TUNING_LEN; ++i) choices[i] = v[i];
   return STAP_OK;
 }
@@ -669,6 +761,7 @@ stap_status stap_plan_set_tuning(stap_plan p, int32_t cpi, const int32_t* choice
   t.solve_nw = choices[3];
   t.solve_lr = choices[4];
   t.apply_kind = choices[5];
+  t.slabs = choices[6];
   drop_graph(p);
   return STAP_OK;
 }

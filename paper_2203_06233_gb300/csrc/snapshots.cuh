@@ -11,7 +11,7 @@
 namespace stap {
 
 __device__ __forceinline__ void stage_snapshots(float2* __restrict__ xs, int ld,
-                                                const float2* __restrict__ dop, int C, int K, int R,
+                                                const float2* __restrict__ dop, int C, int K, int ldr,
                                                 int T, int k, int r_begin, int ncells) {
   // one warp per snapshot row, lanes along range: coalesced, no divisions per element
   const int D = C * T;
@@ -19,7 +19,7 @@ __device__ __forceinline__ void stage_snapshots(float2* __restrict__ xs, int ld,
   for (int d = warp; d < D; d += nw) {
     const int t = d / C, c = d - t * C;
     const int kk = wrap_bin(k + t - T / 2, K);
-    const float2* src = dop + ((size_t)c * K + kk) * R + r_begin;
+    const float2* src = dop + ((size_t)c * K + kk) * ldr + r_begin;
     float2* dst = xs + (size_t)d * ld;
 #pragma unroll 4
     for (int cell = lane; cell < ncells; cell += 32) dst[cell] = __ldg(src + cell);

@@ -32,6 +32,7 @@ struct Tune {
   int solve_nw = 0;    // D <= 32 solve: warps per CTA, 1..4
   int solve_lr = 0;    // D > 32 solve: lanes per right-hand side, 16 (D <= 64) or 32
   int apply_kind = 0;  // FP32 apply: 1 register-resident, 2 general
+  int slabs = 0;       // single-CPI run: range slabs pipelined on prioritised streams, 1..8
 };
 
 // ---------------------------------------------------------------- launchers --
@@ -40,22 +41,22 @@ struct Tune {
 // Hann-windowed DFT over pulses via a two-pass in-register FFT.
 // cube [C][P][R] c64 -> dop [C][K][R] c64; win[P] float; tw[K] = exp(-2 pi i m/K).
 cudaError_t launch_doppler(const float2* cube, float2* dop, const float* win, const float2* tw,
-                           int C, int P, int K, int R, cudaStream_t s, const Tune& t = Tune());
+                           int C, int P, int K, int R, int ldr, cudaStream_t s, const Tune& t = Tune());
 
 // Covariance per (k, block) from the Doppler cube, accumulated error-free in
 // FP32 pairs; written as FP64 complex [K][NB][D][D] (full Hermitian).
-cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K, int R, int T,
-                                   int B, cudaStream_t s, const Tune& t = Tune());
+cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K, int R, int ldr,
+                                   int T, int B, cudaStream_t s, const Tune& t = Tune());
 
 // Same covariance from 3xTF32 tensor-core products (tcgen05), FP32 accumulation.
-cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int T, int B,
-                                 DeviceStatus* status, cudaStream_t s);
+cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int ldr, int T,
+                                 int B, DeviceStatus* status, cudaStream_t s);
 
 // Apply from 3xTF32 tensor-core products; needs B | 128 or 128 | B and at most
 // 128 steering columns per 128-cell tile (apply_tc_supported).
 bool apply_tc_supported(int B, int S);
 cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, int C, int K, int R,
-                            int T, int B, int S, DeviceStatus* status, cudaStream_t s);
+                            int ldr, int T, int B, int S, DeviceStatus* status, cudaStream_t s);
 
 // FP64 loading, Cholesky, solves, refinement and scaling for nsys systems.
 // cov [nsys][D][D] c128 -> wts [nsys][S][D] c64; steer [S][D] c128.  If
@@ -71,7 +72,7 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
 
 // out[s][k][r] = |w^H x|^2; dop [C][K][R] c64, wts [K][NB][S][D] c64, out [S][K][R] f32.
 cudaError_t launch_apply(const float2* dop, const float2* wts, float* out, int C, int K, int R,
-                         int T, int B, int S, cudaStream_t s, const Tune& t = Tune());
+                         int ldr, int T, int B, int S, cudaStream_t s, const Tune& t = Tune());
 
 // ------------------------------------------------------------ device helpers --
 

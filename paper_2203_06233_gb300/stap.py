@@ -40,7 +40,7 @@ EXPORTED = (
     "stap_plan_set_tuning",
 )
 
-STAP_TUNING_LEN = 6
+STAP_TUNING_LEN = 7
 
 # size of the library-owned scratch array used by stap_run_cpi_noalloc
 STAP_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -395,9 +395,11 @@ class Plan:
 
     def _tune_key(self, i: int) -> str:
         d = self.dims[i]
-        return "C%d P%d K%d T%d B%d S%d prec%d ref%d" % (d.n_chan, d.n_pulses, d.n_dop, d.tdof,
-                                                       d.training_block, d.n_steering,
-                                                       self.precision, self.refine_steps)
+        key = "C%d P%d K%d T%d B%d S%d prec%d ref%d" % (d.n_chan, d.n_pulses, d.n_dop, d.tdof,
+                                                      d.training_block, d.n_steering,
+                                                      self.precision, self.refine_steps)
+        # a one-CPI plan also tunes its range slabs, which depend on R
+        return key + (" R%d" % d.n_range if len(self.dims) == 1 else " batch")
 
     def autotune(self, cubes, outs=None, cache_path: Optional[str] = None, reps: int = 3,
                  force: bool = False) -> dict:
@@ -416,7 +418,7 @@ class Plan:
             except (OSError, ValueError):
                 cache = {}
         keys = [self._tune_key(i) for i in range(len(self.dims))]
-        if not force and all(k in cache for k in keys):
+        if not force and all(len(cache.get(k, ())) == STAP_TUNING_LEN for k in keys):
             for i, k in enumerate(keys):
                 stap_plan_set_tuning(self.handle, i, cache[k])
             return {k: cache[k] for k in keys}
