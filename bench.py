@@ -74,13 +74,14 @@ def solve_flops(spec, refine=1, separable=True):
     complex multiply-add): Cholesky D^3/6, then (1 + 2 refine) forward/back
     solve pairs of D^2 each (one solve, then per refinement step a residual
     and a solve) for each right-hand side -- the C basis vectors when the
-    steering set is separable, followed by the S x C combination (S C D) and
-    the S normalisations (D real products each); otherwise the S steering
-    vectors themselves."""
+    steering set is separable, otherwise the S steering vectors, followed by
+    their FP64 normalisations (D real products each).  The separable path's
+    combination of the basis solutions and its normalisations run in
+    double-float on the FP32 pipe and are not FP64 work."""
     C, P, K, R, T, B, S = spec.dims()
     D, NB = C * T, R // B
     if separable:
-        per = 8.0 * (D ** 3 / 6.0 + (1 + 2 * refine) * C * D * D + S * C * D) + 4.0 * S * D
+        per = 8.0 * (D ** 3 / 6.0 + (1 + 2 * refine) * C * D * D)
     else:
         per = 8.0 * (D ** 3 / 6.0 + (1 + 2 * refine) * S * D * D) + 4.0 * S * D
     return K * NB * per

@@ -206,7 +206,7 @@ stap_status stap_run_cpi_noalloc(const stap_dims* dims, const stap_options* opt,
                                  const void* cube_c64, float* out, int64_t* n_failed_systems);
 
 /* Number of launch choices per CPI kept by the autotuner. */
-#define STAP_TUNING_LEN 7
+#define STAP_TUNING_LEN 8
 
 /* Autotune the launch configuration of every distinct CPI shape of the plan
  * (C, P, K, T, B, S; CPIs that differ only in R share one tuning): for each
@@ -215,7 +215,8 @@ stap_status stap_run_cpi_noalloc(const stap_dims* dims, const stap_options* opt,
  * and keeps the fastest.  Candidates: range cells per Doppler CTA (8/16/32);
  * Doppler bins per covariance CTA (plain precision); lanes per system and
  * warps per CTA of the D <= 32 solve, lanes per right-hand side of the larger
- * solve; register-resident or general FP32 apply; for a one-CPI plan, 1, 2, 4
+ * solve, and for D = 8, 12 or 16 the register-resident or the shared-memory
+ * solve kernel; register-resident or general FP32 apply; for a one-CPI plan, 1, 2, 4
  * or 8 pipelined range slabs of the whole run.  Every candidate computes
  * the same result except that the two FP32 apply kernels sum in a different
  * order.  Needs the run workspace; synchronises the plan's stream; overwrites
@@ -227,7 +228,8 @@ stap_status stap_plan_autotune(stap_plan plan, const void* const* cubes, float* 
  * heuristic): Doppler cells per CTA, covariance bins per CTA, solve lanes per
  * system, solve warps per CTA, large-solve lanes per right-hand side, apply
  * kernel (1 register-resident, 2 general), range slabs of a one-CPI
- * stap_run_cpi (at most 8 and NB are used).  set_tuning installs saved choices
+ * stap_run_cpi (at most 8 and NB are used), solve kernel for D = 8, 12, 16
+ * (1 register-resident, 2 shared-memory).  set_tuning installs saved choices
  * (values 0..64; a choice that does not fit a launch falls back to the
  * heuristic). */
 stap_status stap_plan_get_tuning(stap_plan plan, int32_t cpi, int32_t* choices);

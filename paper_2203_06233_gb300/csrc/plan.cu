@@ -699,24 +699,29 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
       const int nrhs = c.separable ? d.n_chan : d.n_steering;
       int base = 1;
       while (base < nrhs && base < 32) base <<= 1;
+      const bool has_reg = c.D == 8 || c.D == 12 || c.D == 16;
       float bt = kNever;
-      int bts = 0, bnw = 0;
-      for (int ts = base; ts <= 32; ts <<= 1)
-        for (int nw = 1; nw <= 4; ++nw) {
-          c.tune.solve_ts = ts;
-          c.tune.solve_nw = nw;
-          const float ms = timeit([&] { return do_solve(p, c, cov, wts, p->stream); });
-          if (ms < bt) {
-            bt = ms;
-            bts = ts;
-            bnw = nw;
+      int bts = 0, bnw = 0, bkind = 0;
+      for (int kind = has_reg ? 1 : 0; kind <= (has_reg ? 2 : 0); ++kind)
+        for (int ts = base; ts <= 32; ts <<= 1)
+          for (int nw = 1; nw <= 4; ++nw) {
+            c.tune.solve_kind = kind;
+            c.tune.solve_ts = ts;
+            c.tune.solve_nw = nw;
+            const float ms = timeit([&] { return do_solve(p, c, cov, wts, p->stream); });
+            if (ms < bt) {
+              bt = ms;
+              bts = ts;
+              bnw = nw;
+              bkind = kind;
+            }
           }
-        }
+      c.tune.solve_kind = bkind;
       c.tune.solve_ts = bts;
       c.tune.solve_nw = bnw;
     } else {
-      std::vector<int> lrs = {32};
-      if (c.D <= 64) lrs.insert(lrs.begin(), 16);
+      std::vector<int> lrs = {16, 32};
+      if (c.D <= 64) lrs.insert(lrs.begin(), 8);
       pick([](stap::Tune& t, int v) { t.solve_lr = v; }, lrs,
            [&] { return do_solve(p, c, cov, wts, p->stream); });
     }
@@ -744,8 +749,8 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
 stap_status stap_plan_get_tuning(stap_plan p, int32_t cpi, int32_t* choices) {
   if (!p || !choices || cpi < 0 || cpi >= (int32_t)p->cpis.size()) return STAP_ERR_INVALID_ARG;
   const stap::Tune& t = p->cpis[cpi].tune;
-  const int32_t v[STAP_TUNING_LEN] = {t.dop_tr, t.cov_kt,   t.solve_ts, t.solve_nw,
-                                      t.solve_lr, t.apply_kind, t.slabs};
+  const int32_t v[STAP_TUNING_LEN] = {t.dop_tr,   t.cov_kt,     t.solve_ts, t.solve_nw,
+                                      t.solve_lr, t.apply_kind, t.slabs,    t.solve_kind};
   for (int i = 0; i < STAP_TUNING_LEN; ++i) choices[i] = v[i];
   return STAP_OK;
 }
@@ -762,6 +767,7 @@ stap_status stap_plan_set_tuning(stap_plan p, int32_t cpi, const int32_t* choice
   t.solve_lr = choices[4];
   t.apply_kind = choices[5];
   t.slabs = choices[6];
+  t.solve_kind = choices[7];
   drop_graph(p);
   return STAP_OK;
 }

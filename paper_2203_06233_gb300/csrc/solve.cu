@@ -37,14 +37,6 @@ namespace {
 
 __device__ __forceinline__ int pidx(int i, int l) { return i * (i + 1) / 2 + l; }
 
-__device__ __forceinline__ void unpack_lower(int q, int& i, int& l) {
-  int r = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-  while (r * (r + 1) / 2 > q) --r;
-  while ((r + 1) * (r + 2) / 2 <= q) ++r;
-  i = r;
-  l = q - r * (r + 1) / 2;
-}
-
 // acc -= a * b
 __device__ __forceinline__ void cfms(double2& acc, double2 a, double2 b) {
   acc.x = fma(-a.x, b.x, acc.x);
@@ -59,6 +51,12 @@ __device__ __forceinline__ void cfms_conj(double2& acc, double2 a, double2 b) {
   acc.x = fma(-a.y, b.y, acc.x);
   acc.y = fma(-a.x, b.y, acc.y);
   acc.y = fma(a.y, b.x, acc.y);
+}
+
+// acc -= d * b for a real d (a diagonal entry of the loaded matrix)
+__device__ __forceinline__ void diag_fms(double2& acc, double d, double2 b) {
+  acc.x = fma(-d, b.x, acc.x);
+  acc.y = fma(-d, b.y, acc.y);
 }
 
 // Lower-triangle element (i, l) of the loaded matrix Rl, i >= l, from the
@@ -92,6 +90,71 @@ __device__ __forceinline__ void chol_solve_inplace(const double2* __restrict__ L
   }
 }
 
+// Step the packed lower-triangle coordinates (i, l), l <= i, of index q to
+// those of q + step (no division).
+__device__ __forceinline__ void step_lower(int& i, int& l, int step) {
+  l += step;
+  while (l > i) {
+    l -= i + 1;
+    ++i;
+  }
+}
+
+// (re, im) as the double-floats (re_hi, re_lo, im_hi, im_lo)
+__device__ __forceinline__ float4 to_ff4(double2 u) {
+  const ff::F2 re = ff::from_double(u.x), im = ff::from_double(u.y);
+  return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+// Separable steering, after the basis solves: u_s = sum_c a_s[c] U_c and
+// w_s = u_s / sqrt(Re v_s^H u_s) for the S steering vectors, lane tl of the
+// team taking s = tl, tl + TS, ...  The combination and the normalisation are
+// not triangular solves; they run in double-float on the FP32 pipe (about
+// 2^-48 relative) from the FP64 basis solutions, which Wt holds as
+// Wt[i * 32 + c] = to_ff4(U_c[i]).  w: the system's weights [S][D] (nullptr:
+// compute nothing to store).
+__device__ __forceinline__ void sep_emit(const float4* Wt, int D, int S, int C, int TS, int tl,
+                                         const float4* __restrict__ steer_ff,
+                                         const float4* __restrict__ sep_a_ff, bool ok,
+                                         float2* __restrict__ w) {
+  auto combine = [&](int s, int i, ff::F2& ur, ff::F2& ui) {
+    const float4* as = sep_a_ff + (size_t)s * C;
+    ur = {0.f, 0.f};
+    ui = {0.f, 0.f};
+    for (int c = 0; c < C; ++c) {
+      const float4 a = __ldg(as + c), x = Wt[i * 32 + c];
+      const ff::F2 ar{a.x, a.y}, ai{a.z, a.w}, xr{x.x, x.y}, xi{x.z, x.w};
+      ur = ff::fms(ff::fma(ur, ar, xr), ai, xi);
+      ui = ff::fma(ff::fma(ui, ar, xi), ai, xr);
+    }
+  };
+  for (int s0 = 0; s0 < S; s0 += TS) {
+    const int s = s0 + tl;
+    if (s < S) {
+      const float4* v = steer_ff + (size_t)s * D;
+      ff::F2 q{0.f, 0.f};                   // Re v^H u
+      for (int i = 0; i < D; ++i) {
+        ff::F2 ur, ui;
+        combine(s, i, ur, ui);
+        const float4 vi = __ldg(v + i);
+        q = ff::fma(ff::fma(q, {vi.x, vi.y}, ur), {vi.z, vi.w}, ui);
+      }
+      const double qd = ff::to_double(q);
+      const bool good = ok && qd > 0.0 && isfinite(qd);
+      const float sf = good ? (float)rsqrt(qd) : 0.f;
+      if (w) {
+        float2* ws = w + (size_t)s * D;
+        for (int i = 0; i < D; ++i) {
+          ff::F2 ur, ui;
+          combine(s, i, ur, ui);
+          ws[i] = good ? make_float2(__fadd_rn(ur.hi, ur.lo) * sf, __fadd_rn(ui.hi, ui.lo) * sf)
+                       : make_float2(0.f, 0.f);
+        }
+      }
+    }
+  }
+}
+
 template <bool SEP>
 __global__ void __launch_bounds__(128)
 solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
@@ -122,10 +185,13 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
     double tr = 0.0;
     for (int j = 0; j < D; ++j) tr += __ldg(&A[(size_t)j * D + j].x);
     const double delta = load_factor * tr * invD;
-    for (int q = tl; q < Dp; q += TS) {
-      int i, l;
-      unpack_lower(q, i, l);
-      L[q] = loaded(A, D, i, l, delta);
+    {
+      int i = 0, l = 0;
+      step_lower(i, l, tl);
+      for (int q = tl; q < Dp; q += TS) {
+        L[q] = loaded(A, D, i, l, delta);
+        step_lower(i, l, TS);
+      }
     }
     __syncwarp();
 
@@ -146,18 +212,33 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       __syncwarp();
       const int m = D - j - 1;
       const int np = m * (m + 1) / 2;
-      for (int q = tl; q < np; q += TS) {
-        int a, b;
-        unpack_lower(q, a, b);
+      // entries (a, b) of the trailing triangle, two per iteration: they only
+      // read column j, which this loop does not write, so both loads go first
+      int a = 0, b = 0;
+      step_lower(a, b, tl);
+      for (int q = tl; q < np; q += 2 * TS) {
+        int a2 = a, b2 = b;
+        step_lower(a2, b2, TS);
+        const bool two = q + TS < np;
         const int i = j + 1 + a, l = j + 1 + b;
-        double2 acc = L[pidx(i, l)];
+        const int i2 = two ? j + 1 + a2 : i, l2 = two ? j + 1 + b2 : l;
+        double2 acc = L[pidx(i, l)], acc2 = L[pidx(i2, l2)];
         const double2 lij = L[pidx(i, j)], llj = L[pidx(l, j)];
+        const double2 lij2 = L[pidx(i2, j)], llj2 = L[pidx(l2, j)];
         // acc -= lij * conj(llj)
         acc.x = fma(-lij.x, llj.x, acc.x);
-        acc.x = fma(-lij.y, llj.y, acc.x);
+        acc2.x = fma(-lij2.x, llj2.x, acc2.x);
         acc.y = fma(-lij.y, llj.x, acc.y);
+        acc2.y = fma(-lij2.y, llj2.x, acc2.y);
+        acc.x = fma(-lij.y, llj.y, acc.x);
+        acc2.x = fma(-lij2.y, llj2.y, acc2.x);
         acc.y = fma(lij.x, llj.y, acc.y);
+        acc2.y = fma(lij2.x, llj2.y, acc2.y);
         L[pidx(i, l)] = acc;
+        if (two) L[pidx(i2, l2)] = acc2;
+        a = a2;
+        b = b2;
+        step_lower(a, b, TS);
       }
       __syncwarp();
       if (tl == 0) {
@@ -210,8 +291,9 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
           // W = b - Rl u  (Rl Hermitian: lower part direct, upper part mirrored)
           for (int i = 0; i < D; ++i) {
             double2 acc = rhs_at(i);
-            for (int l = 0; l <= i; ++l) cfms(acc, loaded(A, D, i, l, delta), U[l * 32]);
-            for (int l = i + 1; l < D; ++l) cfms_conj(acc, loaded(A, D, l, i, delta), U[l * 32]);
+            for (int l = 0; l < i; ++l) cfms(acc, __ldg(A + (size_t)i * D + l), U[l * 32]);
+            diag_fms(acc, __ldg(&A[(size_t)i * D + i].x) + delta, U[i * 32]);
+            for (int l = i + 1; l < D; ++l) cfms_conj(acc, __ldg(A + (size_t)l * D + i), U[l * 32]);
             W[i * 32] = acc;
           }
           chol_solve_inplace(L, invd, W, D);
@@ -224,58 +306,15 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       }
     }
 
-    // ---- SEP: u_s = sum_c a_s[c] U_c (U_c = column of lane team*TS + c) ----
-    // The combination and the normalisation are not triangular solves; they
-    // run in double-float on the FP32 pipe (about 2^-48 relative) from the
-    // FP64 basis solutions: each basis lane first writes its column as
-    // (re_hi, re_lo, im_hi, im_lo) into its W column.
+    // ---- SEP: combine the basis solutions (U_c = column of lane team*TS + c) ----
     if (SEP) {
       __syncwarp();
       float4* Wf = reinterpret_cast<float4*>(W);
       if (tl < C)
-        for (int i = 0; i < D; ++i) {
-          const double2 u = U[i * 32];
-          const ff::F2 re = ff::from_double(u.x), im = ff::from_double(u.y);
-          Wf[i * 32] = make_float4(re.hi, re.lo, im.hi, im.lo);
-        }
+        for (int i = 0; i < D; ++i) Wf[i * 32] = to_ff4(U[i * 32]);
       __syncwarp();
-      const float4* Wt = Wf - lane + team * TS;
-      auto combine = [&](int s, int i, ff::F2& ur, ff::F2& ui) {
-        const float4* as = sep_a_ff + (size_t)s * C;
-        ur = {0.f, 0.f};
-        ui = {0.f, 0.f};
-        for (int c = 0; c < C; ++c) {
-          const float4 a = __ldg(as + c), x = Wt[i * 32 + c];
-          const ff::F2 ar{a.x, a.y}, ai{a.z, a.w}, xr{x.x, x.y}, xi{x.z, x.w};
-          ur = ff::fms(ff::fma(ur, ar, xr), ai, xi);
-          ui = ff::fma(ff::fma(ui, ar, xi), ai, xr);
-        }
-      };
-      for (int s0 = 0; s0 < S; s0 += TS) {
-        const int s = s0 + tl;
-        if (s < S) {
-          const float4* v = steer_ff + (size_t)s * D;
-          ff::F2 q{0.f, 0.f};                   // Re v^H u
-          for (int i = 0; i < D; ++i) {
-            ff::F2 ur, ui;
-            combine(s, i, ur, ui);
-            const float4 vi = __ldg(v + i);
-            q = ff::fma(ff::fma(q, {vi.x, vi.y}, ur), {vi.z, vi.w}, ui);
-          }
-          const double qd = ff::to_double(q);
-          const bool good = ok && qd > 0.0 && isfinite(qd);
-          const float sf = good ? (float)rsqrt(qd) : 0.f;
-          if (valid) {
-            float2* w = wts + ((size_t)sys * S + s) * D;
-            for (int i = 0; i < D; ++i) {
-              ff::F2 ur, ui;
-              combine(s, i, ur, ui);
-              w[i] = good ? make_float2(__fadd_rn(ur.hi, ur.lo) * sf, __fadd_rn(ui.hi, ui.lo) * sf)
-                          : make_float2(0.f, 0.f);
-            }
-          }
-        }
-      }
+      sep_emit(Wf - lane + team * TS, D, S, C, TS, tl, steer_ff, sep_a_ff, ok,
+               valid ? wts + (size_t)sys * S * D : nullptr);
     }
     if (valid && !ok && tl == 0) atomicAdd(&status->n_failed, 1ULL);
     __syncwarp();  // the next batch reuses L, U, W
@@ -283,60 +322,249 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
 }
 
 // ---------------------------------------------------------------------------
+// Register-resident form for the common snapshot lengths (D = 8, 12, 16):
+// the team mapping of solve_kernel, but with D a compile-time constant, every
+// loop over it unrolled, and each lane's right-hand side, solution and
+// residual held in registers.  The substitutions then read nothing but the
+// factor from shared memory, and the compiler interleaves the rows (row i's
+// partial sums start before x_{i-1} is final).  The factor is kept as
+// Rl = Lu Dg Lu^H (unit lower Lu, real pivots Dg): no square roots, and the
+// substitutions scale once, by Dg^{-1}, between the forward and the back
+// pass.  Column j of the elimination divides by the pivot d_j and updates the
+// trailing entries with l_ij conj(a_lj), a_lj the column before the division
+// (= l_lj d_j), kept in a small per-team buffer.
+template <int D, bool SEP>
+__global__ void __launch_bounds__(128, 3)
+solve_reg_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
+                 const double2* __restrict__ steer, const double2* __restrict__ sep_g,
+                 const float4* __restrict__ steer_ff, const float4* __restrict__ sep_a_ff,
+                 long long nsys, int S, int C, int TS, double load_factor, int refine_steps,
+                 DeviceStatus* __restrict__ status) {
+  constexpr int Dp = D * (D + 1) / 2;
+  extern __shared__ double2 sm[];
+  const int nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = 32 / TS, team = lane / TS, tl = lane - team * TS;
+  // per warp: G factors [Dp], G pivot columns [D], (SEP) the [D][32] float4
+  // exchange area for the combination; after all warps: G pivot reciprocals [D]
+  const size_t warp_elems = (size_t)G * (Dp + D) + (SEP ? (size_t)D * 32 : 0);
+  double2* wbase = sm + warp * warp_elems;
+  double2* L = wbase + (size_t)team * Dp;
+  double2* col = wbase + (size_t)G * Dp + (size_t)team * D;
+  float4* Wf = reinterpret_cast<float4*>(wbase + (size_t)G * (Dp + D));
+  double* rdp = reinterpret_cast<double*>(sm + nw * warp_elems) + ((size_t)warp * G + team) * D;
+
+  for (long long base = ((long long)blockIdx.x * nw + warp) * G; base < nsys;
+       base += (long long)gridDim.x * nw * G) {
+    const long long sys = base + team;
+    const bool valid = sys < nsys;
+    const double2* A = cov + (size_t)(valid ? sys : nsys - 1) * D * D;
+
+    // ---- diagonal load and packed copy of Rl ----
+    double tr = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) tr += __ldg(&A[j * D + j].x);
+    const double delta = load_factor * tr * (1.0 / D);
+    {
+      int i = 0, l = 0;
+      step_lower(i, l, tl);
+      for (int q = tl; q < Dp; q += TS) {
+        L[q] = loaded(A, D, i, l, delta);
+        step_lower(i, l, TS);
+      }
+    }
+    __syncwarp();
+
+    // ---- Rl = Lu Dg Lu^H, trailing updates spread over the team ----
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double djj = L[pidx(j, j)].x;
+      if (!(djj > 0.0) || !isfinite(djj)) {
+        ok = false;
+        djj = 1.0;  // keep the control flow uniform; this system's weights become zero
+      }
+      const double rd = 1.0 / djj;
+      for (int i = j + 1 + tl; i < D; i += TS) {
+        const double2 v = L[pidx(i, j)];
+        col[i] = v;
+        L[pidx(i, j)] = make_double2(v.x * rd, v.y * rd);
+      }
+      __syncwarp();
+      const int m = D - 1 - j, np = m * (m + 1) / 2;
+      int a = 0, b = 0;
+      step_lower(a, b, tl);
+      for (int q = tl; q < np; q += TS) {
+        const int i = j + 1 + a, l = j + 1 + b;
+        double2 acc = L[pidx(i, l)];
+        const double2 lij = L[pidx(i, j)], alj = col[l];
+        // acc -= lij * conj(alj)
+        acc.x = fma(-lij.x, alj.x, acc.x);
+        acc.x = fma(-lij.y, alj.y, acc.x);
+        acc.y = fma(-lij.y, alj.x, acc.y);
+        acc.y = fma(lij.x, alj.y, acc.y);
+        L[pidx(i, l)] = acc;
+        step_lower(a, b, TS);
+      }
+      if (tl == 0) rdp[j] = rd;
+      __syncwarp();
+    }
+
+    // x <- Rl^{-1} x: Lu z = x, y = Dg^{-1} z, Lu^H x = y.  The warp
+    // barriers between rows keep the compiler from hoisting every load of
+    // the factor to the top (it would hold them all in registers and spill);
+    // every lane of the warp runs them (see the pass loop below).
+    auto ldl_solve = [&](double2 (&x)[D]) {
+#pragma unroll
+      for (int i = 1; i < D; ++i) {
+#pragma unroll
+        for (int l = 0; l < i; ++l) cfms(x[i], L[pidx(i, l)], x[l]);
+        __syncwarp();
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const double r = rdp[i];
+        x[i].x *= r;
+        x[i].y *= r;
+      }
+#pragma unroll
+      for (int i = D - 2; i >= 0; --i) {
+#pragma unroll
+        for (int l = i + 1; l < D; ++l) cfms_conj(x[i], L[pidx(l, i)], x[l]);
+        __syncwarp();
+      }
+    };
+
+    // ---- per-lane solves: one right-hand side per lane and pass ----
+    // Lanes past the last right-hand side solve a copy of the first one and
+    // store nothing, so that the whole warp reaches the barriers together.
+    const int nrhs = SEP ? C : S;
+    for (int r0 = 0; r0 < nrhs; r0 += TS) {
+      const bool live = r0 + tl < nrhs;
+      const int rhs = live ? r0 + tl : 0;
+      {
+        auto rhs_at = [&](int i) -> double2 {
+          if (SEP) {
+            const int t = i / C;
+            return (i - t * C == rhs) ? __ldg(sep_g + t) : make_double2(0.0, 0.0);
+          }
+          return __ldg(steer + (size_t)rhs * D + i);
+        };
+        double2 u[D], r[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) u[i] = rhs_at(i);
+        ldl_solve(u);
+        for (int it = 0; it < refine_steps; ++it) {
+          // r = b - Rl u  (Rl Hermitian: lower part direct, upper part mirrored)
+#pragma unroll
+          for (int i = 0; i < D; ++i) {
+            double2 acc = rhs_at(i);
+#pragma unroll
+            for (int l = 0; l < i; ++l) cfms(acc, __ldg(A + i * D + l), u[l]);
+            diag_fms(acc, __ldg(&A[i * D + i].x) + delta, u[i]);
+#pragma unroll
+            for (int l = i + 1; l < D; ++l) cfms_conj(acc, __ldg(A + l * D + i), u[l]);
+            r[i] = acc;
+            __syncwarp();
+          }
+          ldl_solve(r);
+#pragma unroll
+          for (int i = 0; i < D; ++i) {
+            u[i].x += r[i].x;
+            u[i].y += r[i].y;
+          }
+        }
+        if (SEP) {
+          if (live)
+#pragma unroll
+            for (int i = 0; i < D; ++i) Wf[i * 32 + lane] = to_ff4(u[i]);
+        } else {
+          const double2* v = steer + (size_t)rhs * D;
+          double q = 0.0;
+#pragma unroll
+          for (int i = 0; i < D; ++i) {
+            const double2 vi = __ldg(v + i);
+            q = fma(vi.x, u[i].x, q);
+            q = fma(vi.y, u[i].y, q);
+          }
+          const bool good = ok && q > 0.0 && isfinite(q);
+          const float sf = good ? (float)rsqrt(q) : 0.f;
+          if (valid && live) {
+            float2* w = wts + ((size_t)sys * S + rhs) * D;
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+              w[i] = good ? make_float2((float)u[i].x * sf, (float)u[i].y * sf) : make_float2(0.f, 0.f);
+          }
+        }
+      }
+    }
+    if (SEP) {
+      __syncwarp();
+      sep_emit(Wf + team * TS, D, S, C, TS, tl, steer_ff, sep_a_ff, ok,
+               valid ? wts + (size_t)sys * S * D : nullptr);
+    }
+    if (valid && !ok && tl == 0) atomicAdd(&status->n_failed, 1ULL);
+    __syncwarp();  // the next batch reuses L, col, Wf
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Larger systems (32 < D <= 128).  The per-lane layout above needs two D-long
 // FP64 vectors per lane, which stops fitting next to the factor, so here one
-// CTA of 4 warps owns one system at a time and the lanes own ROWS:
-//  * L (column-major packed lower triangle) lives in shared memory; the
-//    Cholesky is right-looking with the trailing update of each column spread
-//    over all 128 threads.
+// CTA of 4 (or 8) warps owns one system at a time and the lanes own ROWS:
+//  * The factor lives in shared memory as Rl = Lu Dg Lu^H (unit lower Lu,
+//    column-major packed, and the pivot reciprocals 1/d_j).  The elimination
+//    is right-looking with the trailing update of each column spread over
+//    all threads; it divides column j by d_j and updates with l_ij conj(a_lj),
+//    a_lj the column before the division.  The thread that updates the next
+//    pivot also forms its reciprocal, so no square root and one division per
+//    column.
 //  * A group of LR lanes (LR = 32, or 16 for D <= 64 so that a warp carries
 //    two right-hand sides) solves one right-hand side at a time; lane l of
 //    the group keeps rows l, l + LR, l + 2 LR, l + 3 LR of its vectors in
 //    registers.  Substitution goes column by column: the owner of row j
-//    finishes y_j, a shuffle broadcasts it, and the group updates its rows
-//    below (above, for L^H).
+//    holds x_j, a shuffle broadcasts it, and the group updates its rows below
+//    (above, for Lu^H); with a unit diagonal there is no per-column scaling,
+//    only one Dg^{-1} scaling of every row between the two passes.
 //  * The residual b - Rl u reads Rl from the input through L1: for each
 //    column index l every lane takes A[i][l] (i >= l) or conj(A[l][i]) (i < l)
 //    by a select, so all lanes run every DFMA.
-//  * Separable steering: the C basis solutions are kept in shared memory and
-//    combined per steering vector by lanes over rows.
-constexpr int kBigRPL = 4;          // rows per lane: D <= LR * kBigRPL
+//  * Separable steering: the C basis solutions are kept in shared memory as
+//    double-floats and combined per steering vector, with the normalisation,
+//    on the FP32 pipe (as in the small-system kernels).
 
 __device__ __forceinline__ int colstart(int l, int D) { return l * D - l * (l - 1) / 2; }
 
-// In-place forward (L y = x) or back (L^H y = x) substitution of one vector
-// held as rows li + LR q by the LR lanes of group `grp` (li = lane % LR).
-template <int LR, bool BACK>
-__device__ __forceinline__ void big_subst(double2 (&x)[kBigRPL], const double2* __restrict__ Lc,
-                                          const double* __restrict__ invd, int D, int li, int grp) {
+// In-place forward (Lu z = x) or back (Lu^H z = x) substitution with the unit
+// lower factor, of one vector held as rows li + LR q by the LR lanes of group
+// `grp` (li = lane % LR).
+template <int LR, int RPL, bool BACK>
+__device__ __forceinline__ void big_subst(double2 (&x)[RPL], const double2* __restrict__ Lc,
+                                          int D, int li, int grp) {
   for (int jj = 0; jj < D; ++jj) {
     const int j = BACK ? D - 1 - jj : jj;
     const int owner = (j % LR) + grp * LR, qj = j / LR;
     double2 pick = x[0];
 #pragma unroll
-    for (int q = 1; q < kBigRPL; ++q)
+    for (int q = 1; q < RPL; ++q)
       if (q == qj) pick = x[q];
     double2 yj;
     yj.x = __shfl_sync(0xffffffffu, pick.x, owner);
     yj.y = __shfl_sync(0xffffffffu, pick.y, owner);
-    const double s = invd[j];
-    yj.x *= s;
-    yj.y *= s;
 #pragma unroll
-    for (int q = 0; q < kBigRPL; ++q) {
-      if (q == qj && li == j % LR) x[q] = yj;
+    for (int q = 0; q < RPL; ++q) {
       const bool touch = (BACK ? (q <= qj) : (q >= qj)) && LR * q < D;   // warp-uniform
       if (touch) {
         const int i = li + LR * q;
         const bool act = BACK ? (i < j) : (i > j && i < D);
         if (act) {
-          if (BACK) {  // x_i -= conj(L[j][i]) y_j
+          if (BACK) {  // x_i -= conj(Lu[j][i]) x_j
             const double2 l = Lc[colstart(i, D) + j - i];
             x[q].x = fma(-l.x, yj.x, x[q].x);
             x[q].x = fma(-l.y, yj.y, x[q].x);
             x[q].y = fma(-l.x, yj.y, x[q].y);
             x[q].y = fma(l.y, yj.x, x[q].y);
-          } else {     // x_i -= L[i][j] y_j
+          } else {     // x_i -= Lu[i][j] x_j
             const double2 l = Lc[colstart(j, D) + i - j];
             x[q].x = fma(-l.x, yj.x, x[q].x);
             x[q].x = fma(l.y, yj.y, x[q].x);
@@ -349,30 +577,59 @@ __device__ __forceinline__ void big_subst(double2 (&x)[kBigRPL], const double2* 
   }
 }
 
+// x <- Rl^{-1} x with Rl = Lu Dg Lu^H (rd: the pivot reciprocals).
+template <int LR, int RPL>
+__device__ __forceinline__ void big_solve(double2 (&x)[RPL], const double2* __restrict__ Lc,
+                                          const double* __restrict__ rd, int D, int li, int grp) {
+  big_subst<LR, RPL, false>(x, Lc, D, li, grp);
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    if (LR * q < D) {
+      const int i = li + LR * q;
+      const double r = rd[i < D ? i : D - 1];
+      x[q].x *= r;
+      x[q].y *= r;
+    }
+  }
+  big_subst<LR, RPL, true>(x, Lc, D, li, grp);
+}
+
 template <int LR>
 __device__ __forceinline__ double group_sum(double v) {
   for (int o = LR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-template <bool SEP, int LR, int NT>
+template <bool SEP, int LR, int NT, int RPL>
 __global__ void __launch_bounds__(NT)
 solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
                  const double2* __restrict__ steer, const double2* __restrict__ sep_g,
-                 const double2* __restrict__ sep_a, long long nsys, int D, int S, int C,
-                 double load_factor, int refine_steps, DeviceStatus* __restrict__ status) {
+                 const float4* __restrict__ steer_ff, const float4* __restrict__ sep_a_ff,
+                 long long nsys, int D, int S, int C, double load_factor, int refine_steps,
+                 DeviceStatus* __restrict__ status) {
   extern __shared__ double2 sm[];
   constexpr int NW = NT / 32;
   constexpr int NG = NT / LR;                      // right-hand sides in flight per CTA
   const int Dp = D * (D + 1) / 2;
-  double2* Lc = sm;                                  // [Dp] column-major packed
-  double2* Ub = Lc + Dp;                             // SEP: [C][D] basis solutions
-  double2* uv = Ub + (SEP ? (size_t)C * D : 0);      // [NG][D] broadcast vectors
-  double* invd = reinterpret_cast<double*>(uv + (size_t)NG * D);   // [D]
+  double2* Lc = sm;                                  // [Dp] Lu, column-major packed
+  double2* colb = Lc + Dp;                           // [D] pivot column before division
+  float4* Ubf = reinterpret_cast<float4*>(colb + D); // SEP: [C][D] basis solutions (double-float)
+  double2* uv = colb + D + (SEP ? (size_t)C * D : 0);   // [NG][D] broadcast vectors
+  double* rd = reinterpret_cast<double*>(uv + (size_t)NG * D);   // [D] pivot reciprocals
+  int* okf = reinterpret_cast<int*>(rd + D);                     // pivots all positive
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int li = lane % LR, grp = lane / LR;         // lane in group, group in warp
   const int g = warp * (32 / LR) + grp;              // group in CTA
   const double invD = 1.0 / (double)D;
+
+  // pivot d -> reciprocal, recording a pivot that is not positive and finite
+  auto pivot = [&](double d) -> double {
+    if (!(d > 0.0) || !isfinite(d)) {
+      *okf = 0;
+      return 1.0;  // keep going; this system's weights become zero
+    }
+    return 1.0 / d;
+  };
 
   for (long long sys = blockIdx.x; sys < nsys; sys += gridDim.x) {
     const double2* A = cov + (size_t)sys * D * D;
@@ -381,55 +638,66 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
     const double delta = load_factor * tr * invD;
     for (int i = warp; i < D; i += NW)                 // rows of A, coalesced
       for (int l = lane; l <= i; l += 32) Lc[colstart(l, D) + i - l] = loaded(A, D, i, l, delta);
+    if (tid == 0) {
+      *okf = 1;
+      rd[0] = pivot(__ldg(&A[0].x) + delta);
+    }
     __syncthreads();
 
-    bool ok = true;
     for (int j = 0; j < D; ++j) {
       const int cj = colstart(j, D);
-      double djj = Lc[cj].x;
-      if (!(djj > 0.0) || !isfinite(djj)) {
-        ok = false;
-        djj = 1.0;
-      }
-      const double inv = rsqrt(djj);
-      const double ljj = djj * inv;
+      const double rj = rd[j];
       for (int i = j + 1 + tid; i < D; i += NT) {
         const double2 v = Lc[cj + i - j];
-        Lc[cj + i - j] = make_double2(v.x * inv, v.y * inv);
+        colb[i] = v;
+        Lc[cj + i - j] = make_double2(v.x * rj, v.y * rj);
       }
       __syncthreads();
-      // trailing update, pairs (i, l) with j < l <= i, column-major order
+      // trailing update, pairs (i, l) with j < l <= i, column-major order:
+      // column a of the trailing triangle holds m - a entries; a thread steps
+      // through its entries (a, off) NT at a time, two per iteration (they
+      // only read column j and colb, which this loop does not write).  Entry
+      // (j+1, j+1) is thread 0's first: it then forms the next pivot's
+      // reciprocal.
       const int m = D - j - 1;
       const int np = m * (m + 1) / 2;
-      for (int q = tid; q < np; q += NT) {
-        // column a of the trailing triangle holds m - a entries
-        const float fm = 2.0f * m + 1.0f;
-        int a = (int)((fm - sqrtf(fm * fm - 8.0f * (float)q)) * 0.5f);
-        while (a > 0 && a * m - a * (a - 1) / 2 > q) --a;
-        while ((a + 1) * m - (a + 1) * a / 2 <= q) ++a;
-        const int off = q - (a * m - a * (a - 1) / 2);
+      int a = 0, off = tid;
+      while (a < m && off >= m - a) off -= m - a++;
+      for (int q = tid; q < np; q += 2 * NT) {
+        int a2 = a, off2 = off + NT;
+        while (a2 < m && off2 >= m - a2) off2 -= m - a2++;
+        const bool two = q + NT < np;
         const int l = j + 1 + a, i = l + off;
-        const double2 lij = Lc[cj + i - j], llj = Lc[cj + l - j];
-        double2 acc = Lc[colstart(l, D) + i - l];
-        acc.x = fma(-lij.x, llj.x, acc.x);
-        acc.x = fma(-lij.y, llj.y, acc.x);
-        acc.y = fma(-lij.y, llj.x, acc.y);
-        acc.y = fma(lij.x, llj.y, acc.y);
+        const int l2 = two ? j + 1 + a2 : l, i2 = two ? l2 + off2 : i;
+        const double2 lij = Lc[cj + i - j], alj = colb[l];
+        const double2 lij2 = Lc[cj + i2 - j], alj2 = colb[l2];
+        double2 acc = Lc[colstart(l, D) + i - l], acc2 = Lc[colstart(l2, D) + i2 - l2];
+        // acc -= lij * conj(alj)
+        acc.x = fma(-lij.x, alj.x, acc.x);
+        acc2.x = fma(-lij2.x, alj2.x, acc2.x);
+        acc.y = fma(-lij.y, alj.x, acc.y);
+        acc2.y = fma(-lij2.y, alj2.x, acc2.y);
+        acc.x = fma(-lij.y, alj.y, acc.x);
+        acc2.x = fma(-lij2.y, alj2.y, acc2.x);
+        acc.y = fma(lij.x, alj.y, acc.y);
+        acc2.y = fma(lij2.x, alj2.y, acc2.y);
         Lc[colstart(l, D) + i - l] = acc;
-      }
-      if (tid == 0) {
-        Lc[cj] = make_double2(ljj, 0.0);
-        invd[j] = inv;
+        if (two) Lc[colstart(l2, D) + i2 - l2] = acc2;
+        if (q == 0) rd[j + 1] = pivot(acc.x);
+        a = a2;
+        off = off2 + NT;
+        while (a < m && off >= m - a) off -= m - a++;
       }
       __syncthreads();
     }
+    const bool ok = *okf != 0;
 
     // weights of steering vector s from u (rows li + LR q): group-wide
-    auto emit = [&](int s, const double2 (&u)[kBigRPL]) {
+    auto emit = [&](int s, const double2 (&u)[RPL]) {
       const double2* v = steer + (size_t)s * D;
       double qp = 0.0;
 #pragma unroll
-      for (int q = 0; q < kBigRPL; ++q) {
+      for (int q = 0; q < RPL; ++q) {
         const int i = li + LR * q;
         if (i < D) {
           const double2 vi = __ldg(v + i);
@@ -442,7 +710,7 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       const double scale = good ? rsqrt(qs) : 0.0;
       float2* w = wts + ((size_t)sys * S + s) * D;
 #pragma unroll
-      for (int q = 0; q < kBigRPL; ++q) {
+      for (int q = 0; q < RPL; ++q) {
         const int i = li + LR * q;
         if (i < D)
           w[i] = good ? make_float2((float)(u[q].x * scale), (float)(u[q].y * scale))
@@ -456,9 +724,9 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       const int rhs = r0 + g;
       const bool live = rhs < nrhs;
       const int rsafe = live ? rhs : 0;
-      double2 b[kBigRPL], u[kBigRPL], r[kBigRPL];
+      double2 b[RPL], u[RPL], r[RPL];
 #pragma unroll
-      for (int q = 0; q < kBigRPL; ++q) {
+      for (int q = 0; q < RPL; ++q) {
         const int i = li + LR * q;
         double2 v = make_double2(0.0, 0.0);
         if (i < D) {
@@ -472,30 +740,27 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
         b[q] = v;
         u[q] = v;
       }
-      big_subst<LR, false>(u, Lc, invd, D, li, grp);
-      big_subst<LR, true>(u, Lc, invd, D, li, grp);
+      big_solve<LR, RPL>(u, Lc, rd, D, li, grp);
       for (int it = 0; it < refine_steps; ++it) {
-        // r = b - Rl u
+        // r = b - R u - delta u  (R Hermitian: A[i][l] for i >= l, conj(A[l][i])
+        // above, real diagonal; the load is applied after the sweep)
 #pragma unroll
-        for (int q = 0; q < kBigRPL; ++q)
+        for (int q = 0; q < RPL; ++q)
           if (li + LR * q < D) uv[g * D + li + LR * q] = u[q];
         __syncwarp();
 #pragma unroll
-        for (int q = 0; q < kBigRPL; ++q) r[q] = b[q];
+        for (int q = 0; q < RPL; ++q) r[q] = b[q];
+#pragma unroll 4
         for (int l = 0; l < D; ++l) {
           const double2 ul = uv[g * D + l];
 #pragma unroll
-          for (int q = 0; q < kBigRPL; ++q) {
+          for (int q = 0; q < RPL; ++q) {
             if (LR * q < D) {               // warp-uniform: some lane has a row here
               const int i = li + LR * q;
               const int ic = i < D ? i : D - 1;
               const bool low = ic >= l;
               const double2 a = __ldg(low ? A + (size_t)ic * D + l : A + (size_t)l * D + ic);
-              double ax = a.x, ay = low ? a.y : -a.y;     // Rl[i][l]
-              if (ic == l) {
-                ax += delta;
-                ay = 0.0;
-              }
+              const double ax = a.x, ay = ic == l ? 0.0 : (low ? a.y : -a.y);   // R[i][l]
               r[q].x = fma(-ax, ul.x, r[q].x);
               r[q].x = fma(ay, ul.y, r[q].x);
               r[q].y = fma(-ax, ul.y, r[q].y);
@@ -503,11 +768,17 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
             }
           }
         }
-        __syncwarp();
-        big_subst<LR, false>(r, Lc, invd, D, li, grp);
-        big_subst<LR, true>(r, Lc, invd, D, li, grp);
 #pragma unroll
-        for (int q = 0; q < kBigRPL; ++q) {
+        for (int q = 0; q < RPL; ++q) {
+          if (LR * q < D) {
+            r[q].x = fma(-delta, u[q].x, r[q].x);
+            r[q].y = fma(-delta, u[q].y, r[q].y);
+          }
+        }
+        __syncwarp();
+        big_solve<LR, RPL>(r, Lc, rd, D, li, grp);
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
           u[q].x += r[q].x;
           u[q].y += r[q].y;
         }
@@ -515,56 +786,96 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       if (live) {
         if (SEP) {
 #pragma unroll
-          for (int q = 0; q < kBigRPL; ++q)
-            if (li + LR * q < D) Ub[(size_t)rhs * D + li + LR * q] = u[q];
+          for (int q = 0; q < RPL; ++q)
+            if (li + LR * q < D) Ubf[(size_t)rhs * D + li + LR * q] = to_ff4(u[q]);
         } else {
           emit(rhs, u);
         }
       }
     }
     if (SEP) {
+      // u_s = sum_c a_s[c] U_c and its normalisation in double-float on the
+      // FP32 pipe; the group's partial Re v^H u is summed in FP64
       __syncthreads();
       for (int s0 = 0; s0 < S; s0 += NG) {
         const int s = s0 + g;
         const int ssafe = s < S ? s : 0;
-        const double2* as = sep_a + (size_t)ssafe * C;
-        double2 u[kBigRPL];
+        const float4* as = sep_a_ff + (size_t)ssafe * C;
+        ff::F2 ur[RPL], ui[RPL];
 #pragma unroll
-        for (int q = 0; q < kBigRPL; ++q) u[q] = make_double2(0.0, 0.0);
+        for (int q = 0; q < RPL; ++q) ur[q] = ui[q] = ff::F2{0.f, 0.f};
         for (int c = 0; c < C; ++c) {
-          const double2 a = __ldg(as + c);
+          const float4 a = __ldg(as + c);
+          const ff::F2 ar{a.x, a.y}, ai{a.z, a.w};
 #pragma unroll
-          for (int q = 0; q < kBigRPL; ++q) {
+          for (int q = 0; q < RPL; ++q) {
             if (LR * q < D) {
               const int i = li + LR * q;
-              const double2 x = Ub[(size_t)c * D + (i < D ? i : D - 1)];
-              u[q].x = fma(a.x, x.x, u[q].x);
-              u[q].x = fma(-a.y, x.y, u[q].x);
-              u[q].y = fma(a.x, x.y, u[q].y);
-              u[q].y = fma(a.y, x.x, u[q].y);
+              const float4 x = Ubf[(size_t)c * D + (i < D ? i : D - 1)];
+              const ff::F2 xr{x.x, x.y}, xi{x.z, x.w};
+              ur[q] = ff::fms(ff::fma(ur[q], ar, xr), ai, xi);
+              ui[q] = ff::fma(ff::fma(ui[q], ar, xi), ai, xr);
             }
           }
         }
-        if (s < S) emit(s, u);
+        const float4* v = steer_ff + (size_t)ssafe * D;
+        ff::F2 qp{0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const int i = li + LR * q;
+          if (i < D) {
+            const float4 vi = __ldg(v + i);
+            qp = ff::fma(ff::fma(qp, {vi.x, vi.y}, ur[q]), {vi.z, vi.w}, ui[q]);
+          }
+        }
+        const double qs = group_sum<LR>(ff::to_double(qp));
+        const bool good = ok && qs > 0.0 && isfinite(qs);
+        const float sf = good ? (float)rsqrt(qs) : 0.f;
+        if (s < S) {
+          float2* w = wts + ((size_t)sys * S + s) * D;
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            const int i = li + LR * q;
+            if (i < D)
+              w[i] = good ? make_float2(__fadd_rn(ur[q].hi, ur[q].lo) * sf,
+                                        __fadd_rn(ui[q].hi, ui[q].lo) * sf)
+                          : make_float2(0.f, 0.f);
+          }
+        }
       }
     }
     if (!ok && tid == 0) atomicAdd(&status->n_failed, 1ULL);
-    __syncthreads();  // the next system reuses Lc, Ub
+    __syncthreads();  // the next system reuses Lc, colb, Ubf, rd
   }
 }
 
-template <bool SEP, int LR, int NT>
+template <bool SEP, int LR, int NT, int RPL>
 cudaError_t launch_big(const double2* cov, float2* wts, const double2* steer, const double2* sep_g,
-                       const double2* sep_a, long long nsys, int D, int S, int C, double lf,
-                       int refine, DeviceStatus* status, size_t smem, cudaStream_t s) {
+                       const float4* steer_ff, const float4* sep_a_ff, long long nsys, int D, int S,
+                       int C, double lf, int refine, DeviceStatus* status, size_t smem,
+                       cudaStream_t s) {
   static int set_bytes[64] = {0};
-  cudaError_t e = ensure_smem(solve_big_kernel<SEP, LR, NT>, smem, set_bytes);
+  cudaError_t e = ensure_smem(solve_big_kernel<SEP, LR, NT, RPL>, smem, set_bytes);
   if (e != cudaSuccess) return e;
   const int per_sm = (int)(228 * 1024 / (smem + 1024));
   long long blocks = 152LL * (per_sm < 1 ? 1 : per_sm) * 2;
   if (blocks > nsys) blocks = nsys;
-  solve_big_kernel<SEP, LR, NT><<<(unsigned)blocks, NT, smem, s>>>(
-      cov, wts, steer, sep_g, sep_a, nsys, D, S, C, lf, refine, status);
+  solve_big_kernel<SEP, LR, NT, RPL><<<(unsigned)blocks, NT, smem, s>>>(
+      cov, wts, steer, sep_g, steer_ff, sep_a_ff, nsys, D, S, C, lf, refine, status);
+  return cudaGetLastError();
+}
+
+template <int D, bool SEP>
+cudaError_t launch_reg(const double2* cov, float2* wts, const double2* steer, const double2* sep_g,
+                       const float4* steer_ff, const float4* sep_a_ff, long long nsys, int S, int C,
+                       int TS, int nw, long long blocks, size_t smem, double lf, int refine,
+                       DeviceStatus* status, cudaStream_t s) {
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  static int set_bytes[64] = {0};
+  cudaError_t e = ensure_smem(solve_reg_kernel<D, SEP>, smem, set_bytes);
+  if (e != cudaSuccess) return e;
+  solve_reg_kernel<D, SEP><<<(unsigned)blocks, nw * 32, smem, s>>>(
+      cov, wts, steer, sep_g, steer_ff, sep_a_ff, nsys, S, C, TS, lf, refine, status);
   return cudaGetLastError();
 }
 
@@ -586,29 +897,35 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
   const bool sep = sep_g != nullptr && sep_a != nullptr && steer_ff != nullptr && sep_a_ff != nullptr &&
                    C >= 1 && C <= 32 && D % C == 0;
   if (D > kSmallMaxD) {  // one system per CTA, lanes over rows
-    if (D > 32 * kBigRPL) return cudaErrorInvalidValue;
-    // 16 lanes per right-hand side (two per warp) up to D = 64 with 4 warps
-    // (several CTAs per SM); above that 32 lanes and 8 warps sharing one factor
-    int LR = D <= 16 * kBigRPL ? 16 : 32;
-    if (tn.solve_lr == 32 || (tn.solve_lr == 16 && D <= 16 * kBigRPL)) LR = tn.solve_lr;
-    const int NT = LR == 16 ? 128 : 256;
+    // LR lanes per right-hand side, each holding RPL rows (D <= LR * RPL):
+    //   LR = 8:  RPL 8, 4 warps (D <= 64)
+    //   LR = 16: RPL 4, 4 warps (D <= 64) or RPL 8, 8 warps (D <= 128)
+    //   LR = 32: RPL 4, 8 warps
+    // default: 16 up to D = 64 (several CTAs per SM), 32 above
+    int LR = D <= 64 ? 16 : 32;
+    if (tn.solve_lr == 32 || tn.solve_lr == 16 || (tn.solve_lr == 8 && D <= 64)) LR = tn.solve_lr;
+    const int NT = (LR == 8 || (LR == 16 && D <= 64)) ? 128 : 256;
     const size_t Dp = (size_t)D * (D + 1) / 2;
     const size_t ng = NT / LR;
+    // Lu, pivot column, (SEP) basis solutions, broadcast vectors; pivot
+    // reciprocals and the pivot flag
     auto bytes = [&](bool with_u) {
-      return (Dp + (with_u ? (size_t)C * D : 0) + ng * D) * sizeof(double2) + D * sizeof(double);
+      return (Dp + D + (with_u ? (size_t)C * D : 0) + ng * D) * sizeof(double2) +
+             D * sizeof(double) + 16;
     };
     const bool sep_big = sep && bytes(true) <= 227 * 1024;
     const size_t smem = bytes(sep_big);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    if (LR == 16)
-      return sep_big ? launch_big<true, 16, 128>(cov, wts, steer, sep_g, sep_a, nsys, D, S, C,
-                                                 load_factor, refine_steps, status, smem, s)
-                     : launch_big<false, 16, 128>(cov, wts, steer, nullptr, nullptr, nsys, D, S, C,
-                                                  load_factor, refine_steps, status, smem, s);
-    return sep_big ? launch_big<true, 32, 256>(cov, wts, steer, sep_g, sep_a, nsys, D, S, C,
-                                               load_factor, refine_steps, status, smem, s)
-                   : launch_big<false, 32, 256>(cov, wts, steer, nullptr, nullptr, nsys, D, S, C,
-                                                load_factor, refine_steps, status, smem, s);
+#define STAP_BIG(lr, nt, rpl)                                                                     \
+  return sep_big ? launch_big<true, lr, nt, rpl>(cov, wts, steer, sep_g, steer_ff, sep_a_ff, nsys, D,  \
+                                                 S, C, load_factor, refine_steps, status, smem, s)   \
+                 : launch_big<false, lr, nt, rpl>(cov, wts, steer, nullptr, nullptr, nullptr, nsys, D, \
+                                                  S, C, load_factor, refine_steps, status, smem, s)
+    if (LR == 8) STAP_BIG(8, 128, 8);
+    if (LR == 16 && NT == 128) STAP_BIG(16, 128, 4);
+    if (LR == 16) STAP_BIG(16, 256, 8);
+    STAP_BIG(32, 256, 4);
+#undef STAP_BIG
   }
   constexpr size_t kBudget = 200 * 1024;
   const int Dp = D * (D + 1) / 2;
@@ -621,6 +938,34 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
     const int G = 32 / ts;
     return ((size_t)G * Dp + 2 * (size_t)D * 32) * sizeof(double2) + (size_t)G * D * sizeof(double);
   };
+  // register-resident kernel for D = 8, 12, 16 unless the tuning asks for the generic one
+  const bool reg = (D == 8 || D == 12 || D == 16) && tn.solve_kind != 2;
+  auto reg_bytes = [&](int ts) {
+    const int G = 32 / ts;
+    return ((size_t)G * (Dp + D) + (sep ? (size_t)D * 32 : 0)) * sizeof(double2) +
+           (size_t)G * D * sizeof(double);
+  };
+  if (reg) {
+    while (TS < 32 && reg_bytes(TS) * 4 > kBudget) TS <<= 1;
+    if (tn.solve_ts >= TS && tn.solve_ts <= 32 && (tn.solve_ts & (tn.solve_ts - 1)) == 0)
+      TS = tn.solve_ts;
+    int nw = 4;
+    while (nw > 1 && reg_bytes(TS) * nw > kBudget) --nw;
+    if (tn.solve_nw >= 1 && tn.solve_nw <= nw) nw = tn.solve_nw;
+    const size_t smem = reg_bytes(TS) * nw;
+    const int G = 32 / TS;
+    const long long batches = (nsys + G - 1) / G;
+    long long blocks = (batches + nw - 1) / nw;
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    switch (D) {
+      case 8: return sep ? launch_reg<8, true>(cov, wts, steer, sep_g, steer_ff, sep_a_ff, nsys, S, C, TS, nw, blocks, smem, load_factor, refine_steps, status, s)
+                         : launch_reg<8, false>(cov, wts, steer, nullptr, nullptr, nullptr, nsys, S, C, TS, nw, blocks, smem, load_factor, refine_steps, status, s);
+      case 12: return sep ? launch_reg<12, true>(cov, wts, steer, sep_g, steer_ff, sep_a_ff, nsys, S, C, TS, nw, blocks, smem, load_factor, refine_steps, status, s)
+                          : launch_reg<12, false>(cov, wts, steer, nullptr, nullptr, nullptr, nsys, S, C, TS, nw, blocks, smem, load_factor, refine_steps, status, s);
+      default: return sep ? launch_reg<16, true>(cov, wts, steer, sep_g, steer_ff, sep_a_ff, nsys, S, C, TS, nw, blocks, smem, load_factor, refine_steps, status, s)
+                          : launch_reg<16, false>(cov, wts, steer, nullptr, nullptr, nullptr, nsys, S, C, TS, nw, blocks, smem, load_factor, refine_steps, status, s);
+    }
+  }
   while (TS < 32 && warp_bytes(TS) * 4 > kBudget) TS <<= 1;
   if (tn.solve_ts >= TS && tn.solve_ts <= 32 && (tn.solve_ts & (tn.solve_ts - 1)) == 0)
     TS = tn.solve_ts;

@@ -1,0 +1,60 @@
+"""Run a few whole-CPI steps of one workload for a profiler.
+
+    python -m paper_2203_06233_gb300.profile_step --workload standard --steps 5
+    ncu --profile-from-start off ... python -m paper_2203_06233_gb300.profile_step ...
+
+Builds the plan, takes the launch choices from the autotune cache (timing them
+on the device when the cache lacks the shape), warms up, and then runs
+``--steps`` calls of ``stap_run_cpi`` between cudaProfilerStart and
+cudaProfilerStop, so that a profiler started with profiling off sees exactly
+the launches of those steps.  ``--slabs N`` overrides the tuned number of
+range slabs (1 = the plain four-launch chain).  The input is the workload's
+seeded synthetic cube, generated on the device.
+"""
+import argparse
+
+import torch
+
+from . import stap, synth
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--workload", default="standard", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3"])
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--slabs", type=int, default=0, help="override the tuned range slabs (0 = keep)")
+    a = ap.parse_args(argv)
+    spec = synth.WORKLOADS[a.workload]()
+    if isinstance(spec, (list, tuple)):
+        raise SystemExit("profile_step runs one-CPI workloads")
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    prec = stap.STAP_PREC_FP32 if a.precision == "fp32" else stap.STAP_PREC_TF32X3
+    cube = synth.make_cube_torch(spec, dev)
+    plan = stap.Plan(spec.dims(), device=dev, precision=prec)
+    out = torch.empty(plan.shapes(0)["out"], dtype=torch.float32, device=dev)
+    tuning = plan.autotune(cube, out)
+    if a.slabs > 0:
+        choices = stap.stap_plan_get_tuning(plan.handle, 0)
+        choices[6] = a.slabs
+        stap.stap_plan_set_tuning(plan.handle, 0, choices)
+    for _ in range(a.warmup):
+        plan.run_cpi(cube, out)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(a.steps):
+        plan.run_cpi(cube, out)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    code, failed = plan.status()
+    plan.close()
+    print(f"{a.workload} {a.precision}: dims {spec.dims()}, tuning {tuning}, "
+          f"slabs override {a.slabs}, {a.steps} steps, status {code} ({failed} failed)")
+    if code != stap.STAP_OK:
+        raise SystemExit(1)
+
+
+if __name__ == "__main__":
+    main()

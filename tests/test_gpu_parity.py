@@ -224,3 +224,71 @@ def test_generic_and_separable_solves_agree(spec):
         wts = to_np(plan.solve_weights(covd))
         err = np.linalg.norm(wts - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
         assert np.max(err) <= 2 * EPS32 * np.sqrt(2), np.max(err)
+
+
+# Snapshot lengths with a register-resident solve kernel (D = 8, 12, 16), each
+# with a steering count that leaves idle lanes in the last pass.
+REG_SPECS = {
+    "D8": synth.CPISpec(4, 16, 32, 128, 2, 32, 6, cnr_db=35.0, seed=21),
+    "D12": synth.CPISpec(3, 24, 32, 96, 4, 32, 5, cnr_db=40.0, seed=22),
+    "D16": synth.CPISpec(8, 16, 16, 128, 2, 64, 12, cnr_db=40.0, seed=23),
+}
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+@pytest.mark.parametrize("separable", [True, False], ids=["sep", "explicit"])
+@pytest.mark.parametrize("name", list(REG_SPECS))
+def test_register_and_shared_memory_solves_match_the_oracle(name, separable, refine):
+    """Both small-system solve kernels (tuning choice 8: 1 register-resident
+    LDL^H, 2 shared-memory Cholesky) on the default separable steering and on
+    the same table given explicitly (one solve per steering vector)."""
+    spec = REG_SPECS[name]
+    d = oracle.Dims(*spec.dims())
+    cov = oracle.covariance(d, oracle.doppler(d, _cube(spec)))
+    ref, _, nf = oracle.weights(d, cov)
+    assert nf == 0
+    covd = _dev(cov, torch.complex128)
+    out = {}
+    for kind in (1, 2):
+        plan = _plan(spec, refine_steps=refine)
+        if not separable:
+            plan.set_steering(oracle.default_steering(d))
+        choices = stap.stap_plan_get_tuning(plan.handle, 0)
+        choices[7] = kind
+        stap.stap_plan_set_tuning(plan.handle, 0, choices)
+        wts = to_np(plan.solve_weights(covd))
+        assert plan.status() == (stap.STAP_OK, 0)
+        err = np.linalg.norm(wts - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+        assert np.max(err) <= 2 * EPS32 * np.sqrt(2), (kind, np.max(err))
+        out[kind] = wts
+        plan.close()
+    diff = np.linalg.norm(out[1] - out[2], axis=-1) / np.linalg.norm(out[2], axis=-1)
+    assert np.max(diff) <= 4 * EPS32, np.max(diff)
+
+
+@pytest.mark.parametrize("kind", [1, 2], ids=["register", "shared"])
+def test_not_positive_definite_flagged_by_both_small_solves(kind):
+    spec = synth.CPISpec(4, 4, 4, 12, 2, 4, 3, cnr_db=None, seed=52)   # D = 8, 4 x 3 systems
+    d = oracle.Dims(*spec.dims())
+    rng = np.random.default_rng(6)
+    cov = np.zeros((4, 3, 8, 8), np.complex128)
+    for k in range(4):
+        for b in range(3):
+            M = rng.standard_normal((8, 8)) + 1j * rng.standard_normal((8, 8))
+            cov[k, b] = M @ M.conj().T + np.eye(8)
+    cov[0, 1] = -np.eye(8)                           # indefinite, negative trace
+    cov[2, 2, 5, 3] = np.inf                         # non-finite entry below the diagonal
+    cov[2, 2, 3, 5] = np.inf
+    ref, status, nf = oracle.weights(d, cov)
+    assert nf == 2
+    plan = _plan(spec)
+    choices = stap.stap_plan_get_tuning(plan.handle, 0)
+    choices[7] = kind
+    stap.stap_plan_set_tuning(plan.handle, 0, choices)
+    wts = to_np(plan.solve_weights(_dev(cov, torch.complex128)))
+    code, failed = plan.status()
+    assert code == stap.STAP_ERR_NOT_POSDEF and failed == 2
+    assert np.all(wts[0, 1] == 0) and np.all(wts[2, 2] == 0)
+    good = status == 0
+    err = np.linalg.norm(wts[good] - ref[good], axis=-1) / np.linalg.norm(ref[good], axis=-1)
+    assert np.max(err) <= 2 * EPS32 * np.sqrt(2)
