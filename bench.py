@@ -32,10 +32,12 @@ UNIT = "cells/s"
 NAME = "standard"
 L2_FLUSH_BYTES = 256 << 20
 
-# DRAM bytes (read + write) per launch of the solve kernel on the standard CPI,
-# from one ncu capture (profiles/fp32_path_standard_cpi_full.md), keyed by a hash
-# of the kernel source so that a changed kernel reports null until re-measured.
-SOLVE_TRAFFIC = {"c7f1bac30e4d5176": 33.64e6}
+# DRAM bytes (read + write) per launch of the solve kernel on the standard CPI
+# (dram__bytes_read.sum + dram__bytes_write.sum of one unslabbed launch, from
+# the ncu capture summarised in profiles/fp32_path_standard_cpi_full.md), keyed
+# by a hash of the kernel source so that a changed kernel reports null until
+# re-measured.
+SOLVE_TRAFFIC = {"06fee5a7aa395aa8": 34.04e6}
 
 
 def peaks():
