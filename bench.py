@@ -179,22 +179,39 @@ def time_steps(fn, steps, flush, stream):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def cpu_baseline_oracle(spec, budget_s=12.0):
-    """The oracle, as it stands, on the host cores: whole CPIs until ~budget_s."""
+def power_errors(got, ref):
+    """Normwise relative error of the output power, and the worst cell
+    relative to its own power floored at the median power."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    normwise = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    floor = np.maximum(ref, np.median(ref))
+    return {"normwise": normwise, "max_cell": float(np.max(np.abs(got - ref) / floor))}
+
+
+def cpu_baseline_oracle(spec, outputs=None, budget_s=12.0):
+    """The oracle, as it stands, on the host cores: whole CPIs until ~budget_s.
+    Its output also gives the error of each GPU output in `outputs`
+    ({name: host array [S][K][R]}) on the same cube."""
     import oracle
     from paper_2203_06233_gb300 import synth
     d = oracle.Dims(*spec.dims())
     cube = synth.make_cube(spec)
     n, t0 = 0, time.perf_counter()
+    ref = None
     while True:
-        oracle.run(d, cube)
+        res = oracle.run(d, cube)
+        if ref is None:
+            ref = res["out"]
         n += 1
         el = time.perf_counter() - t0
         if el >= budget_s or n >= 50:
             break
     cells = n * spec.n_dop * spec.n_range
-    return {"value": cells / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    base = {"value": cells / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{n} whole CPI(s) of the standard workload ({cells} cells) in {el:.1f} s"}
+    errors = {name: power_errors(out, ref) for name, out in (outputs or {}).items()}
+    return base, errors
 
 
 def run_gpu(args):
@@ -322,6 +339,36 @@ def run_gpu(args):
         raise RuntimeError(f"mixed path: device status {code} ({failed} failed systems)")
     mplan.close()
 
+    # ---- mixed-precision iterative refinement of the solve (an option beyond
+    # the paper's FP64 solve: FP32 factorisation, double-float residuals) ----
+    mixed_ir = None
+    if stap.stap_abi_version() >= 2 and C * T in (8, 12, 16):
+        iplan = stap.Plan(spec.dims(), device=dev, refine_steps=2, solver=stap.STAP_SOLVE_MIXED_IR)
+        iout = torch.empty_like(out)
+        ituning = iplan.autotune(cube, iout)
+        for _ in range(args.warmup):
+            flush()
+            iplan.run_cpi(cube, iout)
+        torch.cuda.synchronize()
+        itimes = time_steps(lambda: iplan.run_cpi(cube, iout), args.steps, flush, stream)
+        idop = iplan.doppler(cube)
+        icov = iplan.covariance(idop)
+        iwts = iplan.solve_weights(icov)
+        isolve = statistics.mean(time_steps(lambda: iplan.solve_weights(icov, iwts), reps, flush, stream))
+        code, failed = iplan.status()
+        if code != stap.STAP_OK:
+            raise RuntimeError(f"mixed refinement: device status {code} ({failed} failed systems)")
+        iplan.run_cpi(cube, iout)
+        mixed_ir = {
+            "value": world * cells * args.steps / (sum(itimes) * 1e-3),
+            "ms_per_step": sum(itimes) / args.steps,
+            "solver": "FP32 Lu Dg Lu^H factorisation and substitutions, 2 refinement steps with "
+                      "double-float residuals (STAP_SOLVE_MIXED_IR); plain FP32 contractions",
+            "tuning": ituning, "solve_ms": isolve,
+            "solve_speedup_vs_fp64": kt["solve"] / isolve,
+        }
+        iplan.close()
+
     # ---- end to end through the public API from pinned host buffers ----
     cube_pin = torch.from_numpy(cube_h).pin_memory()
     out_pin = torch.empty((S, K, R), dtype=torch.float32).pin_memory()
@@ -352,8 +399,124 @@ def run_gpu(args):
         "kernels": kernels,
         "clocks": clk.summary(),
     }
+    if mixed_ir is not None:
+        line["mixed_ir"] = mixed_ir
     if rank == 0 and world == 1 and not args.no_cpu_baseline and NAME == "standard":
-        line["cpu_baseline"] = cpu_baseline_oracle(spec)
+        outputs = {"plain": out.cpu().numpy(), "mixed": mout.cpu().numpy()}
+        if mixed_ir is not None:
+            outputs["mixed_ir"] = iout.cpu().numpy()
+        line["cpu_baseline"], line["errors_vs_oracle"] = cpu_baseline_oracle(spec, outputs)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """The batch workload: 512 uneven CPIs through one stap_run_cpi call (a
+    captured CUDA graph replayed each step).  Each rank processes its own
+    batch (a different seed)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2203_06233_gb300 import stap, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    specs = synth.batch_cpis(512, seed=4 + 1000 * rank)
+    cubes = [synth.make_cube_torch(s, dev) for s in specs]
+    outs = [torch.empty((s.n_steering, s.n_dop, s.n_range), dtype=torch.float32, device=dev)
+            for s in specs]
+    # workspace: as much of the all-concurrent size as free HBM allows (8 GiB spare)
+    free = torch.cuda.mem_get_info(dev)[0]
+    plan = stap.Plan([s.dims() for s in specs], device=dev, max_workspace_bytes=max(0, free - (8 << 30)))
+    tuning = plan.autotune(cubes, outs)
+    flushbuf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def flush():
+        flushbuf.zero_()
+
+    def step():
+        plan.run_cpi(cubes, outs)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    code, failed = plan.status()
+    if code != stap.STAP_OK:
+        raise RuntimeError(f"device status {code} ({failed} failed systems) after warm-up")
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        times = time_steps(step, args.steps, flush, stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    cells = sum(s.cells for s in specs)
+    total_ms, value = aggregate(sum(times), cells * args.steps, world, dev)
+    ms_per_step = total_ms / args.steps
+    sf = sum(solve_flops(s, refine=1) for s in specs)
+    pk = peaks()
+    achieved = sf / (ms_per_step * 1e-3) / 1e12
+    roofline = {"kernel": "all solve kernels of the batch (FP64)", "bound": "alu",
+                "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / pk["fp64_tflops"], "traffic": None,
+                "basis": "FP64 solve flops of all 512 CPIs / whole step time (a lower bound for "
+                         "the solve kernels: the step also runs the other 1536 launches)",
+                "peak_src": "FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (unit count and max clock)"}
+
+    # end to end: every cube from pinned host memory, every output back
+    h2d = sum(c.numel() * 8 for c in cubes)
+    d2h = sum(o.numel() * 4 for o in outs)
+    e2e = None
+    try:
+        cubes_pin = [c.cpu().pin_memory() for c in cubes]
+        outs_pin = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
+
+        def e2e_step():
+            for c, cp in zip(cubes, cubes_pin):
+                c.copy_(cp, non_blocking=True)
+            plan.run_cpi(cubes, outs)
+            for o, op in zip(outs, outs_pin):
+                op.copy_(o, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = statistics.mean(time_steps(e2e_step, max(1, min(3, args.steps)), flush, stream))
+        e2e = {"value": world * cells / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+        del cubes_pin, outs_pin
+    except RuntimeError as exc:   # pinned host memory exhausted
+        e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "unavailable": f"pinned host buffers: {exc}"[:200]}
+    shapes = {}
+    for s in specs:
+        key = f"C{s.n_chan} T{s.tdof} K{s.n_dop} S{s.n_steering}"
+        shapes[key] = shapes.get(key, 0) + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"batch of {len(specs)} uneven CPIs: C in {{4,8,16}}, T in {{2,3,4}}, "
+                               f"P = K in {{64,128,256}}, R = 64 x U{{16..256}}, B 64, S in {{8,16}}",
+                   "cells_per_step": cells, "n_cpi": len(specs), "distinct_shapes": len(shapes),
+                   "workspace_gib": plan.workspace.numel() / 2 ** 30,
+                   "batch_bytes_gib": plan.batch_bytes / 2 ** 30,
+                   "precision": "plain FP32 contractions, FP64 solve, 1 refinement step",
+                   "l2": "inputs (47 GB of cubes) larger than L2; L2 also flushed between steps",
+                   "tuned_shapes": len(tuning), "parallelism": "one batch per GPU per step"},
+        "e2e": e2e,
+        "gpu_launches": 4 * len(specs) * args.steps,
+        "roofline": roofline,
+        "clocks": clk.summary(),
+    }
     plan.close()
     if world > 1:
         dist.destroy_process_group()
@@ -420,8 +583,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["standard", "mixed", "mixed_small", "large"], default="standard",
-                    help="standard is the benchmark workload; the others are for inspection")
+    ap.add_argument("--workload", choices=["standard", "mixed", "mixed_small", "large", "batch"],
+                    default="standard",
+                    help="standard is the benchmark workload; the others are for inspection "
+                         "(batch: 512 uneven CPIs per step in one graph replay)")
     args = ap.parse_args()
     global NAME
     NAME = args.workload
@@ -429,6 +594,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif NAME == "batch":
+        run_batch(args)
     else:
         run_gpu(args)
 

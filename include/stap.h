@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define STAP_ABI_VERSION 1
+#define STAP_ABI_VERSION 2
 
 typedef enum {
   STAP_OK = 0,
@@ -51,8 +51,7 @@ typedef enum {
 } stap_status;
 
 /* Arithmetic of the contraction steps (Doppler, covariance, apply).  The
- * diagonal loading, Cholesky factorisation and triangular solves are FP64 in
- * every mode. */
+ * factorisation and the triangular solves follow stap_solver. */
 typedef enum {
   STAP_PREC_FP32 = 0,  /* FP32 FFT; covariance accumulated error-free in FP32
                           pairs (two-product / compensated sum); FP32 apply */
@@ -62,6 +61,26 @@ typedef enum {
                           neither B divides 128 nor 128 divides B, or a 128-cell
                           tile needs more than 128 steering columns */
 } stap_precision;
+
+/* Arithmetic of the weight solve (diagonal load, factorisation, substitutions,
+ * refinement). */
+typedef enum {
+  STAP_SOLVE_FP64 = 0,    /* FP64 factorisation and substitutions; each of the
+                             refine_steps refinement steps forms the FP64
+                             residual v - Rl u and solves for the correction in
+                             FP64 (the default) */
+  STAP_SOLVE_MIXED_IR = 1 /* mixed-precision iterative refinement (not in the
+                             paper; a faster option): Rl split into
+                             double-floats (hi + lo, about 2^-48), its FP32 part
+                             factored and solved in FP32, and each of the
+                             refine_steps steps forms the residual v - Rl u in
+                             double-float arithmetic on the FP32 pipe, solves
+                             for the correction in FP32 and adds it to the
+                             double-float solution.  Each step shrinks the error
+                             by about cond(Rl) 2^-24; 2 steps reach FP32 weight
+                             accuracy for cond(Rl) up to about 1e5.  D = 8, 12
+                             or 16 only (STAP_ERR_UNSUPPORTED otherwise) */
+} stap_solver;
 
 typedef struct {
   int32_t n_chan;         /* C >= 1 */
@@ -75,13 +94,14 @@ typedef struct {
 
 typedef struct {
   double load_factor;   /* diagonal load delta = load_factor * Re tr(R) / D; >= 0 (default 1e-3) */
-  int32_t refine_steps; /* iterative-refinement steps after the FP64 solve, 0..4 (default 1) */
+  int32_t refine_steps; /* iterative-refinement steps after the first solve, 0..4 (default 1) */
   int32_t precision;    /* a stap_precision value (default STAP_PREC_FP32) */
+  int32_t solver;       /* a stap_solver value (default STAP_SOLVE_FP64) */
 } stap_options;
 
 typedef struct stap_plan_s* stap_plan;
 
-/* Fill *opt with the defaults (load_factor 1e-3, refine_steps 1, FP32). */
+/* Fill *opt with the defaults (load_factor 1e-3, refine_steps 1, FP32, FP64 solve). */
 void stap_options_default(stap_options* opt);
 
 /* Create a plan for n_cpi CPIs whose shapes are dims[0 .. n_cpi-1].
@@ -126,10 +146,12 @@ stap_status stap_doppler(stap_plan plan, const void* cube_c64, void* dop_c64);
  * dop: c64 [C][K][R]; cov: c128 [K][NB][D][D], full Hermitian. */
 stap_status stap_covariance(stap_plan plan, const void* dop_c64, void* cov_c128);
 
-/* Adaptive weights per (k, b) and steering vector v_s, all in FP64:
+/* Adaptive weights per (k, b) and steering vector v_s (Sec. 4.2's STAP
+ * kernel, loaded sample-matrix reading), in FP64 with the default solver:
  *   delta = load_factor * Re tr(cov) / D,  Rl = cov + delta I = L L^H,
  *   u_s = Rl^{-1} v_s by forward/back substitution, refine_steps refinement
  *   steps u_s += Rl^{-1} (v_s - Rl u_s),  w_s = u_s / sqrt(Re v_s^H u_s).
+ * (STAP_SOLVE_MIXED_IR: see stap_solver.)
  * Only the lower triangle and the real part of the diagonal of each cov are
  * read.  A system whose pivot is not positive and finite gets zero weights
  * and is counted (stap_get_status).  cov: c128 [K][NB][D][D];

@@ -40,6 +40,12 @@ __device__ __forceinline__ F2 fma(F2 acc, F2 a, F2 b) {
 // acc - a * b
 __device__ __forceinline__ F2 fms(F2 acc, F2 a, F2 b) { return fma(acc, {-a.hi, -a.lo}, b); }
 
+// a + b with a a double-float and b a float
+__device__ __forceinline__ F2 add(F2 a, float b) {
+  const F2 s = two_sum(a.hi, b);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
 // Split a double into hi = nearest float, lo = nearest float to the rest.
 __device__ __forceinline__ F2 from_double(double x) {
   const float hi = __double2float_rn(x);

@@ -30,8 +30,8 @@ struct Cpi {
   // spatial factors a [S][C][2]; cleared when the caller replaces the table
   bool separable = false;
   std::vector<double> sep_g, sep_a;
-  std::vector<float> steer_ff, sep_a_ff;   // the tables as double-floats [..][4]
-  size_t steer_ff_off = 0, a_ff_off = 0;
+  std::vector<float> steer_ff, sep_a_ff, g_ff;   // the tables as double-floats [..][4]
+  size_t steer_ff_off = 0, a_ff_off = 0, g_ff_off = 0;
   stap::Tune tune;              // launch choices (autotuner or defaults)
   size_t dop_elems() const { return (size_t)d.n_chan * d.n_dop * d.n_range; }
   size_t cov_elems() const { return (size_t)d.n_dop * NB * D * D; }
@@ -125,6 +125,7 @@ void make_tables(Cpi& c) {
   c.separable = true;
   to_ff(c.steer, c.steer_ff);
   to_ff(c.sep_a, c.sep_a_ff);
+  to_ff(c.sep_g, c.g_ff);
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -182,6 +183,8 @@ stap_status upload_tables(stap_plan p, int only_cpi = -1) {
         cudaMemcpyAsync(p->ws + c.steer_ff_off, c.steer_ff.data(), c.steer_ff.size() * sizeof(float),
                         cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
         cudaMemcpyAsync(p->ws + c.a_ff_off, c.sep_a_ff.data(), c.sep_a_ff.size() * sizeof(float),
+                        cudaMemcpyHostToDevice, p->stream) != cudaSuccess ||
+        cudaMemcpyAsync(p->ws + c.g_ff_off, c.g_ff.data(), c.g_ff.size() * sizeof(float),
                         cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
       return STAP_ERR_CUDA;
   }
@@ -234,8 +237,10 @@ stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts, cuda
       static_cast<const double2*>(cov), static_cast<float2*>(wts),
       p->at<const double2>(c.steer_off), c.separable ? p->at<const double2>(c.g_off) : nullptr,
       c.separable ? p->at<const double2>(c.a_off) : nullptr, p->at<const float4>(c.steer_ff_off),
-      c.separable ? p->at<const float4>(c.a_ff_off) : nullptr, (long long)d.n_dop * nb, c.D,
-      d.n_steering, d.n_chan, p->opt.load_factor, p->opt.refine_steps, p->status(), st, c.tune));
+      c.separable ? p->at<const float4>(c.a_ff_off) : nullptr,
+      c.separable ? p->at<const float4>(c.g_ff_off) : nullptr, (long long)d.n_dop * nb, c.D,
+      d.n_steering, d.n_chan, p->opt.load_factor, p->opt.refine_steps, p->opt.solver, p->status(),
+      st, c.tune));
 }
 
 stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts, float* out,
@@ -425,6 +430,7 @@ void stap_options_default(stap_options* opt) {
   opt->load_factor = 1e-3;
   opt->refine_steps = 1;
   opt->precision = STAP_PREC_FP32;
+  opt->solver = STAP_SOLVE_FP64;
 }
 
 int32_t stap_abi_version(void) { return STAP_ABI_VERSION; }
@@ -455,9 +461,12 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
       o.refine_steps > 4)
     return STAP_ERR_INVALID_ARG;
   if (o.precision != STAP_PREC_FP32 && o.precision != STAP_PREC_TF32X3) return STAP_ERR_UNSUPPORTED;
+  if (o.solver != STAP_SOLVE_FP64 && o.solver != STAP_SOLVE_MIXED_IR) return STAP_ERR_UNSUPPORTED;
   for (int i = 0; i < n_cpi; ++i) {
     stap_status st = validate(dims[i]);
     if (st != STAP_OK) return st;
+    if (o.solver == STAP_SOLVE_MIXED_IR && !stap::mir_supported(dims[i].n_chan * dims[i].tdof))
+      return STAP_ERR_UNSUPPORTED;
   }
   stap_plan p = new (std::nothrow) stap_plan_s;
   if (!p) return STAP_ERR_INVALID_ARG;
@@ -486,6 +495,8 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
     off = align_up(off + c.steer_ff.size() * sizeof(float));
     c.a_ff_off = off;
     off = align_up(off + c.sep_a_ff.size() * sizeof(float));
+    c.g_ff_off = off;
+    off = align_up(off + c.g_ff.size() * sizeof(float));
     if (c.dop_elems() > max_dop) max_dop = c.dop_elems();
     if (c.cov_elems() > max_cov) max_cov = c.cov_elems();
     if (c.wts_elems() > max_wts) max_wts = c.wts_elems();

@@ -334,7 +334,7 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
 // trailing entries with l_ij conj(a_lj), a_lj the column before the division
 // (= l_lj d_j), kept in a small per-team buffer.
 template <int D, bool SEP>
-__global__ void __launch_bounds__(128, 3)
+__global__ void __launch_bounds__(128, 4)
 solve_reg_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
                  const double2* __restrict__ steer, const double2* __restrict__ sep_g,
                  const float4* __restrict__ steer_ff, const float4* __restrict__ sep_a_ff,
@@ -347,11 +347,12 @@ solve_reg_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
   const int G = 32 / TS, team = lane / TS, tl = lane - team * TS;
   // per warp: G factors [Dp], G pivot columns [D], (SEP) the [D][32] float4
   // exchange area for the combination; after all warps: G pivot reciprocals [D]
-  const size_t warp_elems = (size_t)G * (Dp + D) + (SEP ? (size_t)D * 32 : 0);
+  const bool alias = G * Dp >= 32 * D;   // the exchange area fits over the factors
+  const size_t warp_elems = (size_t)G * (Dp + D) + (SEP && !alias ? (size_t)D * 32 : 0);
   double2* wbase = sm + warp * warp_elems;
   double2* L = wbase + (size_t)team * Dp;
   double2* col = wbase + (size_t)G * Dp + (size_t)team * D;
-  float4* Wf = reinterpret_cast<float4*>(wbase + (size_t)G * (Dp + D));
+  float4* Wf = reinterpret_cast<float4*>(alias ? wbase : wbase + (size_t)G * (Dp + D));
   double* rdp = reinterpret_cast<double*>(sm + nw * warp_elems) + ((size_t)warp * G + team) * D;
 
   for (long long base = ((long long)blockIdx.x * nw + warp) * G; base < nsys;
@@ -475,6 +476,7 @@ solve_reg_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
           }
         }
         if (SEP) {
+          __syncwarp();   // every lane is done with the factors the area may overlay
           if (live)
 #pragma unroll
             for (int i = 0; i < D; ++i) Wf[i * 32 + lane] = to_ff4(u[i]);
@@ -505,6 +507,244 @@ solve_reg_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
     }
     if (valid && !ok && tl == 0) atomicAdd(&status->n_failed, 1ULL);
     __syncwarp();  // the next batch reuses L, col, Wf
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision iterative refinement (STAP_SOLVE_MIXED_IR) for D = 8, 12,
+// 16, with the team mapping and register-resident vectors of
+// solve_reg_kernel.  The loaded matrix Rl is kept in shared memory as
+// double-floats (hi + lo, about 2^-48 relative) and its FP32 part is factored
+// as Lu Dg Lu^H in FP32.  Each right-hand side b is solved in FP32; then
+// every refinement step forms the residual r = b - Rl u in double-float on
+// the FP32 pipe, solves Rl c = r in FP32 and adds c to the double-float
+// solution u (the classical three-precision scheme: factorisation 2^-24,
+// working and residual precision 2^-48).  Each step shrinks the error by
+// about kappa(Rl) 2^-24; with the clutter conditioning kappa ~ 1e3 D, two
+// steps reach the FP32 rounding of the stored weights.  The FP64 pipe only
+// adds the diagonal load and splits the input.
+__host__ __device__ constexpr size_t mir_warp_bytes(int D, int G, bool sep) {
+  // G double-float matrices [Dp] (the SEP exchange area [D][32] float4
+  // overlays them when they are large enough, else follows), G FP32 factors
+  // [Dp], the per-lane residual columns [D][32] float2, G pivot columns [D]
+  // float2, G pivot reciprocals [D] float
+  return ((size_t)G * (D * (D + 1) / 2) +
+          (sep && G * (D * (D + 1) / 2) < 32 * D ? (size_t)D * 32 : 0)) * 16 +
+         (size_t)G * (D * (D + 1) / 2) * 8 + (size_t)D * 32 * 8 + (size_t)G * D * 8 +
+         ((size_t)G * D * 4 + 15) / 16 * 16;
+}
+
+// acc -= a * b and acc -= conj(a) * b on double-float complex numbers
+__device__ __forceinline__ void ff_cfms(ff::F2& accr, ff::F2& acci, float4 a, ff::F2 br, ff::F2 bi) {
+  const ff::F2 ar{a.x, a.y}, ai{a.z, a.w};
+  accr = ff::fma(ff::fms(accr, ar, br), ai, bi);
+  acci = ff::fms(ff::fms(acci, ar, bi), ai, br);
+}
+__device__ __forceinline__ void ff_cfms_conj(ff::F2& accr, ff::F2& acci, float4 a, ff::F2 br,
+                                             ff::F2 bi) {
+  const ff::F2 ar{a.x, a.y}, ai{a.z, a.w};
+  accr = ff::fms(ff::fms(accr, ar, br), ai, bi);
+  acci = ff::fma(ff::fms(acci, ar, bi), ai, br);
+}
+
+template <int D, bool SEP>
+__global__ void __launch_bounds__(128, 4)
+solve_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
+                 const float4* __restrict__ steer_ff, const float4* __restrict__ g_ff,
+                 const float4* __restrict__ sep_a_ff, long long nsys, int S, int C, int TS,
+                 double load_factor, int refine_steps, DeviceStatus* __restrict__ status) {
+  constexpr int Dp = D * (D + 1) / 2;
+  extern __shared__ float4 smf[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  const int G = 32 / TS, team = lane / TS, tl = lane - team * TS;
+  const bool alias = G * Dp >= 32 * D;
+  char* wb = reinterpret_cast<char*>(smf) + warp * mir_warp_bytes(D, G, SEP);
+  float4* Ad = reinterpret_cast<float4*>(wb) + (size_t)team * Dp;
+  float4* Wf = reinterpret_cast<float4*>(wb) + (alias ? 0 : (size_t)G * Dp);
+  char* fb = wb + ((size_t)G * Dp + (SEP && !alias ? (size_t)D * 32 : 0)) * 16;
+  float2* Lf = reinterpret_cast<float2*>(fb) + (size_t)team * Dp;
+  float2* Rs = reinterpret_cast<float2*>(fb + (size_t)G * Dp * 8) + lane;     // [D][32]
+  char* pb = fb + (size_t)G * Dp * 8 + (size_t)D * 32 * 8;
+  float2* colf = reinterpret_cast<float2*>(pb) + (size_t)team * D;
+  float* rdf = reinterpret_cast<float*>(pb + (size_t)G * D * 8) + (size_t)team * D;
+
+  for (long long base = ((long long)blockIdx.x * nw + warp) * G; base < nsys;
+       base += (long long)gridDim.x * nw * G) {
+    const long long sys = base + team;
+    const bool valid = sys < nsys;
+    const double2* A = cov + (size_t)(valid ? sys : nsys - 1) * D * D;
+
+    // ---- Rl as double-floats and its FP32 part ----
+    double tr = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) tr += __ldg(&A[j * D + j].x);
+    const double delta = load_factor * tr * (1.0 / D);
+    {
+      int i = 0, l = 0;
+      step_lower(i, l, tl);
+      for (int q = tl; q < Dp; q += TS) {
+        const float4 f = to_ff4(loaded(A, D, i, l, delta));
+        Ad[q] = f;
+        Lf[q] = make_float2(f.x, f.z);
+        step_lower(i, l, TS);
+      }
+    }
+    __syncwarp();
+
+    // ---- FP32 Lu Dg Lu^H ----
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float djj = Lf[pidx(j, j)].x;
+      if (!(djj > 0.f) || !isfinite(djj)) {
+        ok = false;
+        djj = 1.f;
+      }
+      const float rd = 1.0f / djj;
+      for (int i = j + 1 + tl; i < D; i += TS) {
+        const float2 v = Lf[pidx(i, j)];
+        colf[i] = v;
+        Lf[pidx(i, j)] = make_float2(v.x * rd, v.y * rd);
+      }
+      __syncwarp();
+      const int m = D - 1 - j, np = m * (m + 1) / 2;
+      int a = 0, b = 0;
+      step_lower(a, b, tl);
+      for (int q = tl; q < np; q += TS) {
+        const int i = j + 1 + a, l = j + 1 + b;
+        float2 acc = Lf[pidx(i, l)];
+        const float2 lij = Lf[pidx(i, j)], alj = colf[l];
+        acc.x = fmaf(-lij.x, alj.x, acc.x);
+        acc.x = fmaf(-lij.y, alj.y, acc.x);
+        acc.y = fmaf(-lij.y, alj.x, acc.y);
+        acc.y = fmaf(lij.x, alj.y, acc.y);
+        Lf[pidx(i, l)] = acc;
+        step_lower(a, b, TS);
+      }
+      if (tl == 0) rdf[j] = rd;
+      __syncwarp();
+    }
+
+    // x <- Rl^{-1} x in FP32 (warp barriers between rows, as in solve_reg_kernel)
+    auto f32_solve = [&](float2 (&x)[D]) {
+#pragma unroll
+      for (int i = 1; i < D; ++i) {
+#pragma unroll
+        for (int l = 0; l < i; ++l) {
+          const float2 a = Lf[pidx(i, l)];
+          x[i].x = fmaf(-a.x, x[l].x, x[i].x);
+          x[i].x = fmaf(a.y, x[l].y, x[i].x);
+          x[i].y = fmaf(-a.x, x[l].y, x[i].y);
+          x[i].y = fmaf(-a.y, x[l].x, x[i].y);
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const float r = rdf[i];
+        x[i].x *= r;
+        x[i].y *= r;
+      }
+#pragma unroll
+      for (int i = D - 2; i >= 0; --i) {
+#pragma unroll
+        for (int l = i + 1; l < D; ++l) {
+          const float2 a = Lf[pidx(l, i)];
+          x[i].x = fmaf(-a.x, x[l].x, x[i].x);
+          x[i].x = fmaf(-a.y, x[l].y, x[i].x);
+          x[i].y = fmaf(-a.x, x[l].y, x[i].y);
+          x[i].y = fmaf(a.y, x[l].x, x[i].y);
+        }
+        __syncwarp();
+      }
+    };
+
+    // ---- per-lane right-hand sides (idle lanes repeat the first one) ----
+    const int nrhs = SEP ? C : S;
+    for (int r0 = 0; r0 < nrhs; r0 += TS) {
+      const bool live = r0 + tl < nrhs;
+      const int rhs = live ? r0 + tl : 0;
+      auto rhs_ff = [&](int i) -> float4 {
+        if (SEP) {
+          const int t = i / C;
+          return (i - t * C == rhs) ? __ldg(g_ff + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        return __ldg(steer_ff + (size_t)rhs * D + i);
+      };
+      float2 x[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const float4 b = rhs_ff(i);
+        x[i] = make_float2(b.x, b.z);
+      }
+      f32_solve(x);
+      ff::F2 ur[D], ui[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        ur[i] = ff::F2{x[i].x, 0.f};
+        ui[i] = ff::F2{x[i].y, 0.f};
+      }
+      for (int it = 0; it < refine_steps; ++it) {
+        // x = fl32(b - Rl u), the residual formed in double-float.  The row
+        // loop is not unrolled (fully unrolled it is too large, and the
+        // solution would leave the registers); row i goes to this lane's
+        // column of Rs.  Above the diagonal Rl[i][l] = conj(Rl[l][i]).
+        for (int i = 0; i < D; ++i) {
+          const float4 b = rhs_ff(i);
+          ff::F2 rr{b.x, b.y}, ri{b.z, b.w};
+#pragma unroll
+          for (int l = 0; l < D; ++l) {
+            const bool low = l <= i;
+            float4 a = Ad[low ? pidx(i, l) : pidx(l, i)];
+            if (!low) {
+              a.z = -a.z;
+              a.w = -a.w;
+            }
+            ff_cfms(rr, ri, a, ur[l], ui[l]);
+          }
+          Rs[i * 32] = make_float2(__fadd_rn(rr.hi, rr.lo), __fadd_rn(ri.hi, ri.lo));
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) x[i] = Rs[i * 32];
+        f32_solve(x);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          ur[i] = ff::add(ur[i], x[i].x);
+          ui[i] = ff::add(ui[i], x[i].y);
+        }
+      }
+      if (SEP) {
+        __syncwarp();   // every lane is done with Ad, which the exchange area may overlay
+        if (live)
+#pragma unroll
+          for (int i = 0; i < D; ++i) Wf[i * 32 + lane] = make_float4(ur[i].hi, ur[i].lo, ui[i].hi, ui[i].lo);
+      } else {
+        ff::F2 q{0.f, 0.f};                       // Re v^H u
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          const float4 v = __ldg(steer_ff + (size_t)rhs * D + i);
+          q = ff::fma(ff::fma(q, ff::F2{v.x, v.y}, ur[i]), ff::F2{v.z, v.w}, ui[i]);
+        }
+        const double qd = ff::to_double(q);
+        const bool good = ok && qd > 0.0 && isfinite(qd);
+        const float sf = good ? (float)rsqrt(qd) : 0.f;
+        if (valid && live) {
+          float2* w = wts + ((size_t)sys * S + rhs) * D;
+#pragma unroll
+          for (int i = 0; i < D; ++i)
+            w[i] = good ? make_float2(__fadd_rn(ur[i].hi, ur[i].lo) * sf, __fadd_rn(ui[i].hi, ui[i].lo) * sf)
+                        : make_float2(0.f, 0.f);
+        }
+      }
+    }
+    if (SEP) {
+      __syncwarp();
+      sep_emit(Wf + team * TS, D, S, C, TS, tl, steer_ff, sep_a_ff, ok,
+               valid ? wts + (size_t)sys * S * D : nullptr);
+    }
+    if (valid && !ok && tl == 0) atomicAdd(&status->n_failed, 1ULL);
+    __syncwarp();  // the next batch reuses Ad, Lf, colf, Wf
   }
 }
 
@@ -879,6 +1119,26 @@ cudaError_t launch_reg(const double2* cov, float2* wts, const double2* steer, co
   return cudaGetLastError();
 }
 
+template <int D, bool SEP>
+cudaError_t launch_mir(const double2* cov, float2* wts, const float4* steer_ff, const float4* g_ff,
+                       const float4* sep_a_ff, long long nsys, int S, int C, int TS, int nw,
+                       long long blocks, size_t smem, double lf, int refine, DeviceStatus* status,
+                       cudaStream_t s) {
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  static int set_bytes[64] = {0};
+  cudaError_t e = ensure_smem(solve_mir_kernel<D, SEP>, smem, set_bytes);
+  if (e != cudaSuccess) return e;
+  solve_mir_kernel<D, SEP><<<(unsigned)blocks, nw * 32, smem, s>>>(
+      cov, wts, steer_ff, g_ff, sep_a_ff, nsys, S, C, TS, lf, refine, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool mir_supported(int D) { return D == 8 || D == 12 || D == 16; }
+
+namespace {
+
 int pow2ceil(int x) {
   int p = 1;
   while (p < x) p <<= 1;
@@ -889,13 +1149,40 @@ int pow2ceil(int x) {
 
 cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
                          const double2* sep_g, const double2* sep_a, const float4* steer_ff,
-                         const float4* sep_a_ff, long long nsys, int D, int S, int C,
-                         double load_factor, int refine_steps, DeviceStatus* status,
-                         cudaStream_t s, const Tune& tn) {
+                         const float4* sep_a_ff, const float4* g_ff, long long nsys, int D, int S,
+                         int C, double load_factor, int refine_steps, int solver,
+                         DeviceStatus* status, cudaStream_t s, const Tune& tn) {
   if (nsys <= 0) return cudaSuccess;
   if (D < 1 || D > kMaxD || S < 1) return cudaErrorInvalidValue;
   const bool sep = sep_g != nullptr && sep_a != nullptr && steer_ff != nullptr && sep_a_ff != nullptr &&
                    C >= 1 && C <= 32 && D % C == 0;
+  if (solver == 1) {  // mixed-precision iterative refinement (D = 8, 12, 16)
+    if (!mir_supported(D) || steer_ff == nullptr) return cudaErrorNotSupported;
+    const bool msep = sep && g_ff != nullptr;
+    const int nrhs = msep ? C : S;
+    int TS = pow2ceil(nrhs < 32 ? nrhs : 32);
+    constexpr size_t kBudget = 200 * 1024;
+    while (TS < 32 && mir_warp_bytes(D, 32 / TS, msep) * 4 > kBudget) TS <<= 1;
+    if (tn.solve_ts >= TS && tn.solve_ts <= 32 && (tn.solve_ts & (tn.solve_ts - 1)) == 0)
+      TS = tn.solve_ts;
+    int nw = 4;
+    while (nw > 1 && mir_warp_bytes(D, 32 / TS, msep) * nw > kBudget) --nw;
+    if (tn.solve_nw >= 1 && tn.solve_nw <= nw) nw = tn.solve_nw;
+    const size_t smem = mir_warp_bytes(D, 32 / TS, msep) * nw;
+    const int G = 32 / TS;
+    const long long batches = (nsys + G - 1) / G;
+    long long blocks = (batches + nw - 1) / nw;
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
+#define STAP_MIR(d)                                                                                \
+  return msep ? launch_mir<d, true>(cov, wts, steer_ff, g_ff, sep_a_ff, nsys, S, C, TS, nw, blocks, \
+                                    smem, load_factor, refine_steps, status, s)                    \
+              : launch_mir<d, false>(cov, wts, steer_ff, nullptr, nullptr, nsys, S, C, TS, nw,      \
+                                     blocks, smem, load_factor, refine_steps, status, s)
+    if (D == 8) STAP_MIR(8);
+    if (D == 12) STAP_MIR(12);
+    STAP_MIR(16);
+#undef STAP_MIR
+  }
   if (D > kSmallMaxD) {  // one system per CTA, lanes over rows
     // LR lanes per right-hand side, each holding RPL rows (D <= LR * RPL):
     //   LR = 8:  RPL 8, 4 warps (D <= 64)
@@ -942,7 +1229,8 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
   const bool reg = (D == 8 || D == 12 || D == 16) && tn.solve_kind != 2;
   auto reg_bytes = [&](int ts) {
     const int G = 32 / ts;
-    return ((size_t)G * (Dp + D) + (sep ? (size_t)D * 32 : 0)) * sizeof(double2) +
+    const bool alias = G * Dp >= 32 * D;
+    return ((size_t)G * (Dp + D) + (sep && !alias ? (size_t)D * 32 : 0)) * sizeof(double2) +
            (size_t)G * D * sizeof(double);
   };
   if (reg) {

@@ -36,6 +36,9 @@ struct Tune {
   int solve_kind = 0;  // D = 8, 12, 16 solve: 1 register-resident, 2 generic shared-memory
 };
 
+// Snapshot lengths with a mixed-precision iterative-refinement solve.
+bool mir_supported(int D);
+
 // ---------------------------------------------------------------- launchers --
 // Each returns cudaGetLastError() after its launches.
 
@@ -67,9 +70,9 @@ cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, in
 // (re_hi, re_lo, im_hi, im_lo) for the combination on the FP32 pipe.
 cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
                          const double2* sep_g, const double2* sep_a, const float4* steer_ff,
-                         const float4* sep_a_ff, long long nsys, int D, int S, int C,
-                         double load_factor, int refine_steps, DeviceStatus* status,
-                         cudaStream_t s, const Tune& t = Tune());
+                         const float4* sep_a_ff, const float4* g_ff, long long nsys, int D, int S,
+                         int C, double load_factor, int refine_steps, int solver,
+                         DeviceStatus* status, cudaStream_t s, const Tune& t = Tune());
 
 // out[s][k][r] = |w^H x|^2; dop [C][K][R] c64, wts [K][NB][S][D] c64, out [S][K][R] f32.
 cudaError_t launch_apply(const float2* dop, const float2* wts, float* out, int C, int K, int R,

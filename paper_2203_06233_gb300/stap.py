@@ -29,6 +29,8 @@ STAP_ERR_MISALIGNED = 8
 
 STAP_PREC_FP32 = 0
 STAP_PREC_TF32X3 = 2
+STAP_SOLVE_FP64 = 0
+STAP_SOLVE_MIXED_IR = 1
 
 # every symbol include/stap.h declares
 EXPORTED = (
@@ -59,7 +61,7 @@ class stap_dims(ctypes.Structure):
 
 class stap_options(ctypes.Structure):
     _fields_ = [("load_factor", ctypes.c_double), ("refine_steps", ctypes.c_int32),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("solver", ctypes.c_int32)]
 
 
 _lib = None
@@ -295,13 +297,13 @@ class Plan:
 
     def __init__(self, dims, load_factor: float = 1e-3, refine_steps: int = 1,
                  precision: int = STAP_PREC_FP32, device=None, steps_only: bool = False,
-                 max_workspace_bytes: Optional[int] = None):
+                 max_workspace_bytes: Optional[int] = None, solver: int = STAP_SOLVE_FP64):
         dl = list(dims) if isinstance(dims, (list, tuple)) and dims and not isinstance(dims[0], int) \
             else [dims]
         self.dims = [_dims(d) for d in dl]
         self.device = torch.device(device) if device is not None else torch.device("cuda")
-        opts = stap_options(float(load_factor), int(refine_steps), int(precision))
-        self.precision, self.refine_steps = int(precision), int(refine_steps)
+        opts = stap_options(float(load_factor), int(refine_steps), int(precision), int(solver))
+        self.precision, self.refine_steps, self.solver = int(precision), int(refine_steps), int(solver)
         with torch.cuda.device(self.device):
             self.handle, _ = stap_plan_create(self.dims, opts)
             self.step_bytes, self.run_bytes = stap_plan_workspace_sizes(self.handle)
@@ -395,9 +397,9 @@ class Plan:
 
     def _tune_key(self, i: int) -> str:
         d = self.dims[i]
-        key = "C%d P%d K%d T%d B%d S%d prec%d ref%d" % (d.n_chan, d.n_pulses, d.n_dop, d.tdof,
-                                                      d.training_block, d.n_steering,
-                                                      self.precision, self.refine_steps)
+        key = "C%d P%d K%d T%d B%d S%d prec%d ref%d solve%d" % (
+            d.n_chan, d.n_pulses, d.n_dop, d.tdof, d.training_block, d.n_steering, self.precision,
+            self.refine_steps, self.solver)
         # a one-CPI plan also tunes its range slabs, which depend on R
         return key + (" R%d" % d.n_range if len(self.dims) == 1 else " batch")
 

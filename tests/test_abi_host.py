@@ -27,7 +27,7 @@ def test_library_loads_and_exports_every_declared_symbol():
     for name in declared:
         assert hasattr(L, name), f"{name} declared in stap.h but not exported"
     assert set(declared) == set(stap.EXPORTED)
-    assert stap.stap_abi_version() == 1
+    assert stap.stap_abi_version() == 2
 
 
 def _create(dims, opts=None):
@@ -71,21 +71,38 @@ def test_plan_create_rejects_bad_shapes(dims, code):
     assert got == code and not h.value
 
 
-@pytest.mark.parametrize("lf,refine,prec,code", [
-    (-1.0, 1, 0, stap.STAP_ERR_INVALID_ARG),
-    (float("nan"), 1, 0, stap.STAP_ERR_INVALID_ARG),
-    (1e-3, -1, 0, stap.STAP_ERR_INVALID_ARG),
-    (1e-3, 5, 0, stap.STAP_ERR_INVALID_ARG),
-    (1e-3, 1, 7, stap.STAP_ERR_UNSUPPORTED),
-    (1e-3, 1, 1, stap.STAP_ERR_UNSUPPORTED),
-    (1e-3, 1, 2, stap.STAP_OK),
-    (0.0, 0, 0, stap.STAP_OK),
+@pytest.mark.parametrize("lf,refine,prec,solver,code", [
+    (-1.0, 1, 0, 0, stap.STAP_ERR_INVALID_ARG),
+    (float("nan"), 1, 0, 0, stap.STAP_ERR_INVALID_ARG),
+    (1e-3, -1, 0, 0, stap.STAP_ERR_INVALID_ARG),
+    (1e-3, 5, 0, 0, stap.STAP_ERR_INVALID_ARG),
+    (1e-3, 1, 7, 0, stap.STAP_ERR_UNSUPPORTED),
+    (1e-3, 1, 1, 0, stap.STAP_ERR_UNSUPPORTED),
+    (1e-3, 1, 2, 0, stap.STAP_OK),
+    (0.0, 0, 0, 0, stap.STAP_OK),
+    (1e-3, 2, 0, 1, stap.STAP_OK),             # mixed-precision refinement, D = 12
+    (1e-3, 2, 2, 1, stap.STAP_OK),
+    (1e-3, 2, 0, 2, stap.STAP_ERR_UNSUPPORTED),
 ])
-def test_plan_create_checks_options(lf, refine, prec, code):
-    got, h, _ = _create(GOOD, stap.stap_options(lf, refine, prec))
+def test_plan_create_checks_options(lf, refine, prec, solver, code):
+    got, h, _ = _create(GOOD, stap.stap_options(lf, refine, prec, solver))
     assert got == code
     if h.value:
         stap.stap_plan_destroy(h)
+
+
+def test_options_default_and_mixed_refinement_shape_limits():
+    o = stap.stap_options_default()
+    assert o.solver == stap.STAP_SOLVE_FP64
+    mir = stap.stap_options(1e-3, 2, 0, stap.STAP_SOLVE_MIXED_IR)
+    for dims, code in [((4, 16, 32, 256, 2, 32, 4), stap.STAP_OK),          # D = 8
+                       ((8, 16, 32, 256, 2, 32, 4), stap.STAP_OK),          # D = 16
+                       ((5, 16, 32, 256, 2, 32, 4), stap.STAP_ERR_UNSUPPORTED),   # D = 10
+                       ((16, 16, 32, 256, 4, 32, 4), stap.STAP_ERR_UNSUPPORTED)]:  # D = 64
+        got, h, _ = _create(dims, mir)
+        assert got == code, dims
+        if h.value:
+            stap.stap_plan_destroy(h)
 
 
 def test_null_and_misaligned_pointers_and_missing_workspace_fail_before_cuda():

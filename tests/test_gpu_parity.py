@@ -292,3 +292,66 @@ def test_not_positive_definite_flagged_by_both_small_solves(kind):
     good = status == 0
     err = np.linalg.norm(wts[good] - ref[good], axis=-1) / np.linalg.norm(ref[good], axis=-1)
     assert np.max(err) <= 2 * EPS32 * np.sqrt(2)
+
+
+# ---- mixed-precision iterative refinement (STAP_SOLVE_MIXED_IR) ----
+# Each refinement step shrinks the FP32 solve's error by about cond(Rl) 2^-24
+# (cond ~ 1e3 D with the default load): after two steps the weights are at
+# their complex64 rounding, like the FP64 solve's; one step leaves about
+# (cond 2^-24)^2.
+
+@pytest.mark.parametrize("refine", [1, 2, 3])
+@pytest.mark.parametrize("separable", [True, False], ids=["sep", "explicit"])
+@pytest.mark.parametrize("name", list(REG_SPECS))
+def test_mixed_refinement_weights_match_the_oracle(name, separable, refine):
+    spec = REG_SPECS[name]
+    d = oracle.Dims(*spec.dims())
+    cov = oracle.covariance(d, oracle.doppler(d, _cube(spec)))
+    ref, _, nf = oracle.weights(d, cov)
+    assert nf == 0
+    plan = _plan(spec, refine_steps=refine, solver=stap.STAP_SOLVE_MIXED_IR)
+    if not separable:
+        plan.set_steering(oracle.default_steering(d))
+    wts = to_np(plan.solve_weights(_dev(cov, torch.complex128)))
+    assert plan.status() == (stap.STAP_OK, 0)
+    err = np.linalg.norm(wts - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+    print(f"{name} refine={refine}: max weight error {np.max(err):.3e}")
+    bar = 1e-4 if refine == 1 else 4 * EPS32
+    assert np.max(err) <= bar, np.max(err)
+    plan.close()
+
+
+@pytest.mark.parametrize("spec", [synth.small_cpi(), synth.standard_cpi()], ids=["small", "standard"])
+def test_mixed_refinement_end_to_end_meets_the_plain_bar(spec):
+    d = oracle.Dims(*spec.dims())
+    cube = _cube(spec)
+    ref = oracle.run(d, cube)["out"]
+    plan = _plan(spec, refine_steps=2, solver=stap.STAP_SOLVE_MIXED_IR)
+    out = to_np(plan.run_cpi(_dev(cube, torch.complex64)))
+    assert plan.status() == (stap.STAP_OK, 0)
+    e_cell, e_norm = power_errors(out, ref)
+    print(f"{spec.dims()} mixed refinement: max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
+    assert e_norm <= 1e-5 and e_cell <= 1e-3
+
+
+def test_mixed_refinement_flags_breakdown():
+    spec = synth.CPISpec(4, 4, 4, 12, 2, 4, 3, cnr_db=None, seed=52)   # D = 8, 4 x 3 systems
+    d = oracle.Dims(*spec.dims())
+    rng = np.random.default_rng(6)
+    cov = np.zeros((4, 3, 8, 8), np.complex128)
+    for k in range(4):
+        for b in range(3):
+            M = rng.standard_normal((8, 8)) + 1j * rng.standard_normal((8, 8))
+            cov[k, b] = M @ M.conj().T + np.eye(8)
+    cov[0, 1] = -np.eye(8)
+    cov[2, 2, 0, 0] = np.nan
+    ref, status, nf = oracle.weights(d, cov)
+    assert nf == 2
+    plan = _plan(spec, refine_steps=2, solver=stap.STAP_SOLVE_MIXED_IR)
+    wts = to_np(plan.solve_weights(_dev(cov, torch.complex128)))
+    code, failed = plan.status()
+    assert code == stap.STAP_ERR_NOT_POSDEF and failed == 2
+    assert np.all(wts[0, 1] == 0) and np.all(wts[2, 2] == 0)
+    good = status == 0
+    err = np.linalg.norm(wts[good] - ref[good], axis=-1) / np.linalg.norm(ref[good], axis=-1)
+    assert np.max(err) <= 4 * EPS32
