@@ -128,29 +128,30 @@ __device__ __forceinline__ void sep_emit(const float4* Wt, int D, int S, int C, 
       ui = ff::fma(ff::fma(ui, ar, xi), ai, xr);
     }
   };
+  // one combination pass: u_s rounded to FP32 goes straight to the weights
+  // (the value the scaling multiplies), then a pass over them scales by
+  // 1/sqrt(Re v^H u) once that is known
   for (int s0 = 0; s0 < S; s0 += TS) {
     const int s = s0 + tl;
     if (s < S) {
       const float4* v = steer_ff + (size_t)s * D;
+      float2* ws = w ? w + (size_t)s * D : nullptr;
       ff::F2 q{0.f, 0.f};                   // Re v^H u
       for (int i = 0; i < D; ++i) {
         ff::F2 ur, ui;
         combine(s, i, ur, ui);
         const float4 vi = __ldg(v + i);
         q = ff::fma(ff::fma(q, {vi.x, vi.y}, ur), {vi.z, vi.w}, ui);
+        if (ws) ws[i] = make_float2(__fadd_rn(ur.hi, ur.lo), __fadd_rn(ui.hi, ui.lo));
       }
       const double qd = ff::to_double(q);
       const bool good = ok && qd > 0.0 && isfinite(qd);
       const float sf = good ? (float)rsqrt(qd) : 0.f;
-      if (w) {
-        float2* ws = w + (size_t)s * D;
+      if (ws)
         for (int i = 0; i < D; ++i) {
-          ff::F2 ur, ui;
-          combine(s, i, ur, ui);
-          ws[i] = good ? make_float2(__fadd_rn(ur.hi, ur.lo) * sf, __fadd_rn(ui.hi, ui.lo) * sf)
-                       : make_float2(0.f, 0.f);
+          const float2 u = ws[i];
+          ws[i] = good ? make_float2(u.x * sf, u.y * sf) : make_float2(0.f, 0.f);
         }
-      }
     }
   }
 }
@@ -534,17 +535,32 @@ __host__ __device__ constexpr size_t mir_warp_bytes(int D, int G, bool sep) {
          ((size_t)G * D * 4 + 15) / 16 * 16;
 }
 
-// acc -= a * b and acc -= conj(a) * b on double-float complex numbers
-__device__ __forceinline__ void ff_cfms(ff::F2& accr, ff::F2& acci, float4 a, ff::F2 br, ff::F2 bi) {
-  const ff::F2 ar{a.x, a.y}, ai{a.z, a.w};
-  accr = ff::fma(ff::fms(accr, ar, br), ai, bi);
-  acci = ff::fms(ff::fms(acci, ar, bi), ai, br);
+// A compensated sum of double-float products (Dot2 of Ogita, Rump and Oishi,
+// extended to double-float factors): s collects the rounded products with
+// TwoSum, e every rounding error and the cross terms; the value is s + e.
+struct Dot2 {
+  float s, e;
+};
+
+// acc += (ah + al) * (bh + bl), dropping al * bl (below 2^-48 of the product)
+__device__ __forceinline__ void dot2_add(Dot2& acc, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float pe = __fmaf_rn(ah, bh, -p);
+  pe = __fmaf_rn(ah, bl, pe);
+  pe = __fmaf_rn(al, bh, pe);
+  const float t = __fadd_rn(acc.s, p);
+  const float z = __fsub_rn(t, acc.s);
+  const float te = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  acc.s = t;
+  acc.e = __fadd_rn(acc.e, __fadd_rn(te, pe));
 }
-__device__ __forceinline__ void ff_cfms_conj(ff::F2& accr, ff::F2& acci, float4 a, ff::F2 br,
-                                             ff::F2 bi) {
-  const ff::F2 ar{a.x, a.y}, ai{a.z, a.w};
-  accr = ff::fms(ff::fms(accr, ar, br), ai, bi);
-  acci = ff::fma(ff::fms(acci, ar, bi), ai, br);
+
+// accr + i acci -= a * u   (a = (re_hi, re_lo, im_hi, im_lo), u = ur + i ui)
+__device__ __forceinline__ void dot2_cfms(Dot2& accr, Dot2& acci, float4 a, ff::F2 ur, ff::F2 ui) {
+  dot2_add(accr, -a.x, -a.y, ur.hi, ur.lo);
+  dot2_add(accr, a.z, a.w, ui.hi, ui.lo);
+  dot2_add(acci, -a.x, -a.y, ui.hi, ui.lo);
+  dot2_add(acci, -a.z, -a.w, ur.hi, ur.lo);
 }
 
 template <int D, bool SEP>
@@ -690,9 +706,11 @@ solve_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
         // loop is not unrolled (fully unrolled it is too large, and the
         // solution would leave the registers); row i goes to this lane's
         // column of Rs.  Above the diagonal Rl[i][l] = conj(Rl[l][i]).
+        // Two compensated sums per component (even and odd l) keep two
+        // independent dependency chains in flight.
         for (int i = 0; i < D; ++i) {
           const float4 b = rhs_ff(i);
-          ff::F2 rr{b.x, b.y}, ri{b.z, b.w};
+          Dot2 rr{b.x, b.y}, ri{b.z, b.w}, rr2{0.f, 0.f}, ri2{0.f, 0.f};
 #pragma unroll
           for (int l = 0; l < D; ++l) {
             const bool low = l <= i;
@@ -701,9 +719,12 @@ solve_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
               a.z = -a.z;
               a.w = -a.w;
             }
-            ff_cfms(rr, ri, a, ur[l], ui[l]);
+            if (l & 1) dot2_cfms(rr2, ri2, a, ur[l], ui[l]);
+            else dot2_cfms(rr, ri, a, ur[l], ui[l]);
           }
-          Rs[i * 32] = make_float2(__fadd_rn(rr.hi, rr.lo), __fadd_rn(ri.hi, ri.lo));
+          const float xr = __fadd_rn(__fadd_rn(rr.s, rr2.s), __fadd_rn(rr.e, rr2.e));
+          const float xi = __fadd_rn(__fadd_rn(ri.s, ri2.s), __fadd_rn(ri.e, ri2.e));
+          Rs[i * 32] = make_float2(xr, xi);
         }
 #pragma unroll
         for (int i = 0; i < D; ++i) x[i] = Rs[i * 32];

@@ -25,6 +25,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--slabs", type=int, default=0, help="override the tuned range slabs (0 = keep)")
+    ap.add_argument("--solver", default="fp64", choices=["fp64", "mixed_ir"])
+    ap.add_argument("--refine", type=int, default=None,
+                    help="refinement steps (default: 1 for fp64, 2 for mixed_ir)")
     a = ap.parse_args(argv)
     spec = synth.WORKLOADS[a.workload]()
     if isinstance(spec, (list, tuple)):
@@ -33,7 +36,9 @@ def main(argv=None):
     torch.cuda.set_device(dev)
     prec = stap.STAP_PREC_FP32 if a.precision == "fp32" else stap.STAP_PREC_TF32X3
     cube = synth.make_cube_torch(spec, dev)
-    plan = stap.Plan(spec.dims(), device=dev, precision=prec)
+    solver = stap.STAP_SOLVE_FP64 if a.solver == "fp64" else stap.STAP_SOLVE_MIXED_IR
+    refine = a.refine if a.refine is not None else (1 if a.solver == "fp64" else 2)
+    plan = stap.Plan(spec.dims(), device=dev, precision=prec, refine_steps=refine, solver=solver)
     out = torch.empty(plan.shapes(0)["out"], dtype=torch.float32, device=dev)
     tuning = plan.autotune(cube, out)
     if a.slabs > 0:
@@ -50,7 +55,7 @@ def main(argv=None):
     torch.cuda.profiler.stop()
     code, failed = plan.status()
     plan.close()
-    print(f"{a.workload} {a.precision}: dims {spec.dims()}, tuning {tuning}, "
+    print(f"{a.workload} {a.precision} {a.solver} refine {refine}: dims {spec.dims()}, tuning {tuning}, "
           f"slabs override {a.slabs}, {a.steps} steps, status {code} ({failed} failed)")
     if code != stap.STAP_OK:
         raise SystemExit(1)
