@@ -342,7 +342,7 @@ def run_gpu(args):
     # ---- mixed-precision iterative refinement of the solve (an option beyond
     # the paper's FP64 solve: FP32 factorisation, double-float residuals) ----
     mixed_ir = None
-    if stap.stap_abi_version() >= 2 and C * T in (8, 12, 16):
+    if stap.stap_abi_version() >= 2 and (C * T in (8, 12, 16) or 32 < C * T <= 64):
         iplan = stap.Plan(spec.dims(), device=dev, refine_steps=2, solver=stap.STAP_SOLVE_MIXED_IR)
         iout = torch.empty_like(out)
         ituning = iplan.autotune(cube, iout)

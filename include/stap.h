@@ -78,8 +78,8 @@ typedef enum {
                              for the correction in FP32 and adds it to the
                              double-float solution.  Each step shrinks the error
                              by about cond(Rl) 2^-24; 2 steps reach FP32 weight
-                             accuracy for cond(Rl) up to about 1e5.  D = 8, 12
-                             or 16 only (STAP_ERR_UNSUPPORTED otherwise) */
+                             accuracy for cond(Rl) up to about 1e5.  D = 8, 12,
+                             16 or 33..64 (STAP_ERR_UNSUPPORTED otherwise) */
 } stap_solver;
 
 typedef struct {

@@ -1110,6 +1110,329 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision iterative refinement for 32 < D <= 64 (STAP_SOLVE_MIXED_IR),
+// with the layout of solve_big_kernel: one system per CTA, LR lanes per
+// right-hand side holding RPL rows each.  Rl is kept in shared memory as
+// double-floats (column-major packed) next to its FP32 part, which is factored
+// as Lu Dg Lu^H in FP32; each right-hand side is solved in FP32 and refined
+// with residuals formed from the double-float Rl by compensated (Dot2) sums on
+// the FP32 pipe, the correction solved in FP32 and added to the double-float
+// solution.
+__host__ __device__ constexpr size_t big_mir_bytes(int D, int C, int NG, bool sep) {
+  // Rl [Dp] float4, (SEP) basis solutions [C][D] float4, broadcast solutions
+  // [NG][D] float4, FP32 factor [Dp] float2, pivot column [D] float2, pivot
+  // reciprocals [D] float, the pivot flag
+  return ((size_t)(D * (D + 1) / 2) + (sep ? (size_t)C * D : 0) + (size_t)NG * D) * 16 +
+         (size_t)(D * (D + 1) / 2) * 8 + (size_t)D * 8 + (size_t)D * 4 + 16;
+}
+
+// In-place FP32 forward (Lu z = x) or back (Lu^H z = x) substitution, as big_subst.
+template <int LR, int RPL, bool BACK>
+__device__ __forceinline__ void big_subst_f32(float2 (&x)[RPL], const float2* __restrict__ Lc,
+                                              int D, int li, int grp) {
+  for (int jj = 0; jj < D; ++jj) {
+    const int j = BACK ? D - 1 - jj : jj;
+    const int owner = (j % LR) + grp * LR, qj = j / LR;
+    float2 pick = x[0];
+#pragma unroll
+    for (int q = 1; q < RPL; ++q)
+      if (q == qj) pick = x[q];
+    float2 yj;
+    yj.x = __shfl_sync(0xffffffffu, pick.x, owner);
+    yj.y = __shfl_sync(0xffffffffu, pick.y, owner);
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const bool touch = (BACK ? (q <= qj) : (q >= qj)) && LR * q < D;
+      if (touch) {
+        const int i = li + LR * q;
+        const bool act = BACK ? (i < j) : (i > j && i < D);
+        if (act) {
+          if (BACK) {
+            const float2 l = Lc[colstart(i, D) + j - i];
+            x[q].x = fmaf(-l.x, yj.x, x[q].x);
+            x[q].x = fmaf(-l.y, yj.y, x[q].x);
+            x[q].y = fmaf(-l.x, yj.y, x[q].y);
+            x[q].y = fmaf(l.y, yj.x, x[q].y);
+          } else {
+            const float2 l = Lc[colstart(j, D) + i - j];
+            x[q].x = fmaf(-l.x, yj.x, x[q].x);
+            x[q].x = fmaf(l.y, yj.y, x[q].x);
+            x[q].y = fmaf(-l.x, yj.y, x[q].y);
+            x[q].y = fmaf(-l.y, yj.x, x[q].y);
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int LR, int RPL>
+__device__ __forceinline__ void big_solve_f32(float2 (&x)[RPL], const float2* __restrict__ Lc,
+                                              const float* __restrict__ rd, int D, int li, int grp) {
+  big_subst_f32<LR, RPL, false>(x, Lc, D, li, grp);
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    if (LR * q < D) {
+      const int i = li + LR * q;
+      const float r = rd[i < D ? i : D - 1];
+      x[q].x *= r;
+      x[q].y *= r;
+    }
+  }
+  big_subst_f32<LR, RPL, true>(x, Lc, D, li, grp);
+}
+
+template <bool SEP, int LR, int NT, int RPL>
+__global__ void __launch_bounds__(NT)
+solve_big_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
+                     const float4* __restrict__ steer_ff, const float4* __restrict__ g_ff,
+                     const float4* __restrict__ sep_a_ff, long long nsys, int D, int S, int C,
+                     double load_factor, int refine_steps, DeviceStatus* __restrict__ status) {
+  extern __shared__ float4 sm4[];
+  constexpr int NW = NT / 32;
+  constexpr int NG = NT / LR;
+  const int Dp = D * (D + 1) / 2;
+  float4* Ad = sm4;                                   // [Dp] Rl, double-float, column-major
+  float4* Ubf = Ad + Dp;                              // SEP: [C][D] basis solutions
+  float4* uvf = Ubf + (SEP ? (size_t)C * D : 0);      // [NG][D] broadcast solutions
+  float2* Lf = reinterpret_cast<float2*>(uvf + (size_t)NG * D);   // [Dp] FP32 Lu
+  float2* colb = Lf + Dp;                             // [D] pivot column before division
+  float* rd = reinterpret_cast<float*>(colb + D);     // [D] pivot reciprocals
+  int* okf = reinterpret_cast<int*>(rd + D);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int li = lane % LR, grp = lane / LR;
+  const int g = warp * (32 / LR) + grp;
+  const double invD = 1.0 / (double)D;
+
+  auto pivot = [&](float d) -> float {
+    if (!(d > 0.f) || !isfinite(d)) {
+      *okf = 0;
+      return 1.f;
+    }
+    return 1.0f / d;
+  };
+
+  for (long long sys = blockIdx.x; sys < nsys; sys += gridDim.x) {
+    const double2* A = cov + (size_t)sys * D * D;
+    double tr = 0.0;
+    for (int j = 0; j < D; ++j) tr += __ldg(&A[(size_t)j * D + j].x);
+    const double delta = load_factor * tr * invD;
+    for (int i = warp; i < D; i += NW)
+      for (int l = lane; l <= i; l += 32) {
+        const float4 f = to_ff4(loaded(A, D, i, l, delta));
+        Ad[colstart(l, D) + i - l] = f;
+        Lf[colstart(l, D) + i - l] = make_float2(f.x, f.z);
+      }
+    __syncthreads();
+    if (tid == 0) {
+      *okf = 1;
+      rd[0] = pivot(Lf[0].x);
+    }
+    __syncthreads();
+
+    for (int j = 0; j < D; ++j) {   // FP32 Lu Dg Lu^H, as in solve_big_kernel
+      const int cj = colstart(j, D);
+      const float rj = rd[j];
+      for (int i = j + 1 + tid; i < D; i += NT) {
+        const float2 v = Lf[cj + i - j];
+        colb[i] = v;
+        Lf[cj + i - j] = make_float2(v.x * rj, v.y * rj);
+      }
+      __syncthreads();
+      const int m = D - j - 1;
+      const int np = m * (m + 1) / 2;
+      int a = 0, off = tid;
+      while (a < m && off >= m - a) off -= m - a++;
+      for (int q = tid; q < np; q += NT) {
+        const int l = j + 1 + a, i = l + off;
+        const float2 lij = Lf[cj + i - j], alj = colb[l];
+        float2 acc = Lf[colstart(l, D) + i - l];
+        acc.x = fmaf(-lij.x, alj.x, acc.x);
+        acc.x = fmaf(-lij.y, alj.y, acc.x);
+        acc.y = fmaf(-lij.y, alj.x, acc.y);
+        acc.y = fmaf(lij.x, alj.y, acc.y);
+        Lf[colstart(l, D) + i - l] = acc;
+        if (q == 0) rd[j + 1] = pivot(acc.x);
+        off += NT;
+        while (a < m && off >= m - a) off -= m - a++;
+      }
+      __syncthreads();
+    }
+    const bool ok = *okf != 0;
+
+    const int nrhs = SEP ? C : S;
+    for (int r0 = 0; r0 < nrhs; r0 += NG) {
+      const int rhs = r0 + g;
+      const bool live = rhs < nrhs;
+      const int rsafe = live ? rhs : 0;
+      auto rhs_ff = [&](int i) -> float4 {
+        if (i >= D) return make_float4(0.f, 0.f, 0.f, 0.f);
+        if (SEP) {
+          const int t = i / C;
+          return (i - t * C == rsafe) ? __ldg(g_ff + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        return __ldg(steer_ff + (size_t)rsafe * D + i);
+      };
+      float2 x[RPL];
+      ff::F2 ur[RPL], ui[RPL];
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const float4 b = rhs_ff(li + LR * q);
+        x[q] = make_float2(b.x, b.z);
+      }
+      big_solve_f32<LR, RPL>(x, Lf, rd, D, li, grp);
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        ur[q] = ff::F2{x[q].x, 0.f};
+        ui[q] = ff::F2{x[q].y, 0.f};
+      }
+      for (int it = 0; it < refine_steps; ++it) {
+        // x = fl32(b - Rl u): u broadcast through shared memory, Rl[i][l]
+        // from the double-float copy (conjugated above the diagonal)
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+          if (li + LR * q < D)
+            uvf[g * D + li + LR * q] = make_float4(ur[q].hi, ur[q].lo, ui[q].hi, ui[q].lo);
+        __syncwarp();
+        Dot2 rr[RPL], ri[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const float4 b = rhs_ff(li + LR * q);
+          rr[q] = Dot2{b.x, b.y};
+          ri[q] = Dot2{b.z, b.w};
+        }
+        for (int l = 0; l < D; ++l) {
+          const float4 ul = uvf[g * D + l];
+          const ff::F2 ulr{ul.x, ul.y}, uli{ul.z, ul.w};
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            if (LR * q < D) {
+              const int i = li + LR * q;
+              const int ic = i < D ? i : D - 1;
+              const bool low = ic >= l;
+              float4 a = Ad[low ? colstart(l, D) + ic - l : colstart(ic, D) + l - ic];
+              if (!low) {
+                a.z = -a.z;
+                a.w = -a.w;
+              }
+              dot2_cfms(rr[q], ri[q], a, ulr, uli);
+            }
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < RPL; ++q)
+          x[q] = make_float2(__fadd_rn(rr[q].s, rr[q].e), __fadd_rn(ri[q].s, ri[q].e));
+        big_solve_f32<LR, RPL>(x, Lf, rd, D, li, grp);
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          ur[q] = ff::add(ur[q], x[q].x);
+          ui[q] = ff::add(ui[q], x[q].y);
+        }
+      }
+      if (SEP) {
+        if (live)
+#pragma unroll
+          for (int q = 0; q < RPL; ++q)
+            if (li + LR * q < D)
+              Ubf[(size_t)rhs * D + li + LR * q] = make_float4(ur[q].hi, ur[q].lo, ui[q].hi, ui[q].lo);
+      } else {
+        // Re v^H u over the group, the scale, the weights
+        ff::F2 qp{0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const int i = li + LR * q;
+          if (i < D) {
+            const float4 v = __ldg(steer_ff + (size_t)rsafe * D + i);
+            qp = ff::fma(ff::fma(qp, ff::F2{v.x, v.y}, ur[q]), ff::F2{v.z, v.w}, ui[q]);
+          }
+        }
+        const double qs = group_sum<LR>(ff::to_double(qp));
+        const bool good = ok && qs > 0.0 && isfinite(qs);
+        const float sf = good ? (float)rsqrt(qs) : 0.f;
+        if (live) {
+          float2* w = wts + ((size_t)sys * S + rhs) * D;
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            const int i = li + LR * q;
+            if (i < D)
+              w[i] = good ? make_float2(__fadd_rn(ur[q].hi, ur[q].lo) * sf, __fadd_rn(ui[q].hi, ui[q].lo) * sf)
+                          : make_float2(0.f, 0.f);
+          }
+        }
+      }
+    }
+    if (SEP) {   // the combination, as in solve_big_kernel
+      __syncthreads();
+      for (int s0 = 0; s0 < S; s0 += NG) {
+        const int s = s0 + g;
+        const int ssafe = s < S ? s : 0;
+        const float4* as = sep_a_ff + (size_t)ssafe * C;
+        ff::F2 cr[RPL], ci[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) cr[q] = ci[q] = ff::F2{0.f, 0.f};
+        for (int c = 0; c < C; ++c) {
+          const float4 a = __ldg(as + c);
+          const ff::F2 ar{a.x, a.y}, ai{a.z, a.w};
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            if (LR * q < D) {
+              const int i = li + LR * q;
+              const float4 xv = Ubf[(size_t)c * D + (i < D ? i : D - 1)];
+              const ff::F2 xr{xv.x, xv.y}, xi{xv.z, xv.w};
+              cr[q] = ff::fms(ff::fma(cr[q], ar, xr), ai, xi);
+              ci[q] = ff::fma(ff::fma(ci[q], ar, xi), ai, xr);
+            }
+          }
+        }
+        const float4* v = steer_ff + (size_t)ssafe * D;
+        ff::F2 qp{0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const int i = li + LR * q;
+          if (i < D) {
+            const float4 vi = __ldg(v + i);
+            qp = ff::fma(ff::fma(qp, {vi.x, vi.y}, cr[q]), {vi.z, vi.w}, ci[q]);
+          }
+        }
+        const double qs = group_sum<LR>(ff::to_double(qp));
+        const bool good = ok && qs > 0.0 && isfinite(qs);
+        const float sf = good ? (float)rsqrt(qs) : 0.f;
+        if (s < S) {
+          float2* w = wts + ((size_t)sys * S + s) * D;
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            const int i = li + LR * q;
+            if (i < D)
+              w[i] = good ? make_float2(__fadd_rn(cr[q].hi, cr[q].lo) * sf,
+                                        __fadd_rn(ci[q].hi, ci[q].lo) * sf)
+                          : make_float2(0.f, 0.f);
+          }
+        }
+      }
+    }
+    if (!ok && tid == 0) atomicAdd(&status->n_failed, 1ULL);
+    __syncthreads();  // the next system reuses every shared array
+  }
+}
+
+template <bool SEP, int LR, int NT, int RPL>
+cudaError_t launch_big_mir(const double2* cov, float2* wts, const float4* steer_ff, const float4* g_ff,
+                           const float4* sep_a_ff, long long nsys, int D, int S, int C, double lf,
+                           int refine, DeviceStatus* status, size_t smem, cudaStream_t s) {
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  static int set_bytes[64] = {0};
+  cudaError_t e = ensure_smem(solve_big_mir_kernel<SEP, LR, NT, RPL>, smem, set_bytes);
+  if (e != cudaSuccess) return e;
+  const int per_sm = (int)(228 * 1024 / (smem + 1024));
+  long long blocks = 152LL * (per_sm < 1 ? 1 : per_sm) * 2;
+  if (blocks > nsys) blocks = nsys;
+  solve_big_mir_kernel<SEP, LR, NT, RPL><<<(unsigned)blocks, NT, smem, s>>>(
+      cov, wts, steer_ff, g_ff, sep_a_ff, nsys, D, S, C, lf, refine, status);
+  return cudaGetLastError();
+}
+
 template <bool SEP, int LR, int NT, int RPL>
 cudaError_t launch_big(const double2* cov, float2* wts, const double2* steer, const double2* sep_g,
                        const float4* steer_ff, const float4* sep_a_ff, long long nsys, int D, int S,
@@ -1156,7 +1479,7 @@ cudaError_t launch_mir(const double2* cov, float2* wts, const float4* steer_ff, 
 
 }  // namespace
 
-bool mir_supported(int D) { return D == 8 || D == 12 || D == 16; }
+bool mir_supported(int D) { return D == 8 || D == 12 || D == 16 || (D > kSmallMaxD && D <= 64); }
 
 namespace {
 
@@ -1177,6 +1500,22 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
   if (D < 1 || D > kMaxD || S < 1) return cudaErrorInvalidValue;
   const bool sep = sep_g != nullptr && sep_a != nullptr && steer_ff != nullptr && sep_a_ff != nullptr &&
                    C >= 1 && C <= 32 && D % C == 0;
+  if (solver == 1 && D > kSmallMaxD) {  // mixed-precision refinement, 32 < D <= 64
+    if (!mir_supported(D) || steer_ff == nullptr) return cudaErrorNotSupported;
+    const bool msep = sep && g_ff != nullptr;
+    const int LR = (tn.solve_lr == 16) ? 16 : 8;     // 8 lanes x 8 rows or 16 x 4
+    const int NG = 128 / LR;
+    const size_t smem = big_mir_bytes(D, C, NG, msep);
+    if (LR == 8)
+      return msep ? launch_big_mir<true, 8, 128, 8>(cov, wts, steer_ff, g_ff, sep_a_ff, nsys, D, S, C,
+                                                   load_factor, refine_steps, status, smem, s)
+                  : launch_big_mir<false, 8, 128, 8>(cov, wts, steer_ff, nullptr, nullptr, nsys, D, S,
+                                                    C, load_factor, refine_steps, status, smem, s);
+    return msep ? launch_big_mir<true, 16, 128, 4>(cov, wts, steer_ff, g_ff, sep_a_ff, nsys, D, S, C,
+                                                  load_factor, refine_steps, status, smem, s)
+                : launch_big_mir<false, 16, 128, 4>(cov, wts, steer_ff, nullptr, nullptr, nsys, D, S, C,
+                                                   load_factor, refine_steps, status, smem, s);
+  }
   if (solver == 1) {  // mixed-precision iterative refinement (D = 8, 12, 16)
     if (!mir_supported(D) || steer_ff == nullptr) return cudaErrorNotSupported;
     const bool msep = sep && g_ff != nullptr;

@@ -300,11 +300,18 @@ def test_not_positive_definite_flagged_by_both_small_solves(kind):
 # their complex64 rounding, like the FP64 solve's; one step leaves about
 # (cond 2^-24)^2.
 
+MIR_SPECS = dict(REG_SPECS)
+MIR_SPECS.update({
+    "D33": synth.CPISpec(11, 16, 16, 96, 3, 48, 7, cnr_db=35.0, seed=24),     # odd D, S % 8 != 0
+    "D64": synth.CPISpec(16, 32, 64, 256, 4, 128, 8, cnr_db=40.0, seed=14),
+})
+
+
 @pytest.mark.parametrize("refine", [1, 2, 3])
 @pytest.mark.parametrize("separable", [True, False], ids=["sep", "explicit"])
-@pytest.mark.parametrize("name", list(REG_SPECS))
+@pytest.mark.parametrize("name", list(MIR_SPECS))
 def test_mixed_refinement_weights_match_the_oracle(name, separable, refine):
-    spec = REG_SPECS[name]
+    spec = MIR_SPECS[name]
     d = oracle.Dims(*spec.dims())
     cov = oracle.covariance(d, oracle.doppler(d, _cube(spec)))
     ref, _, nf = oracle.weights(d, cov)
@@ -321,7 +328,8 @@ def test_mixed_refinement_weights_match_the_oracle(name, separable, refine):
     plan.close()
 
 
-@pytest.mark.parametrize("spec", [synth.small_cpi(), synth.standard_cpi()], ids=["small", "standard"])
+@pytest.mark.parametrize("spec", [synth.small_cpi(), synth.standard_cpi(), MIR_SPECS["D64"]],
+                         ids=["small", "standard", "D64"])
 def test_mixed_refinement_end_to_end_meets_the_plain_bar(spec):
     d = oracle.Dims(*spec.dims())
     cube = _cube(spec)
@@ -331,7 +339,8 @@ def test_mixed_refinement_end_to_end_meets_the_plain_bar(spec):
     assert plan.status() == (stap.STAP_OK, 0)
     e_cell, e_norm = power_errors(out, ref)
     print(f"{spec.dims()} mixed refinement: max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
-    assert e_norm <= 1e-5 and e_cell <= 1e-3
+    g = growth(spec)
+    assert e_norm <= 1e-5 * g and e_cell <= 1e-3 * g
 
 
 def test_mixed_refinement_flags_breakdown():
@@ -352,6 +361,29 @@ def test_mixed_refinement_flags_breakdown():
     code, failed = plan.status()
     assert code == stap.STAP_ERR_NOT_POSDEF and failed == 2
     assert np.all(wts[0, 1] == 0) and np.all(wts[2, 2] == 0)
+    good = status == 0
+    err = np.linalg.norm(wts[good] - ref[good], axis=-1) / np.linalg.norm(ref[good], axis=-1)
+    assert np.max(err) <= 4 * EPS32
+
+
+def test_large_mixed_refinement_flags_breakdown():
+    spec = synth.CPISpec(16, 4, 4, 12, 3, 4, 5, cnr_db=None, seed=53)   # D = 48, 4 x 3 systems
+    d = oracle.Dims(*spec.dims())
+    rng = np.random.default_rng(7)
+    cov = np.zeros((4, 3, 48, 48), np.complex128)
+    for k in range(4):
+        for b in range(3):
+            M = rng.standard_normal((48, 48)) + 1j * rng.standard_normal((48, 48))
+            cov[k, b] = M @ M.conj().T + np.eye(48)
+    cov[1, 0] = -np.eye(48)
+    cov[3, 2, 20, 20] = np.inf
+    ref, status, nf = oracle.weights(d, cov)
+    assert nf == 2
+    plan = _plan(spec, refine_steps=2, solver=stap.STAP_SOLVE_MIXED_IR)
+    wts = to_np(plan.solve_weights(_dev(cov, torch.complex128)))
+    code, failed = plan.status()
+    assert code == stap.STAP_ERR_NOT_POSDEF and failed == 2
+    assert np.all(wts[1, 0] == 0) and np.all(wts[3, 2] == 0)
     good = status == 0
     err = np.linalg.norm(wts[good] - ref[good], axis=-1) / np.linalg.norm(ref[good], axis=-1)
     assert np.max(err) <= 4 * EPS32
