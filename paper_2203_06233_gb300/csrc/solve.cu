@@ -1122,9 +1122,9 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
 __host__ __device__ constexpr size_t big_mir_bytes(int D, int C, int NG, bool sep) {
   // Rl [Dp] float4, (SEP) basis solutions [C][D] float4, broadcast solutions
   // [NG][D] float4, FP32 factor [Dp] float2, pivot column [D] float2, pivot
-  // reciprocals [D] float, the pivot flag
+  // reciprocals [D] float, the pivot flag and the trace
   return ((size_t)(D * (D + 1) / 2) + (sep ? (size_t)C * D : 0) + (size_t)NG * D) * 16 +
-         (size_t)(D * (D + 1) / 2) * 8 + (size_t)D * 8 + (size_t)D * 4 + 16;
+         (size_t)(D * (D + 1) / 2) * 8 + (size_t)D * 8 + ((size_t)D * 4 + 15) / 16 * 16 + 32;
 }
 
 // In-place FP32 forward (Lu z = x) or back (Lu^H z = x) substitution, as big_subst.
@@ -1199,7 +1199,9 @@ solve_big_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
   float2* Lf = reinterpret_cast<float2*>(uvf + (size_t)NG * D);   // [Dp] FP32 Lu
   float2* colb = Lf + Dp;                             // [D] pivot column before division
   float* rd = reinterpret_cast<float*>(colb + D);     // [D] pivot reciprocals
-  int* okf = reinterpret_cast<int*>(rd + D);
+  char* tail = reinterpret_cast<char*>(rd) + ((size_t)D * 4 + 15) / 16 * 16;
+  int* okf = reinterpret_cast<int*>(tail);                        // pivots all positive
+  double* trs = reinterpret_cast<double*>(tail + 16);             // the trace, from warp 0
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int li = lane % LR, grp = lane / LR;
   const int g = warp * (32 / LR) + grp;
@@ -1215,9 +1217,14 @@ solve_big_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
 
   for (long long sys = blockIdx.x; sys < nsys; sys += gridDim.x) {
     const double2* A = cov + (size_t)sys * D * D;
-    double tr = 0.0;
-    for (int j = 0; j < D; ++j) tr += __ldg(&A[(size_t)j * D + j].x);
-    const double delta = load_factor * tr * invD;
+    if (warp == 0) {   // Re tr(R) by one warp: lanes over the diagonal, then a shuffle sum
+      double tr = 0.0;
+      for (int j = lane; j < D; j += 32) tr += __ldg(&A[(size_t)j * D + j].x);
+      tr = group_sum<32>(tr);
+      if (lane == 0) *trs = tr;
+    }
+    __syncthreads();
+    const double delta = load_factor * *trs * invD;
     for (int i = warp; i < D; i += NW)
       for (int l = lane; l <= i; l += 32) {
         const float4 f = to_ff4(loaded(A, D, i, l, delta));
@@ -1302,6 +1309,15 @@ solve_big_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
           rr[q] = Dot2{b.x, b.y};
           ri[q] = Dot2{b.z, b.w};
         }
+        // packed index of Rl[i][l]: colstart(l) + i - l below the diagonal
+        // (colstart advanced incrementally), colstart(i) + l - i above
+        int csi[RPL];
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const int i = li + LR * q;
+          csi[q] = colstart(i < D ? i : D - 1, D);
+        }
+        int csl = 0;
         for (int l = 0; l < D; ++l) {
           const float4 ul = uvf[g * D + l];
           const ff::F2 ulr{ul.x, ul.y}, uli{ul.z, ul.w};
@@ -1311,7 +1327,7 @@ solve_big_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
               const int i = li + LR * q;
               const int ic = i < D ? i : D - 1;
               const bool low = ic >= l;
-              float4 a = Ad[low ? colstart(l, D) + ic - l : colstart(ic, D) + l - ic];
+              float4 a = Ad[low ? csl + ic - l : csi[q] + l - ic];
               if (!low) {
                 a.z = -a.z;
                 a.w = -a.w;
@@ -1319,6 +1335,7 @@ solve_big_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
               dot2_cfms(rr[q], ri[q], a, ulr, uli);
             }
           }
+          csl += D - l;
         }
         __syncwarp();
 #pragma unroll
