@@ -92,8 +92,9 @@ apply_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts, flo
 // weights as D/2 broadcast 16-byte loads and does 8 D FMAs: FMA-bound.
 constexpr int kRegCells = 2 * kThreads;     // range cells per CTA
 
+// registers: 64 (32 warps per SM) while the snapshots fit, more for larger D
 template <int D>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, D <= 12 ? 4 : (D <= 18 ? 3 : 2))
 apply_reg_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
                  float* __restrict__ out, int C, int K, int R, int ldr, int T, int B, int S) {
   extern __shared__ float4 sm4[];

@@ -113,7 +113,7 @@ covariance_ff_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
 // exact because every q lies on that grid and |sum| <= sig/2.  The remainder
 // fma(a, b, -q) (|.| <= ulp(sig)/2) goes to a second FP32 accumulator.  Five
 // FP32 instructions per real product; the pair is combined in FP64 at the end.
-constexpr int kPairThreads = 256;
+constexpr int kPairMaxThreads = 1024;   // one thread per Q entry, up to this
 
 __device__ __forceinline__ float pow2_ceil(float x) {  // smallest power of two >= x
   if (!(x > 0.f)) return 1.0f;
@@ -133,7 +133,7 @@ __device__ __forceinline__ void grid_add(float& hi, float& lo, float a, float b,
   lo = __fadd_rn(lo, r);
 }
 
-__global__ void __launch_bounds__(kPairThreads)
+__global__ void __launch_bounds__(kPairMaxThreads)
 covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K,
                         int ldr, int T, int B, int NB, int KT, int CB) {
   extern __shared__ double2 smd[];
@@ -235,8 +235,8 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
       const double2 v = Q[j1 * Ediag + c2 * (c2 + 1) / 2 + c1];
       return make_double2(v.x, -v.y);
     }
-    int off = NBIN * Ediag;
-    for (int e = 1; e < d; ++e) off += (NBIN - e) * Eoff;
+    // blocks d' < d come first: NBIN Ediag + sum_{e=1}^{d-1} (NBIN - e) Eoff
+    const int off = NBIN * Ediag + Eoff * ((d - 1) * NBIN - d * (d - 1) / 2);
     return Q[off + j1 * Eoff + c1 * C + c2];
   };
   for (int idx = threadIdx.x; idx < KT * D * D; idx += blockDim.x) {
@@ -288,7 +288,18 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
       cudaError_t e = ensure_smem(covariance_pairs_kernel, smem, set_bytes);
       if (e != cudaSuccess) return e;
       dim3 grid(NB, K / KT);
-      covariance_pairs_kernel<<<grid, kPairThreads, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, KT, CB);
+      // one thread per Q entry (rounded up to whole warps, at least 4 and at
+      // most 32 warps), so that the entries are not spread unevenly over a
+      // last, partly idle round of the threads
+      const int nbin = KT + T - 1;
+      const int nitems = nbin * (C * (C + 1) / 2) + (T - 1) * (2 * nbin - T) / 2 * C * C;
+      int threads = (nitems + 31) / 32 * 32;
+      if (threads < 128) threads = 128;
+      if (threads > kPairMaxThreads) threads = (nitems + (nitems + kPairMaxThreads - 1) / kPairMaxThreads - 1) /
+                                               ((nitems + kPairMaxThreads - 1) / kPairMaxThreads);
+      threads = (threads + 31) / 32 * 32;
+      if (threads > kPairMaxThreads) threads = kPairMaxThreads;
+      covariance_pairs_kernel<<<grid, threads, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, KT, CB);
       return cudaGetLastError();
     }
   }
