@@ -322,10 +322,14 @@ def run_gpu(args):
     mdop = mplan.doppler(cube)
     mcov = mplan.covariance(mdop)
     mwts = mplan.solve_weights(mcov)
+    (mchoices,) = mtuning.values()
     mixed = {
         "value": world * cells * args.steps / (sum(mtimes) * 1e-3),
         "ms_per_step": sum(mtimes) / args.steps,
-        "precision": "3xTF32 tensor-core covariance and apply (tcgen05), FP64 solve",
+        "precision": "3xTF32 tensor-core covariance and apply (tcgen05) where the autotuner finds "
+                     "them faster than the FP32 kernels, FP64 solve",
+        "kernels_used": {"covariance": "FP32 error-free" if mchoices[8] == 1 else "tensor cores",
+                         "apply": "FP32" if mchoices[5] in (1, 2) else "tensor cores"},
         "tuning": mtuning,
         "kernels_ms": {
             "doppler": statistics.mean(time_steps(lambda: mplan.doppler(cube, mdop), reps, flush, stream)),
@@ -342,7 +346,7 @@ def run_gpu(args):
     # ---- mixed-precision iterative refinement of the solve (an option beyond
     # the paper's FP64 solve: FP32 factorisation, double-float residuals) ----
     mixed_ir = None
-    if stap.stap_abi_version() >= 2 and (C * T in (8, 12, 16) or 32 < C * T <= 64):
+    if stap.stap_abi_version() >= 2 and C * T <= 64:
         iplan = stap.Plan(spec.dims(), device=dev, refine_steps=2, solver=stap.STAP_SOLVE_MIXED_IR)
         iout = torch.empty_like(out)
         ituning = iplan.autotune(cube, iout)

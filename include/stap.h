@@ -59,7 +59,9 @@ typedef enum {
                           products (hi*hi + hi*lo + lo*hi) with FP32
                           accumulation; the apply falls back to FP32 when
                           neither B divides 128 nor 128 divides B, or a 128-cell
-                          tile needs more than 128 steering columns */
+                          tile needs more than 128 steering columns, and
+                          stap_plan_autotune keeps the FP32 kernel of a step
+                          where that is faster (small D) */
 } stap_precision;
 
 /* Arithmetic of the weight solve (diagonal load, factorisation, substitutions,
@@ -78,8 +80,8 @@ typedef enum {
                              for the correction in FP32 and adds it to the
                              double-float solution.  Each step shrinks the error
                              by about cond(Rl) 2^-24; 2 steps reach FP32 weight
-                             accuracy for cond(Rl) up to about 1e5.  D = 8, 12,
-                             16 or 33..64 (STAP_ERR_UNSUPPORTED otherwise) */
+                             accuracy for cond(Rl) up to about 1e5.  D <= 64
+                             (STAP_ERR_UNSUPPORTED above) */
 } stap_solver;
 
 typedef struct {
@@ -228,7 +230,7 @@ stap_status stap_run_cpi_noalloc(const stap_dims* dims, const stap_options* opt,
                                  const void* cube_c64, float* out, int64_t* n_failed_systems);
 
 /* Number of launch choices per CPI kept by the autotuner. */
-#define STAP_TUNING_LEN 8
+#define STAP_TUNING_LEN 9
 
 /* Autotune the launch configuration of every distinct CPI shape of the plan
  * (C, P, K, T, B, S; CPIs that differ only in R share one tuning): for each
@@ -239,9 +241,12 @@ stap_status stap_run_cpi_noalloc(const stap_dims* dims, const stap_options* opt,
  * warps per CTA of the D <= 32 solve, lanes per right-hand side of the larger
  * solve, and for D = 8, 12 or 16 the register-resident or the shared-memory
  * solve kernel; register-resident or general FP32 apply; for a one-CPI plan, 1, 2, 4
- * or 8 pipelined range slabs of the whole run.  Every candidate computes
- * the same result except that the two FP32 apply kernels sum in a different
- * order.  Needs the run workspace; synchronises the plan's stream; overwrites
+ * or 8 pipelined range slabs of the whole run; for STAP_PREC_TF32X3 plans,
+ * the tensor-core or the FP32 covariance and apply (the FP32 kernels are
+ * the more accurate, and at small D the faster).  Every candidate computes
+ * the same result except that the apply kernels sum in different orders and
+ * that a mixed-precision plan's FP32 choices are more accurate than its
+ * tensor-core ones.  Needs the run workspace; synchronises the plan's stream; overwrites
  * outs; clears the device status; drops a captured batch graph. */
 stap_status stap_plan_autotune(stap_plan plan, const void* const* cubes, float* const* outs,
                                int32_t reps);
@@ -251,7 +256,8 @@ stap_status stap_plan_autotune(stap_plan plan, const void* const* cubes, float* 
  * system, solve warps per CTA, large-solve lanes per right-hand side, apply
  * kernel (1 register-resident, 2 general), range slabs of a one-CPI
  * stap_run_cpi (at most 8 and NB are used), solve kernel for D = 8, 12, 16
- * (1 register-resident, 2 shared-memory).  set_tuning installs saved choices
+ * (1 register-resident, 2 shared-memory), covariance of a mixed-precision
+ * plan (1 FP32, 2 tensor cores; apply choice 3 = tensor cores).  set_tuning installs saved choices
  * (values 0..64; a choice that does not fit a launch falls back to the
  * heuristic). */
 stap_status stap_plan_get_tuning(stap_plan plan, int32_t cpi, int32_t* choices);

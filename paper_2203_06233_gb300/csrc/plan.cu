@@ -218,7 +218,9 @@ stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov,
                           int nr = -1) {
   const stap_dims& d = c.d;
   const int R = nr < 0 ? d.n_range : nr;
-  if (p->opt.precision == STAP_PREC_TF32X3)
+  // mixed-precision plans use the tensor cores unless the tuning kept the
+  // (more accurate) FP32 kernel as the faster one
+  if (p->opt.precision == STAP_PREC_TF32X3 && c.tune.cov_kind != 1)
     return check_launch(stap::launch_covariance_tc(static_cast<const float2*>(dop),
                                                    static_cast<double2*>(cov), d.n_chan, d.n_dop,
                                                    R, d.n_range, d.tdof, d.training_block,
@@ -247,7 +249,8 @@ stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts
                      cudaStream_t st, int nr = -1) {
   const stap_dims& d = c.d;
   const int R = nr < 0 ? d.n_range : nr;
-  if (p->opt.precision == STAP_PREC_TF32X3 && stap::apply_tc_supported(d.training_block, d.n_steering))
+  if (p->opt.precision == STAP_PREC_TF32X3 && stap::apply_tc_supported(d.training_block, d.n_steering) &&
+      (c.tune.apply_kind == 0 || c.tune.apply_kind == 3))
     return check_launch(stap::launch_apply_tc(static_cast<const float2*>(dop),
                                               static_cast<const float2*>(wts), out, d.n_chan,
                                               d.n_dop, R, d.n_range, d.tdof, d.training_block,
@@ -701,11 +704,16 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
     c.tune = best;
     pick([](stap::Tune& t, int v) { t.dop_tr = v; }, {8, 16, 32},
          [&] { return do_doppler(p, c, cube, dop, p->stream); });
-    if (p->opt.precision == STAP_PREC_FP32) {
+    {
+      const bool mixed = p->opt.precision == STAP_PREC_TF32X3;
+      if (mixed) c.tune.cov_kind = 1;   // tune the FP32 kernel first
       std::vector<int> kts;
       for (int kt = 1; kt <= 32 && kt <= d.n_dop; kt *= 2) kts.push_back(kt);
       pick([](stap::Tune& t, int v) { t.cov_kt = v; }, kts,
            [&] { return do_covariance(p, c, dop, cov, p->stream); });
+      if (mixed)   // then keep the tensor cores only where they are faster
+        pick([](stap::Tune& t, int v) { t.cov_kind = v; }, {2, 1},
+             [&] { return do_covariance(p, c, dop, cov, p->stream); });
     }
     if ((st = do_covariance(p, c, dop, cov, p->stream)) != STAP_OK) break;
     if (c.D <= stap::kSmallMaxD) {
@@ -739,7 +747,10 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
            [&] { return do_solve(p, c, cov, wts, p->stream); });
     }
     if ((st = do_solve(p, c, cov, wts, p->stream)) != STAP_OK) break;
-    if (p->opt.precision == STAP_PREC_FP32)
+    if (p->opt.precision == STAP_PREC_TF32X3 && stap::apply_tc_supported(d.training_block, d.n_steering))
+      pick([](stap::Tune& t, int v) { t.apply_kind = v; }, {3, 1, 2},
+           [&] { return do_apply(p, c, dop, wts, out, p->stream); });
+    else
       pick([](stap::Tune& t, int v) { t.apply_kind = v; }, {1, 2},
            [&] { return do_apply(p, c, dop, wts, out, p->stream); });
     if (p->cpis.size() == 1) {  // the whole run, pipelined over range slabs or not
@@ -775,8 +786,8 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
 stap_status stap_plan_get_tuning(stap_plan p, int32_t cpi, int32_t* choices) {
   if (!p || !choices || cpi < 0 || cpi >= (int32_t)p->cpis.size()) return STAP_ERR_INVALID_ARG;
   const stap::Tune& t = p->cpis[cpi].tune;
-  const int32_t v[STAP_TUNING_LEN] = {t.dop_tr,   t.cov_kt,     t.solve_ts, t.solve_nw,
-                                      t.solve_lr, t.apply_kind, t.slabs,    t.solve_kind};
+  const int32_t v[STAP_TUNING_LEN] = {t.dop_tr,   t.cov_kt,     t.solve_ts,   t.solve_nw, t.solve_lr,
+                                      t.apply_kind, t.slabs,    t.solve_kind, t.cov_kind};
   for (int i = 0; i < STAP_TUNING_LEN; ++i) choices[i] = v[i];
   return STAP_OK;
 }
@@ -794,6 +805,7 @@ stap_status stap_plan_set_tuning(stap_plan p, int32_t cpi, const int32_t* choice
   t.apply_kind = choices[5];
   t.slabs = choices[6];
   t.solve_kind = choices[7];
+  t.cov_kind = choices[8];
   drop_graph(p);
   return STAP_OK;
 }

@@ -1496,7 +1496,7 @@ cudaError_t launch_mir(const double2* cov, float2* wts, const float4* steer_ff, 
 
 }  // namespace
 
-bool mir_supported(int D) { return D == 8 || D == 12 || D == 16 || (D > kSmallMaxD && D <= 64); }
+bool mir_supported(int D) { return D >= 1 && D <= 64; }
 
 namespace {
 
@@ -1517,12 +1517,17 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
   if (D < 1 || D > kMaxD || S < 1) return cudaErrorInvalidValue;
   const bool sep = sep_g != nullptr && sep_a != nullptr && steer_ff != nullptr && sep_a_ff != nullptr &&
                    C >= 1 && C <= 32 && D % C == 0;
-  if (solver == 1 && D > kSmallMaxD) {  // mixed-precision refinement, 32 < D <= 64
+  if (solver == 1 && !(D == 8 || D == 12 || D == 16)) {  // refinement, one system per CTA
     if (!mir_supported(D) || steer_ff == nullptr) return cudaErrorNotSupported;
     const bool msep = sep && g_ff != nullptr;
-    const int LR = (tn.solve_lr == 16) ? 16 : 8;     // 8 lanes x 8 rows or 16 x 4
+    const int LR = (tn.solve_lr == 16 && D > 32) ? 16 : 8;   // 8 lanes x 8 (or 4) rows, or 16 x 4
     const int NG = 128 / LR;
     const size_t smem = big_mir_bytes(D, C, NG, msep);
+    if (D <= 32)
+      return msep ? launch_big_mir<true, 8, 128, 4>(cov, wts, steer_ff, g_ff, sep_a_ff, nsys, D, S, C,
+                                                   load_factor, refine_steps, status, smem, s)
+                  : launch_big_mir<false, 8, 128, 4>(cov, wts, steer_ff, nullptr, nullptr, nsys, D, S,
+                                                    C, load_factor, refine_steps, status, smem, s);
     if (LR == 8)
       return msep ? launch_big_mir<true, 8, 128, 8>(cov, wts, steer_ff, g_ff, sep_a_ff, nsys, D, S, C,
                                                    load_factor, refine_steps, status, smem, s)

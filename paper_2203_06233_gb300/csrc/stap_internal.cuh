@@ -31,9 +31,10 @@ struct Tune {
   int solve_ts = 0;    // D <= 32 solve: lanes per system (power of two, >= one per RHS)
   int solve_nw = 0;    // D <= 32 solve: warps per CTA, 1..4
   int solve_lr = 0;    // D > 32 solve: lanes per right-hand side, 8 (D <= 64), 16 or 32
-  int apply_kind = 0;  // FP32 apply: 1 register-resident, 2 general
+  int apply_kind = 0;  // apply: 1 FP32 register-resident, 2 FP32 general, 3 tensor cores
   int slabs = 0;       // single-CPI run: range slabs pipelined on prioritised streams, 1..8
   int solve_kind = 0;  // D = 8, 12, 16 solve: 1 register-resident, 2 generic shared-memory
+  int cov_kind = 0;    // covariance: 1 FP32 error-free, 2 tensor cores (mixed-precision plans)
 };
 
 // Snapshot lengths with a mixed-precision iterative-refinement solve.

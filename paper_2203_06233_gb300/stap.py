@@ -42,7 +42,7 @@ EXPORTED = (
     "stap_plan_set_tuning",
 )
 
-STAP_TUNING_LEN = 8
+STAP_TUNING_LEN = 9
 
 # size of the library-owned scratch array used by stap_run_cpi_noalloc
 STAP_NOALLOC_SCRATCH_BYTES = 16 << 20

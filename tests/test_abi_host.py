@@ -97,7 +97,7 @@ def test_options_default_and_mixed_refinement_shape_limits():
     mir = stap.stap_options(1e-3, 2, 0, stap.STAP_SOLVE_MIXED_IR)
     for dims, code in [((4, 16, 32, 256, 2, 32, 4), stap.STAP_OK),          # D = 8
                        ((8, 16, 32, 256, 2, 32, 4), stap.STAP_OK),          # D = 16
-                       ((5, 16, 32, 256, 2, 32, 4), stap.STAP_ERR_UNSUPPORTED),   # D = 10
+                       ((5, 16, 32, 256, 2, 32, 4), stap.STAP_OK),                 # D = 10
                        ((16, 16, 32, 256, 4, 32, 4), stap.STAP_OK),                # D = 64
                        ((11, 16, 32, 256, 3, 32, 4), stap.STAP_OK),                # D = 33
                        ((25, 16, 32, 256, 3, 32, 4), stap.STAP_ERR_UNSUPPORTED)]:  # D = 75

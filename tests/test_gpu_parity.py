@@ -302,6 +302,8 @@ def test_not_positive_definite_flagged_by_both_small_solves(kind):
 
 MIR_SPECS = dict(REG_SPECS)
 MIR_SPECS.update({
+    "D6": synth.CPISpec(3, 20, 32, 96, 2, 32, 5, cnr_db=30.0, seed=11),       # one system per CTA
+    "D24": synth.CPISpec(8, 16, 32, 128, 3, 64, 9, cnr_db=35.0, seed=25),
     "D33": synth.CPISpec(11, 16, 16, 96, 3, 48, 7, cnr_db=35.0, seed=24),     # odd D, S % 8 != 0
     "D64": synth.CPISpec(16, 32, 64, 256, 4, 128, 8, cnr_db=40.0, seed=14),
 })
