@@ -13,6 +13,9 @@ remaining steps are the standard post-Doppler STAP reading):
 1. ``doppler``     Hann-windowed direct DFT over pulses, zero-padded to K bins.
 2. ``snapshot``    D = C*T entries from T adjacent bins, channel fastest.
 3. ``covariance``  R = (1/B) sum x x^H per (Doppler bin, range block).
+   ``train_neighbours`` (an option beyond the paper): block b trained on the
+   mean of the covariances of blocks b-1 and b+1, leaving out the cell under
+   test and its block (guard cells).
 4-7. ``weights``   diagonal load, Cholesky, forward/back solve, AMF scaling.
 8. ``apply``       P = |w^H x|^2 per cell and steering vector.
 
@@ -85,6 +88,8 @@ def lib():
         L.oracle_weights.argtypes = [D, P, i32, P, ctypes.c_double, P, P]
         L.oracle_apply.argtypes = [D, P, i32, P, P]
         L.oracle_run.argtypes = [D, P, P, ctypes.c_double, i32, i32, P, P, P, P, P]
+        L.oracle_train_neighbours.argtypes = [D, P, i32, i32, i32, P]
+        L.oracle_run_neighbours.argtypes = [D, P, P, ctypes.c_double, i32, i32, P, P]
         for f in ("oracle_doppler_window", "oracle_doppler", "oracle_snapshot", "oracle_covariance",
                   "oracle_cholesky", "oracle_cholesky_solve", "oracle_default_steering",
                   "oracle_weights", "oracle_apply", "oracle_run"):
@@ -205,12 +210,39 @@ def apply(d: Dims, dop, wts) -> np.ndarray:
     return out
 
 
-def run(d: Dims, cube, r0=0, nr=None, steer=None, load_factor=1e-3, keep=False):
+def train_neighbours(d: Dims, cov) -> np.ndarray:
+    """Training matrices cov_t[K][NB][D][D] of neighbour-block training from the
+    per-block covariances cov[K][NB][D][D] of a whole range (NB >= 2)."""
+    cov = _c128(cov)
+    K, nb = cov.shape[:2]
+    out = np.empty_like(cov)
+    _check(lib().oracle_train_neighbours(ctypes.byref(d.c()), _ptr(cov), nb, 0, nb, _ptr(out)),
+           "train_neighbours")
+    return out
+
+
+def run(d: Dims, cube, r0=0, nr=None, steer=None, load_factor=1e-3, keep=False, training=0):
     """Steps 1-8 on the range cells [r0, r0+nr) of a [C][P][R] cube.
 
     Returns a dict with ``out`` [S][K][nr] (float64), ``status`` [K][nr/B] and
-    ``n_failed``; with ``keep`` also ``dop``, ``cov`` and ``wts``.
+    ``n_failed``; with ``keep`` also ``dop``, ``cov`` and ``wts``.  With
+    ``training=1`` each block is trained on its neighbours (``train_neighbours``);
+    the window is then computed from a slab one block wider on each side.
     """
+    if training:
+        if keep:
+            raise ValueError("keep is not available with neighbour training")
+        nr = d.n_range - r0 if nr is None else nr
+        B = d.training_block
+        e0, e1 = max(0, r0 - B), min(d.n_range, r0 + nr + B)
+        x = _c128(np.asarray(cube)[:, :, e0:e1])
+        out = np.empty((d.n_steering, d.n_dop, nr), np.float64)
+        status = np.empty((d.n_dop, nr // B), np.int32)
+        st = None if steer is None else _c128(steer)
+        rc = lib().oracle_run_neighbours(ctypes.byref(d.c(e1 - e0)), _ptr(x),
+                                         _ptr(st) if st is not None else ctypes.c_void_p(0),
+                                         float(load_factor), r0 - e0, nr, _ptr(out), _ptr(status))
+        return {"out": out, "status": status, "n_failed": _check(rc, "run")}
     nr, x = _slab(d, cube, r0, nr)
     NB = nr // d.training_block
     out = np.empty((d.n_steering, d.n_dop, nr), np.float64)

@@ -21,6 +21,8 @@
  *        x_{k,r}[t*C + c] = X[c][(k + t - floor(T/2)) mod K][r]
  *   3. Covariance per (Doppler bin k, range block b of B cells) (statement U):
  *        R_{k,b} = (1/B) sum_{r in block b} x_{k,r} x_{k,r}^H
+ *      Optional training with guard cells (not in the paper): block b's
+ *      weights use the mean of R_{k,b-1} and R_{k,b+1} (oracle_train_neighbours).
  *   4. Diagonal loading:  delta = lf * Re tr(R) / D,  Rl = R + delta I.
  *   5. Cholesky Rl = L L^H (L lower, real positive diagonal), column by column.
  *   6. u_s = Rl^{-1} v_s by forward then back substitution (no refinement:
@@ -387,6 +389,85 @@ done:
   free(dop_t);
   free(cov_t);
   free(wts_t);
+  free(steer_t);
+  return rc;
+}
+
+/* Training with guard cells (a reading beyond the paper, which trains each
+ * block on its own cells): the covariance that block b's weights use is the
+ * mean of the covariances of the adjacent blocks b-1 and b+1, or the one of
+ * them that exists at either end of the range, so that the cell under test
+ * and the other cells of its own block (its guard cells) are left out of its
+ * training data.  With equal block sizes the mean of two sample covariances is
+ * the sample covariance of their 2B cells.
+ * cov_in: [K][nb][D][D] for nb consecutive blocks that include both ends of the
+ * range where a window block has no neighbour; out: [K][nbw][D][D] for the
+ * blocks b0 .. b0+nbw-1 of cov_in. */
+int oracle_train_neighbours(const oracle_dims* d, const cplx* cov_in, int32_t nb, int32_t b0,
+                            int32_t nbw, cplx* out) {
+  if (!dims_ok(d) || !cov_in || !out || nb < 2 || b0 < 0 || nbw < 1 || b0 + nbw > nb)
+    return ORACLE_BAD_ARGS;
+  const int K = d->n_dop, D = d->n_chan * d->tdof;
+  const size_t DD = (size_t)D * D;
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < K; ++k)
+    for (int j = 0; j < nbw; ++j) {
+      const int b = b0 + j;
+      const cplx* lo = b > 0 ? cov_in + ((size_t)k * nb + b - 1) * DD : NULL;
+      const cplx* hi = b + 1 < nb ? cov_in + ((size_t)k * nb + b + 1) * DD : NULL;
+      cplx* o = out + ((size_t)k * nbw + j) * DD;
+      for (size_t e = 0; e < DD; ++e) {
+        if (lo && hi) o[e] = 0.5 * (lo[e] + hi[e]);
+        else o[e] = lo ? lo[e] : hi[e];
+      }
+    }
+  return ORACLE_OK;
+}
+
+/* Steps 1-8 with the neighbour-block training above, for the window of nr
+ * cells starting at cell w0 of a cube slab of d->n_range cells; the slab
+ * reaches one block beyond the window on each side unless the window touches
+ * that end of the range.  out: [S][K][nr]; status: [K][nr/B]. */
+int oracle_run_neighbours(const oracle_dims* d, const cplx* cube, const cplx* steer,
+                          double load_factor, int32_t w0, int32_t nr, double* out,
+                          int32_t* status) {
+  if (!dims_ok(d) || !cube || !out || !window_ok(d, w0, nr)) return ORACLE_BAD_ARGS;
+  const int B = d->training_block;
+  if (w0 % B != 0) return ORACLE_BAD_ARGS;
+  const int C = d->n_chan, K = d->n_dop, S = d->n_steering, D = d->n_chan * d->tdof;
+  const int W = d->n_range, NBS = W / B, NBW = nr / B;
+  if (NBS < 2) return ORACLE_BAD_ARGS;
+  cplx* dop = (cplx*)malloc(sizeof(cplx) * (size_t)C * K * W);
+  cplx* dopw = (cplx*)malloc(sizeof(cplx) * (size_t)C * K * nr);
+  cplx* cov = (cplx*)malloc(sizeof(cplx) * (size_t)K * NBS * D * D);
+  cplx* trn = (cplx*)malloc(sizeof(cplx) * (size_t)K * NBW * D * D);
+  cplx* wts = (cplx*)malloc(sizeof(cplx) * (size_t)K * NBW * S * D);
+  cplx* steer_t = NULL;
+  int rc = ORACLE_NO_MEMORY;
+  if (!steer) {
+    steer = steer_t = (cplx*)malloc(sizeof(cplx) * (size_t)S * D);
+    if (steer_t && oracle_default_steering(d, steer_t) != ORACLE_OK) goto done;
+  }
+  if (!dop || !dopw || !cov || !trn || !wts || !steer) goto done;
+  if ((rc = oracle_doppler(d, cube, 0, W, dop)) != ORACLE_OK) goto done;
+  if ((rc = oracle_covariance(d, dop, W, cov)) != ORACLE_OK) goto done;
+  if ((rc = oracle_train_neighbours(d, cov, NBS, w0 / B, NBW, trn)) != ORACLE_OK) goto done;
+  for (int c = 0; c < C; ++c)
+    for (int k = 0; k < K; ++k)
+      memcpy(dopw + ((size_t)c * K + k) * nr, dop + ((size_t)c * K + k) * W + w0, sizeof(cplx) * nr);
+  int failed = oracle_weights(d, trn, K * NBW, steer, load_factor, wts, status);
+  if (failed < 0) {
+    rc = failed;
+    goto done;
+  }
+  if ((rc = oracle_apply(d, dopw, nr, wts, out)) != ORACLE_OK) goto done;
+  rc = failed;
+done:
+  free(dop);
+  free(dopw);
+  free(cov);
+  free(trn);
+  free(wts);
   free(steer_t);
   return rc;
 }

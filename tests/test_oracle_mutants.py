@@ -31,6 +31,10 @@ MUTANTS = {
                          "h[p] = 0.5 - 0.5 * cos(2.0 * kPi * (double)p / (double)P);"),
     "steering_sign": ("double fs = 0.5 * sin(theta);", "double fs = -0.5 * sin(theta);"),
     "steering_bin_offset": ("int m = t - T / 2;", "int m = t;"),
+    "training_own_block": ("const cplx* lo = b > 0 ? cov_in + ((size_t)k * nb + b - 1) * DD : NULL;",
+                           "const cplx* lo = b > 0 ? cov_in + ((size_t)k * nb + b) * DD : NULL;"),
+    "training_mean_scale": ("if (lo && hi) o[e] = 0.5 * (lo[e] + hi[e]);",
+                            "if (lo && hi) o[e] = lo[e] + hi[e];"),
 }
 
 

@@ -402,3 +402,59 @@ def test_noise_only_output_mean_near_one():
     d = oracle.Dims(*spec.dims())
     P = oracle.run(d, synth.make_cube(spec))["out"]
     assert 0.85 < P.mean() < 1.05, P.mean()
+
+
+# ------------------------------------------- training with guard cells ------
+
+def test_neighbour_training_is_the_covariance_of_the_adjacent_blocks_cells():
+    """Block b's training matrix is the sample covariance of the cells of blocks
+    b-1 and b+1 (only the one that exists at either end), computed here from the
+    gathered snapshots of exactly those cells."""
+    d = dims(C=2, P=8, K=8, R=80, T=3, B=16, S=1)                # NB = 5
+    dop = crandn(2, 8, 80)
+    got = oracle.train_neighbours(d, oracle.covariance(d, dop))
+    x = _gather(dop, 3)                                          # [K][R][D]
+    for b in range(5):
+        cells = [r for nb in (b - 1, b + 1) if 0 <= nb < 5 for r in range(16 * nb, 16 * nb + 16)]
+        xs = x[:, cells]
+        ref = np.einsum("kri,krj->kij", xs, xs.conj()) / len(cells)
+        assert np.max(np.abs(got[:, b] - ref)) < 1e-13 * np.max(np.abs(ref)), b
+
+
+def test_neighbour_training_run_composes_and_windows_are_slices():
+    spec = synth.CPISpec(3, 16, 32, 128, 3, 32, 4, cnr_db=30.0,
+                         targets=(synth.Target(40, 7, 1, 10.0),), seed=9)
+    d = oracle.Dims(*spec.dims())
+    cube = synth.make_cube(spec)
+    full = oracle.run(d, cube, training=1)
+    dop = oracle.doppler(d, cube)
+    w, _, _ = oracle.weights(d, oracle.train_neighbours(d, oracle.covariance(d, dop)))
+    np.testing.assert_array_equal(full["out"], oracle.apply(d, dop, w))
+    for r0, nr in ((0, 32), (32, 64), (96, 32)):               # ends and middle
+        part = oracle.run(d, cube, r0=r0, nr=nr, training=1)
+        np.testing.assert_array_equal(part["out"], full["out"][:, :, r0:r0 + nr])
+
+
+def test_neighbour_training_keeps_the_target_out_of_its_own_training():
+    """The small workload's target trains its own block's weights, which then
+    partly null it; trained on the neighbouring blocks its output stands more
+    than four times higher above the median, and is still its row's maximum."""
+    spec = synth.small_cpi()
+    d = oracle.Dims(*spec.dims())
+    cube = synth.make_cube(spec)
+    own = oracle.run(d, cube)["out"]
+    nbr = oracle.run(d, cube, training=1)["out"]
+    assert int(np.argmax(nbr[2, 24])) == 128
+    ratio_own = own[2, 24, 128] / np.median(own)
+    ratio_nbr = nbr[2, 24, 128] / np.median(nbr)
+    assert ratio_nbr > 4 * ratio_own, (ratio_own, ratio_nbr)
+
+
+def test_neighbour_training_noise_only_output_mean_above_one():
+    """With the cell under test outside its training data the AMF output on
+    noise alone averages a little above 1 (about N / (N - D) for N training
+    cells), where own-block training stays at or below 1."""
+    spec = synth.CPISpec(4, 32, 32, 4096, 3, 256, 4, cnr_db=None, seed=21)
+    d = oracle.Dims(*spec.dims())
+    P = oracle.run(d, synth.make_cube(spec), training=1)["out"]
+    assert 1.0 < P.mean() < 1.1, P.mean()
