@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define STAP_ABI_VERSION 2
+#define STAP_ABI_VERSION 3
 
 typedef enum {
   STAP_OK = 0,
@@ -84,6 +84,18 @@ typedef enum {
                              (STAP_ERR_UNSUPPORTED above) */
 } stap_solver;
 
+/* Which range cells train the covariance that block b's weights use. */
+typedef enum {
+  STAP_TRAIN_OWN_BLOCK = 0,      /* the B cells of block b itself, the cell under
+                                    test included (the default) */
+  STAP_TRAIN_NEIGHBOURS = 1      /* not in the paper: the blocks b-1 and b+1 (the
+                                    one that exists at either end of the range),
+                                    i.e. the cell under test and the other cells
+                                    of its block are guard cells; needs NB >= 2.
+                                    One-CPI runs are then not cut into range
+                                    slabs (block b needs its neighbours' data) */
+} stap_training;
+
 typedef struct {
   int32_t n_chan;         /* C >= 1 */
   int32_t n_pulses;       /* P >= 1 */
@@ -99,11 +111,13 @@ typedef struct {
   int32_t refine_steps; /* iterative-refinement steps after the first solve, 0..4 (default 1) */
   int32_t precision;    /* a stap_precision value (default STAP_PREC_FP32) */
   int32_t solver;       /* a stap_solver value (default STAP_SOLVE_FP64) */
+  int32_t training;     /* a stap_training value (default STAP_TRAIN_OWN_BLOCK) */
 } stap_options;
 
 typedef struct stap_plan_s* stap_plan;
 
-/* Fill *opt with the defaults (load_factor 1e-3, refine_steps 1, FP32, FP64 solve). */
+/* Fill *opt with the defaults (load_factor 1e-3, refine_steps 1, FP32, FP64
+ * solve, own-block training). */
 void stap_options_default(stap_options* opt);
 
 /* Create a plan for n_cpi CPIs whose shapes are dims[0 .. n_cpi-1].
@@ -147,6 +161,16 @@ stap_status stap_doppler(stap_plan plan, const void* cube_c64, void* dop_c64);
  *   cov[k][b] = (1/B) sum_{r = bB}^{bB+B-1} x_{k,r} x_{k,r}^H
  * dop: c64 [C][K][R]; cov: c128 [K][NB][D][D], full Hermitian. */
 stap_status stap_covariance(stap_plan plan, const void* dop_c64, void* cov_c128);
+
+/* Training matrices for STAP_TRAIN_NEIGHBOURS, from the per-block covariances
+ * of stap_covariance:
+ *   cov_train[k][b] = (cov[k][b-1] + cov[k][b+1]) / 2, or the one of them
+ *   that exists for b = 0 and b = NB-1.
+ * cov, cov_train: c128 [K][NB][D][D], distinct buffers.  stap_run_cpi applies
+ * it between the covariance and the solve when the plan's training is
+ * STAP_TRAIN_NEIGHBOURS; step-by-step callers pass cov_train to
+ * stap_solve_weights themselves.  STAP_ERR_SHAPE if NB < 2. */
+stap_status stap_train_neighbours(stap_plan plan, const void* cov_c128, void* cov_train_c128);
 
 /* Adaptive weights per (k, b) and steering vector v_s (Sec. 4.2's STAP
  * kernel, loaded sample-matrix reading), in FP64 with the default solver:

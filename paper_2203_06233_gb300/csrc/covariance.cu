@@ -142,7 +142,7 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
   const int h = T / 2;
   const int NBIN = KT + T - 1;                    // staged bins k0-h .. k0+KT-1+(T-1-h)
   const int nrows = NBIN * C;
-  const int ld = CB + 1;
+  const int ld = (CB + 2) & ~1;   // even: rows start on 16-byte boundaries
   const int Ediag = C * (C + 1) / 2, Eoff = C * C;
   // items: d-major; d = 0 has NBIN * Ediag items, d > 0 has (NBIN - d) * Eoff
   const int nitems = NBIN * Ediag + (T - 1) * (2 * NBIN - T) / 2 * Eoff;
@@ -201,10 +201,25 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
       const float2* xb = X + rb * ld;
       const float sig = pow2_ceil(fourB * m[ra] * m[rb]);
       float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
+      // a * conj(bb) = (a.x bb.x + a.y bb.y) + i (a.y bb.x - a.x bb.y), two
+      // cells per 16-byte shared-memory load
+      const float4* xa4 = reinterpret_cast<const float4*>(xa);
+      const float4* xb4 = reinterpret_cast<const float4*>(xb);
+      const int cc2 = cc >> 1;
 #pragma unroll 4
-      for (int cell = 0; cell < cc; ++cell) {
-        const float2 a = xa[cell], bb = xb[cell];
-        // a * conj(bb) = (a.x bb.x + a.y bb.y) + i (a.y bb.x - a.x bb.y)
+      for (int p2 = 0; p2 < cc2; ++p2) {
+        const float4 a = xa4[p2], bb = xb4[p2];
+        grid_add(hr, lr, a.x, bb.x, sig);
+        grid_add(hr, lr, a.y, bb.y, sig);
+        grid_add(hi, li, a.y, bb.x, sig);
+        grid_add(hi, li, -a.x, bb.y, sig);
+        grid_add(hr, lr, a.z, bb.z, sig);
+        grid_add(hr, lr, a.w, bb.w, sig);
+        grid_add(hi, li, a.w, bb.z, sig);
+        grid_add(hi, li, -a.z, bb.w, sig);
+      }
+      if (cc & 1) {
+        const float2 a = xa[cc - 1], bb = xb[cc - 1];
         grid_add(hr, lr, a.x, bb.x, sig);
         grid_add(hr, lr, a.y, bb.y, sig);
         grid_add(hi, li, a.y, bb.x, sig);
@@ -274,7 +289,7 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
                             (size_t)(T - 1) * (2 * nbin - T) / 2 * C * C;
       const size_t nrows = (size_t)nbin * C;
       return nitems * sizeof(double2) + ((nrows + 3) & ~(size_t)3) * sizeof(float) +
-             nrows * (cb + 1) * sizeof(float2);
+             nrows * ((cb + 2) & ~1) * sizeof(float2);
     };
     int KT = K < 16 ? K : 16;  // K is a power of two, so KT divides it
     while (KT > 1 && pair_smem(KT, B) > kPairBudget) KT >>= 1;
@@ -288,17 +303,19 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
       cudaError_t e = ensure_smem(covariance_pairs_kernel, smem, set_bytes);
       if (e != cudaSuccess) return e;
       dim3 grid(NB, K / KT);
-      // one thread per Q entry (rounded up to whole warps, at least 4 and at
-      // most 32 warps), so that the entries are not spread unevenly over a
-      // last, partly idle round of the threads
+      // Many Q entries (large C): one thread per entry, rounded up to whole
+      // warps (at most 32 warps, rounds balanced above that), so that they
+      // are not spread unevenly over a last, partly idle round of threads.
+      // Few entries: 256 threads, which share the SMs better with the solve
+      // kernels of other range slabs.
       const int nbin = KT + T - 1;
       const int nitems = nbin * (C * (C + 1) / 2) + (T - 1) * (2 * nbin - T) / 2 * C * C;
-      int threads = (nitems + 31) / 32 * 32;
-      if (threads < 128) threads = 128;
-      if (threads > kPairMaxThreads) threads = (nitems + (nitems + kPairMaxThreads - 1) / kPairMaxThreads - 1) /
-                                               ((nitems + kPairMaxThreads - 1) / kPairMaxThreads);
-      threads = (threads + 31) / 32 * 32;
-      if (threads > kPairMaxThreads) threads = kPairMaxThreads;
+      int threads = 256;
+      if (nitems > 512) {
+        const int rounds = (nitems + kPairMaxThreads - 1) / kPairMaxThreads;
+        threads = ((nitems + rounds - 1) / rounds + 31) / 32 * 32;
+        if (threads > kPairMaxThreads) threads = kPairMaxThreads;
+      }
       covariance_pairs_kernel<<<grid, threads, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, KT, CB);
       return cudaGetLastError();
     }

@@ -37,6 +37,11 @@ struct Tune {
   int cov_kind = 0;    // covariance: 1 FP32 error-free, 2 tensor cores (mixed-precision plans)
 };
 
+// Training with guard cells: out[k][b] = mean of in[k][b-1] and in[k][b+1]
+// (the one that exists at either end); NB >= 2.
+cudaError_t launch_train_neighbours(const double2* in, double2* out, int K, int NB, int D,
+                                    cudaStream_t s);
+
 // Snapshot lengths with a mixed-precision iterative-refinement solve.
 bool mir_supported(int D);
 

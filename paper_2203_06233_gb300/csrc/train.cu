@@ -1,0 +1,49 @@
+// Training with guard cells (an option beyond the paper's own-block training,
+// which leaves the cell under test in its training data): the covariance that
+// block b's weights use is the mean of the covariances of the adjacent blocks
+// b-1 and b+1, or the one of them that exists at either end of the range, so
+// that the cell under test and the other cells of its own block act as guard
+// cells.  With equal block sizes the mean of two sample covariances is the
+// sample covariance of their 2B cells.
+//
+// Memory-bound: reads two c128 matrices and writes one per system (in 16-byte
+// elements, coalesced along the flattened [K][NB][D][D] index); the halving is
+// exact.
+#include "stap_internal.cuh"
+
+namespace stap {
+namespace {
+
+__global__ void __launch_bounds__(256)
+train_neighbours_kernel(const double2* __restrict__ in, double2* __restrict__ out, int NB,
+                        long long DD, long long total) {
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long sys = idx / DD;
+    const int b = (int)(sys % NB);
+    const bool lo = b > 0, hi = b + 1 < NB;
+    double2 v;
+    if (lo && hi) {
+      const double2 p = __ldg(in + idx - DD), q = __ldg(in + idx + DD);
+      v = make_double2((p.x + q.x) * 0.5, (p.y + q.y) * 0.5);
+    } else {
+      v = __ldg(in + idx + (lo ? -DD : DD));
+    }
+    out[idx] = v;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_train_neighbours(const double2* in, double2* out, int K, int NB, int D,
+                                    cudaStream_t s) {
+  if (NB < 2) return cudaErrorInvalidValue;
+  const long long DD = (long long)D * D;
+  const long long total = (long long)K * NB * DD;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152LL * 16) blocks = 152LL * 16;
+  train_neighbours_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, NB, DD, total);
+  return cudaGetLastError();
+}
+
+}  // namespace stap

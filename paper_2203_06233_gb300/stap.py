@@ -31,6 +31,8 @@ STAP_PREC_FP32 = 0
 STAP_PREC_TF32X3 = 2
 STAP_SOLVE_FP64 = 0
 STAP_SOLVE_MIXED_IR = 1
+STAP_TRAIN_OWN_BLOCK = 0
+STAP_TRAIN_NEIGHBOURS = 1
 
 # every symbol include/stap.h declares
 EXPORTED = (
@@ -39,7 +41,7 @@ EXPORTED = (
     "stap_plan_destroy", "stap_doppler", "stap_covariance", "stap_solve_weights", "stap_apply",
     "stap_run_cpi", "stap_get_status", "stap_status_string", "stap_abi_version",
     "stap_run_cpi_noalloc", "stap_plan_batch_bytes", "stap_plan_autotune", "stap_plan_get_tuning",
-    "stap_plan_set_tuning",
+    "stap_plan_set_tuning", "stap_train_neighbours",
 )
 
 STAP_TUNING_LEN = 9
@@ -61,7 +63,8 @@ class stap_dims(ctypes.Structure):
 
 class stap_options(ctypes.Structure):
     _fields_ = [("load_factor", ctypes.c_double), ("refine_steps", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("solver", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
+                ("training", ctypes.c_int32)]
 
 
 _lib = None
@@ -92,6 +95,7 @@ def lib():
             L.stap_doppler.argtypes = [vp, vp, vp]
             L.stap_covariance.argtypes = [vp, vp, vp]
             L.stap_solve_weights.argtypes = [vp, vp, vp]
+            L.stap_train_neighbours.argtypes = [vp, vp, vp]
             L.stap_apply.argtypes = [vp, vp, vp, vp]
             L.stap_run_cpi.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
             L.stap_get_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
@@ -214,6 +218,11 @@ def stap_covariance(plan, dop: torch.Tensor, cov: torch.Tensor):
            "stap_covariance")
 
 
+def stap_train_neighbours(plan, cov: torch.Tensor, cov_train: torch.Tensor):
+    _check(lib().stap_train_neighbours(plan, ctypes.c_void_p(cov.data_ptr()),
+                                       ctypes.c_void_p(cov_train.data_ptr())), "stap_train_neighbours")
+
+
 def stap_solve_weights(plan, cov: torch.Tensor, wts: torch.Tensor):
     _check(lib().stap_solve_weights(plan, ctypes.c_void_p(cov.data_ptr()),
                                     ctypes.c_void_p(wts.data_ptr())), "stap_solve_weights")
@@ -297,13 +306,16 @@ class Plan:
 
     def __init__(self, dims, load_factor: float = 1e-3, refine_steps: int = 1,
                  precision: int = STAP_PREC_FP32, device=None, steps_only: bool = False,
-                 max_workspace_bytes: Optional[int] = None, solver: int = STAP_SOLVE_FP64):
+                 max_workspace_bytes: Optional[int] = None, solver: int = STAP_SOLVE_FP64,
+                 training: int = STAP_TRAIN_OWN_BLOCK):
         dl = list(dims) if isinstance(dims, (list, tuple)) and dims and not isinstance(dims[0], int) \
             else [dims]
         self.dims = [_dims(d) for d in dl]
         self.device = torch.device(device) if device is not None else torch.device("cuda")
-        opts = stap_options(float(load_factor), int(refine_steps), int(precision), int(solver))
+        opts = stap_options(float(load_factor), int(refine_steps), int(precision), int(solver),
+                            int(training))
         self.precision, self.refine_steps, self.solver = int(precision), int(refine_steps), int(solver)
+        self.training = int(training)
         with torch.cuda.device(self.device):
             self.handle, _ = stap_plan_create(self.dims, opts)
             self.step_bytes, self.run_bytes = stap_plan_workspace_sizes(self.handle)
@@ -358,6 +370,16 @@ class Plan:
         stap_covariance(self.handle, dop, cov)
         return cov
 
+    def train_neighbours(self, cov, cov_train=None):
+        """Training matrices of STAP_TRAIN_NEIGHBOURS from per-block covariances."""
+        sh = self.shapes()
+        cov_train = torch.empty_like(cov) if cov_train is None else cov_train
+        _dev(cov, torch.complex128, sh["cov"], "cov")
+        _dev(cov_train, torch.complex128, sh["cov"], "cov_train")
+        self._sync_stream()
+        stap_train_neighbours(self.handle, cov, cov_train)
+        return cov_train
+
     def solve_weights(self, cov, wts=None):
         sh = self.shapes()
         wts = torch.empty(sh["wts"], dtype=torch.complex64, device=self.device) if wts is None else wts
@@ -397,9 +419,9 @@ class Plan:
 
     def _tune_key(self, i: int) -> str:
         d = self.dims[i]
-        key = "C%d P%d K%d T%d B%d S%d prec%d ref%d solve%d" % (
+        key = "C%d P%d K%d T%d B%d S%d prec%d ref%d solve%d train%d" % (
             d.n_chan, d.n_pulses, d.n_dop, d.tdof, d.training_block, d.n_steering, self.precision,
-            self.refine_steps, self.solver)
+            self.refine_steps, self.solver, self.training)
         # a one-CPI plan also tunes its range slabs, which depend on R
         return key + (" R%d" % d.n_range if len(self.dims) == 1 else " batch")
 

@@ -27,7 +27,7 @@ def test_library_loads_and_exports_every_declared_symbol():
     for name in declared:
         assert hasattr(L, name), f"{name} declared in stap.h but not exported"
     assert set(declared) == set(stap.EXPORTED)
-    assert stap.stap_abi_version() == 2
+    assert stap.stap_abi_version() == 3
 
 
 def _create(dims, opts=None):
@@ -91,6 +91,30 @@ def test_plan_create_checks_options(lf, refine, prec, solver, code):
         stap.stap_plan_destroy(h)
 
 
+def test_training_option_values_and_block_count():
+    o = stap.stap_options_default()
+    assert o.training == stap.STAP_TRAIN_OWN_BLOCK
+    for training, dims, code in [(1, GOOD, stap.STAP_OK),
+                                 (2, GOOD, stap.STAP_ERR_INVALID_ARG),
+                                 (-1, GOOD, stap.STAP_ERR_INVALID_ARG),
+                                 (1, (4, 16, 32, 64, 2, 64, 4), stap.STAP_ERR_SHAPE),   # NB = 1
+                                 (1, (4, 16, 32, 128, 2, 64, 4), stap.STAP_OK)]:         # NB = 2
+        got, h, _ = _create(dims, stap.stap_options(1e-3, 1, 0, 0, training))
+        assert got == code, (training, dims)
+        if h.value:
+            stap.stap_plan_destroy(h)
+
+
+def test_training_workspace_holds_the_training_matrices():
+    C, P, K, R, T, B, S = GOOD
+    D, NB = C * T, R // B
+    _, h0, ws0 = _create(GOOD)
+    _, h1, ws1 = _create(GOOD, stap.stap_options(1e-3, 1, 0, 0, 1))
+    assert ws1 - ws0 >= K * NB * D * D * 16 and ws1 - ws0 < K * NB * D * D * 16 + 512
+    stap.stap_plan_destroy(h0)
+    stap.stap_plan_destroy(h1)
+
+
 def test_options_default_and_mixed_refinement_shape_limits():
     o = stap.stap_options_default()
     assert o.solver == stap.STAP_SOLVE_FP64
@@ -126,6 +150,11 @@ def test_null_and_misaligned_pointers_and_missing_workspace_fail_before_cuda():
     assert L.stap_covariance(h, fake, fake) == stap.STAP_ERR_NO_WORKSPACE
     assert L.stap_solve_weights(h, fake, fake) == stap.STAP_ERR_NO_WORKSPACE
     assert L.stap_apply(h, fake, fake, fake) == stap.STAP_ERR_NO_WORKSPACE
+    other = ctypes.c_void_p(0x20000)
+    assert L.stap_train_neighbours(h, fake, fake) == stap.STAP_ERR_INVALID_ARG   # in place
+    assert L.stap_train_neighbours(h, None, other) == stap.STAP_ERR_INVALID_ARG
+    assert L.stap_train_neighbours(h, odd, other) == stap.STAP_ERR_MISALIGNED
+    assert L.stap_train_neighbours(h, fake, other) == stap.STAP_ERR_NO_WORKSPACE
     arr = (ctypes.c_void_p * 1)(fake)
     assert L.stap_run_cpi(h, arr, arr) == stap.STAP_ERR_NO_WORKSPACE
     assert L.stap_get_status(h, None) == stap.STAP_ERR_NO_WORKSPACE
