@@ -189,10 +189,11 @@ def power_errors(got, ref):
     return {"normwise": normwise, "max_cell": float(np.max(np.abs(got - ref) / floor))}
 
 
-def cpu_baseline_oracle(spec, outputs=None, budget_s=12.0):
+def cpu_baseline_oracle(spec, outputs=None, neighbour_outputs=None, budget_s=12.0):
     """The oracle, as it stands, on the host cores: whole CPIs until ~budget_s.
     Its output also gives the error of each GPU output in `outputs`
-    ({name: host array [S][K][R]}) on the same cube."""
+    ({name: host array [S][K][R]}) on the same cube, and of those in
+    `neighbour_outputs` against its neighbour-block-training output."""
     import oracle
     from paper_2203_06233_gb300 import synth
     d = oracle.Dims(*spec.dims())
@@ -211,6 +212,9 @@ def cpu_baseline_oracle(spec, outputs=None, budget_s=12.0):
     base = {"value": cells / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{n} whole CPI(s) of the standard workload ({cells} cells) in {el:.1f} s"}
     errors = {name: power_errors(out, ref) for name, out in (outputs or {}).items()}
+    if neighbour_outputs:
+        ref_n = oracle.run(d, cube, training=1)["out"]
+        errors.update({name: power_errors(out, ref_n) for name, out in neighbour_outputs.items()})
     return base, errors
 
 
@@ -373,6 +377,29 @@ def run_gpu(args):
         }
         iplan.close()
 
+    # ---- training with guard cells (neighbour blocks; an option beyond the paper) ----
+    neighbours = None
+    if stap.stap_abi_version() >= 3 and NB >= 2:
+        nplan = stap.Plan(spec.dims(), device=dev, training=stap.STAP_TRAIN_NEIGHBOURS)
+        nout = torch.empty_like(out)
+        ntuning = nplan.autotune(cube, nout)
+        for _ in range(args.warmup):
+            flush()
+            nplan.run_cpi(cube, nout)
+        torch.cuda.synchronize()
+        ntimes = time_steps(lambda: nplan.run_cpi(cube, nout), args.steps, flush, stream)
+        code, failed = nplan.status()
+        if code != stap.STAP_OK:
+            raise RuntimeError(f"neighbour training: device status {code} ({failed} failed systems)")
+        nplan.run_cpi(cube, nout)
+        neighbours = {
+            "value": world * cells * args.steps / (sum(ntimes) * 1e-3),
+            "ms_per_step": sum(ntimes) / args.steps,
+            "training": "block b trained on blocks b-1 and b+1 (STAP_TRAIN_NEIGHBOURS), FP64 solve",
+            "tuning": ntuning,
+        }
+        nplan.close()
+
     # ---- end to end through the public API from pinned host buffers ----
     cube_pin = torch.from_numpy(cube_h).pin_memory()
     out_pin = torch.empty((S, K, R), dtype=torch.float32).pin_memory()
@@ -405,11 +432,14 @@ def run_gpu(args):
     }
     if mixed_ir is not None:
         line["mixed_ir"] = mixed_ir
+    if neighbours is not None:
+        line["neighbour_training"] = neighbours
     if rank == 0 and world == 1 and not args.no_cpu_baseline and NAME == "standard":
         outputs = {"plain": out.cpu().numpy(), "mixed": mout.cpu().numpy()}
         if mixed_ir is not None:
             outputs["mixed_ir"] = iout.cpu().numpy()
-        line["cpu_baseline"], line["errors_vs_oracle"] = cpu_baseline_oracle(spec, outputs)
+        nbr_outputs = {"neighbour_training": nout.cpu().numpy()} if neighbours is not None else None
+        line["cpu_baseline"], line["errors_vs_oracle"] = cpu_baseline_oracle(spec, outputs, nbr_outputs)
     plan.close()
     if world > 1:
         dist.destroy_process_group()
