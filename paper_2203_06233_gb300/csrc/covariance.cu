@@ -142,7 +142,7 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
   const int h = T / 2;
   const int NBIN = KT + T - 1;                    // staged bins k0-h .. k0+KT-1+(T-1-h)
   const int nrows = NBIN * C;
-  const int ld = (CB + 2) & ~1;   // even: rows start on 16-byte boundaries
+  const int ld = CB + 1;
   const int Ediag = C * (C + 1) / 2, Eoff = C * C;
   // items: d-major; d = 0 has NBIN * Ediag items, d > 0 has (NBIN - d) * Eoff
   const int nitems = NBIN * Ediag + (T - 1) * (2 * NBIN - T) / 2 * Eoff;
@@ -201,25 +201,9 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
       const float2* xb = X + rb * ld;
       const float sig = pow2_ceil(fourB * m[ra] * m[rb]);
       float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
-      // a * conj(bb) = (a.x bb.x + a.y bb.y) + i (a.y bb.x - a.x bb.y), two
-      // cells per 16-byte shared-memory load
-      const float4* xa4 = reinterpret_cast<const float4*>(xa);
-      const float4* xb4 = reinterpret_cast<const float4*>(xb);
-      const int cc2 = cc >> 1;
 #pragma unroll 4
-      for (int p2 = 0; p2 < cc2; ++p2) {
-        const float4 a = xa4[p2], bb = xb4[p2];
-        grid_add(hr, lr, a.x, bb.x, sig);
-        grid_add(hr, lr, a.y, bb.y, sig);
-        grid_add(hi, li, a.y, bb.x, sig);
-        grid_add(hi, li, -a.x, bb.y, sig);
-        grid_add(hr, lr, a.z, bb.z, sig);
-        grid_add(hr, lr, a.w, bb.w, sig);
-        grid_add(hi, li, a.w, bb.z, sig);
-        grid_add(hi, li, -a.z, bb.w, sig);
-      }
-      if (cc & 1) {
-        const float2 a = xa[cc - 1], bb = xb[cc - 1];
+      for (int cell = 0; cell < cc; ++cell) {
+        const float2 a = xa[cell], bb = xb[cell];
         grid_add(hr, lr, a.x, bb.x, sig);
         grid_add(hr, lr, a.y, bb.y, sig);
         grid_add(hi, li, a.y, bb.x, sig);
@@ -289,7 +273,7 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
                             (size_t)(T - 1) * (2 * nbin - T) / 2 * C * C;
       const size_t nrows = (size_t)nbin * C;
       return nitems * sizeof(double2) + ((nrows + 3) & ~(size_t)3) * sizeof(float) +
-             nrows * ((cb + 2) & ~1) * sizeof(float2);
+             nrows * (cb + 1) * sizeof(float2);
     };
     int KT = K < 16 ? K : 16;  // K is a power of two, so KT divides it
     while (KT > 1 && pair_smem(KT, B) > kPairBudget) KT >>= 1;
