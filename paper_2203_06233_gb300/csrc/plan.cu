@@ -811,7 +811,11 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
       };
       const int cands[4] = {1, 2, 4, 8};
       float best[4] = {kNever, kNever, kNever, kNever};
-      for (int round = 0; round < 3; ++round)
+      // a CPI of tens of milliseconds gains nothing from overlapping its
+      // short steps: one cold run decides whether to look at all
+      c.tune.slabs = 1;
+      const int rounds = cold_run() > 20.f ? 0 : 3;
+      for (int round = 0; round < rounds; ++round)
         for (int k = 0; k < 4; ++k) {
           c.tune.slabs = cands[k];
           if (run_single(p, cube, out) != STAP_OK) continue;   // streams and untimed first run
@@ -825,7 +829,7 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
       int bk = 0;
       for (int k = 1; k < 4; ++k)
         if (best[k] < best[bk]) bk = k;
-      c.tune.slabs = cands[bk];
+      c.tune.slabs = rounds ? cands[bk] : 1;
     }
     for (size_t j = i; j < p->cpis.size(); ++j)
       if (!tuned[j] && same_key(p->cpis[j].d, d)) {
