@@ -350,7 +350,7 @@ def run_gpu(args):
     # ---- mixed-precision iterative refinement of the solve (an option beyond
     # the paper's FP64 solve: FP32 factorisation, double-float residuals) ----
     mixed_ir = None
-    if stap.stap_abi_version() >= 2 and C * T <= 64:
+    if stap.stap_abi_version() >= 2:
         iplan = stap.Plan(spec.dims(), device=dev, refine_steps=2, solver=stap.STAP_SOLVE_MIXED_IR)
         iout = torch.empty_like(out)
         ituning = iplan.autotune(cube, iout)

@@ -80,8 +80,10 @@ typedef enum {
                              for the correction in FP32 and adds it to the
                              double-float solution.  Each step shrinks the error
                              by about cond(Rl) 2^-24; 2 steps reach FP32 weight
-                             accuracy for cond(Rl) up to about 1e5.  D <= 64
-                             (STAP_ERR_UNSUPPORTED above) */
+                             accuracy for cond(Rl) up to about 1e5.  For
+                             D > 64 the residual is formed in FP64 from the
+                             input instead (the double-float matrix would not
+                             fit on chip) */
 } stap_solver;
 
 /* Which range cells train the covariance that block b's weights use. */

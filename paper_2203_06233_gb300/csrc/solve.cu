@@ -29,6 +29,8 @@
 // from S to C right-hand sides.  The combination stays in FP64: u_s can be
 // two orders of magnitude smaller than the terms it sums (steering vectors
 // near the clutter ridge), so FP32 there costs ~1e-4 in the weights.
+#include <type_traits>
+
 #include "df64.cuh"
 #include "snapshots.cuh"
 
@@ -861,35 +863,101 @@ __device__ __forceinline__ double group_sum(double v) {
   return v;
 }
 
-template <bool SEP, int LR, int NT, int RPL>
+// In-place FP32 forward (Lu z = x) or back (Lu^H z = x) substitution, as big_subst.
+template <int LR, int RPL, bool BACK>
+__device__ __forceinline__ void big_subst_f32(float2 (&x)[RPL], const float2* __restrict__ Lc,
+                                              int D, int li, int grp) {
+  for (int jj = 0; jj < D; ++jj) {
+    const int j = BACK ? D - 1 - jj : jj;
+    const int owner = (j % LR) + grp * LR, qj = j / LR;
+    float2 pick = x[0];
+#pragma unroll
+    for (int q = 1; q < RPL; ++q)
+      if (q == qj) pick = x[q];
+    float2 yj;
+    yj.x = __shfl_sync(0xffffffffu, pick.x, owner);
+    yj.y = __shfl_sync(0xffffffffu, pick.y, owner);
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const bool touch = (BACK ? (q <= qj) : (q >= qj)) && LR * q < D;
+      if (touch) {
+        const int i = li + LR * q;
+        const bool act = BACK ? (i < j) : (i > j && i < D);
+        if (act) {
+          if (BACK) {
+            const float2 l = Lc[colstart(i, D) + j - i];
+            x[q].x = fmaf(-l.x, yj.x, x[q].x);
+            x[q].x = fmaf(-l.y, yj.y, x[q].x);
+            x[q].y = fmaf(-l.x, yj.y, x[q].y);
+            x[q].y = fmaf(l.y, yj.x, x[q].y);
+          } else {
+            const float2 l = Lc[colstart(j, D) + i - j];
+            x[q].x = fmaf(-l.x, yj.x, x[q].x);
+            x[q].x = fmaf(l.y, yj.y, x[q].x);
+            x[q].y = fmaf(-l.x, yj.y, x[q].y);
+            x[q].y = fmaf(-l.y, yj.x, x[q].y);
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int LR, int RPL>
+__device__ __forceinline__ void big_solve_f32(float2 (&x)[RPL], const float2* __restrict__ Lc,
+                                              const float* __restrict__ rd, int D, int li, int grp) {
+  big_subst_f32<LR, RPL, false>(x, Lc, D, li, grp);
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    if (LR * q < D) {
+      const int i = li + LR * q;
+      const float r = rd[i < D ? i : D - 1];
+      x[q].x *= r;
+      x[q].y *= r;
+    }
+  }
+  big_subst_f32<LR, RPL, true>(x, Lc, D, li, grp);
+}
+
+// F32F: the refinement option's form for D > 64 (where the double-float
+// matrix of solve_big_mir_kernel does not fit in shared memory): the factor
+// and the substitutions in FP32, the solution in FP64, each refinement step's
+// residual in FP64 from the input as below, its FP32 correction added in FP64.
+template <bool SEP, int LR, int NT, int RPL, bool F32F = false>
 __global__ void __launch_bounds__(NT)
 solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
                  const double2* __restrict__ steer, const double2* __restrict__ sep_g,
                  const float4* __restrict__ steer_ff, const float4* __restrict__ sep_a_ff,
                  long long nsys, int D, int S, int C, double load_factor, int refine_steps,
                  DeviceStatus* __restrict__ status) {
+  using LT = typename std::conditional<F32F, float2, double2>::type;   // factor entries
+  using RT = typename std::conditional<F32F, float, double>::type;     // pivots
   extern __shared__ double2 sm[];
   constexpr int NW = NT / 32;
   constexpr int NG = NT / LR;                      // right-hand sides in flight per CTA
   const int Dp = D * (D + 1) / 2;
-  double2* Lc = sm;                                  // [Dp] Lu, column-major packed
-  double2* colb = Lc + Dp;                           // [D] pivot column before division
-  float4* Ubf = reinterpret_cast<float4*>(colb + D); // SEP: [C][D] basis solutions (double-float)
-  double2* uv = colb + D + (SEP ? (size_t)C * D : 0);   // [NG][D] broadcast vectors
-  double* rd = reinterpret_cast<double*>(uv + (size_t)NG * D);   // [D] pivot reciprocals
-  int* okf = reinterpret_cast<int*>(rd + D);                     // pivots all positive
+  // Lu [Dp] (column-major packed) and the pivot column before division [D];
+  // from the next 16-byte boundary the SEP basis solutions [C][D]
+  // (double-float), the broadcast vectors [NG][D], the pivot reciprocals [D]
+  // and the pivot flag
+  LT* Lc = reinterpret_cast<LT*>(sm);
+  LT* colb = Lc + Dp;
+  float4* Ubf = reinterpret_cast<float4*>(sm) + ((size_t)(Dp + D) * sizeof(LT) + 15) / 16;
+  double2* uv = reinterpret_cast<double2*>(Ubf + (SEP ? (size_t)C * D : 0));
+  RT* rd = reinterpret_cast<RT*>(uv + (size_t)NG * D);
+  int* okf = reinterpret_cast<int*>(rd + D);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int li = lane % LR, grp = lane / LR;         // lane in group, group in warp
   const int g = warp * (32 / LR) + grp;              // group in CTA
   const double invD = 1.0 / (double)D;
 
   // pivot d -> reciprocal, recording a pivot that is not positive and finite
-  auto pivot = [&](double d) -> double {
-    if (!(d > 0.0) || !isfinite(d)) {
+  auto pivot = [&](RT d) -> RT {
+    if (!(d > RT(0)) || !isfinite(d)) {
       *okf = 0;
-      return 1.0;  // keep going; this system's weights become zero
+      return RT(1);  // keep going; this system's weights become zero
     }
-    return 1.0 / d;
+    return RT(1) / d;
   };
 
   for (long long sys = blockIdx.x; sys < nsys; sys += gridDim.x) {
@@ -898,20 +966,23 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
     for (int j = 0; j < D; ++j) tr += __ldg(&A[(size_t)j * D + j].x);
     const double delta = load_factor * tr * invD;
     for (int i = warp; i < D; i += NW)                 // rows of A, coalesced
-      for (int l = lane; l <= i; l += 32) Lc[colstart(l, D) + i - l] = loaded(A, D, i, l, delta);
+      for (int l = lane; l <= i; l += 32) {
+        const double2 a = loaded(A, D, i, l, delta);
+        Lc[colstart(l, D) + i - l] = LT{(RT)a.x, (RT)a.y};
+      }
     if (tid == 0) {
       *okf = 1;
-      rd[0] = pivot(__ldg(&A[0].x) + delta);
+      rd[0] = pivot((RT)(__ldg(&A[0].x) + delta));
     }
     __syncthreads();
 
     for (int j = 0; j < D; ++j) {
       const int cj = colstart(j, D);
-      const double rj = rd[j];
+      const RT rj = rd[j];
       for (int i = j + 1 + tid; i < D; i += NT) {
-        const double2 v = Lc[cj + i - j];
+        const LT v = Lc[cj + i - j];
         colb[i] = v;
-        Lc[cj + i - j] = make_double2(v.x * rj, v.y * rj);
+        Lc[cj + i - j] = LT{v.x * rj, v.y * rj};
       }
       __syncthreads();
       // trailing update, pairs (i, l) with j < l <= i, column-major order:
@@ -930,9 +1001,9 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
         const bool two = q + NT < np;
         const int l = j + 1 + a, i = l + off;
         const int l2 = two ? j + 1 + a2 : l, i2 = two ? l2 + off2 : i;
-        const double2 lij = Lc[cj + i - j], alj = colb[l];
-        const double2 lij2 = Lc[cj + i2 - j], alj2 = colb[l2];
-        double2 acc = Lc[colstart(l, D) + i - l], acc2 = Lc[colstart(l2, D) + i2 - l2];
+        const LT lij = Lc[cj + i - j], alj = colb[l];
+        const LT lij2 = Lc[cj + i2 - j], alj2 = colb[l2];
+        LT acc = Lc[colstart(l, D) + i - l], acc2 = Lc[colstart(l2, D) + i2 - l2];
         // acc -= lij * conj(alj)
         acc.x = fma(-lij.x, alj.x, acc.x);
         acc2.x = fma(-lij2.x, alj2.x, acc2.x);
@@ -986,6 +1057,7 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       const bool live = rhs < nrhs;
       const int rsafe = live ? rhs : 0;
       double2 b[RPL], u[RPL], r[RPL];
+      float2 xf[RPL];
 #pragma unroll
       for (int q = 0; q < RPL; ++q) {
         const int i = li + LR * q;
@@ -1001,7 +1073,15 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
         b[q] = v;
         u[q] = v;
       }
-      big_solve<LR, RPL>(u, Lc, rd, D, li, grp);
+      if constexpr (F32F) {   // FP32 solve of the rounded right-hand side
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) xf[q] = make_float2((float)u[q].x, (float)u[q].y);
+        big_solve_f32<LR, RPL>(xf, Lc, rd, D, li, grp);
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) u[q] = make_double2(xf[q].x, xf[q].y);
+      } else {
+        big_solve<LR, RPL>(u, Lc, rd, D, li, grp);
+      }
       for (int it = 0; it < refine_steps; ++it) {
         // r = b - R u - delta u  (R Hermitian: A[i][l] for i >= l, conj(A[l][i])
         // above, real diagonal; the load is applied after the sweep)
@@ -1037,7 +1117,15 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
           }
         }
         __syncwarp();
-        big_solve<LR, RPL>(r, Lc, rd, D, li, grp);
+        if constexpr (F32F) {   // FP32 correction, added in FP64
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) xf[q] = make_float2((float)r[q].x, (float)r[q].y);
+          big_solve_f32<LR, RPL>(xf, Lc, rd, D, li, grp);
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) r[q] = make_double2(xf[q].x, xf[q].y);
+        } else {
+          big_solve<LR, RPL>(r, Lc, rd, D, li, grp);
+        }
 #pragma unroll
         for (int q = 0; q < RPL; ++q) {
           u[q].x += r[q].x;
@@ -1125,62 +1213,6 @@ __host__ __device__ constexpr size_t big_mir_bytes(int D, int C, int NG, bool se
   // reciprocals [D] float, the pivot flag and the trace
   return ((size_t)(D * (D + 1) / 2) + (sep ? (size_t)C * D : 0) + (size_t)NG * D) * 16 +
          (size_t)(D * (D + 1) / 2) * 8 + (size_t)D * 8 + ((size_t)D * 4 + 15) / 16 * 16 + 32;
-}
-
-// In-place FP32 forward (Lu z = x) or back (Lu^H z = x) substitution, as big_subst.
-template <int LR, int RPL, bool BACK>
-__device__ __forceinline__ void big_subst_f32(float2 (&x)[RPL], const float2* __restrict__ Lc,
-                                              int D, int li, int grp) {
-  for (int jj = 0; jj < D; ++jj) {
-    const int j = BACK ? D - 1 - jj : jj;
-    const int owner = (j % LR) + grp * LR, qj = j / LR;
-    float2 pick = x[0];
-#pragma unroll
-    for (int q = 1; q < RPL; ++q)
-      if (q == qj) pick = x[q];
-    float2 yj;
-    yj.x = __shfl_sync(0xffffffffu, pick.x, owner);
-    yj.y = __shfl_sync(0xffffffffu, pick.y, owner);
-#pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      const bool touch = (BACK ? (q <= qj) : (q >= qj)) && LR * q < D;
-      if (touch) {
-        const int i = li + LR * q;
-        const bool act = BACK ? (i < j) : (i > j && i < D);
-        if (act) {
-          if (BACK) {
-            const float2 l = Lc[colstart(i, D) + j - i];
-            x[q].x = fmaf(-l.x, yj.x, x[q].x);
-            x[q].x = fmaf(-l.y, yj.y, x[q].x);
-            x[q].y = fmaf(-l.x, yj.y, x[q].y);
-            x[q].y = fmaf(l.y, yj.x, x[q].y);
-          } else {
-            const float2 l = Lc[colstart(j, D) + i - j];
-            x[q].x = fmaf(-l.x, yj.x, x[q].x);
-            x[q].x = fmaf(l.y, yj.y, x[q].x);
-            x[q].y = fmaf(-l.x, yj.y, x[q].y);
-            x[q].y = fmaf(-l.y, yj.x, x[q].y);
-          }
-        }
-      }
-    }
-  }
-}
-
-template <int LR, int RPL>
-__device__ __forceinline__ void big_solve_f32(float2 (&x)[RPL], const float2* __restrict__ Lc,
-                                              const float* __restrict__ rd, int D, int li, int grp) {
-  big_subst_f32<LR, RPL, false>(x, Lc, D, li, grp);
-#pragma unroll
-  for (int q = 0; q < RPL; ++q) {
-    if (LR * q < D) {
-      const int i = li + LR * q;
-      const float r = rd[i < D ? i : D - 1];
-      x[q].x *= r;
-      x[q].y *= r;
-    }
-  }
-  big_subst_f32<LR, RPL, true>(x, Lc, D, li, grp);
 }
 
 template <bool SEP, int LR, int NT, int RPL>
@@ -1450,18 +1482,18 @@ cudaError_t launch_big_mir(const double2* cov, float2* wts, const float4* steer_
   return cudaGetLastError();
 }
 
-template <bool SEP, int LR, int NT, int RPL>
+template <bool SEP, int LR, int NT, int RPL, bool F32F = false>
 cudaError_t launch_big(const double2* cov, float2* wts, const double2* steer, const double2* sep_g,
                        const float4* steer_ff, const float4* sep_a_ff, long long nsys, int D, int S,
                        int C, double lf, int refine, DeviceStatus* status, size_t smem,
                        cudaStream_t s) {
   static int set_bytes[64] = {0};
-  cudaError_t e = ensure_smem(solve_big_kernel<SEP, LR, NT, RPL>, smem, set_bytes);
+  cudaError_t e = ensure_smem(solve_big_kernel<SEP, LR, NT, RPL, F32F>, smem, set_bytes);
   if (e != cudaSuccess) return e;
   const int per_sm = (int)(228 * 1024 / (smem + 1024));
   long long blocks = 152LL * (per_sm < 1 ? 1 : per_sm) * 2;
   if (blocks > nsys) blocks = nsys;
-  solve_big_kernel<SEP, LR, NT, RPL><<<(unsigned)blocks, NT, smem, s>>>(
+  solve_big_kernel<SEP, LR, NT, RPL, F32F><<<(unsigned)blocks, NT, smem, s>>>(
       cov, wts, steer, sep_g, steer_ff, sep_a_ff, nsys, D, S, C, lf, refine, status);
   return cudaGetLastError();
 }
@@ -1496,7 +1528,7 @@ cudaError_t launch_mir(const double2* cov, float2* wts, const float4* steer_ff, 
 
 }  // namespace
 
-bool mir_supported(int D) { return D >= 1 && D <= 64; }
+bool mir_supported(int D) { return D >= 1 && D <= kMaxD; }
 
 namespace {
 
@@ -1517,6 +1549,28 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
   if (D < 1 || D > kMaxD || S < 1) return cudaErrorInvalidValue;
   const bool sep = sep_g != nullptr && sep_a != nullptr && steer_ff != nullptr && sep_a_ff != nullptr &&
                    C >= 1 && C <= 32 && D % C == 0;
+  if (solver == 1 && D > 64) {   // refinement with an FP32 factor and FP64 residuals
+    if (!mir_supported(D) || steer_ff == nullptr) return cudaErrorNotSupported;
+    const int LR = tn.solve_lr == 16 ? 16 : 32;    // 16 lanes x 8 rows or 32 x 4, 8 warps
+    const size_t Dp = (size_t)D * (D + 1) / 2, ng = 256 / LR;
+    auto bytes = [&](bool with_u) {
+      return ((Dp + D) * sizeof(float2) + 15) / 16 * 16 + ((with_u ? (size_t)C * D : 0) + ng * D) * 16 +
+             D * sizeof(float) + 16;
+    };
+    const bool sep_big = sep && bytes(true) <= 227 * 1024;
+    const size_t smem = bytes(sep_big);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+#define STAP_BIGF(lr, rpl)                                                                           \
+  return sep_big ? launch_big<true, lr, 256, rpl, true>(cov, wts, steer, sep_g, steer_ff, sep_a_ff, \
+                                                        nsys, D, S, C, load_factor, refine_steps,   \
+                                                        status, smem, s)                             \
+                 : launch_big<false, lr, 256, rpl, true>(cov, wts, steer, nullptr, nullptr, nullptr,\
+                                                         nsys, D, S, C, load_factor, refine_steps,  \
+                                                         status, smem, s)
+    if (LR == 16) STAP_BIGF(16, 8);
+    STAP_BIGF(32, 4);
+#undef STAP_BIGF
+  }
   if (solver == 1 && !(D == 8 || D == 12 || D == 16)) {  // refinement, one system per CTA
     if (!mir_supported(D) || steer_ff == nullptr) return cudaErrorNotSupported;
     const bool msep = sep && g_ff != nullptr;
@@ -1579,7 +1633,7 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
     // Lu, pivot column, (SEP) basis solutions, broadcast vectors; pivot
     // reciprocals and the pivot flag
     auto bytes = [&](bool with_u) {
-      return (Dp + D + (with_u ? (size_t)C * D : 0) + ng * D) * sizeof(double2) +
+      return (Dp + D) * sizeof(double2) + ((with_u ? (size_t)C * D : 0) + ng * D) * 16 +
              D * sizeof(double) + 16;
     };
     const bool sep_big = sep && bytes(true) <= 227 * 1024;

@@ -124,7 +124,8 @@ def test_options_default_and_mixed_refinement_shape_limits():
                        ((5, 16, 32, 256, 2, 32, 4), stap.STAP_OK),                 # D = 10
                        ((16, 16, 32, 256, 4, 32, 4), stap.STAP_OK),                # D = 64
                        ((11, 16, 32, 256, 3, 32, 4), stap.STAP_OK),                # D = 33
-                       ((25, 16, 32, 256, 3, 32, 4), stap.STAP_ERR_UNSUPPORTED)]:  # D = 75
+                       ((25, 16, 32, 256, 3, 32, 4), stap.STAP_OK),                # D = 75
+                       ((43, 16, 32, 256, 3, 32, 4), stap.STAP_ERR_UNSUPPORTED)]:  # D = 129
         got, h, _ = _create(dims, mir)
         assert got == code, dims
         if h.value:

@@ -306,6 +306,8 @@ MIR_SPECS.update({
     "D24": synth.CPISpec(8, 16, 32, 128, 3, 64, 9, cnr_db=35.0, seed=25),
     "D33": synth.CPISpec(11, 16, 16, 96, 3, 48, 7, cnr_db=35.0, seed=24),     # odd D, S % 8 != 0
     "D64": synth.CPISpec(16, 32, 64, 256, 4, 128, 8, cnr_db=40.0, seed=14),
+    "D100": EDGE_SPECS[9],                                                      # FP32 factor,
+    "D128": EDGE_SPECS[8],                                                      # FP64 residuals
 })
 
 
@@ -330,8 +332,8 @@ def test_mixed_refinement_weights_match_the_oracle(name, separable, refine):
     plan.close()
 
 
-@pytest.mark.parametrize("spec", [synth.small_cpi(), synth.standard_cpi(), MIR_SPECS["D64"]],
-                         ids=["small", "standard", "D64"])
+@pytest.mark.parametrize("spec", [synth.small_cpi(), synth.standard_cpi(), MIR_SPECS["D64"],
+                                  MIR_SPECS["D128"]], ids=["small", "standard", "D64", "D128"])
 def test_mixed_refinement_end_to_end_meets_the_plain_bar(spec):
     d = oracle.Dims(*spec.dims())
     cube = _cube(spec)
