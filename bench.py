@@ -35,9 +35,13 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the solve kernel on the standard CPI
 # (dram__bytes_read.sum + dram__bytes_write.sum of one unslabbed launch, from
 # the ncu capture summarised in profiles/fp32_path_standard_cpi_full.md), keyed
-# by a hash of the kernel source so that a changed kernel reports null until
-# re-measured.
-SOLVE_TRAFFIC = {"481129e722416c2f": 34.66e6}
+# by a hash of the kernel source and the solve kernel the tuning chose
+# (1 register-resident, 2 shared-memory teams, 3 one system per CTA), so that
+# a changed or different kernel reports null until re-measured.
+SOLVE_TRAFFIC = {("481129e722416c2f", 1): 34.66e6}
+SOLVE_KERNELS = {1: "solve_reg_kernel (register-resident FP64 LDL^H, solves, refinement)",
+                 2: "solve_kernel (shared-memory FP64 Cholesky teams, solves, refinement)",
+                 3: "solve_big_kernel (one system per CTA: FP64 LDL^H, solves, refinement)"}
 
 
 def peaks():
@@ -307,12 +311,13 @@ def run_gpu(args):
                   "frac": apply_flops / kt["apply"] / 1e9 / pk["fp32_tflops"],
                   "hbm_frac": apply_bytes / kt["apply"] / 1e6 / pk["hbm_gbs"]},
     }
-    roofline = {"kernel": "solve_kernel (FP64 loading, Cholesky, solves, refinement)",
+    solve_kind = list(tuning.values())[0][7]
+    roofline = {"kernel": SOLVE_KERNELS.get(solve_kind, "solve"),
                 "bound": "alu", "achieved": kernels["solve"]["achieved_tflops"],
                 "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
                 "frac": kernels["solve"]["frac"], "traffic": None,
                 "peak_src": "FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (unit count and max clock)"}
-    roofline["traffic"] = SOLVE_TRAFFIC.get(kernel_hash())
+    roofline["traffic"] = SOLVE_TRAFFIC.get((kernel_hash(), solve_kind))
 
     # ---- the mixed-precision path (tensor-core contractions) on the same CPI ----
     mplan = stap.Plan(spec.dims(), device=dev, precision=stap.STAP_PREC_TF32X3)

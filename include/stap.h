@@ -281,8 +281,9 @@ stap_status stap_plan_autotune(stap_plan plan, const void* const* cubes, float* 
  * heuristic): Doppler cells per CTA, covariance bins per CTA, solve lanes per
  * system, solve warps per CTA, large-solve lanes per right-hand side, apply
  * kernel (1 register-resident, 2 general), range slabs of a one-CPI
- * stap_run_cpi (at most 8 and NB are used), solve kernel for D = 8, 12, 16
- * (1 register-resident, 2 shared-memory), covariance of a mixed-precision
+ * stap_run_cpi (at most 8 and NB are used), solve kernel for D <= 32
+ * (1 register-resident for D = 8, 12, 16, 2 shared-memory teams, 3 one
+ * system per CTA), covariance of a mixed-precision
  * plan (1 FP32, 2 tensor cores; apply choice 3 = tensor cores).  set_tuning installs saved choices
  * (values 0..64; a choice that does not fit a launch falls back to the
  * heuristic). */

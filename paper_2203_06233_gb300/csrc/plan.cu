@@ -773,6 +773,10 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
               bkind = kind;
             }
           }
+      c.tune.solve_kind = 3;   // one system per CTA instead of teams
+      if (p->opt.solver == STAP_SOLVE_FP64 &&
+          timeit([&] { return do_solve(p, c, cov, wts, p->stream); }) < bt)
+        bkind = 3;
       c.tune.solve_kind = bkind;
       c.tune.solve_ts = bts;
       c.tune.solve_nw = bnw;

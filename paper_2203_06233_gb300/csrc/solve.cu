@@ -1024,8 +1024,10 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
     }
     const bool ok = *okf != 0;
 
-    // weights of steering vector s from u (rows li + LR q): group-wide
-    auto emit = [&](int s, const double2 (&u)[RPL]) {
+    // weights of steering vector s from u (rows li + LR q): group-wide, and
+    // called by every group (the sum shuffles across the whole warp); only a
+    // live group stores
+    auto emit = [&](int s, const double2 (&u)[RPL], bool live) {
       const double2* v = steer + (size_t)s * D;
       double qp = 0.0;
 #pragma unroll
@@ -1040,6 +1042,7 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       const double qs = group_sum<LR>(qp);
       const bool good = ok && qs > 0.0 && isfinite(qs);
       const double scale = good ? rsqrt(qs) : 0.0;
+      if (!live) return;
       float2* w = wts + ((size_t)sys * S + s) * D;
 #pragma unroll
       for (int q = 0; q < RPL; ++q) {
@@ -1132,14 +1135,13 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
           u[q].y += r[q].y;
         }
       }
-      if (live) {
-        if (SEP) {
+      if (SEP) {
+        if (live)
 #pragma unroll
           for (int q = 0; q < RPL; ++q)
             if (li + LR * q < D) Ubf[(size_t)rhs * D + li + LR * q] = to_ff4(u[q]);
-        } else {
-          emit(rhs, u);
-        }
+      } else {
+        emit(rsafe, u, live);
       }
     }
     if (SEP) {
@@ -1619,7 +1621,9 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
     STAP_MIR(16);
 #undef STAP_MIR
   }
-  if (D > kSmallMaxD) {  // one system per CTA, lanes over rows
+  // one system per CTA, lanes over rows: above D = 32, and below where the
+  // tuning found it faster (solve_kind 3)
+  if (D > kSmallMaxD || tn.solve_kind == 3) {
     // LR lanes per right-hand side, each holding RPL rows (D <= LR * RPL):
     //   LR = 8:  RPL 8, 4 warps (D <= 64)
     //   LR = 16: RPL 4, 4 warps (D <= 64) or RPL 8, 8 warps (D <= 128)
@@ -1627,6 +1631,7 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
     // default: 16 up to D = 64 (several CTAs per SM), 32 above
     int LR = D <= 64 ? 16 : 32;
     if (tn.solve_lr == 32 || tn.solve_lr == 16 || (tn.solve_lr == 8 && D <= 64)) LR = tn.solve_lr;
+    if (D <= kSmallMaxD) LR = 8;
     const int NT = (LR == 8 || (LR == 16 && D <= 64)) ? 128 : 256;
     const size_t Dp = (size_t)D * (D + 1) / 2;
     const size_t ng = NT / LR;

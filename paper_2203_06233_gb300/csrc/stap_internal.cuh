@@ -33,7 +33,8 @@ struct Tune {
   int solve_lr = 0;    // D > 32 solve: lanes per right-hand side, 8 (D <= 64), 16 or 32
   int apply_kind = 0;  // apply: 1 FP32 register-resident, 2 FP32 general, 3 tensor cores
   int slabs = 0;       // single-CPI run: range slabs pipelined on prioritised streams, 1..8
-  int solve_kind = 0;  // D = 8, 12, 16 solve: 1 register-resident, 2 generic shared-memory
+  int solve_kind = 0;  // D <= 32 solve: 1 register-resident (D = 8, 12, 16), 2 shared-memory
+                       // teams, 3 one system per CTA
   int cov_kind = 0;    // covariance: 1 FP32 error-free, 2 tensor cores (mixed-precision plans)
 };
 

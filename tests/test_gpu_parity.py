@@ -226,6 +226,31 @@ def test_generic_and_separable_solves_agree(spec):
         assert np.max(err) <= 2 * EPS32 * np.sqrt(2), np.max(err)
 
 
+@pytest.mark.parametrize("separable", [True, False], ids=["sep", "explicit"])
+@pytest.mark.parametrize("lr", [8, 16, 32])
+def test_per_cta_solve_with_idle_lane_groups(lr, separable):
+    """One system per CTA with LR lanes per right-hand side: D = 40 and S = 5
+    leave a warp holding both a live and an idle lane group (LR = 8, 16), so
+    the normalisation's group-wide sum runs in every group and only live
+    groups store.  Weights must match the oracle at every LR."""
+    spec = synth.CPISpec(10, 16, 16, 128, 4, 64, 5, cnr_db=35.0, seed=26)   # D = 40, S = 5
+    d = oracle.Dims(*spec.dims())
+    cov = oracle.covariance(d, oracle.doppler(d, _cube(spec)))
+    ref, _, nf = oracle.weights(d, cov)
+    assert nf == 0
+    plan = _plan(spec)
+    if not separable:
+        plan.set_steering(oracle.default_steering(d))
+    choices = stap.stap_plan_get_tuning(plan.handle, 0)
+    choices[4] = lr
+    stap.stap_plan_set_tuning(plan.handle, 0, choices)
+    wts = to_np(plan.solve_weights(_dev(cov, torch.complex128)))
+    assert plan.status() == (stap.STAP_OK, 0)
+    err = np.linalg.norm(wts - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+    assert np.max(err) <= 2 * EPS32 * np.sqrt(2), np.max(err)
+    plan.close()
+
+
 # Snapshot lengths with a register-resident solve kernel (D = 8, 12, 16), each
 # with a steering count that leaves idle lanes in the last pass.
 REG_SPECS = {
@@ -235,21 +260,29 @@ REG_SPECS = {
 }
 
 
+SMALL_SPECS = dict(REG_SPECS)
+SMALL_SPECS.update({
+    "D6": synth.CPISpec(3, 20, 32, 96, 2, 32, 5, cnr_db=30.0, seed=11),
+    "D24": synth.CPISpec(8, 16, 32, 128, 3, 64, 9, cnr_db=35.0, seed=25),
+})
+
+
 @pytest.mark.parametrize("refine", [0, 1])
 @pytest.mark.parametrize("separable", [True, False], ids=["sep", "explicit"])
-@pytest.mark.parametrize("name", list(REG_SPECS))
+@pytest.mark.parametrize("name", list(SMALL_SPECS))
 def test_register_and_shared_memory_solves_match_the_oracle(name, separable, refine):
-    """Both small-system solve kernels (tuning choice 8: 1 register-resident
-    LDL^H, 2 shared-memory Cholesky) on the default separable steering and on
-    the same table given explicitly (one solve per steering vector)."""
-    spec = REG_SPECS[name]
+    """The small-system solve kernels (tuning choice 8: 1 register-resident
+    LDL^H where D = 8, 12, 16, 2 shared-memory Cholesky teams, 3 one system per
+    CTA) on the default separable steering and on the same table given
+    explicitly (one solve per steering vector)."""
+    spec = SMALL_SPECS[name]
     d = oracle.Dims(*spec.dims())
     cov = oracle.covariance(d, oracle.doppler(d, _cube(spec)))
     ref, _, nf = oracle.weights(d, cov)
     assert nf == 0
     covd = _dev(cov, torch.complex128)
     out = {}
-    for kind in (1, 2):
+    for kind in (1, 2, 3):
         plan = _plan(spec, refine_steps=refine)
         if not separable:
             plan.set_steering(oracle.default_steering(d))
@@ -262,11 +295,12 @@ def test_register_and_shared_memory_solves_match_the_oracle(name, separable, ref
         assert np.max(err) <= 2 * EPS32 * np.sqrt(2), (kind, np.max(err))
         out[kind] = wts
         plan.close()
-    diff = np.linalg.norm(out[1] - out[2], axis=-1) / np.linalg.norm(out[2], axis=-1)
-    assert np.max(diff) <= 4 * EPS32, np.max(diff)
+    for kind in (1, 3):
+        diff = np.linalg.norm(out[kind] - out[2], axis=-1) / np.linalg.norm(out[2], axis=-1)
+        assert np.max(diff) <= 4 * EPS32, (kind, np.max(diff))
 
 
-@pytest.mark.parametrize("kind", [1, 2], ids=["register", "shared"])
+@pytest.mark.parametrize("kind", [1, 2, 3], ids=["register", "shared", "per_cta"])
 def test_not_positive_definite_flagged_by_both_small_solves(kind):
     spec = synth.CPISpec(4, 4, 4, 12, 2, 4, 3, cnr_db=None, seed=52)   # D = 8, 4 x 3 systems
     d = oracle.Dims(*spec.dims())
