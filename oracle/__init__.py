@@ -11,6 +11,10 @@ statement T is the `fft` over pulses, statement U the array multiply; the
 remaining steps are the standard post-Doppler STAP reading):
 
 1. ``doppler``     Hann-windowed direct DFT over pulses, zero-padded to K bins.
+   ``doppler_staggered`` (an option beyond the paper): T sub-windows of
+   P - T + 1 pulses, each transformed with its pulses' CPI phase; the result
+   is a Doppler cube of C*T channels (``staggered_dims``) with one bin per
+   snapshot, and ``default_steering_staggered`` its steering.
 2. ``snapshot``    D = C*T entries from T adjacent bins, channel fastest.
 3. ``covariance``  R = (1/B) sum x x^H per (Doppler bin, range block).
    ``train_neighbours`` (an option beyond the paper): block b trained on the
@@ -90,9 +94,14 @@ def lib():
         L.oracle_run.argtypes = [D, P, P, ctypes.c_double, i32, i32, P, P, P, P, P]
         L.oracle_train_neighbours.argtypes = [D, P, i32, i32, i32, P]
         L.oracle_run_neighbours.argtypes = [D, P, P, ctypes.c_double, i32, i32, P, P]
+        L.oracle_doppler_staggered.argtypes = [D, P, i32, i32, P]
+        L.oracle_default_steering_staggered.argtypes = [D, P]
+        L.oracle_run_staggered.argtypes = [D, P, P, ctypes.c_double, i32, i32, P, P, P, P, P]
         for f in ("oracle_doppler_window", "oracle_doppler", "oracle_snapshot", "oracle_covariance",
                   "oracle_cholesky", "oracle_cholesky_solve", "oracle_default_steering",
-                  "oracle_weights", "oracle_apply", "oracle_run"):
+                  "oracle_weights", "oracle_apply", "oracle_run", "oracle_train_neighbours",
+                  "oracle_run_neighbours", "oracle_doppler_staggered",
+                  "oracle_default_steering_staggered", "oracle_run_staggered"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -221,14 +230,43 @@ def train_neighbours(d: Dims, cov) -> np.ndarray:
     return out
 
 
-def run(d: Dims, cube, r0=0, nr=None, steer=None, load_factor=1e-3, keep=False, training=0):
+def staggered_dims(d: Dims) -> Dims:
+    """The dims under which covariance, weights and apply see staggered
+    snapshots: C*T channels, one bin (T = 1)."""
+    return Dims(d.n_chan * d.tdof, d.n_pulses, d.n_dop, d.n_range, 1, d.training_block,
+                d.n_steering)
+
+
+def doppler_staggered(d: Dims, cube, r0=0, nr=None) -> np.ndarray:
+    """Xs[T*C][K][nr]: sub-window t (pulses t .. t+P-T) of channel c in row t*C + c."""
+    nr, x = _slab(d, cube, r0, nr)
+    out = np.empty((d.tdof * d.n_chan, d.n_dop, nr), np.complex128)
+    _check(lib().oracle_doppler_staggered(ctypes.byref(d.c(nr)), _ptr(x), 0, nr, _ptr(out)),
+           "doppler_staggered")
+    return out
+
+
+def default_steering_staggered(d: Dims) -> np.ndarray:
+    """steer[S][D] of staggered snapshots: v_s[t*C + c] = (sum h') a_c."""
+    st = np.empty((d.n_steering, d.D), np.complex128)
+    _check(lib().oracle_default_steering_staggered(ctypes.byref(d.c()), _ptr(st)),
+           "default_steering_staggered")
+    return st
+
+
+def run(d: Dims, cube, r0=0, nr=None, steer=None, load_factor=1e-3, keep=False, training=0,
+        staggered=False):
     """Steps 1-8 on the range cells [r0, r0+nr) of a [C][P][R] cube.
 
     Returns a dict with ``out`` [S][K][nr] (float64), ``status`` [K][nr/B] and
     ``n_failed``; with ``keep`` also ``dop``, ``cov`` and ``wts``.  With
     ``training=1`` each block is trained on its neighbours (``train_neighbours``);
-    the window is then computed from a slab one block wider on each side.
+    the window is then computed from a slab one block wider on each side.  With
+    ``staggered`` the snapshots are PRI-staggered (``doppler_staggered``; ``dop``
+    is then [T*C][K][nr]).
     """
+    if training and staggered:
+        raise ValueError("neighbour training with staggered snapshots is not defined here")
     if training:
         if keep:
             raise ValueError("keep is not available with neighbour training")
@@ -250,12 +288,13 @@ def run(d: Dims, cube, r0=0, nr=None, steer=None, load_factor=1e-3, keep=False, 
     res = {"out": out, "status": status}
     dop = cov = wts = None
     if keep:
-        dop = res["dop"] = np.empty((d.n_chan, d.n_dop, nr), np.complex128)
+        dop = res["dop"] = np.empty((d.D if staggered else d.n_chan, d.n_dop, nr), np.complex128)
         cov = res["cov"] = np.empty((d.n_dop, NB, d.D, d.D), np.complex128)
         wts = res["wts"] = np.empty((d.n_dop, NB, d.n_steering, d.D), np.complex128)
     st = None if steer is None else _c128(steer)
     nul = ctypes.c_void_p(0)
-    rc = lib().oracle_run(ctypes.byref(d.c(nr)), _ptr(x), _ptr(st) if st is not None else nul,
+    fn = lib().oracle_run_staggered if staggered else lib().oracle_run
+    rc = fn(ctypes.byref(d.c(nr)), _ptr(x), _ptr(st) if st is not None else nul,
                           float(load_factor), 0, nr,
                           _ptr(dop) if keep else nul, _ptr(cov) if keep else nul,
                           _ptr(wts) if keep else nul, _ptr(out), _ptr(status))

@@ -30,6 +30,10 @@
  *   7. w_s = u_s / sqrt(Re v_s^H u_s)      (unit noise gain / AMF weights)
  *   8. P[s][k][r] = |w_{k,b(r),s}^H x_{k,r}|^2
  *
+ *   PRI-staggered snapshots (an option beyond the paper; oracle_run_staggered):
+ *   T sub-windows of P - T + 1 pulses replace the T adjacent bins (see the
+ *   block comment above oracle_doppler_staggered).
+ *
  *   Default steering (same for every Doppler bin):
  *        theta_s = -90 deg + 180 deg (s + 1/2) / S,  f_s = sin(theta_s) / 2
  *        a_c     = exp(j 2 pi f_s c)
@@ -468,6 +472,134 @@ done:
   free(cov);
   free(trn);
   free(wts);
+  free(steer_t);
+  return rc;
+}
+
+/* ---------------------------------------------------------------------------
+ * PRI-staggered post-Doppler (a variant beyond the paper's kernel, which fixes
+ * only an fft over pulses): the T temporal degrees of freedom come from T
+ * sub-windows of P' = P - T + 1 consecutive pulses instead of T adjacent bins
+ * of one transform.  Sub-window t holds the pulses t .. t+P'-1, windowed by the
+ * symmetric Hann h' of length P'; each pulse keeps the phase of its index in
+ * the whole CPI:
+ *   Xs[t][c][k][r] = sum_{p=t}^{t+P'-1} h'[p - t] x[c][p][r] exp(-j 2 pi p k / K)
+ * The snapshot of cell (k, r) takes the same bin of every sub-window,
+ *   x_{k,r}[t*C + c] = Xs[t][c][k][r],
+ * so Xs[T][C][K][R] is a Doppler cube of C*T channels with one bin per
+ * snapshot, and steps 3-8 are the ones above for the dims (C*T, P, K, R, 1, B,
+ * S).  A unit target at bin centre k/K and angle theta_s gives
+ * Xs[t][c][k] = G a_c in every sub-window (G = sum h'), hence the steering
+ *   v_s[t*C + c] = G a_c.
+ * Referencing each sub-window to its own first pulse instead multiplies
+ * sub-window t's bin k by exp(j 2 pi k t / K) and the steering by the same
+ * factor; that diagonal unitary change of basis leaves every output power
+ * unchanged.
+ */
+
+/* The dims under which steps 3-8 see the staggered snapshots. */
+static oracle_dims staggered_inner(const oracle_dims* d) {
+  oracle_dims e = *d;
+  e.n_chan = d->n_chan * d->tdof;
+  e.tdof = 1;
+  return e;
+}
+
+static int staggered_ok(const oracle_dims* d) {
+  return dims_ok(d) && d->tdof <= d->n_pulses;
+}
+
+/* dop[T][C][K][nr] for the range cells r0 .. r0+nr-1 of cube[C][P][R]. */
+int oracle_doppler_staggered(const oracle_dims* d, const cplx* cube, int32_t r0, int32_t nr,
+                             cplx* dop) {
+  if (!staggered_ok(d) || !cube || !dop || r0 < 0 || nr < 0 || r0 + nr > d->n_range)
+    return ORACLE_BAD_ARGS;
+  const int C = d->n_chan, P = d->n_pulses, K = d->n_dop, R = d->n_range, T = d->tdof;
+  const int Ps = P - T + 1;
+  double* h = (double*)malloc(sizeof(double) * (size_t)Ps);
+  cplx* tw = (cplx*)malloc(sizeof(cplx) * (size_t)K);
+  if (!h || !tw) {
+    free(h);
+    free(tw);
+    return ORACLE_NO_MEMORY;
+  }
+  oracle_hann(Ps, h);
+  for (int n = 0; n < K; ++n) tw[n] = twiddle(n, K);
+#pragma omp parallel for collapse(3) schedule(static)
+  for (int t = 0; t < T; ++t) {
+    for (int c = 0; c < C; ++c) {
+      for (int k = 0; k < K; ++k) {
+        for (int rr = 0; rr < nr; ++rr) {
+          cplx acc = 0.0;
+          for (int p = t; p < t + Ps; ++p) {
+            const cplx x = cube[((size_t)c * P + p) * R + (size_t)(r0 + rr)];
+            acc += h[p - t] * x * tw[((int64_t)p * k) % K];
+          }
+          dop[(((size_t)t * C + c) * K + k) * nr + rr] = acc;
+        }
+      }
+    }
+  }
+  free(h);
+  free(tw);
+  return ORACLE_OK;
+}
+
+/* Default steering steer[S][D] of the staggered snapshots (same for every bin). */
+int oracle_default_steering_staggered(const oracle_dims* d, cplx* steer) {
+  if (!staggered_ok(d) || !steer) return ORACLE_BAD_ARGS;
+  const int C = d->n_chan, T = d->tdof, S = d->n_steering, D = C * T;
+  const int Ps = d->n_pulses - T + 1;
+  double* h = (double*)malloc(sizeof(double) * (size_t)Ps);
+  if (!h) return ORACLE_NO_MEMORY;
+  oracle_hann(Ps, h);
+  double G = 0.0;
+  for (int p = 0; p < Ps; ++p) G += h[p];
+  for (int s = 0; s < S; ++s) {
+    double theta = (-90.0 + 180.0 * ((double)s + 0.5) / (double)S) * kPi / 180.0;
+    double fs = 0.5 * sin(theta);
+    for (int t = 0; t < T; ++t)
+      for (int c = 0; c < C; ++c) {
+        double a = 2.0 * kPi * fs * (double)c;
+        steer[(size_t)s * D + t * C + c] = G * (cos(a) + I * sin(a));
+      }
+  }
+  free(h);
+  return ORACLE_OK;
+}
+
+/* Steps 1-8 with the staggered transform, as oracle_run: dop [T][C][K][nr],
+ * cov [K][nr/B][D][D], wts [K][nr/B][S][D] (each may be NULL), out [S][K][nr]. */
+int oracle_run_staggered(const oracle_dims* d, const cplx* cube, const cplx* steer,
+                         double load_factor, int32_t r0, int32_t nr, cplx* dop, cplx* cov,
+                         cplx* wts, double* out, int32_t* status) {
+  if (!staggered_ok(d) || !cube || !out || !window_ok(d, r0, nr)) return ORACLE_BAD_ARGS;
+  const oracle_dims e = staggered_inner(d);
+  const int K = d->n_dop, S = d->n_steering, D = d->n_chan * d->tdof;
+  const int NB = nr / d->training_block;
+  cplx *dop_t = NULL, *cov_t = NULL, *wts_t = NULL, *steer_t = NULL;
+  int rc = ORACLE_NO_MEMORY;
+  if (!dop) dop = dop_t = (cplx*)malloc(sizeof(cplx) * (size_t)D * K * nr);
+  if (!cov) cov = cov_t = (cplx*)malloc(sizeof(cplx) * (size_t)K * NB * D * D);
+  if (!wts) wts = wts_t = (cplx*)malloc(sizeof(cplx) * (size_t)K * NB * S * D);
+  if (!steer) {
+    steer = steer_t = (cplx*)malloc(sizeof(cplx) * (size_t)S * D);
+    if (steer_t && oracle_default_steering_staggered(d, steer_t) != ORACLE_OK) goto done;
+  }
+  if (!dop || !cov || !wts || !steer) goto done;
+  if ((rc = oracle_doppler_staggered(d, cube, r0, nr, dop)) != ORACLE_OK) goto done;
+  if ((rc = oracle_covariance(&e, dop, nr, cov)) != ORACLE_OK) goto done;
+  int failed = oracle_weights(&e, cov, K * NB, steer, load_factor, wts, status);
+  if (failed < 0) {
+    rc = failed;
+    goto done;
+  }
+  if ((rc = oracle_apply(&e, dop, nr, wts, out)) != ORACLE_OK) goto done;
+  rc = failed;
+done:
+  free(dop_t);
+  free(cov_t);
+  free(wts_t);
   free(steer_t);
   return rc;
 }

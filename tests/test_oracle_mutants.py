@@ -35,6 +35,13 @@ MUTANTS = {
                            "const cplx* lo = b > 0 ? cov_in + ((size_t)k * nb + b) * DD : NULL;"),
     "training_mean_scale": ("if (lo && hi) o[e] = 0.5 * (lo[e] + hi[e]);",
                             "if (lo && hi) o[e] = lo[e] + hi[e];"),
+    "staggered_phase_reference": ("acc += h[p - t] * x * tw[((int64_t)p * k) % K];",
+                                  "acc += h[p - t] * x * tw[((int64_t)(p - t) * k) % K];"),
+    "staggered_window_length": ("const int Ps = P - T + 1;", "const int Ps = P - T;"),
+    "staggered_steering_gain": ("for (int p = 0; p < Ps; ++p) G += h[p];",
+                                "for (int p = 0; p < Ps; ++p) G += 1.0;"),
+    "staggered_snapshot_order": ("dop[(((size_t)t * C + c) * K + k) * nr + rr] = acc;",
+                                 "dop[(((size_t)c * T + t) * K + k) * nr + rr] = acc;"),
 }
 
 
