@@ -244,6 +244,15 @@ int oracle_cholesky_solve(int32_t D, const cplx* L, const cplx* b, cplx* u) {
   return ORACLE_OK;
 }
 
+/* Spatial part a_c of steering vector s of S: theta_s = -90 deg + 180 deg
+ * (s + 1/2) / S, f_s = sin(theta_s) / 2, a_c = exp(j 2 pi f_s c). */
+static cplx spatial_phase(int s, int S, int c) {
+  double theta = (-90.0 + 180.0 * ((double)s + 0.5) / (double)S) * kPi / 180.0;
+  double fs = 0.5 * sin(theta);
+  double a = 2.0 * kPi * fs * (double)c;
+  return cos(a) + I * sin(a);
+}
+
 /* Default steering table steer[S][D] (see the header comment). */
 int oracle_default_steering(const oracle_dims* d, cplx* steer) {
   if (!dims_ok(d) || !steer) return ORACLE_BAD_ARGS;
@@ -263,15 +272,9 @@ int oracle_default_steering(const oracle_dims* d, cplx* steer) {
     for (int p = 0; p < P; ++p) acc += h[p] * twiddle((int64_t)m * p, K);
     g[t] = acc;
   }
-  for (int s = 0; s < S; ++s) {
-    double theta = (-90.0 + 180.0 * ((double)s + 0.5) / (double)S) * kPi / 180.0;
-    double fs = 0.5 * sin(theta);
+  for (int s = 0; s < S; ++s)
     for (int t = 0; t < T; ++t)
-      for (int c = 0; c < C; ++c) {
-        double a = 2.0 * kPi * fs * (double)c;
-        steer[(size_t)s * D + t * C + c] = g[t] * (cos(a) + I * sin(a));
-      }
-  }
+      for (int c = 0; c < C; ++c) steer[(size_t)s * D + t * C + c] = g[t] * spatial_phase(s, S, c);
   free(h);
   free(g);
   return ORACLE_OK;
@@ -555,15 +558,9 @@ int oracle_default_steering_staggered(const oracle_dims* d, cplx* steer) {
   oracle_hann(Ps, h);
   double G = 0.0;
   for (int p = 0; p < Ps; ++p) G += h[p];
-  for (int s = 0; s < S; ++s) {
-    double theta = (-90.0 + 180.0 * ((double)s + 0.5) / (double)S) * kPi / 180.0;
-    double fs = 0.5 * sin(theta);
+  for (int s = 0; s < S; ++s)
     for (int t = 0; t < T; ++t)
-      for (int c = 0; c < C; ++c) {
-        double a = 2.0 * kPi * fs * (double)c;
-        steer[(size_t)s * D + t * C + c] = G * (cos(a) + I * sin(a));
-      }
-  }
+      for (int c = 0; c < C; ++c) steer[(size_t)s * D + t * C + c] = G * spatial_phase(s, S, c);
   free(h);
   return ORACLE_OK;
 }
