@@ -193,11 +193,12 @@ def power_errors(got, ref):
     return {"normwise": normwise, "max_cell": float(np.max(np.abs(got - ref) / floor))}
 
 
-def cpu_baseline_oracle(spec, outputs=None, neighbour_outputs=None, budget_s=12.0):
+def cpu_baseline_oracle(spec, outputs=None, option_outputs=None, budget_s=12.0):
     """The oracle, as it stands, on the host cores: whole CPIs until ~budget_s.
     Its output also gives the error of each GPU output in `outputs`
-    ({name: host array [S][K][R]}) on the same cube, and of those in
-    `neighbour_outputs` against its neighbour-block-training output."""
+    ({name: host array [S][K][R]}) on the same cube, and of each entry
+    {name: (output, oracle.run keyword arguments)} of `option_outputs` against
+    the oracle run with those options."""
     import oracle
     from paper_2203_06233_gb300 import synth
     d = oracle.Dims(*spec.dims())
@@ -216,9 +217,8 @@ def cpu_baseline_oracle(spec, outputs=None, neighbour_outputs=None, budget_s=12.
     base = {"value": cells / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{n} whole CPI(s) of the standard workload ({cells} cells) in {el:.1f} s"}
     errors = {name: power_errors(out, ref) for name, out in (outputs or {}).items()}
-    if neighbour_outputs:
-        ref_n = oracle.run(d, cube, training=1)["out"]
-        errors.update({name: power_errors(out, ref_n) for name, out in neighbour_outputs.items()})
+    for name, (out, kw) in (option_outputs or {}).items():
+        errors[name] = power_errors(out, oracle.run(d, cube, **kw)["out"])
     return base, errors
 
 
@@ -382,28 +382,35 @@ def run_gpu(args):
         }
         iplan.close()
 
-    # ---- training with guard cells (neighbour blocks; an option beyond the paper) ----
-    neighbours = None
-    if stap.stap_abi_version() >= 3 and NB >= 2:
-        nplan = stap.Plan(spec.dims(), device=dev, training=stap.STAP_TRAIN_NEIGHBOURS)
-        nout = torch.empty_like(out)
-        ntuning = nplan.autotune(cube, nout)
+    # ---- options beyond the paper, each on the same CPI with its own tuning ----
+    def option_leg(what, **plan_kw):
+        oplan = stap.Plan(spec.dims(), device=dev, **plan_kw)
+        oout = torch.empty_like(out)
+        otuning = oplan.autotune(cube, oout)
         for _ in range(args.warmup):
             flush()
-            nplan.run_cpi(cube, nout)
+            oplan.run_cpi(cube, oout)
         torch.cuda.synchronize()
-        ntimes = time_steps(lambda: nplan.run_cpi(cube, nout), args.steps, flush, stream)
-        code, failed = nplan.status()
+        otimes = time_steps(lambda: oplan.run_cpi(cube, oout), args.steps, flush, stream)
+        code, failed = oplan.status()
         if code != stap.STAP_OK:
-            raise RuntimeError(f"neighbour training: device status {code} ({failed} failed systems)")
-        nplan.run_cpi(cube, nout)
-        neighbours = {
-            "value": world * cells * args.steps / (sum(ntimes) * 1e-3),
-            "ms_per_step": sum(ntimes) / args.steps,
-            "training": "block b trained on blocks b-1 and b+1 (STAP_TRAIN_NEIGHBOURS), FP64 solve",
-            "tuning": ntuning,
-        }
-        nplan.close()
+            raise RuntimeError(f"{what}: device status {code} ({failed} failed systems)")
+        oplan.run_cpi(cube, oout)
+        oplan.close()
+        return {"value": world * cells * args.steps / (sum(otimes) * 1e-3),
+                "ms_per_step": sum(otimes) / args.steps, "tuning": otuning}, oout
+
+    # training with guard cells (neighbour blocks)
+    neighbours = None
+    if stap.stap_abi_version() >= 3 and NB >= 2:
+        neighbours, nout = option_leg("neighbour training", training=stap.STAP_TRAIN_NEIGHBOURS)
+        neighbours["training"] = "block b trained on blocks b-1 and b+1 (STAP_TRAIN_NEIGHBOURS), FP64 solve"
+    # PRI-staggered snapshots
+    staggered = None
+    if stap.stap_abi_version() >= 4 and T <= P:
+        staggered, sout = option_leg("staggered snapshots", snapshots=stap.STAP_SNAP_PRI_STAGGERED)
+        staggered["snapshots"] = ("T sub-windows of P - T + 1 pulses, bin k of each "
+                                  "(STAP_SNAP_PRI_STAGGERED), FP64 solve")
 
     # ---- end to end through the public API from pinned host buffers ----
     cube_pin = torch.from_numpy(cube_h).pin_memory()
@@ -439,12 +446,18 @@ def run_gpu(args):
         line["mixed_ir"] = mixed_ir
     if neighbours is not None:
         line["neighbour_training"] = neighbours
+    if staggered is not None:
+        line["staggered"] = staggered
     if rank == 0 and world == 1 and not args.no_cpu_baseline and NAME == "standard":
         outputs = {"plain": out.cpu().numpy(), "mixed": mout.cpu().numpy()}
         if mixed_ir is not None:
             outputs["mixed_ir"] = iout.cpu().numpy()
-        nbr_outputs = {"neighbour_training": nout.cpu().numpy()} if neighbours is not None else None
-        line["cpu_baseline"], line["errors_vs_oracle"] = cpu_baseline_oracle(spec, outputs, nbr_outputs)
+        opt_outputs = {}
+        if neighbours is not None:
+            opt_outputs["neighbour_training"] = (nout.cpu().numpy(), {"training": 1})
+        if staggered is not None:
+            opt_outputs["staggered"] = (sout.cpu().numpy(), {"staggered": True})
+        line["cpu_baseline"], line["errors_vs_oracle"] = cpu_baseline_oracle(spec, outputs, opt_outputs)
     plan.close()
     if world > 1:
         dist.destroy_process_group()

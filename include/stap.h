@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define STAP_ABI_VERSION 3
+#define STAP_ABI_VERSION 4
 
 typedef enum {
   STAP_OK = 0,
@@ -98,6 +98,21 @@ typedef enum {
                                     slabs (block b needs its neighbours' data) */
 } stap_training;
 
+/* Where a snapshot's T temporal degrees of freedom come from. */
+typedef enum {
+  STAP_SNAP_ADJACENT_BINS = 0, /* T adjacent bins of one Doppler transform of all
+                                  P pulses (the default) */
+  STAP_SNAP_PRI_STAGGERED = 1  /* not in the paper: T transforms of P' = P - T + 1
+                                  pulses each, sub-window t starting at pulse t,
+                                  windowed by the symmetric Hann of length P' and
+                                  keeping each pulse's CPI phase:
+                                    Xs[t][c][k][r] = sum_{p=t}^{t+P'-1}
+                                      h'[p-t] cube[c][p][r] exp(-j 2 pi p k / K);
+                                  the snapshot of bin k takes bin k of every
+                                  sub-window.  The Doppler output then has C*T
+                                  rows (row t*C + c); needs T <= P */
+} stap_snapshots;
+
 typedef struct {
   int32_t n_chan;         /* C >= 1 */
   int32_t n_pulses;       /* P >= 1 */
@@ -114,12 +129,13 @@ typedef struct {
   int32_t precision;    /* a stap_precision value (default STAP_PREC_FP32) */
   int32_t solver;       /* a stap_solver value (default STAP_SOLVE_FP64) */
   int32_t training;     /* a stap_training value (default STAP_TRAIN_OWN_BLOCK) */
+  int32_t snapshots;    /* a stap_snapshots value (default STAP_SNAP_ADJACENT_BINS) */
 } stap_options;
 
 typedef struct stap_plan_s* stap_plan;
 
 /* Fill *opt with the defaults (load_factor 1e-3, refine_steps 1, FP32, FP64
- * solve, own-block training). */
+ * solve, own-block training, adjacent-bin snapshots). */
 void stap_options_default(stap_options* opt);
 
 /* Create a plan for n_cpi CPIs whose shapes are dims[0 .. n_cpi-1].
@@ -130,7 +146,9 @@ void stap_options_default(stap_options* opt);
  * makes no CUDA call.  Sets the default steering table of every CPI:
  *   theta_s = -90 + 180 (s + 1/2)/S degrees, f_s = sin(theta_s)/2,
  *   a_c = exp(j 2 pi f_s c),  g_t = sum_p h[p] exp(-j 2 pi (t - floor(T/2)) p / K),
- *   v_s[t*C + c] = g_t a_c   (h = symmetric Hann of length P). */
+ *   v_s[t*C + c] = g_t a_c   (h = symmetric Hann of length P).
+ * With STAP_SNAP_PRI_STAGGERED, g_t = sum_p h'[p] for every t (a target at a
+ * bin centre has the same response in every sub-window). */
 stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_options* opt,
                              void* cuda_stream, stap_plan* out, size_t* workspace_bytes);
 
@@ -155,13 +173,17 @@ stap_status stap_plan_destroy(stap_plan plan);
 
 /* Statement T (Sec. 4.2): Hann-windowed DFT over pulses, zero-padded to K.
  *   dop[c][k][r] = sum_{p<P} h[p] cube[c][p][r] exp(-j 2 pi p k / K)
- * cube: c64 [C][P][R]; dop: c64 [C][K][R].  Single-CPI plans only. */
+ * cube: c64 [C][P][R]; dop: c64 [C][K][R].  With STAP_SNAP_PRI_STAGGERED:
+ * dop[t*C + c][k][r] = Xs[t][c][k][r] (see stap_snapshots), c64 [C*T][K][R].
+ * Single-CPI plans only. */
 stap_status stap_doppler(stap_plan plan, const void* cube_c64, void* dop_c64);
 
 /* Statement U (Sec. 4.2), one covariance per (Doppler bin k, range block b):
  *   x_{k,r}[t*C + c] = dop[c][(k + t - floor(T/2)) mod K][r]
  *   cov[k][b] = (1/B) sum_{r = bB}^{bB+B-1} x_{k,r} x_{k,r}^H
- * dop: c64 [C][K][R]; cov: c128 [K][NB][D][D], full Hermitian. */
+ * dop: c64 [C][K][R]; cov: c128 [K][NB][D][D], full Hermitian.
+ * With STAP_SNAP_PRI_STAGGERED: x_{k,r}[t*C + c] = dop[t*C + c][k][r], dop
+ * c64 [C*T][K][R]. */
 stap_status stap_covariance(stap_plan plan, const void* dop_c64, void* cov_c128);
 
 /* Training matrices for STAP_TRAIN_NEIGHBOURS, from the per-block covariances
@@ -188,7 +210,8 @@ stap_status stap_solve_weights(stap_plan plan, const void* cov_c128, void* wts_c
 
 /* Output power of every range-Doppler cell:
  *   out[s][k][r] = | w_{k, r/B, s}^H x_{k,r} |^2
- * dop: c64 [C][K][R]; wts: c64 [K][NB][S][D]; out: float [S][K][R]. */
+ * dop: c64 [C][K][R] (STAP_SNAP_PRI_STAGGERED: [C*T][K][R], snapshots as in
+ * stap_covariance); wts: c64 [K][NB][S][D]; out: float [S][K][R]. */
 stap_status stap_apply(stap_plan plan, const void* dop_c64, const void* wts_c64, float* out);
 
 /* The whole chain (Doppler, covariance, weights, apply) for every CPI of the

@@ -15,6 +15,14 @@
 // consecutive complex samples of pulse/bin rows.  The window and the zero
 // padding are applied while loading.  HBM traffic is the algorithmic minimum:
 // 8*C*P*R bytes read + 8*C*K*R bytes written.
+//
+// PRI-staggered snapshots: TW sub-windows of PW = P - TW + 1 pulses per
+// channel, sub-window t covering the pulses t .. t+PW-1 with the window
+// h'[n - t] (length PW) and the pulses' own phase exp(-j 2 pi n k / K), i.e. the
+// same zero-padded FFT of the window-shifted pulse train; sub-window t of
+// channel c is written as output row t*C + c.  CTA row y = c*TW + t, so the TW
+// transforms of one channel run back to back and re-read its pulses from L2.
+// (TW = 1, PW = P: the plain transform.)
 #include "snapshots.cuh"
 
 namespace stap {
@@ -63,7 +71,7 @@ template <int LOGK, int TR>
 __global__ void __launch_bounds__(TR * (1 << ((LOGK + 1) / 2)))
 doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
                    const float* __restrict__ win, const float2* __restrict__ twg, int P, int R,
-                   int ldr) {
+                   int ldr, int C, int TW, int PW) {
   constexpr int K = 1 << LOGK;
   constexpr int N1 = 1 << ((LOGK + 1) / 2);
   constexpr int N2 = 1 << (LOGK / 2);
@@ -72,7 +80,7 @@ doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
   float2* Y = smem + K;     // [N1][N2][TR]
 
   const int tid = threadIdx.x;
-  const int c = blockIdx.y;
+  const int c = blockIdx.y / TW, t = blockIdx.y - c * TW;   // channel, sub-window
   const int r0 = blockIdx.x * TR;
   for (int m = tid; m < K; m += blockDim.x) tw[m] = twg[m];
 
@@ -87,9 +95,9 @@ doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
     for (int n2 = 0; n2 < N2; ++n2) {
       const int n = n1 + N1 * n2;
       float2 x = make_float2(0.f, 0.f);
-      if (in_range && n < P) {
+      if (in_range && n >= t && n < t + PW) {
         x = __ldg(src + (size_t)n * ldr);
-        const float h = __ldg(win + n);
+        const float h = __ldg(win + (n - t));
         x.x *= h;
         x.y *= h;
       }
@@ -114,7 +122,7 @@ doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
     for (int n1 = 0; n1 < N1; ++n1) u[n1] = Y[(n1 * N2 + k2) * TR + col];
     fft_reg<N1, K>(u, tw);
     if (r < R) {
-      float2* dst = dop + (size_t)c * K * ldr + r;
+      float2* dst = dop + ((size_t)t * C + c) * K * ldr + r;
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) dst[(size_t)(k2 + N2 * k1) * ldr] = u[k1];
     }
@@ -123,7 +131,7 @@ doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
 
 template <int LOGK, int TR>
 cudaError_t launch_logk_tr(const float2* cube, float2* dop, const float* win, const float2* tw, int C,
-                           int P, int R, int ldr, cudaStream_t s) {
+                           int TW, int P, int R, int ldr, cudaStream_t s) {
   constexpr int K = 1 << LOGK;
   constexpr int N1 = 1 << ((LOGK + 1) / 2);
   const size_t smem = (size_t)K * sizeof(float2) * (1 + TR);
@@ -132,8 +140,8 @@ cudaError_t launch_logk_tr(const float2* cube, float2* dop, const float* win, co
   static int set_bytes[64] = {0};
   cudaError_t e = ensure_smem(kern, smem, set_bytes);
   if (e != cudaSuccess) return e;
-  dim3 grid((R + TR - 1) / TR, C);
-  kern<<<grid, TR * N1, smem, s>>>(cube, dop, win, tw, P, R, ldr);
+  dim3 grid((R + TR - 1) / TR, C * TW);
+  kern<<<grid, TR * N1, smem, s>>>(cube, dop, win, tw, P, R, ldr, C, TW, P - TW + 1);
   return cudaGetLastError();
 }
 
@@ -142,13 +150,13 @@ cudaError_t launch_logk_tr(const float2* cube, float2* dop, const float* win, co
 // contiguous bytes of a row (two full 32-byte sectors)
 template <int LOGK>
 cudaError_t launch_logk(const float2* cube, float2* dop, const float* win, const float2* tw, int C,
-                        int P, int R, int ldr, cudaStream_t s, int tr) {
+                        int TW, int P, int R, int ldr, cudaStream_t s, int tr) {
   constexpr int N1 = 1 << ((LOGK + 1) / 2);
   if (tr == 0) tr = (N1 >= 32) ? 8 : (N1 >= 16 ? 16 : 32);
   switch (tr) {
-    case 8: return launch_logk_tr<LOGK, 8>(cube, dop, win, tw, C, P, R, ldr, s);
-    case 16: return launch_logk_tr<LOGK, 16>(cube, dop, win, tw, C, P, R, ldr, s);
-    case 32: return launch_logk_tr<LOGK, 32>(cube, dop, win, tw, C, P, R, ldr, s);
+    case 8: return launch_logk_tr<LOGK, 8>(cube, dop, win, tw, C, TW, P, R, ldr, s);
+    case 16: return launch_logk_tr<LOGK, 16>(cube, dop, win, tw, C, TW, P, R, ldr, s);
+    case 32: return launch_logk_tr<LOGK, 32>(cube, dop, win, tw, C, TW, P, R, ldr, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -156,20 +164,21 @@ cudaError_t launch_logk(const float2* cube, float2* dop, const float* win, const
 }  // namespace
 
 cudaError_t launch_doppler(const float2* cube, float2* dop, const float* win, const float2* tw,
-                           int C, int P, int K, int R, int ldr, cudaStream_t s, const Tune& t) {
+                           int C, int TW, int P, int K, int R, int ldr, cudaStream_t s, const Tune& t) {
   const int tr = t.dop_tr;
+  if (TW < 1 || TW > P || (long long)C * TW > 65535) return cudaErrorInvalidValue;
   switch (ilog2c(K)) {
-    case 0: return launch_logk<0>(cube, dop, win, tw, C, P, R, ldr, s, tr);
-    case 1: return launch_logk<1>(cube, dop, win, tw, C, P, R, ldr, s, tr);
-    case 2: return launch_logk<2>(cube, dop, win, tw, C, P, R, ldr, s, tr);
-    case 3: return launch_logk<3>(cube, dop, win, tw, C, P, R, ldr, s, tr);
-    case 4: return launch_logk<4>(cube, dop, win, tw, C, P, R, ldr, s, tr);
-    case 5: return launch_logk<5>(cube, dop, win, tw, C, P, R, ldr, s, tr);
-    case 6: return launch_logk<6>(cube, dop, win, tw, C, P, R, ldr, s, tr);
-    case 7: return launch_logk<7>(cube, dop, win, tw, C, P, R, ldr, s, tr);
-    case 8: return launch_logk<8>(cube, dop, win, tw, C, P, R, ldr, s, tr);
-    case 9: return launch_logk<9>(cube, dop, win, tw, C, P, R, ldr, s, tr);
-    case 10: return launch_logk<10>(cube, dop, win, tw, C, P, R, ldr, s, tr);
+    case 0: return launch_logk<0>(cube, dop, win, tw, C, TW, P, R, ldr, s, tr);
+    case 1: return launch_logk<1>(cube, dop, win, tw, C, TW, P, R, ldr, s, tr);
+    case 2: return launch_logk<2>(cube, dop, win, tw, C, TW, P, R, ldr, s, tr);
+    case 3: return launch_logk<3>(cube, dop, win, tw, C, TW, P, R, ldr, s, tr);
+    case 4: return launch_logk<4>(cube, dop, win, tw, C, TW, P, R, ldr, s, tr);
+    case 5: return launch_logk<5>(cube, dop, win, tw, C, TW, P, R, ldr, s, tr);
+    case 6: return launch_logk<6>(cube, dop, win, tw, C, TW, P, R, ldr, s, tr);
+    case 7: return launch_logk<7>(cube, dop, win, tw, C, TW, P, R, ldr, s, tr);
+    case 8: return launch_logk<8>(cube, dop, win, tw, C, TW, P, R, ldr, s, tr);
+    case 9: return launch_logk<9>(cube, dop, win, tw, C, TW, P, R, ldr, s, tr);
+    case 10: return launch_logk<10>(cube, dop, win, tw, C, TW, P, R, ldr, s, tr);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -21,9 +21,12 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Cpi {
   stap_dims d{};
   int D = 0, NB = 0;
+  // snapshot geometry: Doppler rows Cd and bins per snapshot Td (C, T for
+  // adjacent bins; C*T, 1 for PRI-staggered sub-windows, of which there are TW)
+  int Cd = 0, Td = 0, TW = 1;
   // offsets of this CPI's tables inside the workspace
   size_t win_off = 0, tw_off = 0, steer_off = 0, g_off = 0, a_off = 0;
-  std::vector<float> win;       // [P]
+  std::vector<float> win;       // [P - TW + 1]
   std::vector<float> tw;        // [K][2]
   std::vector<double> steer;    // [S][D][2]
   // steer[s] = g (x) a_s for the default table: temporal factor g [T][2] and
@@ -33,7 +36,7 @@ struct Cpi {
   std::vector<float> steer_ff, sep_a_ff, g_ff;   // the tables as double-floats [..][4]
   size_t steer_ff_off = 0, a_ff_off = 0, g_ff_off = 0;
   stap::Tune tune;              // launch choices (autotuner or defaults)
-  size_t dop_elems() const { return (size_t)d.n_chan * d.n_dop * d.n_range; }
+  size_t dop_elems() const { return (size_t)Cd * d.n_dop * d.n_range; }
   size_t cov_elems() const { return (size_t)d.n_dop * NB * D * D; }
   size_t wts_elems() const { return (size_t)d.n_dop * NB * d.n_steering * D; }
 };
@@ -71,7 +74,8 @@ void to_ff(const std::vector<double>& src, std::vector<float>& dst) {
 
 void make_tables(Cpi& c) {
   const stap_dims& d = c.d;
-  const int P = d.n_pulses, K = d.n_dop, T = d.tdof, C = d.n_chan, S = d.n_steering;
+  const int K = d.n_dop, T = d.tdof, C = d.n_chan, S = d.n_steering;
+  const int P = d.n_pulses - c.TW + 1;   // window length (the sub-window's)
   std::vector<double> h(P);
   for (int p = 0; p < P; ++p)
     h[p] = (P == 1) ? 1.0 : 0.5 - 0.5 * std::cos(2.0 * kPi * p / (double)(P - 1));
@@ -83,10 +87,11 @@ void make_tables(Cpi& c) {
     c.tw[2 * m] = (float)std::cos(a);
     c.tw[2 * m + 1] = (float)std::sin(a);
   }
-  // temporal part: the window's response at the T bin offsets around the bin
+  // temporal part: the window's response at the T bin offsets around the bin;
+  // staggered sub-windows all answer a bin-centre target with sum h' (offset 0)
   std::vector<double> gr(T), gi(T);
   for (int t = 0; t < T; ++t) {
-    const long long m = t - T / 2;
+    const long long m = c.TW > 1 ? 0 : t - T / 2;
     double sr = 0, si = 0;
     for (int p = 0; p < P; ++p) {
       long long n = (m * p) % K;
@@ -211,7 +216,7 @@ stap_status do_doppler(stap_plan p, const Cpi& c, const void* cube, void* dop, c
   const stap_dims& d = c.d;
   return check_launch(stap::launch_doppler(
       static_cast<const float2*>(cube), static_cast<float2*>(dop), p->at<const float>(c.win_off),
-      p->at<const float2>(c.tw_off), d.n_chan, d.n_pulses, d.n_dop, nr < 0 ? d.n_range : nr,
+      p->at<const float2>(c.tw_off), d.n_chan, c.TW, d.n_pulses, d.n_dop, nr < 0 ? d.n_range : nr,
       d.n_range, st, c.tune));
 }
 
@@ -223,12 +228,12 @@ stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov,
   // (more accurate) FP32 kernel as the faster one
   if (p->opt.precision == STAP_PREC_TF32X3 && c.tune.cov_kind != 1)
     return check_launch(stap::launch_covariance_tc(static_cast<const float2*>(dop),
-                                                   static_cast<double2*>(cov), d.n_chan, d.n_dop,
-                                                   R, d.n_range, d.tdof, d.training_block,
+                                                   static_cast<double2*>(cov), c.Cd, d.n_dop,
+                                                   R, d.n_range, c.Td, d.training_block,
                                                    p->status(), st));
   return check_launch(stap::launch_covariance_fp32(static_cast<const float2*>(dop),
-                                                   static_cast<double2*>(cov), d.n_chan, d.n_dop,
-                                                   R, d.n_range, d.tdof, d.training_block, st,
+                                                   static_cast<double2*>(cov), c.Cd, d.n_dop,
+                                                   R, d.n_range, c.Td, d.training_block, st,
                                                    c.tune));
 }
 
@@ -253,12 +258,12 @@ stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts
   if (p->opt.precision == STAP_PREC_TF32X3 && stap::apply_tc_supported(d.training_block, d.n_steering) &&
       (c.tune.apply_kind == 0 || c.tune.apply_kind == 3))
     return check_launch(stap::launch_apply_tc(static_cast<const float2*>(dop),
-                                              static_cast<const float2*>(wts), out, d.n_chan,
-                                              d.n_dop, R, d.n_range, d.tdof, d.training_block,
+                                              static_cast<const float2*>(wts), out, c.Cd,
+                                              d.n_dop, R, d.n_range, c.Td, d.training_block,
                                               d.n_steering, p->status(), st));
   return check_launch(stap::launch_apply(static_cast<const float2*>(dop),
-                                         static_cast<const float2*>(wts), out, d.n_chan, d.n_dop,
-                                         R, d.n_range, d.tdof, d.training_block, d.n_steering, st,
+                                         static_cast<const float2*>(wts), out, c.Cd, d.n_dop,
+                                         R, d.n_range, c.Td, d.training_block, d.n_steering, st,
                                          c.tune));
 }
 
@@ -454,6 +459,7 @@ void stap_options_default(stap_options* opt) {
   opt->precision = STAP_PREC_FP32;
   opt->solver = STAP_SOLVE_FP64;
   opt->training = STAP_TRAIN_OWN_BLOCK;
+  opt->snapshots = STAP_SNAP_ADJACENT_BINS;
 }
 
 int32_t stap_abi_version(void) { return STAP_ABI_VERSION; }
@@ -487,6 +493,9 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
   if (o.solver != STAP_SOLVE_FP64 && o.solver != STAP_SOLVE_MIXED_IR) return STAP_ERR_UNSUPPORTED;
   if (o.training != STAP_TRAIN_OWN_BLOCK && o.training != STAP_TRAIN_NEIGHBOURS)
     return STAP_ERR_INVALID_ARG;
+  if (o.snapshots != STAP_SNAP_ADJACENT_BINS && o.snapshots != STAP_SNAP_PRI_STAGGERED)
+    return STAP_ERR_INVALID_ARG;
+  const bool stag = o.snapshots == STAP_SNAP_PRI_STAGGERED;
   for (int i = 0; i < n_cpi; ++i) {
     stap_status st = validate(dims[i]);
     if (st != STAP_OK) return st;
@@ -494,6 +503,7 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
       return STAP_ERR_UNSUPPORTED;
     if (o.training == STAP_TRAIN_NEIGHBOURS && dims[i].n_range / dims[i].training_block < 2)
       return STAP_ERR_SHAPE;
+    if (stag && dims[i].tdof > dims[i].n_pulses) return STAP_ERR_SHAPE;   // sub-windows of >= 1 pulse
   }
   stap_plan p = new (std::nothrow) stap_plan_s;
   if (!p) return STAP_ERR_INVALID_ARG;
@@ -506,6 +516,9 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
     Cpi& c = p->cpis[i];
     c.d = dims[i];
     c.D = c.d.n_chan * c.d.tdof;
+    c.TW = stag ? c.d.tdof : 1;
+    c.Cd = stag ? c.D : c.d.n_chan;
+    c.Td = stag ? 1 : c.d.tdof;
     c.NB = c.d.n_range / c.d.training_block;
     make_tables(c);
     c.win_off = off;

@@ -51,8 +51,11 @@ bool mir_supported(int D);
 
 // Hann-windowed DFT over pulses via a two-pass in-register FFT.
 // cube [C][P][R] c64 -> dop [C][K][R] c64; win[P] float; tw[K] = exp(-2 pi i m/K).
+// TW = 1: the plain transform (win: Hann of length P); TW > 1: PRI-staggered
+// sub-windows (win: Hann of length P - TW + 1), dop rows t*C + c.
 cudaError_t launch_doppler(const float2* cube, float2* dop, const float* win, const float2* tw,
-                           int C, int P, int K, int R, int ldr, cudaStream_t s, const Tune& t = Tune());
+                           int C, int TW, int P, int K, int R, int ldr, cudaStream_t s,
+                           const Tune& t = Tune());
 
 // Covariance per (k, block) from the Doppler cube, accumulated error-free in
 // FP32 pairs; written as FP64 complex [K][NB][D][D] (full Hermitian).

@@ -33,6 +33,8 @@ STAP_SOLVE_FP64 = 0
 STAP_SOLVE_MIXED_IR = 1
 STAP_TRAIN_OWN_BLOCK = 0
 STAP_TRAIN_NEIGHBOURS = 1
+STAP_SNAP_ADJACENT_BINS = 0
+STAP_SNAP_PRI_STAGGERED = 1
 
 # every symbol include/stap.h declares
 EXPORTED = (
@@ -64,7 +66,7 @@ class stap_dims(ctypes.Structure):
 class stap_options(ctypes.Structure):
     _fields_ = [("load_factor", ctypes.c_double), ("refine_steps", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
-                ("training", ctypes.c_int32)]
+                ("training", ctypes.c_int32), ("snapshots", ctypes.c_int32)]
 
 
 _lib = None
@@ -307,15 +309,15 @@ class Plan:
     def __init__(self, dims, load_factor: float = 1e-3, refine_steps: int = 1,
                  precision: int = STAP_PREC_FP32, device=None, steps_only: bool = False,
                  max_workspace_bytes: Optional[int] = None, solver: int = STAP_SOLVE_FP64,
-                 training: int = STAP_TRAIN_OWN_BLOCK):
+                 training: int = STAP_TRAIN_OWN_BLOCK, snapshots: int = STAP_SNAP_ADJACENT_BINS):
         dl = list(dims) if isinstance(dims, (list, tuple)) and dims and not isinstance(dims[0], int) \
             else [dims]
         self.dims = [_dims(d) for d in dl]
         self.device = torch.device(device) if device is not None else torch.device("cuda")
         opts = stap_options(float(load_factor), int(refine_steps), int(precision), int(solver),
-                            int(training))
+                            int(training), int(snapshots))
         self.precision, self.refine_steps, self.solver = int(precision), int(refine_steps), int(solver)
-        self.training = int(training)
+        self.training, self.snapshots = int(training), int(snapshots)
         with torch.cuda.device(self.device):
             self.handle, _ = stap_plan_create(self.dims, opts)
             self.step_bytes, self.run_bytes = stap_plan_workspace_sizes(self.handle)
@@ -346,7 +348,8 @@ class Plan:
         C, P, K, R, T, B, S = (d.n_chan, d.n_pulses, d.n_dop, d.n_range, d.tdof,
                                d.training_block, d.n_steering)
         D, NB = C * T, R // B
-        return dict(cube=(C, P, R), dop=(C, K, R), cov=(K, NB, D, D), wts=(K, NB, S, D),
+        rows = D if self.snapshots == STAP_SNAP_PRI_STAGGERED else C   # Doppler rows
+        return dict(cube=(C, P, R), dop=(rows, K, R), cov=(K, NB, D, D), wts=(K, NB, S, D),
                     out=(S, K, R))
 
     def _sync_stream(self):
@@ -422,6 +425,8 @@ class Plan:
         key = "C%d P%d K%d T%d B%d S%d prec%d ref%d solve%d train%d" % (
             d.n_chan, d.n_pulses, d.n_dop, d.tdof, d.training_block, d.n_steering, self.precision,
             self.refine_steps, self.solver, self.training)
+        if self.snapshots:
+            key += " snap%d" % self.snapshots
         # a one-CPI plan also tunes its range slabs, which depend on R
         return key + (" R%d" % d.n_range if len(self.dims) == 1 else " batch")
 

@@ -27,7 +27,7 @@ def test_library_loads_and_exports_every_declared_symbol():
     for name in declared:
         assert hasattr(L, name), f"{name} declared in stap.h but not exported"
     assert set(declared) == set(stap.EXPORTED)
-    assert stap.stap_abi_version() == 3
+    assert stap.stap_abi_version() == 4
 
 
 def _create(dims, opts=None):
@@ -111,6 +111,32 @@ def test_training_workspace_holds_the_training_matrices():
     _, h0, ws0 = _create(GOOD)
     _, h1, ws1 = _create(GOOD, stap.stap_options(1e-3, 1, 0, 0, 1))
     assert ws1 - ws0 >= K * NB * D * D * 16 and ws1 - ws0 < K * NB * D * D * 16 + 512
+    stap.stap_plan_destroy(h0)
+    stap.stap_plan_destroy(h1)
+
+
+def test_snapshot_option_values_and_pulse_limit():
+    o = stap.stap_options_default()
+    assert o.snapshots == stap.STAP_SNAP_ADJACENT_BINS
+    for snaps, dims, code in [(1, GOOD, stap.STAP_OK),
+                              (2, GOOD, stap.STAP_ERR_INVALID_ARG),
+                              (-1, GOOD, stap.STAP_ERR_INVALID_ARG),
+                              (1, (4, 2, 32, 64, 3, 16, 4), stap.STAP_ERR_SHAPE),   # T > P
+                              (0, (4, 2, 32, 64, 3, 16, 4), stap.STAP_OK),          # adjacent bins
+                              (1, (4, 3, 32, 64, 3, 16, 4), stap.STAP_OK)]:         # one-pulse sub-windows
+        got, h, _ = _create(dims, stap.stap_options(1e-3, 1, 0, 0, 0, snaps))
+        assert got == code, (snaps, dims)
+        if h.value:
+            stap.stap_plan_destroy(h)
+
+
+def test_staggered_workspace_holds_the_wider_doppler_cube():
+    """PRI-staggered snapshots: the Doppler intermediate has C*T rows, not C."""
+    C, P, K, R, T, B, S = GOOD
+    _, h0, ws0 = _create(GOOD)
+    _, h1, ws1 = _create(GOOD, stap.stap_options(1e-3, 1, 0, 0, 0, stap.STAP_SNAP_PRI_STAGGERED))
+    extra = (T - 1) * C * K * R * 8
+    assert abs((ws1 - ws0) - extra) <= 256
     stap.stap_plan_destroy(h0)
     stap.stap_plan_destroy(h1)
 
