@@ -242,6 +242,32 @@ stap_status stap_run_cpi(stap_plan plan, const void* const* cubes, float* const*
  * i.e. stap_run_cpi runs the whole batch as one wave. */
 stap_status stap_plan_batch_bytes(stap_plan plan, size_t* all_concurrent_bytes);
 
+/* Workspace size stap_run_stream needs: run_bytes plus two device cubes and
+ * two device outputs.  Single-CPI plans only (STAP_ERR_INVALID_ARG
+ * otherwise).  Host-only. */
+stap_status stap_plan_stream_bytes(stap_plan plan, size_t* bytes);
+
+/* Stream n CPIs of a single-CPI plan's shape from host memory through the
+ * whole chain (a runtime feature with no counterpart in the paper, whose GPU
+ * tasks copy each cube in and each result back in turn): for i = 0 .. n-1,
+ * host_cubes[i] (HOST c64 [C][P][R]) is copied to one of two device cube
+ * buffers, stap_run_cpi's chain runs on it, and its output is copied to
+ * host_outs[i] (HOST float [S][K][R]).  The copies run on two internal
+ * streams, so that the copy-in of CPI i+1 and the copy-out of CPI i-1
+ * overlap the chain of CPI i; with page-locked host buffers (cudaHostAlloc,
+ * torch pin_memory) a long stream then runs at the rate of the slowest of the
+ * three.  Pageable buffers also work, with less overlap.
+ *
+ * host_cubes, host_outs: HOST arrays of n host pointers; every buffer must
+ * stay valid, and the cubes unmodified, until the plan's stream has passed
+ * the call: the plan's stream waits for the last copy-out, so synchronising it
+ * makes every host_outs[i] ready.  Needs a workspace of at least
+ * stap_plan_stream_bytes (else STAP_ERR_NO_WORKSPACE).  n == 0 queues nothing.
+ * Returns once everything is queued.  The first call creates the two copy
+ * streams and their events. */
+stap_status stap_run_stream(stap_plan plan, int64_t n, const void* const* host_cubes,
+                            float* const* host_outs);
+
 /* Size of the device scratch array that libstap itself holds for
  * stap_run_cpi_noalloc: 16 MiB on every GPU that loads the library, kept
  * until the process exits. */

@@ -144,6 +144,11 @@ struct stap_plan_s {
   char* ws = nullptr;
   size_t ws_bytes = 0;
   size_t step_bytes = 0, run_bytes = 0, batch_bytes = 0;
+  // streamed runs (stap_run_stream): two device cubes and two device outputs
+  // beyond run_bytes
+  size_t stream_bytes = 0, cube_bytes = 0, out_bytes = 0;
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_in[2] = {}, ev_done[2] = {}, ev_out[2] = {};
   size_t dop_off = 0, cov_off = 0, wts_off = 0;   // run intermediates (sized for the largest CPI)
   size_t ctr_off = 0;                             // neighbour-training matrices (STAP_TRAIN_NEIGHBOURS)
   bool tables_ready = false;
@@ -555,6 +560,12 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
   size_t all = p->step_bytes;
   for (const Cpi& c : p->cpis) all += inter_bytes(o, c);
   p->batch_bytes = all > p->run_bytes ? all : p->run_bytes;
+  if (n_cpi == 1) {
+    const stap_dims& d = dims[0];
+    p->cube_bytes = (size_t)d.n_chan * d.n_pulses * d.n_range * 8;
+    p->out_bytes = (size_t)d.n_steering * d.n_dop * d.n_range * 4;
+    p->stream_bytes = p->run_bytes + 2 * align_up(p->cube_bytes) + 2 * align_up(p->out_bytes);
+  }
   *out = p;
   if (workspace_bytes) *workspace_bytes = p->run_bytes;
   return STAP_OK;
@@ -604,6 +615,17 @@ stap_status stap_plan_set_steering(stap_plan p, int32_t cpi, const double* host_
 stap_status stap_plan_destroy(stap_plan p) {
   if (!p) return STAP_ERR_INVALID_ARG;
   drop_graph(p);
+  if (p->ev_start) {
+    for (cudaStream_t s : {p->h2d, p->d2h})
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+    for (int j = 0; j < 2; ++j)
+      for (cudaEvent_t e : {p->ev_in[j], p->ev_done[j], p->ev_out[j]})
+        if (e) cudaEventDestroy(e);
+    cudaEventDestroy(p->ev_start);
+  }
   if (p->fork_ev) {
     for (int i = 0; i < stap_plan_s::kSideStreams; ++i) {
       if (p->side[i]) {
@@ -693,6 +715,83 @@ stap_status stap_plan_batch_bytes(stap_plan p, size_t* all_concurrent_bytes) {
   if (!p || !all_concurrent_bytes) return STAP_ERR_INVALID_ARG;
   *all_concurrent_bytes = p->batch_bytes;
   return STAP_OK;
+}
+
+stap_status stap_plan_stream_bytes(stap_plan p, size_t* bytes) {
+  if (!p || !bytes) return STAP_ERR_INVALID_ARG;
+  if (p->cpis.size() != 1) return STAP_ERR_INVALID_ARG;
+  *bytes = p->stream_bytes;
+  return STAP_OK;
+}
+
+// CPI i: copy-in on h2d into device cube j = i % 2, the chain on the plan's
+// stream into device output j, copy-out on d2h.  Buffer j is rewritten by CPI
+// i + 2 only after CPI i's chain has read it (ev_done) and its output has been
+// copied out (ev_out); a wait takes the event's latest record at enqueue time,
+// which is CPI i's.
+stap_status stap_run_stream(stap_plan p, int64_t n, const void* const* host_cubes,
+                            float* const* host_outs) {
+  if (!p || n < 0 || (n > 0 && (!host_cubes || !host_outs))) return STAP_ERR_INVALID_ARG;
+  if (p->cpis.size() != 1) return STAP_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i)
+    if (!host_cubes[i] || !host_outs[i]) return STAP_ERR_INVALID_ARG;
+  stap_status st = ready(p, p->stream_bytes);
+  if (st != STAP_OK || n == 0) return st;
+  if (!p->ev_start) {
+    if (cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming) != cudaSuccess)
+      return STAP_ERR_CUDA;
+    for (int j = 0; j < 2; ++j)
+      if (cudaEventCreateWithFlags(&p->ev_in[j], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p->ev_done[j], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p->ev_out[j], cudaEventDisableTiming) != cudaSuccess)
+        return STAP_ERR_CUDA;
+  }
+  char* cube_buf[2];
+  float* out_buf[2];
+  size_t off = p->run_bytes;
+  for (int j = 0; j < 2; ++j) {
+    cube_buf[j] = p->ws + off;
+    off += align_up(p->cube_bytes);
+  }
+  for (int j = 0; j < 2; ++j) {
+    out_buf[j] = reinterpret_cast<float*>(p->ws + off);
+    off += align_up(p->out_bytes);
+  }
+  // both copy streams start after the work already queued on the plan's stream
+  if (cudaEventRecord(p->ev_start, p->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(p->h2d, p->ev_start, 0) != cudaSuccess ||
+      cudaStreamWaitEvent(p->d2h, p->ev_start, 0) != cudaSuccess)
+    return STAP_ERR_CUDA;
+  int64_t i = 0;
+  for (; i < n && st == STAP_OK; ++i) {
+    const int j = (int)(i & 1);
+    if (i >= 2 && cudaStreamWaitEvent(p->h2d, p->ev_done[j], 0) != cudaSuccess) { st = STAP_ERR_CUDA; break; }
+    if (cudaMemcpyAsync(cube_buf[j], host_cubes[i], p->cube_bytes, cudaMemcpyHostToDevice, p->h2d) !=
+            cudaSuccess ||
+        cudaEventRecord(p->ev_in[j], p->h2d) != cudaSuccess ||
+        cudaStreamWaitEvent(p->stream, p->ev_in[j], 0) != cudaSuccess ||
+        (i >= 2 && cudaStreamWaitEvent(p->stream, p->ev_out[j], 0) != cudaSuccess)) {
+      st = STAP_ERR_CUDA;
+      break;
+    }
+    st = run_single(p, cube_buf[j], out_buf[j]);
+    if (st != STAP_OK) break;
+    if (cudaEventRecord(p->ev_done[j], p->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(p->d2h, p->ev_done[j], 0) != cudaSuccess ||
+        cudaMemcpyAsync(host_outs[i], out_buf[j], p->out_bytes, cudaMemcpyDeviceToHost, p->d2h) !=
+            cudaSuccess ||
+        cudaEventRecord(p->ev_out[j], p->d2h) != cudaSuccess)
+      st = STAP_ERR_CUDA;
+  }
+  // the plan's stream passes the call only after every copy it queued
+  if (cudaEventRecord(p->ev_start, p->h2d) != cudaSuccess ||
+      cudaStreamWaitEvent(p->stream, p->ev_start, 0) != cudaSuccess ||
+      cudaEventRecord(p->ev_start, p->d2h) != cudaSuccess ||
+      cudaStreamWaitEvent(p->stream, p->ev_start, 0) != cudaSuccess)
+    st = STAP_ERR_CUDA;
+  return st;
 }
 
 stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* const* outs,

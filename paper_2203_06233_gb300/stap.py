@@ -43,7 +43,7 @@ EXPORTED = (
     "stap_plan_destroy", "stap_doppler", "stap_covariance", "stap_solve_weights", "stap_apply",
     "stap_run_cpi", "stap_get_status", "stap_status_string", "stap_abi_version",
     "stap_run_cpi_noalloc", "stap_plan_batch_bytes", "stap_plan_autotune", "stap_plan_get_tuning",
-    "stap_plan_set_tuning", "stap_train_neighbours",
+    "stap_plan_set_tuning", "stap_train_neighbours", "stap_plan_stream_bytes", "stap_run_stream",
 )
 
 STAP_TUNING_LEN = 9
@@ -105,6 +105,8 @@ def lib():
             L.stap_status_string.restype = ctypes.c_char_p
             L.stap_abi_version.argtypes = []
             L.stap_plan_batch_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+            L.stap_plan_stream_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+            L.stap_run_stream.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(vp), ctypes.POINTER(vp)]
             L.stap_plan_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32]
             L.stap_plan_get_tuning.argtypes = [vp, i32, ctypes.POINTER(i32)]
             L.stap_plan_set_tuning.argtypes = [vp, i32, ctypes.POINTER(i32)]
@@ -155,6 +157,18 @@ def _dev(t: torch.Tensor, dtype, shape, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _host(t: torch.Tensor, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise TypeError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
 # ------------------------------------------------------------- C entry points --
 
 def stap_options_default() -> stap_options:
@@ -184,6 +198,12 @@ def stap_plan_workspace_sizes(plan):
 def stap_plan_batch_bytes(plan) -> int:
     a = ctypes.c_size_t()
     _check(lib().stap_plan_batch_bytes(plan, ctypes.byref(a)), "stap_plan_batch_bytes")
+    return a.value
+
+
+def stap_plan_stream_bytes(plan) -> int:
+    a = ctypes.c_size_t()
+    _check(lib().stap_plan_stream_bytes(plan, ctypes.byref(a)), "stap_plan_stream_bytes")
     return a.value
 
 
@@ -240,6 +260,13 @@ def stap_run_cpi(plan, cubes: Sequence[torch.Tensor], outs: Sequence[torch.Tenso
     ca = (ctypes.c_void_p * n)(*[t.data_ptr() for t in cubes])
     oa = (ctypes.c_void_p * n)(*[t.data_ptr() for t in outs])
     _check(lib().stap_run_cpi(plan, ca, oa), "stap_run_cpi")
+
+
+def stap_run_stream(plan, host_cubes: Sequence[torch.Tensor], host_outs: Sequence[torch.Tensor]):
+    n = len(host_cubes)
+    ca = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in host_cubes])
+    oa = (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in host_outs])
+    _check(lib().stap_run_stream(plan, n, ca, oa), "stap_run_stream")
 
 
 def stap_get_status(plan):
@@ -419,6 +446,37 @@ class Plan:
         self._sync_stream()
         stap_run_cpi(self.handle, cubes, outs)
         return outs[0] if single else outs
+
+    def run_stream(self, host_cubes, host_outs=None) -> List[torch.Tensor]:
+        """Stream host cubes through the whole chain (stap_run_stream): the
+        copy-in of cube i+1 and the copy-out of result i-1 overlap the chain of
+        cube i.  host_cubes: CPU complex64 tensors [C][P][R] (page-locked, e.g.
+        ``pin_memory()``, for the copies to overlap); host_outs: CPU float32
+        [S][K][R] (allocated page-locked when None).  Grows the workspace to
+        stap_plan_stream_bytes on first use.  Returns once the work is queued on
+        the current stream; synchronise it before reading host_outs or
+        modifying host_cubes."""
+        if len(self.dims) != 1:
+            raise ValueError("run_stream needs a single-CPI plan")
+        sh = self.shapes()
+        host_cubes = list(host_cubes)
+        if host_outs is None:
+            host_outs = [torch.empty(sh["out"], dtype=torch.float32).pin_memory() for _ in host_cubes]
+        host_outs = list(host_outs)
+        if len(host_outs) != len(host_cubes):
+            raise ValueError("host_outs and host_cubes differ in length")
+        for i, (c, o) in enumerate(zip(host_cubes, host_outs)):
+            _host(c, torch.complex64, sh["cube"], f"host_cubes[{i}]")
+            _host(o, torch.float32, sh["out"], f"host_outs[{i}]")
+        need = stap_plan_stream_bytes(self.handle)
+        if self.workspace.numel() < need:
+            with torch.cuda.device(self.device):
+                torch.cuda.synchronize(self.device)      # nothing still uses the old workspace
+                self.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+                stap_plan_set_workspace(self.handle, self.workspace)
+        self._sync_stream()
+        stap_run_stream(self.handle, host_cubes, host_outs)
+        return host_outs
 
     def _tune_key(self, i: int) -> str:
         d = self.dims[i]

@@ -141,6 +141,33 @@ def test_staggered_workspace_holds_the_wider_doppler_cube():
     stap.stap_plan_destroy(h1)
 
 
+def test_stream_workspace_and_arguments_fail_before_cuda():
+    L = stap.lib()
+    C, P, K, R, T, B, S = GOOD
+    code, h, ws = _create(GOOD)
+    assert code == 0
+    sb = ctypes.c_size_t()
+    assert L.stap_plan_stream_bytes(h, ctypes.byref(sb)) == stap.STAP_OK
+    cube_b, out_b = C * P * R * 8, S * K * R * 4
+    assert sb.value >= ws + 2 * cube_b + 2 * out_b and sb.value <= ws + 2 * cube_b + 2 * out_b + 1024
+    assert L.stap_plan_stream_bytes(h, None) == stap.STAP_ERR_INVALID_ARG
+    fake = ctypes.c_void_p(0x10000)                           # never dereferenced
+    arr = (ctypes.c_void_p * 1)(fake)
+    nul = (ctypes.c_void_p * 1)(None)
+    assert L.stap_run_stream(h, -1, arr, arr) == stap.STAP_ERR_INVALID_ARG
+    assert L.stap_run_stream(h, 1, None, arr) == stap.STAP_ERR_INVALID_ARG
+    assert L.stap_run_stream(h, 1, arr, nul) == stap.STAP_ERR_INVALID_ARG
+    assert L.stap_run_stream(h, 1, arr, arr) == stap.STAP_ERR_NO_WORKSPACE
+    stap.stap_plan_destroy(h)
+    # a batch plan has no streamed form
+    dims2 = (stap.stap_dims * 2)(stap.stap_dims(*GOOD), stap.stap_dims(*GOOD))
+    h2 = ctypes.c_void_p()
+    assert L.stap_plan_create(dims2, 2, None, None, ctypes.byref(h2), None) == stap.STAP_OK
+    assert L.stap_plan_stream_bytes(h2, ctypes.byref(sb)) == stap.STAP_ERR_INVALID_ARG
+    assert L.stap_run_stream(h2, 1, arr, arr) == stap.STAP_ERR_INVALID_ARG
+    stap.stap_plan_destroy(h2)
+
+
 def test_options_default_and_mixed_refinement_shape_limits():
     o = stap.stap_options_default()
     assert o.solver == stap.STAP_SOLVE_FP64
