@@ -15,6 +15,9 @@ remaining steps are the standard post-Doppler STAP reading):
    P - T + 1 pulses, each transformed with its pulses' CPI phase; the result
    is a Doppler cube of C*T channels (``staggered_dims``) with one bin per
    snapshot, and ``default_steering_staggered`` its steering.
+   ``reduce_channels`` (a front end beyond the paper): N element channels
+   combined into C channels by a matrix W[C][N] (``subarray_weights``: C
+   contiguous subarrays), with ``reduced_steering`` the matching steering.
 2. ``snapshot``    D = C*T entries from T adjacent bins, channel fastest.
 3. ``covariance``  R = (1/B) sum x x^H per (Doppler bin, range block).
    ``train_neighbours`` (an option beyond the paper): block b trained on the
@@ -97,11 +100,15 @@ def lib():
         L.oracle_doppler_staggered.argtypes = [D, P, i32, i32, P]
         L.oracle_default_steering_staggered.argtypes = [D, P]
         L.oracle_run_staggered.argtypes = [D, P, P, ctypes.c_double, i32, i32, P, P, P, P, P]
+        L.oracle_reduce_channels.argtypes = [i32, i32, i32, i32, P, P, P]
+        L.oracle_subarray_weights.argtypes = [i32, i32, P]
+        L.oracle_reduced_steering.argtypes = [D, i32, P, P]
         for f in ("oracle_doppler_window", "oracle_doppler", "oracle_snapshot", "oracle_covariance",
                   "oracle_cholesky", "oracle_cholesky_solve", "oracle_default_steering",
                   "oracle_weights", "oracle_apply", "oracle_run", "oracle_train_neighbours",
                   "oracle_run_neighbours", "oracle_doppler_staggered",
-                  "oracle_default_steering_staggered", "oracle_run_staggered"):
+                  "oracle_default_steering_staggered", "oracle_run_staggered",
+                  "oracle_reduce_channels", "oracle_subarray_weights", "oracle_reduced_steering"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -228,6 +235,35 @@ def train_neighbours(d: Dims, cov) -> np.ndarray:
     _check(lib().oracle_train_neighbours(ctypes.byref(d.c()), _ptr(cov), nb, 0, nb, _ptr(out)),
            "train_neighbours")
     return out
+
+
+def reduce_channels(W, x) -> np.ndarray:
+    """y[C][P][R] = sum_n conj(W[c][n]) x[n][P][R]: the reduced-DOF front end
+    (N element channels of x combined into C channels by W[C][N])."""
+    W, x = _c128(W), _c128(x)
+    (C, N), (N2, P, R) = W.shape, x.shape
+    assert N == N2
+    y = np.empty((C, P, R), np.complex128)
+    _check(lib().oracle_reduce_channels(N, C, P, R, _ptr(W), _ptr(x), _ptr(y)), "reduce_channels")
+    return y
+
+
+def subarray_weights(N: int, C: int) -> np.ndarray:
+    """W[C][N] summing C contiguous subarrays of N / C elements."""
+    W = np.empty((C, N), np.complex128)
+    _check(lib().oracle_subarray_weights(N, C, _ptr(W)), "subarray_weights")
+    return W
+
+
+def reduced_steering(d: Dims, W) -> np.ndarray:
+    """steer[S][D] of the channels reduced by W[C][N] (d.n_chan = C):
+    v_s[t*C + c] = g_t sum_n conj(W[c][n]) exp(j 2 pi f_s n)."""
+    W = _c128(W)
+    assert W.shape[0] == d.n_chan
+    st = np.empty((d.n_steering, d.D), np.complex128)
+    _check(lib().oracle_reduced_steering(ctypes.byref(d.c()), W.shape[1], _ptr(W), _ptr(st)),
+           "reduced_steering")
+    return st
 
 
 def staggered_dims(d: Dims) -> Dims:

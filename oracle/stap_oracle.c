@@ -30,6 +30,9 @@
  *   7. w_s = u_s / sqrt(Re v_s^H u_s)      (unit noise gain / AMF weights)
  *   8. P[s][k][r] = |w_{k,b(r),s}^H x_{k,r}|^2
  *
+ *   Reduced-DOF front end (beyond the paper; oracle_reduce_channels): N
+ *   element channels combined into the C channels of the cube by a matrix W.
+ *
  *   PRI-staggered snapshots (an option beyond the paper; oracle_run_staggered):
  *   T sub-windows of P - T + 1 pulses replace the T adjacent bins (see the
  *   block comment above oracle_doppler_staggered).
@@ -254,17 +257,12 @@ static cplx spatial_phase(int s, int S, int c) {
 }
 
 /* Default steering table steer[S][D] (see the header comment). */
-int oracle_default_steering(const oracle_dims* d, cplx* steer) {
-  if (!dims_ok(d) || !steer) return ORACLE_BAD_ARGS;
-  const int C = d->n_chan, P = d->n_pulses, K = d->n_dop, T = d->tdof, S = d->n_steering;
-  const int D = C * T;
+/* Temporal part g[T] of the default steering: the window's response at the
+ * T bin offsets m_t = t - floor(T/2), g_t = sum_p h[p] exp(-j 2 pi m_t p / K). */
+static int temporal_response(const oracle_dims* d, cplx* g) {
+  const int P = d->n_pulses, K = d->n_dop, T = d->tdof;
   double* h = (double*)malloc(sizeof(double) * (size_t)P);
-  cplx* g = (cplx*)malloc(sizeof(cplx) * (size_t)T);
-  if (!h || !g) {
-    free(h);
-    free(g);
-    return ORACLE_NO_MEMORY;
-  }
+  if (!h) return ORACLE_NO_MEMORY;
   oracle_hann(P, h);
   for (int t = 0; t < T; ++t) {
     int m = t - T / 2;
@@ -272,10 +270,23 @@ int oracle_default_steering(const oracle_dims* d, cplx* steer) {
     for (int p = 0; p < P; ++p) acc += h[p] * twiddle((int64_t)m * p, K);
     g[t] = acc;
   }
+  free(h);
+  return ORACLE_OK;
+}
+
+int oracle_default_steering(const oracle_dims* d, cplx* steer) {
+  if (!dims_ok(d) || !steer) return ORACLE_BAD_ARGS;
+  const int C = d->n_chan, T = d->tdof, S = d->n_steering;
+  const int D = C * T;
+  cplx* g = (cplx*)malloc(sizeof(cplx) * (size_t)T);
+  if (!g) return ORACLE_NO_MEMORY;
+  if (temporal_response(d, g) != ORACLE_OK) {
+    free(g);
+    return ORACLE_NO_MEMORY;
+  }
   for (int s = 0; s < S; ++s)
     for (int t = 0; t < T; ++t)
       for (int c = 0; c < C; ++c) steer[(size_t)s * D + t * C + c] = g[t] * spatial_phase(s, S, c);
-  free(h);
   free(g);
   return ORACLE_OK;
 }
@@ -599,4 +610,69 @@ done:
   free(wts_t);
   free(steer_t);
   return rc;
+}
+
+/* ---------------------------------------------------------------------------
+ * Reduced-DOF front end (a step beyond the paper, whose 1000-channel cubes
+ * would make D = 1000 T): the N element channels of an element cube
+ * x[N][P][R] (a half-wavelength line array, element n at phase
+ * exp(j 2 pi f n) for spatial frequency f) are combined into the C channels
+ * of the STAP cube by a matrix W[C][N]:
+ *   y[c][p][r] = sum_{n<N} conj(W[c][n]) x[n][p][r].
+ * The default W sums C contiguous subarrays of N / C elements (N a multiple of
+ * C).  A plane wave at spatial frequency f_s reaches channel c with gain
+ *   b_s[c] = sum_n conj(W[c][n]) exp(j 2 pi f_s n),
+ * so the steering of the reduced snapshots is v_s[t*C + c] = g_t b_s[c]
+ * (g as in the default steering); steps 1-8 then run unchanged on y.
+ */
+
+/* y[C][P][R] from x[N][P][R] and W[C][N]. */
+int oracle_reduce_channels(int32_t N, int32_t C, int32_t P, int32_t R, const cplx* W,
+                           const cplx* x, cplx* y) {
+  if (N < 1 || C < 1 || P < 1 || R < 1 || !W || !x || !y) return ORACLE_BAD_ARGS;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int c = 0; c < C; ++c)
+    for (int p = 0; p < P; ++p)
+      for (int r = 0; r < R; ++r) {
+        cplx acc = 0.0;
+        for (int n = 0; n < N; ++n)
+          acc += conj(W[(size_t)c * N + n]) * x[((size_t)n * P + p) * R + r];
+        y[((size_t)c * P + p) * R + r] = acc;
+      }
+  return ORACLE_OK;
+}
+
+/* W[C][N] of C contiguous subarrays: 1 for c N/C <= n < (c+1) N/C, else 0. */
+int oracle_subarray_weights(int32_t N, int32_t C, cplx* W) {
+  if (N < 1 || C < 1 || N % C != 0 || !W) return ORACLE_BAD_ARGS;
+  const int M = N / C;
+  for (int c = 0; c < C; ++c)
+    for (int n = 0; n < N; ++n) W[(size_t)c * N + n] = (n / M == c) ? 1.0 : 0.0;
+  return ORACLE_OK;
+}
+
+/* Steering steer[S][D] of snapshots of the reduced channels (d->n_chan = C). */
+int oracle_reduced_steering(const oracle_dims* d, int32_t N, const cplx* W, cplx* steer) {
+  if (!dims_ok(d) || N < 1 || !W || !steer) return ORACLE_BAD_ARGS;
+  const int C = d->n_chan, T = d->tdof, S = d->n_steering;
+  const int D = C * T;
+  cplx* g = (cplx*)malloc(sizeof(cplx) * (size_t)T);
+  cplx* b = (cplx*)malloc(sizeof(cplx) * (size_t)C);
+  if (!g || !b || temporal_response(d, g) != ORACLE_OK) {
+    free(g);
+    free(b);
+    return ORACLE_NO_MEMORY;
+  }
+  for (int s = 0; s < S; ++s) {
+    for (int c = 0; c < C; ++c) {
+      cplx acc = 0.0;
+      for (int n = 0; n < N; ++n) acc += conj(W[(size_t)c * N + n]) * spatial_phase(s, S, n);
+      b[c] = acc;
+    }
+    for (int t = 0; t < T; ++t)
+      for (int c = 0; c < C; ++c) steer[(size_t)s * D + t * C + c] = g[t] * b[c];
+  }
+  free(g);
+  free(b);
+  return ORACLE_OK;
 }

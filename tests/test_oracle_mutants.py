@@ -42,6 +42,13 @@ MUTANTS = {
                                 "for (int p = 0; p < Ps; ++p) G += 1.0;"),
     "staggered_snapshot_order": ("dop[(((size_t)t * C + c) * K + k) * nr + rr] = acc;",
                                  "dop[(((size_t)c * T + t) * K + k) * nr + rr] = acc;"),
+    "front_end_conjugate": ("acc += conj(W[(size_t)c * N + n]) * x[((size_t)n * P + p) * R + r];",
+                            "acc += W[(size_t)c * N + n] * x[((size_t)n * P + p) * R + r];"),
+    "front_end_steering_conjugate": (
+        "for (int n = 0; n < N; ++n) acc += conj(W[(size_t)c * N + n]) * spatial_phase(s, S, n);",
+        "for (int n = 0; n < N; ++n) acc += W[(size_t)c * N + n] * conj(spatial_phase(s, S, n));"),
+    "subarray_membership": ("W[(size_t)c * N + n] = (n / M == c) ? 1.0 : 0.0;",
+                            "W[(size_t)c * N + n] = (n % C == c) ? 1.0 : 0.0;"),
 }
 
 

@@ -583,3 +583,61 @@ def test_staggered_small_workload_recovers_injected_target():
     assert res["n_failed"] == 0
     assert int(np.argmax(P[2, 24])) == 128
     assert 10 * np.log10(P[2, 24, 128] / np.median(P)) > 10.0
+
+
+# ------------------------------------------------ reduced-DOF front end ----
+# N element channels combined into C channels by W[C][N]:
+# y[c] = sum_n conj(W[c][n]) x[n]; default W: C contiguous subarrays.
+
+def test_reduce_channels_is_the_conjugate_weighted_sum():
+    W = crandn(3, 37)
+    x = crandn(37, 5, 11)
+    y = oracle.reduce_channels(W, x)
+    np.testing.assert_allclose(y, np.einsum("cn,npr->cpr", W.conj(), x), rtol=0,
+                               atol=1e-12 * np.abs(y).max())
+
+
+def test_identity_front_end_is_the_plain_path():
+    """W = I: the channels pass through, and the reduced steering is the default
+    steering bit for bit."""
+    d = dims(C=4, P=16, K=16, R=32, T=3, B=16, S=5)
+    x = crandn(4, 16, 32)
+    I4 = np.eye(4, dtype=np.complex128)
+    np.testing.assert_array_equal(oracle.reduce_channels(I4, x), x)
+    np.testing.assert_array_equal(oracle.reduced_steering(d, I4), oracle.default_steering(d))
+
+
+@pytest.mark.parametrize("N,C,s0,k0", [(64, 4, 2, 5), (30, 3, 0, 11), (48, 8, 4, 0)])
+def test_reduced_steering_is_the_noise_free_target_snapshot(N, C, s0, k0):
+    """A unit plane wave on the steering grid at a bin centre, through the
+    subarray front end, has snapshot v_{s0}."""
+    P, K, T, S, R = 16, 16, 3, 5, 8
+    d = oracle.Dims(C, P, K, R, T, 8, S)
+    W = oracle.subarray_weights(N, C)
+    th = np.deg2rad(synth.steering_angle_deg(s0, S))
+    x = np.zeros((N, P, R), np.complex128)
+    x[:, :, 3] = np.exp(2j * np.pi * 0.5 * np.sin(th) * np.arange(N))[:, None] * \
+        np.exp(2j * np.pi * k0 / K * np.arange(P))[None, :]
+    y = oracle.reduce_channels(W, x)
+    snap = oracle.snapshot(d, oracle.doppler(d, y), k0, 3)
+    v = oracle.reduced_steering(d, W)[s0]
+    np.testing.assert_allclose(snap, v, rtol=0, atol=1e-12 * np.abs(v).max())
+
+
+def test_subarray_weights_and_their_gain_closed_form():
+    """Subarray c sums elements cM .. cM+M-1; its gain for spatial frequency f
+    is the geometric series exp(j 2 pi f c M) (1 - e^{j 2 pi f M}) / (1 - e^{j 2 pi f})."""
+    N, C, S = 40, 4, 6
+    M = N // C
+    W = oracle.subarray_weights(N, C)
+    assert W.shape == (C, N) and np.all(W.imag == 0)
+    for c in range(C):
+        np.testing.assert_array_equal(W[c].real, (np.arange(N) // M == c).astype(float))
+    d = oracle.Dims(C, 8, 8, 8, 1, 8, S)
+    st = oracle.reduced_steering(d, W)             # T = 1: g_0 = sum h
+    g0 = np.hanning(8).sum()
+    for s in range(S):
+        f = 0.5 * np.sin(np.deg2rad(synth.steering_angle_deg(s, S)))
+        z = np.exp(2j * np.pi * f)
+        b = z ** (np.arange(C) * M) * (1 - z ** M) / (1 - z)
+        np.testing.assert_allclose(st[s], g0 * b, rtol=0, atol=1e-11 * np.abs(g0 * b).max())
