@@ -242,6 +242,32 @@ stap_status stap_run_cpi(stap_plan plan, const void* const* cubes, float* const*
  * i.e. stap_run_cpi runs the whole batch as one wave. */
 stap_status stap_plan_batch_bytes(stap_plan plan, size_t* all_concurrent_bytes);
 
+/* Reduced-DOF front end (not in the paper, whose cubes have 1000 channels,
+ * i.e. D = 1000 T): the n_elem element channels of an element cube
+ * x[N][P][R] (a half-wavelength line array, element n answering a plane wave
+ * of spatial frequency f with exp(j 2 pi f n)) are combined into the plan's C
+ * channels by the matrix W[C][N] (host c128, row-major, copied):
+ *   cube[c][p][r] = sum_{n<N} conj(W[c][n]) x[n][p][r]
+ * (e.g. W[c][n] = 1 on C contiguous subarrays of N/C elements).  The plan's
+ * default steering becomes the reduced one,
+ *   v_s[t*C + c] = g_t b_s[c],  b_s[c] = sum_n conj(W[c][n]) exp(j 2 pi f_s n),
+ * which is the snapshot of a unit plane-wave target, and stays separable.
+ * Single-CPI plans only; call once, before stap_plan_set_workspace: it adds W
+ * to the run workspace and the element chunk buffers to the stream
+ * workspace (stap_plan_workspace_sizes, stap_plan_stream_bytes).  The
+ * reduction goes chunk_elems elements at a time (< 1: about 512 MB of element
+ * rows), each chunk summed in FP32 and added to the running result.  With a
+ * front end, stap_run_stream takes HOST element cubes c64 [N][P][R] and copies
+ * them in chunk by chunk. */
+stap_status stap_plan_set_front_end(stap_plan plan, int32_t n_elem, const double* W_c128,
+                                    int32_t chunk_elems);
+
+/* The front end on the device: elem_cube c64 [N][P][R] -> cube c64 [C][P][R],
+ * in one pass over all N elements (the same bits as a streamed run whose
+ * chunk holds all N elements).  STAP_ERR_INVALID_ARG if the plan has no front
+ * end. */
+stap_status stap_reduce_channels(stap_plan plan, const void* elem_cube_c64, void* cube_c64);
+
 /* Workspace size stap_run_stream needs: run_bytes plus two device cubes and
  * two device outputs.  Single-CPI plans only (STAP_ERR_INVALID_ARG
  * otherwise).  Host-only. */

@@ -1,6 +1,7 @@
 // Host side of libstap: plan creation and validation, workspace layout,
 // host-computed tables (window, twiddles, default steering) and the C entry
 // points that launch the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -148,7 +149,13 @@ struct stap_plan_s {
   // beyond run_bytes
   size_t stream_bytes = 0, cube_bytes = 0, out_bytes = 0;
   cudaStream_t h2d = nullptr, d2h = nullptr;
-  cudaEvent_t ev_start = nullptr, ev_in[2] = {}, ev_done[2] = {}, ev_out[2] = {};
+  cudaEvent_t ev_start = nullptr, ev_in[2] = {}, ev_done[2] = {}, ev_out[2] = {}, ev_red[2] = {};
+  // reduced-DOF front end (stap_plan_set_front_end): N element channels, the
+  // matrix W [C][N] (c64, at fe_w_off) and the element chunk of one copy /
+  // reduction; streamed runs then take element cubes
+  int fe_N = 0, fe_chunk = 0;
+  size_t fe_w_off = 0;
+  std::vector<float> fe_w;
   size_t dop_off = 0, cov_off = 0, wts_off = 0;   // run intermediates (sized for the largest CPI)
   size_t ctr_off = 0;                             // neighbour-training matrices (STAP_TRAIN_NEIGHBOURS)
   bool tables_ready = false;
@@ -199,6 +206,10 @@ stap_status upload_tables(stap_plan p, int only_cpi = -1) {
                         cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
       return STAP_ERR_CUDA;
   }
+  if (p->fe_N && (only_cpi <= 0) &&
+      cudaMemcpyAsync(p->ws + p->fe_w_off, p->fe_w.data(), p->fe_w.size() * sizeof(float),
+                      cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+    return STAP_ERR_CUDA;
   return STAP_OK;
 }
 
@@ -448,6 +459,87 @@ stap_status run_batched(stap_plan p, const void* const* cubes, float* const* out
   return cudaGraphLaunch(p->graph_exec, p->stream) == cudaSuccess ? STAP_OK : STAP_ERR_CUDA;
 }
 
+// The front end over a whole element cube on the device: one pass over all N
+// elements, so the reduced cube is written once (the streamed runs add chunk
+// after chunk into it instead; with one chunk of all N elements they give the
+// same bits).
+stap_status reduce_all(stap_plan p, const float2* elem, float2* y, cudaStream_t st) {
+  const stap_dims& d = p->cpis[0].d;
+  return check_launch(stap::launch_reduce_channels(elem, p->at<const float2>(p->fe_w_off), y,
+                                                   p->fe_N, 0, p->fe_N, d.n_chan, d.n_pulses,
+                                                   d.n_range, false, st));
+}
+
+// Streamed runs with the front end: every element cube goes in chunks of
+// fe_chunk elements through two device chunk buffers (copy on h2d, reduction
+// into the reduced cube y on the plan's stream), then the chain runs on y and
+// the output leaves on d2h.  Chunk buffer b is refilled only after the
+// reduction that read it (ev_red); y is rewritten by the next cube's first
+// reduction, which the plan's stream orders after this cube's chain.
+stap_status run_stream_elements(stap_plan p, int64_t n, const void* const* host_cubes,
+                                float* const* host_outs) {
+  const stap_dims& d = p->cpis[0].d;
+  const size_t PR8 = (size_t)d.n_pulses * d.n_range * 8;
+  size_t off = p->run_bytes;
+  float2* y = reinterpret_cast<float2*>(p->ws + off);
+  off += align_up(p->cube_bytes);
+  char* chunk_buf[2];
+  for (int j = 0; j < 2; ++j) {
+    chunk_buf[j] = p->ws + off;
+    off += align_up((size_t)p->fe_chunk * PR8);
+  }
+  float* out_buf[2];
+  for (int j = 0; j < 2; ++j) {
+    out_buf[j] = reinterpret_cast<float*>(p->ws + off);
+    off += align_up(p->out_bytes);
+  }
+  if (cudaEventRecord(p->ev_start, p->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(p->h2d, p->ev_start, 0) != cudaSuccess ||
+      cudaStreamWaitEvent(p->d2h, p->ev_start, 0) != cudaSuccess)
+    return STAP_ERR_CUDA;
+  stap_status st = STAP_OK;
+  long long g = 0;   // chunks queued so far
+  for (int64_t i = 0; i < n && st == STAP_OK; ++i) {
+    const char* src = static_cast<const char*>(host_cubes[i]);
+    for (int n0 = 0; n0 < p->fe_N && st == STAP_OK; n0 += p->fe_chunk, ++g) {
+      const int nc = std::min(p->fe_chunk, p->fe_N - n0);
+      const int b = (int)(g & 1);
+      if ((g >= 2 && cudaStreamWaitEvent(p->h2d, p->ev_red[b], 0) != cudaSuccess) ||
+          cudaMemcpyAsync(chunk_buf[b], src + (size_t)n0 * PR8, (size_t)nc * PR8,
+                          cudaMemcpyHostToDevice, p->h2d) != cudaSuccess ||
+          cudaEventRecord(p->ev_in[b], p->h2d) != cudaSuccess ||
+          cudaStreamWaitEvent(p->stream, p->ev_in[b], 0) != cudaSuccess) {
+        st = STAP_ERR_CUDA;
+        break;
+      }
+      st = check_launch(stap::launch_reduce_channels(
+          reinterpret_cast<const float2*>(chunk_buf[b]), p->at<const float2>(p->fe_w_off), y,
+          p->fe_N, n0, nc, d.n_chan, d.n_pulses, d.n_range, n0 > 0, p->stream));
+      if (st == STAP_OK && cudaEventRecord(p->ev_red[b], p->stream) != cudaSuccess) st = STAP_ERR_CUDA;
+    }
+    if (st != STAP_OK) break;
+    const int j = (int)(i & 1);
+    if (i >= 2 && cudaStreamWaitEvent(p->stream, p->ev_out[j], 0) != cudaSuccess) {
+      st = STAP_ERR_CUDA;
+      break;
+    }
+    st = run_single(p, y, out_buf[j]);
+    if (st != STAP_OK) break;
+    if (cudaEventRecord(p->ev_done[j], p->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(p->d2h, p->ev_done[j], 0) != cudaSuccess ||
+        cudaMemcpyAsync(host_outs[i], out_buf[j], p->out_bytes, cudaMemcpyDeviceToHost, p->d2h) !=
+            cudaSuccess ||
+        cudaEventRecord(p->ev_out[j], p->d2h) != cudaSuccess)
+      st = STAP_ERR_CUDA;
+  }
+  if (cudaEventRecord(p->ev_start, p->h2d) != cudaSuccess ||
+      cudaStreamWaitEvent(p->stream, p->ev_start, 0) != cudaSuccess ||
+      cudaEventRecord(p->ev_start, p->d2h) != cudaSuccess ||
+      cudaStreamWaitEvent(p->stream, p->ev_start, 0) != cudaSuccess)
+    st = STAP_ERR_CUDA;
+  return st;
+}
+
 stap_status single_cpi(stap_plan p) {
   if (!p) return STAP_ERR_INVALID_ARG;
   return p->cpis.size() == 1 ? STAP_OK : STAP_ERR_INVALID_ARG;
@@ -622,7 +714,7 @@ stap_status stap_plan_destroy(stap_plan p) {
         cudaStreamDestroy(s);
       }
     for (int j = 0; j < 2; ++j)
-      for (cudaEvent_t e : {p->ev_in[j], p->ev_done[j], p->ev_out[j]})
+      for (cudaEvent_t e : {p->ev_in[j], p->ev_done[j], p->ev_out[j], p->ev_red[j]})
         if (e) cudaEventDestroy(e);
     cudaEventDestroy(p->ev_start);
   }
@@ -724,6 +816,74 @@ stap_status stap_plan_stream_bytes(stap_plan p, size_t* bytes) {
   return STAP_OK;
 }
 
+stap_status stap_plan_set_front_end(stap_plan p, int32_t n_elem, const double* W,
+                                    int32_t chunk_elems) {
+  if (!p || !W || n_elem < 1 || p->cpis.size() != 1) return STAP_ERR_INVALID_ARG;
+  if (p->ws || p->fe_N) return STAP_ERR_INVALID_ARG;   // once, before the workspace
+  Cpi& c = p->cpis[0];
+  const stap_dims& d = c.d;
+  const int C = d.n_chan, N = n_elem, S = d.n_steering, T = d.tdof, D = c.D;
+  const size_t PR8 = (size_t)d.n_pulses * d.n_range * 8;
+  if ((size_t)N * PR8 > ((size_t)1 << 44)) return STAP_ERR_UNSUPPORTED;
+  for (size_t i = 0; i < 2 * (size_t)C * N; ++i)
+    if (!std::isfinite(W[i])) return STAP_ERR_INVALID_ARG;
+  int chunk = chunk_elems;
+  if (chunk < 1) {   // about 512 MB of element rows per copy and reduction
+    const size_t want = ((size_t)512 << 20) / PR8;
+    chunk = (int)std::min<size_t>(std::max<size_t>(want, 1), (size_t)N);
+  }
+  if (chunk > N) chunk = N;
+  // spatial gains b_s[c] = sum_n conj(W[c][n]) exp(j 2 pi f_s n): the separable
+  // steering's spatial factors, and v_s = g (x) b_s
+  for (int s = 0; s < S; ++s) {
+    const double th = (-90.0 + 180.0 * (s + 0.5) / S) * kPi / 180.0;
+    const double fs = 0.5 * std::sin(th);
+    for (int ch = 0; ch < C; ++ch) {
+      double br = 0, bi = 0;
+      for (int e = 0; e < N; ++e) {
+        const double a = 2.0 * kPi * fs * e;
+        const double er = std::cos(a), ei = std::sin(a);
+        const double wr = W[2 * ((size_t)ch * N + e)], wi = W[2 * ((size_t)ch * N + e) + 1];
+        br += wr * er + wi * ei;   // conj(w) e
+        bi += wr * ei - wi * er;
+      }
+      c.sep_a[2 * ((size_t)s * C + ch)] = br;
+      c.sep_a[2 * ((size_t)s * C + ch) + 1] = bi;
+    }
+    for (int t = 0; t < T; ++t)
+      for (int ch = 0; ch < C; ++ch) {
+        const double gr = c.sep_g[2 * t], gi = c.sep_g[2 * t + 1];
+        const double ar = c.sep_a[2 * ((size_t)s * C + ch)], ai = c.sep_a[2 * ((size_t)s * C + ch) + 1];
+        double* v = &c.steer[2 * ((size_t)s * D + t * C + ch)];
+        v[0] = gr * ar - gi * ai;
+        v[1] = gr * ai + gi * ar;
+      }
+  }
+  c.separable = true;
+  to_ff(c.steer, c.steer_ff);
+  to_ff(c.sep_a, c.sep_a_ff);
+  p->fe_w.resize(2 * (size_t)C * N);
+  for (size_t i = 0; i < p->fe_w.size(); ++i) p->fe_w[i] = (float)W[i];
+  p->fe_N = N;
+  p->fe_chunk = chunk;
+  p->fe_w_off = p->run_bytes;
+  p->run_bytes = align_up(p->run_bytes + p->fe_w.size() * sizeof(float));
+  p->stream_bytes = p->run_bytes + align_up(p->cube_bytes) + 2 * align_up((size_t)chunk * PR8) +
+                    2 * align_up(p->out_bytes);
+  if (p->batch_bytes < p->run_bytes) p->batch_bytes = p->run_bytes;
+  return STAP_OK;
+}
+
+stap_status stap_reduce_channels(stap_plan p, const void* elem_cube_c64, void* cube_c64) {
+  if (!p || !elem_cube_c64 || !cube_c64) return STAP_ERR_INVALID_ARG;
+  if (!aligned16(elem_cube_c64) || !aligned16(cube_c64)) return STAP_ERR_MISALIGNED;
+  if (!p->fe_N) return STAP_ERR_INVALID_ARG;
+  stap_status st = ready(p, p->run_bytes);
+  if (st != STAP_OK) return st;
+  return reduce_all(p, static_cast<const float2*>(elem_cube_c64), static_cast<float2*>(cube_c64),
+                    p->stream);
+}
+
 // CPI i: copy-in on h2d into device cube j = i % 2, the chain on the plan's
 // stream into device output j, copy-out on d2h.  Buffer j is rewritten by CPI
 // i + 2 only after CPI i's chain has read it (ev_done) and its output has been
@@ -745,9 +905,11 @@ stap_status stap_run_stream(stap_plan p, int64_t n, const void* const* host_cube
     for (int j = 0; j < 2; ++j)
       if (cudaEventCreateWithFlags(&p->ev_in[j], cudaEventDisableTiming) != cudaSuccess ||
           cudaEventCreateWithFlags(&p->ev_done[j], cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&p->ev_out[j], cudaEventDisableTiming) != cudaSuccess)
+          cudaEventCreateWithFlags(&p->ev_out[j], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p->ev_red[j], cudaEventDisableTiming) != cudaSuccess)
         return STAP_ERR_CUDA;
   }
+  if (p->fe_N) return run_stream_elements(p, n, host_cubes, host_outs);
   char* cube_buf[2];
   float* out_buf[2];
   size_t off = p->run_bytes;

@@ -51,6 +51,12 @@ bool mir_supported(int D);
 
 // Hann-windowed DFT over pulses via a two-pass in-register FFT.
 // cube [C][P][R] c64 -> dop [C][K][R] c64; win[P] float; tw[K] = exp(-2 pi i m/K).
+// Reduced-DOF front end: y[c][p][r] (+)= sum_{n<Nc} conj(W[c][n0+n]) x_chunk[n][p][r]
+// for one chunk of Nc element channels (x_chunk [Nc][P][R], W [C][N], y [C][P][R],
+// all c64); accumulate adds to y instead of writing it.
+cudaError_t launch_reduce_channels(const float2* x_chunk, const float2* W, float2* y, int N, int n0,
+                                   int Nc, int C, int P, int R, bool accumulate, cudaStream_t s);
+
 // TW = 1: the plain transform (win: Hann of length P); TW > 1: PRI-staggered
 // sub-windows (win: Hann of length P - TW + 1), dop rows t*C + c.
 cudaError_t launch_doppler(const float2* cube, float2* dop, const float* win, const float2* tw,

@@ -7,12 +7,15 @@ Builds the plan, takes the launch choices from the autotune cache (timing them
 on the device when the cache lacks the shape), warms up, and then runs
 ``--steps`` calls of ``stap_run_cpi`` between cudaProfilerStart and
 cudaProfilerStop, so that a profiler started with profiling off sees exactly
-the launches of those steps.  ``--slabs N`` overrides the tuned number of
+the launches of those steps.  The paper_cube workloads run the subarray front
+end (1000 elements to 4 channels) before the chain in every step.  ``--slabs N`` overrides the tuned number of
 range slabs (1 = the plain four-launch chain).  The input is the workload's
 seeded synthetic cube, generated on the device.
 """
 import argparse
+import dataclasses
 
+import numpy as np
 import torch
 
 from . import stap, synth
@@ -20,7 +23,8 @@ from . import stap, synth
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--workload", default="standard", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="standard",
+                    choices=sorted(synth.WORKLOADS) + sorted(synth.ELEMENT_WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3"])
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -29,28 +33,47 @@ def main(argv=None):
     ap.add_argument("--refine", type=int, default=None,
                     help="refinement steps (default: 1 for fp64, 2 for mixed_ir)")
     a = ap.parse_args(argv)
-    spec = synth.WORKLOADS[a.workload]()
-    if isinstance(spec, (list, tuple)):
-        raise SystemExit("profile_step runs one-CPI workloads")
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     prec = stap.STAP_PREC_FP32 if a.precision == "fp32" else stap.STAP_PREC_TF32X3
-    cube = synth.make_cube_torch(spec, dev)
     solver = stap.STAP_SOLVE_FP64 if a.solver == "fp64" else stap.STAP_SOLVE_MIXED_IR
     refine = a.refine if a.refine is not None else (1 if a.solver == "fp64" else 2)
-    plan = stap.Plan(spec.dims(), device=dev, precision=prec, refine_steps=refine, solver=solver)
+    elem = None
+    if a.workload in synth.ELEMENT_WORKLOADS:
+        # element cube through the subarray front end, then the chain
+        es = synth.ELEMENT_WORKLOADS[a.workload]()
+        N, P, K, R, T, B, S = es.dims()
+        C = synth.PAPER_CUBE_CHANNELS
+        W = (np.arange(N)[None, :] // (N // C) == np.arange(C)[:, None]).astype(np.complex128)
+        spec = dataclasses.replace(es, n_chan=C)
+        plan = stap.Plan(spec.dims(), device=dev, precision=prec, refine_steps=refine, solver=solver,
+                         front_end=W)
+        elem = synth.make_cube_torch(es, dev)
+        cube = plan.reduce_channels(elem)
+    else:
+        spec = synth.WORKLOADS[a.workload]()
+        if isinstance(spec, (list, tuple)):
+            raise SystemExit("profile_step runs one-CPI workloads")
+        cube = synth.make_cube_torch(spec, dev)
+        plan = stap.Plan(spec.dims(), device=dev, precision=prec, refine_steps=refine, solver=solver)
     out = torch.empty(plan.shapes(0)["out"], dtype=torch.float32, device=dev)
     tuning = plan.autotune(cube, out)
     if a.slabs > 0:
         choices = stap.stap_plan_get_tuning(plan.handle, 0)
         choices[6] = a.slabs
         stap.stap_plan_set_tuning(plan.handle, 0, choices)
-    for _ in range(a.warmup):
+
+    def step():
+        if elem is not None:
+            plan.reduce_channels(elem, cube)
         plan.run_cpi(cube, out)
+
+    for _ in range(a.warmup):
+        step()
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
     for _ in range(a.steps):
-        plan.run_cpi(cube, out)
+        step()
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     code, failed = plan.status()

@@ -13,6 +13,7 @@ import os
 import threading
 from typing import List, Optional, Sequence
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -44,6 +45,7 @@ EXPORTED = (
     "stap_run_cpi", "stap_get_status", "stap_status_string", "stap_abi_version",
     "stap_run_cpi_noalloc", "stap_plan_batch_bytes", "stap_plan_autotune", "stap_plan_get_tuning",
     "stap_plan_set_tuning", "stap_train_neighbours", "stap_plan_stream_bytes", "stap_run_stream",
+    "stap_plan_set_front_end", "stap_reduce_channels",
 )
 
 STAP_TUNING_LEN = 9
@@ -106,6 +108,8 @@ def lib():
             L.stap_abi_version.argtypes = []
             L.stap_plan_batch_bytes.argtypes = [vp, ctypes.POINTER(sz)]
             L.stap_plan_stream_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+            L.stap_plan_set_front_end.argtypes = [vp, i32, vp, i32]
+            L.stap_reduce_channels.argtypes = [vp, vp, vp]
             L.stap_run_stream.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(vp), ctypes.POINTER(vp)]
             L.stap_plan_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32]
             L.stap_plan_get_tuning.argtypes = [vp, i32, ctypes.POINTER(i32)]
@@ -205,6 +209,18 @@ def stap_plan_stream_bytes(plan) -> int:
     a = ctypes.c_size_t()
     _check(lib().stap_plan_stream_bytes(plan, ctypes.byref(a)), "stap_plan_stream_bytes")
     return a.value
+
+
+def stap_plan_set_front_end(plan, W, chunk_elems: int = 0):
+    """W: [C][N] complex (host); copied."""
+    Wn = np.ascontiguousarray(np.asarray(W, dtype=np.complex128))
+    _check(lib().stap_plan_set_front_end(plan, Wn.shape[1], Wn.ctypes.data_as(ctypes.c_void_p),
+                                         int(chunk_elems)), "stap_plan_set_front_end")
+
+
+def stap_reduce_channels(plan, elem_cube: torch.Tensor, cube: torch.Tensor):
+    _check(lib().stap_reduce_channels(plan, ctypes.c_void_p(elem_cube.data_ptr()),
+                                      ctypes.c_void_p(cube.data_ptr())), "stap_reduce_channels")
 
 
 def stap_plan_set_workspace(plan, workspace: torch.Tensor):
@@ -336,7 +352,8 @@ class Plan:
     def __init__(self, dims, load_factor: float = 1e-3, refine_steps: int = 1,
                  precision: int = STAP_PREC_FP32, device=None, steps_only: bool = False,
                  max_workspace_bytes: Optional[int] = None, solver: int = STAP_SOLVE_FP64,
-                 training: int = STAP_TRAIN_OWN_BLOCK, snapshots: int = STAP_SNAP_ADJACENT_BINS):
+                 training: int = STAP_TRAIN_OWN_BLOCK, snapshots: int = STAP_SNAP_ADJACENT_BINS,
+                 front_end=None, front_end_chunk: int = 0):
         dl = list(dims) if isinstance(dims, (list, tuple)) and dims and not isinstance(dims[0], int) \
             else [dims]
         self.dims = [_dims(d) for d in dl]
@@ -345,8 +362,12 @@ class Plan:
                             int(training), int(snapshots))
         self.precision, self.refine_steps, self.solver = int(precision), int(refine_steps), int(solver)
         self.training, self.snapshots = int(training), int(snapshots)
+        self.n_elem = 0
         with torch.cuda.device(self.device):
             self.handle, _ = stap_plan_create(self.dims, opts)
+            if front_end is not None:   # N element channels -> C by W [C][N]
+                stap_plan_set_front_end(self.handle, front_end, front_end_chunk)
+                self.n_elem = int(np.asarray(front_end).shape[1])
             self.step_bytes, self.run_bytes = stap_plan_workspace_sizes(self.handle)
             self.batch_bytes = stap_plan_batch_bytes(self.handle)
             nbytes = self.step_bytes if steps_only else self.run_bytes
@@ -376,8 +397,23 @@ class Plan:
                                d.training_block, d.n_steering)
         D, NB = C * T, R // B
         rows = D if self.snapshots == STAP_SNAP_PRI_STAGGERED else C   # Doppler rows
-        return dict(cube=(C, P, R), dop=(rows, K, R), cov=(K, NB, D, D), wts=(K, NB, S, D),
-                    out=(S, K, R))
+        sh = dict(cube=(C, P, R), dop=(rows, K, R), cov=(K, NB, D, D), wts=(K, NB, S, D),
+                  out=(S, K, R))
+        if self.n_elem:
+            sh["elements"] = (self.n_elem, P, R)
+        return sh
+
+    def reduce_channels(self, elem_cube, cube=None):
+        """The front end on the device: element cube [N][P][R] -> cube [C][P][R]."""
+        sh = self.shapes()
+        if not self.n_elem:
+            raise ValueError("the plan has no front end")
+        cube = torch.empty(sh["cube"], dtype=torch.complex64, device=self.device) if cube is None else cube
+        _dev(elem_cube, torch.complex64, sh["elements"], "elem_cube")
+        _dev(cube, torch.complex64, sh["cube"], "cube")
+        self._sync_stream()
+        stap_reduce_channels(self.handle, elem_cube, cube)
+        return cube
 
     def _sync_stream(self):
         stap_plan_set_stream(self.handle, torch.cuda.current_stream(self.device))
@@ -466,7 +502,7 @@ class Plan:
         if len(host_outs) != len(host_cubes):
             raise ValueError("host_outs and host_cubes differ in length")
         for i, (c, o) in enumerate(zip(host_cubes, host_outs)):
-            _host(c, torch.complex64, sh["cube"], f"host_cubes[{i}]")
+            _host(c, torch.complex64, sh["elements"] if self.n_elem else sh["cube"], f"host_cubes[{i}]")
             _host(o, torch.float32, sh["out"], f"host_outs[{i}]")
         need = stap_plan_stream_bytes(self.handle)
         if self.workspace.numel() < need:

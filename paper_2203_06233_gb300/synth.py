@@ -226,6 +226,32 @@ def batch_cpis(n: int = 512, seed: int = 4) -> List[CPISpec]:
     return out
 
 
+def paper_cube_elements() -> CPISpec:
+    """The element cube of the paper's STAP data shape (Sec. 5.3: 1000 channels,
+    100 pulses, 30000 samples per pulse; about 24 GB as complex64), as elements
+    of a half-wavelength line array: 40 dB CNR per element, 8 targets.  Its
+    K, T, B, S (128, 3, 100, 16) are the chain's after a front end that
+    reduces the 1000 elements to PAPER_CUBE_CHANNELS channels."""
+    return CPISpec(1000, 100, 128, 30000, 3, 100, 16, cnr_db=40.0,
+                   targets=random_targets(6, 8, 30000, 128, 16), seed=6)
+
+
+PAPER_CUBE_CHANNELS = 4     # contiguous subarrays of 250 elements
+
+
+def paper_cube_small_elements() -> CPISpec:
+    """The paper cube with a tenth of its range (R = 3000, about 2.4 GB), for
+    profiles of the front end."""
+    return CPISpec(1000, 100, 128, 3000, 3, 100, 16, cnr_db=40.0,
+                   targets=random_targets(6, 8, 3000, 128, 16), seed=6)
+
+
+ELEMENT_WORKLOADS = {
+    "paper_cube": paper_cube_elements,
+    "paper_cube_small": paper_cube_small_elements,
+}
+
+
 WORKLOADS = {
     "small": small_cpi,
     "standard": standard_cpi,

@@ -168,6 +168,44 @@ def test_stream_workspace_and_arguments_fail_before_cuda():
     stap.stap_plan_destroy(h2)
 
 
+def test_front_end_arguments_and_workspace_growth():
+    import numpy as np
+    L = stap.lib()
+    C, P, K, R, T, B, S = GOOD
+    N = 1000
+    W = np.zeros((C, N), np.complex128)
+    W[:, :4] = np.eye(C)
+    Wp = W.ctypes.data_as(ctypes.c_void_p)
+    code, h, ws = _create(GOOD)
+    step, run = stap.stap_plan_workspace_sizes(h)
+    sb0 = stap.stap_plan_stream_bytes(h)
+    assert L.stap_plan_set_front_end(h, 0, Wp, 0) == stap.STAP_ERR_INVALID_ARG
+    assert L.stap_plan_set_front_end(h, N, None, 0) == stap.STAP_ERR_INVALID_ARG
+    bad = W.copy()
+    bad[1, 7] = np.nan
+    assert L.stap_plan_set_front_end(h, N, bad.ctypes.data_as(ctypes.c_void_p), 0) == stap.STAP_ERR_INVALID_ARG
+    fake = ctypes.c_void_p(0x10000)                           # never dereferenced
+    assert L.stap_reduce_channels(h, fake, fake) == stap.STAP_ERR_INVALID_ARG   # no front end yet
+    assert L.stap_plan_set_front_end(h, N, Wp, 0) == stap.STAP_OK
+    assert L.stap_plan_set_front_end(h, N, Wp, 0) == stap.STAP_ERR_INVALID_ARG  # only once
+    step1, run1 = stap.stap_plan_workspace_sizes(h)
+    assert step1 == step and 0 <= run1 - run - C * N * 8 < 256
+    # default chunk: 128 element rows of 4 MiB (512 MiB); the stream holds the
+    # reduced cube, two chunks and two outputs beyond the run workspace
+    PR8 = P * R * 8
+    sb1 = stap.stap_plan_stream_bytes(h)
+    expect = run1 + C * PR8 + 2 * 128 * PR8 + 2 * S * K * R * 4
+    assert 0 <= sb1 - expect < 1024 and sb1 != sb0
+    assert L.stap_reduce_channels(h, fake, fake) == stap.STAP_ERR_NO_WORKSPACE
+    assert L.stap_reduce_channels(h, ctypes.c_void_p(0x10008), fake) == stap.STAP_ERR_MISALIGNED
+    stap.stap_plan_destroy(h)
+    dims2 = (stap.stap_dims * 2)(stap.stap_dims(*GOOD), stap.stap_dims(*GOOD))
+    h2 = ctypes.c_void_p()
+    assert L.stap_plan_create(dims2, 2, None, None, ctypes.byref(h2), None) == stap.STAP_OK
+    assert L.stap_plan_set_front_end(h2, N, Wp, 0) == stap.STAP_ERR_INVALID_ARG   # batch plan
+    stap.stap_plan_destroy(h2)
+
+
 def test_options_default_and_mixed_refinement_shape_limits():
     o = stap.stap_options_default()
     assert o.solver == stap.STAP_SOLVE_FP64
