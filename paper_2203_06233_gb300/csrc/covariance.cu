@@ -19,6 +19,7 @@
 // D x B snapshot tiles in shared memory (chunks of BC cells if B is large) and
 // gives each thread whole entries (i >= l) of the lower triangle; the upper
 // triangle is written as the conjugate mirror.
+#include "df64.cuh"
 #include "snapshots.cuh"
 
 namespace stap {
@@ -48,7 +49,7 @@ __device__ __forceinline__ void unpack_lower(int q, int& i, int& l) {
 
 __global__ void __launch_bounds__(256)
 covariance_ff_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K, int ldr,
-                     int T, int B, int NB, int NS, int BC) {
+                     int T, int B, int NB, int NS, int BC, double invB) {
   extern __shared__ float2 xs[];  // [NS][D][BC + 1]
   const int k = blockIdx.y;
   const int b0 = blockIdx.x * NS;
@@ -56,7 +57,6 @@ covariance_ff_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
   const int E = D * (D + 1) / 2;
   const int ld = BC + 1;
   const int ns = min(NS, NB - b0);
-  const double invB = 1.0 / (double)B;
 
   for (int c0 = 0; c0 < B; c0 += BC) {
     const int bc = min(BC, B - c0);
@@ -79,8 +79,8 @@ covariance_ff_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
         ff_add_prod(im, a.y, b.x);
         ff_add_prod(im, -a.x, b.y);
       }
-      double vr = ((double)re.s + (double)re.e) * invB;
-      double vi = ((double)im.s + (double)im.e) * invB;
+      double vr = (ff::f2d_exact(re.s) + ff::f2d_exact(re.e)) * invB;
+      double vi = (ff::f2d_exact(im.s) + ff::f2d_exact(im.e)) * invB;
       double2* out = cov + ((size_t)k * NB + b0 + j) * (size_t)D * D;
       if (c0 > 0) {  // later chunks add to what earlier chunks wrote (same thread owns the entry)
         const double2 prev = out[(size_t)i * D + l];
@@ -89,7 +89,7 @@ covariance_ff_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
       }
       if (i == l) vi = 0.0;
       out[(size_t)i * D + l] = make_double2(vr, vi);
-      if (i != l) out[(size_t)l * D + i] = make_double2(vr, -vi);
+      if (i != l) out[(size_t)l * D + i] = make_double2(vr, ff::dneg(vi));
     }
   }
 }
@@ -135,7 +135,7 @@ __device__ __forceinline__ void grid_add(float& hi, float& lo, float a, float b,
 
 __global__ void __launch_bounds__(kPairMaxThreads)
 covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K,
-                        int ldr, int T, int B, int NB, int KT, int CB) {
+                        int ldr, int T, int B, int NB, int KT, int CB, double invB) {
   extern __shared__ double2 smd[];
   const int b = blockIdx.x;
   const int k0 = blockIdx.y * KT;
@@ -150,7 +150,6 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
   float* m = reinterpret_cast<float*>(Q + nitems);              // [nrows] row maxima
   float2* X = reinterpret_cast<float2*>(m + ((nrows + 3) & ~3));  // [nrows][ld]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const double invB = 1.0 / (double)B;
   const bool pow2B = (B & (B - 1)) == 0;
   const float invBf = 1.0f / (float)B;
 
@@ -211,10 +210,10 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
       }
       double2 v;
       if (pow2B) {  // 1/B is a power of two: scaling the pair in FP32 is exact
-        v = make_double2((double)(hr * invBf) + (double)(lr * invBf),
-                         (double)(hi * invBf) + (double)(li * invBf));
+        v = make_double2(ff::f2d_exact(hr * invBf) + ff::f2d_exact(lr * invBf),
+                         ff::f2d_exact(hi * invBf) + ff::f2d_exact(li * invBf));
       } else {
-        v = make_double2(((double)hr + (double)lr) * invB, ((double)hi + (double)li) * invB);
+        v = make_double2((ff::f2d_exact(hr) + ff::f2d_exact(lr)) * invB, (ff::f2d_exact(hi) + ff::f2d_exact(li)) * invB);
       }
       if (c0 > 0) {
         const double2 p = Q[it];
@@ -232,7 +231,7 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
     if (d == 0) {
       if (c1 >= c2) return Q[j1 * Ediag + c1 * (c1 + 1) / 2 + c2];
       const double2 v = Q[j1 * Ediag + c2 * (c2 + 1) / 2 + c1];
-      return make_double2(v.x, -v.y);
+      return make_double2(v.x, ff::dneg(v.y));
     }
     // blocks d' < d come first: NBIN Ediag + sum_{e=1}^{d-1} (NBIN - e) Eoff
     const int off = NBIN * Ediag + Eoff * ((d - 1) * NBIN - d * (d - 1) / 2);
@@ -248,7 +247,7 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
       v = qat(kl + t1, t2 - t1, c1, c2);
     } else {
       const double2 w = qat(kl + t2, t1 - t2, c2, c1);
-      v = make_double2(w.x, -w.y);
+      v = make_double2(w.x, ff::dneg(w.y));
     }
     if (i == l) v.y = 0.0;
     cov[(((size_t)(k0 + kl) * NB + b) * D + i) * D + l] = v;
@@ -300,7 +299,8 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
         threads = ((nitems + rounds - 1) / rounds + 31) / 32 * 32;
         if (threads > kPairMaxThreads) threads = kPairMaxThreads;
       }
-      covariance_pairs_kernel<<<grid, threads, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, KT, CB);
+      covariance_pairs_kernel<<<grid, threads, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, KT, CB,
+                                                         1.0 / (double)B);
       return cudaGetLastError();
     }
   }
@@ -318,7 +318,7 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
   cudaError_t e = ensure_smem(covariance_ff_kernel, smem, set_bytes);
   if (e != cudaSuccess) return e;
   dim3 grid((NB + NS - 1) / NS, K);
-  covariance_ff_kernel<<<grid, 256, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, NS, BC);
+  covariance_ff_kernel<<<grid, 256, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, NS, BC, 1.0 / (double)B);
   return cudaGetLastError();
 }
 

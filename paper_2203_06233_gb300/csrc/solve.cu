@@ -102,9 +102,17 @@ __device__ __forceinline__ void step_lower(int& i, int& l, int step) {
   }
 }
 
-// (re, im) as the double-floats (re_hi, re_lo, im_hi, im_lo)
+// (re, im) as the double-floats (re_hi, re_lo, im_hi, im_lo); the split runs
+// on the integer pipe, off the FP64 pipe that the FP64 solve kernels are bound by
 __device__ __forceinline__ float4 to_ff4(double2 u) {
   const ff::F2 re = ff::from_double(u.x), im = ff::from_double(u.y);
+  return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+// the same with the conversion instructions, for the refinement kernels, whose
+// FP32 and integer issue is the bottleneck
+__device__ __forceinline__ float4 to_ff4_cvt(double2 u) {
+  const ff::F2 re = ff::from_double_cvt(u.x), im = ff::from_double_cvt(u.y);
   return make_float4(re.hi, re.lo, im.hi, im.lo);
 }
 
@@ -602,7 +610,7 @@ solve_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       int i = 0, l = 0;
       step_lower(i, l, tl);
       for (int q = tl; q < Dp; q += TS) {
-        const float4 f = to_ff4(loaded(A, D, i, l, delta));
+        const float4 f = to_ff4_cvt(loaded(A, D, i, l, delta));
         Ad[q] = f;
         Lf[q] = make_float2(f.x, f.z);
         step_lower(i, l, TS);
@@ -1261,7 +1269,7 @@ solve_big_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
     const double delta = load_factor * *trs * invD;
     for (int i = warp; i < D; i += NW)
       for (int l = lane; l <= i; l += 32) {
-        const float4 f = to_ff4(loaded(A, D, i, l, delta));
+        const float4 f = to_ff4_cvt(loaded(A, D, i, l, delta));
         Ad[colstart(l, D) + i - l] = f;
         Lf[colstart(l, D) + i - l] = make_float2(f.x, f.z);
       }

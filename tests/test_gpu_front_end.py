@@ -29,12 +29,15 @@ def _dev(a, dtype=torch.complex64):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda().to(dtype)
 
 
-def test_reduce_channels_matches_the_oracle_within_the_fp32_sum_bound():
+@pytest.mark.parametrize("N,C,P,K,R,B", [(77, 3, 16, 16, 64, 16),     # P R even: bulk-copy kernel
+                                          (77, 6, 5, 8, 63, 9),       # P R odd: register kernel
+                                          (1000, 4, 4, 4, 1030, 10)],  # ragged last tile
+                         ids=["bulk", "odd", "ragged"])
+def test_reduce_channels_matches_the_oracle_within_the_fp32_sum_bound(N, C, P, K, R, B):
     rng = np.random.default_rng(7)
-    N, C = 77, 3
-    spec = synth.CPISpec(C, 16, 16, 64, 2, 16, 4, cnr_db=None, seed=62)
+    spec = synth.CPISpec(C, P, K, R, 2, B, 4, cnr_db=None, seed=62)
     W = rng.standard_normal((C, N)) + 1j * rng.standard_normal((C, N))
-    x = (rng.standard_normal((N, 16, 64)) + 1j * rng.standard_normal((N, 16, 64))).astype(np.complex64)
+    x = (rng.standard_normal((N, P, R)) + 1j * rng.standard_normal((N, P, R))).astype(np.complex64)
     ref = oracle.reduce_channels(W, x)
     plan = stap.Plan(spec.dims(), front_end=W)
     y = to_np(plan.reduce_channels(_dev(x)))

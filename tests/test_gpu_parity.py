@@ -80,6 +80,40 @@ def test_covariance_parity(spec):
     assert np.max(num / den) <= 1e-10, np.max(num / den)
 
 
+def test_covariance_parity_with_subnormal_error_terms():
+    """A Doppler cube scaled by 1e-16: the products are near 1e-32, so the
+    error terms of the float pairs fall into FP32's subnormal range while
+    their high parts stay normal; both convert exactly to FP64."""
+    spec = synth.small_cpi()
+    d = oracle.Dims(*spec.dims())
+    dop64 = (oracle.doppler(d, _cube(spec)) * 1e-16).astype(np.complex64)
+    ref = oracle.covariance(d, dop64)
+    cov = to_np(_plan(spec).covariance(_dev(dop64, torch.complex64)))
+    num = np.linalg.norm((cov - ref).reshape(spec.n_dop, spec.NB, -1), axis=-1)
+    den = np.linalg.norm(ref.reshape(spec.n_dop, spec.NB, -1), axis=-1)
+    assert np.max(num / den) <= 1e-10, np.max(num / den)
+
+
+def test_covariance_of_an_infinite_sample_is_not_finite_where_the_oracle_is_not():
+    spec = synth.small_cpi()
+    d = oracle.Dims(*spec.dims())
+    dop64 = oracle.doppler(d, _cube(spec)).astype(np.complex64)
+    dop64[1, 7, 40] = np.inf
+    with np.errstate(invalid="ignore", over="ignore"):
+        ref = oracle.covariance(d, dop64)
+    cov = to_np(_plan(spec).covariance(_dev(dop64, torch.complex64)))
+    bad_ref = ~np.isfinite(ref.real) | ~np.isfinite(ref.imag)
+    bad = ~np.isfinite(cov.real) | ~np.isfinite(cov.imag)
+    # entries of the systems that never saw the sample stay finite and exact to 1e-10
+    hit = bad_ref.reshape(spec.n_dop, spec.NB, -1).any(axis=-1)
+    assert hit.any() and not hit.all()
+    assert np.array_equal(bad.reshape(spec.n_dop, spec.NB, -1).any(axis=-1), hit)
+    ok = ~hit
+    num = np.linalg.norm((cov - ref).reshape(spec.n_dop, spec.NB, -1)[ok], axis=-1)
+    den = np.linalg.norm(ref.reshape(spec.n_dop, spec.NB, -1)[ok], axis=-1)
+    assert np.max(num / den) <= 1e-10
+
+
 @pytest.mark.parametrize("refine", [0, 1, 2])
 @pytest.mark.parametrize("spec", SPECS, ids=IDS)
 def test_solve_weights_parity(spec, refine):
