@@ -1071,10 +1071,14 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
       // The candidates differ by a few percent and by how well the steps of
       // different slabs overlap, which depends on the cube being read cold
       // (as a new CPI is): before each timed run, writes to the output and
-      // to the intermediates (more than the L2 holds for the standard CPI)
-      // evict it.  Best of three rounds taken round-robin, reps runs each.
+      // to every intermediate region (more than the L2 holds for the
+      // standard CPI) evict it.  Seven rounds taken round-robin, reps runs
+      // each; the candidate with the lowest median round wins (the minimum
+      // rewarded rounds that happened to find part of the cube in L2).
       const size_t out_bytes = (size_t)d.n_steering * d.n_dop * d.n_range * sizeof(float);
-      const size_t mid_bytes = p->wts_off - p->dop_off;   // dop and cov regions
+      // dop, cov, wts (and training) regions; the front end's W table, kept
+      // after them, must survive
+      const size_t mid_bytes = (p->fe_N ? p->fe_w_off : p->run_bytes) - p->dop_off;
       auto cold_run = [&]() -> float {
         if (cudaMemsetAsync(out, 0, out_bytes, p->stream) != cudaSuccess ||
             cudaMemsetAsync(p->ws + p->dop_off, 0, mid_bytes, p->stream) != cudaSuccess)
@@ -1087,26 +1091,35 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
         cudaEventElapsedTime(&ms, e0, e1);
         return ms;
       };
+      constexpr int kRounds = 7;
       const int cands[4] = {1, 2, 4, 8};
-      float best[4] = {kNever, kNever, kNever, kNever};
+      float per_round[4][kRounds];
       // a CPI of tens of milliseconds gains nothing from overlapping its
       // short steps: one cold run decides whether to look at all
       c.tune.slabs = 1;
-      const int rounds = cold_run() > 20.f ? 0 : 3;
+      const int rounds = cold_run() > 20.f ? 0 : kRounds;
       for (int round = 0; round < rounds; ++round)
         for (int k = 0; k < 4; ++k) {
           c.tune.slabs = cands[k];
-          if (run_single(p, cube, out) != STAP_OK) continue;   // streams and untimed first run
-          float ms = 0.f;
+          float ms = run_single(p, cube, out) == STAP_OK ? 0.f : kNever;   // streams, untimed run
           for (int r = 0; r < reps && ms < kNever; ++r) {
             const float t = cold_run();
             ms = t >= kNever ? kNever : ms + t;
           }
-          if (ms < best[k]) best[k] = ms;
+          per_round[k][round] = ms;
         }
+      float med[4];
+      for (int k = 0; k < 4; ++k) {
+        med[k] = kNever;
+        if (!rounds) continue;
+        float v[kRounds];
+        for (int r = 0; r < kRounds; ++r) v[r] = per_round[k][r];
+        std::sort(v, v + kRounds);
+        med[k] = v[kRounds / 2];
+      }
       int bk = 0;
       for (int k = 1; k < 4; ++k)
-        if (best[k] < best[bk]) bk = k;
+        if (med[k] < med[bk]) bk = k;
       c.tune.slabs = rounds ? cands[bk] : 1;
     }
     for (size_t j = i; j < p->cpis.size(); ++j)

@@ -115,3 +115,17 @@ def test_streamed_element_cubes_in_chunks_match_the_oracle():
         e_cell, e_norm = power_errors(o.numpy(), ref)
         assert e_norm <= 1e-5 and e_cell <= 1e-3, (e_norm, e_cell)
     plan.close()
+
+
+def test_autotune_keeps_the_front_end_table(tmp_path):
+    """The slab search evicts the L2 by writing the intermediates; the W table
+    stored after them must survive it."""
+    spec = _reduced_spec(ELEM, 4)
+    W = oracle.subarray_weights(ELEM.n_chan, 4)
+    x = _dev(synth.make_cube(ELEM))
+    plan = stap.Plan(spec.dims(), front_end=W)
+    y = plan.reduce_channels(x).clone()
+    out = torch.empty(plan.shapes()["out"], dtype=torch.float32, device="cuda")
+    plan.autotune(y, out, cache_path=str(tmp_path / "tune.json"), force=True)
+    assert torch.equal(plan.reduce_channels(x), y)
+    plan.close()
