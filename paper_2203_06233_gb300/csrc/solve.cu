@@ -1147,7 +1147,8 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
         if (live)
 #pragma unroll
           for (int q = 0; q < RPL; ++q)
-            if (li + LR * q < D) Ubf[(size_t)rhs * D + li + LR * q] = to_ff4(u[q]);
+            if (li + LR * q < D)
+              Ubf[(size_t)rhs * D + li + LR * q] = F32F ? to_ff4_cvt(u[q]) : to_ff4(u[q]);
       } else {
         emit(rsafe, u, live);
       }
