@@ -30,6 +30,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--slabs", type=int, default=0, help="override the tuned range slabs (0 = keep)")
     ap.add_argument("--solver", default="fp64", choices=["fp64", "mixed_ir"])
+    ap.add_argument("--snapshots", default="adjacent", choices=["adjacent", "staggered"])
+    ap.add_argument("--training", default="own", choices=["own", "neighbours"])
     ap.add_argument("--refine", type=int, default=None,
                     help="refinement steps (default: 1 for fp64, 2 for mixed_ir)")
     a = ap.parse_args(argv)
@@ -38,6 +40,10 @@ def main(argv=None):
     prec = stap.STAP_PREC_FP32 if a.precision == "fp32" else stap.STAP_PREC_TF32X3
     solver = stap.STAP_SOLVE_FP64 if a.solver == "fp64" else stap.STAP_SOLVE_MIXED_IR
     refine = a.refine if a.refine is not None else (1 if a.solver == "fp64" else 2)
+    opts = dict(snapshots=stap.STAP_SNAP_PRI_STAGGERED if a.snapshots == "staggered"
+                else stap.STAP_SNAP_ADJACENT_BINS,
+                training=stap.STAP_TRAIN_NEIGHBOURS if a.training == "neighbours"
+                else stap.STAP_TRAIN_OWN_BLOCK)
     elem = None
     if a.workload in synth.ELEMENT_WORKLOADS:
         # element cube through the subarray front end, then the chain
@@ -47,7 +53,7 @@ def main(argv=None):
         W = (np.arange(N)[None, :] // (N // C) == np.arange(C)[:, None]).astype(np.complex128)
         spec = dataclasses.replace(es, n_chan=C)
         plan = stap.Plan(spec.dims(), device=dev, precision=prec, refine_steps=refine, solver=solver,
-                         front_end=W)
+                         front_end=W, **opts)
         elem = synth.make_cube_torch(es, dev)
         cube = plan.reduce_channels(elem)
     else:
@@ -55,7 +61,8 @@ def main(argv=None):
         if isinstance(spec, (list, tuple)):
             raise SystemExit("profile_step runs one-CPI workloads")
         cube = synth.make_cube_torch(spec, dev)
-        plan = stap.Plan(spec.dims(), device=dev, precision=prec, refine_steps=refine, solver=solver)
+        plan = stap.Plan(spec.dims(), device=dev, precision=prec, refine_steps=refine, solver=solver,
+                         **opts)
     out = torch.empty(plan.shapes(0)["out"], dtype=torch.float32, device=dev)
     tuning = plan.autotune(cube, out)
     if a.slabs > 0:
