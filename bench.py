@@ -39,7 +39,7 @@ L2_FLUSH_BYTES = 256 << 20
 # by a hash of the kernel source and the solve kernel the tuning chose
 # (1 register-resident, 2 shared-memory teams, 3 one system per CTA), so that
 # a changed or different kernel reports null until re-measured.
-SOLVE_TRAFFIC = {("79ae3edf10d13113", 1): 35.42e6}
+SOLVE_TRAFFIC = {("ff7d4f537fa26316", 1): 35.32e6}
 SOLVE_KERNELS = {1: "solve_reg_kernel (register-resident FP64 LDL^H, solves, refinement)",
                  2: "solve_kernel (shared-memory FP64 Cholesky teams, solves, refinement)",
                  3: "solve_big_kernel (one system per CTA: FP64 LDL^H, solves, refinement)"}
@@ -102,9 +102,12 @@ class ClockSampler:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to $STAP_CLOCK_LOG_DIR (kept) or the temporary directory
+        d = os.environ.get("STAP_CLOCK_LOG_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"stap_clocks_rank{index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
