@@ -1112,7 +1112,11 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
               const int ic = i < D ? i : D - 1;
               const bool low = ic >= l;
               const double2 a = __ldg(low ? A + (size_t)ic * D + l : A + (size_t)l * D + ic);
-              const double ax = a.x, ay = ic == l ? 0.0 : (low ? a.y : -a.y);   // R[i][l]
+              // R[i][l]: the conjugate above the diagonal by a sign-bit flip (a
+              // negation would be one more FP64-pipe instruction per product)
+              const long long flip = low ? 0LL : (long long)0x8000000000000000ull;
+              const double ax = a.x,
+                           ay = ic == l ? 0.0 : __longlong_as_double(__double_as_longlong(a.y) ^ flip);
               r[q].x = fma(-ax, ul.x, r[q].x);
               r[q].x = fma(ay, ul.y, r[q].x);
               r[q].y = fma(-ax, ul.y, r[q].y);
