@@ -90,11 +90,15 @@ apply_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts, flo
 // stay in registers, while the weights of the CTA's blocks sit in shared
 // memory as [block][s][d].  For each steering vector the thread reads its
 // weights as D/2 broadcast 16-byte loads and does 8 D FMAs: FMA-bound.
-constexpr int kRegCells = 2 * kThreads;     // range cells per CTA
+// 128-thread CTAs: in a one-CPI run the apply of one range slab shares the
+// SMs with the FP64 solves of others, and a smaller CTA takes fewer of a
+// solve's warp slots (registers, shared memory) wherever it lands.
+constexpr int kRegThreads = 128;
+constexpr int kRegCells = 2 * kRegThreads;  // range cells per CTA
 
-// registers: 64 (32 warps per SM) while the snapshots fit, more for larger D
+// registers: 64 while the snapshots fit, more for larger D
 template <int D>
-__global__ void __launch_bounds__(kThreads, D <= 12 ? 4 : (D <= 18 ? 3 : 2))
+__global__ void __launch_bounds__(kRegThreads, D <= 12 ? 8 : (D <= 18 ? 6 : 4))
 apply_reg_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
                  float* __restrict__ out, int C, int K, int R, int ldr, int T, int B, int S) {
   extern __shared__ float4 sm4[];
@@ -155,7 +159,7 @@ cudaError_t launch_apply_reg(const float2* dop, const float2* wts, float* out, i
   cudaError_t e = ensure_smem(apply_reg_kernel<D>, smem, set_bytes);
   if (e != cudaSuccess) return e;
   dim3 grid((R + kRegCells - 1) / kRegCells, K);
-  apply_reg_kernel<D><<<grid, kThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S);
+  apply_reg_kernel<D><<<grid, kRegThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S);
   return cudaGetLastError();
 }
 
