@@ -818,6 +818,10 @@ def main():
     NAME = args.workload
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.gpus != world:
+        ap.error(f"--gpus {args.gpus} but {world} process(es): launch N > 1 GPUs with "
+                 "torch.distributed.run (one process per GPU)")
     if args.impl == "reference":
         run_reference(args)
     elif NAME == "batch":
