@@ -341,8 +341,8 @@ stap_status stap_run_cpi_noalloc(const stap_dims* dims, const stap_options* opt,
  * Doppler bins per covariance CTA (plain precision); lanes per system and
  * warps per CTA of the D <= 32 solve, lanes per right-hand side of the larger
  * solve, and for D = 8, 12 or 16 the register-resident or the shared-memory
- * solve kernel; register-resident or general FP32 apply; for a one-CPI plan, 1, 2, 4
- * or 8 pipelined range slabs of the whole run; for STAP_PREC_TF32X3 plans,
+ * solve kernel; register-resident or general FP32 apply; for a one-CPI plan, 1, 2, 3,
+ * 4, 6 or 8 pipelined range slabs of the whole run; for STAP_PREC_TF32X3 plans,
  * the tensor-core or the FP32 covariance and apply (the FP32 kernels are
  * the more accurate, and at small D the faster).  Every candidate computes
  * the same result except that the apply kernels sum in different orders and

@@ -1092,14 +1092,15 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
         return ms;
       };
       constexpr int kRounds = 7;
-      const int cands[4] = {1, 2, 4, 8};
-      float per_round[4][kRounds];
+      constexpr int kCands = 6;
+      const int cands[kCands] = {1, 2, 3, 4, 6, 8};
+      float per_round[kCands][kRounds];
       // a CPI of tens of milliseconds gains nothing from overlapping its
       // short steps: one cold run decides whether to look at all
       c.tune.slabs = 1;
       const int rounds = cold_run() > 20.f ? 0 : kRounds;
       for (int round = 0; round < rounds; ++round)
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kCands; ++k) {
           c.tune.slabs = cands[k];
           float ms = run_single(p, cube, out) == STAP_OK ? 0.f : kNever;   // streams, untimed run
           for (int r = 0; r < reps && ms < kNever; ++r) {
@@ -1108,8 +1109,8 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
           }
           per_round[k][round] = ms;
         }
-      float med[4];
-      for (int k = 0; k < 4; ++k) {
+      float med[kCands];
+      for (int k = 0; k < kCands; ++k) {
         med[k] = kNever;
         if (!rounds) continue;
         float v[kRounds];
@@ -1118,7 +1119,7 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
         med[k] = v[kRounds / 2];
       }
       int bk = 0;
-      for (int k = 1; k < 4; ++k)
+      for (int k = 1; k < kCands; ++k)
         if (med[k] < med[bk]) bk = k;
       c.tune.slabs = rounds ? cands[bk] : 1;
     }
