@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define STAP_ABI_VERSION 4
+#define STAP_ABI_VERSION 5
 
 typedef enum {
   STAP_OK = 0,
@@ -161,6 +161,19 @@ stap_status stap_plan_workspace_sizes(stap_plan plan, size_t* step_bytes, size_t
  * owned, kept until destroy or the next call of this function).  Uploads the
  * plan's tables on the plan's stream and clears the device status. */
 stap_status stap_plan_set_workspace(stap_plan plan, void* dev_ptr, size_t bytes);
+
+/* Polls of an mbarrier after which a pipeline wait of the tensor-core
+ * kernels (STAP_PREC_TF32X3 covariance and apply) gives up, by default
+ * STAP_DEFAULT_WAIT_POLLS.  A CTA whose wait gave up records a timeout (read
+ * by stap_get_status as STAP_ERR_TIMEOUT), waits for the tensor-core
+ * operations it has in flight (those waits always use the default limit),
+ * frees its tensor memory and exits; that launch's outputs are then
+ * incomplete.  0 makes every pipeline wait give up at once, which exercises
+ * this path on a healthy GPU.  No counterpart in the paper (failure
+ * detection of the device code).  STAP_ERR_INVALID_ARG if max_polls < 0.
+ * Drops a captured batch graph. */
+#define STAP_DEFAULT_WAIT_POLLS 4194304
+stap_status stap_plan_set_wait_limit(stap_plan plan, int32_t max_polls);
 
 /* Change the stream later calls are issued on. */
 stap_status stap_plan_set_stream(stap_plan plan, void* cuda_stream);

@@ -17,8 +17,12 @@
 // one of two shared-memory stages (four 128 x 32 TF32 tiles: Xr hi/lo, Xi
 // hi/lo, in the K-major core-matrix layout), thread 0 issues the 48 MMAs of
 // the chunk and commits them to that stage's mbarrier, and the next chunk is
-// staged into the other stage meanwhile.  All waits are bounded: on expiry
-// the CTA records a timeout in the device status and stops.
+// staged into the other stage meanwhile.  All waits are bounded: a pipeline
+// wait gives up after wait_polls polls (a launch argument, default
+// kDefaultWaitPolls); the CTA then records a timeout in the device status,
+// waits (bounded by kDefaultWaitPolls) for the MMAs it still has in flight,
+// frees its TMEM and stops.  A stage whose wait gave up stays pending, so that
+// final drain covers it.
 #include "snapshots.cuh"
 #include "tcgen05.cuh"
 
@@ -30,13 +34,13 @@ constexpr int kUnroll = 8;                    // staging loads in flight per lan
 constexpr int kKC = 32;                       // cells per chunk (K of one stage)
 constexpr int kTile = 128 * kKC * 4;          // one 128 x 32 TF32 operand tile (16 KB)
 constexpr int kStage = 4 * kTile;             // Xr hi, Xr lo, Xi hi, Xi lo (64 KB)
-constexpr int kWaitIter = 1 << 22;
+constexpr int kWaitIter = kDefaultWaitPolls;    // drain waits before TMEM is freed
 constexpr int kTmemCols = 512;                // 3 x 128 accumulators, rounded up
 
 __global__ void __launch_bounds__(kTcThreads)
 covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K,
                      int ldr, int T, int B, int NB, int G, long long ntiles,
-                     DeviceStatus* __restrict__ status) {
+                     DeviceStatus* __restrict__ status, int wait_polls) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
@@ -84,9 +88,11 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
       const int st = (int)(gch & 1);
       uint8_t* stage = sm + st * kStage;
       if (pending[st]) {  // the MMAs that last read this stage must be done
-        ok = tc::mbar_wait(&mbar[st], parity[st], kWaitIter);
-        parity[st] ^= 1u;
-        pending[st] = false;
+        ok = tc::mbar_wait(&mbar[st], parity[st], wait_polls);
+        if (ok) {
+          parity[st] ^= 1u;
+          pending[st] = false;
+        }
       }
       ok = __syncthreads_and(ok);
       if (!ok) break;
@@ -159,10 +165,12 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
     }
     // all MMAs of this tile done (commits complete in order; drain both stages)
     for (int s2 = 0; s2 < 2; ++s2) {
-      if (pending[s2] && ok) ok = tc::mbar_wait(&mbar[s2], parity[s2], kWaitIter);
-      if (pending[s2]) {
-        parity[s2] ^= 1u;
-        pending[s2] = false;
+      if (pending[s2] && ok) {
+        ok = tc::mbar_wait(&mbar[s2], parity[s2], wait_polls);
+        if (ok) {
+          parity[s2] ^= 1u;
+          pending[s2] = false;
+        }
       }
     }
     ok = __syncthreads_and(ok);
@@ -225,7 +233,8 @@ constexpr int kAStage = 8 * kAX;              // X: re/im x hi/lo, W: re/im x hi
 __global__ void __launch_bounds__(kTcThreads)
 apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
                 float* __restrict__ out, int C, int K, int R, int ldr, int T, int B, int S, int NB,
-                int NP, long long ntiles, DeviceStatus* __restrict__ status) {
+                int NP, long long ntiles, DeviceStatus* __restrict__ status,
+                int wait_polls) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
@@ -271,9 +280,11 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
       const int st = (int)(gch & 1);
       uint8_t* stage = sm + st * kAStage;
       if (pending[st]) {
-        ok = tc::mbar_wait(&mbar[st], parity[st], kWaitIter);
-        parity[st] ^= 1u;
-        pending[st] = false;
+        ok = tc::mbar_wait(&mbar[st], parity[st], wait_polls);
+        if (ok) {
+          parity[st] ^= 1u;
+          pending[st] = false;
+        }
       }
       ok = __syncthreads_and(ok);
       if (!ok) break;
@@ -357,10 +368,12 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
       pending[st] = true;
     }
     for (int s2 = 0; s2 < 2; ++s2) {
-      if (pending[s2] && ok) ok = tc::mbar_wait(&mbar[s2], parity[s2], kWaitIter);
-      if (pending[s2]) {
-        parity[s2] ^= 1u;
-        pending[s2] = false;
+      if (pending[s2] && ok) {
+        ok = tc::mbar_wait(&mbar[s2], parity[s2], wait_polls);
+        if (ok) {
+          parity[s2] ^= 1u;
+          pending[s2] = false;
+        }
       }
     }
     ok = __syncthreads_and(ok);
@@ -404,7 +417,7 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
 }  // namespace
 
 cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int ldr, int T,
-                                 int B, DeviceStatus* status, cudaStream_t s) {
+                                 int B, DeviceStatus* status, cudaStream_t s, int wait_polls) {
   const int D = C * T;
   const int NB = R / B;
   if (NB == 0) return cudaSuccess;
@@ -418,7 +431,8 @@ cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, 
   if (e != cudaSuccess) return e;
   long long blocks = ntiles < 152 ? ntiles : 152;   // one CTA per SM (TMEM and shared memory)
   covariance_tc_kernel<<<(unsigned)blocks, kTcThreads, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, G,
-                                                                    ntiles, status);
+                                                                    ntiles, status,
+                                                                    wait_polls);
   return cudaGetLastError();
 }
 
@@ -430,7 +444,8 @@ bool apply_tc_supported(int B, int S) {
 }
 
 cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, int C, int K, int R,
-                            int ldr, int T, int B, int S, DeviceStatus* status, cudaStream_t s) {
+                            int ldr, int T, int B, int S, DeviceStatus* status, cudaStream_t s,
+                            int wait_polls) {
   const int NB = R / B;
   if (NB == 0) return cudaSuccess;
   if (!apply_tc_supported(B, S) || C * T > 128) return cudaErrorInvalidValue;
@@ -443,7 +458,7 @@ cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, in
   if (e != cudaSuccess) return e;
   long long blocks = ntiles < 152 ? ntiles : 152;
   apply_tc_kernel<<<(unsigned)blocks, kTcThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S, NB, NP,
-                                                               ntiles, status);
+                                                               ntiles, status, wait_polls);
   return cudaGetLastError();
 }
 

@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "stap_internal.cuh"
 
 using stap::DeviceStatus;
@@ -18,6 +20,16 @@ constexpr int kMaxSlabs = 8;     // range slabs of a pipelined single-CPI run
 constexpr double kPi = 3.14159265358979323846264338327950288;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// An NVTX range around the host-side launch of one step's kernel(s), so that
+// profilers and timeline tools label every launch with its step.  With no
+// tool attached the push and pop return at once.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct Cpi {
   stap_dims d{};
@@ -159,6 +171,9 @@ struct stap_plan_s {
   size_t dop_off = 0, cov_off = 0, wts_off = 0;   // run intermediates (sized for the largest CPI)
   size_t ctr_off = 0;                             // neighbour-training matrices (STAP_TRAIN_NEIGHBOURS)
   bool tables_ready = false;
+  // polls before a pipeline wait of the tensor-core kernels gives up
+  // (stap_plan_set_wait_limit)
+  int wait_polls = stap::kDefaultWaitPolls;
 
   // batched runs (n_cpi > 1): forked streams and the captured launch graph
   static constexpr int kSideStreams = 8;
@@ -229,6 +244,7 @@ stap_status ready(stap_plan p, size_t need) {
 
 stap_status do_doppler(stap_plan p, const Cpi& c, const void* cube, void* dop, cudaStream_t st,
                        int nr = -1) {
+  NvtxRange range("stap_doppler");
   const stap_dims& d = c.d;
   return check_launch(stap::launch_doppler(
       static_cast<const float2*>(cube), static_cast<float2*>(dop), p->at<const float>(c.win_off),
@@ -238,6 +254,7 @@ stap_status do_doppler(stap_plan p, const Cpi& c, const void* cube, void* dop, c
 
 stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov, cudaStream_t st,
                           int nr = -1) {
+  NvtxRange range("stap_covariance");
   const stap_dims& d = c.d;
   const int R = nr < 0 ? d.n_range : nr;
   // mixed-precision plans use the tensor cores unless the tuning kept the
@@ -246,7 +263,7 @@ stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov,
     return check_launch(stap::launch_covariance_tc(static_cast<const float2*>(dop),
                                                    static_cast<double2*>(cov), c.Cd, d.n_dop,
                                                    R, d.n_range, c.Td, d.training_block,
-                                                   p->status(), st));
+                                                   p->status(), st, p->wait_polls));
   return check_launch(stap::launch_covariance_fp32(static_cast<const float2*>(dop),
                                                    static_cast<double2*>(cov), c.Cd, d.n_dop,
                                                    R, d.n_range, c.Td, d.training_block, st,
@@ -255,6 +272,7 @@ stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov,
 
 stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts, cudaStream_t st,
                      int nr = -1) {
+  NvtxRange range("stap_solve_weights");
   const stap_dims& d = c.d;
   const long long nb = nr < 0 ? c.NB : nr / d.training_block;
   return check_launch(stap::launch_solve(
@@ -269,6 +287,7 @@ stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts, cuda
 
 stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts, float* out,
                      cudaStream_t st, int nr = -1) {
+  NvtxRange range("stap_apply");
   const stap_dims& d = c.d;
   const int R = nr < 0 ? d.n_range : nr;
   if (p->opt.precision == STAP_PREC_TF32X3 && stap::apply_tc_supported(d.training_block, d.n_steering) &&
@@ -276,7 +295,7 @@ stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts
     return check_launch(stap::launch_apply_tc(static_cast<const float2*>(dop),
                                               static_cast<const float2*>(wts), out, c.Cd,
                                               d.n_dop, R, d.n_range, c.Td, d.training_block,
-                                              d.n_steering, p->status(), st));
+                                              d.n_steering, p->status(), st, p->wait_polls));
   return check_launch(stap::launch_apply(static_cast<const float2*>(dop),
                                          static_cast<const float2*>(wts), out, c.Cd, d.n_dop,
                                          R, d.n_range, c.Td, d.training_block, d.n_steering, st,
@@ -284,6 +303,7 @@ stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts
 }
 
 stap_status do_train(const Cpi& c, const void* cov, void* ctr, cudaStream_t st) {
+  NvtxRange range("stap_train_neighbours");
   return check_launch(stap::launch_train_neighbours(static_cast<const double2*>(cov),
                                                     static_cast<double2*>(ctr), c.d.n_dop, c.NB,
                                                     c.D, st));
@@ -464,6 +484,7 @@ stap_status run_batched(stap_plan p, const void* const* cubes, float* const* out
 // after chunk into it instead; with one chunk of all N elements they give the
 // same bits).
 stap_status reduce_all(stap_plan p, const float2* elem, float2* y, cudaStream_t st) {
+  NvtxRange range("stap_reduce_channels");
   const stap_dims& d = p->cpis[0].d;
   return check_launch(stap::launch_reduce_channels(elem, p->at<const float2>(p->fe_w_off), y,
                                                    p->fe_N, 0, p->fe_N, d.n_chan, d.n_pulses,
@@ -682,6 +703,13 @@ stap_status stap_plan_set_workspace(stap_plan p, void* dev_ptr, size_t bytes) {
   stap_status st = upload_tables(p);
   if (st != STAP_OK) return st;
   p->tables_ready = true;
+  return STAP_OK;
+}
+
+stap_status stap_plan_set_wait_limit(stap_plan p, int32_t max_polls) {
+  if (!p || max_polls < 0) return STAP_ERR_INVALID_ARG;
+  p->wait_polls = max_polls;
+  drop_graph(p);   // captured launches carry the limit
   return STAP_OK;
 }
 

@@ -6,6 +6,8 @@
 // the same cell fall in different banks).
 #pragma once
 
+#include <mutex>
+
 #include "stap_internal.cuh"
 
 namespace stap {
@@ -27,14 +29,23 @@ __device__ __forceinline__ void stage_snapshots(float2* __restrict__ xs, int ld,
 }
 
 // Raise a kernel's dynamic shared-memory limit above the 48 KB default, once
-// per device and size (set_bytes: per-device record of the limit already set).
+// per device and size (set_bytes: per-device record of the limit already set,
+// devices 0..63).  The check and the update run under one lock and only ever
+// raise the limit, so that host threads launching the same kernel with
+// different sizes cannot lower it under each other.
+inline std::mutex& smem_attr_lock() {
+  static std::mutex m;
+  return m;
+}
+
 template <typename F>
 cudaError_t ensure_smem(F* kern, size_t bytes, int* set_bytes /* [64] */) {
   if (bytes <= 48 * 1024) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  dev &= 63;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> guard(smem_attr_lock());
   if (set_bytes[dev] >= (int)bytes) return cudaSuccess;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) set_bytes[dev] = (int)bytes;

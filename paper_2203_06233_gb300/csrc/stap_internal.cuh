@@ -21,6 +21,7 @@ static_assert(sizeof(DeviceStatus) <= 256, "status block must fit its slot");
 constexpr int kMaxD = 128;       // largest snapshot length the solve kernels handle
 constexpr int kSmallMaxD = 32;   // above this, one system per CTA (lanes over rows)
 constexpr int kMaxLogK = 10;     // K <= 1024
+constexpr int kDefaultWaitPolls = STAP_DEFAULT_WAIT_POLLS;   // mbarrier polls before a bounded wait gives up
 
 // Launch choices the autotuner can make for one CPI shape (0 = the built-in
 // heuristic).  Every choice computes the same result, except that the two FP32
@@ -69,14 +70,17 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
                                    int T, int B, cudaStream_t s, const Tune& t = Tune());
 
 // Same covariance from 3xTF32 tensor-core products (tcgen05), FP32 accumulation.
+// wait_polls: polls before a pipeline wait gives up (kDefaultWaitPolls normally).
 cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int ldr, int T,
-                                 int B, DeviceStatus* status, cudaStream_t s);
+                                 int B, DeviceStatus* status, cudaStream_t s,
+                                 int wait_polls = kDefaultWaitPolls);
 
 // Apply from 3xTF32 tensor-core products; needs B | 128 or 128 | B and at most
 // 128 steering columns per 128-cell tile (apply_tc_supported).
 bool apply_tc_supported(int B, int S);
 cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, int C, int K, int R,
-                            int ldr, int T, int B, int S, DeviceStatus* status, cudaStream_t s);
+                            int ldr, int T, int B, int S, DeviceStatus* status, cudaStream_t s,
+                            int wait_polls = kDefaultWaitPolls);
 
 // FP64 loading, Cholesky, solves, refinement and scaling for nsys systems.
 // cov [nsys][D][D] c128 -> wts [nsys][S][D] c64; steer [S][D] c128.  If

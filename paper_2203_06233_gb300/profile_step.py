@@ -1,7 +1,11 @@
 """Run a few whole-CPI steps of one workload for a profiler.
 
     python -m paper_2203_06233_gb300.profile_step --workload standard --steps 5
-    ncu --profile-from-start off ... python -m paper_2203_06233_gb300.profile_step ...
+    ncu --clock-control none --profile-from-start off -k regex:<kernel> -c 1 \
+        python -m paper_2203_06233_gb300.profile_step ...
+
+(--clock-control none leaves the GPU's clocks alone; capture one kernel and a
+few launches at a time.)
 
 Builds the plan, takes the launch choices from the autotune cache (timing them
 on the device when the cache lacks the shape), warms up, and then runs

@@ -45,10 +45,13 @@ EXPORTED = (
     "stap_run_cpi", "stap_get_status", "stap_status_string", "stap_abi_version",
     "stap_run_cpi_noalloc", "stap_plan_batch_bytes", "stap_plan_autotune", "stap_plan_get_tuning",
     "stap_plan_set_tuning", "stap_train_neighbours", "stap_plan_stream_bytes", "stap_run_stream",
-    "stap_plan_set_front_end", "stap_reduce_channels",
+    "stap_plan_set_front_end", "stap_reduce_channels", "stap_plan_set_wait_limit",
 )
 
 STAP_TUNING_LEN = 9
+
+# mbarrier polls before a tensor-core pipeline wait gives up (default)
+STAP_DEFAULT_WAIT_POLLS = 4194304
 
 # size of the library-owned scratch array used by stap_run_cpi_noalloc
 STAP_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -94,6 +97,7 @@ def lib():
             L.stap_plan_workspace_sizes.argtypes = [vp, ctypes.POINTER(sz), ctypes.POINTER(sz)]
             L.stap_plan_set_workspace.argtypes = [vp, vp, sz]
             L.stap_plan_set_stream.argtypes = [vp, vp]
+            L.stap_plan_set_wait_limit.argtypes = [vp, i32]
             L.stap_plan_set_steering.argtypes = [vp, i32, vp]
             L.stap_plan_destroy.argtypes = [vp]
             L.stap_doppler.argtypes = [vp, vp, vp]
@@ -229,6 +233,10 @@ def stap_plan_set_workspace(plan, workspace: torch.Tensor):
     nbytes = workspace.numel() * workspace.element_size()
     _check(lib().stap_plan_set_workspace(plan, ctypes.c_void_p(workspace.data_ptr()), nbytes),
            "stap_plan_set_workspace")
+
+
+def stap_plan_set_wait_limit(plan, max_polls: int):
+    _check(lib().stap_plan_set_wait_limit(plan, int(max_polls)), "stap_plan_set_wait_limit")
 
 
 def stap_plan_set_stream(plan, stream=None):
@@ -564,6 +572,10 @@ class Plan:
         except OSError:
             pass
         return result
+
+    def set_wait_limit(self, max_polls: int = STAP_DEFAULT_WAIT_POLLS):
+        """Polls after which a tensor-core pipeline wait gives up (0: at once)."""
+        stap_plan_set_wait_limit(self.handle, max_polls)
 
     def set_steering(self, steer, cpi: int = 0):
         self._sync_stream()

@@ -6,6 +6,26 @@ from paper_2203_06233_gb300 import synth
 
 EPS32 = 2.0 ** -24          # unit roundoff of FP32
 
+# Worst cell of the plain FP32 path, |P - P_ref| / max(P_ref, median P_ref),
+# for D <= 12 (grown by (D + 2)/14 above).  No FP32 path reaches 1e-5 in every
+# cell: the FP32 Doppler output, the complex64 weights and the FP32 apply
+# alone leave 5.9e-5 in the worst cell of the standard CPI (measured by feeding
+# the FP64 oracle those roundings); the bar sits at about 5x that floor.
+PLAIN_CELL_BAR = 1e-3
+
+# The mixed-precision contraction modes (tensor-core covariance and apply,
+# FP64 solve), as (test id, stap precision value).
+MIXED_PRECISIONS = [("tf32x3", 2)]
+
+# Worst cell of the mixed path, |P - P_ref| / max(P_ref, median P_ref), for
+# D <= 12 (grown by (D + 2)/14 above, as the normwise bars).  The mixed
+# contractions leave a relative error of about 2^-21 in each product (against
+# the plain path's error-free covariance); the plain path's floor study put a
+# complex64 rounding of the covariance (2^-24) at 8.0e-4 in the worst cell of
+# the standard CPI, so 2^3 x 8.0e-4 = 6.4e-3 is the scale of the mixed
+# path's worst cell, and the bar sits at about 1.5x that.
+MIXED_CELL_BAR = 1e-2
+
 
 def to_np(t):
     return t.detach().cpu().numpy()

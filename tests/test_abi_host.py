@@ -27,7 +27,7 @@ def test_library_loads_and_exports_every_declared_symbol():
     for name in declared:
         assert hasattr(L, name), f"{name} declared in stap.h but not exported"
     assert set(declared) == set(stap.EXPORTED)
-    assert stap.stap_abi_version() == 4
+    assert stap.stap_abi_version() == 5
 
 
 def _create(dims, opts=None):
@@ -273,3 +273,14 @@ def test_status_strings():
         s = stap.status_string(code)
         assert s and s != "unknown status"
     assert stap.status_string(99) == "unknown status"
+
+
+def test_wait_limit_is_validated_without_cuda():
+    L = stap.lib()
+    code, h, _ = _create(GOOD)
+    assert code == 0
+    assert L.stap_plan_set_wait_limit(h, -1) == stap.STAP_ERR_INVALID_ARG
+    assert L.stap_plan_set_wait_limit(h, 0) == stap.STAP_OK
+    assert L.stap_plan_set_wait_limit(h, stap.STAP_DEFAULT_WAIT_POLLS) == stap.STAP_OK
+    assert L.stap_plan_set_wait_limit(None, 1) == stap.STAP_ERR_INVALID_ARG
+    stap.stap_plan_destroy(h)

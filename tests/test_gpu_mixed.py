@@ -81,3 +81,34 @@ def test_mixed_apply_parity(spec):
     bound = 2 * np.abs(y) * g + g * g + 2 * EPS32 * np.abs(y) ** 2
     viol = np.abs(out - ref) > bound
     assert not viol.any(), (int(viol.sum()), float(np.max(np.abs(out - ref) - bound)))
+
+
+@pytest.mark.parametrize("step", ["covariance", "apply"])
+def test_pipeline_wait_limit_reports_timeout_and_next_call_runs_clean(step):
+    """With a pipeline wait limit of 0 polls every tensor-core CTA gives up at
+    its first wait on an MMA commit: it records the timeout, drains the MMAs it
+    issued (with the default limit), frees its TMEM and exits.  The host reads
+    STAP_ERR_TIMEOUT, the status is then clear, and with the default limit
+    restored the same call gives the result of a fresh plan.  Nothing here
+    waits on something that never happens: the MMAs complete normally, the
+    waits just stop looking early."""
+    spec = synth.CPISpec(16, 32, 64, 256, 4, 128, 8, cnr_db=40.0, seed=14)   # D = 64
+    d = oracle.Dims(*spec.dims())
+    dop = oracle.doppler(d, synth.make_cube(spec)).astype(np.complex64)
+    w, _, _ = oracle.weights(d, oracle.covariance(d, dop))
+    dop_d = torch.from_numpy(dop).cuda()
+    w_d = torch.from_numpy(w.astype(np.complex64)).cuda()
+    fresh = _plan(spec)
+    want = fresh.covariance(dop_d) if step == "covariance" else fresh.apply(dop_d, w_d)
+    assert fresh.status() == (stap.STAP_OK, 0)
+    plan = _plan(spec)
+    plan.set_wait_limit(0)
+    plan.covariance(dop_d) if step == "covariance" else plan.apply(dop_d, w_d)
+    assert plan.status()[0] == stap.STAP_ERR_TIMEOUT
+    assert plan.status() == (stap.STAP_OK, 0)          # read and cleared
+    plan.set_wait_limit()                               # the default limit again
+    got = plan.covariance(dop_d) if step == "covariance" else plan.apply(dop_d, w_d)
+    assert plan.status() == (stap.STAP_OK, 0)
+    assert torch.equal(got, want)
+    with pytest.raises(stap.StapError):
+        plan.set_wait_limit(-1)
