@@ -51,17 +51,35 @@ typedef enum {
 } stap_status;
 
 /* Arithmetic of the contraction steps (Doppler, covariance, apply).  The
- * factorisation and the triangular solves follow stap_solver. */
+ * factorisation and the triangular solves follow stap_solver.  The mixed
+ * precisions put the covariance (statement U, Sec. 4.2) and the apply on the
+ * tensor cores as split products with FP32 accumulation; the Doppler
+ * transform stays the FP32 FFT.  Each product of two values is formed from
+ * pieces that the values are split into:
+ *   TF32X3       x = hi + lo (TF32); hi*hi + hi*lo + lo*hi: about 2^-21
+ *                relative per product;
+ *   BF16X3       x = hi + mid + lo (BF16, each the rounding of what the
+ *                earlier pieces leave); the six products of pieces whose
+ *                orders sum to at most 2: about 2^-24 relative per product;
+ *   FP16_SCALED  per-block scaling: every value of a block (one covariance
+ *                system, i.e. one Doppler bin and range block; the snapshots
+ *                of one 128-cell apply tile; one weight vector) is multiplied
+ *                by the power of two that brings the block's largest
+ *                magnitude into [2^14, 2^15); then x 2^e = hi + lo (FP16);
+ *                hi*hi + hi*lo + lo*hi, the scales removed exactly afterwards:
+ *                about 2^-21 relative to the block's largest magnitude.
+ * The tensor-core apply needs B | 128 or 128 | B and at most 256 real weight
+ * rows (2 per steering vector and block) per 128-cell tile, and falls back
+ * to the FP32 apply otherwise; stap_plan_autotune keeps the FP32 kernel of a
+ * step where that is faster (small D). */
 typedef enum {
-  STAP_PREC_FP32 = 0,  /* FP32 FFT; covariance accumulated error-free in FP32
-                          pairs (two-product / compensated sum); FP32 apply */
-  STAP_PREC_TF32X3 = 2 /* mixed: covariance and apply from 3xTF32 tensor-core
-                          products (hi*hi + hi*lo + lo*hi) with FP32
-                          accumulation; the apply falls back to FP32 when
-                          neither B divides 128 nor 128 divides B, or a 128-cell
-                          tile needs more than 128 steering columns, and
-                          stap_plan_autotune keeps the FP32 kernel of a step
-                          where that is faster (small D) */
+  STAP_PREC_FP32 = 0,        /* FP32 FFT; covariance accumulated error-free in
+                                FP32 pairs (two-product / compensated sum); FP32
+                                apply */
+  STAP_PREC_BF16X3 = 1,      /* mixed: BF16 three-piece split, 6 products */
+  STAP_PREC_TF32X3 = 2,      /* mixed: TF32 two-piece split, 3 products */
+  STAP_PREC_FP16_SCALED = 3  /* mixed: FP16 two-piece split with per-block
+                                power-of-two scaling, 3 products */
 } stap_precision;
 
 /* Arithmetic of the weight solve (diagonal load, factorisation, substitutions,

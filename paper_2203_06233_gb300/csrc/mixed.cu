@@ -1,58 +1,185 @@
-// Mixed-precision contractions on the tensor cores (tcgen05, kind::tf32).
+// Mixed-precision contractions on the tensor cores (tcgen05): the covariance
+// (statement U of the paper's STAP kernel, Sec. 4.2) and the weight
+// application, as split products with FP32 accumulation in TMEM.  Three
+// arithmetics (stap_precision):
+//   TF32X3  kind::tf32.  x = hi + lo, hi = tf32(x), lo = tf32(x - hi);
+//           products hi*hi + hi*lo + lo*hi (about 2^-21 relative each).
+//   BF16X3  kind::f16 on bf16.  x = hi + mid + lo, each piece the bf16
+//           rounding of what the earlier pieces leave (x - hi and
+//           x - hi - mid are exact in FP32); the six products whose piece
+//           orders sum to at most 2 (hi*hi, hi*mid, mid*hi, hi*lo, mid*mid,
+//           lo*hi), about 2^-24 relative each.
+//   FP16S   kind::f16 on fp16 with per-block scaling.  Every value of a
+//           block (one covariance system; one apply tile of 128 cells, and
+//           each weight vector) is multiplied by one power of two 2^e that
+//           brings the block's largest magnitude into [2^14, 2^15), well
+//           inside fp16's range; then x 2^e = hi + lo (fp16 pieces, about 22
+//           significant bits down to 2^-18 of the block maximum) and the
+//           products are hi*hi + hi*lo + lo*hi.  The epilogue removes the
+//           scales exactly (powers of two).
 //
-// Covariance per (Doppler bin, range block), R = (1/B) X X^H with X the D x B
-// snapshot tile, as three real accumulators in TMEM:
-//   Re R = Xr Xr^T + Xi Xi^T,   Im R = Xi Xr^T - Xr Xi^T
-// (accumulators A = Xr Xr^T + Xi Xi^T, Bm = Xi Xr^T, Cm = Xr Xi^T; Im R =
-// Bm - Cm in the epilogue).  Every product is a 3xTF32 split, hi*hi + hi*lo +
-// lo*hi with hi = tf32(v), lo = tf32(v - hi), accumulated in FP32 by the
-// tensor core: about 2^-21 relative per product instead of TF32's 2^-11.
-// The M = N = 128 tile holds floor(128 / D) systems on its diagonal (rows and
-// columns g*D .. g*D + D - 1 belong to system g; off-diagonal blocks are
-// never read), so D up to 128 needs no second tile.  Thread i of the CTA owns
-// TMEM lane i, i.e. row i of all three accumulators, so the epilogue forms
-// its row of R without any exchange.
+// Covariance.  R = (1/B) X X^H per (Doppler bin, range block) with X the
+// D x B snapshot tile, X = Xr + j Xi.  The operand rows are stacked as
+// Y = [Xr ; Xi] for G = floor(128 / D8) systems at once (D8 = D rounded up
+// to 8; rows of entries a >= D are zero): rows 0 .. G D8 - 1 hold Xr of the
+// G systems, rows G D8 .. 2 G D8 - 1 their Xi.  Two MMAs per product and K
+// step, both with M = 128 and N = 2 G D8 (<= 256), B = Y:
+//   top = Xr Y^T  (A = rows 0 .. 127)       -> [Xr Xr^T | Xr Xi^T]
+//   bot = Xi Y^T  (A = rows G D8 .. +127)    -> [Xi Xr^T | Xi Xi^T]
+// so TMEM lane i (entry a of system g) holds everything its row of R needs:
+//   Re R[a][l] = XrXr[a][l] + XiXi[a][l],  Im R[a][l] = XiXr[a][l] - XrXi[a][l].
+// Only the blocks between different systems (G > 1) are computed and not
+// used.  Each snapshot element is loaded once, split once and stored once
+// per piece (the B operand is the A operand's own rows).  Thread a writes
+// R[a][l] for l >= a as conj into row l, column a, so a warp's stores of one
+// output row are contiguous; the full Hermitian form (the ABI call) mirrors
+// the same value into row a, so it is Hermitian bit for bit.
 //
-// Pipeline per CTA (128 threads): the B cells are staged in chunks of 32 into
-// one of two shared-memory stages (four 128 x 32 TF32 tiles: Xr hi/lo, Xi
-// hi/lo, in the K-major core-matrix layout), thread 0 issues the 48 MMAs of
-// the chunk and commits them to that stage's mbarrier, and the next chunk is
-// staged into the other stage meanwhile.  All waits are bounded: a pipeline
-// wait gives up after wait_polls polls (a launch argument, default
-// kDefaultWaitPolls); the CTA then records a timeout in the device status,
-// waits (bounded by kDefaultWaitPolls) for the MMAs it still has in flight,
-// frees its TMEM and stops.  A stage whose wait gave up stays pending, so that
-// final drain covers it.
+// Apply.  out[s][k][r] = |w_{k,b(r),s}^H x_{k,r}|^2 per tile of 128 range
+// cells of one bin: M = 128 cells, K = 2 D (the snapshot's re/im pairs in
+// memory order), N = two rows per (block j, steering s) of the tile:
+//   [wr_0, wi_0, wr_1, wi_1, ...] -> Re y,  [-wi_0, wr_0, -wi_1, wr_1, ...] -> Im y.
+// One accumulator; lane m (cell r0 + m) reads the columns of its own block.
+//
+// Pipeline per CTA (256 threads, persistent over tiles): the operand chunk
+// is staged into one of two shared-memory stages (K-major core matrices, no
+// swizzle) by all threads, thread 0 issues the chunk's MMAs and commits them
+// to that stage's mbarrier, and the next chunk is staged into the other
+// stage meanwhile.  Waits are bounded: a pipeline wait gives up after
+// wait_polls polls; the CTA then records a timeout, waits (bounded by
+// kDefaultWaitPolls) for the MMAs it still has in flight, frees its TMEM and
+// stops.  A stage whose wait gave up stays pending, so that drain covers it.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "df64.cuh"
 #include "snapshots.cuh"
 #include "tcgen05.cuh"
 
 namespace stap {
 namespace {
 
-constexpr int kTcThreads = 256;              // 8 warps stage; warps 0-3 own the TMEM lanes
-constexpr int kUnroll = 8;                    // staging loads in flight per lane
-constexpr int kKC = 32;                       // cells per chunk (K of one stage)
-constexpr int kTile = 128 * kKC * 4;          // one 128 x 32 TF32 operand tile (16 KB)
-constexpr int kStage = 4 * kTile;             // Xr hi, Xr lo, Xi hi, Xi lo (64 KB)
-constexpr int kWaitIter = kDefaultWaitPolls;    // drain waits before TMEM is freed
-constexpr int kTmemCols = 512;                // 3 x 128 accumulators, rounded up
+enum { kTF32X3 = 0, kBF16X3 = 1, kFP16S = 2 };
 
-__global__ void __launch_bounds__(kTcThreads)
-covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K,
-                     int ldr, int T, int B, int NB, int G, long long ntiles,
-                     DeviceStatus* __restrict__ status, int wait_polls) {
+template <int PREC>
+struct Fmt;
+template <>
+struct Fmt<kTF32X3> {
+  static constexpr int NPC = 2, ESZ = 4, KI = 8, NPROD = 3;
+};
+template <>
+struct Fmt<kBF16X3> {
+  static constexpr int NPC = 3, ESZ = 2, KI = 16, NPROD = 6;
+};
+template <>
+struct Fmt<kFP16S> {
+  static constexpr int NPC = 2, ESZ = 2, KI = 16, NPROD = 3;
+};
+
+// pieces (A, B) of the products kept, leading product first
+__device__ __forceinline__ int prod_a(int i) { return i < 3 ? (i == 2 ? 1 : 0) : (i == 3 ? 0 : (i == 4 ? 1 : 2)); }
+__device__ __forceinline__ int prod_b(int i) { return i < 3 ? (i == 1 ? 1 : 0) : (i == 3 ? 2 : (i == 4 ? 1 : 0)); }
+
+constexpr int kThreads = 256;                 // 8 warps stage; warp w reads TMEM lanes 32 (w % 4) ..
+constexpr int kUnroll = 4;                    // staging units in flight per lane
+constexpr int kWaitIter = kDefaultWaitPolls;  // drain waits before TMEM is freed
+
+// ---- splitting ---------------------------------------------------------------
+
+// TF32 pieces of one value
+__device__ __forceinline__ void split_tf32(float x, uint32_t (&w)[2]) {
+  w[0] = tc::to_tf32(x);
+  w[1] = tc::to_tf32(x - __uint_as_float(w[0]));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+__device__ __forceinline__ uint32_t pack_f16(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+// bf16 pieces hi, mid, lo of a pair (a in the low half of each word)
+__device__ __forceinline__ void split_bf16(float a, float b, uint32_t (&w)[3]) {
+  const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
+  const float ar = a - __bfloat162float(ah), br = b - __bfloat162float(bh);   // exact
+  const __nv_bfloat16 am = __float2bfloat16_rn(ar), bm = __float2bfloat16_rn(br);
+  const float ar2 = ar - __bfloat162float(am), br2 = br - __bfloat162float(bm);   // exact
+  w[0] = pack_bf16(ah, bh);
+  w[1] = pack_bf16(am, bm);
+  w[2] = pack_bf16(__float2bfloat16_rn(ar2), __float2bfloat16_rn(br2));
+}
+
+// fp16 pieces hi, lo of a pair already scaled into fp16's range
+__device__ __forceinline__ void split_f16(float a, float b, uint32_t (&w)[2]) {
+  const __half ah = __float2half_rn(a), bh = __float2half_rn(b);
+  w[0] = pack_f16(ah, bh);
+  w[1] = pack_f16(__float2half_rn(a - __half2float(ah)), __float2half_rn(b - __half2float(bh)));
+}
+
+// Power of two 2^e with m 2^e in [2^14, 2^15) for a block maximum m (1 for a
+// zero or non-finite maximum; non-finite inputs then propagate).
+__device__ __forceinline__ float block_scale(float m) {
+  if (!(m > 0.f) || !isfinite(m)) return 1.f;
+  int E = 0;
+  frexpf(m, &E);              // m = f 2^E, f in [1/2, 1)
+  int e = 15 - E;
+  e = e < -126 ? -126 : (e > 127 ? 127 : e);
+  return ldexpf(1.f, e);
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <int PREC>
+__device__ __forceinline__ void issue_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, bool acc) {
+  if constexpr (PREC == kTF32X3)
+    tc::mma_tf32(d, a, b, idesc, acc);
+  else
+    tc::mma_f16(d, a, b, idesc, acc);
+}
+
+template <int PREC>
+__host__ __device__ constexpr uint32_t idesc_for(int N) {
+  return PREC == kTF32X3 ? tc::idesc_tf32(128, N) : tc::idesc_f16(128, N, PREC == kBF16X3);
+}
+
+// ---- covariance -----------------------------------------------------------------
+
+constexpr int kCovRB = 128;                   // bytes of one operand row per chunk (8 core matrices)
+constexpr int kCovPiece = 256 * kCovRB;       // 256 rows of one piece (32 KB)
+
+template <int PREC>
+constexpr size_t cov_smem() { return 2 * (size_t)Fmt<PREC>::NPC * kCovPiece; }
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads)
+covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K,
+                      int ldr, int T, int B, int NB, int D8, int G, long long ntiles, int lower_only,
+                      DeviceStatus* __restrict__ status, int wait_polls) {
+  using F = Fmt<PREC>;
+  constexpr int KC = kCovRB / F::ESZ;        // cells per chunk: 32 (tf32) or 64 (16-bit)
+  constexpr int SBO = 8 * kCovRB;            // bytes between 8-row groups
+  constexpr int STAGE = F::NPC * kCovPiece;
+  constexpr int CPW = 16 / F::ESZ;           // cells per core-matrix row
+  constexpr int CPL = CPW / 4;               // cells per lane in a staging unit
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
-  __shared__ long long rowbase[128];          // dop offset of each tile row's range block, or -1
+  __shared__ long long rowbase[128];          // dop offset of Xr/Xi row p, or -1
+  __shared__ float sscale[128];               // per system scale (FP16S)
+  __shared__ int smax[128];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int D = C * T;
-  const int rows = G * D;
+  const int GD = G * D8;
   const long long nsys = (long long)K * NB;
-  const int nchunks = (B + kKC - 1) / kKC;
+  const int nchunks = (B + KC - 1) / KC;
+  const int units = GD;                      // (GD / 8) row groups x 8 core matrices along K
 
-  for (int i = tid; i < 2 * kStage / 4; i += kTcThreads) reinterpret_cast<uint32_t*>(sm)[i] = 0u;
-  if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+  for (int i = tid; i < 2 * STAGE / 4; i += kThreads) reinterpret_cast<uint32_t*>(sm)[i] = 0u;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
   if (tid == 0) {
     tc::mbar_init(&mbar[0], 1);
     tc::mbar_init(&mbar[1], 1);
@@ -61,8 +188,7 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
-  const uint32_t accA = tmem, accB = tmem + 128, accC = tmem + 256;
-  const uint32_t idesc = tc::idesc_tf32(128, 128);
+  const uint32_t idesc = idesc_for<PREC>(2 * GD);
   uint32_t parity[2] = {0u, 0u};
   bool pending[2] = {false, false};
   bool ok = true;
@@ -70,23 +196,38 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
 
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const long long sys0 = tile * G;
-    if (tid < 128) {  // row p = g*D + i: snapshot entry i of system sys0 + g
+    if (tid < GD) {  // row p = g D8 + a: entry a of system sys0 + g
       long long base = -1;
-      if (tid < rows) {
-        const int g = tid / D, i = tid - g * D;
-        const long long sys = sys0 + g;
-        if (sys < nsys) {
-          const int k = (int)(sys / NB), b = (int)(sys - (long long)k * NB);
-          const int t = i / C, c = i - t * C;
-          const int kk = wrap_bin(k + t - T / 2, K);
-          base = ((long long)c * K + kk) * ldr + (long long)b * B;
-        }
+      const int g = tid / D8, a = tid - g * D8;
+      const long long sys = sys0 + g;
+      if (a < D && sys < nsys) {
+        const int k = (int)(sys / NB), b = (int)(sys - (long long)k * NB);
+        const int t = a / C, c = a - t * C;
+        base = ((long long)c * K + wrap_bin(k + t - T / 2, K)) * ldr + (long long)b * B;
       }
       rowbase[tid] = base;
     }
+    if (PREC == kFP16S && tid < G) smax[tid] = 0;
+    __syncthreads();
+    if constexpr (PREC == kFP16S) {   // each system's largest |re|, |im| over its B cells
+      for (int p = warp; p < GD; p += kThreads / 32) {
+        const long long base = rowbase[p];
+        float m = 0.f;
+        if (base >= 0)
+          for (int j = lane; j < B; j += 32) {
+            const float2 v = __ldg(dop + base + j);
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+          }
+        m = warp_max(m);
+        if (lane == 0) atomicMax(&smax[p / D8], __float_as_int(m));   // m >= 0: int order
+      }
+      __syncthreads();
+      if (tid < G) sscale[tid] = block_scale(__int_as_float(smax[tid]));
+      __syncthreads();
+    }
     for (int ch = 0; ch < nchunks && ok; ++ch, ++gch) {
       const int st = (int)(gch & 1);
-      uint8_t* stage = sm + st * kStage;
+      uint8_t* stage = sm + st * STAGE;
       if (pending[st]) {  // the MMAs that last read this stage must be done
         ok = tc::mbar_wait(&mbar[st], parity[st], wait_polls);
         if (ok) {
@@ -96,37 +237,58 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
       }
       ok = __syncthreads_and(ok);
       if (!ok) break;
-      // stage cells c0 .. c0+31: one core matrix (8 rows x 4 cells) per warp
-      // pass, kUnroll loads in flight per lane before the conversions
-      const int c0 = ch * kKC;
-      const int ncm = (rows + 7) / 8 * (kKC / 4);
-      constexpr int NWS = kTcThreads / 32;
-      for (int cb0 = warp; cb0 < ncm; cb0 += NWS * kUnroll) {
-        float2 xv[kUnroll];
+      // stage cells c0 .. c0 + KC - 1: a unit is one core matrix (8 rows x 16
+      // bytes) of the Xr rows and the matching one of the Xi rows; lane l
+      // takes row 8 rg + l/4 and CPL cells, and writes one 32-bit word per
+      // piece into each
+      const int c0 = ch * KC;
+      for (int u0 = warp; u0 < units; u0 += (kThreads / 32) * kUnroll) {
+        float2 v[kUnroll][CPL];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const int cmi = cb0 + u * NWS;
-          xv[u] = make_float2(0.f, 0.f);
-          if (cmi < ncm) {
-            const int p = (cmi >> 3) * 8 + (lane >> 2), j = (cmi & 7) * 4 + (lane & 3);
-            const long long base = rowbase[p];
-            if (base >= 0 && c0 + j < B) xv[u] = __ldg(dop + base + c0 + j);
-          }
+        for (int uu = 0; uu < kUnroll; ++uu) {
+          const int unit = u0 + uu * (kThreads / 32);
+          const int p = (unit >> 3) * 8 + (lane >> 2);
+          const int j = c0 + (unit & 7) * CPW + (lane & 3) * CPL;
+          const long long base = unit < units ? rowbase[p] : -1;
+#pragma unroll
+          for (int cc = 0; cc < CPL; ++cc)
+            v[uu][cc] = (base >= 0 && j + cc < B) ? __ldg(dop + base + j + cc) : make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const int cmi = cb0 + u * NWS;
-          if (cmi < ncm) {
-            const int p = (cmi >> 3) * 8 + (lane >> 2), j = (cmi & 7) * 4 + (lane & 3);
-            const float2 x = xv[u];
-            const uint32_t rh = tc::to_tf32(x.x), ih = tc::to_tf32(x.y);
-            const uint32_t rl = tc::to_tf32(x.x - __uint_as_float(rh));
-            const uint32_t il = tc::to_tf32(x.y - __uint_as_float(ih));
-            const int off = tc::cm_offset(p, j, kKC);
-            *reinterpret_cast<uint32_t*>(stage + 0 * kTile + off) = rh;
-            *reinterpret_cast<uint32_t*>(stage + 1 * kTile + off) = rl;
-            *reinterpret_cast<uint32_t*>(stage + 2 * kTile + off) = ih;
-            *reinterpret_cast<uint32_t*>(stage + 3 * kTile + off) = il;
+        for (int uu = 0; uu < kUnroll; ++uu) {
+          const int unit = u0 + uu * (kThreads / 32);
+          if (unit >= units) continue;
+          const int rg = unit >> 3, cmk = unit & 7;
+          const int off = rg * SBO + cmk * 128 + (lane >> 2) * 16 + (lane & 3) * 4;
+          const int offi = off + (GD / 8) * SBO;
+          if constexpr (PREC == kTF32X3) {
+            uint32_t wr[2], wi[2];
+            split_tf32(v[uu][0].x, wr);
+            split_tf32(v[uu][0].y, wi);
+#pragma unroll
+            for (int pc = 0; pc < 2; ++pc) {
+              *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + off) = wr[pc];
+              *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + offi) = wi[pc];
+            }
+          } else if constexpr (PREC == kBF16X3) {
+            uint32_t wr[3], wi[3];
+            split_bf16(v[uu][0].x, v[uu][1].x, wr);
+            split_bf16(v[uu][0].y, v[uu][1].y, wi);
+#pragma unroll
+            for (int pc = 0; pc < 3; ++pc) {
+              *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + off) = wr[pc];
+              *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + offi) = wi[pc];
+            }
+          } else {
+            const float sc = sscale[((unit >> 3) * 8 + (lane >> 2)) / D8];
+            uint32_t wr[2], wi[2];
+            split_f16(v[uu][0].x * sc, v[uu][1].x * sc, wr);
+            split_f16(v[uu][0].y * sc, v[uu][1].y * sc, wi);
+#pragma unroll
+            for (int pc = 0; pc < 2; ++pc) {
+              *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + off) = wr[pc];
+              *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + offi) = wi[pc];
+            }
           }
         }
       }
@@ -136,28 +298,19 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
       tc::fence_after_sync();
       if (tid == 0) {
         const uint32_t base = tc::smem_u32(stage);
-        const uint32_t rh = base, rl = base + kTile, ih = base + 2 * kTile, il = base + 3 * kTile;
-        constexpr uint32_t LBO = 128, SBO = 128 * (kKC / 4);
-        for (int ks = 0; ks < kKC / 8; ++ks) {
+        const uint32_t bot = (uint32_t)(GD / 8) * SBO;
+#pragma unroll
+        for (int ks = 0; ks < KC / F::KI; ++ks) {
           const uint32_t o = ks * 256;
-          const bool first = (ch == 0 && ks == 0);
-          const uint64_t drh = tc::smem_desc(rh + o, LBO, SBO), drl = tc::smem_desc(rl + o, LBO, SBO);
-          const uint64_t dih = tc::smem_desc(ih + o, LBO, SBO), dil = tc::smem_desc(il + o, LBO, SBO);
-          // A += Xr Xr^T + Xi Xi^T
-          tc::mma_tf32(accA, drh, drh, idesc, !first);
-          tc::mma_tf32(accA, drh, drl, idesc, true);
-          tc::mma_tf32(accA, drl, drh, idesc, true);
-          tc::mma_tf32(accA, dih, dih, idesc, true);
-          tc::mma_tf32(accA, dih, dil, idesc, true);
-          tc::mma_tf32(accA, dil, dih, idesc, true);
-          // Bm += Xi Xr^T
-          tc::mma_tf32(accB, dih, drh, idesc, !first);
-          tc::mma_tf32(accB, dih, drl, idesc, true);
-          tc::mma_tf32(accB, dil, drh, idesc, true);
-          // Cm += Xr Xi^T
-          tc::mma_tf32(accC, drh, dih, idesc, !first);
-          tc::mma_tf32(accC, drh, dil, idesc, true);
-          tc::mma_tf32(accC, drl, dih, idesc, true);
+#pragma unroll
+          for (int pr = 0; pr < F::NPROD; ++pr) {
+            const uint32_t pa = base + prod_a(pr) * kCovPiece + o;
+            const uint32_t pb = base + prod_b(pr) * kCovPiece + o;
+            const bool acc = !(ch == 0 && ks == 0 && pr == 0);
+            const uint64_t db = tc::smem_desc(pb, 128, SBO);
+            issue_mma<PREC>(tmem, tc::smem_desc(pa, 128, SBO), db, idesc, acc);
+            issue_mma<PREC>(tmem + 256, tc::smem_desc(pa + bot, 128, SBO), db, idesc, acc);
+          }
         }
         tc::mma_commit(&mbar[st]);
       }
@@ -176,28 +329,39 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
     ok = __syncthreads_and(ok);
     if (!ok) break;
     tc::fence_after_sync();
-    // epilogue (warps 0-3): thread tid owns row tid of the tile = row i of system g
-    const int g = tid / D, i = tid - g * D;
-    const long long sys = sys0 + g;
-    const bool mine = tid < 128 && tid < rows && sys < nsys;
-    const float invBf = 1.0f / (float)B;
-    double2* out = cov + (size_t)(mine ? sys : 0) * D * D;
-    const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
-    for (int cb = 0; cb < rows && warp < 4; cb += 8) {   // columns in blocks of 8 (warp-collective)
-      float a[8], bm[8], cm[8];
-      tc::tmem_ld8(accA + lanebase + cb, a);
-      tc::tmem_ld8(accB + lanebase + cb, bm);
-      tc::tmem_ld8(accC + lanebase + cb, cm);
-      if (mine) {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows i of the
+    // tile); warps w and w + 4 take alternate column blocks of 8
+    {
+      const int q4 = warp & 3, hf = warp >> 2;
+      const int i = q4 * 32 + lane;
+      const int g = i / D8, a = i - g * D8;
+      const long long sys = sys0 + g;
+      const bool mine = i < GD && a < D && sys < nsys;
+      const float sc = (PREC == kFP16S && i < GD) ? 1.f / sscale[g] : 1.f;   // exact
+      const float invB = 1.f / (float)B;
+      double2* out = cov + (size_t)(mine ? sys : 0) * D * D;
+      const int gw0 = (q4 * 32) / D8;
+      const int gw1 = min(G - 1, (q4 * 32 + 31) / D8);
+      const uint32_t lb = (uint32_t)(q4 * 32) << 16;
+      for (int gg = gw0; gg <= gw1; ++gg) {
+        for (int cb = hf * 8; cb < D8; cb += 16) {   // warp-uniform bounds
+          float rr[8], ri[8], ir[8], ii[8];
+          tc::tmem_ld8(tmem + lb + gg * D8 + cb, rr);
+          tc::tmem_ld8(tmem + lb + GD + gg * D8 + cb, ri);
+          tc::tmem_ld8(tmem + 256 + lb + gg * D8 + cb, ir);
+          tc::tmem_ld8(tmem + 256 + lb + GD + gg * D8 + cb, ii);
+          if (mine && g == gg) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int col = cb + u;
-          const int l = col - g * D;
-          if (l >= 0 && l <= i && l < D) {        // lower triangle of this system, mirrored
-            const double re = (double)(a[u] * invBf);
-            const double im = (l == i) ? 0.0 : (double)((bm[u] - cm[u]) * invBf);
-            out[(size_t)i * D + l] = make_double2(re, im);
-            if (l != i) out[(size_t)l * D + i] = make_double2(re, -im);
+            for (int u = 0; u < 8; ++u) {
+              const int l = cb + u;
+              if (l >= a && l < D) {   // R[a][l], stored conjugated at [l][a]
+                const float re = (rr[u] + ii[u]) * sc * sc * invB;
+                const float im = l == a ? 0.f : (ir[u] - ri[u]) * sc * sc * invB;
+                const double dre = ff::f2d_exact(re), dim = ff::f2d_exact(im);
+                out[(size_t)l * D + a] = make_double2(dre, -dim);
+                if (!lower_only && l != a) out[(size_t)a * D + l] = make_double2(dre, dim);
+              }
+            }
           }
         }
       }
@@ -213,42 +377,49 @@ covariance_tc_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, 
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-// ---------------------------------------------------------------------------
-// Apply, out[s][k][r] = |w_{k,b(r),s}^H x_{k,r}|^2, as a real GEMM per tile of
-// 128 range cells of one Doppler bin (M = cells, N = steering vectors of the
-// nbt blocks the tile covers, K = D):
-//   Re y = Xr Wr^T + Xi Wi^T,   Im y = Xi Wr^T - Xr Wi^T
-// with accumulators A = Xr Wr^T + Xi Wi^T, Bm = Xi Wr^T, Cm = Xr Wi^T, each a
-// 3xTF32 product.  Column j*S + s of the tile holds steering vector s of the
-// tile's block j; a cell only reads its own block's columns.  K = D goes in
-// double-buffered chunks of 16.  Thread m owns TMEM lane m (cell r0 + m), so
-// the epilogue writes each output row out[s][k][r0 .. r0+127] coalesced.
-constexpr int kAKC = 16;                      // snapshot entries per chunk
-constexpr int kAX = 128 * kAKC * 4;           // one 128 x 16 TF32 tile (8 KB)
-constexpr int kAStage = 8 * kAX;              // X: re/im x hi/lo, W: re/im x hi/lo (64 KB)
+// ---- apply ------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kTcThreads)
-apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
-                float* __restrict__ out, int C, int K, int R, int ldr, int T, int B, int S, int NB,
-                int NP, long long ntiles, DeviceStatus* __restrict__ status,
-                int wait_polls) {
+constexpr int kAppRB = 64;                    // bytes of one operand row per chunk (4 core matrices)
+constexpr int kAppA = 128 * kAppRB;           // A piece: 128 cells (8 KB)
+constexpr int kAppB = 256 * kAppRB;           // B piece: up to 256 weight rows (16 KB)
+
+template <int PREC>
+constexpr size_t apply_smem() { return 2 * (size_t)Fmt<PREC>::NPC * (kAppA + kAppB); }
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads)
+apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
+                 float* __restrict__ out, int C, int K, int R, int ldr, int T, int B, int S, int NB,
+                 int NP, int tmem_cols, long long ntiles, DeviceStatus* __restrict__ status,
+                 int wait_polls) {
+  using F = Fmt<PREC>;
+  constexpr int KC = kAppRB / F::ESZ;         // K elements per chunk: 16 (tf32) or 32 (16-bit)
+  constexpr int SBO = 8 * kAppRB;
+  constexpr int NCM = kAppRB / 16;            // core matrices along K per chunk
+  constexpr int PIECE = kAppA + kAppB;
+  constexpr int STAGE = F::NPC * PIECE;
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
-  __shared__ long long colbase[128];          // dop offset of snapshot entry d's row (bin k)
-  __shared__ long long wbase[128];            // wts offset of weight row n, or -1
+  __shared__ long long colbase[128];          // dop offset of snapshot entry d's row
+  __shared__ long long wbase[256];            // wts offset of weight row n (vector n/2), or -1
+  __shared__ float wsc[128];                  // per weight vector scale (FP16S)
+  __shared__ float xsc_s;
+  __shared__ int xmax;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int D = C * T;
+  const int K2 = 2 * D;
   const int tiles_per_k = (R + 127) / 128;
-  const int nbt_max = B < 128 ? 128 / B : 1;
-  const int N = nbt_max * S;
-  const int nchunks = (D + kAKC - 1) / kAKC;
+  const int nbt = B < 128 ? 128 / B : 1;
+  const int Nq = nbt * S;                     // weight vectors per tile
+  const int nchunks = (K2 + KC - 1) / KC;
+  const int unitsA = 16 * NCM, units = unitsA + (NP / 8) * NCM;
 
-  for (int i = tid; i < 2 * kAStage / 4; i += kTcThreads) reinterpret_cast<uint32_t*>(sm)[i] = 0u;
-  if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+  for (int i = tid; i < 2 * STAGE / 4; i += kThreads) reinterpret_cast<uint32_t*>(sm)[i] = 0u;
+  if (warp == 0) tc::tmem_alloc(&tmem_base, tmem_cols);
   if (tid == 0) {
     tc::mbar_init(&mbar[0], 1);
     tc::mbar_init(&mbar[1], 1);
@@ -257,8 +428,7 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
-  const uint32_t accA = tmem, accB = tmem + 128, accC = tmem + 256;
-  const uint32_t idesc = tc::idesc_tf32(128, NP);
+  const uint32_t idesc = idesc_for<PREC>(NP);
   uint32_t parity[2] = {0u, 0u};
   bool pending[2] = {false, false};
   bool ok = true;
@@ -268,17 +438,44 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
     const int k = (int)(tile / tiles_per_k);
     const int r0 = (int)(tile - (long long)k * tiles_per_k) * 128;
     const int b0 = r0 / B;
-    if (tid < 128) {
-      if (tid < D) {
-        const int t = tid / C, c = tid - t * C;
-        colbase[tid] = ((long long)c * K + wrap_bin(k + t - T / 2, K)) * ldr;
+    if (tid < D) {
+      const int t = tid / C, c = tid - t * C;
+      colbase[tid] = ((long long)c * K + wrap_bin(k + t - T / 2, K)) * ldr;
+    }
+    {
+      const int q = tid >> 1, j = q / S, s = q - j * S;
+      wbase[tid] = (tid < NP && q < Nq && b0 + j < NB) ? ((((long long)k * NB + b0 + j) * S + s) * D) : -1;
+    }
+    if (PREC == kFP16S && tid == 0) xmax = 0;
+    __syncthreads();
+    if constexpr (PREC == kFP16S) {   // the tile's largest |x| component, each vector's largest |w|
+      float m = 0.f;
+      for (int d = warp; d < D; d += kThreads / 32)
+        for (int mm = lane; mm < 128; mm += 32)
+          if (r0 + mm < R) {
+            const float2 v = __ldg(dop + colbase[d] + r0 + mm);
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+          }
+      m = warp_max(m);
+      if (lane == 0) atomicMax(&xmax, __float_as_int(m));
+      for (int q = warp; q < Nq; q += kThreads / 32) {
+        const long long wb = wbase[2 * q];
+        float mw = 0.f;
+        if (wb >= 0)
+          for (int d = lane; d < D; d += 32) {
+            const float2 w = __ldg(wts + wb + d);
+            mw = fmaxf(mw, fmaxf(fabsf(w.x), fabsf(w.y)));
+          }
+        mw = warp_max(mw);
+        if (lane == 0) wsc[q] = block_scale(mw);
       }
-      const int j = tid / S, s = tid - j * S;
-      wbase[tid] = (tid < N && b0 + j < NB) ? ((((long long)k * NB + b0 + j) * S + s) * D) : -1;
+      __syncthreads();
+      if (tid == 0) xsc_s = block_scale(__int_as_float(xmax));
+      __syncthreads();
     }
     for (int ch = 0; ch < nchunks && ok; ++ch, ++gch) {
       const int st = (int)(gch & 1);
-      uint8_t* stage = sm + st * kAStage;
+      uint8_t* stage = sm + st * STAGE;
       if (pending[st]) {
         ok = tc::mbar_wait(&mbar[st], parity[st], wait_polls);
         if (ok) {
@@ -288,44 +485,70 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
       }
       ok = __syncthreads_and(ok);
       if (!ok) break;
-      const int d0 = ch * kAKC;
-      // X tile (rows = cells) and W tile (rows n = j*S + s of block b0 + j),
-      // K = snapshot entries d0 .. d0+15; kUnroll loads in flight per lane
-      constexpr int NWS = kTcThreads / 32;
-      const int ncx = 16 * (kAKC / 4), ncw = (NP / 8) * (kAKC / 4), ncm = ncx + ncw;
-      for (int cb0 = warp; cb0 < ncm; cb0 += NWS * kUnroll) {
-        float2 xv[kUnroll];
+      // K elements kap0 .. kap0 + KC - 1 of the A rows (cells) and of the B
+      // rows (weights); a unit is one core matrix, lane l takes row 8 rg + l/4
+      // and K elements 4 cm + (l & 3) (tf32) or one re/im pair (16-bit)
+      const int kap0 = ch * KC;
+      for (int u0 = warp; u0 < units; u0 += (kThreads / 32) * kUnroll) {
+        float2 v[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const int cmi = cb0 + u * NWS;
-          xv[u] = make_float2(0.f, 0.f);
-          if (cmi < ncx) {
-            const int m = (cmi >> 2) * 8 + (lane >> 2), d = d0 + (cmi & 3) * 4 + (lane & 3);
-            const int r = r0 + m;
-            if (d < D && r < R) xv[u] = __ldg(dop + colbase[d] + r);
-          } else if (cmi < ncm) {
-            const int cw = cmi - ncx;
-            const int n = (cw >> 2) * 8 + (lane >> 2), d = d0 + (cw & 3) * 4 + (lane & 3);
-            const long long wb = wbase[n];
-            if (wb >= 0 && d < D) xv[u] = __ldg(wts + wb + d);
+        for (int uu = 0; uu < kUnroll; ++uu) {
+          const int unit = u0 + uu * (kThreads / 32);
+          v[uu] = make_float2(0.f, 0.f);
+          if (unit < units) {
+            const bool isA = unit < unitsA;
+            const int ul = isA ? unit : unit - unitsA;
+            const int row = (ul / NCM) * 8 + (lane >> 2), cmk = ul % NCM;
+            int d, comp;
+            if constexpr (PREC == kTF32X3) {
+              const int kap = kap0 + cmk * 4 + (lane & 3);
+              d = kap >> 1;
+              comp = kap & 1;
+            } else {
+              d = (kap0 + cmk * 8 + (lane & 3) * 2) >> 1;
+              comp = 0;
+            }
+            (void)comp;
+            if (d < D) {
+              if (isA) {
+                if (r0 + row < R) v[uu] = __ldg(dop + colbase[d] + r0 + row);
+              } else {
+                const long long wb = wbase[row];
+                if (wb >= 0) v[uu] = __ldg(wts + wb + d);
+              }
+            }
           }
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const int cmi = cb0 + u * NWS;
-          if (cmi < ncm) {
-            const bool isx = cmi < ncx;
-            const int cl = isx ? cmi : cmi - ncx;
-            const int row = (cl >> 2) * 8 + (lane >> 2), dd = (cl & 3) * 4 + (lane & 3);
-            const float2 x = xv[u];
-            const uint32_t rh = tc::to_tf32(x.x), ih = tc::to_tf32(x.y);
-            const uint32_t rl = tc::to_tf32(x.x - __uint_as_float(rh));
-            const uint32_t il = tc::to_tf32(x.y - __uint_as_float(ih));
-            uint8_t* t0 = stage + (isx ? 0 : 4 * kAX) + tc::cm_offset(row, dd, kAKC);
-            *reinterpret_cast<uint32_t*>(t0 + 0 * kAX) = rh;
-            *reinterpret_cast<uint32_t*>(t0 + 1 * kAX) = rl;
-            *reinterpret_cast<uint32_t*>(t0 + 2 * kAX) = ih;
-            *reinterpret_cast<uint32_t*>(t0 + 3 * kAX) = il;
+        for (int uu = 0; uu < kUnroll; ++uu) {
+          const int unit = u0 + uu * (kThreads / 32);
+          if (unit >= units) continue;
+          const bool isA = unit < unitsA;
+          const int ul = isA ? unit : unit - unitsA;
+          const int row = (ul / NCM) * 8 + (lane >> 2), cmk = ul % NCM;
+          const int off = (isA ? 0 : kAppA) + (ul / NCM) * SBO + cmk * 128 + (lane >> 2) * 16 +
+                          (lane & 3) * 4;
+          // the pair this row holds at (re, im) positions: x, or the weight
+          // rows (wr, wi) and (-wi, wr)
+          float2 e = v[uu];
+          if (!isA && (row & 1)) e = make_float2(-e.y, e.x);
+          if constexpr (PREC == kTF32X3) {
+            const int kap = kap0 + cmk * 4 + (lane & 3);
+            uint32_t w[2];
+            split_tf32((kap & 1) ? e.y : e.x, w);
+            *reinterpret_cast<uint32_t*>(stage + off) = w[0];
+            *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
+          } else if constexpr (PREC == kBF16X3) {
+            uint32_t w[3];
+            split_bf16(e.x, e.y, w);
+#pragma unroll
+            for (int pc = 0; pc < 3; ++pc) *reinterpret_cast<uint32_t*>(stage + pc * PIECE + off) = w[pc];
+          } else {
+            const float sc = isA ? xsc_s : ((row >> 1) < Nq ? wsc[row >> 1] : 1.f);
+            uint32_t w[2];
+            split_f16(e.x * sc, e.y * sc, w);
+            *reinterpret_cast<uint32_t*>(stage + off) = w[0];
+            *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
           }
         }
       }
@@ -335,33 +558,16 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
       tc::fence_after_sync();
       if (tid == 0) {
         const uint32_t base = tc::smem_u32(stage);
-        constexpr uint32_t LBO = 128, SBO = 128 * (kAKC / 4);
-        for (int ks = 0; ks < kAKC / 8; ++ks) {
+#pragma unroll
+        for (int ks = 0; ks < KC / F::KI; ++ks) {
           const uint32_t o = ks * 256;
-          const bool first = (ch == 0 && ks == 0);
-          const uint64_t xrh = tc::smem_desc(base + 0 * kAX + o, LBO, SBO);
-          const uint64_t xrl = tc::smem_desc(base + 1 * kAX + o, LBO, SBO);
-          const uint64_t xih = tc::smem_desc(base + 2 * kAX + o, LBO, SBO);
-          const uint64_t xil = tc::smem_desc(base + 3 * kAX + o, LBO, SBO);
-          const uint64_t wrh = tc::smem_desc(base + 4 * kAX + o, LBO, SBO);
-          const uint64_t wrl = tc::smem_desc(base + 5 * kAX + o, LBO, SBO);
-          const uint64_t wih = tc::smem_desc(base + 6 * kAX + o, LBO, SBO);
-          const uint64_t wil = tc::smem_desc(base + 7 * kAX + o, LBO, SBO);
-          // A += Xr Wr^T + Xi Wi^T
-          tc::mma_tf32(accA, xrh, wrh, idesc, !first);
-          tc::mma_tf32(accA, xrh, wrl, idesc, true);
-          tc::mma_tf32(accA, xrl, wrh, idesc, true);
-          tc::mma_tf32(accA, xih, wih, idesc, true);
-          tc::mma_tf32(accA, xih, wil, idesc, true);
-          tc::mma_tf32(accA, xil, wih, idesc, true);
-          // Bm += Xi Wr^T
-          tc::mma_tf32(accB, xih, wrh, idesc, !first);
-          tc::mma_tf32(accB, xih, wrl, idesc, true);
-          tc::mma_tf32(accB, xil, wrh, idesc, true);
-          // Cm += Xr Wi^T
-          tc::mma_tf32(accC, xrh, wih, idesc, !first);
-          tc::mma_tf32(accC, xrh, wil, idesc, true);
-          tc::mma_tf32(accC, xrl, wih, idesc, true);
+#pragma unroll
+          for (int pr = 0; pr < F::NPROD; ++pr) {
+            const uint32_t pa = base + prod_a(pr) * PIECE + o;
+            const uint32_t pb = base + prod_b(pr) * PIECE + kAppA + o;
+            issue_mma<PREC>(tmem, tc::smem_desc(pa, 128, SBO), tc::smem_desc(pb, 128, SBO), idesc,
+                            !(ch == 0 && ks == 0 && pr == 0));
+          }
         }
         tc::mma_commit(&mbar[st]);
       }
@@ -379,23 +585,38 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
     ok = __syncthreads_and(ok);
     if (!ok) break;
     tc::fence_after_sync();
-    // epilogue (warps 0-3): cell r0 + tid, block b0 + j, columns j*S .. j*S + S - 1
-    const int r = r0 + tid;
-    const int j = (r / B) - b0;
-    const bool mine = tid < 128 && r < R;
-    const uint32_t lanebase = (uint32_t)(warp * 32) << 16;
-    for (int cb = 0; cb < NP && warp < 4; cb += 8) {
-      float a[8], bm[8], cm[8];
-      tc::tmem_ld8(accA + lanebase + cb, a);
-      tc::tmem_ld8(accB + lanebase + cb, bm);
-      tc::tmem_ld8(accC + lanebase + cb, cm);
-      if (mine) {
+    // epilogue: lane m of warp quarter q4 is cell r0 + m; columns 2 (j S + s)
+    // and 2 (j S + s) + 1 hold Re y and Im y of its block j
+    {
+      const int q4 = warp & 3, hf = warp >> 2;
+      const int m = q4 * 32 + lane;
+      const int r = r0 + m;
+      const bool mine = r < R;
+      const int j = mine ? r / B - b0 : -1;
+      const int jw0 = (r0 + q4 * 32) / B - b0;
+      const int jw1 = min(nbt - 1, (r0 + q4 * 32 + 31) / B - b0);
+      const uint32_t lb = (uint32_t)(q4 * 32) << 16;
+      for (int jj = jw0; jj <= jw1; ++jj) {
+        // blocks of 8 columns starting on a multiple of 8 (column 2 jj S is
+        // even, so a (Re, Im) pair never straddles two blocks)
+        const int c_lo = 2 * jj * S, c_hi = c_lo + 2 * S;
+        for (int cb = (c_lo & ~7) + hf * 8; cb < c_hi; cb += 16) {   // warp-uniform bounds
+          float a[8];
+          tc::tmem_ld8(tmem + lb + cb, a);
+          if (mine && j == jj) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int s = cb + u - j * S;
-          if (s >= 0 && s < S) {
-            const float re = a[u], im = bm[u] - cm[u];
-            out[((size_t)s * K + k) * ldr + r] = fmaf(re, re, im * im);
+            for (int u = 0; u < 8; u += 2) {
+              const int s = (cb + u - c_lo) >> 1;
+              if (cb + u >= c_lo && s < S) {
+                float re = a[u], im = a[u + 1];
+                if constexpr (PREC == kFP16S) {
+                  const float inv = 1.f / wsc[jj * S + s], invx = 1.f / xsc_s;   // exact
+                  re = re * inv * invx;
+                  im = im * inv * invx;
+                }
+                out[((size_t)s * K + k) * ldr + r] = fmaf(re, re, im * im);
+              }
+            }
           }
         }
       }
@@ -411,55 +632,93 @@ apply_tc_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+  if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
+}
+
+template <int PREC>
+cudaError_t launch_cov(const float2* dop, double2* cov, int C, int K, int R, int ldr, int T, int B,
+                       bool lower_only, DeviceStatus* status, cudaStream_t s, int wait_polls) {
+  const int D = C * T;
+  const int NB = R / B;
+  const int D8 = (D + 7) / 8 * 8;
+  const int G = 128 / D8;
+  const long long nsys = (long long)K * NB;
+  const long long ntiles = (nsys + G - 1) / G;
+  const size_t smem = cov_smem<PREC>();
+  static int set_bytes[64] = {0};
+  cudaError_t e = ensure_smem(covariance_tcx_kernel<PREC>, smem, set_bytes);
+  if (e != cudaSuccess) return e;
+  const long long blocks = ntiles < 152 ? ntiles : 152;   // one CTA per SM (TMEM: 512 columns)
+  covariance_tcx_kernel<PREC><<<(unsigned)blocks, kThreads, smem, s>>>(
+      dop, cov, C, K, ldr, T, B, NB, D8, G, ntiles, lower_only ? 1 : 0, status, wait_polls);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_app(const float2* dop, const float2* wts, float* out, int C, int K, int R, int ldr,
+                       int T, int B, int S, DeviceStatus* status, cudaStream_t s, int wait_polls) {
+  const int NB = R / B;
+  const int nbt = B < 128 ? 128 / B : 1;
+  const int NP = (2 * nbt * S + 15) / 16 * 16;
+  const int cols = NP + 8 <= 256 ? 256 : 512;   // epilogue reads whole blocks of 8 columns
+  const long long ntiles = (long long)K * ((R + 127) / 128);
+  const size_t smem = apply_smem<PREC>();
+  static int set_bytes[64] = {0};
+  cudaError_t e = ensure_smem(apply_tcx_kernel<PREC>, smem, set_bytes);
+  if (e != cudaSuccess) return e;
+  const int per_sm = (cols == 256 && 2 * smem <= 220 * 1024) ? 2 : 1;
+  const long long cap = 152LL * per_sm;
+  const long long blocks = ntiles < cap ? ntiles : cap;
+  apply_tcx_kernel<PREC><<<(unsigned)blocks, kThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S,
+                                                                   NB, NP, cols, ntiles, status,
+                                                                   wait_polls);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
+bool tc_precision(int precision) {
+  return precision == STAP_PREC_TF32X3 || precision == STAP_PREC_BF16X3 ||
+         precision == STAP_PREC_FP16_SCALED;
+}
+
 cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int ldr, int T,
-                                 int B, DeviceStatus* status, cudaStream_t s, int wait_polls) {
-  const int D = C * T;
-  const int NB = R / B;
-  if (NB == 0) return cudaSuccess;
-  if (D > 128) return cudaErrorInvalidValue;
-  const int G = 128 / D;
-  const long long nsys = (long long)K * NB;
-  const long long ntiles = (nsys + G - 1) / G;
-  const size_t smem = 2 * (size_t)kStage;
-  static int set_bytes[64] = {0};
-  cudaError_t e = ensure_smem(covariance_tc_kernel, smem, set_bytes);
-  if (e != cudaSuccess) return e;
-  long long blocks = ntiles < 152 ? ntiles : 152;   // one CTA per SM (TMEM and shared memory)
-  covariance_tc_kernel<<<(unsigned)blocks, kTcThreads, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, G,
-                                                                    ntiles, status,
-                                                                    wait_polls);
-  return cudaGetLastError();
+                                 int B, int precision, bool lower_only, DeviceStatus* status,
+                                 cudaStream_t s, int wait_polls) {
+  if (R / B == 0) return cudaSuccess;
+  if (C * T > 128) return cudaErrorInvalidValue;
+  switch (precision) {
+    case STAP_PREC_TF32X3:
+      return launch_cov<kTF32X3>(dop, cov, C, K, R, ldr, T, B, lower_only, status, s, wait_polls);
+    case STAP_PREC_BF16X3:
+      return launch_cov<kBF16X3>(dop, cov, C, K, R, ldr, T, B, lower_only, status, s, wait_polls);
+    case STAP_PREC_FP16_SCALED:
+      return launch_cov<kFP16S>(dop, cov, C, K, R, ldr, T, B, lower_only, status, s, wait_polls);
+  }
+  return cudaErrorInvalidValue;
 }
 
 bool apply_tc_supported(int B, int S) {
   const bool tiles = (B <= 128 && 128 % B == 0) || (B % 128 == 0);
   if (!tiles) return false;
-  const int N = (B < 128 ? 128 / B : 1) * S;
-  return (N + 15) / 16 * 16 <= 128;
+  const int nbt = B < 128 ? 128 / B : 1;
+  return 2 * nbt * S <= 256;
 }
 
 cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, int C, int K, int R,
-                            int ldr, int T, int B, int S, DeviceStatus* status, cudaStream_t s,
-                            int wait_polls) {
-  const int NB = R / B;
-  if (NB == 0) return cudaSuccess;
+                            int ldr, int T, int B, int S, int precision, DeviceStatus* status,
+                            cudaStream_t s, int wait_polls) {
+  if (R / B == 0) return cudaSuccess;
   if (!apply_tc_supported(B, S) || C * T > 128) return cudaErrorInvalidValue;
-  const int N = (B < 128 ? 128 / B : 1) * S;
-  const int NP = (N + 15) / 16 * 16;
-  const long long ntiles = (long long)K * ((R + 127) / 128);
-  const size_t smem = 2 * (size_t)kAStage;
-  static int set_bytes[64] = {0};
-  cudaError_t e = ensure_smem(apply_tc_kernel, smem, set_bytes);
-  if (e != cudaSuccess) return e;
-  long long blocks = ntiles < 152 ? ntiles : 152;
-  apply_tc_kernel<<<(unsigned)blocks, kTcThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S, NB, NP,
-                                                               ntiles, status, wait_polls);
-  return cudaGetLastError();
+  switch (precision) {
+    case STAP_PREC_TF32X3:
+      return launch_app<kTF32X3>(dop, wts, out, C, K, R, ldr, T, B, S, status, s, wait_polls);
+    case STAP_PREC_BF16X3:
+      return launch_app<kBF16X3>(dop, wts, out, C, K, R, ldr, T, B, S, status, s, wait_polls);
+    case STAP_PREC_FP16_SCALED:
+      return launch_app<kFP16S>(dop, wts, out, C, K, R, ldr, T, B, S, status, s, wait_polls);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace stap

@@ -252,18 +252,21 @@ stap_status do_doppler(stap_plan p, const Cpi& c, const void* cube, void* dop, c
       d.n_range, st, c.tune));
 }
 
+// lower: the chain's own buffer, of which the solve reads only the lower
+// triangle (the tensor-core kernels then skip the upper one)
 stap_status do_covariance(stap_plan p, const Cpi& c, const void* dop, void* cov, cudaStream_t st,
-                          int nr = -1) {
+                          int nr = -1, bool lower = false) {
   NvtxRange range("stap_covariance");
   const stap_dims& d = c.d;
   const int R = nr < 0 ? d.n_range : nr;
   // mixed-precision plans use the tensor cores unless the tuning kept the
   // (more accurate) FP32 kernel as the faster one
-  if (p->opt.precision == STAP_PREC_TF32X3 && c.tune.cov_kind != 1)
+  if (stap::tc_precision(p->opt.precision) && c.tune.cov_kind != 1)
     return check_launch(stap::launch_covariance_tc(static_cast<const float2*>(dop),
                                                    static_cast<double2*>(cov), c.Cd, d.n_dop,
                                                    R, d.n_range, c.Td, d.training_block,
-                                                   p->status(), st, p->wait_polls));
+                                                   p->opt.precision, lower, p->status(), st,
+                                                   p->wait_polls));
   return check_launch(stap::launch_covariance_fp32(static_cast<const float2*>(dop),
                                                    static_cast<double2*>(cov), c.Cd, d.n_dop,
                                                    R, d.n_range, c.Td, d.training_block, st,
@@ -290,12 +293,14 @@ stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts
   NvtxRange range("stap_apply");
   const stap_dims& d = c.d;
   const int R = nr < 0 ? d.n_range : nr;
-  if (p->opt.precision == STAP_PREC_TF32X3 && stap::apply_tc_supported(d.training_block, d.n_steering) &&
+  if (stap::tc_precision(p->opt.precision) &&
+      stap::apply_tc_supported(d.training_block, d.n_steering) &&
       (c.tune.apply_kind == 0 || c.tune.apply_kind == 3))
     return check_launch(stap::launch_apply_tc(static_cast<const float2*>(dop),
                                               static_cast<const float2*>(wts), out, c.Cd,
                                               d.n_dop, R, d.n_range, c.Td, d.training_block,
-                                              d.n_steering, p->status(), st, p->wait_polls));
+                                              d.n_steering, p->opt.precision, p->status(), st,
+                                              p->wait_polls));
   return check_launch(stap::launch_apply(static_cast<const float2*>(dop),
                                          static_cast<const float2*>(wts), out, c.Cd, d.n_dop,
                                          R, d.n_range, c.Td, d.training_block, d.n_steering, st,
@@ -315,7 +320,7 @@ stap_status do_chain(stap_plan p, const Cpi& c, const void* cube, float* out, ch
                      char* wts, char* ctr, cudaStream_t st, int nr = -1) {
   stap_status r;
   if ((r = do_doppler(p, c, cube, dop, st, nr)) != STAP_OK) return r;
-  if ((r = do_covariance(p, c, dop, cov, st, nr)) != STAP_OK) return r;
+  if ((r = do_covariance(p, c, dop, cov, st, nr, true)) != STAP_OK) return r;
   const char* trained = cov;
   if (p->opt.training == STAP_TRAIN_NEIGHBOURS) {
     if ((r = do_train(c, cov, ctr, st)) != STAP_OK) return r;
@@ -607,7 +612,7 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
   if (!(o.load_factor >= 0.0) || !std::isfinite(o.load_factor) || o.refine_steps < 0 ||
       o.refine_steps > 4)
     return STAP_ERR_INVALID_ARG;
-  if (o.precision != STAP_PREC_FP32 && o.precision != STAP_PREC_TF32X3) return STAP_ERR_UNSUPPORTED;
+  if (o.precision != STAP_PREC_FP32 && !stap::tc_precision(o.precision)) return STAP_ERR_UNSUPPORTED;
   if (o.solver != STAP_SOLVE_FP64 && o.solver != STAP_SOLVE_MIXED_IR) return STAP_ERR_UNSUPPORTED;
   if (o.training != STAP_TRAIN_OWN_BLOCK && o.training != STAP_TRAIN_NEIGHBOURS)
     return STAP_ERR_INVALID_ARG;
@@ -1043,7 +1048,7 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
     pick([](stap::Tune& t, int v) { t.dop_tr = v; }, {8, 16, 32},
          [&] { return do_doppler(p, c, cube, dop, p->stream); });
     {
-      const bool mixed = p->opt.precision == STAP_PREC_TF32X3;
+      const bool mixed = stap::tc_precision(p->opt.precision);
       if (mixed) c.tune.cov_kind = 1;   // tune the FP32 kernel first
       std::vector<int> kts;
       for (int kt = 1; kt <= 32 && kt <= d.n_dop; kt *= 2) kts.push_back(kt);
@@ -1089,7 +1094,7 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
            [&] { return do_solve(p, c, cov, wts, p->stream); });
     }
     if ((st = do_solve(p, c, cov, wts, p->stream)) != STAP_OK) break;
-    if (p->opt.precision == STAP_PREC_TF32X3 && stap::apply_tc_supported(d.training_block, d.n_steering))
+    if (stap::tc_precision(p->opt.precision) && stap::apply_tc_supported(d.training_block, d.n_steering))
       pick([](stap::Tune& t, int v) { t.apply_kind = v; }, {3, 1, 2},
            [&] { return do_apply(p, c, dop, wts, out, p->stream); });
     else

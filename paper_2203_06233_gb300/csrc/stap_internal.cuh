@@ -69,18 +69,26 @@ cudaError_t launch_doppler(const float2* cube, float2* dop, const float* win, co
 cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K, int R, int ldr,
                                    int T, int B, cudaStream_t s, const Tune& t = Tune());
 
-// Same covariance from 3xTF32 tensor-core products (tcgen05), FP32 accumulation.
-// wait_polls: polls before a pipeline wait gives up (kDefaultWaitPolls normally).
-cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int ldr, int T,
-                                 int B, DeviceStatus* status, cudaStream_t s,
-                                 int wait_polls = kDefaultWaitPolls);
+// True for the precisions whose covariance and apply run on the tensor cores.
+bool tc_precision(int precision);
 
-// Apply from 3xTF32 tensor-core products; needs B | 128 or 128 | B and at most
-// 128 steering columns per 128-cell tile (apply_tc_supported).
+// The same covariance from split tensor-core products (tcgen05) with FP32
+// accumulation, in the arithmetic of `precision` (STAP_PREC_TF32X3,
+// STAP_PREC_BF16X3 or STAP_PREC_FP16_SCALED).  lower_only: write only the
+// lower triangle (with the real diagonal) of each system, which is all the
+// solve reads; otherwise the full Hermitian matrix.  wait_polls: polls before
+// a pipeline wait gives up (kDefaultWaitPolls normally).
+cudaError_t launch_covariance_tc(const float2* dop, double2* cov, int C, int K, int R, int ldr, int T,
+                                 int B, int precision, bool lower_only, DeviceStatus* status,
+                                 cudaStream_t s, int wait_polls = kDefaultWaitPolls);
+
+// Apply from split tensor-core products; needs B | 128 or 128 | B and at most
+// 256 real weight rows (two per steering vector and block) per 128-cell tile
+// (apply_tc_supported).
 bool apply_tc_supported(int B, int S);
 cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, int C, int K, int R,
-                            int ldr, int T, int B, int S, DeviceStatus* status, cudaStream_t s,
-                            int wait_polls = kDefaultWaitPolls);
+                            int ldr, int T, int B, int S, int precision, DeviceStatus* status,
+                            cudaStream_t s, int wait_polls = kDefaultWaitPolls);
 
 // FP64 loading, Cholesky, solves, refinement and scaling for nsys systems.
 // cov [nsys][D][D] c128 -> wts [nsys][S][D] c64; steer [S][D] c128.  If

@@ -1,12 +1,14 @@
 // Thin wrappers over the sm_100-family tensor-core instructions (tcgen05.*,
 // mbarrier) used by the mixed-precision kernels, as inline PTX.
 //
-// Operand layout (K-major, no swizzle): an M x K (or N x K) tile of 32-bit
-// elements is stored as 8-row x 16-byte "core matrices".  Element (m, k) sits
-// at byte (m / 8) * SBO + (k / 4) * LBO + (m % 8) * 16 + (k % 4) * 4 with
-// LBO = 128 (core matrices adjacent along K) and SBO = 128 * (K / 4) (along
-// M).  One kind::tf32 MMA consumes K = 8 (two core matrices), so the k-th
-// step starts 256 bytes further.  The accumulator of an M = 128 MMA lives in
+// Operand layout (K-major, no swizzle): an M x K (or N x K) tile is stored as
+// 8-row x 16-byte "core matrices" (4 TF32 or 8 16-bit elements per row).
+// Element (m, k) of e-byte elements sits at byte (m / 8) * SBO +
+// (k / (16/e)) * LBO + (m % 8) * 16 + (k % (16/e)) * e with LBO = 128 (core
+// matrices adjacent along K) and SBO = 8 x the bytes of one tile row (along
+// M).  One MMA consumes 32 bytes of K (two core matrices: K = 8 for
+// kind::tf32, K = 16 for kind::f16), so the k-th step starts 256 bytes
+// further.  The accumulator of an M = 128 MMA lives in
 // TMEM: row m in lane m, column n in column base + n, and warp w of a
 // 4-warp group can read lanes 32 w .. 32 w + 31.
 #pragma once
@@ -36,6 +38,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor for kind::f16 with an FP32 accumulator: A and B both
+// BF16 (bf16 = true) or both FP16 (A and B of one MMA always share the type),
+// both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t to_tf32(float v) {  // round to nearest, ties away
@@ -83,6 +93,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate ? 1u : 0u));
+}
+
+// D (+)= A * B^T for 16-bit inputs (kind::f16), one K = 16 step, issued by one thread.
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, bool accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate ? 1u : 0u));
 }
 

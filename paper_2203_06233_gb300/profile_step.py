@@ -24,12 +24,15 @@ import torch
 
 from . import stap, synth
 
+PRECISIONS = {"fp32": stap.STAP_PREC_FP32, "tf32x3": stap.STAP_PREC_TF32X3,
+              "bf16x3": stap.STAP_PREC_BF16X3, "fp16s": stap.STAP_PREC_FP16_SCALED}
+
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--workload", default="standard",
                     choices=sorted(synth.WORKLOADS) + sorted(synth.ELEMENT_WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3"])
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--slabs", type=int, default=0, help="override the tuned range slabs (0 = keep)")
@@ -41,7 +44,7 @@ def main(argv=None):
     a = ap.parse_args(argv)
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    prec = stap.STAP_PREC_FP32 if a.precision == "fp32" else stap.STAP_PREC_TF32X3
+    prec = PRECISIONS[a.precision]
     solver = stap.STAP_SOLVE_FP64 if a.solver == "fp64" else stap.STAP_SOLVE_MIXED_IR
     refine = a.refine if a.refine is not None else (1 if a.solver == "fp64" else 2)
     opts = dict(snapshots=stap.STAP_SNAP_PRI_STAGGERED if a.snapshots == "staggered"

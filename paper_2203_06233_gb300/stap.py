@@ -29,7 +29,9 @@ STAP_ERR_NO_WORKSPACE = 7
 STAP_ERR_MISALIGNED = 8
 
 STAP_PREC_FP32 = 0
+STAP_PREC_BF16X3 = 1
 STAP_PREC_TF32X3 = 2
+STAP_PREC_FP16_SCALED = 3
 STAP_SOLVE_FP64 = 0
 STAP_SOLVE_MIXED_IR = 1
 STAP_TRAIN_OWN_BLOCK = 0

@@ -15,7 +15,7 @@ PLAIN_CELL_BAR = 1e-3
 
 # The mixed-precision contraction modes (tensor-core covariance and apply,
 # FP64 solve), as (test id, stap precision value).
-MIXED_PRECISIONS = [("tf32x3", 2)]
+MIXED_PRECISIONS = [("tf32x3", 2), ("bf16x3", 1), ("fp16s", 3)]
 
 # Worst cell of the mixed path, |P - P_ref| / max(P_ref, median P_ref), for
 # D <= 12 (grown by (D + 2)/14 above, as the normwise bars).  The mixed

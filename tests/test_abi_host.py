@@ -77,8 +77,10 @@ def test_plan_create_rejects_bad_shapes(dims, code):
     (1e-3, -1, 0, 0, stap.STAP_ERR_INVALID_ARG),
     (1e-3, 5, 0, 0, stap.STAP_ERR_INVALID_ARG),
     (1e-3, 1, 7, 0, stap.STAP_ERR_UNSUPPORTED),
-    (1e-3, 1, 1, 0, stap.STAP_ERR_UNSUPPORTED),
-    (1e-3, 1, 2, 0, stap.STAP_OK),
+    (1e-3, 1, 4, 0, stap.STAP_ERR_UNSUPPORTED),
+    (1e-3, 1, 1, 0, stap.STAP_OK),             # BF16X3
+    (1e-3, 1, 2, 0, stap.STAP_OK),             # TF32X3
+    (1e-3, 1, 3, 0, stap.STAP_OK),             # FP16_SCALED
     (0.0, 0, 0, 0, stap.STAP_OK),
     (1e-3, 2, 0, 1, stap.STAP_OK),             # mixed-precision refinement, D = 12
     (1e-3, 2, 2, 1, stap.STAP_OK),

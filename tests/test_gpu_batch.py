@@ -74,6 +74,7 @@ def test_full_batch_workload_on_sampled_cpis():
         s = specs[i]
         B = s.training_block
         refs[i] = oracle.run(oracle.Dims(*s.dims()), cubes[i].cpu().numpy(), r0=b * B, nr=B)["out"]
+    bad = []
     for pname, prec in [("plain", stap.STAP_PREC_FP32)] + MIXED_PRECISIONS:
         plan = stap.Plan([s.dims() for s in specs], precision=prec)
         outs = plan.run_cpi(cubes)
@@ -95,12 +96,15 @@ def test_full_batch_workload_on_sampled_cpis():
                   f"normwise={e_norm:.3e}")
             g = growth(s)
             if pname == "plain":
-                assert e_norm <= 1e-5 * g and e_cell <= PLAIN_CELL_BAR * g, (i, e_cell, e_norm)
+                ok = e_norm <= 1e-5 * g and e_cell <= PLAIN_CELL_BAR * g
             else:
-                assert e_norm <= 1e-3 * g and e_cell <= MIXED_CELL_BAR * g, (pname, i, e_cell, e_norm)
+                ok = e_norm <= 1e-3 * g and e_cell <= MIXED_CELL_BAR * g
+            if not ok:
+                bad.append((pname, i, e_cell, e_norm))
         plan.close()
         del outs
         torch.cuda.empty_cache()
+    assert not bad, bad
 
 
 def test_autotune_keeps_results_and_round_trips_through_the_cache(tmp_path):
