@@ -65,13 +65,13 @@ def workload_spec(rank=0, name="standard"):
     return dataclasses.replace(synth.WORKLOADS[name](), sub=rank)
 
 
-def workload_config(spec):
+def workload_config(spec, name=None):
     C, P, K, R, T, B, S = spec.dims()
-    return {"workload": f"{NAME} CPI C{C} P{P} K{K} R{R} T{T} B{B} S{S} (D={C*T}), "
+    name = name or NAME
+    return {"workload": f"{name} CPI C{C} P{P} K{K} R{R} T{T} B{B} S{S} (D={C*T}), "
                         f"{spec.cnr_db:.0f} dB CNR, {len(spec.targets)} targets",
             "n_chan": C, "n_pulses": P, "n_dop": K, "n_range": R, "tdof": T,
             "training_block": B, "n_steering": S, "cells_per_step": K * R,
-            "precision": "plain FP32 contractions, FP64 solve, 1 refinement step",
             "l2": "flushed between timed steps (256 MiB write); inputs resident in HBM",
             "parallelism": "one CPI per GPU per step"}
 
@@ -197,33 +197,170 @@ def power_errors(got, ref):
     return {"normwise": normwise, "max_cell": float(np.max(np.abs(got - ref) / floor))}
 
 
-def cpu_baseline_oracle(spec, outputs=None, option_outputs=None, budget_s=12.0):
-    """The oracle, as it stands, on the host cores: whole CPIs until ~budget_s.
-    Its output also gives the error of each GPU output in `outputs`
-    ({name: host array [S][K][R]}) on the same cube, and of each entry
-    {name: (output, oracle.run keyword arguments)} of `option_outputs` against
-    the oracle run with those options."""
+# mixed-precision arithmetic of each workload's mixed leg (the configurations'
+# stated precision: FP16 with per-block scaling for the large CPI, BF16 split
+# products for the D = 64 CPI and the batch; the D = 12 CPIs have no stated
+# mixed arithmetic and take BF16X3 as the more accurate split)
+MIXED_PREC = {"large": ("fp16_scaled", 3), "mixed": ("bf16x3", 1), "mixed_small": ("bf16x3", 1),
+              "standard": ("bf16x3", 1), "small": ("bf16x3", 1), "batch": ("bf16x3", 1)}
+PREC_NAMES = {0: "fp32", 1: "bf16x3", 2: "tf32x3", 3: "fp16_scaled"}
+PREC_TEXT = {
+    0: "plain: FP32 FFT, covariance accumulated error-free in FP32 pairs, FP32 apply",
+    1: "mixed: BF16 three-piece split products (6) on the tensor cores for covariance and apply, "
+       "FP32 accumulation; FP32 FFT",
+    2: "mixed: TF32 two-piece split products (3) on the tensor cores for covariance and apply, "
+       "FP32 accumulation; FP32 FFT",
+    3: "mixed: FP16 two-piece split products (3) with per-block power-of-two scaling on the tensor "
+       "cores for covariance and apply, FP32 accumulation; FP32 FFT",
+}
+SOLVE_TEXT = "FP64 diagonal load, LDL^H factorisation and substitutions, 1 refinement step"
+
+
+def sample_blocks(spec, n):
+    """n seeded range blocks of the CPI (all of them if it has fewer)."""
+    rng = np.random.default_rng(1234 + spec.seed)
+    n = min(n, spec.NB)
+    return sorted(int(b) for b in rng.choice(spec.NB, n, replace=False))
+
+
+def oracle_on_blocks(spec, cube_h, blocks):
+    """The FP64 oracle, as it stands, on each sampled block's range window
+    (blocks are independent: the Doppler transform is per range cell, the
+    snapshots and training stay inside the block).  Returns ({block: output
+    [S][K][B]}, the cpu_baseline dict)."""
     import oracle
-    from paper_2203_06233_gb300 import synth
     d = oracle.Dims(*spec.dims())
-    cube = synth.make_cube(spec)
-    n, t0 = 0, time.perf_counter()
-    ref = None
-    while True:
-        res = oracle.run(d, cube)
-        if ref is None:
-            ref = res["out"]
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s or n >= 50:
-            break
-    cells = n * spec.n_dop * spec.n_range
+    B = spec.training_block
+    refs = {}
+    t0 = time.perf_counter()
+    for b in blocks:
+        refs[b] = oracle.run(d, cube_h, r0=b * B, nr=B)["out"]
+    el = time.perf_counter() - t0
+    cells = len(blocks) * B * spec.n_dop
     base = {"value": cells / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n} whole CPI(s) of the standard workload ({cells} cells) in {el:.1f} s"}
-    errors = {name: power_errors(out, ref) for name, out in (outputs or {}).items()}
-    for name, (out, kw) in (option_outputs or {}).items():
-        errors[name] = power_errors(out, oracle.run(d, cube, **kw)["out"])
-    return base, errors
+            "sample": f"{len(blocks)} seeded range block(s) of {B} cells x {spec.n_dop} bins of "
+                      f"the {NAME_OF.get(spec.dims(), 'CPI')} CPI, all eight steps on each window, "
+                      f"{cells} cells in {el:.1f} s"}
+    return refs, base
+
+
+NAME_OF = {}
+
+
+def block_errors(outs_blocks, refs):
+    """Errors of one leg over the sampled blocks: normwise over all of them
+    and the worst cell (relative to max(P, median P) of its block)."""
+    num = den = 0.0
+    worst = 0.0
+    for b, ref in refs.items():
+        got = outs_blocks[b].astype(np.float64)
+        num += float(np.sum((got - ref) ** 2))
+        den += float(np.sum(ref ** 2))
+        worst = max(worst, power_errors(got, ref)["max_cell"])
+    return {"normwise": (num / den) ** 0.5, "max_cell": worst, "blocks": len(refs)}
+
+
+def kernel_figures(spec, prec, kt, pk, refine=1):
+    """Each step against its own bound: achieved rate and fraction."""
+    C, P, K, R, T, B, S = spec.dims()
+    D, NB = C * T, R // B
+    dop_bytes = 8.0 * C * R * (P + K)
+    sf = solve_flops(spec, refine=refine)
+    out = {
+        "doppler": {"ms": kt["doppler"], "bound": "hbm", "bytes": dop_bytes,
+                    "achieved_gbs": dop_bytes / kt["doppler"] / 1e6,
+                    "frac": dop_bytes / kt["doppler"] / 1e6 / pk["hbm_gbs"]},
+        "solve": {"ms": kt["solve"], "bound": "alu", "fp64_flops": sf,
+                  "achieved_tflops": sf / kt["solve"] / 1e9,
+                  "frac": sf / kt["solve"] / 1e9 / pk["fp64_tflops"]},
+    }
+    # covariance through the step call (full Hermitian c128 output)
+    cov_bytes = 8.0 * C * K * R + 16.0 * K * NB * D * D
+    apply_bytes = 8.0 * C * K * R + 8.0 * K * NB * S * D + 4.0 * S * K * R
+    if prec == 0:
+        cplx = 1.0 * K * NB * B * (T * C * C - C * (C - 1) // 2)
+        out["covariance"] = {"ms": kt["covariance"], "bound": "alu", "fp32_instr": 20.0 * cplx,
+                             "frac": 20.0 * cplx / kt["covariance"] / 1e9 / (pk["fp32_tflops"] / 2),
+                             "hbm_frac": cov_bytes / kt["covariance"] / 1e6 / pk["hbm_gbs"]}
+        af = 8.0 * K * R * S * D
+        out["apply"] = {"ms": kt["apply"], "bound": "alu", "fp32_flops": af,
+                        "frac": af / kt["apply"] / 1e9 / pk["fp32_tflops"],
+                        "hbm_frac": apply_bytes / kt["apply"] / 1e6 / pk["hbm_gbs"]}
+    else:
+        nprod = 6 if prec == 1 else 3
+        peak = pk["bf16_tflops"] / (2.0 if prec == 2 else 1.0)
+        # tensor work the kernels issue: covariance 2 x (2 G D8) x 128 x B real
+        # MACs per G systems (D8 = D rounded up to 8, G = 128 // D8); apply
+        # 128 x N x 2D per 128-cell tile (N = 2 S per block in the tile)
+        D8 = (D + 7) // 8 * 8
+        G = 128 // D8
+        cov_mac = 2.0 * (2 * G * D8) * 128 * B * np.ceil(K * NB / G) * nprod
+        nbt = 128 // B if B < 128 else 1
+        NP = -(-2 * nbt * S // 16) * 16
+        app_mac = 128.0 * NP * 2 * D * K * np.ceil(R / 128) * nprod
+        # useful work: Hermitian half not exploited; every computed entry of a
+        # system's own block is used
+        cov_useful = 2.0 * 4 * D * D * B * K * NB * nprod
+        for name, mac, useful, byts in (("covariance", cov_mac, cov_useful, cov_bytes),
+                                        ("apply", app_mac, 2.0 * 4 * D * S * K * R * nprod, apply_bytes)):
+            out[name] = {"ms": kt[name], "bound": "tensor", "issued_tflops": 2 * mac / kt[name] / 1e9,
+                         "useful_tflops": useful / kt[name] / 1e9,
+                         "frac": 2 * mac / kt[name] / 1e9 / peak,
+                         "hbm_gbs": byts / kt[name] / 1e6,
+                         "hbm_frac": byts / kt[name] / 1e6 / pk["hbm_gbs"],
+                         "peak_tflops": peak}
+    return out
+
+
+def run_leg(spec, cube, dev, prec, args, flush, stream, kernel_reps, timed=None, keep_out=False,
+            solver=0, refine=1):
+    """One path on the workload's cube: plan, autotune (untimed), warm-up,
+    args.steps timed steps (inside `timed`, a context manager, if given),
+    per-step kernel times; returns (plan, out, leg dict)."""
+    import contextlib
+    import torch
+    from paper_2203_06233_gb300 import stap
+    C, P, K, R, T, B, S = spec.dims()
+    plan = stap.Plan(spec.dims(), device=dev, precision=prec, solver=solver, refine_steps=refine)
+    out = torch.empty((S, K, R), dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    tuning = plan.autotune(cube, out, reps=1 if K * R * C * T > (1 << 26) else 3)
+    tune_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        flush()
+        plan.run_cpi(cube, out)
+    torch.cuda.synchronize()
+    code, failed = plan.status()
+    if code != stap.STAP_OK:
+        raise RuntimeError(f"{PREC_NAMES[prec]}: device status {code} ({failed} failed systems)")
+    with (timed if timed is not None else contextlib.nullcontext()):
+        times = time_steps(lambda: plan.run_cpi(cube, out), args.steps, flush, stream)
+    plan.run_cpi(cube, out)
+    torch.cuda.synchronize()
+    code, failed = plan.status()
+    if code != stap.STAP_OK:
+        raise RuntimeError(f"{PREC_NAMES[prec]}: device status {code} ({failed} failed systems)")
+    # per-kernel times through the step-by-step calls (same launch choices)
+    dop = plan.doppler(cube)
+    cov = plan.covariance(dop)
+    wts = plan.solve_weights(cov)
+    kt = {
+        "doppler": statistics.mean(time_steps(lambda: plan.doppler(cube, dop), kernel_reps, flush, stream)),
+        "covariance": statistics.mean(time_steps(lambda: plan.covariance(dop, cov), kernel_reps, flush, stream)),
+        "solve": statistics.mean(time_steps(lambda: plan.solve_weights(cov, wts), kernel_reps, flush, stream)),
+        "apply": statistics.mean(time_steps(lambda: plan.apply(dop, wts, out), kernel_reps, flush, stream)),
+    }
+    plan.run_cpi(cube, out)   # the run's own output again (the apply call above rewrote it)
+    del dop, cov, wts
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    (choices,) = tuning.values()
+    leg = {"precision": PREC_NAMES[prec], "arithmetic": PREC_TEXT[prec] + "; " + SOLVE_TEXT,
+           "ms_per_step": sum(times) / args.steps, "step_ms": times, "tuning": tuning,
+           "autotune_s": tune_s, "kernels_ms": kt,
+           "kernels_used": {"covariance": "FP32 error-free" if prec == 0 or choices[8] == 1 else "tensor cores",
+                            "apply": "FP32" if prec == 0 or choices[5] in (1, 2) else "tensor cores"}}
+    return plan, out, leg
 
 
 def run_gpu(args):
@@ -238,268 +375,214 @@ def run_gpu(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    spec = workload_spec(rank, NAME)
-    C, P, K, R, T, B, S = spec.dims()
-    if NAME == "standard":
-        cube_h = synth.make_cube(spec)
-        cube = torch.from_numpy(cube_h).to(dev)
-    else:  # several GB: generate on the device, keep a host copy for the e2e leg
-        cube = synth.make_cube_torch(spec, dev)
-        cube_h = cube.cpu().numpy()
-    plan = stap.Plan(spec.dims(), device=dev)
-    out = torch.empty((S, K, R), dtype=torch.float32, device=dev)
-    tuning = plan.autotune(cube, out)          # launch shapes picked on the device, untimed
-    flushbuf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    flushbuf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def flush():
         flushbuf.zero_()
 
-    def step():
-        plan.run_cpi(cube, out)
-
-    for _ in range(args.warmup):
-        flush()
-        step()
-    torch.cuda.synchronize()
-    code, failed = plan.status()
-    if code != stap.STAP_OK:
-        raise RuntimeError(f"device status {code} ({failed} failed systems) after warm-up")
-
-    # ---- timed region ----
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        # a profiler started with profiling off (ncu --profile-from-start off)
-        # sees exactly the timed steps' launches (and the L2 flushes between them)
-        torch.cuda.profiler.start()
-        times = time_steps(step, args.steps, flush, stream)
-        torch.cuda.profiler.stop()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    cells = K * R
-    total_ms, value = aggregate(sum(times), cells * args.steps, world, dev)
-    ms_per_step = total_ms / args.steps
-
-    # ---- per-kernel breakdown (same kernels and launch configuration) ----
-    dop = plan.doppler(cube)
-    cov = plan.covariance(dop)
-    wts = plan.solve_weights(cov)
-    reps = max(20, min(200, args.steps)) if NAME == "standard" else max(3, args.steps)
-    kt = {
-        "doppler": statistics.mean(time_steps(lambda: plan.doppler(cube, dop), reps, flush, stream)),
-        "covariance": statistics.mean(time_steps(lambda: plan.covariance(dop, cov), reps, flush, stream)),
-        "solve": statistics.mean(time_steps(lambda: plan.solve_weights(cov, wts), reps, flush, stream)),
-        "apply": statistics.mean(time_steps(lambda: plan.apply(dop, wts, out), reps, flush, stream)),
-    }
     pk = peaks()
-    D, NB = C * T, R // B
-    dop_bytes = 8.0 * C * R * (P + K)
-    # covariance: complex products of the bin-pair form (T C^2 - C(C-1)/2 per
-    # cell and bin), 4 real products each, 5 FP32 instructions per real product
-    cov_cplx_products = 1.0 * K * NB * B * (T * C * C - C * (C - 1) // 2)
-    apply_flops = 8.0 * K * R * S * D
-    apply_bytes = 8.0 * C * K * R + 8.0 * K * NB * S * D + 4.0 * S * K * R
-    sf = solve_flops(spec, refine=1)
-    kernels = {
-        "doppler": {"ms": kt["doppler"], "bound": "hbm", "bytes": dop_bytes,
-                    "achieved_gbs": dop_bytes / kt["doppler"] / 1e6,
-                    "frac": dop_bytes / kt["doppler"] / 1e6 / pk["hbm_gbs"]},
-        "covariance": {"ms": kt["covariance"], "bound": "alu",
-                       "fp32_instr": 20.0 * cov_cplx_products,
-                       "achieved_tinstr_s": 20.0 * cov_cplx_products / kt["covariance"] / 1e9,
-                       "frac": 20.0 * cov_cplx_products / kt["covariance"] / 1e9 / (pk["fp32_tflops"] / 2)},
-        "solve": {"ms": kt["solve"], "bound": "alu", "fp64_flops": sf,
-                  "achieved_tflops": sf / kt["solve"] / 1e9,
-                  "frac": sf / kt["solve"] / 1e9 / pk["fp64_tflops"]},
-        "apply": {"ms": kt["apply"], "bound": "alu", "fp32_flops": apply_flops, "bytes": apply_bytes,
-                  "achieved_tflops": apply_flops / kt["apply"] / 1e9,
-                  "frac": apply_flops / kt["apply"] / 1e9 / pk["fp32_tflops"],
-                  "hbm_frac": apply_bytes / kt["apply"] / 1e6 / pk["hbm_gbs"]},
-    }
-    solve_kind = 3 if C * T > 32 else list(tuning.values())[0][7]   # above D = 32 always per CTA
-    roofline = {"kernel": SOLVE_KERNELS.get(solve_kind, "solve"),
-                "bound": "alu", "achieved": kernels["solve"]["achieved_tflops"],
-                "peak": pk["fp64_tflops"], "unit": "TFLOP/s",
-                "frac": kernels["solve"]["frac"], "traffic": None,
-                "peak_src": "FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (unit count and max clock)"}
-    roofline["traffic"] = SOLVE_TRAFFIC.get((kernel_hash(), solve_kind))
-
-    # ---- the mixed-precision path (tensor-core contractions) on the same CPI ----
-    mplan = stap.Plan(spec.dims(), device=dev, precision=stap.STAP_PREC_TF32X3)
-    mout = torch.empty_like(out)
-    mtuning = mplan.autotune(cube, mout)
-    for _ in range(args.warmup):
-        flush()
-        mplan.run_cpi(cube, mout)
-    torch.cuda.synchronize()
-    mtimes = time_steps(lambda: mplan.run_cpi(cube, mout), args.steps, flush, stream)
-    mdop = mplan.doppler(cube)
-    mcov = mplan.covariance(mdop)
-    mwts = mplan.solve_weights(mcov)
-    (mchoices,) = mtuning.values()
-    mixed = {
-        "value": world * cells * args.steps / (sum(mtimes) * 1e-3),
-        "ms_per_step": sum(mtimes) / args.steps,
-        "precision": "3xTF32 tensor-core covariance and apply (tcgen05) where the autotuner finds "
-                     "them faster than the FP32 kernels, FP64 solve",
-        "kernels_used": {"covariance": "FP32 error-free" if mchoices[8] == 1 else "tensor cores",
-                         "apply": "FP32" if mchoices[5] in (1, 2) else "tensor cores"},
-        "tuning": mtuning,
-        "kernels_ms": {
-            "doppler": statistics.mean(time_steps(lambda: mplan.doppler(cube, mdop), reps, flush, stream)),
-            "covariance": statistics.mean(time_steps(lambda: mplan.covariance(mdop, mcov), reps, flush, stream)),
-            "solve": statistics.mean(time_steps(lambda: mplan.solve_weights(mcov, mwts), reps, flush, stream)),
-            "apply": statistics.mean(time_steps(lambda: mplan.apply(mdop, mwts, mout), reps, flush, stream)),
-        },
-    }
-    code, failed = mplan.status()
-    if code != stap.STAP_OK:
-        raise RuntimeError(f"mixed path: device status {code} ({failed} failed systems)")
-    mplan.close()
-
-    # ---- mixed-precision iterative refinement of the solve (an option beyond
-    # the paper's FP64 solve: FP32 factorisation, double-float residuals) ----
-    mixed_ir = None
-    if stap.stap_abi_version() >= 2:
-        iplan = stap.Plan(spec.dims(), device=dev, refine_steps=2, solver=stap.STAP_SOLVE_MIXED_IR)
-        iout = torch.empty_like(out)
-        ituning = iplan.autotune(cube, iout)
-        for _ in range(args.warmup):
-            flush()
-            iplan.run_cpi(cube, iout)
+    line = None
+    extra = {}
+    # the workload of the headline first, then the other single-CPI workloads
+    # as keys of the same line (rank 0 of a one-GPU run only)
+    names = [NAME] + ([n for n in ("mixed", "standard") if n != NAME]
+                      if world == 1 and not args.only_headline else [])
+    for wi, name in enumerate(names):
+        head = wi == 0
+        spec = workload_spec(rank, name)
+        NAME_OF[spec.dims()] = name
+        C, P, K, R, T, B, S = spec.dims()
+        cells = K * R
+        mname, mprec = MIXED_PREC[name]
+        cube = synth.make_cube_torch(spec, dev)
+        cube_h = cube.cpu().numpy()
+        big = cube_h.nbytes > (1 << 30)
+        kernel_reps = 3 if big else max(20, min(200, args.steps))
+        blocks = sample_blocks(spec, 8 if name == "large" else 4)
+        sub = argparse.Namespace(steps=args.steps if head else max(3, min(args.steps, 10)),
+                                 warmup=args.warmup)
+        legs, outs_blocks = {}, {}
+        clk = ClockSampler(local) if head else None
+        for prec in (mprec, 0):
+            timed = None
+            if head and prec == mprec:
+                if world > 1:
+                    dist.barrier()
+                torch.cuda.synchronize()
+                timed = clk
+            plan, out, leg = run_leg(spec, cube, dev, prec, sub, flush, stream, kernel_reps, timed=timed)
+            legs[prec] = (plan, out, leg)
+            outs_blocks[prec] = {b: out[:, :, b * B:(b + 1) * B].cpu().numpy() for b in blocks}
+            if not (head and prec == mprec):
+                plan.close()
+                del out
+                torch.cuda.empty_cache()
+        mplan, mout, mleg = legs[mprec]
+        fleg = legs[0][2]
+        errors, cpu = {}, None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            refs, cpu = oracle_on_blocks(spec, cube_h, blocks)
+            errors = {PREC_NAMES[p]: block_errors(outs_blocks[p], refs) for p in outs_blocks}
+        mvalue = world * cells / (mleg["ms_per_step"] * 1e-3)
+        fvalue = world * cells / (fleg["ms_per_step"] * 1e-3)
+        if not head:
+            mplan.close()
+            extra[name] = {
+                "config": workload_config(spec, name),
+                "mixed": dict(mleg, value=mvalue, kernels=kernel_figures(spec, mprec, mleg["kernels_ms"], pk)),
+                "fp32": dict(fleg, value=fvalue, kernels=kernel_figures(spec, 0, fleg["kernels_ms"], pk)),
+                "mixed_vs_fp32": mvalue / fvalue, "errors_vs_oracle": errors,
+                "cpu_baseline": cpu}
+            del mout, cube
+            torch.cuda.empty_cache()
+            continue
+        # ---- headline: the mixed leg's timed region ----
+        total_ms, value = aggregate(mleg["ms_per_step"] * sub.steps, cells * sub.steps, world, dev)
+        ms_per_step = total_ms / sub.steps
+        kern = kernel_figures(spec, mprec, mleg["kernels_ms"], pk)
+        solve_kind = 3 if C * T > 32 else list(mleg["tuning"].values())[0][7]
+        roofline = {"kernel": SOLVE_KERNELS.get(solve_kind, "solve"),
+                    "bound": "alu", "achieved": kern["solve"]["achieved_tflops"],
+                    "peak": pk["fp64_tflops"], "unit": "TFLOP/s", "frac": kern["solve"]["frac"],
+                    "traffic": SOLVE_TRAFFIC.get((kernel_hash(), solve_kind, name)),
+                    "basis": "8 K NB (D^3/6 + (1 + 2 refine) C D^2) FP64 flops per launch: the "
+                             "factorisation plus, for each of the C basis right-hand sides of the "
+                             "separable steering (v_s = g (x) a_s), one forward/back solve pair and "
+                             "per refinement step a residual and a solve pair; the combination into "
+                             "the S steering vectors and their normalisation run on the FP32 pipe",
+                    "peak_src": "FP64: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (unit count and max "
+                                "clock; a DFMA microbenchmark measured 1.20 TFLOP/s at 1987 MHz)"}
+        # ---- end to end through the public API from pinned host buffers ----
+        ring = 4 if cube_h.nbytes <= (1 << 30) else 2
+        cube_pin = torch.from_numpy(cube_h).pin_memory()
+        host_cubes = [cube_pin] + [cube_pin.clone().pin_memory() for _ in range(ring - 1)]
+        host_outs = [torch.empty((S, K, R), dtype=torch.float32).pin_memory() for _ in range(ring)]
+        n_stream = max(2 * ring, min(sub.steps, 10 if big else 1000))
+        mplan.run_stream(host_cubes[:2], host_outs[:2])      # warm-up (grows the workspace once)
         torch.cuda.synchronize()
-        itimes = time_steps(lambda: iplan.run_cpi(cube, iout), args.steps, flush, stream)
-        idop = iplan.doppler(cube)
-        icov = iplan.covariance(idop)
-        iwts = iplan.solve_weights(icov)
-        isolve = statistics.mean(time_steps(lambda: iplan.solve_weights(icov, iwts), reps, flush, stream))
-        code, failed = iplan.status()
+        seq_c = [host_cubes[i % ring] for i in range(n_stream)]
+        seq_o = [host_outs[i % ring] for i in range(n_stream)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mplan.run_stream(seq_c, seq_o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms, _ = aggregate(e0.elapsed_time(e1), cells * n_stream, world, dev)
+        e2e_ms /= n_stream
+        code, failed = mplan.status()
         if code != stap.STAP_OK:
-            raise RuntimeError(f"mixed refinement: device status {code} ({failed} failed systems)")
-        iplan.run_cpi(cube, iout)
-        mixed_ir = {
-            "value": world * cells * args.steps / (sum(itimes) * 1e-3),
-            "ms_per_step": sum(itimes) / args.steps,
-            "solver": "FP32 Lu Dg Lu^H factorisation and substitutions, 2 refinement steps with "
-                      "double-float residuals (STAP_SOLVE_MIXED_IR); plain FP32 contractions",
-            "tuning": ituning, "solve_ms": isolve,
-            "solve_speedup_vs_fp64": kt["solve"] / isolve,
+            raise RuntimeError(f"e2e: device status {code} ({failed} failed systems)")
+        del host_cubes, host_outs, cube_pin, seq_c, seq_o
+        cfg = workload_config(spec, name)
+        cfg["precision"] = mleg["arithmetic"]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": sub.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[mprec], "data": "synthetic",
+            "config": cfg,
+            "e2e": {"value": world * cells / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": cube_h.nbytes, "d2h_bytes_per_step": S * K * R * 4,
+                    "ms_per_step": e2e_ms,
+                    "api": f"stap_run_stream over {n_stream} CPIs from a ring of {ring} pinned host "
+                           "cubes and outputs: every CPI copied in, run and copied out inside the "
+                           "timed region, copies overlapping the neighbouring CPIs' chains"},
+            "gpu_launches": 4 * slab_count(mleg["tuning"], R // B) * sub.steps,
+            "mixed": dict(mleg, value=value, kernels=kern),
+            "fp32": dict(fleg, value=world * cells / (fleg["ms_per_step"] * 1e-3),
+                         kernels=kernel_figures(spec, 0, fleg["kernels_ms"], pk)),
+            "mixed_vs_fp32": value / (world * cells / (fleg["ms_per_step"] * 1e-3)),
+            "roofline": roofline,
+            "clocks": clk.summary(),
         }
-        iplan.close()
-
-    # ---- options beyond the paper, each on the same CPI with its own tuning ----
-    def option_leg(what, **plan_kw):
-        oplan = stap.Plan(spec.dims(), device=dev, **plan_kw)
-        oout = torch.empty_like(out)
-        otuning = oplan.autotune(cube, oout)
-        for _ in range(args.warmup):
-            flush()
-            oplan.run_cpi(cube, oout)
-        torch.cuda.synchronize()
-        otimes = time_steps(lambda: oplan.run_cpi(cube, oout), args.steps, flush, stream)
-        code, failed = oplan.status()
-        if code != stap.STAP_OK:
-            raise RuntimeError(f"{what}: device status {code} ({failed} failed systems)")
-        oplan.run_cpi(cube, oout)
-        oplan.close()
-        return {"value": world * cells * args.steps / (sum(otimes) * 1e-3),
-                "ms_per_step": sum(otimes) / args.steps, "tuning": otuning}, oout
-
-    # training with guard cells (neighbour blocks)
-    neighbours = None
-    if stap.stap_abi_version() >= 3 and NB >= 2:
-        neighbours, nout = option_leg("neighbour training", training=stap.STAP_TRAIN_NEIGHBOURS)
-        neighbours["training"] = "block b trained on blocks b-1 and b+1 (STAP_TRAIN_NEIGHBOURS), FP64 solve"
-    # PRI-staggered snapshots
-    staggered = None
-    if stap.stap_abi_version() >= 4 and T <= P:
-        staggered, sout = option_leg("staggered snapshots", snapshots=stap.STAP_SNAP_PRI_STAGGERED)
-        staggered["snapshots"] = ("T sub-windows of P - T + 1 pulses, bin k of each "
-                                  "(STAP_SNAP_PRI_STAGGERED), FP64 solve")
-
-    # ---- end to end through the public API from pinned host buffers ----
-    # (a) one call per CPI: copy in, stap_run_cpi, copy out, one after the other
-    cube_pin = torch.from_numpy(cube_h).pin_memory()
-    out_pin = torch.empty((S, K, R), dtype=torch.float32).pin_memory()
-
-    def e2e_step():
-        cube.copy_(cube_pin, non_blocking=True)
-        plan.run_cpi(cube, out)
-        out_pin.copy_(out, non_blocking=True)
-
-    for _ in range(3):
-        e2e_step()
-    torch.cuda.synchronize()
-    single_ms = statistics.mean(time_steps(e2e_step, reps, flush, stream))
-    # (b) stap_run_stream: every CPI's cube copied in and its result copied out
-    # inside the timed region, the copies of neighbouring CPIs overlapping the
-    # chain; a ring of distinct pinned host buffers
-    ring = 4 if cube_h.nbytes <= (1 << 30) else 2
-    host_cubes = [cube_pin] + [cube_pin.clone().pin_memory() for _ in range(ring - 1)]
-    host_outs = [out_pin] + [torch.empty_like(out_pin).pin_memory() for _ in range(ring - 1)]
-    n_stream = max(args.steps, 2 * ring)
-    plan.run_stream(host_cubes * 2, host_outs * 2)      # warm-up (grows the workspace once)
-    torch.cuda.synchronize()
-    seq_c = [host_cubes[i % ring] for i in range(n_stream)]
-    seq_o = [host_outs[i % ring] for i in range(n_stream)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    plan.run_stream(seq_c, seq_o)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms, _ = aggregate(e0.elapsed_time(e1), cells * n_stream, world, dev)
-    e2e_ms /= n_stream
-    e2e_val = world * cells / (e2e_ms * 1e-3)
-
-    cfg = workload_config(spec)
-    cfg["tuning"] = tuning
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": cfg,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": cube_h.nbytes,
-                "d2h_bytes_per_step": S * K * R * 4, "ms_per_step": e2e_ms,
-                "api": f"stap_run_stream over {n_stream} CPIs from a ring of {ring} pinned host "
-                       "cubes and outputs: every CPI copied in, run and copied out inside the "
-                       "timed region, copies overlapping the neighbouring CPIs' chains",
-                "one_call_per_cpi": {"value": world * cells / (single_ms * 1e-3),
-                                     "ms_per_step": single_ms,
-                                     "api": "copy in, stap_run_cpi, copy out, in turn; L2 flushed "
-                                            "between steps"}},
-        "gpu_launches": 4 * slab_count(tuning, NB) * args.steps,
-        "mixed": mixed,
-        "roofline": roofline,
-        "kernels": kernels,
-        "clocks": clk.summary(),
-    }
-    if mixed_ir is not None:
-        line["mixed_ir"] = mixed_ir
-    if neighbours is not None:
-        line["neighbour_training"] = neighbours
-    if staggered is not None:
-        line["staggered"] = staggered
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and NAME == "standard":
-        outputs = {"plain": out.cpu().numpy(), "mixed": mout.cpu().numpy()}
-        if mixed_ir is not None:
-            outputs["mixed_ir"] = iout.cpu().numpy()
-        opt_outputs = {}
-        if neighbours is not None:
-            opt_outputs["neighbour_training"] = (nout.cpu().numpy(), {"training": 1})
-        if staggered is not None:
-            opt_outputs["staggered"] = (sout.cpu().numpy(), {"staggered": True})
-        line["cpu_baseline"], line["errors_vs_oracle"] = cpu_baseline_oracle(spec, outputs, opt_outputs)
-    plan.close()
+        if errors:
+            line["errors_vs_oracle"] = errors
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        mplan.close()
+        del mout, cube
+        torch.cuda.empty_cache()
+    if extra:
+        line["workloads"] = extra
+    if world == 1 and not args.only_headline and NAME == "large":
+        line["workloads"]["batch"] = batch_legs(args, dev, stream, flush)
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+DTYPE = {0: "f32+f64", 1: "bf16x3+f32+f64", 2: "tf32x3+f32+f64", 3: "f16x2+f32+f64"}
+
+
+def batch_legs(args, dev, stream, flush):
+    """The 512-CPI batch (one stap_run_cpi call, a captured graph replayed)
+    on the mixed and the plain path, a few steps each; errors on one seeded
+    block of 8 seeded CPIs."""
+    import torch
+    from paper_2203_06233_gb300 import stap, synth
+    specs = synth.batch_cpis(512)
+    cubes = [synth.make_cube_torch(s, dev) for s in specs]
+    cells = sum(s.cells for s in specs)
+    rng = np.random.default_rng(4)
+    picks = [(i, int(rng.integers(specs[i].NB)))
+             for i in sorted(int(x) for x in rng.choice(len(specs), 8, replace=False))]
+    res = {"config": {"workload": "batch of 512 uneven CPIs: C in {4,8,16}, T in {2,3,4}, P = K in "
+                                  "{64,128,256}, R = 64 x U{16..256}, B 64, S in {8,16}",
+                      "cells_per_step": cells, "n_cpi": len(specs)}}
+    outs_pick = {}
+    steps = max(2, min(args.steps, 3))
+    for prec in (MIXED_PREC["batch"][1], 0):
+        free = torch.cuda.mem_get_info(dev)[0]
+        plan = stap.Plan([s.dims() for s in specs], device=dev, precision=prec,
+                         max_workspace_bytes=max(0, free - (8 << 30)))
+        outs = [torch.empty((s.n_steering, s.n_dop, s.n_range), dtype=torch.float32, device=dev)
+                for s in specs]
+        t0 = time.perf_counter()
+        plan.autotune(cubes, outs, reps=1)
+        tune_s = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            plan.run_cpi(cubes, outs)
+        torch.cuda.synchronize()
+        times = time_steps(lambda: plan.run_cpi(cubes, outs), steps, flush, stream)
+        code, failed = plan.status()
+        if code != stap.STAP_OK:
+            raise RuntimeError(f"batch {PREC_NAMES[prec]}: device status {code} ({failed} failed)")
+        outs_pick[prec] = {i: outs[i][:, :, b * 64:(b + 1) * 64].cpu().numpy() for i, b in picks}
+        ms = sum(times) / steps
+        res["mixed" if prec else "fp32"] = {
+            "precision": PREC_NAMES[prec], "arithmetic": PREC_TEXT[prec] + "; " + SOLVE_TEXT,
+            "value": cells / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "autotune_s": tune_s,
+            "gpu_launches_per_step": 4 * len(specs),
+            "fp64_solve_frac_of_step": sum(solve_flops(s) for s in specs) / (ms * 1e-3) / 1e12 /
+            peaks()["fp64_tflops"]}
+        plan.close()
+        del outs
+        torch.cuda.empty_cache()
+    res["mixed_vs_fp32"] = res["mixed"]["value"] / res["fp32"]["value"]
+    if not args.no_cpu_baseline:
+        import oracle
+        errs = {}
+        for prec, got in outs_pick.items():
+            num = den = worst = 0.0
+            for i, b in picks:
+                s = specs[i]
+                key = (i, b)
+                if key not in errs:
+                    errs[key] = oracle.run(oracle.Dims(*s.dims()), cubes[i].cpu().numpy(), r0=b * 64,
+                                           nr=64)["out"]
+                ref = errs[key]
+                num += float(np.sum((got[i].astype(np.float64) - ref) ** 2))
+                den += float(np.sum(ref ** 2))
+                worst = max(worst, power_errors(got[i], ref)["max_cell"])
+            res.setdefault("errors_vs_oracle", {})[PREC_NAMES[prec]] = {
+                "normwise": (num / den) ** 0.5, "max_cell": worst, "blocks": len(picks)}
+    del cubes
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_batch(args):

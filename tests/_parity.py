@@ -10,21 +10,29 @@ EPS32 = 2.0 ** -24          # unit roundoff of FP32
 # for D <= 12 (grown by (D + 2)/14 above).  No FP32 path reaches 1e-5 in every
 # cell: the FP32 Doppler output, the complex64 weights and the FP32 apply
 # alone leave 5.9e-5 in the worst cell of the standard CPI (measured by feeding
-# the FP64 oracle those roundings); the bar sits at about 5x that floor.
-PLAIN_CELL_BAR = 1e-3
+# the FP64 oracle those roundings).  The bar is 5x that floor; the largest
+# value the GPU path shows across these tests, after the growth factor, is
+# 1.2e-4.
+PLAIN_CELL_BAR = 3e-4
 
 # The mixed-precision contraction modes (tensor-core covariance and apply,
 # FP64 solve), as (test id, stap precision value).
 MIXED_PRECISIONS = [("tf32x3", 2), ("bf16x3", 1), ("fp16s", 3)]
 
-# Worst cell of the mixed path, |P - P_ref| / max(P_ref, median P_ref), for
-# D <= 12 (grown by (D + 2)/14 above, as the normwise bars).  The mixed
-# contractions leave a relative error of about 2^-21 in each product (against
-# the plain path's error-free covariance); the plain path's floor study put a
-# complex64 rounding of the covariance (2^-24) at 8.0e-4 in the worst cell of
-# the standard CPI, so 2^3 x 8.0e-4 = 6.4e-3 is the scale of the mixed
-# path's worst cell, and the bar sits at about 1.5x that.
-MIXED_CELL_BAR = 1e-2
+# Worst cell of the mixed path, |P - P_ref| / max(P_ref, median P_ref).  The
+# split products and their FP32 accumulation leave a relative error of about
+# eps = 2^-21 in each covariance (all three arithmetics).  To first order, a
+# relative covariance error eps moves the loaded solution by at most
+# kappa eps, and the diagonal load bounds the conditioning:
+# kappa <= (tr R + delta) / delta = D / lf + 1 with delta = lf tr R / D.  The
+# output power is quadratic in the weights, so a cell's power moves by about
+# 2 kappa eps of the power floor.
+def mixed_cell_bar(spec, load_factor=1e-3):
+    return 2.0 * 2.0 ** -21 * (spec.D / load_factor + 1.0)
+
+
+# Normwise error of the mixed path: the task's 1e-3, at every size.
+MIXED_NORM_BAR = 1e-3
 
 
 def to_np(t):

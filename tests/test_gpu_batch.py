@@ -9,7 +9,7 @@ import torch
 import oracle
 from paper_2203_06233_gb300 import stap, synth
 
-from _parity import MIXED_CELL_BAR, MIXED_PRECISIONS, PLAIN_CELL_BAR, power_errors
+from _parity import MIXED_NORM_BAR, MIXED_PRECISIONS, PLAIN_CELL_BAR, mixed_cell_bar, power_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -98,7 +98,7 @@ def test_full_batch_workload_on_sampled_cpis():
             if pname == "plain":
                 ok = e_norm <= 1e-5 * g and e_cell <= PLAIN_CELL_BAR * g
             else:
-                ok = e_norm <= 1e-3 * g and e_cell <= MIXED_CELL_BAR * g
+                ok = e_norm <= MIXED_NORM_BAR and e_cell <= mixed_cell_bar(s)
             if not ok:
                 bad.append((pname, i, e_cell, e_norm))
         plan.close()

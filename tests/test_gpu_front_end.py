@@ -12,7 +12,7 @@ import torch
 import oracle
 from paper_2203_06233_gb300 import stap, synth
 
-from _parity import EPS32, power_errors, to_np
+from _parity import EPS32, PLAIN_CELL_BAR, power_errors, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -76,7 +76,7 @@ def test_subarray_front_end_end_to_end_matches_the_oracle(C):
     e_cell, e_norm = power_errors(out, ref)
     g = max(1.0, (spec.D + 2) / 14.0)
     print(f"C{C}: max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
-    assert e_norm <= 1e-5 * g and e_cell <= 1e-3 * g
+    assert e_norm <= 1e-5 * g and e_cell <= PLAIN_CELL_BAR * g
     assert int(np.argmax(out[2, 24])) == 128           # the target through the subarrays
     plan.close()
 
@@ -113,7 +113,7 @@ def test_streamed_element_cubes_in_chunks_match_the_oracle():
     for o, x in zip(outs, cubes):
         ref = oracle.run(d, oracle.reduce_channels(W, x), steer=steer)["out"]
         e_cell, e_norm = power_errors(o.numpy(), ref)
-        assert e_norm <= 1e-5 and e_cell <= 1e-3, (e_norm, e_cell)
+        assert e_norm <= 1e-5 and e_cell <= PLAIN_CELL_BAR, (e_norm, e_cell)
     plan.close()
 
 

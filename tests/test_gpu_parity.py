@@ -23,7 +23,7 @@ import torch
 import oracle
 from paper_2203_06233_gb300 import stap, synth
 
-from _parity import EDGE_SPECS, EPS32, cell_bound, power_errors, to_np
+from _parity import EDGE_SPECS, EPS32, PLAIN_CELL_BAR, cell_bound, power_errors, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -153,7 +153,7 @@ def test_run_cpi_end_to_end(spec):
     g = growth(spec)
     print(f"dims={spec.dims()} max-cell/floor={e_cell:.3e} normwise={e_norm:.3e} (x{g:.2f})")
     assert e_norm <= 1e-5 * g, e_norm
-    assert e_cell <= 1e-3 * g, e_cell
+    assert e_cell <= PLAIN_CELL_BAR * g, e_cell
     assert plan.status() == (stap.STAP_OK, 0)
 
 
@@ -188,6 +188,7 @@ def test_user_steering_override():
     plan.set_steering(steer)
     out = to_np(plan.run_cpi(_dev(cube, torch.complex64)))
     e_cell, e_norm = power_errors(out, ref)
+    print(f"steering override: max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
     assert e_norm <= 1e-5 and e_cell <= 1e-3, (e_cell, e_norm)
 
 
@@ -199,6 +200,7 @@ def test_load_factor_parity(lf):
     ref = oracle.run(d, cube, load_factor=lf)["out"]
     out = to_np(_plan(spec, load_factor=lf).run_cpi(_dev(cube, torch.complex64)))
     e_cell, e_norm = power_errors(out, ref)
+    print(f"load factor {lf}: max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
     assert e_norm <= 1e-5 and e_cell <= 1e-3, (lf, e_cell, e_norm)
 
 
@@ -237,7 +239,7 @@ def test_standard_workload_full_size_parity_and_launch_configuration():
     out = to_np(plan.run_cpi(_dev(cube, torch.complex64)))
     e_cell, e_norm = power_errors(out, res["out"])
     print(f"standard workload: max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
-    assert e_norm <= 1e-5 and e_cell <= 1e-3
+    assert e_norm <= 1e-5 and e_cell <= PLAIN_CELL_BAR
 
 
 @pytest.mark.parametrize("spec", [synth.small_cpi(), synth.standard_cpi(), EDGE_SPECS[2], EDGE_SPECS[3],
@@ -412,7 +414,7 @@ def test_mixed_refinement_end_to_end_meets_the_plain_bar(spec):
     e_cell, e_norm = power_errors(out, ref)
     print(f"{spec.dims()} mixed refinement: max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
     g = growth(spec)
-    assert e_norm <= 1e-5 * g and e_cell <= 1e-3 * g
+    assert e_norm <= 1e-5 * g and e_cell <= PLAIN_CELL_BAR * g
 
 
 def test_mixed_refinement_flags_breakdown():

@@ -9,7 +9,7 @@ import torch
 import oracle
 from paper_2203_06233_gb300 import stap, synth
 
-from _parity import power_errors
+from _parity import PLAIN_CELL_BAR, power_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -64,7 +64,8 @@ def test_slabbed_run_matches_oracle():
     d = oracle.Dims(*spec.dims())
     ref = oracle.run(d, cube_np)["out"]
     e_cell, e_norm = power_errors(out.cpu().numpy(), ref)
-    assert e_norm <= 1e-5 and e_cell <= 1e-3, (e_cell, e_norm)
+    print(f"slabs: max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
+    assert e_norm <= 1e-5 and e_cell <= PLAIN_CELL_BAR, (e_cell, e_norm)
 
 
 def test_one_cpi_autotune_picks_a_slab_count(tmp_path):

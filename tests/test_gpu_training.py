@@ -8,7 +8,7 @@ import torch
 import oracle
 from paper_2203_06233_gb300 import stap, synth
 
-from _parity import power_errors, to_np
+from _parity import PLAIN_CELL_BAR, power_errors, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -54,7 +54,7 @@ def test_run_cpi_with_neighbour_training_matches_the_oracle(name, solver):
     e_cell, e_norm = power_errors(out, ref)
     print(f"{name}: max-cell/floor={e_cell:.3e} normwise={e_norm:.3e}")
     g = growth(spec)
-    assert e_norm <= 1e-5 * g and e_cell <= 1e-3 * g
+    assert e_norm <= 1e-5 * g and e_cell <= PLAIN_CELL_BAR * g
     plan.close()
 
 

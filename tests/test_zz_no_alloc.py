@@ -14,7 +14,7 @@ import pytest
 
 from paper_2203_06233_gb300 import stap, synth
 
-from _parity import power_errors
+from _parity import PLAIN_CELL_BAR, power_errors
 
 
 def _noalloc_dims():
@@ -99,4 +99,4 @@ def test_noalloc_matches_workspace_entry_point_on_consecutive_calls():
         s, _, _, okw = cases[i]
         ref = oracle.run(oracle.Dims(*s.dims()), synth.make_cube(s), **okw)["out"]
         e_cell, e_norm = power_errors(outs[i].cpu().numpy(), ref)
-        assert e_norm <= 1e-5 and e_cell <= 1e-3, (i, e_cell, e_norm)
+        assert e_norm <= 1e-5 and e_cell <= PLAIN_CELL_BAR, (i, e_cell, e_norm)
