@@ -173,6 +173,44 @@ def make_cube(spec: CPISpec, chan_chunk: int = 4) -> np.ndarray:
     return cube
 
 
+def make_cube_window(spec: CPISpec, r0: int, nr: int) -> np.ndarray:
+    """Range cells [r0, r0 + nr) of ``make_cube(spec)``, bit for bit, without
+    generating the rest of the cube (every sample's counters depend only on
+    its own (channel, pulse, cell) and (patch, cell) indices)."""
+    C, P, R = spec.n_chan, spec.n_pulses, spec.n_range
+    if not (0 <= r0 and nr >= 0 and r0 + nr <= R):
+        raise ValueError("window outside the range axis")
+    cube = np.empty((C, P, nr), np.complex64)
+    f = patch_frequencies()
+    r = np.arange(r0, r0 + nr, dtype=np.uint64)
+    alpha = None
+    if spec.cnr_db is not None:
+        cnr = 10.0 ** (spec.cnr_db / 10.0)
+        idx = (np.arange(N_PATCH, dtype=np.uint64)[:, None] * np.uint64(R) + r[None, :]).ravel()
+        alpha = complex_normal(spec.seed, STREAM_CLUTTER, idx, cnr / N_PATCH, spec.sub).reshape(N_PATCH, nr)
+    dop_steer = np.exp(2j * np.pi * np.outer(np.arange(P), f))            # [P][patch]
+    for c in range(C):
+        blk = np.zeros((P, nr), np.complex128)
+        if spec.noise:
+            idx = (np.uint64(c * P * R) + np.arange(P, dtype=np.uint64)[:, None] * np.uint64(R) +
+                   r[None, :]).ravel()
+            blk += complex_normal(spec.seed, STREAM_NOISE, idx, 1.0, spec.sub).reshape(P, nr)
+        if alpha is not None:
+            sp = np.exp(2j * np.pi * f * c)
+            blk += (dop_steer * sp[None, :]) @ alpha
+        cube[c] = blk
+    for t in spec.targets:
+        if r0 <= t.r0 < r0 + nr:
+            th = np.deg2rad(steering_angle_deg(t.s0, spec.n_steering))
+            fs = 0.5 * np.sin(th)
+            amp = np.sqrt(10.0 ** (t.snr_db / 10.0)) * np.exp(1j * t.phase)
+            sig = amp * np.exp(2j * np.pi * fs * np.arange(C))[:, None] * \
+                np.exp(2j * np.pi * (t.k0 / spec.n_dop) * np.arange(P))[None, :]
+            j = t.r0 - r0
+            cube[:, :, j] = (cube[:, :, j].astype(np.complex128) + sig).astype(np.complex64)
+    return cube
+
+
 # ----------------------------------------------------------------------------
 # The workloads: a small single-CPI case, the standard single-CPI case, a
 # mixed-precision case, a batch of uneven CPIs and a large single CPI.

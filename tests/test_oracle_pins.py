@@ -641,3 +641,14 @@ def test_subarray_weights_and_their_gain_closed_form():
         z = np.exp(2j * np.pi * f)
         b = z ** (np.arange(C) * M) * (1 - z ** M) / (1 - z)
         np.testing.assert_allclose(st[s], g0 * b, rtol=0, atol=1e-11 * np.abs(g0 * b).max())
+
+
+def test_cube_window_equals_the_slice_of_the_whole_cube():
+    """The input generator's range windows are the whole cube's slices, bit
+    for bit (so windowed oracle runs see exactly the benchmark's input)."""
+    for spec in (synth.small_cpi(),
+                 synth.CPISpec(3, 20, 32, 96, 2, 32, 5, cnr_db=30.0,
+                               targets=(synth.Target(50, 3, 1, 12.0),), seed=11)):
+        whole = synth.make_cube(spec)
+        for r0, nr in ((0, spec.training_block), (spec.n_range - 17, 17), (33, 40), (0, spec.n_range)):
+            np.testing.assert_array_equal(synth.make_cube_window(spec, r0, nr), whole[:, :, r0:r0 + nr])
