@@ -46,12 +46,16 @@ SOLVE_KERNELS = {1: "solve_reg_kernel (register-resident FP64 LDL^H, solves, ref
 
 
 def peaks():
-    p = {"hbm_gbs": 6800.0, "src": "fallback"}
+    """Roofline denominators: MEASURED_PEAKS.json (HBM copy bandwidth, cuBLAS
+    bf16 burst and sustained) when present, else the recipe's fallbacks; FP64
+    and FP32 ALU peaks from unit counts and the maximum SM clock."""
+    p = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
             m = json.load(f)
-        p = {"hbm_gbs": float(m["hbm_gbs"]), "src": "measured"}
+        p = {"hbm_gbs": float(m["hbm_gbs"]), "bf16_tflops": float(m.get("bf16_tflops", 1900.0)),
+             "bf16_tflops_sustained": float(m.get("bf16_tflops_sustained", 1700.0)), "src": "measured"}
     # FP64 / FP32 ALU peaks from unit counts and the maximum SM clock:
     # 152 SMs x 2 DFMA lanes/clk (x2 flops) and x 128 FFMA lanes/clk (x2 flops) at 2070 MHz.
     p["fp64_tflops"] = 152 * 2 * 2 * 2.070e9 / 1e12
@@ -312,11 +316,11 @@ def kernel_figures(spec, prec, kt, pk, refine=1):
     return out
 
 
-def run_leg(spec, cube, dev, prec, args, flush, stream, kernel_reps, timed=None, keep_out=False,
+def run_leg(spec, cube, dev, prec, args, flush, stream, kernel_reps, timed=None, barrier=None,
             solver=0, refine=1):
     """One path on the workload's cube: plan, autotune (untimed), warm-up,
-    args.steps timed steps (inside `timed`, a context manager, if given),
-    per-step kernel times; returns (plan, out, leg dict)."""
+    args.steps timed steps (after `barrier()` and inside `timed`, a context
+    manager, if given), per-step kernel times; returns (plan, out, leg dict)."""
     import contextlib
     import torch
     from paper_2203_06233_gb300 import stap
@@ -333,6 +337,8 @@ def run_leg(spec, cube, dev, prec, args, flush, stream, kernel_reps, timed=None,
     code, failed = plan.status()
     if code != stap.STAP_OK:
         raise RuntimeError(f"{PREC_NAMES[prec]}: device status {code} ({failed} failed systems)")
+    if barrier is not None:
+        barrier()
     with (timed if timed is not None else contextlib.nullcontext()):
         times = time_steps(lambda: plan.run_cpi(cube, out), args.steps, flush, stream)
     plan.run_cpi(cube, out)
@@ -404,22 +410,26 @@ def run_gpu(args):
                                  warmup=args.warmup)
         legs, outs_blocks = {}, {}
         clk = ClockSampler(local) if head else None
+        mplan = mout = None
+
+        def barrier():
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+
         for prec in (mprec, 0):
-            timed = None
-            if head and prec == mprec:
-                if world > 1:
-                    dist.barrier()
-                torch.cuda.synchronize()
-                timed = clk
-            plan, out, leg = run_leg(spec, cube, dev, prec, sub, flush, stream, kernel_reps, timed=timed)
-            legs[prec] = (plan, out, leg)
+            keep = head and prec == mprec          # the headline leg: timed with clocks, kept for e2e
+            plan, out, leg = run_leg(spec, cube, dev, prec, sub, flush, stream, kernel_reps,
+                                     timed=clk if keep else None, barrier=barrier if keep else None)
             outs_blocks[prec] = {b: out[:, :, b * B:(b + 1) * B].cpu().numpy() for b in blocks}
-            if not (head and prec == mprec):
+            legs[prec] = leg
+            if keep:
+                mplan, mout = plan, out
+            else:
                 plan.close()
-                del out
+                del plan, out
                 torch.cuda.empty_cache()
-        mplan, mout, mleg = legs[mprec]
-        fleg = legs[0][2]
+        mleg, fleg = legs[mprec], legs[0]
         errors, cpu = {}, None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             refs, cpu = oracle_on_blocks(spec, cube_h, blocks)
@@ -427,14 +437,13 @@ def run_gpu(args):
         mvalue = world * cells / (mleg["ms_per_step"] * 1e-3)
         fvalue = world * cells / (fleg["ms_per_step"] * 1e-3)
         if not head:
-            mplan.close()
             extra[name] = {
                 "config": workload_config(spec, name),
                 "mixed": dict(mleg, value=mvalue, kernels=kernel_figures(spec, mprec, mleg["kernels_ms"], pk)),
                 "fp32": dict(fleg, value=fvalue, kernels=kernel_figures(spec, 0, fleg["kernels_ms"], pk)),
                 "mixed_vs_fp32": mvalue / fvalue, "errors_vs_oracle": errors,
                 "cpu_baseline": cpu}
-            del mout, cube
+            del cube
             torch.cuda.empty_cache()
             continue
         # ---- headline: the mixed leg's timed region ----
@@ -681,7 +690,7 @@ def run_batch(args):
                    "cells_per_step": cells, "n_cpi": len(specs), "distinct_shapes": len(shapes),
                    "workspace_gib": plan.workspace.numel() / 2 ** 30,
                    "batch_bytes_gib": plan.batch_bytes / 2 ** 30,
-                   "precision": "plain FP32 contractions, FP64 solve, 1 refinement step",
+                   "precision": PREC_TEXT[0] + "; " + SOLVE_TEXT,
                    "l2": "inputs (47 GB of cubes) larger than L2; L2 also flushed between steps",
                    "tuned_shapes": len(tuning), "parallelism": "one batch per GPU per step"},
         "e2e": e2e,

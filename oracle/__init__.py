@@ -97,6 +97,8 @@ def lib():
         L.oracle_run.argtypes = [D, P, P, ctypes.c_double, i32, i32, P, P, P, P, P]
         L.oracle_train_neighbours.argtypes = [D, P, i32, i32, i32, P]
         L.oracle_run_neighbours.argtypes = [D, P, P, ctypes.c_double, i32, i32, P, P]
+        L.oracle_train_window.argtypes = [D, P, i32, i32, i32, i32, i32, P]
+        L.oracle_run_window.argtypes = [D, P, P, ctypes.c_double, i32, i32, i32, i32, P, P]
         L.oracle_doppler_staggered.argtypes = [D, P, i32, i32, P]
         L.oracle_default_steering_staggered.argtypes = [D, P]
         L.oracle_run_staggered.argtypes = [D, P, P, ctypes.c_double, i32, i32, P, P, P, P, P]
@@ -106,7 +108,8 @@ def lib():
         for f in ("oracle_doppler_window", "oracle_doppler", "oracle_snapshot", "oracle_covariance",
                   "oracle_cholesky", "oracle_cholesky_solve", "oracle_default_steering",
                   "oracle_weights", "oracle_apply", "oracle_run", "oracle_train_neighbours",
-                  "oracle_run_neighbours", "oracle_doppler_staggered",
+                  "oracle_run_neighbours", "oracle_train_window", "oracle_run_window",
+                  "oracle_doppler_staggered",
                   "oracle_default_steering_staggered", "oracle_run_staggered",
                   "oracle_reduce_channels", "oracle_subarray_weights", "oracle_reduced_steering"):
             getattr(L, f).restype = ctypes.c_int
@@ -237,6 +240,18 @@ def train_neighbours(d: Dims, cov) -> np.ndarray:
     return out
 
 
+def train_window(d: Dims, cov, guard: int, half: int) -> np.ndarray:
+    """Training matrices cov_t[K][NG][D][D] of the sliding training window
+    (``half`` groups on each side beyond ``guard`` guard groups) from the
+    per-group covariances cov[K][NG][D][D] of a whole range."""
+    cov = _c128(cov)
+    K, nb = cov.shape[:2]
+    out = np.empty_like(cov)
+    _check(lib().oracle_train_window(ctypes.byref(d.c()), _ptr(cov), nb, 0, nb, int(guard), int(half),
+                                     _ptr(out)), "train_window")
+    return out
+
+
 def reduce_channels(W, x) -> np.ndarray:
     """y[C][P][R] = sum_n conj(W[c][n]) x[n][P][R]: the reduced-DOF front end
     (N element channels of x combined into C channels by W[C][N])."""
@@ -291,18 +306,39 @@ def default_steering_staggered(d: Dims) -> np.ndarray:
 
 
 def run(d: Dims, cube, r0=0, nr=None, steer=None, load_factor=1e-3, keep=False, training=0,
-        staggered=False):
+        staggered=False, guard=0, half=1):
     """Steps 1-8 on the range cells [r0, r0+nr) of a [C][P][R] cube.
 
     Returns a dict with ``out`` [S][K][nr] (float64), ``status`` [K][nr/B] and
     ``n_failed``; with ``keep`` also ``dop``, ``cov`` and ``wts``.  With
     ``training=1`` each block is trained on its neighbours (``train_neighbours``);
     the window is then computed from a slab one block wider on each side.  With
+    ``training=2`` each group of B cells is trained on a sliding window
+    (``train_window``: ``half`` groups on each side beyond ``guard`` guard
+    groups), computed from a slab guard + half groups wider on each side.  With
     ``staggered`` the snapshots are PRI-staggered (``doppler_staggered``; ``dop``
     is then [T*C][K][nr]).
     """
     if training and staggered:
         raise ValueError("neighbour training with staggered snapshots is not defined here")
+    if training == 2:
+        if keep:
+            raise ValueError("keep is not available with a training window")
+        nr = d.n_range - r0 if nr is None else nr
+        B = d.training_block
+        if d.n_range // B < 2 * guard + 2 or half < 1 or guard < 0:
+            raise ValueError("the training window needs half >= 1, guard >= 0, NB >= 2 guard + 2")
+        ext = (guard + half) * B
+        e0, e1 = max(0, r0 - ext), min(d.n_range, r0 + nr + ext)
+        x = _c128(np.asarray(cube)[:, :, e0:e1])
+        out = np.empty((d.n_steering, d.n_dop, nr), np.float64)
+        status = np.empty((d.n_dop, nr // B), np.int32)
+        st = None if steer is None else _c128(steer)
+        rc = lib().oracle_run_window(ctypes.byref(d.c(e1 - e0)), _ptr(x),
+                                     _ptr(st) if st is not None else ctypes.c_void_p(0),
+                                     float(load_factor), r0 - e0, nr, int(guard), int(half),
+                                     _ptr(out), _ptr(status))
+        return {"out": out, "status": status, "n_failed": _check(rc, "run")}
     if training:
         if keep:
             raise ValueError("keep is not available with neighbour training")

@@ -22,7 +22,9 @@
  *   3. Covariance per (Doppler bin k, range block b of B cells) (statement U):
  *        R_{k,b} = (1/B) sum_{r in block b} x_{k,r} x_{k,r}^H
  *      Optional training with guard cells (not in the paper): block b's
- *      weights use the mean of R_{k,b-1} and R_{k,b+1} (oracle_train_neighbours).
+ *      weights use the mean of R_{k,b-1} and R_{k,b+1} (oracle_train_neighbours),
+ *      or, more generally, a sliding window of training groups beyond a guard
+ *      band on each side of the group under test (oracle_train_window).
  *   4. Diagonal loading:  delta = lf * Re tr(R) / D,  Rl = R + delta I.
  *   5. Cholesky Rl = L L^H (L lower, real positive diagonal), column by column.
  *   6. u_s = Rl^{-1} v_s by forward then back substitution (no refinement:
@@ -470,6 +472,101 @@ int oracle_run_neighbours(const oracle_dims* d, const cplx* cube, const cplx* st
   if ((rc = oracle_doppler(d, cube, 0, W, dop)) != ORACLE_OK) goto done;
   if ((rc = oracle_covariance(d, dop, W, cov)) != ORACLE_OK) goto done;
   if ((rc = oracle_train_neighbours(d, cov, NBS, w0 / B, NBW, trn)) != ORACLE_OK) goto done;
+  for (int c = 0; c < C; ++c)
+    for (int k = 0; k < K; ++k)
+      memcpy(dopw + ((size_t)c * K + k) * nr, dop + ((size_t)c * K + k) * W + w0, sizeof(cplx) * nr);
+  int failed = oracle_weights(d, trn, K * NBW, steer, load_factor, wts, status);
+  if (failed < 0) {
+    rc = failed;
+    goto done;
+  }
+  if ((rc = oracle_apply(d, dopw, nr, wts, out)) != ORACLE_OK) goto done;
+  rc = failed;
+done:
+  free(dop);
+  free(dopw);
+  free(cov);
+  free(trn);
+  free(wts);
+  free(steer_t);
+  return rc;
+}
+
+/* Sliding training window with guard cells (a reading beyond the paper,
+ * which trains each block on its own cells; it generalises the neighbour-block
+ * training above).  The range axis is cut into groups of B cells (B = 1: each
+ * cell is its own group, i.e. a per-cell window); group j's weights come from
+ * the training groups
+ *   T(j) = { j-guard-half, ..., j-guard-1 }  u  { j+guard+1, ..., j+guard+half }
+ * that exist in 0 .. nb-1: `guard` groups on each side of j (and j itself)
+ * are guard cells, left out of j's training data, and `half` groups on each
+ * side beyond them train it.  Near the ends of the range the groups that do
+ * not exist are dropped.  The training covariance is the mean of the groups'
+ * covariances, summed left side first, in increasing group order:
+ *   R_train(j) = (1 / |T(j)|) sum_{i in T(j)} R_{k,i}
+ * which with equal group sizes is the sample covariance of all the training
+ * cells.  guard = 0, half = 1 is the neighbour-block training.  Needs
+ * half >= 1, guard >= 0 and nb >= 2 guard + 2 (then every group has
+ * training groups on at least one side).
+ * cov_in: [K][nb][D][D] for nb consecutive groups that include every group
+ * that trains a window group; out: [K][nbw][D][D] for the groups
+ * b0 .. b0+nbw-1 of cov_in. */
+int oracle_train_window(const oracle_dims* d, const cplx* cov_in, int32_t nb, int32_t b0,
+                        int32_t nbw, int32_t guard, int32_t half, cplx* out) {
+  if (!dims_ok(d) || !cov_in || !out || guard < 0 || half < 1 || nb < 2 * guard + 2 || b0 < 0 ||
+      nbw < 1 || b0 + nbw > nb)
+    return ORACLE_BAD_ARGS;
+  const int K = d->n_dop, D = d->n_chan * d->tdof;
+  const size_t DD = (size_t)D * D;
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < K; ++k)
+    for (int jw = 0; jw < nbw; ++jw) {
+      const int j = b0 + jw;
+      cplx* o = out + ((size_t)k * nbw + jw) * DD;
+      for (size_t e = 0; e < DD; ++e) o[e] = 0.0;
+      int count = 0;
+      for (int side = 0; side < 2; ++side)
+        for (int m = 0; m < half; ++m) {
+          const int i = side == 0 ? j - guard - half + m : j + guard + 1 + m;
+          if (i < 0 || i >= nb) continue;
+          const cplx* in = cov_in + ((size_t)k * nb + i) * DD;
+          for (size_t e = 0; e < DD; ++e) o[e] += in[e];
+          ++count;
+        }
+      for (size_t e = 0; e < DD; ++e) o[e] /= (double)count;
+    }
+  return ORACLE_OK;
+}
+
+/* Steps 1-8 with the sliding training window above, for the window of nr
+ * cells starting at cell w0 of a cube slab of d->n_range cells; the slab
+ * reaches (guard + half) groups beyond the window on each side unless the
+ * window touches that end of the range (the slab then starts or ends there).
+ * out: [S][K][nr]; status: [K][nr/B]. */
+int oracle_run_window(const oracle_dims* d, const cplx* cube, const cplx* steer, double load_factor,
+                      int32_t w0, int32_t nr, int32_t guard, int32_t half, double* out,
+                      int32_t* status) {
+  if (!dims_ok(d) || !cube || !out || !window_ok(d, w0, nr)) return ORACLE_BAD_ARGS;
+  const int B = d->training_block;
+  if (w0 % B != 0) return ORACLE_BAD_ARGS;
+  const int C = d->n_chan, K = d->n_dop, S = d->n_steering, D = d->n_chan * d->tdof;
+  const int W = d->n_range, NBS = W / B, NBW = nr / B;
+  if (guard < 0 || half < 1 || NBS < 2 * guard + 2) return ORACLE_BAD_ARGS;
+  cplx* dop = (cplx*)malloc(sizeof(cplx) * (size_t)C * K * W);
+  cplx* dopw = (cplx*)malloc(sizeof(cplx) * (size_t)C * K * nr);
+  cplx* cov = (cplx*)malloc(sizeof(cplx) * (size_t)K * NBS * D * D);
+  cplx* trn = (cplx*)malloc(sizeof(cplx) * (size_t)K * NBW * D * D);
+  cplx* wts = (cplx*)malloc(sizeof(cplx) * (size_t)K * NBW * S * D);
+  cplx* steer_t = NULL;
+  int rc = ORACLE_NO_MEMORY;
+  if (!steer) {
+    steer = steer_t = (cplx*)malloc(sizeof(cplx) * (size_t)S * D);
+    if (steer_t && oracle_default_steering(d, steer_t) != ORACLE_OK) goto done;
+  }
+  if (!dop || !dopw || !cov || !trn || !wts || !steer) goto done;
+  if ((rc = oracle_doppler(d, cube, 0, W, dop)) != ORACLE_OK) goto done;
+  if ((rc = oracle_covariance(d, dop, W, cov)) != ORACLE_OK) goto done;
+  if ((rc = oracle_train_window(d, cov, NBS, w0 / B, NBW, guard, half, trn)) != ORACLE_OK) goto done;
   for (int c = 0; c < C; ++c)
     for (int k = 0; k < K; ++k)
       memcpy(dopw + ((size_t)c * K + k) * nr, dop + ((size_t)c * K + k) * W + w0, sizeof(cplx) * nr);

@@ -35,6 +35,10 @@ MUTANTS = {
                            "const cplx* lo = b > 0 ? cov_in + ((size_t)k * nb + b) * DD : NULL;"),
     "training_mean_scale": ("if (lo && hi) o[e] = 0.5 * (lo[e] + hi[e]);",
                             "if (lo && hi) o[e] = lo[e] + hi[e];"),
+    "window_includes_own_group": ("const int i = side == 0 ? j - guard - half + m : j + guard + 1 + m;",
+                                  "const int i = side == 0 ? j - guard - half + m + 1 : j + guard + 1 + m;"),
+    "window_mean_count": ("for (size_t e = 0; e < DD; ++e) o[e] /= (double)count;",
+                          "for (size_t e = 0; e < DD; ++e) o[e] /= (double)(2 * half);"),
     "staggered_phase_reference": ("acc += h[p - t] * x * tw[((int64_t)p * k) % K];",
                                   "acc += h[p - t] * x * tw[((int64_t)(p - t) * k) % K];"),
     "staggered_window_length": ("const int Ps = P - T + 1;", "const int Ps = P - T;"),

@@ -6,6 +6,7 @@ The paper (arXiv 2203.06233) prints no STAP numbers, so nothing here is a
 value from it; the definitions pinned are the post-Doppler reading of its STAP
 kernel (Sec. 4.2: `fft` over pulses, 2-D x 2-D array multiply).
 """
+import dataclasses
 from fractions import Fraction
 
 import numpy as np
@@ -458,6 +459,76 @@ def test_neighbour_training_noise_only_output_mean_above_one():
     d = oracle.Dims(*spec.dims())
     P = oracle.run(d, synth.make_cube(spec), training=1)["out"]
     assert 1.0 < P.mean() < 1.1, P.mean()
+
+
+# --------------------------------------------- sliding training window ----
+# Group j (B cells; B = 1: one cell) trains on the `half` groups on each side
+# beyond `guard` guard groups, dropping groups outside the range.
+
+@pytest.mark.parametrize("B,guard,half", [(1, 2, 6), (4, 1, 3), (16, 0, 1), (8, 2, 1)])
+def test_training_window_is_the_covariance_of_exactly_its_training_cells(B, guard, half):
+    """Group j's training matrix is the sample covariance of the cells of
+    groups j-guard-half .. j-guard-1 and j+guard+1 .. j+guard+half that exist,
+    computed here from the gathered snapshots of exactly those cells."""
+    R = 96
+    NG = R // B
+    d = dims(C=2, P=8, K=8, R=R, T=3, B=B, S=1)
+    dop = crandn(2, 8, R)
+    got = oracle.train_window(d, oracle.covariance(d, dop), guard, half)
+    x = _gather(dop, 3)                                          # [K][R][D]
+    for j in range(NG):
+        groups = [i for i in list(range(j - guard - half, j - guard)) +
+                  list(range(j + guard + 1, j + guard + half + 1)) if 0 <= i < NG]
+        assert groups and j not in groups
+        cells = [r for i in groups for r in range(B * i, B * i + B)]
+        xs = x[:, cells]
+        ref = np.einsum("kri,krj->kij", xs, xs.conj()) / len(cells)
+        assert np.max(np.abs(got[:, j] - ref)) < 1e-13 * np.max(np.abs(ref)), j
+
+
+def test_training_window_reduces_to_neighbour_blocks_and_rejects_short_ranges():
+    d = dims(C=2, P=8, K=8, R=80, T=3, B=16, S=1)                # NB = 5
+    cov = oracle.covariance(d, crandn(2, 8, 80))
+    np.testing.assert_array_equal(oracle.train_window(d, cov, 0, 1), oracle.train_neighbours(d, cov))
+    with pytest.raises(RuntimeError):
+        oracle.train_window(d, cov, 2, 1)                        # NB = 5 < 2 guard + 2
+    with pytest.raises(RuntimeError):
+        oracle.train_window(d, cov, 0, 0)
+
+
+def test_training_window_run_composes_and_windows_are_slices():
+    spec = synth.CPISpec(3, 16, 32, 128, 3, 4, 4, cnr_db=30.0,
+                         targets=(synth.Target(40, 7, 1, 10.0),), seed=9)
+    d = oracle.Dims(*spec.dims())
+    cube = synth.make_cube(spec)
+    full = oracle.run(d, cube, training=2, guard=1, half=4)
+    dop = oracle.doppler(d, cube)
+    w, _, _ = oracle.weights(d, oracle.train_window(d, oracle.covariance(d, dop), 1, 4))
+    np.testing.assert_array_equal(full["out"], oracle.apply(d, dop, w))
+    for r0, nr in ((0, 8), (40, 24), (120, 8), (0, 128)):       # ends, middle, whole
+        part = oracle.run(d, cube, r0=r0, nr=nr, training=2, guard=1, half=4)
+        np.testing.assert_array_equal(part["out"], full["out"][:, :, r0:r0 + nr])
+
+
+def test_per_cell_training_window_keeps_the_target_out_of_its_own_training():
+    """Per-cell windows (B = 1) with a guard of 2 cells on each side and 16
+    training cells on each side: the small workload's target no longer trains
+    its own weights, so its output stands far higher above the median than
+    with own-block training (and above the neighbour-block form's), and is its
+    row's maximum."""
+    spec = synth.small_cpi()
+    cube = synth.make_cube(spec)
+    own = oracle.run(oracle.Dims(*spec.dims()), cube)["out"]
+    nbr = oracle.run(oracle.Dims(*spec.dims()), cube, training=1)["out"]
+    cell = dataclasses.replace(spec, training_block=1)
+    win = oracle.run(oracle.Dims(*cell.dims()), cube, training=2, guard=2, half=16)["out"]
+    assert int(np.argmax(win[2, 24])) == 128
+    ratio_own = own[2, 24, 128] / np.median(own)
+    ratio_nbr = nbr[2, 24, 128] / np.median(nbr)
+    ratio_win = win[2, 24, 128] / np.median(win)
+    print(f"target over median: own block {ratio_own:.1f}, neighbour blocks {ratio_nbr:.1f}, "
+          f"per-cell window {ratio_win:.1f}")
+    assert ratio_win > 4 * ratio_own and ratio_win > ratio_nbr, (ratio_own, ratio_nbr, ratio_win)
 
 
 # ------------------------------------------------- PRI-staggered snapshots ----
