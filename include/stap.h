@@ -108,12 +108,27 @@ typedef enum {
 typedef enum {
   STAP_TRAIN_OWN_BLOCK = 0,      /* the B cells of block b itself, the cell under
                                     test included (the default) */
-  STAP_TRAIN_NEIGHBOURS = 1      /* not in the paper: the blocks b-1 and b+1 (the
+  STAP_TRAIN_NEIGHBOURS = 1,     /* not in the paper: the blocks b-1 and b+1 (the
                                     one that exists at either end of the range),
                                     i.e. the cell under test and the other cells
                                     of its block are guard cells; needs NB >= 2.
                                     One-CPI runs are then not cut into range
                                     slabs (block b needs its neighbours' data) */
+  STAP_TRAIN_WINDOW = 2          /* not in the paper: a sliding window with a
+                                    guard band.  The range axis is cut into groups
+                                    of B = training_block cells (B = 1: a window
+                                    per cell); group j's weights come from the
+                                    covariances of the groups
+                                      j-g-h .. j-g-1  and  j+g+1 .. j+g+h
+                                    that exist (g = train_guard guard groups on
+                                    each side, h = train_half training groups
+                                    beyond them), averaged, i.e. the sample
+                                    covariance of those h B .. 2 h B cells.  The
+                                    cell under test, its group and g groups on
+                                    each side are left out of its training.
+                                    g = 0, h = 1 is STAP_TRAIN_NEIGHBOURS.  Needs
+                                    NB >= 2 g + 2.  One-CPI runs are not cut into
+                                    range slabs */
 } stap_training;
 
 /* Where a snapshot's T temporal degrees of freedom come from. */
@@ -148,12 +163,15 @@ typedef struct {
   int32_t solver;       /* a stap_solver value (default STAP_SOLVE_FP64) */
   int32_t training;     /* a stap_training value (default STAP_TRAIN_OWN_BLOCK) */
   int32_t snapshots;    /* a stap_snapshots value (default STAP_SNAP_ADJACENT_BINS) */
+  int32_t train_guard;  /* STAP_TRAIN_WINDOW: guard groups on each side, >= 0 (default 0) */
+  int32_t train_half;   /* STAP_TRAIN_WINDOW: training groups on each side, >= 1 (default 1) */
 } stap_options;
 
 typedef struct stap_plan_s* stap_plan;
 
 /* Fill *opt with the defaults (load_factor 1e-3, refine_steps 1, FP32, FP64
- * solve, own-block training, adjacent-bin snapshots). */
+ * solve, own-block training, adjacent-bin snapshots, train_guard 0,
+ * train_half 1). */
 void stap_options_default(stap_options* opt);
 
 /* Create a plan for n_cpi CPIs whose shapes are dims[0 .. n_cpi-1].
@@ -226,6 +244,17 @@ stap_status stap_covariance(stap_plan plan, const void* dop_c64, void* cov_c128)
  * STAP_TRAIN_NEIGHBOURS; step-by-step callers pass cov_train to
  * stap_solve_weights themselves.  STAP_ERR_SHAPE if NB < 2. */
 stap_status stap_train_neighbours(stap_plan plan, const void* cov_c128, void* cov_train_c128);
+
+/* Training matrices of the sliding window (STAP_TRAIN_WINDOW, with the
+ * plan's train_guard g and train_half h; other plans use g = 0, h = 1, the
+ * neighbour-block form), from the per-group covariances of stap_covariance:
+ *   cov_train[k][j] = mean of cov[k][i] over the groups i in
+ *                     j-g-h .. j-g-1 and j+g+1 .. j+g+h with 0 <= i < NB,
+ * summed left side first in increasing i, each component then divided by
+ * the count.  cov, cov_train: c128 [K][NB][D][D], distinct buffers.
+ * stap_run_cpi applies it between the covariance and the solve when the
+ * plan's training is STAP_TRAIN_WINDOW.  STAP_ERR_SHAPE if NB < 2 g + 2. */
+stap_status stap_train_window(stap_plan plan, const void* cov_c128, void* cov_train_c128);
 
 /* Adaptive weights per (k, b) and steering vector v_s (Sec. 4.2's STAP
  * kernel, loaded sample-matrix reading), in FP64 with the default solver:

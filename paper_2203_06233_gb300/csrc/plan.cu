@@ -169,7 +169,7 @@ struct stap_plan_s {
   size_t fe_w_off = 0;
   std::vector<float> fe_w;
   size_t dop_off = 0, cov_off = 0, wts_off = 0;   // run intermediates (sized for the largest CPI)
-  size_t ctr_off = 0;                             // neighbour-training matrices (STAP_TRAIN_NEIGHBOURS)
+  size_t ctr_off = 0;                             // training matrices (neighbour blocks or window)
   bool tables_ready = false;
   // polls before a pipeline wait of the tensor-core kernels gives up
   // (stap_plan_set_wait_limit)
@@ -307,7 +307,13 @@ stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts
                                          c.tune));
 }
 
-stap_status do_train(const Cpi& c, const void* cov, void* ctr, cudaStream_t st) {
+stap_status do_train(stap_plan p, const Cpi& c, const void* cov, void* ctr, cudaStream_t st) {
+  if (p->opt.training == STAP_TRAIN_WINDOW) {
+    NvtxRange range("stap_train_window");
+    return check_launch(stap::launch_train_window(static_cast<const double2*>(cov),
+                                                  static_cast<double2*>(ctr), c.d.n_dop, c.NB, c.D,
+                                                  p->opt.train_guard, p->opt.train_half, st));
+  }
   NvtxRange range("stap_train_neighbours");
   return check_launch(stap::launch_train_neighbours(static_cast<const double2*>(cov),
                                                     static_cast<double2*>(ctr), c.d.n_dop, c.NB,
@@ -322,8 +328,8 @@ stap_status do_chain(stap_plan p, const Cpi& c, const void* cube, float* out, ch
   if ((r = do_doppler(p, c, cube, dop, st, nr)) != STAP_OK) return r;
   if ((r = do_covariance(p, c, dop, cov, st, nr, true)) != STAP_OK) return r;
   const char* trained = cov;
-  if (p->opt.training == STAP_TRAIN_NEIGHBOURS) {
-    if ((r = do_train(c, cov, ctr, st)) != STAP_OK) return r;
+  if (p->opt.training != STAP_TRAIN_OWN_BLOCK) {
+    if ((r = do_train(p, c, cov, ctr, st)) != STAP_OK) return r;
     trained = ctr;
   }
   if ((r = do_solve(p, c, trained, wts, st, nr)) != STAP_OK) return r;
@@ -331,7 +337,7 @@ stap_status do_chain(stap_plan p, const Cpi& c, const void* cube, float* out, ch
 }
 
 int slab_count(stap_plan p, const Cpi& c) {
-  if (p->opt.training == STAP_TRAIN_NEIGHBOURS) return 1;   // blocks need their neighbours
+  if (p->opt.training != STAP_TRAIN_OWN_BLOCK) return 1;   // blocks need their neighbours
   int ns = c.tune.slabs < 1 ? 1 : c.tune.slabs;
   if (ns > kMaxSlabs) ns = kMaxSlabs;
   if (ns > c.NB) ns = c.NB;
@@ -395,7 +401,7 @@ stap_status run_single(stap_plan p, const void* cube, float* out) {
 
 size_t inter_bytes(const stap_options& o, const Cpi& c) {
   return align_up(c.dop_elems() * 8) + align_up(c.cov_elems() * 16) + align_up(c.wts_elems() * 8) +
-         (o.training == STAP_TRAIN_NEIGHBOURS ? align_up(c.cov_elems() * 16) : 0);
+         (o.training != STAP_TRAIN_OWN_BLOCK ? align_up(c.cov_elems() * 16) : 0);
 }
 
 void drop_graph(stap_plan p) {
@@ -582,6 +588,8 @@ void stap_options_default(stap_options* opt) {
   opt->precision = STAP_PREC_FP32;
   opt->solver = STAP_SOLVE_FP64;
   opt->training = STAP_TRAIN_OWN_BLOCK;
+  opt->train_guard = 0;
+  opt->train_half = 1;
   opt->snapshots = STAP_SNAP_ADJACENT_BINS;
 }
 
@@ -614,7 +622,11 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
     return STAP_ERR_INVALID_ARG;
   if (o.precision != STAP_PREC_FP32 && !stap::tc_precision(o.precision)) return STAP_ERR_UNSUPPORTED;
   if (o.solver != STAP_SOLVE_FP64 && o.solver != STAP_SOLVE_MIXED_IR) return STAP_ERR_UNSUPPORTED;
-  if (o.training != STAP_TRAIN_OWN_BLOCK && o.training != STAP_TRAIN_NEIGHBOURS)
+  if (o.training != STAP_TRAIN_OWN_BLOCK && o.training != STAP_TRAIN_NEIGHBOURS &&
+      o.training != STAP_TRAIN_WINDOW)
+    return STAP_ERR_INVALID_ARG;
+  if (o.training == STAP_TRAIN_WINDOW && (o.train_guard < 0 || o.train_half < 1 ||
+                                          o.train_guard > (1 << 20) || o.train_half > (1 << 20)))
     return STAP_ERR_INVALID_ARG;
   if (o.snapshots != STAP_SNAP_ADJACENT_BINS && o.snapshots != STAP_SNAP_PRI_STAGGERED)
     return STAP_ERR_INVALID_ARG;
@@ -625,6 +637,9 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
     if (o.solver == STAP_SOLVE_MIXED_IR && !stap::mir_supported(dims[i].n_chan * dims[i].tdof))
       return STAP_ERR_UNSUPPORTED;
     if (o.training == STAP_TRAIN_NEIGHBOURS && dims[i].n_range / dims[i].training_block < 2)
+      return STAP_ERR_SHAPE;
+    if (o.training == STAP_TRAIN_WINDOW &&
+        (long long)dims[i].n_range / dims[i].training_block < 2LL * o.train_guard + 2)
       return STAP_ERR_SHAPE;
     if (stag && dims[i].tdof > dims[i].n_pulses) return STAP_ERR_SHAPE;   // sub-windows of >= 1 pulse
   }
@@ -673,7 +688,7 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
   off = align_up(off + max_wts * 8);
   if (n_cpi == 1) off += 2 * kMaxSlabs * kAlign;   // per-slab alignment of cov and wts
   p->ctr_off = off;
-  if (o.training == STAP_TRAIN_NEIGHBOURS) off = align_up(off + max_cov * 16);
+  if (o.training != STAP_TRAIN_OWN_BLOCK) off = align_up(off + max_cov * 16);
   p->run_bytes = off;
   size_t all = p->step_bytes;
   for (const Cpi& c : p->cpis) all += inter_bytes(o, c);
@@ -803,7 +818,27 @@ stap_status stap_train_neighbours(stap_plan p, const void* cov, void* ctr) {
   if (!aligned16(cov) || !aligned16(ctr)) return STAP_ERR_MISALIGNED;
   if (p->cpis[0].NB < 2) return STAP_ERR_SHAPE;
   if ((st = ready(p, p->step_bytes)) != STAP_OK) return st;
-  return do_train(p->cpis[0], cov, ctr, p->stream);
+  NvtxRange range("stap_train_neighbours");
+  const Cpi& c = p->cpis[0];
+  return check_launch(stap::launch_train_neighbours(static_cast<const double2*>(cov),
+                                                    static_cast<double2*>(ctr), c.d.n_dop, c.NB,
+                                                    c.D, p->stream));
+}
+
+stap_status stap_train_window(stap_plan p, const void* cov, void* ctr) {
+  stap_status st = single_cpi(p);
+  if (st != STAP_OK) return st;
+  if (!cov || !ctr || cov == ctr) return STAP_ERR_INVALID_ARG;
+  if (!aligned16(cov) || !aligned16(ctr)) return STAP_ERR_MISALIGNED;
+  const int guard = p->opt.training == STAP_TRAIN_WINDOW ? p->opt.train_guard : 0;
+  const int half = p->opt.training == STAP_TRAIN_WINDOW ? p->opt.train_half : 1;
+  if ((long long)p->cpis[0].NB < 2LL * guard + 2) return STAP_ERR_SHAPE;
+  if ((st = ready(p, p->step_bytes)) != STAP_OK) return st;
+  NvtxRange range("stap_train_window");
+  const Cpi& c = p->cpis[0];
+  return check_launch(stap::launch_train_window(static_cast<const double2*>(cov),
+                                                static_cast<double2*>(ctr), c.d.n_dop, c.NB, c.D,
+                                                guard, half, p->stream));
 }
 
 stap_status stap_solve_weights(stap_plan p, const void* cov, void* wts) {

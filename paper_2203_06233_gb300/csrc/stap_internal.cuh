@@ -44,6 +44,12 @@ struct Tune {
 cudaError_t launch_train_neighbours(const double2* in, double2* out, int K, int NB, int D,
                                     cudaStream_t s);
 
+// Sliding training window: out[k][j] = mean of in[k][i] over the groups
+// i = j-guard-half .. j-guard-1 and j+guard+1 .. j+guard+half in 0 .. NB-1;
+// needs guard >= 0, half >= 1, NB >= 2 guard + 2.
+cudaError_t launch_train_window(const double2* in, double2* out, int K, int NB, int D, int guard,
+                                int half, cudaStream_t s);
+
 // Snapshot lengths with a mixed-precision iterative-refinement solve.
 bool mir_supported(int D);
 

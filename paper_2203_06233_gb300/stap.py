@@ -36,6 +36,7 @@ STAP_SOLVE_FP64 = 0
 STAP_SOLVE_MIXED_IR = 1
 STAP_TRAIN_OWN_BLOCK = 0
 STAP_TRAIN_NEIGHBOURS = 1
+STAP_TRAIN_WINDOW = 2
 STAP_SNAP_ADJACENT_BINS = 0
 STAP_SNAP_PRI_STAGGERED = 1
 
@@ -48,6 +49,7 @@ EXPORTED = (
     "stap_run_cpi_noalloc", "stap_plan_batch_bytes", "stap_plan_autotune", "stap_plan_get_tuning",
     "stap_plan_set_tuning", "stap_train_neighbours", "stap_plan_stream_bytes", "stap_run_stream",
     "stap_plan_set_front_end", "stap_reduce_channels", "stap_plan_set_wait_limit",
+    "stap_train_window",
 )
 
 STAP_TUNING_LEN = 9
@@ -73,7 +75,8 @@ class stap_dims(ctypes.Structure):
 class stap_options(ctypes.Structure):
     _fields_ = [("load_factor", ctypes.c_double), ("refine_steps", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
-                ("training", ctypes.c_int32), ("snapshots", ctypes.c_int32)]
+                ("training", ctypes.c_int32), ("snapshots", ctypes.c_int32),
+                ("train_guard", ctypes.c_int32), ("train_half", ctypes.c_int32)]
 
 
 _lib = None
@@ -106,6 +109,7 @@ def lib():
             L.stap_covariance.argtypes = [vp, vp, vp]
             L.stap_solve_weights.argtypes = [vp, vp, vp]
             L.stap_train_neighbours.argtypes = [vp, vp, vp]
+            L.stap_train_window.argtypes = [vp, vp, vp]
             L.stap_apply.argtypes = [vp, vp, vp, vp]
             L.stap_run_cpi.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
             L.stap_get_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
@@ -271,6 +275,11 @@ def stap_train_neighbours(plan, cov: torch.Tensor, cov_train: torch.Tensor):
                                        ctypes.c_void_p(cov_train.data_ptr())), "stap_train_neighbours")
 
 
+def stap_train_window(plan, cov: torch.Tensor, cov_train: torch.Tensor):
+    _check(lib().stap_train_window(plan, ctypes.c_void_p(cov.data_ptr()),
+                                   ctypes.c_void_p(cov_train.data_ptr())), "stap_train_window")
+
+
 def stap_solve_weights(plan, cov: torch.Tensor, wts: torch.Tensor):
     _check(lib().stap_solve_weights(plan, ctypes.c_void_p(cov.data_ptr()),
                                     ctypes.c_void_p(wts.data_ptr())), "stap_solve_weights")
@@ -363,15 +372,16 @@ class Plan:
                  precision: int = STAP_PREC_FP32, device=None, steps_only: bool = False,
                  max_workspace_bytes: Optional[int] = None, solver: int = STAP_SOLVE_FP64,
                  training: int = STAP_TRAIN_OWN_BLOCK, snapshots: int = STAP_SNAP_ADJACENT_BINS,
-                 front_end=None, front_end_chunk: int = 0):
+                 front_end=None, front_end_chunk: int = 0, train_guard: int = 0, train_half: int = 1):
         dl = list(dims) if isinstance(dims, (list, tuple)) and dims and not isinstance(dims[0], int) \
             else [dims]
         self.dims = [_dims(d) for d in dl]
         self.device = torch.device(device) if device is not None else torch.device("cuda")
         opts = stap_options(float(load_factor), int(refine_steps), int(precision), int(solver),
-                            int(training), int(snapshots))
+                            int(training), int(snapshots), int(train_guard), int(train_half))
         self.precision, self.refine_steps, self.solver = int(precision), int(refine_steps), int(solver)
         self.training, self.snapshots = int(training), int(snapshots)
+        self.train_guard, self.train_half = int(train_guard), int(train_half)
         self.n_elem = 0
         with torch.cuda.device(self.device):
             self.handle, _ = stap_plan_create(self.dims, opts)
@@ -456,6 +466,16 @@ class Plan:
         stap_train_neighbours(self.handle, cov, cov_train)
         return cov_train
 
+    def train_window(self, cov, cov_train=None):
+        """Training matrices of the sliding window (the plan's guard and half)."""
+        sh = self.shapes()
+        cov_train = torch.empty_like(cov) if cov_train is None else cov_train
+        _dev(cov, torch.complex128, sh["cov"], "cov")
+        _dev(cov_train, torch.complex128, sh["cov"], "cov_train")
+        self._sync_stream()
+        stap_train_window(self.handle, cov, cov_train)
+        return cov_train
+
     def solve_weights(self, cov, wts=None):
         sh = self.shapes()
         wts = torch.empty(sh["wts"], dtype=torch.complex64, device=self.device) if wts is None else wts
@@ -531,6 +551,8 @@ class Plan:
             self.refine_steps, self.solver, self.training)
         if self.snapshots:
             key += " snap%d" % self.snapshots
+        if self.training == STAP_TRAIN_WINDOW:
+            key += " guard%d half%d" % (self.train_guard, self.train_half)
         # a one-CPI plan also tunes its range slabs, which depend on R
         return key + (" R%d" % d.n_range if len(self.dims) == 1 else " batch")
 

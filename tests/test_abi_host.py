@@ -96,13 +96,21 @@ def test_plan_create_checks_options(lf, refine, prec, solver, code):
 def test_training_option_values_and_block_count():
     o = stap.stap_options_default()
     assert o.training == stap.STAP_TRAIN_OWN_BLOCK
-    for training, dims, code in [(1, GOOD, stap.STAP_OK),
-                                 (2, GOOD, stap.STAP_ERR_INVALID_ARG),
-                                 (-1, GOOD, stap.STAP_ERR_INVALID_ARG),
-                                 (1, (4, 16, 32, 64, 2, 64, 4), stap.STAP_ERR_SHAPE),   # NB = 1
-                                 (1, (4, 16, 32, 128, 2, 64, 4), stap.STAP_OK)]:         # NB = 2
-        got, h, _ = _create(dims, stap.stap_options(1e-3, 1, 0, 0, training))
-        assert got == code, (training, dims)
+    assert o.train_guard == 0 and o.train_half == 1
+    W = stap.STAP_TRAIN_WINDOW
+    for training, dims, guard, half, code in [
+            (1, GOOD, 0, 0, stap.STAP_OK),
+            (3, GOOD, 0, 1, stap.STAP_ERR_INVALID_ARG),
+            (-1, GOOD, 0, 1, stap.STAP_ERR_INVALID_ARG),
+            (1, (4, 16, 32, 64, 2, 64, 4), 0, 1, stap.STAP_ERR_SHAPE),           # NB = 1
+            (1, (4, 16, 32, 128, 2, 64, 4), 0, 1, stap.STAP_OK),                 # NB = 2
+            (W, GOOD, 2, 16, stap.STAP_OK),
+            (W, GOOD, 0, 0, stap.STAP_ERR_INVALID_ARG),                          # half < 1
+            (W, GOOD, -1, 1, stap.STAP_ERR_INVALID_ARG),
+            (W, (4, 16, 32, 128, 2, 1, 4), 63, 4, stap.STAP_OK),                 # NB = 128 = 2 g + 2
+            (W, (4, 16, 32, 128, 2, 1, 4), 64, 4, stap.STAP_ERR_SHAPE)]:         # NB < 2 g + 2
+        got, h, _ = _create(dims, stap.stap_options(1e-3, 1, 0, 0, training, 0, guard, half))
+        assert got == code, (training, dims, guard, half)
         if h.value:
             stap.stap_plan_destroy(h)
 
@@ -112,9 +120,11 @@ def test_training_workspace_holds_the_training_matrices():
     D, NB = C * T, R // B
     _, h0, ws0 = _create(GOOD)
     _, h1, ws1 = _create(GOOD, stap.stap_options(1e-3, 1, 0, 0, 1))
+    _, h2, ws2 = _create(GOOD, stap.stap_options(1e-3, 1, 0, 0, stap.STAP_TRAIN_WINDOW, 0, 1, 4))
     assert ws1 - ws0 >= K * NB * D * D * 16 and ws1 - ws0 < K * NB * D * D * 16 + 512
-    stap.stap_plan_destroy(h0)
-    stap.stap_plan_destroy(h1)
+    assert ws2 == ws1
+    for h in (h0, h1, h2):
+        stap.stap_plan_destroy(h)
 
 
 def test_snapshot_option_values_and_pulse_limit():
