@@ -220,6 +220,11 @@ PREC_TEXT = {
 SOLVE_TEXT = "FP64 diagonal load, LDL^H factorisation and substitutions, 1 refinement step"
 
 
+def log(msg):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def sample_blocks(spec, n):
     """n seeded range blocks of the CPI (all of them if it has fewer)."""
     rng = np.random.default_rng(1234 + spec.seed)
@@ -361,6 +366,8 @@ def run_leg(spec, cube, dev, prec, args, flush, stream, kernel_reps, timed=None,
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     (choices,) = tuning.values()
+    log(f"{spec.dims()} {PREC_NAMES[prec]}: {sum(times) / args.steps:.3f} ms/step, autotune {tune_s:.1f} s, "
+        f"kernels {kt}")
     leg = {"precision": PREC_NAMES[prec], "arithmetic": PREC_TEXT[prec] + "; " + SOLVE_TEXT,
            "ms_per_step": sum(times) / args.steps, "step_ms": times, "tuning": tuning,
            "autotune_s": tune_s, "kernels_ms": kt,
@@ -396,6 +403,14 @@ def run_gpu(args):
                       if world == 1 and not args.only_headline else [])
     for wi, name in enumerate(names):
         head = wi == 0
+        if not head:
+            try:
+                extra[name] = workload_keys(args, name, rank, dev, stream, flush, pk)
+            except Exception as exc:   # an extra key must not lose the headline line
+                log(f"{name}: {type(exc).__name__}: {exc}")
+                extra[name] = {"error": f"{type(exc).__name__}: {exc}"[:400]}
+            torch.cuda.empty_cache()
+            continue
         spec = workload_spec(rank, name)
         NAME_OF[spec.dims()] = name
         C, P, K, R, T, B, S = spec.dims()
@@ -436,16 +451,6 @@ def run_gpu(args):
             errors = {PREC_NAMES[p]: block_errors(outs_blocks[p], refs) for p in outs_blocks}
         mvalue = world * cells / (mleg["ms_per_step"] * 1e-3)
         fvalue = world * cells / (fleg["ms_per_step"] * 1e-3)
-        if not head:
-            extra[name] = {
-                "config": workload_config(spec, name),
-                "mixed": dict(mleg, value=mvalue, kernels=kernel_figures(spec, mprec, mleg["kernels_ms"], pk)),
-                "fp32": dict(fleg, value=fvalue, kernels=kernel_figures(spec, 0, fleg["kernels_ms"], pk)),
-                "mixed_vs_fp32": mvalue / fvalue, "errors_vs_oracle": errors,
-                "cpu_baseline": cpu}
-            del cube
-            torch.cuda.empty_cache()
-            continue
         # ---- headline: the mixed leg's timed region ----
         total_ms, value = aggregate(mleg["ms_per_step"] * sub.steps, cells * sub.steps, world, dev)
         ms_per_step = total_ms / sub.steps
@@ -517,11 +522,51 @@ def run_gpu(args):
     if extra:
         line["workloads"] = extra
     if world == 1 and not args.only_headline and NAME == "large":
-        line["workloads"]["batch"] = batch_legs(args, dev, stream, flush)
+        try:
+            line["workloads"]["batch"] = batch_legs(args, dev, stream, flush)
+        except Exception as exc:   # an extra key must not lose the headline line
+            log(f"batch: {type(exc).__name__}: {exc}")
+            line["workloads"]["batch"] = {"error": f"{type(exc).__name__}: {exc}"[:400]}
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def workload_keys(args, name, rank, dev, stream, flush, pk):
+    """Another single-CPI workload as a key of the line: its mixed and FP32
+    legs (a few timed steps each) and their errors on sampled blocks."""
+    import torch
+    from paper_2203_06233_gb300 import synth
+    spec = workload_spec(rank, name)
+    NAME_OF[spec.dims()] = name
+    C, P, K, R, T, B, S = spec.dims()
+    cells = K * R
+    mprec = MIXED_PREC[name][1]
+    cube = synth.make_cube_torch(spec, dev)
+    cube_h = cube.cpu().numpy()
+    kernel_reps = 3 if cube_h.nbytes > (1 << 30) else max(20, min(200, args.steps))
+    blocks = sample_blocks(spec, 4)
+    sub = argparse.Namespace(steps=max(3, min(args.steps, 10)), warmup=args.warmup)
+    legs, outs_blocks = {}, {}
+    for prec in (mprec, 0):
+        plan, out, leg = run_leg(spec, cube, dev, prec, sub, flush, stream, kernel_reps)
+        outs_blocks[prec] = {b: out[:, :, b * B:(b + 1) * B].cpu().numpy() for b in blocks}
+        legs[prec] = leg
+        plan.close()
+        del plan, out
+        torch.cuda.empty_cache()
+    errors, cpu = {}, None
+    if not args.no_cpu_baseline:
+        refs, cpu = oracle_on_blocks(spec, cube_h, blocks)
+        errors = {PREC_NAMES[p]: block_errors(outs_blocks[p], refs) for p in outs_blocks}
+    mvalue = cells / (legs[mprec]["ms_per_step"] * 1e-3)
+    fvalue = cells / (legs[0]["ms_per_step"] * 1e-3)
+    return {"config": workload_config(spec, name),
+            "mixed": dict(legs[mprec], value=mvalue,
+                          kernels=kernel_figures(spec, mprec, legs[mprec]["kernels_ms"], pk)),
+            "fp32": dict(legs[0], value=fvalue, kernels=kernel_figures(spec, 0, legs[0]["kernels_ms"], pk)),
+            "mixed_vs_fp32": mvalue / fvalue, "errors_vs_oracle": errors, "cpu_baseline": cpu}
 
 
 DTYPE = {0: "f32+f64", 1: "bf16x3+f32+f64", 2: "tf32x3+f32+f64", 3: "f16x2+f32+f64"}
@@ -545,11 +590,14 @@ def batch_legs(args, dev, stream, flush):
     outs_pick = {}
     steps = max(2, min(args.steps, 3))
     for prec in (MIXED_PREC["batch"][1], 0):
+        outs = [torch.empty((s.n_steering, s.n_dop, s.n_range), dtype=torch.float32, device=dev)
+                for s in specs]
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        # workspace: as much of the all-concurrent size as free HBM allows (8 GiB spare)
         free = torch.cuda.mem_get_info(dev)[0]
         plan = stap.Plan([s.dims() for s in specs], device=dev, precision=prec,
                          max_workspace_bytes=max(0, free - (8 << 30)))
-        outs = [torch.empty((s.n_steering, s.n_dop, s.n_range), dtype=torch.float32, device=dev)
-                for s in specs]
         t0 = time.perf_counter()
         plan.autotune(cubes, outs, reps=1)
         tune_s = time.perf_counter() - t0
@@ -569,7 +617,7 @@ def batch_legs(args, dev, stream, flush):
             "fp64_solve_frac_of_step": sum(solve_flops(s) for s in specs) / (ms * 1e-3) / 1e12 /
             peaks()["fp64_tflops"]}
         plan.close()
-        del outs
+        del plan, outs
         torch.cuda.empty_cache()
     res["mixed_vs_fp32"] = res["mixed"]["value"] / res["fp32"]["value"]
     if not args.no_cpu_baseline:
