@@ -81,7 +81,6 @@ __device__ __forceinline__ int prod_a(int i) { return i < 3 ? (i == 2 ? 1 : 0) :
 __device__ __forceinline__ int prod_b(int i) { return i < 3 ? (i == 1 ? 1 : 0) : (i == 3 ? 2 : (i == 4 ? 1 : 0)); }
 
 constexpr int kThreads = 256;                 // 8 warps stage; warp w reads TMEM lanes 32 (w % 4) ..
-constexpr int kUnroll = 4;                    // staging units in flight per lane
 constexpr int kWaitIter = kDefaultWaitPolls;  // drain waits before TMEM is freed
 
 // ---- splitting ---------------------------------------------------------------
@@ -149,6 +148,7 @@ __host__ __device__ constexpr uint32_t idesc_for(int N) {
 // ---- covariance -----------------------------------------------------------------
 
 constexpr int kCovRB = 128;                   // bytes of one operand row per chunk (8 core matrices)
+constexpr int kCovU = 16;                     // staging units per warp and chunk (G D8 / 8 <= 16)
 constexpr int kCovPiece = 256 * kCovRB;       // 256 rows of one piece (32 KB)
 
 template <int PREC>
@@ -213,11 +213,13 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
       for (int p = warp; p < GD; p += kThreads / 32) {
         const long long base = rowbase[p];
         float m = 0.f;
-        if (base >= 0)
+        if (base >= 0) {
+#pragma unroll 8
           for (int j = lane; j < B; j += 32) {
-            const float2 v = __ldg(dop + base + j);
-            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+            const float2 x = __ldg(dop + base + j);
+            m = fmaxf(m, fmaxf(fabsf(x.x), fabsf(x.y)));
           }
+        }
         m = warp_max(m);
         if (lane == 0) atomicMax(&smax[p / D8], __float_as_int(m));   // m >= 0: int order
       }
@@ -225,6 +227,27 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
       if (tid < G) sscale[tid] = block_scale(__int_as_float(smax[tid]));
       __syncthreads();
     }
+    // A unit is one core matrix (8 rows x 16 bytes) of the Xr rows and the
+    // matching one of the Xi rows; lane l takes row 8 rg + l/4 and CPL cells
+    // and writes one 32-bit word per piece into each.  Warp w takes units
+    // w, w + 8, ... (at most kCovU of them).  The next chunk's loads are
+    // issued before this chunk's barrier and MMAs, so their latency overlaps
+    // both.
+    float2 v[kCovU][CPL];
+    auto load_chunk = [&](int ch) {
+      const int c0 = ch * KC;
+#pragma unroll
+      for (int uu = 0; uu < kCovU; ++uu) {
+        const int unit = warp + uu * (kThreads / 32);
+        const int p = (unit >> 3) * 8 + (lane >> 2);
+        const int j = c0 + (unit & 7) * CPW + (lane & 3) * CPL;
+        const long long base = unit < units ? rowbase[p] : -1;
+#pragma unroll
+        for (int cc = 0; cc < CPL; ++cc)
+          v[uu][cc] = (base >= 0 && j + cc < B) ? __ldg(dop + base + j + cc) : make_float2(0.f, 0.f);
+      }
+    };
+    if (ok) load_chunk(0);
     for (int ch = 0; ch < nchunks && ok; ++ch, ++gch) {
       const int st = (int)(gch & 1);
       uint8_t* stage = sm + st * STAGE;
@@ -237,61 +260,44 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
       }
       ok = __syncthreads_and(ok);
       if (!ok) break;
-      // stage cells c0 .. c0 + KC - 1: a unit is one core matrix (8 rows x 16
-      // bytes) of the Xr rows and the matching one of the Xi rows; lane l
-      // takes row 8 rg + l/4 and CPL cells, and writes one 32-bit word per
-      // piece into each
-      const int c0 = ch * KC;
-      for (int u0 = warp; u0 < units; u0 += (kThreads / 32) * kUnroll) {
-        float2 v[kUnroll][CPL];
 #pragma unroll
-        for (int uu = 0; uu < kUnroll; ++uu) {
-          const int unit = u0 + uu * (kThreads / 32);
-          const int p = (unit >> 3) * 8 + (lane >> 2);
-          const int j = c0 + (unit & 7) * CPW + (lane & 3) * CPL;
-          const long long base = unit < units ? rowbase[p] : -1;
+      for (int uu = 0; uu < kCovU; ++uu) {
+        const int unit = warp + uu * (kThreads / 32);
+        if (unit >= units) continue;
+        const int rg = unit >> 3, cmk = unit & 7;
+        const int off = rg * SBO + cmk * 128 + (lane >> 2) * 16 + (lane & 3) * 4;
+        const int offi = off + (GD / 8) * SBO;
+        if constexpr (PREC == kTF32X3) {
+          uint32_t wr[2], wi[2];
+          split_tf32(v[uu][0].x, wr);
+          split_tf32(v[uu][0].y, wi);
 #pragma unroll
-          for (int cc = 0; cc < CPL; ++cc)
-            v[uu][cc] = (base >= 0 && j + cc < B) ? __ldg(dop + base + j + cc) : make_float2(0.f, 0.f);
-        }
+          for (int pc = 0; pc < 2; ++pc) {
+            *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + off) = wr[pc];
+            *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + offi) = wi[pc];
+          }
+        } else if constexpr (PREC == kBF16X3) {
+          uint32_t wr[3], wi[3];
+          split_bf16(v[uu][0].x, v[uu][1].x, wr);
+          split_bf16(v[uu][0].y, v[uu][1].y, wi);
 #pragma unroll
-        for (int uu = 0; uu < kUnroll; ++uu) {
-          const int unit = u0 + uu * (kThreads / 32);
-          if (unit >= units) continue;
-          const int rg = unit >> 3, cmk = unit & 7;
-          const int off = rg * SBO + cmk * 128 + (lane >> 2) * 16 + (lane & 3) * 4;
-          const int offi = off + (GD / 8) * SBO;
-          if constexpr (PREC == kTF32X3) {
-            uint32_t wr[2], wi[2];
-            split_tf32(v[uu][0].x, wr);
-            split_tf32(v[uu][0].y, wi);
+          for (int pc = 0; pc < 3; ++pc) {
+            *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + off) = wr[pc];
+            *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + offi) = wi[pc];
+          }
+        } else {
+          const float sc = sscale[(rg * 8 + (lane >> 2)) / D8];
+          uint32_t wr[2], wi[2];
+          split_f16(v[uu][0].x * sc, v[uu][1].x * sc, wr);
+          split_f16(v[uu][0].y * sc, v[uu][1].y * sc, wi);
 #pragma unroll
-            for (int pc = 0; pc < 2; ++pc) {
-              *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + off) = wr[pc];
-              *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + offi) = wi[pc];
-            }
-          } else if constexpr (PREC == kBF16X3) {
-            uint32_t wr[3], wi[3];
-            split_bf16(v[uu][0].x, v[uu][1].x, wr);
-            split_bf16(v[uu][0].y, v[uu][1].y, wi);
-#pragma unroll
-            for (int pc = 0; pc < 3; ++pc) {
-              *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + off) = wr[pc];
-              *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + offi) = wi[pc];
-            }
-          } else {
-            const float sc = sscale[((unit >> 3) * 8 + (lane >> 2)) / D8];
-            uint32_t wr[2], wi[2];
-            split_f16(v[uu][0].x * sc, v[uu][1].x * sc, wr);
-            split_f16(v[uu][0].y * sc, v[uu][1].y * sc, wi);
-#pragma unroll
-            for (int pc = 0; pc < 2; ++pc) {
-              *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + off) = wr[pc];
-              *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + offi) = wi[pc];
-            }
+          for (int pc = 0; pc < 2; ++pc) {
+            *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + off) = wr[pc];
+            *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + offi) = wi[pc];
           }
         }
       }
+      if (ch + 1 < nchunks) load_chunk(ch + 1);
       tc::fence_proxy_async();
       tc::fence_before_sync();
       __syncthreads();
@@ -385,6 +391,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
 constexpr int kAppRB = 64;                    // bytes of one operand row per chunk (4 core matrices)
 constexpr int kAppA = 128 * kAppRB;           // A piece: 128 cells (8 KB)
 constexpr int kAppB = 256 * kAppRB;           // B piece: up to 256 weight rows (16 KB)
+constexpr int kAppU = 24;                     // staging units per warp and chunk ((16 + 32) x 4 / 8)
 
 template <int PREC>
 constexpr size_t apply_smem() { return 2 * (size_t)Fmt<PREC>::NPC * (kAppA + kAppB); }
@@ -473,6 +480,36 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
       if (tid == 0) xsc_s = block_scale(__int_as_float(xmax));
       __syncthreads();
     }
+    // K elements kap0 .. kap0 + KC - 1 of the A rows (cells) and of the B
+    // rows (weights); a unit is one core matrix, lane l takes row 8 rg + l/4
+    // and K elements 4 cm + (l & 3) (tf32) or one re/im pair (16-bit).  Warp
+    // w takes units w, w + 8, ... (at most kAppU); the next chunk's loads are
+    // issued before this chunk's barrier and MMAs.
+    float2 v[kAppU];
+    auto load_chunk = [&](int ch) {
+      const int kap0 = ch * KC;
+#pragma unroll
+      for (int uu = 0; uu < kAppU; ++uu) {
+        const int unit = warp + uu * (kThreads / 32);
+        v[uu] = make_float2(0.f, 0.f);
+        if (unit < units) {
+          const bool isA = unit < unitsA;
+          const int ul = isA ? unit : unit - unitsA;
+          const int row = (ul / NCM) * 8 + (lane >> 2), cmk = ul % NCM;
+          const int d = PREC == kTF32X3 ? (kap0 + cmk * 4 + (lane & 3)) >> 1
+                                        : (kap0 + cmk * 8 + (lane & 3) * 2) >> 1;
+          if (d < D) {
+            if (isA) {
+              if (r0 + row < R) v[uu] = __ldg(dop + colbase[d] + r0 + row);
+            } else {
+              const long long wb = wbase[row];
+              if (wb >= 0) v[uu] = __ldg(wts + wb + d);
+            }
+          }
+        }
+      }
+    };
+    if (ok) load_chunk(0);
     for (int ch = 0; ch < nchunks && ok; ++ch, ++gch) {
       const int st = (int)(gch & 1);
       uint8_t* stage = sm + st * STAGE;
@@ -485,73 +522,40 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
       }
       ok = __syncthreads_and(ok);
       if (!ok) break;
-      // K elements kap0 .. kap0 + KC - 1 of the A rows (cells) and of the B
-      // rows (weights); a unit is one core matrix, lane l takes row 8 rg + l/4
-      // and K elements 4 cm + (l & 3) (tf32) or one re/im pair (16-bit)
       const int kap0 = ch * KC;
-      for (int u0 = warp; u0 < units; u0 += (kThreads / 32) * kUnroll) {
-        float2 v[kUnroll];
 #pragma unroll
-        for (int uu = 0; uu < kUnroll; ++uu) {
-          const int unit = u0 + uu * (kThreads / 32);
-          v[uu] = make_float2(0.f, 0.f);
-          if (unit < units) {
-            const bool isA = unit < unitsA;
-            const int ul = isA ? unit : unit - unitsA;
-            const int row = (ul / NCM) * 8 + (lane >> 2), cmk = ul % NCM;
-            int d, comp;
-            if constexpr (PREC == kTF32X3) {
-              const int kap = kap0 + cmk * 4 + (lane & 3);
-              d = kap >> 1;
-              comp = kap & 1;
-            } else {
-              d = (kap0 + cmk * 8 + (lane & 3) * 2) >> 1;
-              comp = 0;
-            }
-            (void)comp;
-            if (d < D) {
-              if (isA) {
-                if (r0 + row < R) v[uu] = __ldg(dop + colbase[d] + r0 + row);
-              } else {
-                const long long wb = wbase[row];
-                if (wb >= 0) v[uu] = __ldg(wts + wb + d);
-              }
-            }
-          }
-        }
+      for (int uu = 0; uu < kAppU; ++uu) {
+        const int unit = warp + uu * (kThreads / 32);
+        if (unit >= units) continue;
+        const bool isA = unit < unitsA;
+        const int ul = isA ? unit : unit - unitsA;
+        const int row = (ul / NCM) * 8 + (lane >> 2), cmk = ul % NCM;
+        const int off = (isA ? 0 : kAppA) + (ul / NCM) * SBO + cmk * 128 + (lane >> 2) * 16 +
+                        (lane & 3) * 4;
+        // the pair this row holds at (re, im) positions: x, or the weight
+        // rows (wr, wi) and (-wi, wr)
+        float2 e = v[uu];
+        if (!isA && (row & 1)) e = make_float2(-e.y, e.x);
+        if constexpr (PREC == kTF32X3) {
+          const int kap = kap0 + cmk * 4 + (lane & 3);
+          uint32_t w[2];
+          split_tf32((kap & 1) ? e.y : e.x, w);
+          *reinterpret_cast<uint32_t*>(stage + off) = w[0];
+          *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
+        } else if constexpr (PREC == kBF16X3) {
+          uint32_t w[3];
+          split_bf16(e.x, e.y, w);
 #pragma unroll
-        for (int uu = 0; uu < kUnroll; ++uu) {
-          const int unit = u0 + uu * (kThreads / 32);
-          if (unit >= units) continue;
-          const bool isA = unit < unitsA;
-          const int ul = isA ? unit : unit - unitsA;
-          const int row = (ul / NCM) * 8 + (lane >> 2), cmk = ul % NCM;
-          const int off = (isA ? 0 : kAppA) + (ul / NCM) * SBO + cmk * 128 + (lane >> 2) * 16 +
-                          (lane & 3) * 4;
-          // the pair this row holds at (re, im) positions: x, or the weight
-          // rows (wr, wi) and (-wi, wr)
-          float2 e = v[uu];
-          if (!isA && (row & 1)) e = make_float2(-e.y, e.x);
-          if constexpr (PREC == kTF32X3) {
-            const int kap = kap0 + cmk * 4 + (lane & 3);
-            uint32_t w[2];
-            split_tf32((kap & 1) ? e.y : e.x, w);
-            *reinterpret_cast<uint32_t*>(stage + off) = w[0];
-            *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
-          } else if constexpr (PREC == kBF16X3) {
-            uint32_t w[3];
-            split_bf16(e.x, e.y, w);
-#pragma unroll
-            for (int pc = 0; pc < 3; ++pc) *reinterpret_cast<uint32_t*>(stage + pc * PIECE + off) = w[pc];
-          } else {
-            const float sc = isA ? xsc_s : ((row >> 1) < Nq ? wsc[row >> 1] : 1.f);
-            uint32_t w[2];
-            split_f16(e.x * sc, e.y * sc, w);
-            *reinterpret_cast<uint32_t*>(stage + off) = w[0];
-            *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
-          }
+          for (int pc = 0; pc < 3; ++pc) *reinterpret_cast<uint32_t*>(stage + pc * PIECE + off) = w[pc];
+        } else {
+          const float sc = isA ? xsc_s : ((row >> 1) < Nq ? wsc[row >> 1] : 1.f);
+          uint32_t w[2];
+          split_f16(e.x * sc, e.y * sc, w);
+          *reinterpret_cast<uint32_t*>(stage + off) = w[0];
+          *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
         }
       }
+      if (ch + 1 < nchunks) load_chunk(ch + 1);
       tc::fence_proxy_async();
       tc::fence_before_sync();
       __syncthreads();
@@ -666,7 +670,13 @@ cudaError_t launch_app(const float2* dop, const float2* wts, float* out, int C, 
   static int set_bytes[64] = {0};
   cudaError_t e = ensure_smem(apply_tcx_kernel<PREC>, smem, set_bytes);
   if (e != cudaSuccess) return e;
-  const int per_sm = (cols == 256 && 2 * smem <= 220 * 1024) ? 2 : 1;
+  // resident CTAs per SM: registers and shared memory (occupancy query),
+  // and at most two when each holds 256 TMEM columns (one with 512)
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_tcx_kernel<PREC>, kThreads, smem) !=
+          cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  per_sm = per_sm > (cols == 256 ? 2 : 1) ? (cols == 256 ? 2 : 1) : per_sm;
   const long long cap = 152LL * per_sm;
   const long long blocks = ntiles < cap ? ntiles : cap;
   apply_tcx_kernel<PREC><<<(unsigned)blocks, kThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S,

@@ -931,8 +931,10 @@ __device__ __forceinline__ void big_solve_f32(float2 (&x)[RPL], const float2* __
 // matrix of solve_big_mir_kernel does not fit in shared memory): the factor
 // and the substitutions in FP32, the solution in FP64, each refinement step's
 // residual in FP64 from the input as below, its FP32 correction added in FP64.
+// 256-thread CTAs hold a D > 64 system's factor (one CTA per SM), so they may
+// use the whole register file; 128-thread CTAs run three per SM.
 template <bool SEP, int LR, int NT, int RPL, bool F32F = false>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, NT >= 256 ? 1 : 3)
 solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
                  const double2* __restrict__ steer, const double2* __restrict__ sep_g,
                  const float4* __restrict__ steer_ff, const float4* __restrict__ sep_a_ff,
@@ -946,13 +948,11 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
   const int Dp = D * (D + 1) / 2;
   // Lu [Dp] (column-major packed) and the pivot column before division [D];
   // from the next 16-byte boundary the SEP basis solutions [C][D]
-  // (double-float), the broadcast vectors [NG][D], the pivot reciprocals [D]
-  // and the pivot flag
+  // (double-float), the pivot reciprocals [D] and the pivot flag
   LT* Lc = reinterpret_cast<LT*>(sm);
   LT* colb = Lc + Dp;
   float4* Ubf = reinterpret_cast<float4*>(sm) + ((size_t)(Dp + D) * sizeof(LT) + 15) / 16;
-  double2* uv = reinterpret_cast<double2*>(Ubf + (SEP ? (size_t)C * D : 0));
-  RT* rd = reinterpret_cast<RT*>(uv + (size_t)NG * D);
+  RT* rd = reinterpret_cast<RT*>(Ubf + (SEP ? (size_t)C * D : 0));
   int* okf = reinterpret_cast<int*>(rd + D);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int li = lane % LR, grp = lane / LR;         // lane in group, group in warp
@@ -1097,14 +1097,19 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
         // r = b - R u - delta u  (R Hermitian: A[i][l] for i >= l, conj(A[l][i])
         // above, real diagonal; the load is applied after the sweep)
 #pragma unroll
-        for (int q = 0; q < RPL; ++q)
-          if (li + LR * q < D) uv[g * D + li + LR * q] = u[q];
-        __syncwarp();
-#pragma unroll
         for (int q = 0; q < RPL; ++q) r[q] = b[q];
+        // u_l lives in register ql = l / LR of the group's lane l % LR: a
+        // shuffle broadcasts it (the loops' bounds are warp-uniform)
+#pragma unroll
+        for (int ql = 0; ql < RPL; ++ql) {
+          if (LR * ql >= D) break;
 #pragma unroll 4
-        for (int l = 0; l < D; ++l) {
-          const double2 ul = uv[g * D + l];
+          for (int lo = 0; lo < LR; ++lo) {
+          const int l = LR * ql + lo;
+          if (l >= D) break;
+          double2 ul;
+          ul.x = __shfl_sync(0xffffffffu, u[ql].x, grp * LR + lo);
+          ul.y = __shfl_sync(0xffffffffu, u[ql].y, grp * LR + lo);
 #pragma unroll
           for (int q = 0; q < RPL; ++q) {
             if (LR * q < D) {               // warp-uniform: some lane has a row here
@@ -1122,6 +1127,7 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
               r[q].y = fma(-ax, ul.y, r[q].y);
               r[q].y = fma(-ay, ul.x, r[q].y);
             }
+          }
           }
         }
 #pragma unroll
@@ -1567,9 +1573,9 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
   if (solver == 1 && D > 64) {   // refinement with an FP32 factor and FP64 residuals
     if (!mir_supported(D) || steer_ff == nullptr) return cudaErrorNotSupported;
     const int LR = tn.solve_lr == 16 ? 16 : 32;    // 16 lanes x 8 rows or 32 x 4, 8 warps
-    const size_t Dp = (size_t)D * (D + 1) / 2, ng = 256 / LR;
+    const size_t Dp = (size_t)D * (D + 1) / 2;
     auto bytes = [&](bool with_u) {
-      return ((Dp + D) * sizeof(float2) + 15) / 16 * 16 + ((with_u ? (size_t)C * D : 0) + ng * D) * 16 +
+      return ((Dp + D) * sizeof(float2) + 15) / 16 * 16 + (with_u ? (size_t)C * D : 0) * 16 +
              D * sizeof(float) + 16;
     };
     const bool sep_big = sep && bytes(true) <= 227 * 1024;
@@ -1647,12 +1653,10 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
     if (D <= kSmallMaxD) LR = 8;
     const int NT = (LR == 8 || (LR == 16 && D <= 64)) ? 128 : 256;
     const size_t Dp = (size_t)D * (D + 1) / 2;
-    const size_t ng = NT / LR;
-    // Lu, pivot column, (SEP) basis solutions, broadcast vectors; pivot
-    // reciprocals and the pivot flag
+    // Lu, pivot column, (SEP) basis solutions; pivot reciprocals and the
+    // pivot flag
     auto bytes = [&](bool with_u) {
-      return (Dp + D) * sizeof(double2) + ((with_u ? (size_t)C * D : 0) + ng * D) * 16 +
-             D * sizeof(double) + 16;
+      return (Dp + D) * sizeof(double2) + (with_u ? (size_t)C * D : 0) * 16 + D * sizeof(double) + 16;
     };
     const bool sep_big = sep && bytes(true) <= 227 * 1024;
     const size_t smem = bytes(sep_big);

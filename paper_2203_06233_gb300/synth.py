@@ -246,6 +246,13 @@ def large_cpi() -> CPISpec:
                    targets=random_targets(5, 32, 32768, 512, 64), seed=5)
 
 
+def large_small_cpi() -> CPISpec:
+    """An eighth of the large workload (R = 4096, about 540 MB) for profiling:
+    C32 P512 K512 R4096 T4 B256 S64."""
+    return CPISpec(32, 512, 512, 4096, 4, 256, 64, cnr_db=40.0,
+                   targets=random_targets(5, 8, 4096, 512, 64), seed=5)
+
+
 def batch_cpis(n: int = 512, seed: int = 4) -> List[CPISpec]:
     """n uneven CPIs: C in {4,8,16}, T in {2,3,4}, P = K in {64,128,256},
     R = 64 * U{16..256}, B = 64, S in {8,16}, CNR uniform in 20-40 dB, 4 targets each."""
@@ -296,6 +303,7 @@ WORKLOADS = {
     "mixed": mixed_cpi,
     "mixed_small": mixed_small_cpi,
     "large": large_cpi,
+    "large_small": large_small_cpi,
 }
 
 
