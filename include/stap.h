@@ -434,6 +434,24 @@ stap_status stap_get_status(stap_plan plan, int64_t* n_failed_systems);
 /* Static description of a status code. */
 const char* stap_status_string(stap_status status);
 
+/* 1 if this library is the checked build (compiled with -DSTAP_CHECKED),
+ * else 0.  No counterpart in the paper: a debugging aid. */
+int32_t stap_checked_build(void);
+
+/* Checked build only: every kernel compares each index into a global buffer
+ * (and the tensor-core kernels each shared- and tensor-memory offset) with
+ * the extent of that buffer as the launch sees it, skips an access outside
+ * it and records it; nothing traps.  This call waits for the current device,
+ * then reports and clears the records of all kernels on it: *count = accesses
+ * skipped since the last call; *site (a code naming the kind of access: 1/2
+ * Doppler input/output, 3/4 covariance input/output, 5/6 solve input/output,
+ * 7/8 apply input/output, 9/10 tensor-core input/output, 11 tensor-core
+ * shared memory, 12 tensor memory, 13 training matrices), *index and *extent
+ * of the first one found (site, index, extent may be NULL).  The normal build
+ * returns STAP_ERR_UNSUPPORTED with *count = 0.  No counterpart in the paper:
+ * a debugging aid. */
+stap_status stap_check_report(int64_t* count, int32_t* site, int64_t* index, int64_t* extent);
+
 /* STAP_ABI_VERSION of the loaded library. */
 int32_t stap_abi_version(void);
 

@@ -19,6 +19,10 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libstap.so")
+# the checked build (-DSTAP_CHECKED: bounds checks on every kernel index that
+# record and skip an out-of-range access), for debugging and its tests
+OBJ_DIR_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(LIB_DIR, "libstap_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -44,19 +48,26 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile every kernel source for sm_103a and link libstap.so; returns its path."""
-    os.makedirs(OBJ_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          checked: bool = False) -> str:
+    """Compile every kernel source for sm_103a and link libstap.so (with
+    checked=True: libstap_checked.so, compiled with -DSTAP_CHECKED); returns
+    its path."""
+    obj_dir = OBJ_DIR_CHECKED if checked else OBJ_DIR
+    lib = LIB_CHECKED if checked else LIB
+    os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
     cc = nvcc()
     srcs = _sources()
     hdrs = _headers()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    if checked:
+        flags += ["-DSTAP_CHECKED"]
     if ptxas_info:
         flags += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         if force or ptxas_info or _stale(obj, [src] + hdrs):
             cmd = [cc] + flags + ["-c", src, "-o", obj]
             if verbose:
@@ -70,16 +81,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    if force or _stale(LIB, objs):
-        tmp = LIB + ".tmp.%d" % os.getpid()
+    if force or _stale(lib, objs):
+        tmp = lib + ".tmp.%d" % os.getpid()
         cmd = [cc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                ptxas_info="--ptxas" in sys.argv))
+                ptxas_info="--ptxas" in sys.argv, checked="--checked" in sys.argv))

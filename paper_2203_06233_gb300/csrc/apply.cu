@@ -11,6 +11,7 @@
 // snapshot entry it reads x once and the chunk's weights as broadcast 16-byte
 // loads, i.e. 1 + SC/2 shared loads for 4*SC FMAs.  Each output row
 // out[s][k][cells] is written coalesced along range.
+#include "checked.cuh"
 #include "snapshots.cuh"
 
 namespace stap {
@@ -40,7 +41,10 @@ apply_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts, flo
       const int j = row / Sp, s = row - j * Sp;
       const float2* src = wts + (((size_t)k * NB + b0 + j) * S + s) * D;
       for (int d = lane; d < D; d += 32)
-        ws[((size_t)j * D + d) * Sp + s] = (s < S) ? __ldg(src + d) : make_float2(0.f, 0.f);
+        ws[((size_t)j * D + d) * Sp + s] =
+            (s < S && in_bounds((((long long)k * NB + b0 + j) * S + s) * D + d, (long long)K * NB * S * D,
+                                kSiteApplyIn))
+                ? __ldg(src + d) : make_float2(0.f, 0.f);
     }
   }
   const int cells = nbb * B;
@@ -76,7 +80,8 @@ apply_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts, flo
         }
 #pragma unroll
         for (int q = 0; q < SC; ++q)
-          if (s0 + q < S)
+          if (s0 + q < S && in_bounds(((long long)(s0 + q) * K + k) * ldr + (long long)r,
+                                      ((long long)S * K - 1) * ldr + R, kSiteApplyOut))
             out[((size_t)(s0 + q) * K + k) * ldr + r] = fmaf(acc[q].x, acc[q].x, acc[q].y * acc[q].y);
       }
     }
@@ -112,7 +117,9 @@ apply_reg_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
   {
     const float2* src = wts + ((size_t)k * NB + jb0) * S * D;
     const int n = nblk * S * D;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) ws[i] = __ldg(src + i);
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      ws[i] = in_bounds(((long long)k * NB + jb0) * S * D + i, (long long)K * NB * S * D, kSiteApplyIn)
+                  ? __ldg(src + i) : make_float2(0.f, 0.f);
   }
   const int r0 = cta_r0 + 2 * threadIdx.x;
   float4 x[D];                                    // (cell r0, cell r0 + 1) per entry
@@ -121,7 +128,9 @@ apply_reg_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
     for (int d = 0; d < D; ++d) {
       const int t = d / C, c = d - t * C;
       const int kk = wrap_bin(k + t - T / 2, K);
-      x[d] = __ldg(reinterpret_cast<const float4*>(dop + ((size_t)c * K + kk) * ldr + r0));
+      const long long o = ((long long)c * K + kk) * ldr + r0;
+      x[d] = in_bounds(o + 1, ((long long)C * K - 1) * ldr + R, kSiteApplyIn)
+                 ? __ldg(reinterpret_cast<const float4*>(dop + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
   __syncthreads();
@@ -144,8 +153,9 @@ apply_reg_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
       a1r = fmaf(w.z, xb.z, a1r); a1r = fmaf(w.w, xb.w, a1r);
       a1i = fmaf(w.z, xb.w, a1i); a1i = fmaf(-w.w, xb.z, a1i);
     }
-    *reinterpret_cast<float2*>(out + ((size_t)s * K + k) * ldr + r0) =
-        make_float2(fmaf(a0r, a0r, a0i * a0i), fmaf(a1r, a1r, a1i * a1i));
+    if (in_bounds(((long long)s * K + k) * ldr + r0 + 1, ((long long)S * K - 1) * ldr + R, kSiteApplyOut))
+      *reinterpret_cast<float2*>(out + ((size_t)s * K + k) * ldr + r0) =
+          make_float2(fmaf(a0r, a0r, a0i * a0i), fmaf(a1r, a1r, a1i * a1i));
   }
 }
 
@@ -212,4 +222,8 @@ cudaError_t launch_apply(const float2* dop, const float2* wts, float* out, int C
   return cudaGetLastError();
 }
 
+}  // namespace stap
+
+namespace stap {
+cudaError_t check_record_apply(CheckRecord* out) { return read_check_record(out); }
 }  // namespace stap

@@ -20,6 +20,7 @@
 // gives each thread whole entries (i >= l) of the lower triangle; the upper
 // triangle is written as the conjugate mirror.
 #include "df64.cuh"
+#include "checked.cuh"
 #include "snapshots.cuh"
 
 namespace stap {
@@ -165,7 +166,9 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
       float2* dst = X + row * ld;
       float mx = 0.f;
       for (int cell = lane; cell < cc; cell += 32) {
-        const float2 x = __ldg(src + cell);
+        const bool ok = in_bounds(((long long)c * K + kk) * ldr + (long long)b * B + c0 + cell,
+                                  ((long long)C * K - 1) * ldr + (long long)NB * B, kSiteCovIn);
+        const float2 x = ok ? __ldg(src + cell) : make_float2(0.f, 0.f);
         dst[cell] = x;
         mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
       }
@@ -250,7 +253,8 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
       v = make_double2(w.x, ff::dneg(w.y));
     }
     if (i == l) v.y = 0.0;
-    cov[(((size_t)(k0 + kl) * NB + b) * D + i) * D + l] = v;
+    const long long o = (((long long)(k0 + kl) * NB + b) * D + i) * D + l;
+    if (in_bounds(o, (long long)K * NB * D * D, kSiteCovOut)) cov[o] = v;
   }
 }
 
@@ -322,4 +326,8 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
   return cudaGetLastError();
 }
 
+}  // namespace stap
+
+namespace stap {
+cudaError_t check_record_covariance(CheckRecord* out) { return read_check_record(out); }
 }  // namespace stap

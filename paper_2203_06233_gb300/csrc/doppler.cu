@@ -23,6 +23,7 @@
 // channel c is written as output row t*C + c.  CTA row y = c*TW + t, so the TW
 // transforms of one channel run back to back and re-read its pulses from L2.
 // (TW = 1, PW = P: the plain transform.)
+#include "checked.cuh"
 #include "snapshots.cuh"
 
 namespace stap {
@@ -95,7 +96,9 @@ doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
     for (int n2 = 0; n2 < N2; ++n2) {
       const int n = n1 + N1 * n2;
       float2 x = make_float2(0.f, 0.f);
-      if (in_range && n >= t && n < t + PW) {
+      if (in_range && n >= t && n < t + PW &&
+          in_bounds((long long)c * P * ldr + r + (long long)n * ldr, (long long)(C * P - 1) * ldr + R,
+                    kSiteDopplerIn)) {
         x = __ldg(src + (size_t)n * ldr);
         const float h = __ldg(win + (n - t));
         x.x *= h;
@@ -124,7 +127,10 @@ doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
     if (r < R) {
       float2* dst = dop + ((size_t)t * C + c) * K * ldr + r;
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) dst[(size_t)(k2 + N2 * k1) * ldr] = u[k1];
+      for (int k1 = 0; k1 < N1; ++k1)
+        if (in_bounds(((long long)t * C + c) * K * ldr + r + (long long)(k2 + N2 * k1) * ldr,
+                      ((long long)C * TW * K - 1) * ldr + R, kSiteDopplerOut))
+          dst[(size_t)(k2 + N2 * k1) * ldr] = u[k1];
     }
   }
 }
@@ -183,4 +189,8 @@ cudaError_t launch_doppler(const float2* cube, float2* dop, const float* win, co
   }
 }
 
+}  // namespace stap
+
+namespace stap {
+cudaError_t check_record_doppler(CheckRecord* out) { return read_check_record(out); }
 }  // namespace stap

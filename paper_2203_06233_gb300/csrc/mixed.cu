@@ -53,6 +53,7 @@
 #include <cuda_fp16.h>
 
 #include "df64.cuh"
+#include "checked.cuh"
 #include "snapshots.cuh"
 #include "tcgen05.cuh"
 
@@ -244,7 +245,9 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
         const long long base = unit < units ? rowbase[p] : -1;
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc)
-          v[uu][cc] = (base >= 0 && j + cc < B) ? __ldg(dop + base + j + cc) : make_float2(0.f, 0.f);
+          v[uu][cc] = (base >= 0 && j + cc < B &&
+                       in_bounds(base + j + cc, ((long long)C * K - 1) * ldr + (long long)NB * B, kSiteTcIn))
+                          ? __ldg(dop + base + j + cc) : make_float2(0.f, 0.f);
       }
     };
     if (ok) load_chunk(0);
@@ -267,6 +270,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
         const int rg = unit >> 3, cmk = unit & 7;
         const int off = rg * SBO + cmk * 128 + (lane >> 2) * 16 + (lane & 3) * 4;
         const int offi = off + (GD / 8) * SBO;
+        if (!in_bounds(offi + 4, kCovPiece, kSiteTcSmem)) continue;
         if constexpr (PREC == kTF32X3) {
           uint32_t wr[2], wi[2];
           split_tf32(v[uu][0].x, wr);
@@ -352,6 +356,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
       for (int gg = gw0; gg <= gw1; ++gg) {
         for (int cb = hf * 8; cb < D8; cb += 16) {   // warp-uniform bounds
           float rr[8], ri[8], ir[8], ii[8];
+          in_bounds(256 + GD + gg * D8 + cb + 7, 512, kSiteTcTmem);   // recorded only
           tc::tmem_ld8(tmem + lb + gg * D8 + cb, rr);
           tc::tmem_ld8(tmem + lb + GD + gg * D8 + cb, ri);
           tc::tmem_ld8(tmem + 256 + lb + gg * D8 + cb, ir);
@@ -364,8 +369,11 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
                 const float re = (rr[u] + ii[u]) * sc * sc * invB;
                 const float im = l == a ? 0.f : (ir[u] - ri[u]) * sc * sc * invB;
                 const double dre = ff::f2d_exact(re), dim = ff::f2d_exact(im);
-                out[(size_t)l * D + a] = make_double2(dre, -dim);
-                if (!lower_only && l != a) out[(size_t)a * D + l] = make_double2(dre, dim);
+                const long long ext = nsys * D * D, o = sys * D * D;
+                if (in_bounds(o + (long long)l * D + a, ext, kSiteTcOut))
+                  out[(size_t)l * D + a] = make_double2(dre, -dim);
+                if (!lower_only && l != a && in_bounds(o + (long long)a * D + l, ext, kSiteTcOut))
+                  out[(size_t)a * D + l] = make_double2(dre, dim);
               }
             }
           }
@@ -500,10 +508,12 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
                                         : (kap0 + cmk * 8 + (lane & 3) * 2) >> 1;
           if (d < D) {
             if (isA) {
-              if (r0 + row < R) v[uu] = __ldg(dop + colbase[d] + r0 + row);
+              if (r0 + row < R &&
+                  in_bounds(colbase[d] + r0 + row, ((long long)C * K - 1) * ldr + R, kSiteTcIn))
+                v[uu] = __ldg(dop + colbase[d] + r0 + row);
             } else {
               const long long wb = wbase[row];
-              if (wb >= 0) v[uu] = __ldg(wts + wb + d);
+              if (wb >= 0 && in_bounds(wb + d, (long long)K * NB * S * D, kSiteTcIn)) v[uu] = __ldg(wts + wb + d);
             }
           }
         }
@@ -532,6 +542,7 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
         const int row = (ul / NCM) * 8 + (lane >> 2), cmk = ul % NCM;
         const int off = (isA ? 0 : kAppA) + (ul / NCM) * SBO + cmk * 128 + (lane >> 2) * 16 +
                         (lane & 3) * 4;
+        if (!in_bounds(off + 4, isA ? kAppA : PIECE, kSiteTcSmem)) continue;
         // the pair this row holds at (re, im) positions: x, or the weight
         // rows (wr, wi) and (-wi, wr)
         float2 e = v[uu];
@@ -606,6 +617,7 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
         const int c_lo = 2 * jj * S, c_hi = c_lo + 2 * S;
         for (int cb = (c_lo & ~7) + hf * 8; cb < c_hi; cb += 16) {   // warp-uniform bounds
           float a[8];
+          in_bounds(cb + 7, tmem_cols, kSiteTcTmem);   // recorded only
           tc::tmem_ld8(tmem + lb + cb, a);
           if (mine && j == jj) {
 #pragma unroll
@@ -618,7 +630,8 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
                   re = re * inv * invx;
                   im = im * inv * invx;
                 }
-                out[((size_t)s * K + k) * ldr + r] = fmaf(re, re, im * im);
+                if (in_bounds(((long long)s * K + k) * ldr + r, ((long long)S * K - 1) * ldr + R, kSiteTcOut))
+                  out[((size_t)s * K + k) * ldr + r] = fmaf(re, re, im * im);
               }
             }
           }
@@ -731,4 +744,8 @@ cudaError_t launch_apply_tc(const float2* dop, const float2* wts, float* out, in
   return cudaErrorInvalidValue;
 }
 
+}  // namespace stap
+
+namespace stap {
+cudaError_t check_record_mixed(CheckRecord* out) { return read_check_record(out); }
 }  // namespace stap

@@ -595,6 +595,43 @@ void stap_options_default(stap_options* opt) {
 
 int32_t stap_abi_version(void) { return STAP_ABI_VERSION; }
 
+int32_t stap_checked_build(void) {
+#ifdef STAP_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+stap_status stap_check_report(int64_t* count, int32_t* site, int64_t* index, int64_t* extent) {
+  if (!count) return STAP_ERR_INVALID_ARG;
+  *count = 0;
+  if (site) *site = 0;
+  if (index) *index = 0;
+  if (extent) *extent = 0;
+#ifndef STAP_CHECKED
+  return STAP_ERR_UNSUPPORTED;
+#else
+  if (cudaDeviceSynchronize() != cudaSuccess) return STAP_ERR_CUDA;
+  cudaError_t (*readers[])(stap::CheckRecord*) = {
+      stap::check_record_doppler, stap::check_record_covariance, stap::check_record_solve,
+      stap::check_record_apply,   stap::check_record_mixed,      stap::check_record_train};
+  bool first = true;
+  for (auto rd : readers) {
+    stap::CheckRecord r{};
+    if (rd(&r) != cudaSuccess) return STAP_ERR_CUDA;
+    *count += (int64_t)r.count;
+    if (r.count && first) {
+      first = false;
+      if (site) *site = r.site;
+      if (index) *index = r.index;
+      if (extent) *extent = r.extent;
+    }
+  }
+  return STAP_OK;
+#endif
+}
+
 const char* stap_status_string(stap_status s) {
   switch (s) {
     case STAP_OK: return "ok";

@@ -32,6 +32,7 @@
 #include <type_traits>
 
 #include "df64.cuh"
+#include "checked.cuh"
 #include "snapshots.cuh"
 
 namespace stap {
@@ -275,7 +276,7 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
         float2* w = wts + ((size_t)sys * S + s) * D;
         for (int i = 0; i < D; ++i) {
           const double2 ui = u[i * 32];
-          w[i] = good ? make_float2((float)ui.x * sf, (float)ui.y * sf) : make_float2(0.f, 0.f);
+          if (in_bounds((long long)(w - wts) + i, (long long)nsys * S * D, kSiteSolveOut)) w[i] = good ? make_float2((float)ui.x * sf, (float)ui.y * sf) : make_float2(0.f, 0.f);
         }
       }
     };
@@ -506,7 +507,7 @@ solve_reg_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
             float2* w = wts + ((size_t)sys * S + rhs) * D;
 #pragma unroll
             for (int i = 0; i < D; ++i)
-              w[i] = good ? make_float2((float)u[i].x * sf, (float)u[i].y * sf) : make_float2(0.f, 0.f);
+              if (in_bounds((long long)(w - wts) + i, (long long)nsys * S * D, kSiteSolveOut)) w[i] = good ? make_float2((float)u[i].x * sf, (float)u[i].y * sf) : make_float2(0.f, 0.f);
           }
         }
       }
@@ -764,7 +765,7 @@ solve_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
           float2* w = wts + ((size_t)sys * S + rhs) * D;
 #pragma unroll
           for (int i = 0; i < D; ++i)
-            w[i] = good ? make_float2(__fadd_rn(ur[i].hi, ur[i].lo) * sf, __fadd_rn(ui[i].hi, ui[i].lo) * sf)
+            if (in_bounds((long long)(w - wts) + i, (long long)nsys * S * D, kSiteSolveOut)) w[i] = good ? make_float2(__fadd_rn(ur[i].hi, ur[i].lo) * sf, __fadd_rn(ui[i].hi, ui[i].lo) * sf)
                         : make_float2(0.f, 0.f);
         }
       }
@@ -1056,7 +1057,7 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
       for (int q = 0; q < RPL; ++q) {
         const int i = li + LR * q;
         if (i < D)
-          w[i] = good ? make_float2((float)(u[q].x * scale), (float)(u[q].y * scale))
+          if (in_bounds((long long)(w - wts) + i, (long long)nsys * S * D, kSiteSolveOut)) w[i] = good ? make_float2((float)(u[q].x * scale), (float)(u[q].y * scale))
                       : make_float2(0.f, 0.f);
       }
     };
@@ -1116,7 +1117,9 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
               const int i = li + LR * q;
               const int ic = i < D ? i : D - 1;
               const bool low = ic >= l;
-              const double2 a = __ldg(low ? A + (size_t)ic * D + l : A + (size_t)l * D + ic);
+              const long long ao = low ? (long long)ic * D + l : (long long)l * D + ic;
+              const double2 a = in_bounds((long long)(A - cov) + ao, (long long)nsys * D * D, kSiteSolveIn)
+                                    ? __ldg(A + ao) : make_double2(0.0, 0.0);
               // R[i][l]: the conjugate above the diagonal by a sign-bit flip (a
               // negation would be one more FP64-pipe instruction per product)
               const long long flip = low ? 0LL : (long long)0x8000000000000000ull;
@@ -1207,7 +1210,7 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
           for (int q = 0; q < RPL; ++q) {
             const int i = li + LR * q;
             if (i < D)
-              w[i] = good ? make_float2(__fadd_rn(ur[q].hi, ur[q].lo) * sf,
+              if (in_bounds((long long)(w - wts) + i, (long long)nsys * S * D, kSiteSolveOut)) w[i] = good ? make_float2(__fadd_rn(ur[q].hi, ur[q].lo) * sf,
                                         __fadd_rn(ui[q].hi, ui[q].lo) * sf)
                           : make_float2(0.f, 0.f);
           }
@@ -1427,7 +1430,7 @@ solve_big_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
           for (int q = 0; q < RPL; ++q) {
             const int i = li + LR * q;
             if (i < D)
-              w[i] = good ? make_float2(__fadd_rn(ur[q].hi, ur[q].lo) * sf, __fadd_rn(ui[q].hi, ui[q].lo) * sf)
+              if (in_bounds((long long)(w - wts) + i, (long long)nsys * S * D, kSiteSolveOut)) w[i] = good ? make_float2(__fadd_rn(ur[q].hi, ur[q].lo) * sf, __fadd_rn(ui[q].hi, ui[q].lo) * sf)
                           : make_float2(0.f, 0.f);
           }
         }
@@ -1475,7 +1478,7 @@ solve_big_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
           for (int q = 0; q < RPL; ++q) {
             const int i = li + LR * q;
             if (i < D)
-              w[i] = good ? make_float2(__fadd_rn(cr[q].hi, cr[q].lo) * sf,
+              if (in_bounds((long long)(w - wts) + i, (long long)nsys * S * D, kSiteSolveOut)) w[i] = good ? make_float2(__fadd_rn(cr[q].hi, cr[q].lo) * sf,
                                         __fadd_rn(ci[q].hi, ci[q].lo) * sf)
                           : make_float2(0.f, 0.f);
           }
@@ -1741,4 +1744,8 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
   return cudaGetLastError();
 }
 
+}  // namespace stap
+
+namespace stap {
+cudaError_t check_record_solve(CheckRecord* out) { return read_check_record(out); }
 }  // namespace stap

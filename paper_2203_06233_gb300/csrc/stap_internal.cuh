@@ -50,6 +50,24 @@ cudaError_t launch_train_neighbours(const double2* in, double2* out, int K, int 
 cudaError_t launch_train_window(const double2* in, double2* out, int K, int NB, int D, int guard,
                                 int half, cudaStream_t s);
 
+// First out-of-range index found by the checked build in one source file
+// (checked.cuh): how many accesses were skipped, and the first one's site
+// code, index and the extent it was checked against.
+struct CheckRecord {
+  unsigned long long count;
+  long long index;
+  long long extent;
+  int site;
+  int pad;
+};
+// Each kernel source file's record, read and cleared (zeros in the normal build).
+cudaError_t check_record_doppler(CheckRecord* out);
+cudaError_t check_record_covariance(CheckRecord* out);
+cudaError_t check_record_solve(CheckRecord* out);
+cudaError_t check_record_apply(CheckRecord* out);
+cudaError_t check_record_mixed(CheckRecord* out);
+cudaError_t check_record_train(CheckRecord* out);
+
 // Snapshot lengths with a mixed-precision iterative-refinement solve.
 bool mir_supported(int D);
 

@@ -13,6 +13,7 @@
 // The sliding window below generalises it: a guard band of `guard` groups on
 // each side of the group under test and `half` training groups beyond it on
 // each side (guard 0, half 1 is the neighbour-block form).
+#include "checked.cuh"
 #include "stap_internal.cuh"
 
 namespace stap {
@@ -27,11 +28,12 @@ train_neighbours_kernel(const double2* __restrict__ in, double2* __restrict__ ou
     const int b = (int)(sys % NB);
     const bool lo = b > 0, hi = b + 1 < NB;
     double2 v;
-    if (lo && hi) {
+    if (lo && hi && in_bounds(idx - DD, total, kSiteTrain) && in_bounds(idx + DD, total, kSiteTrain)) {
       const double2 p = __ldg(in + idx - DD), q = __ldg(in + idx + DD);
       v = make_double2((p.x + q.x) * 0.5, (p.y + q.y) * 0.5);
     } else {
-      v = __ldg(in + idx + (lo ? -DD : DD));
+      const long long src = idx + (lo ? -DD : DD);
+      v = in_bounds(src, total, kSiteTrain) ? __ldg(in + src) : make_double2(0.0, 0.0);
     }
     out[idx] = v;
   }
@@ -60,7 +62,8 @@ train_window_kernel(const double2* __restrict__ in, double2* __restrict__ out, i
       for (int m = 0; m < half; ++m) {
         const int i = i0 + m;
         if (i < 0 || i >= NB) continue;
-        const double2 v = __ldg(base + (long long)i * DD);
+        const double2 v = in_bounds((sys - j + i) * DD + e, total, kSiteTrain) ? __ldg(base + (long long)i * DD)
+                                                                               : make_double2(0.0, 0.0);
         re += v.x;
         im += v.y;
         ++count;
@@ -94,4 +97,8 @@ cudaError_t launch_train_neighbours(const double2* in, double2* out, int K, int 
   return cudaGetLastError();
 }
 
+}  // namespace stap
+
+namespace stap {
+cudaError_t check_record_train(CheckRecord* out) { return read_check_record(out); }
 }  // namespace stap

@@ -49,7 +49,7 @@ EXPORTED = (
     "stap_run_cpi_noalloc", "stap_plan_batch_bytes", "stap_plan_autotune", "stap_plan_get_tuning",
     "stap_plan_set_tuning", "stap_train_neighbours", "stap_plan_stream_bytes", "stap_run_stream",
     "stap_plan_set_front_end", "stap_reduce_channels", "stap_plan_set_wait_limit",
-    "stap_train_window",
+    "stap_train_window", "stap_checked_build", "stap_check_report",
 )
 
 STAP_TUNING_LEN = 9
@@ -83,16 +83,22 @@ _lib = None
 _lock = threading.Lock()
 
 
+def checked_requested() -> bool:
+    """STAP_CHECKED=1 in the environment selects the checked build."""
+    return os.environ.get("STAP_CHECKED", "") not in ("", "0")
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked_requested() else _build.LIB
 
 
 def lib():
-    """Load libstap.so (building it first if it is missing or stale)."""
+    """Load libstap.so, or libstap_checked.so with STAP_CHECKED=1 (building it
+    first if it is missing or stale)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(checked=checked_requested())
             L = ctypes.CDLL(path)
             vp, i32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
             L.stap_options_default.argtypes = [ctypes.POINTER(stap_options)]
@@ -124,6 +130,9 @@ def lib():
             L.stap_plan_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32]
             L.stap_plan_get_tuning.argtypes = [vp, i32, ctypes.POINTER(i32)]
             L.stap_plan_set_tuning.argtypes = [vp, i32, ctypes.POINTER(i32)]
+            L.stap_checked_build.argtypes = []
+            L.stap_check_report.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i32),
+                                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
             L.stap_run_cpi_noalloc.argtypes = [ctypes.POINTER(stap_dims), ctypes.POINTER(stap_options),
                                                vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
             for f in EXPORTED:
@@ -357,6 +366,19 @@ def default_tune_cache() -> str:
 
 def stap_abi_version() -> int:
     return lib().stap_abi_version()
+
+
+def stap_checked_build() -> bool:
+    return lib().stap_checked_build() == 1
+
+
+def stap_check_report():
+    """(skipped accesses, site, index, extent) of the checked build, read and
+    cleared; raises StapError (unsupported) on the normal build."""
+    n, site, idx, ext = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().stap_check_report(ctypes.byref(n), ctypes.byref(site), ctypes.byref(idx),
+                                   ctypes.byref(ext)), "stap_check_report")
+    return n.value, site.value, idx.value, ext.value
 
 
 # --------------------------------------------------------------- convenience --

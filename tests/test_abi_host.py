@@ -296,3 +296,27 @@ def test_wait_limit_is_validated_without_cuda():
     assert L.stap_plan_set_wait_limit(h, stap.STAP_DEFAULT_WAIT_POLLS) == stap.STAP_OK
     assert L.stap_plan_set_wait_limit(None, 1) == stap.STAP_ERR_INVALID_ARG
     stap.stap_plan_destroy(h)
+
+
+def test_check_report_is_unsupported_in_the_normal_build():
+    assert not stap.stap_checked_build()
+    with pytest.raises(stap.StapError) as e:
+        stap.stap_check_report()
+    assert e.value.code == stap.STAP_ERR_UNSUPPORTED
+
+
+def test_checked_build_loads_and_exports_the_same_symbols():
+    """The checked library (compiled with -DSTAP_CHECKED) loads without a GPU,
+    says it is the checked build and exports every declared symbol."""
+    import subprocess
+    import sys
+    code = ("from paper_2203_06233_gb300 import stap\n"
+            "L = stap.lib()\n"
+            "assert stap.lib_path().endswith('libstap_checked.so')\n"
+            "assert stap.stap_checked_build()\n"
+            "missing = [n for n in stap.EXPORTED if not hasattr(L, n)]\n"
+            "assert not missing, missing\n"
+            "print('checked ok')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       env=dict(os.environ, STAP_CHECKED="1"), timeout=900)
+    assert r.returncode == 0 and "checked ok" in r.stdout, r.stdout + r.stderr
