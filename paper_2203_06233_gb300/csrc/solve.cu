@@ -809,24 +809,30 @@ __device__ __forceinline__ int colstart(int l, int D) { return l * D - l * (l - 
 
 // In-place forward (Lu z = x) or back (Lu^H z = x) substitution with the unit
 // lower factor, of one vector held as rows li + LR q by the LR lanes of group
-// `grp` (li = lane % LR).
+// `grp` (li = lane % LR).  The columns go in blocks of LR: block qb's columns
+// live in register x[qb] of the group's lanes (a shuffle broadcasts x_j), and
+// only the row blocks the block's columns update are visited -- q >= qb
+// forward, q <= qb back -- with the block indices compile-time constants, so
+// no FP64 instruction is issued for a row block with nothing to do (a warp
+// FP64 instruction costs the same with no lane active).
 template <int LR, int RPL, bool BACK>
 __device__ __forceinline__ void big_subst(double2 (&x)[RPL], const double2* __restrict__ Lc,
                                           int D, int li, int grp) {
-  for (int jj = 0; jj < D; ++jj) {
-    const int j = BACK ? D - 1 - jj : jj;
-    const int owner = (j % LR) + grp * LR, qj = j / LR;
-    double2 pick = x[0];
 #pragma unroll
-    for (int q = 1; q < RPL; ++q)
-      if (q == qj) pick = x[q];
-    double2 yj;
-    yj.x = __shfl_sync(0xffffffffu, pick.x, owner);
-    yj.y = __shfl_sync(0xffffffffu, pick.y, owner);
+  for (int bb = 0; bb < RPL; ++bb) {
+    const int qb = BACK ? RPL - 1 - bb : bb;
+    if (LR * qb >= D) continue;                           // warp-uniform
+    const int jn = min(LR, D - LR * qb);
+    for (int jj = 0; jj < jn; ++jj) {
+      const int jo = BACK ? jn - 1 - jj : jj;
+      const int j = LR * qb + jo;
+      double2 yj;
+      yj.x = __shfl_sync(0xffffffffu, x[qb].x, grp * LR + jo);
+      yj.y = __shfl_sync(0xffffffffu, x[qb].y, grp * LR + jo);
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      const bool touch = (BACK ? (q <= qj) : (q >= qj)) && LR * q < D;   // warp-uniform
-      if (touch) {
+      for (int q = 0; q < RPL; ++q) {
+        if (BACK ? (q > qb) : (q < qb)) continue;         // compile-time
+        if (LR * q >= D) continue;                        // warp-uniform
         const int i = li + LR * q;
         const bool act = BACK ? (i < j) : (i > j && i < D);
         if (act) {
@@ -876,20 +882,21 @@ __device__ __forceinline__ double group_sum(double v) {
 template <int LR, int RPL, bool BACK>
 __device__ __forceinline__ void big_subst_f32(float2 (&x)[RPL], const float2* __restrict__ Lc,
                                               int D, int li, int grp) {
-  for (int jj = 0; jj < D; ++jj) {
-    const int j = BACK ? D - 1 - jj : jj;
-    const int owner = (j % LR) + grp * LR, qj = j / LR;
-    float2 pick = x[0];
 #pragma unroll
-    for (int q = 1; q < RPL; ++q)
-      if (q == qj) pick = x[q];
-    float2 yj;
-    yj.x = __shfl_sync(0xffffffffu, pick.x, owner);
-    yj.y = __shfl_sync(0xffffffffu, pick.y, owner);
+  for (int bb = 0; bb < RPL; ++bb) {
+    const int qb = BACK ? RPL - 1 - bb : bb;
+    if (LR * qb >= D) continue;
+    const int jn = min(LR, D - LR * qb);
+    for (int jj = 0; jj < jn; ++jj) {
+      const int jo = BACK ? jn - 1 - jj : jj;
+      const int j = LR * qb + jo;
+      float2 yj;
+      yj.x = __shfl_sync(0xffffffffu, x[qb].x, grp * LR + jo);
+      yj.y = __shfl_sync(0xffffffffu, x[qb].y, grp * LR + jo);
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-      const bool touch = (BACK ? (q <= qj) : (q >= qj)) && LR * q < D;
-      if (touch) {
+      for (int q = 0; q < RPL; ++q) {
+        if (BACK ? (q > qb) : (q < qb)) continue;
+        if (LR * q >= D) continue;
         const int i = li + LR * q;
         const bool act = BACK ? (i < j) : (i > j && i < D);
         if (act) {
