@@ -398,11 +398,12 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
 
 constexpr int kAppRB = 64;                    // bytes of one operand row per chunk (4 core matrices)
 constexpr int kAppA = 128 * kAppRB;           // A piece: 128 cells (8 KB)
-constexpr int kAppB = 256 * kAppRB;           // B piece: up to 256 weight rows (16 KB)
+constexpr int kAppB = 256 * kAppRB;           // B piece: at most 256 weight rows (16 KB)
 constexpr int kAppU = 24;                     // staging units per warp and chunk ((16 + 32) x 4 / 8)
 
+// two stages of the pieces of 128 cell rows and NP weight rows
 template <int PREC>
-constexpr size_t apply_smem() { return 2 * (size_t)Fmt<PREC>::NPC * (kAppA + kAppB); }
+constexpr size_t apply_smem(int NP) { return 2 * (size_t)Fmt<PREC>::NPC * (kAppA + (size_t)NP * kAppRB); }
 
 template <int PREC>
 __global__ void __launch_bounds__(kThreads)
@@ -414,8 +415,8 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
   constexpr int KC = kAppRB / F::ESZ;         // K elements per chunk: 16 (tf32) or 32 (16-bit)
   constexpr int SBO = 8 * kAppRB;
   constexpr int NCM = kAppRB / 16;            // core matrices along K per chunk
-  constexpr int PIECE = kAppA + kAppB;
-  constexpr int STAGE = F::NPC * PIECE;
+  const int PIECE = kAppA + NP * kAppRB;      // cell rows, then NP weight rows
+  const int STAGE = F::NPC * PIECE;
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
@@ -677,19 +678,22 @@ cudaError_t launch_app(const float2* dop, const float2* wts, float* out, int C, 
   const int NB = R / B;
   const int nbt = B < 128 ? 128 / B : 1;
   const int NP = (2 * nbt * S + 15) / 16 * 16;
-  const int cols = NP + 8 <= 256 ? 256 : 512;   // epilogue reads whole blocks of 8 columns
+  // TMEM columns: a power of two >= 32 that holds NP columns plus the
+  // epilogue's whole blocks of 8
+  int cols = 32;
+  while (cols < NP + 8) cols <<= 1;
   const long long ntiles = (long long)K * ((R + 127) / 128);
-  const size_t smem = apply_smem<PREC>();
+  const size_t smem = apply_smem<PREC>(NP);
   static int set_bytes[64] = {0};
   cudaError_t e = ensure_smem(apply_tcx_kernel<PREC>, smem, set_bytes);
   if (e != cudaSuccess) return e;
   // resident CTAs per SM: registers and shared memory (occupancy query),
-  // and at most two when each holds 256 TMEM columns (one with 512)
+  // and no more than the SM's 512 TMEM columns hold
   int per_sm = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_tcx_kernel<PREC>, kThreads, smem) !=
           cudaSuccess || per_sm < 1)
     per_sm = 1;
-  per_sm = per_sm > (cols == 256 ? 2 : 1) ? (cols == 256 ? 2 : 1) : per_sm;
+  if (per_sm > 512 / cols) per_sm = 512 / cols;
   const long long cap = 152LL * per_sm;
   const long long blocks = ntiles < cap ? ntiles : cap;
   apply_tcx_kernel<PREC><<<(unsigned)blocks, kThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S,
