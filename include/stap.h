@@ -290,13 +290,37 @@ stap_status stap_apply(stap_plan plan, const void* dop_c64, const void* wts_c64,
  * With n_cpi > 1 the CPIs are packed, in order, into waves whose
  * intermediates fit in the workspace beyond step_bytes (any workspace of at
  * least run_bytes works; stap_plan_batch_bytes gives the size at which all
- * CPIs run in one wave).  Within a wave each CPI's chain runs on one of
- * several internal streams forked from the plan's stream, so CPIs overlap on
- * the GPU.  The launch sequence is captured into a CUDA graph on the first
- * call and replayed by later calls that pass the same cubes, outs, workspace
- * and stream; any change re-captures it.  The first batched call also creates
- * the plan's internal streams and events. */
+ * CPIs run in one wave).  Within a wave the CPIs run by the plan's batch
+ * schedule (stap_plan_set_batch_schedule): phase by phase in persistent
+ * launches over all the wave's CPIs (the default), or each CPI's chain on
+ * one of several internal streams.  The launch sequence is captured into a
+ * CUDA graph on the first call and replayed by later calls that pass the
+ * same cubes, outs, workspace and stream; any change re-captures it.  The
+ * first batched call also creates the plan's internal streams and events,
+ * and (persistent schedule) uploads the per-CPI parameter blocks to the
+ * workspace synchronously, before the capture. */
 stap_status stap_run_cpi(stap_plan plan, const void* const* cubes, float* const* outs);
+
+/* How stap_run_cpi schedules a batch (n_cpi > 1) within each wave:
+ *   STAP_BATCH_PERSISTENT  phase by phase (Doppler, covariance, training,
+ *                          solve, apply): the launches that the CPIs of the
+ *                          wave need are grouped by kernel, and each group
+ *                          runs as ONE persistent launch whose CTAs pull the
+ *                          next work item (a CPI's block of range cells,
+ *                          bins or systems) from an atomic counter over a
+ *                          device array of per-CPI parameter blocks, with no
+ *                          waits between CTAs; kernels without a persistent
+ *                          form (the mixed-precision refinement solves, the
+ *                          training averages, the tensor-core kernels) run
+ *                          one launch per CPI in that phase.  The default.
+ *   STAP_BATCH_STREAMS     each CPI's four-step chain on one of several
+ *                          internal streams, so that CPIs overlap.
+ * Either way the whole sequence is captured into a CUDA graph and replayed
+ * (see stap_run_cpi).  The results are the same.  stap_plan_autotune times
+ * both for a batch plan and keeps the faster. */
+typedef enum { STAP_BATCH_PERSISTENT = 0, STAP_BATCH_STREAMS = 1 } stap_batch_schedule;
+stap_status stap_plan_set_batch_schedule(stap_plan plan, int32_t schedule);
+stap_status stap_plan_get_batch_schedule(stap_plan plan, int32_t* schedule);
 
 /* Workspace size at which every CPI of the plan has its own intermediates,
  * i.e. stap_run_cpi runs the whole batch as one wave. */

@@ -11,6 +11,7 @@
 // snapshot entry it reads x once and the chunk's weights as broadcast 16-byte
 // loads, i.e. 1 + SC/2 shared loads for 4*SC FMAs.  Each output row
 // out[s][k][cells] is written coalesced along range.
+#include "batch.cuh"
 #include "checked.cuh"
 #include "snapshots.cuh"
 
@@ -20,15 +21,27 @@ namespace {
 constexpr int SC = 8;       // steering vectors per register chunk
 constexpr int kThreads = 256;
 
-__global__ void __launch_bounds__(kThreads)
-apply_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts, float* __restrict__ out,
-             int C, int K, int R, int ldr, int T, int B, int S, int NBB, int CC) {
+// Parameters of one apply launch (one CPI); gx = the launch's grid.x.
+struct ApplyParams {
+  const float2* dop;
+  const float2* wts;
+  float* out;
+  int C, K, R, ldr, T, B, S, NBB, CC;
+  int gx;
+};
+
+__device__ __forceinline__ void apply_body(const ApplyParams& prm, int bx, int by) {
+  const float2* __restrict__ dop = prm.dop;
+  const float2* __restrict__ wts = prm.wts;
+  float* __restrict__ out = prm.out;
+  const int C = prm.C, K = prm.K, R = prm.R, ldr = prm.ldr, T = prm.T, B = prm.B, S = prm.S,
+            NBB = prm.NBB, CC = prm.CC;
   extern __shared__ float4 sm4[];
   float2* sm = reinterpret_cast<float2*>(sm4);
   const int D = C * T;
   const int NB = R / B;
-  const int k = blockIdx.y;
-  const int b0 = blockIdx.x * NBB;
+  const int k = by;
+  const int b0 = bx * NBB;
   const int nbb = min(NBB, NB - b0);
   const int Sp = (S + SC - 1) / SC * SC;        // padded steering count (zero weights beyond S)
   float2* ws = sm;                              // [nbb][D][Sp]
@@ -88,6 +101,17 @@ apply_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts, flo
   }
 }
 
+__global__ void __launch_bounds__(kThreads)
+apply_kernel(ApplyParams p) {
+  apply_body(p, blockIdx.x, blockIdx.y);
+}
+
+// the same apply as a persistent launch over the CPIs of a batch
+__global__ void __launch_bounds__(kThreads)
+apply_batched(BatchCtl ctl) {
+  batched_loop<ApplyParams>(ctl, [&](const ApplyParams& p, int bx, int by, int) { apply_body(p, bx, by); });
+}
+
 // Register-resident form for small even D (the common shapes).  A thread owns
 // two adjacent range cells: their 2 x D snapshot entries are loaded straight
 // from the Doppler cube with one 16-byte load per entry (coalesced along
@@ -103,14 +127,16 @@ constexpr int kRegCells = 2 * kRegThreads;  // range cells per CTA
 
 // registers: 64 while the snapshots fit, more for larger D
 template <int D>
-__global__ void __launch_bounds__(kRegThreads, D <= 12 ? 8 : (D <= 18 ? 6 : 4))
-apply_reg_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
-                 float* __restrict__ out, int C, int K, int R, int ldr, int T, int B, int S) {
+__device__ __forceinline__ void apply_reg_body(const ApplyParams& prm, int bx, int by) {
+  const float2* __restrict__ dop = prm.dop;
+  const float2* __restrict__ wts = prm.wts;
+  float* __restrict__ out = prm.out;
+  const int C = prm.C, K = prm.K, R = prm.R, ldr = prm.ldr, T = prm.T, B = prm.B, S = prm.S;
   extern __shared__ float4 sm4[];
   float2* ws = reinterpret_cast<float2*>(sm4);    // [nblk][S][D]
   const int NB = R / B;
-  const int k = blockIdx.y;
-  const int cta_r0 = blockIdx.x * kRegCells;
+  const int k = by;
+  const int cta_r0 = bx * kRegCells;
   const int jb0 = cta_r0 / B;
   const int jb1 = min(NB - 1, (min(cta_r0 + kRegCells, R) - 1) / B);
   const int nblk = jb1 - jb0 + 1;
@@ -160,17 +186,33 @@ apply_reg_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
 }
 
 template <int D>
+__global__ void __launch_bounds__(kRegThreads, D <= 12 ? 8 : (D <= 18 ? 6 : 4))
+apply_reg_kernel(ApplyParams p) {
+  apply_reg_body<D>(p, blockIdx.x, blockIdx.y);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kRegThreads, D <= 12 ? 8 : (D <= 18 ? 6 : 4))
+apply_reg_batched(BatchCtl ctl) {
+  batched_loop<ApplyParams>(ctl, [&](const ApplyParams& p, int bx, int by, int) {
+    apply_reg_body<D>(p, bx, by);
+  });
+}
+
+template <int D>
 cudaError_t launch_apply_reg(const float2* dop, const float2* wts, float* out, int C, int K, int R,
                              int ldr, int T, int B, int S, cudaStream_t s) {
   const int NB = R / B;
   const int max_blk = kRegCells / B + 2;
   const size_t smem = (size_t)(max_blk < NB ? max_blk : NB) * S * D * sizeof(float2);
-  static int set_bytes[64] = {0};
+  static int set_bytes[64] = {0}, set_bytes_b[64] = {0};
   cudaError_t e = ensure_smem(apply_reg_kernel<D>, smem, set_bytes);
+  if (e == cudaSuccess) e = ensure_smem(apply_reg_batched<D>, smem, set_bytes_b);
   if (e != cudaSuccess) return e;
   dim3 grid((R + kRegCells - 1) / kRegCells, K);
-  apply_reg_kernel<D><<<grid, kRegThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S);
-  return cudaGetLastError();
+  const ApplyParams p{dop, wts, out, C, K, R, ldr, T, B, S, 0, 0, (int)grid.x};
+  return launch_params(reinterpret_cast<const void*>(apply_reg_kernel<D>),
+                       reinterpret_cast<const void*>(apply_reg_batched<D>), grid, kRegThreads, smem, s, p);
 }
 
 }  // namespace
@@ -214,12 +256,14 @@ cudaError_t launch_apply(const float2* dop, const float2* wts, float* out, int C
   if (wbytes(NBB) + (size_t)D * (CC + 1) * sizeof(float2) > kBudget)
     CC = (int)((kBudget - wbytes(NBB)) / ((size_t)D * sizeof(float2))) - 1;
   const size_t smem = wbytes(NBB) + (size_t)D * (CC + 1) * sizeof(float2);
-  static int set_bytes[64] = {0};
+  static int set_bytes[64] = {0}, set_bytes_b[64] = {0};
   cudaError_t e = ensure_smem(apply_kernel, smem, set_bytes);
+  if (e == cudaSuccess) e = ensure_smem(apply_batched, smem, set_bytes_b);
   if (e != cudaSuccess) return e;
   dim3 grid((NB + NBB - 1) / NBB, K);
-  apply_kernel<<<grid, kThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S, NBB, CC);
-  return cudaGetLastError();
+  const ApplyParams p{dop, wts, out, C, K, R, ldr, T, B, S, NBB, CC, (int)grid.x};
+  return launch_params(reinterpret_cast<const void*>(apply_kernel), reinterpret_cast<const void*>(apply_batched),
+                       grid, kThreads, smem, s, p);
 }
 
 }  // namespace stap

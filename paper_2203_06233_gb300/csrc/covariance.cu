@@ -20,6 +20,7 @@
 // gives each thread whole entries (i >= l) of the lower triangle; the upper
 // triangle is written as the conjugate mirror.
 #include "df64.cuh"
+#include "batch.cuh"
 #include "checked.cuh"
 #include "snapshots.cuh"
 
@@ -134,12 +135,25 @@ __device__ __forceinline__ void grid_add(float& hi, float& lo, float a, float b,
   lo = __fadd_rn(lo, r);
 }
 
-__global__ void __launch_bounds__(kPairMaxThreads)
-covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K,
-                        int ldr, int T, int B, int NB, int KT, int CB, double invB) {
+// Parameters of one bin-pair launch (one CPI): grid gx = NB blocks by K / KT
+// bin groups.
+struct CovPairsParams {
+  const float2* dop;
+  double2* cov;
+  int C, K, ldr, T, B, NB, KT, CB;
+  double invB;
+  int gx;
+};
+
+__device__ __forceinline__ void covariance_pairs_body(const CovPairsParams& prm, int bx, int by) {
+  const float2* __restrict__ dop = prm.dop;
+  double2* __restrict__ cov = prm.cov;
+  const int C = prm.C, K = prm.K, ldr = prm.ldr, T = prm.T, B = prm.B, NB = prm.NB, KT = prm.KT,
+            CB = prm.CB;
+  const double invB = prm.invB;
   extern __shared__ double2 smd[];
-  const int b = blockIdx.x;
-  const int k0 = blockIdx.y * KT;
+  const int b = bx;
+  const int k0 = by * KT;
   const int h = T / 2;
   const int NBIN = KT + T - 1;                    // staged bins k0-h .. k0+KT-1+(T-1-h)
   const int nrows = NBIN * C;
@@ -258,6 +272,19 @@ covariance_pairs_kernel(const float2* __restrict__ dop, double2* __restrict__ co
   }
 }
 
+__global__ void __launch_bounds__(kPairMaxThreads)
+covariance_pairs_kernel(CovPairsParams p) {
+  covariance_pairs_body(p, blockIdx.x, blockIdx.y);
+}
+
+// the same covariances as a persistent launch over the CPIs of a batch
+__global__ void __launch_bounds__(kPairMaxThreads)
+covariance_pairs_batched(BatchCtl ctl) {
+  batched_loop<CovPairsParams>(ctl, [&](const CovPairsParams& p, int bx, int by, int) {
+    covariance_pairs_body(p, bx, by);
+  });
+}
+
 }  // namespace
 
 cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K, int R, int ldr,
@@ -286,8 +313,9 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
     while (CB > 32 && pair_smem(KT, CB) > kPairBudget) CB = (CB + 1) / 2;
     if (pair_smem(KT, CB) <= kPairBudget) {
       const size_t smem = pair_smem(KT, CB);
-      static int set_bytes[64] = {0};
+      static int set_bytes[64] = {0}, set_bytes_b[64] = {0};
       cudaError_t e = ensure_smem(covariance_pairs_kernel, smem, set_bytes);
+      if (e == cudaSuccess) e = ensure_smem(covariance_pairs_batched, smem, set_bytes_b);
       if (e != cudaSuccess) return e;
       dim3 grid(NB, K / KT);
       // Many Q entries (large C): one thread per entry, rounded up to whole
@@ -303,9 +331,10 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
         threads = ((nitems + rounds - 1) / rounds + 31) / 32 * 32;
         if (threads > kPairMaxThreads) threads = kPairMaxThreads;
       }
-      covariance_pairs_kernel<<<grid, threads, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, KT, CB,
-                                                         1.0 / (double)B);
-      return cudaGetLastError();
+      const CovPairsParams p{dop, cov, C, K, ldr, T, B, NB, KT, CB, 1.0 / (double)B, (int)grid.x};
+      return launch_params(reinterpret_cast<const void*>(covariance_pairs_kernel),
+                           reinterpret_cast<const void*>(covariance_pairs_batched), grid, threads, smem,
+                           s, p);
     }
   }
   // general form: one tile per system, cells in chunks
@@ -322,8 +351,10 @@ cudaError_t launch_covariance_fp32(const float2* dop, double2* cov, int C, int K
   cudaError_t e = ensure_smem(covariance_ff_kernel, smem, set_bytes);
   if (e != cudaSuccess) return e;
   dim3 grid((NB + NS - 1) / NS, K);
-  covariance_ff_kernel<<<grid, 256, smem, s>>>(dop, cov, C, K, ldr, T, B, NB, NS, BC, 1.0 / (double)B);
-  return cudaGetLastError();
+  return launch_or_defer(s, [=](cudaStream_t st) {
+    covariance_ff_kernel<<<grid, 256, smem, st>>>(dop, cov, C, K, ldr, T, B, NB, NS, BC, 1.0 / (double)B);
+    return cudaGetLastError();
+  });
 }
 
 }  // namespace stap

@@ -23,6 +23,7 @@
 // channel c is written as output row t*C + c.  CTA row y = c*TW + t, so the TW
 // transforms of one channel run back to back and re-read its pulses from L2.
 // (TW = 1, PW = P: the plain transform.)
+#include "batch.cuh"
 #include "checked.cuh"
 #include "snapshots.cuh"
 
@@ -68,11 +69,24 @@ __device__ __forceinline__ void fft_reg(float2 (&v)[N], const float2* __restrict
   }
 }
 
+// Parameters of one launch (one CPI): grid gx = ceil(R / TR) range tiles by
+// C * TW rows.
+struct DopplerParams {
+  const float2* cube;
+  float2* dop;
+  const float* win;
+  const float2* tw;
+  int P, R, ldr, C, TW, PW;
+  int gx;
+};
+
 template <int LOGK, int TR>
-__global__ void __launch_bounds__(TR * (1 << ((LOGK + 1) / 2)))
-doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
-                   const float* __restrict__ win, const float2* __restrict__ twg, int P, int R,
-                   int ldr, int C, int TW, int PW) {
+__device__ __forceinline__ void doppler_body(const DopplerParams& prm, int bx, int by) {
+  const float2* __restrict__ cube = prm.cube;
+  float2* __restrict__ dop = prm.dop;
+  const float* __restrict__ win = prm.win;
+  const float2* __restrict__ twg = prm.tw;
+  const int P = prm.P, R = prm.R, ldr = prm.ldr, C = prm.C, TW = prm.TW, PW = prm.PW;
   constexpr int K = 1 << LOGK;
   constexpr int N1 = 1 << ((LOGK + 1) / 2);
   constexpr int N2 = 1 << (LOGK / 2);
@@ -81,8 +95,8 @@ doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
   float2* Y = smem + K;     // [N1][N2][TR]
 
   const int tid = threadIdx.x;
-  const int c = blockIdx.y / TW, t = blockIdx.y - c * TW;   // channel, sub-window
-  const int r0 = blockIdx.x * TR;
+  const int c = by / TW, t = by - c * TW;   // channel, sub-window
+  const int r0 = bx * TR;
   for (int m = tid; m < K; m += blockDim.x) tw[m] = twg[m];
 
   // ---- pass A: thread (col, n1), N2-point FFT over n2 ----
@@ -136,19 +150,36 @@ doppler_fft_kernel(const float2* __restrict__ cube, float2* __restrict__ dop,
 }
 
 template <int LOGK, int TR>
+__global__ void __launch_bounds__(TR * (1 << ((LOGK + 1) / 2)))
+doppler_fft_kernel(DopplerParams p) {
+  doppler_body<LOGK, TR>(p, blockIdx.x, blockIdx.y);
+}
+
+// the same transform as a persistent launch over the CPIs of a batch
+template <int LOGK, int TR>
+__global__ void __launch_bounds__(TR * (1 << ((LOGK + 1) / 2)))
+doppler_fft_batched(BatchCtl ctl) {
+  batched_loop<DopplerParams>(ctl, [&](const DopplerParams& p, int bx, int by, int) {
+    doppler_body<LOGK, TR>(p, bx, by);
+  });
+}
+
+template <int LOGK, int TR>
 cudaError_t launch_logk_tr(const float2* cube, float2* dop, const float* win, const float2* tw, int C,
                            int TW, int P, int R, int ldr, cudaStream_t s) {
   constexpr int K = 1 << LOGK;
   constexpr int N1 = 1 << ((LOGK + 1) / 2);
   const size_t smem = (size_t)K * sizeof(float2) * (1 + TR);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  auto kern = doppler_fft_kernel<LOGK, TR>;
-  static int set_bytes[64] = {0};
-  cudaError_t e = ensure_smem(kern, smem, set_bytes);
+  static int set_bytes[64] = {0}, set_bytes_b[64] = {0};
+  cudaError_t e = ensure_smem(doppler_fft_kernel<LOGK, TR>, smem, set_bytes);
+  if (e == cudaSuccess) e = ensure_smem(doppler_fft_batched<LOGK, TR>, smem, set_bytes_b);
   if (e != cudaSuccess) return e;
   dim3 grid((R + TR - 1) / TR, C * TW);
-  kern<<<grid, TR * N1, smem, s>>>(cube, dop, win, tw, P, R, ldr, C, TW, P - TW + 1);
-  return cudaGetLastError();
+  const DopplerParams p{cube, dop, win, tw, P, R, ldr, C, TW, P - TW + 1, (int)grid.x};
+  return launch_params(reinterpret_cast<const void*>(doppler_fft_kernel<LOGK, TR>),
+                       reinterpret_cast<const void*>(doppler_fft_batched<LOGK, TR>), grid, TR * N1,
+                       smem, s, p);
 }
 
 // range cells per CTA: by default 256-thread CTAs (TR * N1) of at most 32

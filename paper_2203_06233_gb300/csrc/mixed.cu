@@ -53,6 +53,7 @@
 #include <cuda_fp16.h>
 
 #include "df64.cuh"
+#include "batch.cuh"
 #include "checked.cuh"
 #include "snapshots.cuh"
 #include "tcgen05.cuh"
@@ -270,7 +271,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
         const int rg = unit >> 3, cmk = unit & 7;
         const int off = rg * SBO + cmk * 128 + (lane >> 2) * 16 + (lane & 3) * 4;
         const int offi = off + (GD / 8) * SBO;
-        if (!in_bounds(offi + 4, kCovPiece, kSiteTcSmem)) continue;
+        if (!in_bounds(offi + 3, kCovPiece, kSiteTcSmem)) continue;   // the word's last byte
         if constexpr (PREC == kTF32X3) {
           uint32_t wr[2], wi[2];
           split_tf32(v[uu][0].x, wr);
@@ -543,7 +544,7 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
         const int row = (ul / NCM) * 8 + (lane >> 2), cmk = ul % NCM;
         const int off = (isA ? 0 : kAppA) + (ul / NCM) * SBO + cmk * 128 + (lane >> 2) * 16 +
                         (lane & 3) * 4;
-        if (!in_bounds(off + 4, isA ? kAppA : PIECE, kSiteTcSmem)) continue;
+        if (!in_bounds(off + 3, isA ? kAppA : PIECE, kSiteTcSmem)) continue;   // the word's last byte
         // the pair this row holds at (re, im) positions: x, or the weight
         // rows (wr, wi) and (-wi, wr)
         float2 e = v[uu];
@@ -667,9 +668,11 @@ cudaError_t launch_cov(const float2* dop, double2* cov, int C, int K, int R, int
   cudaError_t e = ensure_smem(covariance_tcx_kernel<PREC>, smem, set_bytes);
   if (e != cudaSuccess) return e;
   const long long blocks = ntiles < 152 ? ntiles : 152;   // one CTA per SM (TMEM: 512 columns)
-  covariance_tcx_kernel<PREC><<<(unsigned)blocks, kThreads, smem, s>>>(
-      dop, cov, C, K, ldr, T, B, NB, D8, G, ntiles, lower_only ? 1 : 0, status, wait_polls);
-  return cudaGetLastError();
+  return launch_or_defer(s, [=](cudaStream_t st) {
+    covariance_tcx_kernel<PREC><<<(unsigned)blocks, kThreads, smem, st>>>(
+        dop, cov, C, K, ldr, T, B, NB, D8, G, ntiles, lower_only ? 1 : 0, status, wait_polls);
+    return cudaGetLastError();
+  });
 }
 
 template <int PREC>
@@ -689,17 +692,16 @@ cudaError_t launch_app(const float2* dop, const float2* wts, float* out, int C, 
   if (e != cudaSuccess) return e;
   // resident CTAs per SM: registers and shared memory (occupancy query),
   // and no more than the SM's 512 TMEM columns hold
-  int per_sm = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_tcx_kernel<PREC>, kThreads, smem) !=
-          cudaSuccess || per_sm < 1)
-    per_sm = 1;
+  int per_sm = resident_ctas(apply_tcx_kernel<PREC>, kThreads, smem);
   if (per_sm > 512 / cols) per_sm = 512 / cols;
   const long long cap = 152LL * per_sm;
   const long long blocks = ntiles < cap ? ntiles : cap;
-  apply_tcx_kernel<PREC><<<(unsigned)blocks, kThreads, smem, s>>>(dop, wts, out, C, K, R, ldr, T, B, S,
+  return launch_or_defer(s, [=](cudaStream_t st) {
+    apply_tcx_kernel<PREC><<<(unsigned)blocks, kThreads, smem, st>>>(dop, wts, out, C, K, R, ldr, T, B, S,
                                                                    NB, NP, cols, ntiles, status,
                                                                    wait_polls);
-  return cudaGetLastError();
+    return cudaGetLastError();
+  });
 }
 
 }  // namespace

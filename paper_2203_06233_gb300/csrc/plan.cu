@@ -4,11 +4,14 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
+#include "batch.cuh"
+#include "snapshots.cuh"
 #include "stap_internal.cuh"
 
 using stap::DeviceStatus;
@@ -148,6 +151,19 @@ void make_tables(Cpi& c) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// One step of a captured persistent batch: a persistent launch over a group
+// of recorded launches, or a recorded launch issued as it is.
+struct BatchStep {
+  const void* batched = nullptr;
+  int block = 0;
+  size_t smem = 0;
+  long long total = 0;
+  int n = 0;
+  size_t params_off = 0, prefix_off = 0, counter_off = 0;
+  int record = -1;   // replay of records[record]
+};
+
+
 }  // namespace
 
 struct stap_plan_s {
@@ -174,6 +190,13 @@ struct stap_plan_s {
   // polls before a pipeline wait of the tensor-core kernels gives up
   // (stap_plan_set_wait_limit)
   int wait_polls = stap::kDefaultWaitPolls;
+  // batch schedule (stap_plan_set_batch_schedule) and the workspace region
+  // that holds the persistent launches' parameter blocks, prefix sums and
+  // counters (batch plans only)
+  int batch_schedule = STAP_BATCH_PERSISTENT;
+  size_t ctl_off = 0, ctl_bytes = 0;
+  std::vector<BatchStep> batch_steps;                                    // the captured schedule
+  std::vector<std::function<cudaError_t(cudaStream_t)>> batch_replays;  // its one-CPI launches
 
   // batched runs (n_cpi > 1): forked streams and the captured launch graph
   static constexpr int kSideStreams = 8;
@@ -416,6 +439,10 @@ void drop_graph(stap_plan p) {
 // of kSideStreams forked streams, so small CPIs overlap.  The whole sequence
 // is captured once into a CUDA graph and replayed while the same buffers,
 // workspace and stream are passed.
+stap_status run_batched_persistent(stap_plan p, const void* const* cubes, float* const* outs,
+                                   cudaStream_t cs);
+stap_status issue_persistent_steps(stap_plan p, cudaStream_t cs);
+
 stap_status run_batched(stap_plan p, const void* const* cubes, float* const* outs) {
   const size_t n = p->cpis.size();
   bool same = p->graph_exec && p->graph_ws == p->ws && p->graph_ws_bytes == p->ws_bytes &&
@@ -438,11 +465,17 @@ stap_status run_batched(stap_plan p, const void* const* cubes, float* const* out
   const size_t arena = p->ws_bytes - p->step_bytes;
   char* base = p->ws + p->step_bytes;
   cudaStream_t cs = p->cap;
+  const bool persistent = p->batch_schedule == STAP_BATCH_PERSISTENT;
+  if (persistent) {   // record, group and upload the schedule before the capture
+    const stap_status ps = run_batched_persistent(p, cubes, outs, cs);
+    if (ps != STAP_OK) return ps;
+  }
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess)
     return STAP_ERR_CUDA;
   stap_status st = STAP_OK;
   int waves = 0;
-  size_t i = 0;
+  size_t i = persistent ? n : 0;
+  if (persistent) st = issue_persistent_steps(p, cs);
   while (st == STAP_OK && i < n) {
     // fork
     if (cudaEventRecord(p->fork_ev, cs) != cudaSuccess) { st = STAP_ERR_CUDA; break; }
@@ -488,6 +521,147 @@ stap_status run_batched(stap_plan p, const void* const* cubes, float* const* out
   p->graph_stream = p->stream;
   p->graph_waves = waves;
   return cudaGraphLaunch(p->graph_exec, p->stream) == cudaSuccess ? STAP_OK : STAP_ERR_CUDA;
+}
+
+// Persistent schedule: the CPIs of each wave phase by phase; the launches a
+// phase records for the wave's CPIs are grouped by persistent kernel and CTA
+// size (one persistent launch per group, its per-CPI parameter blocks and
+// prefix sums in the workspace's control region, uploaded before the
+// capture); launches without a persistent form are issued as recorded.
+stap_status run_batched_persistent(stap_plan p, const void* const* cubes, float* const* outs,
+                                   cudaStream_t cs) {
+  const size_t n = p->cpis.size();
+  const size_t arena = p->ws_bytes - p->step_bytes;
+  char* base = p->ws + p->step_bytes;
+  stap::LaunchRecorder rec;
+  std::vector<BatchStep> steps;
+  p->batch_steps.clear();
+  p->batch_replays.clear();
+  std::vector<unsigned char> ctl(p->ctl_bytes, 0);
+  size_t ctl_used = 0;
+  auto take = [&](size_t bytes) -> size_t {
+    const size_t at = ctl_used;
+    ctl_used = align_up(ctl_used + bytes);
+    return at;
+  };
+  stap_status st = STAP_OK;
+  size_t i = 0;
+  while (st == STAP_OK && i < n) {
+    // the wave: CPIs whose intermediates fit the arena together
+    struct Slot { size_t cpi; char *dop, *cov, *wts, *ctr; };
+    std::vector<Slot> wave;
+    size_t used = 0;
+    while (i < n && (wave.empty() || used + inter_bytes(p->opt, p->cpis[i]) <= arena)) {
+      const Cpi& c = p->cpis[i];
+      Slot sl;
+      sl.cpi = i;
+      sl.dop = base + used;
+      sl.cov = sl.dop + align_up(c.dop_elems() * 8);
+      sl.wts = sl.cov + align_up(c.cov_elems() * 16);
+      sl.ctr = sl.wts + align_up(c.wts_elems() * 8);
+      used += inter_bytes(p->opt, c);
+      wave.push_back(sl);
+      ++i;
+    }
+    const int nphase = p->opt.training != STAP_TRAIN_OWN_BLOCK ? 5 : 4;
+    for (int ph = 0; ph < nphase && st == STAP_OK; ++ph) {
+      rec.records.clear();
+      stap::current_recorder() = &rec;
+      for (const Slot& sl : wave) {
+        const Cpi& c = p->cpis[sl.cpi];
+        const bool trained = p->opt.training != STAP_TRAIN_OWN_BLOCK;
+        const char* solve_in = trained ? sl.ctr : sl.cov;
+        stap_status r = STAP_OK;
+        switch (trained ? ph : (ph < 2 ? ph : ph + 1)) {
+          case 0: r = do_doppler(p, c, cubes[sl.cpi], sl.dop, cs); break;
+          case 1: r = do_covariance(p, c, sl.dop, sl.cov, cs, -1, true); break;
+          case 2: r = do_train(p, c, sl.cov, sl.ctr, cs); break;
+          case 3: r = do_solve(p, c, solve_in, sl.wts, cs); break;
+          default: r = do_apply(p, c, sl.dop, sl.wts, outs[sl.cpi], cs); break;
+        }
+        if (r != STAP_OK) st = r;
+      }
+      stap::current_recorder() = nullptr;
+      if (st != STAP_OK) break;
+      // group the phase's records: same persistent kernel and CTA size
+      std::vector<char> done(rec.records.size(), 0);
+      for (size_t a = 0; a < rec.records.size(); ++a) {
+        if (done[a]) continue;
+        const stap::LaunchRecord& ra = rec.records[a];
+        if (!ra.batched) {   // issued as recorded, below
+          done[a] = 1;
+          continue;
+        }
+        std::vector<size_t> members;
+        for (size_t b = a; b < rec.records.size(); ++b)
+          if (!done[b] && rec.records[b].batched == ra.batched && rec.records[b].block == ra.block) {
+            members.push_back(b);
+            done[b] = 1;
+          }
+        BatchStep bs;
+        bs.batched = ra.batched;
+        bs.block = ra.block;
+        bs.n = (int)members.size();
+        bs.params_off = take(members.size() * stap::kMaxParamBytes);
+        bs.prefix_off = take((members.size() + 1) * sizeof(long long));
+        bs.counter_off = take(sizeof(unsigned long long));
+        if (ctl_used > p->ctl_bytes) return STAP_ERR_NO_WORKSPACE;
+        long long acc = 0;
+        for (size_t m = 0; m < members.size(); ++m) {
+          const stap::LaunchRecord& r = rec.records[members[m]];
+          std::memcpy(&ctl[bs.params_off + m * stap::kMaxParamBytes], r.params, (size_t)r.psize);
+          std::memcpy(&ctl[bs.prefix_off + m * sizeof(long long)], &acc, sizeof(long long));
+          acc += r.vblocks;
+          if (r.smem > bs.smem) bs.smem = r.smem;
+        }
+        std::memcpy(&ctl[bs.prefix_off + members.size() * sizeof(long long)], &acc, sizeof(long long));
+        bs.total = acc;
+        steps.push_back(bs);
+      }
+      // launches without a persistent form, in the order recorded
+      for (size_t a = 0; a < rec.records.size(); ++a)
+        if (!rec.records[a].batched) {
+          BatchStep bs;
+          bs.record = (int)p->batch_replays.size();
+          p->batch_replays.push_back(std::move(rec.records[a].replay));
+          steps.push_back(bs);
+        }
+    }
+    // the next wave reuses the arena: its steps follow in the same stream
+  }
+  if (st != STAP_OK) return st;
+  // parameter blocks, prefix sums and zeroed counters to the device, before the capture
+  if (ctl_used && cudaMemcpy(p->ws + p->ctl_off, ctl.data(), ctl_used, cudaMemcpyHostToDevice) != cudaSuccess)
+    return STAP_ERR_CUDA;
+  p->batch_steps = steps;
+  return STAP_OK;
+}
+
+// Issue the persistent schedule's steps on `cs` (inside the capture).
+stap_status issue_persistent_steps(stap_plan p, cudaStream_t cs) {
+  for (const BatchStep& bs : p->batch_steps) {
+    if (bs.record >= 0) {
+      if (p->batch_replays[bs.record](cs) != cudaSuccess) return STAP_ERR_CUDA;
+      continue;
+    }
+    if (bs.total == 0) continue;
+    unsigned long long* counter = p->at<unsigned long long>(p->ctl_off + bs.counter_off);
+    if (cudaMemsetAsync(counter, 0, sizeof(unsigned long long), cs) != cudaSuccess) return STAP_ERR_CUDA;
+    const int per_sm = stap::resident_ctas(bs.batched, bs.block, bs.smem);
+    int sms = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long grid = (long long)sms * per_sm;
+    if (grid > bs.total) grid = bs.total;
+    stap::BatchCtl ctl{p->at<const unsigned char>(p->ctl_off + bs.params_off),
+                       p->at<const long long>(p->ctl_off + bs.prefix_off), counter, bs.n,
+                       stap::kMaxParamBytes};
+    void* args[] = {&ctl};
+    if (cudaLaunchKernel(bs.batched, dim3((unsigned)grid), dim3(bs.block), args, bs.smem, cs) != cudaSuccess)
+      return STAP_ERR_CUDA;
+  }
+  return STAP_OK;
 }
 
 // The front end over a whole element cube on the device: one pass over all N
@@ -716,6 +890,12 @@ stap_status stap_plan_create(const stap_dims* dims, int32_t n_cpi, const stap_op
     if (c.cov_elems() > max_cov) max_cov = c.cov_elems();
     if (c.wts_elems() > max_wts) max_wts = c.wts_elems();
   }
+  if (n_cpi > 1) {   // persistent batch schedules: at most 5 launches per CPI and wave
+    const size_t recs = 5 * (size_t)n_cpi;
+    p->ctl_off = off;
+    p->ctl_bytes = align_up(recs * (stap::kMaxParamBytes + 2 * sizeof(long long)) + recs * 3 * kAlign);
+    off += p->ctl_bytes;
+  }
   p->step_bytes = off;
   p->dop_off = off;
   off = align_up(off + max_dop * 8);
@@ -906,6 +1086,20 @@ stap_status stap_run_cpi(stap_plan p, const void* const* cubes, float* const* ou
   if (st != STAP_OK) return st;
   if (p->cpis.size() > 1) return run_batched(p, cubes, outs);
   return run_single(p, cubes[0], outs[0]);
+}
+
+stap_status stap_plan_set_batch_schedule(stap_plan p, int32_t schedule) {
+  if (!p || (schedule != STAP_BATCH_PERSISTENT && schedule != STAP_BATCH_STREAMS))
+    return STAP_ERR_INVALID_ARG;
+  if (p->batch_schedule != schedule) drop_graph(p);
+  p->batch_schedule = schedule;
+  return STAP_OK;
+}
+
+stap_status stap_plan_get_batch_schedule(stap_plan p, int32_t* schedule) {
+  if (!p || !schedule) return STAP_ERR_INVALID_ARG;
+  *schedule = p->batch_schedule;
+  return STAP_OK;
 }
 
 stap_status stap_plan_batch_bytes(stap_plan p, size_t* all_concurrent_bytes) {
@@ -1234,6 +1428,27 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
         tuned[j] = 1;
       }
   }
+  // a batch: the persistent or the multi-stream schedule, whichever replays faster
+  if (st == STAP_OK && p->cpis.size() > 1) {
+    float best = kNever;
+    int bsched = p->batch_schedule;
+    for (int sched : {(int)STAP_BATCH_PERSISTENT, (int)STAP_BATCH_STREAMS}) {
+      p->batch_schedule = sched;
+      drop_graph(p);
+      if (run_batched(p, cubes, outs) != STAP_OK) continue;   // capture and first launch
+      cudaEventRecord(e0, p->stream);
+      bool ok = true;
+      for (int r = 0; r < reps && ok; ++r) ok = run_batched(p, cubes, outs) == STAP_OK;
+      cudaEventRecord(e1, p->stream);
+      float ms = kNever;
+      if (ok && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bsched = sched;
+      }
+    }
+    p->batch_schedule = bsched;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   drop_graph(p);
@@ -1284,3 +1499,10 @@ stap_status stap_get_status(stap_plan p, int64_t* n_failed) {
 }
 
 }  // extern "C"
+
+namespace stap {
+LaunchRecorder*& current_recorder() {
+  thread_local LaunchRecorder* r = nullptr;
+  return r;
+}
+}  // namespace stap

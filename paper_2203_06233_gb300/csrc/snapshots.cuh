@@ -28,8 +28,8 @@ __device__ __forceinline__ void stage_snapshots(float2* __restrict__ xs, int ld,
   }
 }
 
-// Raise a kernel's dynamic shared-memory limit above the 48 KB default, once
-// per device and size (set_bytes: per-device record of the limit already set,
+// Raise a kernel's dynamic shared-memory limit (static plus dynamic shared
+// memory above 48 KB needs it), once per device and size (set_bytes: per-device record of the limit already set,
 // devices 0..63).  The check and the update run under one lock and only ever
 // raise the limit, so that host threads launching the same kernel with
 // different sizes cannot lower it under each other.
@@ -40,7 +40,9 @@ inline std::mutex& smem_attr_lock() {
 
 template <typename F>
 cudaError_t ensure_smem(F* kern, size_t bytes, int* set_bytes /* [64] */) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  // the default limit covers static plus dynamic shared memory up to 48 KB;
+  // kernels here hold at most a few KB of static arrays
+  if (bytes <= 32 * 1024) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -50,6 +52,30 @@ cudaError_t ensure_smem(F* kern, size_t bytes, int* set_bytes /* [64] */) {
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) set_bytes[dev] = (int)bytes;
   return e;
+}
+
+// CTAs of `kern` that fit on one SM with `threads` threads and `dyn_smem`
+// bytes of dynamic shared memory: the smallest of the register, shared-memory
+// and thread limits (from the kernel's attributes and the device's limits).
+template <typename F>
+int resident_ctas(F* kern, int threads, size_t dyn_smem) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return 1;
+  int dev = 0, regs_sm = 65536, smem_sm = 233472, thr_sm = 2048;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  }
+  // registers are allocated per warp in units of 256
+  const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+  const int by_regs = warp_regs > 0 ? regs_sm / (warp_regs * (threads / 32)) : 1;
+  const size_t per_cta = dyn_smem + fa.sharedSizeBytes + 1024;   // 1 KB reserved per CTA
+  const int by_smem = (int)(smem_sm / per_cta);
+  const int by_thr = thr_sm / threads;
+  int n = by_regs < by_smem ? by_regs : by_smem;
+  n = n < by_thr ? n : by_thr;
+  return n < 1 ? 1 : n;
 }
 
 }  // namespace stap

@@ -32,6 +32,7 @@
 #include <type_traits>
 
 #include "df64.cuh"
+#include "batch.cuh"
 #include "checked.cuh"
 #include "snapshots.cuh"
 
@@ -167,13 +168,40 @@ __device__ __forceinline__ void sep_emit(const float4* Wt, int D, int S, int C, 
   }
 }
 
+// Parameters of one solve launch (one CPI); gx = the launch's grid size.
+struct SolveParams {
+  const double2* cov;
+  float2* wts;
+  const double2* steer;
+  const double2* sep_g;
+  const double2* sep_a;
+  const float4* steer_ff;
+  const float4* sep_a_ff;
+  long long nsys;
+  int D, S, C, TS;
+  double load_factor;
+  int refine_steps;
+  DeviceStatus* status;
+  int gx;
+};
+
 template <bool SEP>
-__global__ void __launch_bounds__(128)
-solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
-             const double2* __restrict__ steer, const double2* __restrict__ sep_g,
-             const double2* __restrict__ sep_a, const float4* __restrict__ steer_ff,
-             const float4* __restrict__ sep_a_ff, long long nsys, int D, int S, int C, int TS,
-             double load_factor, int refine_steps, DeviceStatus* __restrict__ status) {
+__device__ __forceinline__ void solve_kernel_body(const SolveParams& prm, long long bx, long long gx) {
+  const double2* __restrict__ cov = prm.cov;
+  float2* __restrict__ wts = prm.wts;
+  const double2* __restrict__ steer = prm.steer;
+  const double2* __restrict__ sep_g = prm.sep_g;
+  const float4* __restrict__ steer_ff = prm.steer_ff;
+  const float4* __restrict__ sep_a_ff = prm.sep_a_ff;
+  const long long nsys = prm.nsys;
+  const int S = prm.S, C = prm.C;
+  const double load_factor = prm.load_factor;
+  const int refine_steps = prm.refine_steps;
+  DeviceStatus* __restrict__ status = prm.status;
+  (void)steer; (void)sep_g; (void)steer_ff; (void)sep_a_ff;
+  const double2* __restrict__ sep_a = prm.sep_a;
+  const int D = prm.D, TS = prm.TS;
+  (void)sep_a;
   extern __shared__ double2 sm[];
   const int nw = blockDim.x >> 5;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -187,8 +215,8 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
   double* invd = reinterpret_cast<double*>(sm + nw * warp_elems) + ((size_t)warp * G + team) * D;
   const double invD = 1.0 / (double)D;
 
-  for (long long base = ((long long)blockIdx.x * nw + warp) * G; base < nsys;
-       base += (long long)gridDim.x * nw * G) {
+  for (long long base = ((long long)bx * nw + warp) * G; base < nsys;
+       base += (long long)gx * nw * G) {
     const long long sys = base + team;
     const bool valid = sys < nsys;
     const double2* A = cov + (size_t)(valid ? sys : nsys - 1) * D * D;
@@ -333,6 +361,21 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
   }
 }
 
+template <bool SEP>
+__global__ void __launch_bounds__(128)
+solve_kernel(SolveParams p) {
+  solve_kernel_body<SEP>(p, blockIdx.x, gridDim.x);
+}
+
+// the same solves as a persistent launch over the CPIs of a batch
+template <bool SEP>
+__global__ void __launch_bounds__(128)
+solve_kernel_batched(BatchCtl ctl) {
+  batched_loop<SolveParams>(ctl, [&](const SolveParams& p, int bx, int, int gx) {
+    solve_kernel_body<SEP>(p, bx, gx);
+  });
+}
+
 // ---------------------------------------------------------------------------
 // Register-resident form for the common snapshot lengths (D = 8, 12, 16):
 // the team mapping of solve_kernel, but with D a compile-time constant, every
@@ -346,12 +389,20 @@ solve_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
 // trailing entries with l_ij conj(a_lj), a_lj the column before the division
 // (= l_lj d_j), kept in a small per-team buffer.
 template <int D, bool SEP>
-__global__ void __launch_bounds__(128, 4)
-solve_reg_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
-                 const double2* __restrict__ steer, const double2* __restrict__ sep_g,
-                 const float4* __restrict__ steer_ff, const float4* __restrict__ sep_a_ff,
-                 long long nsys, int S, int C, int TS, double load_factor, int refine_steps,
-                 DeviceStatus* __restrict__ status) {
+__device__ __forceinline__ void solve_reg_kernel_body(const SolveParams& prm, long long bx, long long gx) {
+  const double2* __restrict__ cov = prm.cov;
+  float2* __restrict__ wts = prm.wts;
+  const double2* __restrict__ steer = prm.steer;
+  const double2* __restrict__ sep_g = prm.sep_g;
+  const float4* __restrict__ steer_ff = prm.steer_ff;
+  const float4* __restrict__ sep_a_ff = prm.sep_a_ff;
+  const long long nsys = prm.nsys;
+  const int S = prm.S, C = prm.C;
+  const double load_factor = prm.load_factor;
+  const int refine_steps = prm.refine_steps;
+  DeviceStatus* __restrict__ status = prm.status;
+  (void)steer; (void)sep_g; (void)steer_ff; (void)sep_a_ff;
+  const int TS = prm.TS;
   constexpr int Dp = D * (D + 1) / 2;
   extern __shared__ double2 sm[];
   const int nw = blockDim.x >> 5;
@@ -367,8 +418,8 @@ solve_reg_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
   float4* Wf = reinterpret_cast<float4*>(alias ? wbase : wbase + (size_t)G * (Dp + D));
   double* rdp = reinterpret_cast<double*>(sm + nw * warp_elems) + ((size_t)warp * G + team) * D;
 
-  for (long long base = ((long long)blockIdx.x * nw + warp) * G; base < nsys;
-       base += (long long)gridDim.x * nw * G) {
+  for (long long base = ((long long)bx * nw + warp) * G; base < nsys;
+       base += (long long)gx * nw * G) {
     const long long sys = base + team;
     const bool valid = sys < nsys;
     const double2* A = cov + (size_t)(valid ? sys : nsys - 1) * D * D;
@@ -520,6 +571,21 @@ solve_reg_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
     if (valid && !ok && tl == 0) atomicAdd(&status->n_failed, 1ULL);
     __syncwarp();  // the next batch reuses L, col, Wf
   }
+}
+
+template <int D, bool SEP>
+__global__ void __launch_bounds__(128, 4)
+solve_reg_kernel(SolveParams p) {
+  solve_reg_kernel_body<D, SEP>(p, blockIdx.x, gridDim.x);
+}
+
+// the same solves as a persistent launch over the CPIs of a batch
+template <int D, bool SEP>
+__global__ void __launch_bounds__(128, 4)
+solve_reg_kernel_batched(BatchCtl ctl) {
+  batched_loop<SolveParams>(ctl, [&](const SolveParams& p, int bx, int, int gx) {
+    solve_reg_kernel_body<D, SEP>(p, bx, gx);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -941,13 +1007,21 @@ __device__ __forceinline__ void big_solve_f32(float2 (&x)[RPL], const float2* __
 // residual in FP64 from the input as below, its FP32 correction added in FP64.
 // 256-thread CTAs hold a D > 64 system's factor (one CTA per SM), so they may
 // use the whole register file; 128-thread CTAs run three per SM.
-template <bool SEP, int LR, int NT, int RPL, bool F32F = false>
-__global__ void __launch_bounds__(NT, NT >= 256 ? 1 : 3)
-solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
-                 const double2* __restrict__ steer, const double2* __restrict__ sep_g,
-                 const float4* __restrict__ steer_ff, const float4* __restrict__ sep_a_ff,
-                 long long nsys, int D, int S, int C, double load_factor, int refine_steps,
-                 DeviceStatus* __restrict__ status) {
+template <bool SEP, int LR, int NT, int RPL, bool F32F>
+__device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, long long bx, long long gx) {
+  const double2* __restrict__ cov = prm.cov;
+  float2* __restrict__ wts = prm.wts;
+  const double2* __restrict__ steer = prm.steer;
+  const double2* __restrict__ sep_g = prm.sep_g;
+  const float4* __restrict__ steer_ff = prm.steer_ff;
+  const float4* __restrict__ sep_a_ff = prm.sep_a_ff;
+  const long long nsys = prm.nsys;
+  const int S = prm.S, C = prm.C;
+  const double load_factor = prm.load_factor;
+  const int refine_steps = prm.refine_steps;
+  DeviceStatus* __restrict__ status = prm.status;
+  (void)steer; (void)sep_g; (void)steer_ff; (void)sep_a_ff;
+  const int D = prm.D;
   using LT = typename std::conditional<F32F, float2, double2>::type;   // factor entries
   using RT = typename std::conditional<F32F, float, double>::type;     // pivots
   extern __shared__ double2 sm[];
@@ -976,7 +1050,7 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
     return RT(1) / d;
   };
 
-  for (long long sys = blockIdx.x; sys < nsys; sys += gridDim.x) {
+  for (long long sys = bx; sys < nsys; sys += gx) {
     const double2* A = cov + (size_t)sys * D * D;
     double tr = 0.0;
     for (int j = 0; j < D; ++j) tr += __ldg(&A[(size_t)j * D + j].x);
@@ -1227,6 +1301,21 @@ solve_big_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
     if (!ok && tid == 0) atomicAdd(&status->n_failed, 1ULL);
     __syncthreads();  // the next system reuses Lc, colb, Ubf, rd
   }
+}
+
+template <bool SEP, int LR, int NT, int RPL, bool F32F>
+__global__ void __launch_bounds__(NT, NT >= 256 ? 1 : 3)
+solve_big_kernel(SolveParams p) {
+  solve_big_kernel_body<SEP, LR, NT, RPL, F32F>(p, blockIdx.x, gridDim.x);
+}
+
+// the same solves as a persistent launch over the CPIs of a batch
+template <bool SEP, int LR, int NT, int RPL, bool F32F>
+__global__ void __launch_bounds__(NT, NT >= 256 ? 1 : 3)
+solve_big_kernel_batched(BatchCtl ctl) {
+  batched_loop<SolveParams>(ctl, [&](const SolveParams& p, int bx, int, int gx) {
+    solve_big_kernel_body<SEP, LR, NT, RPL, F32F>(p, bx, gx);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -1508,9 +1597,11 @@ cudaError_t launch_big_mir(const double2* cov, float2* wts, const float4* steer_
   const int per_sm = (int)(228 * 1024 / (smem + 1024));
   long long blocks = 152LL * (per_sm < 1 ? 1 : per_sm) * 2;
   if (blocks > nsys) blocks = nsys;
-  solve_big_mir_kernel<SEP, LR, NT, RPL><<<(unsigned)blocks, NT, smem, s>>>(
-      cov, wts, steer_ff, g_ff, sep_a_ff, nsys, D, S, C, lf, refine, status);
-  return cudaGetLastError();
+  return launch_or_defer(s, [=](cudaStream_t st) {
+    solve_big_mir_kernel<SEP, LR, NT, RPL><<<(unsigned)blocks, NT, smem, st>>>(
+        cov, wts, steer_ff, g_ff, sep_a_ff, nsys, D, S, C, lf, refine, status);
+    return cudaGetLastError();
+  });
 }
 
 template <bool SEP, int LR, int NT, int RPL, bool F32F = false>
@@ -1518,15 +1609,19 @@ cudaError_t launch_big(const double2* cov, float2* wts, const double2* steer, co
                        const float4* steer_ff, const float4* sep_a_ff, long long nsys, int D, int S,
                        int C, double lf, int refine, DeviceStatus* status, size_t smem,
                        cudaStream_t s) {
-  static int set_bytes[64] = {0};
+  static int set_bytes[64] = {0}, set_bytes_b[64] = {0};
   cudaError_t e = ensure_smem(solve_big_kernel<SEP, LR, NT, RPL, F32F>, smem, set_bytes);
+  if (e == cudaSuccess) e = ensure_smem(solve_big_kernel_batched<SEP, LR, NT, RPL, F32F>, smem, set_bytes_b);
   if (e != cudaSuccess) return e;
   const int per_sm = (int)(228 * 1024 / (smem + 1024));
   long long blocks = 152LL * (per_sm < 1 ? 1 : per_sm) * 2;
   if (blocks > nsys) blocks = nsys;
-  solve_big_kernel<SEP, LR, NT, RPL, F32F><<<(unsigned)blocks, NT, smem, s>>>(
-      cov, wts, steer, sep_g, steer_ff, sep_a_ff, nsys, D, S, C, lf, refine, status);
-  return cudaGetLastError();
+  // one system per virtual block of the persistent twin
+  const SolveParams p{cov, wts, steer, sep_g, nullptr, steer_ff, sep_a_ff, nsys, D, S, C, 0, lf,
+                      refine, status, (int)nsys};
+  return launch_params(reinterpret_cast<const void*>(solve_big_kernel<SEP, LR, NT, RPL, F32F>),
+                       reinterpret_cast<const void*>(solve_big_kernel_batched<SEP, LR, NT, RPL, F32F>),
+                       dim3((unsigned)blocks), NT, smem, s, p, nsys);
 }
 
 template <int D, bool SEP>
@@ -1535,12 +1630,18 @@ cudaError_t launch_reg(const double2* cov, float2* wts, const double2* steer, co
                        int TS, int nw, long long blocks, size_t smem, double lf, int refine,
                        DeviceStatus* status, cudaStream_t s) {
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  static int set_bytes[64] = {0};
+  static int set_bytes[64] = {0}, set_bytes_b[64] = {0};
   cudaError_t e = ensure_smem(solve_reg_kernel<D, SEP>, smem, set_bytes);
+  if (e == cudaSuccess) e = ensure_smem(solve_reg_kernel_batched<D, SEP>, smem, set_bytes_b);
   if (e != cudaSuccess) return e;
-  solve_reg_kernel<D, SEP><<<(unsigned)blocks, nw * 32, smem, s>>>(
-      cov, wts, steer, sep_g, steer_ff, sep_a_ff, nsys, S, C, TS, lf, refine, status);
-  return cudaGetLastError();
+  // one CTA's nw warps x 32/TS systems per virtual block of the persistent twin
+  const long long per = (long long)nw * (32 / TS);
+  const long long vb = (nsys + per - 1) / per;
+  const SolveParams p{cov, wts, steer, sep_g, nullptr, steer_ff, sep_a_ff, nsys, D, S, C, TS, lf,
+                      refine, status, (int)vb};
+  return launch_params(reinterpret_cast<const void*>(solve_reg_kernel<D, SEP>),
+                       reinterpret_cast<const void*>(solve_reg_kernel_batched<D, SEP>),
+                       dim3((unsigned)blocks), nw * 32, smem, s, p, vb);
 }
 
 template <int D, bool SEP>
@@ -1552,9 +1653,11 @@ cudaError_t launch_mir(const double2* cov, float2* wts, const float4* steer_ff, 
   static int set_bytes[64] = {0};
   cudaError_t e = ensure_smem(solve_mir_kernel<D, SEP>, smem, set_bytes);
   if (e != cudaSuccess) return e;
-  solve_mir_kernel<D, SEP><<<(unsigned)blocks, nw * 32, smem, s>>>(
-      cov, wts, steer_ff, g_ff, sep_a_ff, nsys, S, C, TS, lf, refine, status);
-  return cudaGetLastError();
+  return launch_or_defer(s, [=](cudaStream_t st) {
+    solve_mir_kernel<D, SEP><<<(unsigned)blocks, nw * 32, smem, st>>>(
+        cov, wts, steer_ff, g_ff, sep_a_ff, nsys, S, C, TS, lf, refine, status);
+    return cudaGetLastError();
+  });
 }
 
 }  // namespace
@@ -1735,20 +1838,27 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
   long long blocks = (batches + nw - 1) / nw;
   if (blocks > 152LL * 64) blocks = 152LL * 64;
   cudaError_t e;
+  // one CTA's nw warps x 32/TS systems per virtual block of the persistent twin
+  const long long per = (long long)nw * G;
+  const long long vb = (nsys + per - 1) / per;
   if (sep) {
-    static int set_bytes[64] = {0};
+    static int set_bytes[64] = {0}, set_bytes_b[64] = {0};
     if ((e = ensure_smem(solve_kernel<true>, smem, set_bytes)) != cudaSuccess) return e;
-    solve_kernel<true><<<(unsigned)blocks, nw * 32, smem, s>>>(cov, wts, steer, sep_g, sep_a,
-                                                               steer_ff, sep_a_ff, nsys, D, S, C,
-                                                               TS, load_factor, refine_steps, status);
-  } else {
-    static int set_bytes[64] = {0};
-    if ((e = ensure_smem(solve_kernel<false>, smem, set_bytes)) != cudaSuccess) return e;
-    solve_kernel<false><<<(unsigned)blocks, nw * 32, smem, s>>>(cov, wts, steer, nullptr, nullptr,
-                                                                nullptr, nullptr, nsys, D, S, C, TS,
-                                                                load_factor, refine_steps, status);
+    if ((e = ensure_smem(solve_kernel_batched<true>, smem, set_bytes_b)) != cudaSuccess) return e;
+    const SolveParams p{cov, wts, steer, sep_g, sep_a, steer_ff, sep_a_ff, nsys, D, S, C, TS,
+                        load_factor, refine_steps, status, (int)vb};
+    return launch_params(reinterpret_cast<const void*>(solve_kernel<true>),
+                         reinterpret_cast<const void*>(solve_kernel_batched<true>),
+                         dim3((unsigned)blocks), nw * 32, smem, s, p, vb);
   }
-  return cudaGetLastError();
+  static int set_bytes[64] = {0}, set_bytes_b[64] = {0};
+  if ((e = ensure_smem(solve_kernel<false>, smem, set_bytes)) != cudaSuccess) return e;
+  if ((e = ensure_smem(solve_kernel_batched<false>, smem, set_bytes_b)) != cudaSuccess) return e;
+  const SolveParams p{cov, wts, steer, nullptr, nullptr, nullptr, nullptr, nsys, D, S, C, TS,
+                      load_factor, refine_steps, status, (int)vb};
+  return launch_params(reinterpret_cast<const void*>(solve_kernel<false>),
+                       reinterpret_cast<const void*>(solve_kernel_batched<false>),
+                       dim3((unsigned)blocks), nw * 32, smem, s, p, vb);
 }
 
 }  // namespace stap

@@ -13,6 +13,7 @@
 // The sliding window below generalises it: a guard band of `guard` groups on
 // each side of the group under test and `half` training groups beyond it on
 // each side (guard 0, half 1 is the neighbour-block form).
+#include "batch.cuh"
 #include "checked.cuh"
 #include "stap_internal.cuh"
 
@@ -82,8 +83,10 @@ cudaError_t launch_train_window(const double2* in, double2* out, int K, int NB, 
   const long long total = (long long)K * NB * DD;
   long long blocks = (total + 255) / 256;
   if (blocks > 152LL * 16) blocks = 152LL * 16;
-  train_window_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, NB, DD, total, guard, half);
-  return cudaGetLastError();
+  return launch_or_defer(s, [=](cudaStream_t st) {
+    train_window_kernel<<<(unsigned)blocks, 256, 0, st>>>(in, out, NB, DD, total, guard, half);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_train_neighbours(const double2* in, double2* out, int K, int NB, int D,
@@ -93,8 +96,10 @@ cudaError_t launch_train_neighbours(const double2* in, double2* out, int K, int 
   const long long total = (long long)K * NB * DD;
   long long blocks = (total + 255) / 256;
   if (blocks > 152LL * 16) blocks = 152LL * 16;
-  train_neighbours_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, NB, DD, total);
-  return cudaGetLastError();
+  return launch_or_defer(s, [=](cudaStream_t st) {
+    train_neighbours_kernel<<<(unsigned)blocks, 256, 0, st>>>(in, out, NB, DD, total);
+    return cudaGetLastError();
+  });
 }
 
 }  // namespace stap

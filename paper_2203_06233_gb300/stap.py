@@ -37,6 +37,8 @@ STAP_SOLVE_MIXED_IR = 1
 STAP_TRAIN_OWN_BLOCK = 0
 STAP_TRAIN_NEIGHBOURS = 1
 STAP_TRAIN_WINDOW = 2
+STAP_BATCH_PERSISTENT = 0
+STAP_BATCH_STREAMS = 1
 STAP_SNAP_ADJACENT_BINS = 0
 STAP_SNAP_PRI_STAGGERED = 1
 
@@ -49,7 +51,8 @@ EXPORTED = (
     "stap_run_cpi_noalloc", "stap_plan_batch_bytes", "stap_plan_autotune", "stap_plan_get_tuning",
     "stap_plan_set_tuning", "stap_train_neighbours", "stap_plan_stream_bytes", "stap_run_stream",
     "stap_plan_set_front_end", "stap_reduce_channels", "stap_plan_set_wait_limit",
-    "stap_train_window", "stap_checked_build", "stap_check_report",
+    "stap_train_window", "stap_checked_build", "stap_check_report", "stap_plan_set_batch_schedule",
+    "stap_plan_get_batch_schedule",
 )
 
 STAP_TUNING_LEN = 9
@@ -131,6 +134,8 @@ def lib():
             L.stap_plan_get_tuning.argtypes = [vp, i32, ctypes.POINTER(i32)]
             L.stap_plan_set_tuning.argtypes = [vp, i32, ctypes.POINTER(i32)]
             L.stap_checked_build.argtypes = []
+            L.stap_plan_set_batch_schedule.argtypes = [vp, i32]
+            L.stap_plan_get_batch_schedule.argtypes = [vp, ctypes.POINTER(i32)]
             L.stap_check_report.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i32),
                                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
             L.stap_run_cpi_noalloc.argtypes = [ctypes.POINTER(stap_dims), ctypes.POINTER(stap_options),
@@ -252,6 +257,16 @@ def stap_plan_set_workspace(plan, workspace: torch.Tensor):
 
 def stap_plan_set_wait_limit(plan, max_polls: int):
     _check(lib().stap_plan_set_wait_limit(plan, int(max_polls)), "stap_plan_set_wait_limit")
+
+
+def stap_plan_set_batch_schedule(plan, schedule: int):
+    _check(lib().stap_plan_set_batch_schedule(plan, int(schedule)), "stap_plan_set_batch_schedule")
+
+
+def stap_plan_get_batch_schedule(plan) -> int:
+    v = ctypes.c_int32()
+    _check(lib().stap_plan_get_batch_schedule(plan, ctypes.byref(v)), "stap_plan_get_batch_schedule")
+    return v.value
 
 
 def stap_plan_set_stream(plan, stream=None):
@@ -595,9 +610,19 @@ class Plan:
             except (OSError, ValueError):
                 cache = {}
         keys = [self._tune_key(i) for i in range(len(self.dims))]
-        if not force and all(len(cache.get(k, ())) == STAP_TUNING_LEN for k in keys):
+        # a batch also keeps its schedule, keyed by all its CPI shapes
+        import hashlib
+        skey = None
+        if len(self.dims) > 1:
+            skey = "batch schedule prec%d %s" % (self.precision, hashlib.sha256(
+                "|".join(self._tune_key(i) + " R%d" % self.dims[i].n_range
+                         for i in range(len(self.dims))).encode()).hexdigest()[:16])
+        if not force and all(len(cache.get(k, ())) == STAP_TUNING_LEN for k in keys) and \
+                (skey is None or skey in cache):
             for i, k in enumerate(keys):
                 stap_plan_set_tuning(self.handle, i, cache[k])
+            if skey is not None:
+                stap_plan_set_batch_schedule(self.handle, int(cache[skey]))
             return {k: cache[k] for k in keys}
         if outs is None:
             outs = [torch.empty(self.shapes(i)["out"], dtype=torch.float32, device=self.device)
@@ -609,6 +634,8 @@ class Plan:
         result = {}
         for i, k in enumerate(keys):
             result[k] = cache[k] = stap_plan_get_tuning(self.handle, i)
+        if skey is not None:
+            cache[skey] = stap_plan_get_batch_schedule(self.handle)
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)
             tmp = path + ".tmp.%d" % os.getpid()
@@ -618,6 +645,10 @@ class Plan:
         except OSError:
             pass
         return result
+
+    def set_batch_schedule(self, schedule: int):
+        """STAP_BATCH_PERSISTENT or STAP_BATCH_STREAMS for a batch plan."""
+        stap_plan_set_batch_schedule(self.handle, schedule)
 
     def set_wait_limit(self, max_polls: int = STAP_DEFAULT_WAIT_POLLS):
         """Polls after which a tensor-core pipeline wait gives up (0: at once)."""

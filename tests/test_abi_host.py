@@ -320,3 +320,15 @@ def test_checked_build_loads_and_exports_the_same_symbols():
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
                        env=dict(os.environ, STAP_CHECKED="1"), timeout=900)
     assert r.returncode == 0 and "checked ok" in r.stdout, r.stdout + r.stderr
+
+
+def test_batch_schedule_values_without_cuda():
+    L = stap.lib()
+    arr = (stap.stap_dims * 2)(stap.stap_dims(*GOOD), stap.stap_dims(4, 64, 64, 1024, 2, 64, 8))
+    h = ctypes.c_void_p()
+    assert L.stap_plan_create(arr, 2, None, None, ctypes.byref(h), None) == 0
+    assert stap.stap_plan_get_batch_schedule(h) == stap.STAP_BATCH_PERSISTENT
+    assert L.stap_plan_set_batch_schedule(h, 2) == stap.STAP_ERR_INVALID_ARG
+    stap.stap_plan_set_batch_schedule(h, stap.STAP_BATCH_STREAMS)
+    assert stap.stap_plan_get_batch_schedule(h) == stap.STAP_BATCH_STREAMS
+    stap.stap_plan_destroy(h)

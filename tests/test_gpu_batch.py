@@ -33,7 +33,13 @@ def _uneven(n=12, seed=7):
     return out
 
 
-def test_batch_equals_single_cpi_runs_across_waves_and_replays():
+@pytest.mark.parametrize("schedule", [stap.STAP_BATCH_PERSISTENT, stap.STAP_BATCH_STREAMS],
+                         ids=["persistent", "streams"])
+def test_batch_equals_single_cpi_runs_across_waves_and_replays(schedule):
+    """Both batch schedules -- persistent launches per phase over all the
+    wave's CPIs, or each CPI's chain on a side stream -- give each CPI exactly
+    the output of its own one-CPI run, in one wave and in one wave per CPI,
+    on the captured launch and on graph replays."""
     specs = _uneven()
     cubes = [torch.from_numpy(synth.make_cube(s)).cuda() for s in specs]
     singles = []
@@ -44,6 +50,7 @@ def test_batch_equals_single_cpi_runs_across_waves_and_replays():
     full = stap.Plan([s.dims() for s in specs])                    # one wave
     tight = stap.Plan([s.dims() for s in specs], max_workspace_bytes=0)   # one CPI per wave
     for plan in (full, tight):
+        plan.set_batch_schedule(schedule)
         outs = plan.run_cpi(cubes)                                 # capture + launch
         again = plan.run_cpi(cubes, outs)                          # graph replay
         torch.cuda.synchronize()
@@ -132,3 +139,28 @@ def test_autotune_keeps_results_and_round_trips_through_the_cache(tmp_path):
     assert tuned.status() == (stap.STAP_OK, 0)
     for p in (base, tuned, again):
         p.close()
+
+
+@pytest.mark.parametrize("prec", [stap.STAP_PREC_FP32, stap.STAP_PREC_BF16X3], ids=["fp32", "bf16x3"])
+def test_persistent_batch_with_options_equals_single_runs(prec):
+    """Persistent batches with the launches that have no persistent form
+    mixed in (tensor-core kernels, neighbour training, the mixed-precision
+    refinement solve): still each CPI's own one-CPI output."""
+    specs = _uneven(6, seed=11)
+    cubes = [torch.from_numpy(synth.make_cube(s)).cuda() for s in specs]
+    for kw in ({}, {"training": stap.STAP_TRAIN_NEIGHBOURS},
+               {"solver": stap.STAP_SOLVE_MIXED_IR, "refine_steps": 2}):
+        singles = []
+        for s, c in zip(specs, cubes):
+            p = stap.Plan(s.dims(), precision=prec, **kw)
+            singles.append(p.run_cpi(c).clone())
+            p.close()
+        plan = stap.Plan([s.dims() for s in specs], precision=prec, **kw)
+        plan.set_batch_schedule(stap.STAP_BATCH_PERSISTENT)
+        outs = plan.run_cpi(cubes)
+        again = plan.run_cpi(cubes, outs)
+        torch.cuda.synchronize()
+        for o, ref in zip(again, singles):
+            assert torch.equal(o, ref), kw
+        assert plan.status() == (stap.STAP_OK, 0)
+        plan.close()
