@@ -1176,6 +1176,61 @@ __device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, lo
         big_solve<LR, RPL>(u, Lc, rd, D, li, grp);
       }
       for (int it = 0; it < refine_steps; ++it) {
+        if constexpr (F32F) {
+          // r = b - Rl u in double-float arithmetic (about 2^-48) on the FP32
+          // pipe: Rl read in FP64 from the input (the lower triangle, the
+          // conjugate above it by a sign flip) and split on the integer pipe,
+          // u split once per step and broadcast by shuffles; the load is
+          // applied after the sweep.  The FP64 pipe only splits the few values
+          // outside the fast split's range.
+          ff::F2 rre[RPL], rim[RPL];
+          float4 uf[RPL];
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            uf[q] = to_ff4(u[q]);
+            rre[q] = ff::from_double(b[q].x);
+            rim[q] = ff::from_double(b[q].y);
+          }
+#pragma unroll
+          for (int ql = 0; ql < RPL; ++ql) {
+            if (LR * ql >= D) break;
+#pragma unroll 2
+            for (int lo = 0; lo < LR; ++lo) {
+            const int l = LR * ql + lo;
+            if (l >= D) break;
+            const int src = grp * LR + lo;
+            const ff::F2 ur{__shfl_sync(0xffffffffu, uf[ql].x, src), __shfl_sync(0xffffffffu, uf[ql].y, src)};
+            const ff::F2 ui{__shfl_sync(0xffffffffu, uf[ql].z, src), __shfl_sync(0xffffffffu, uf[ql].w, src)};
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+              if (LR * q < D) {
+                const int i = li + LR * q;
+                const int ic = i < D ? i : D - 1;
+                const bool low = ic >= l;
+                const long long ao = low ? (long long)ic * D + l : (long long)l * D + ic;
+                const double2 a = in_bounds((long long)(A - cov) + ao, (long long)nsys * D * D, kSiteSolveIn)
+                                      ? __ldg(A + ao) : make_double2(0.0, 0.0);
+                const ff::F2 ar = ff::from_double(a.x);
+                ff::F2 ai = ic == l ? ff::F2{0.f, 0.f} : ff::from_double(a.y);
+                if (!low) ai = ff::F2{-ai.hi, -ai.lo};           // conj above the diagonal
+                const ff::F2 nar{-ar.hi, -ar.lo}, nai{-ai.hi, -ai.lo};
+                // r -= R[i][l] u_l:  re -= ar ur - ai ui,  im -= ar ui + ai ur
+                rre[q] = ff::fma(ff::fma(rre[q], nar, ur), ai, ui);
+                rim[q] = ff::fma(ff::fma(rim[q], nar, ui), nai, ur);
+              }
+            }
+            }
+          }
+          const ff::F2 nd = ff::from_double(-delta);
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            if (LR * q < D) {
+              rre[q] = ff::fma(rre[q], nd, ff::F2{uf[q].x, uf[q].y});
+              rim[q] = ff::fma(rim[q], nd, ff::F2{uf[q].z, uf[q].w});
+            }
+            xf[q] = make_float2(__fadd_rn(rre[q].hi, rre[q].lo), __fadd_rn(rim[q].hi, rim[q].lo));
+          }
+        } else {
         // r = b - R u - delta u  (R Hermitian: A[i][l] for i >= l, conj(A[l][i])
         // above, real diagonal; the load is applied after the sweep)
 #pragma unroll
@@ -1221,10 +1276,9 @@ __device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, lo
             r[q].y = fma(-delta, u[q].y, r[q].y);
           }
         }
+        }
         __syncwarp();
         if constexpr (F32F) {   // FP32 correction, added in FP64
-#pragma unroll
-          for (int q = 0; q < RPL; ++q) xf[q] = make_float2((float)r[q].x, (float)r[q].y);
           big_solve_f32<LR, RPL>(xf, Lc, rd, D, li, grp);
 #pragma unroll
           for (int q = 0; q < RPL; ++q) r[q] = make_double2(xf[q].x, xf[q].y);

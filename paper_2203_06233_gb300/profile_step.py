@@ -11,7 +11,8 @@ Builds the plan, takes the launch choices from the autotune cache (timing them
 on the device when the cache lacks the shape), warms up, and then runs
 ``--steps`` calls of ``stap_run_cpi`` between cudaProfilerStart and
 cudaProfilerStop, so that a profiler started with profiling off sees exactly
-the launches of those steps.  The paper_cube workloads run the subarray front
+the launches of those steps, and prints their mean time per step (CUDA
+events on the current stream; no L2 flush between the steps).  The paper_cube workloads run the subarray front
 end (1000 elements to 4 channels) before the chain in every step.  ``--slabs N`` overrides the tuned number of
 range slabs (1 = the plain four-launch chain).  The input is the workload's
 seeded synthetic cube, generated on the device.
@@ -85,15 +86,19 @@ def main(argv=None):
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.profiler.start()
+    t0.record()
     for _ in range(a.steps):
         step()
+    t1.record()
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
+    ms = t0.elapsed_time(t1) / max(a.steps, 1)
     code, failed = plan.status()
     plan.close()
     print(f"{a.workload} {a.precision} {a.solver} refine {refine}: dims {spec.dims()}, tuning {tuning}, "
-          f"slabs override {a.slabs}, {a.steps} steps, status {code} ({failed} failed)")
+          f"slabs override {a.slabs}, {a.steps} steps, {ms:.3f} ms per step, status {code} ({failed} failed)")
     if code != stap.STAP_OK:
         raise SystemExit(1)
 
