@@ -1,10 +1,17 @@
 """Benchmark of the STAP path on GB300: range-Doppler cells per second.
 
 One step = one whole CPI through ``stap_run_cpi`` (Doppler transform,
-covariance, FP64 loading/Cholesky/solve/refinement, apply) on the standard
-workload: C=4 channels, P=128 pulses, K=256 Doppler bins, R=4096 range cells,
-T=3 (D=12), B=64-cell training blocks, S=16 steering vectors, seeded synthetic
-cube (unit noise, 40 dB CNR clutter ridge, 8 targets).
+covariance, FP64 loading/LDL^H/solves/refinement, apply).  The headline is the
+large CPI (C=32 channels, P=512 pulses, K=512 Doppler bins, R=32768 range
+cells, T=4 so D=128, B=256-cell training blocks, S=64 steering vectors; a
+seeded synthetic 4.3 GB cube: unit noise, 40 dB CNR clutter ridge, 32
+targets) on the mixed path (FP16 per-block-scaled split products on the tensor
+cores for the covariance and the apply, FP64 solve), with the plain FP32 path
+timed on the same cube beside it.  The D = 64 CPI, the standard D = 12 CPI and
+the 512-CPI batch are keys of the same line, each with its mixed and plain
+legs; every single-CPI workload also runs the mixed-precision refinement
+solve, and the standard CPI runs the training and snapshot options.  Errors
+against the FP64 oracle on seeded range blocks accompany every leg.
 
 Timing: inputs resident in HBM, L2 flushed (256 MiB write) between timed steps,
 each step bracketed by CUDA events on the launching stream; barrier and
@@ -218,6 +225,8 @@ PREC_TEXT = {
        "cores for covariance and apply, FP32 accumulation; FP32 FFT",
 }
 SOLVE_TEXT = "FP64 diagonal load, LDL^H factorisation and substitutions, 1 refinement step"
+MIR_TEXT = ("mixed-precision refinement solve: FP64 diagonal load, FP32 LDL^H and substitutions, "
+            "2 refinement steps with double-float residuals (STAP_SOLVE_MIXED_IR)")
 
 
 def log(msg):
@@ -269,8 +278,10 @@ def block_errors(outs_blocks, refs):
     return {"normwise": (num / den) ** 0.5, "max_cell": worst, "blocks": len(refs)}
 
 
-def kernel_figures(spec, prec, kt, pk, refine=1):
+def kernel_figures(spec, prec, kt, pk, refine=1, solver=0):
     """Each step against its own bound: achieved rate and fraction."""
+    if not kt:
+        return {}
     C, P, K, R, T, B, S = spec.dims()
     D, NB = C * T, R // B
     dop_bytes = 8.0 * C * R * (P + K)
@@ -283,6 +294,11 @@ def kernel_figures(spec, prec, kt, pk, refine=1):
                   "achieved_tflops": sf / kt["solve"] / 1e9,
                   "frac": sf / kt["solve"] / 1e9 / pk["fp64_tflops"]},
     }
+    if solver == 1:   # FP32 factor and substitutions, double-float residuals: no FP64 roofline
+        out["solve"] = {"ms": kt["solve"], "bound": "fp32 issue",
+                        "fp64_equivalent_tflops": sf / kt["solve"] / 1e9,
+                        "note": "FP64-solve flop count over this solve's time, for comparison with "
+                                "the FP64 solve; the kernel itself runs on the FP32 and integer pipes"}
     # covariance through the step call (full Hermitian c128 output)
     cov_bytes = 8.0 * C * K * R + 16.0 * K * NB * D * D
     apply_bytes = 8.0 * C * K * R + 8.0 * K * NB * S * D + 4.0 * S * K * R
@@ -322,15 +338,17 @@ def kernel_figures(spec, prec, kt, pk, refine=1):
 
 
 def run_leg(spec, cube, dev, prec, args, flush, stream, kernel_reps, timed=None, barrier=None,
-            solver=0, refine=1):
-    """One path on the workload's cube: plan, autotune (untimed), warm-up,
-    args.steps timed steps (after `barrier()` and inside `timed`, a context
-    manager, if given), per-step kernel times; returns (plan, out, leg dict)."""
+            solver=0, refine=1, opts=None, label=None):
+    """One path on the workload's cube: plan (with the plan options `opts`),
+    autotune (untimed), warm-up, args.steps timed steps (after `barrier()` and
+    inside `timed`, a context manager, if given), per-step kernel times;
+    returns (plan, out, leg dict)."""
     import contextlib
     import torch
     from paper_2203_06233_gb300 import stap
     C, P, K, R, T, B, S = spec.dims()
-    plan = stap.Plan(spec.dims(), device=dev, precision=prec, solver=solver, refine_steps=refine)
+    plan = stap.Plan(spec.dims(), device=dev, precision=prec, solver=solver, refine_steps=refine,
+                     **(opts or {}))
     out = torch.empty((S, K, R), dtype=torch.float32, device=dev)
     t0 = time.perf_counter()
     tuning = plan.autotune(cube, out, reps=1 if K * R * C * T > (1 << 26) else 3)
@@ -358,23 +376,28 @@ def run_leg(spec, cube, dev, prec, args, flush, stream, kernel_reps, timed=None,
     if code != stap.STAP_OK:
         raise RuntimeError(f"{PREC_NAMES[prec]}: device status {code} ({failed} failed systems)")
     # per-kernel times through the step-by-step calls (same launch choices)
-    dop = plan.doppler(cube)
-    cov = plan.covariance(dop)
-    wts = plan.solve_weights(cov)
-    kt = {
-        "doppler": statistics.mean(time_steps(lambda: plan.doppler(cube, dop), kernel_reps, flush, stream)),
-        "covariance": statistics.mean(time_steps(lambda: plan.covariance(dop, cov), kernel_reps, flush, stream)),
-        "solve": statistics.mean(time_steps(lambda: plan.solve_weights(cov, wts), kernel_reps, flush, stream)),
-        "apply": statistics.mean(time_steps(lambda: plan.apply(dop, wts, out), kernel_reps, flush, stream)),
-    }
-    plan.run_cpi(cube, out)   # the run's own output again (the apply call above rewrote it)
-    del dop, cov, wts
+    kt = {}
+    if not opts:   # the training options add a step between covariance and solve
+        dop = plan.doppler(cube)
+        cov = plan.covariance(dop)
+        wts = plan.solve_weights(cov)
+        kt = {
+            "doppler": statistics.mean(time_steps(lambda: plan.doppler(cube, dop), kernel_reps, flush, stream)),
+            "covariance": statistics.mean(time_steps(lambda: plan.covariance(dop, cov), kernel_reps, flush,
+                                                     stream)),
+            "solve": statistics.mean(time_steps(lambda: plan.solve_weights(cov, wts), kernel_reps, flush,
+                                                stream)),
+            "apply": statistics.mean(time_steps(lambda: plan.apply(dop, wts, out), kernel_reps, flush, stream)),
+        }
+        plan.run_cpi(cube, out)   # the run's own output again (the apply call above rewrote it)
+        del dop, cov, wts
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     (choices,) = tuning.values()
-    log(f"{spec.dims()} {PREC_NAMES[prec]}: {sum(times) / args.steps:.3f} ms/step, autotune {tune_s:.1f} s, "
-        f"kernels {kt}")
-    leg = {"precision": PREC_NAMES[prec], "arithmetic": PREC_TEXT[prec] + "; " + SOLVE_TEXT,
+    log(f"{spec.dims()} {label or PREC_NAMES[prec]}: {sum(times) / args.steps:.3f} ms/step, "
+        f"autotune {tune_s:.1f} s, kernels {kt}")
+    leg = {"precision": PREC_NAMES[prec],
+           "arithmetic": PREC_TEXT[prec] + "; " + (MIR_TEXT if solver == 1 else SOLVE_TEXT),
            "ms_per_step": sum(times) / args.steps, "step_ms": times, "tuning": tuning,
            "autotune_s": tune_s, "kernels_ms": kt,
            "kernels_used": {"covariance": "FP32 error-free" if prec == 0 or choices[8] == 1 else "tensor cores",
@@ -438,23 +461,36 @@ def run_gpu(args):
                 dist.barrier()
             torch.cuda.synchronize()
 
-        for prec in (mprec, 0):
-            keep = head and prec == mprec          # the headline leg: timed with clocks, kept for e2e
-            plan, out, leg = run_leg(spec, cube, dev, prec, sub, flush, stream, kernel_reps,
-                                     timed=clk if keep else None, barrier=barrier if keep else None)
-            outs_blocks[prec] = {b: out[:, :, b * B:(b + 1) * B].cpu().numpy() for b in blocks}
-            legs[prec] = leg
+        mlabel, flabel, ilabel = PREC_NAMES[mprec], PREC_NAMES[0], PREC_NAMES[mprec] + "+mixed_ir"
+        short = argparse.Namespace(steps=max(3, min(args.steps, 5)), warmup=args.warmup)
+        for label, prec, solver, refine in ((mlabel, mprec, 0, 1), (flabel, 0, 0, 1), (ilabel, mprec, 1, 2)):
+            keep = head and label == mlabel        # the headline leg: timed with clocks, kept for e2e
+            if label == ilabel and (world > 1 or args.only_headline):
+                continue
+            try:
+                plan, out, leg = run_leg(spec, cube, dev, prec, sub if label != ilabel else short, flush,
+                                         stream, kernel_reps, timed=clk if keep else None,
+                                         barrier=barrier if keep else None, solver=solver, refine=refine,
+                                         label=label)
+            except Exception as exc:
+                if label != ilabel:
+                    raise
+                log(f"{label}: {type(exc).__name__}: {exc}")   # a side leg must not lose the line
+                torch.cuda.empty_cache()
+                continue
+            outs_blocks[label] = {b: out[:, :, b * B:(b + 1) * B].cpu().numpy() for b in blocks}
+            legs[label] = leg
             if keep:
                 mplan, mout = plan, out
             else:
                 plan.close()
                 del plan, out
                 torch.cuda.empty_cache()
-        mleg, fleg = legs[mprec], legs[0]
+        mleg, fleg = legs[mlabel], legs[flabel]
         errors, cpu = {}, None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             refs, cpu = oracle_on_blocks(spec, cube_h, blocks)
-            errors = {PREC_NAMES[p]: block_errors(outs_blocks[p], refs) for p in outs_blocks}
+            errors = {lb: block_errors(outs_blocks[lb], refs) for lb in outs_blocks}
         mvalue = world * cells / (mleg["ms_per_step"] * 1e-3)
         fvalue = world * cells / (fleg["ms_per_step"] * 1e-3)
         # ---- headline: the mixed leg's timed region ----
@@ -518,6 +554,10 @@ def run_gpu(args):
             "roofline": roofline,
             "clocks": clk.summary(),
         }
+        if ilabel in legs:
+            ileg = legs[ilabel]
+            line["mixed_ir"] = dict(ileg, value=world * cells / (ileg["ms_per_step"] * 1e-3),
+                                    kernels=kernel_figures(spec, mprec, ileg["kernels_ms"], pk, solver=1))
         if errors:
             line["errors_vs_oracle"] = errors
         if cpu is not None:
@@ -541,7 +581,9 @@ def run_gpu(args):
 
 def workload_keys(args, name, rank, dev, stream, flush, pk):
     """Another single-CPI workload as a key of the line: its mixed and FP32
-    legs (a few timed steps each) and their errors on sampled blocks."""
+    legs and the mixed leg with the mixed-precision refinement solve (a few
+    timed steps each), their errors on sampled blocks, and on the standard CPI
+    the option legs."""
     import torch
     from paper_2203_06233_gb300 import synth
     spec = workload_spec(rank, name)
@@ -555,24 +597,76 @@ def workload_keys(args, name, rank, dev, stream, flush, pk):
     blocks = sample_blocks(spec, 4)
     sub = argparse.Namespace(steps=max(3, min(args.steps, 10)), warmup=args.warmup)
     legs, outs_blocks = {}, {}
-    for prec in (mprec, 0):
-        plan, out, leg = run_leg(spec, cube, dev, prec, sub, flush, stream, kernel_reps)
-        outs_blocks[prec] = {b: out[:, :, b * B:(b + 1) * B].cpu().numpy() for b in blocks}
-        legs[prec] = leg
+    mlabel, flabel, ilabel = PREC_NAMES[mprec], PREC_NAMES[0], PREC_NAMES[mprec] + "+mixed_ir"
+    for label, prec, solver, refine in ((mlabel, mprec, 0, 1), (flabel, 0, 0, 1), (ilabel, mprec, 1, 2)):
+        plan, out, leg = run_leg(spec, cube, dev, prec, sub, flush, stream, kernel_reps, solver=solver,
+                                 refine=refine, label=label)
+        outs_blocks[label] = {b: out[:, :, b * B:(b + 1) * B].cpu().numpy() for b in blocks}
+        legs[label] = leg
         plan.close()
         del plan, out
         torch.cuda.empty_cache()
     errors, cpu = {}, None
     if not args.no_cpu_baseline:
         refs, cpu = oracle_on_blocks(spec, cube_h, blocks)
-        errors = {PREC_NAMES[p]: block_errors(outs_blocks[p], refs) for p in outs_blocks}
-    mvalue = cells / (legs[mprec]["ms_per_step"] * 1e-3)
-    fvalue = cells / (legs[0]["ms_per_step"] * 1e-3)
-    return {"config": workload_config(spec, name),
-            "mixed": dict(legs[mprec], value=mvalue,
-                          kernels=kernel_figures(spec, mprec, legs[mprec]["kernels_ms"], pk)),
-            "fp32": dict(legs[0], value=fvalue, kernels=kernel_figures(spec, 0, legs[0]["kernels_ms"], pk)),
-            "mixed_vs_fp32": mvalue / fvalue, "errors_vs_oracle": errors, "cpu_baseline": cpu}
+        errors = {lb: block_errors(outs_blocks[lb], refs) for lb in outs_blocks}
+    value = {lb: cells / (legs[lb]["ms_per_step"] * 1e-3) for lb in legs}
+    res = {"config": workload_config(spec, name),
+           "mixed": dict(legs[mlabel], value=value[mlabel],
+                         kernels=kernel_figures(spec, mprec, legs[mlabel]["kernels_ms"], pk)),
+           "fp32": dict(legs[flabel], value=value[flabel],
+                        kernels=kernel_figures(spec, 0, legs[flabel]["kernels_ms"], pk)),
+           "mixed_ir": dict(legs[ilabel], value=value[ilabel],
+                            kernels=kernel_figures(spec, mprec, legs[ilabel]["kernels_ms"], pk, solver=1)),
+           "mixed_vs_fp32": value[mlabel] / value[flabel], "errors_vs_oracle": errors,
+           "cpu_baseline": cpu}
+    if name == "standard":
+        res["options"] = option_legs(args, spec, cube, cube_h, dev, stream, flush, kernel_reps)
+    return res
+
+
+def option_legs(args, spec, cube, cube_h, dev, stream, flush, kernel_reps):
+    """The plain path with each snapshot and training option on the standard
+    CPI's cube: PRI-staggered snapshots, neighbour-block training, and a
+    sliding training window over groups of 8 cells (1 guard group and 8
+    training groups on each side); errors against the oracle run with the same
+    option on seeded 64-cell range windows."""
+    import torch
+    from paper_2203_06233_gb300 import stap
+    C, P, K, R, T, B, S = spec.dims()
+    cells = K * R
+    sub = argparse.Namespace(steps=max(3, min(args.steps, 10)), warmup=args.warmup)
+    wspec = dataclasses.replace(spec, training_block=8)
+    cases = [
+        ("staggered", spec, dict(snapshots=stap.STAP_SNAP_PRI_STAGGERED), dict(staggered=True),
+         "PRI-staggered snapshots: T sub-windows of P - T + 1 pulses"),
+        ("neighbour_training", spec, dict(training=stap.STAP_TRAIN_NEIGHBOURS), dict(training=1),
+         "block b trained on blocks b - 1 and b + 1"),
+        ("window_training", wspec, dict(training=stap.STAP_TRAIN_WINDOW, train_guard=1, train_half=8),
+         dict(training=2, guard=1, half=8),
+         "groups of 8 cells, each trained on 8 groups on each side beyond 1 guard group"),
+    ]
+    rng = np.random.default_rng(77)
+    windows = sorted(int(w) for w in rng.choice(R // 64, 4, replace=False))
+    res = {}
+    for key, sp, kw, okw, text in cases:
+        try:
+            plan, out, leg = run_leg(sp, cube, dev, 0, sub, flush, stream, kernel_reps, opts=kw, label=key)
+            got = {w: out[:, :, w * 64:(w + 1) * 64].cpu().numpy() for w in windows}
+            plan.close()
+            del plan, out
+            torch.cuda.empty_cache()
+            entry = dict(leg, option=text, value=cells / (leg["ms_per_step"] * 1e-3))
+            if not args.no_cpu_baseline:
+                import oracle
+                d = oracle.Dims(*sp.dims())
+                refs = {w: oracle.run(d, cube_h, r0=w * 64, nr=64, **okw)["out"] for w in windows}
+                entry["errors_vs_oracle"] = block_errors(got, refs)
+            res[key] = entry
+        except Exception as exc:   # an option leg must not lose the line
+            log(f"{key}: {type(exc).__name__}: {exc}")
+            res[key] = {"error": f"{type(exc).__name__}: {exc}"[:400]}
+    return res
 
 
 DTYPE = {0: "f32+f64", 1: "bf16x3+f32+f64", 2: "tf32x3+f32+f64", 3: "f16x2+f32+f64"}

@@ -426,9 +426,11 @@ stap_status stap_run_cpi_noalloc(const stap_dims* dims, const stap_options* opt,
  * warps per CTA of the D <= 32 solve, lanes per right-hand side of the larger
  * solve, and for D = 8, 12 or 16 the register-resident or the shared-memory
  * solve kernel; register-resident or general FP32 apply; for a one-CPI plan, 1, 2, 3,
- * 4, 6 or 8 pipelined range slabs of the whole run; for STAP_PREC_TF32X3 plans,
- * the tensor-core or the FP32 covariance and apply (the FP32 kernels are
- * the more accurate, and at small D the faster).  Every candidate computes
+ * 4, 6 or 8 pipelined range slabs of the whole run; for the mixed precisions
+ * (STAP_PREC_BF16X3, STAP_PREC_TF32X3, STAP_PREC_FP16_SCALED), the tensor-core
+ * or the FP32 covariance and apply (the FP32 kernels are the more accurate,
+ * and at small D the faster); for a batch, the persistent or the stream
+ * schedule (stap_plan_set_batch_schedule).  Every candidate computes
  * the same result except that the apply kernels sum in different orders and
  * that a mixed-precision plan's FP32 choices are more accurate than its
  * tensor-core ones.  Needs the run workspace; synchronises the plan's stream; overwrites

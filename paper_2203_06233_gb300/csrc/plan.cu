@@ -1077,6 +1077,7 @@ stap_status stap_apply(stap_plan p, const void* dop, const void* wts, float* out
 }
 
 stap_status stap_run_cpi(stap_plan p, const void* const* cubes, float* const* outs) {
+  NvtxRange range("stap_run_cpi");
   if (!p || !cubes || !outs) return STAP_ERR_INVALID_ARG;
   for (size_t i = 0; i < p->cpis.size(); ++i) {
     if (!cubes[i] || !outs[i]) return STAP_ERR_INVALID_ARG;

@@ -95,6 +95,22 @@ def lib_path() -> str:
     return _build.LIB_CHECKED if checked_requested() else _build.LIB
 
 
+_lib_tag = None
+
+
+def lib_tag() -> str:
+    """A short hash of the loaded library file: autotune cache entries are
+    keyed by it, so a rebuilt library re-tunes instead of reusing choices
+    timed on other kernels."""
+    global _lib_tag
+    if _lib_tag is None:
+        import hashlib
+        lib()
+        with open(lib_path(), "rb") as f:
+            _lib_tag = hashlib.sha256(f.read()).hexdigest()[:12]
+    return _lib_tag
+
+
 def lib():
     """Load libstap.so, or libstap_checked.so with STAP_CHECKED=1 (building it
     first if it is missing or stale)."""
@@ -590,6 +606,7 @@ class Plan:
             key += " snap%d" % self.snapshots
         if self.training == STAP_TRAIN_WINDOW:
             key += " guard%d half%d" % (self.train_guard, self.train_half)
+        key += " lib" + lib_tag()
         # a one-CPI plan also tunes its range slabs, which depend on R
         return key + (" R%d" % d.n_range if len(self.dims) == 1 else " batch")
 
