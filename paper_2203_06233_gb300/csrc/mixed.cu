@@ -212,18 +212,28 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
     if (PREC == kFP16S && tid < G) smax[tid] = 0;
     __syncthreads();
     if constexpr (PREC == kFP16S) {   // each system's largest |re|, |im| over its B cells
-      for (int p = warp; p < GD; p += kThreads / 32) {
-        const long long base = rowbase[p];
-        float m = 0.f;
-        if (base >= 0) {
-#pragma unroll 8
-          for (int j = lane; j < B; j += 32) {
-            const float2 x = __ldg(dop + base + j);
-            m = fmaxf(m, fmaxf(fabsf(x.x), fabsf(x.y)));
+      // two rows per warp and pass, so that both rows' loads are in flight together
+      for (int p0 = warp; p0 < GD; p0 += 2 * (kThreads / 32)) {
+        const int p1 = p0 + kThreads / 32;
+        const long long base0 = rowbase[p0], base1 = p1 < GD ? rowbase[p1] : -1;
+        float m0 = 0.f, m1 = 0.f;
+#pragma unroll 4
+        for (int j = lane; j < B; j += 32) {
+          if (base0 >= 0) {
+            const float2 x = __ldg(dop + base0 + j);
+            m0 = fmaxf(m0, fmaxf(fabsf(x.x), fabsf(x.y)));
+          }
+          if (base1 >= 0) {
+            const float2 x = __ldg(dop + base1 + j);
+            m1 = fmaxf(m1, fmaxf(fabsf(x.x), fabsf(x.y)));
           }
         }
-        m = warp_max(m);
-        if (lane == 0) atomicMax(&smax[p / D8], __float_as_int(m));   // m >= 0: int order
+        m0 = warp_max(m0);
+        m1 = warp_max(m1);
+        if (lane == 0) {   // m >= 0: int order
+          atomicMax(&smax[p0 / D8], __float_as_int(m0));
+          if (p1 < GD) atomicMax(&smax[p1 / D8], __float_as_int(m1));
+        }
       }
       __syncthreads();
       if (tid < G) sscale[tid] = block_scale(__int_as_float(smax[tid]));
@@ -356,6 +366,9 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
       const uint32_t lb = (uint32_t)(q4 * 32) << 16;
       for (int gg = gw0; gg <= gw1; ++gg) {
         for (int cb = hf * 8; cb < D8; cb += 16) {   // warp-uniform bounds
+          // one system per tile: a block of columns left of the warp's first
+          // row has no l >= a entry
+          if (G == 1 && cb + 8 <= q4 * 32) continue;
           float rr[8], ri[8], ir[8], ii[8];
           in_bounds(256 + GD + gg * D8 + cb + 7, 512, kSiteTcTmem);   // recorded only
           tc::tmem_ld8(tmem + lb + gg * D8 + cb, rr);
@@ -407,7 +420,7 @@ template <int PREC>
 constexpr size_t apply_smem(int NP) { return 2 * (size_t)Fmt<PREC>::NPC * (kAppA + (size_t)NP * kAppRB); }
 
 template <int PREC>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)   // two CTAs per SM (TMEM <= 256 columns each)
 apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
                  float* __restrict__ out, int C, int K, int R, int ldr, int T, int B, int S, int NB,
                  int NP, int tmem_cols, long long ntiles, DeviceStatus* __restrict__ status,
@@ -424,6 +437,7 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
   __shared__ long long colbase[128];          // dop offset of snapshot entry d's row
   __shared__ long long wbase[256];            // wts offset of weight row n (vector n/2), or -1
   __shared__ float wsc[128];                  // per weight vector scale (FP16S)
+  __shared__ float winv[128];                 // its inverse times the tile's (exact: powers of two)
   __shared__ float xsc_s;
   __shared__ int xmax;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -467,12 +481,15 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
     __syncthreads();
     if constexpr (PREC == kFP16S) {   // the tile's largest |x| component, each vector's largest |w|
       float m = 0.f;
-      for (int d = warp; d < D; d += kThreads / 32)
-        for (int mm = lane; mm < 128; mm += 32)
-          if (r0 + mm < R) {
-            const float2 v = __ldg(dop + colbase[d] + r0 + mm);
-            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
-          }
+      const int rn = min(128, R - r0);
+#pragma unroll 8
+      for (int e = tid; e < D * 128; e += kThreads) {   // entry d = e / 128 of cell e % 128
+        const int d = e >> 7, mm = e & 127;
+        if (mm < rn) {
+          const float2 v = __ldg(dop + colbase[d] + r0 + mm);
+          m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+      }
       m = warp_max(m);
       if (lane == 0) atomicMax(&xmax, __float_as_int(m));
       for (int q = warp; q < Nq; q += kThreads / 32) {
@@ -487,7 +504,9 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
         if (lane == 0) wsc[q] = block_scale(mw);
       }
       __syncthreads();
-      if (tid == 0) xsc_s = block_scale(__int_as_float(xmax));
+      const float xs = block_scale(__int_as_float(xmax));
+      if (tid == 0) xsc_s = xs;
+      if (tid < Nq) winv[tid] = 1.f / (wsc[tid] * xs);   // powers of two: exact
       __syncthreads();
     }
     // K elements kap0 .. kap0 + KC - 1 of the A rows (cells) and of the B
@@ -628,9 +647,9 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
               if (cb + u >= c_lo && s < S) {
                 float re = a[u], im = a[u + 1];
                 if constexpr (PREC == kFP16S) {
-                  const float inv = 1.f / wsc[jj * S + s], invx = 1.f / xsc_s;   // exact
-                  re = re * inv * invx;
-                  im = im * inv * invx;
+                  const float inv = winv[jj * S + s];
+                  re *= inv;
+                  im *= inv;
                 }
                 if (in_bounds(((long long)s * K + k) * ldr + r, ((long long)S * K - 1) * ldr + R, kSiteTcOut))
                   out[((size_t)s * K + k) * ldr + r] = fmaf(re, re, im * im);

@@ -1359,6 +1359,9 @@ stap_status stap_plan_autotune(stap_plan p, const void* const* cubes, float* con
       if (c.D <= 64) lrs.insert(lrs.begin(), 8);
       pick([](stap::Tune& t, int v) { t.solve_lr = v; }, lrs,
            [&] { return do_solve(p, c, cov, wts, p->stream); });
+      if (c.D > 64 && p->opt.solver == STAP_SOLVE_FP64 && c.tune.solve_lr == 32)   // 8 or 16 warps
+        pick([](stap::Tune& t, int v) { t.solve_nw = v; }, {0, 16},
+             [&] { return do_solve(p, c, cov, wts, p->stream); });
     }
     if ((st = do_solve(p, c, cov, wts, p->stream)) != STAP_OK) break;
     if (stap::tc_precision(p->opt.precision) && stap::apply_tc_supported(d.training_block, d.n_steering))

@@ -104,6 +104,22 @@ __device__ __forceinline__ void step_lower(int& i, int& l, int step) {
   }
 }
 
+// 1/d for a positive, finite, normal d: Newton-Raphson iteration for the
+// reciprocal, r <- r + r (1 - d r), whose relative error squares at each step
+// (Muller et al., Handbook of Floating-Point Arithmetic, 2nd ed., sec. 4.7),
+// started from the hardware's approximate reciprocal; three steps take any
+// start error below 2^-8 under FP64's unit roundoff.  The chain of dependent
+// FP64 operations is shorter than a full IEEE division's, and in the
+// one-system-per-CTA factorisation it sits between two barriers, where each
+// of its operations waits behind the other warps' DFMAs in the FP64 pipe.
+__device__ __forceinline__ double recip_newton(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r = fma(r, fma(-d, r, 1.0), r);
+  return r;
+}
+
 // (re, im) as the double-floats (re_hi, re_lo, im_hi, im_lo); the split runs
 // on the integer pipe, off the FP64 pipe that the FP64 solve kernels are bound by
 __device__ __forceinline__ float4 to_ff4(double2 u) {
@@ -1001,12 +1017,18 @@ __device__ __forceinline__ void big_solve_f32(float2 (&x)[RPL], const float2* __
   big_subst_f32<LR, RPL, true>(x, Lc, D, li, grp);
 }
 
-// F32F: the refinement option's form for D > 64 (where the double-float
-// matrix of solve_big_mir_kernel does not fit in shared memory): the factor
-// and the substitutions in FP32, the solution in FP64, each refinement step's
-// residual in FP64 from the input as below, its FP32 correction added in FP64.
-// 256-thread CTAs hold a D > 64 system's factor (one CTA per SM), so they may
-// use the whole register file; 128-thread CTAs run three per SM.
+// F32F: the refinement option's form for D > 64 (where solve_big_mir_kernel's
+// layout, with the broadcast area and the basis solutions beside the
+// double-float matrix, does not fit in shared memory): the factor and the
+// substitutions in FP32, the solution in FP64, each refinement step's
+// residual in double-float from a double-float copy of Rl kept in shared
+// memory where the FP64 kernel keeps the basis solutions, its FP32
+// correction added in FP64.  With separable steering the basis solutions are
+// parked in the system's own weight rows (which hold S D >= 2 C D floats)
+// until every right-hand side is done, then copied over the matrix copy for
+// the combination.  256-thread CTAs hold a D > 64 system's factor (one CTA
+// per SM), so they may use the whole register file; 128-thread CTAs run
+// three per SM.
 template <bool SEP, int LR, int NT, int RPL, bool F32F>
 __device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, long long bx, long long gx) {
   const double2* __restrict__ cov = prm.cov;
@@ -1028,13 +1050,17 @@ __device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, lo
   constexpr int NW = NT / 32;
   constexpr int NG = NT / LR;                      // right-hand sides in flight per CTA
   const int Dp = D * (D + 1) / 2;
-  // Lu [Dp] (column-major packed) and the pivot column before division [D];
+  // Lu [Dp] (column-major packed) and the two pivot columns before division [2][D];
   // from the next 16-byte boundary the SEP basis solutions [C][D]
-  // (double-float), the pivot reciprocals [D] and the pivot flag
+  // (double-float) -- F32F: the loaded Rl [Dp] (double-float, column-major
+  // packed), which the basis solutions overwrite for the combination -- the
+  // pivot reciprocals [D] and the pivot flag
   LT* Lc = reinterpret_cast<LT*>(sm);
-  LT* colb = Lc + Dp;
-  float4* Ubf = reinterpret_cast<float4*>(sm) + ((size_t)(Dp + D) * sizeof(LT) + 15) / 16;
-  RT* rd = reinterpret_cast<RT*>(Ubf + (SEP ? (size_t)C * D : 0));
+  LT* colb = Lc + Dp;                              // columns j and j+1 before division
+  LT* colb2 = colb + D;
+  float4* Ubf = reinterpret_cast<float4*>(sm) + ((size_t)(Dp + 2 * D) * sizeof(LT) + 15) / 16;
+  float4* Adf = Ubf;
+  RT* rd = reinterpret_cast<RT*>(Ubf + (F32F ? (size_t)Dp : (SEP ? (size_t)C * D : 0)));
   int* okf = reinterpret_cast<int*>(rd + D);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int li = lane % LR, grp = lane / LR;         // lane in group, group in warp
@@ -1047,7 +1073,8 @@ __device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, lo
       *okf = 0;
       return RT(1);  // keep going; this system's weights become zero
     }
-    return RT(1) / d;
+    if constexpr (F32F) return RT(1) / d;
+    else return recip_newton(d);
   };
 
   for (long long sys = bx; sys < nsys; sys += gx) {
@@ -1059,56 +1086,108 @@ __device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, lo
       for (int l = lane; l <= i; l += 32) {
         const double2 a = loaded(A, D, i, l, delta);
         Lc[colstart(l, D) + i - l] = LT{(RT)a.x, (RT)a.y};
+        if constexpr (F32F) Adf[colstart(l, D) + i - l] = to_ff4_cvt(a);
       }
-    if (tid == 0) {
-      *okf = 1;
-      rd[0] = pivot((RT)(__ldg(&A[0].x) + delta));
-    }
+    if (tid == 0) *okf = 1;
     __syncthreads();
 
-    for (int j = 0; j < D; ++j) {
+    // Right-looking Lu Dg Lu^H, two columns per round (two barriers per two
+    // columns instead of four).  Phase 1: the thread of row i > j scales
+    // column j (l_ij = a_ij / d_j), brings column j+1 up to date with it and
+    // scales that too; every thread forms d_j, d_{j+1} and their reciprocals
+    // itself from the same shared values and with the same operations (so
+    // with the same bits), which keeps the reciprocals off the path between
+    // the barriers.  l_{j+1,j} is read by every thread in phase 1, so its
+    // owner stores it only in phase 2.  Phase 2: the rank-2 update of the
+    // trailing triangle (columns >= j+2).
+    for (int j = 0; j < D; j += 2) {
       const int cj = colstart(j, D);
-      const RT rj = rd[j];
-      for (int i = j + 1 + tid; i < D; i += NT) {
+      const int j1 = j + 1;
+      const bool pair = j1 < D;
+      const int c1 = pair ? colstart(j1, D) : cj;
+      // only threads with a row in phase 1 (and thread 0, which stores the
+      // reciprocals) need them: FP64 work costs per warp instruction
+      const bool rows = j1 + tid < D || tid == 0;
+      const RT rj = rows ? pivot(Lc[cj].x) : RT(1);
+      LT a1j{RT(0), RT(0)};
+      RT r1 = RT(1);
+      if (pair && rows) {
+        a1j = Lc[cj + 1];                                    // a_{j+1,j}
+        const LT l1j{a1j.x * rj, a1j.y * rj};
+        RT d1 = Lc[c1].x;
+        d1 = fma(-l1j.x, a1j.x, d1);
+        d1 = fma(-l1j.y, a1j.y, d1);
+        r1 = pivot(d1);
+      }
+      LT l1j_own{RT(0), RT(0)};
+      bool own1 = false;
+      for (int i = j1 + tid; i < D; i += NT) {
         const LT v = Lc[cj + i - j];
         colb[i] = v;
-        Lc[cj + i - j] = LT{v.x * rj, v.y * rj};
+        const LT lij{v.x * rj, v.y * rj};
+        if (i == j1) {
+          l1j_own = lij;
+          own1 = true;
+        } else {
+          Lc[cj + i - j] = lij;
+          // a_{i,j+1} -= l_ij conj(a_{j+1,j}); then l_{i,j+1} = a_{i,j+1} / d_{j+1}
+          LT w = Lc[c1 + i - j1];
+          w.x = fma(-lij.x, a1j.x, w.x);
+          w.y = fma(-lij.y, a1j.x, w.y);
+          w.x = fma(-lij.y, a1j.y, w.x);
+          w.y = fma(lij.x, a1j.y, w.y);
+          colb2[i] = w;
+          Lc[c1 + i - j1] = LT{w.x * r1, w.y * r1};
+        }
+      }
+      if (tid == 0) {
+        rd[j] = rj;
+        if (pair) rd[j1] = r1;
       }
       __syncthreads();
-      // trailing update, pairs (i, l) with j < l <= i, column-major order:
+      if (own1) Lc[cj + 1] = l1j_own;
+      // rank-2 update, pairs (i, l) with j+1 < l <= i, column-major order:
       // column a of the trailing triangle holds m - a entries; a thread steps
       // through its entries (a, off) NT at a time, two per iteration (they
-      // only read column j and colb, which this loop does not write).  Entry
-      // (j+1, j+1) is thread 0's first: it then forms the next pivot's
-      // reciprocal.
-      const int m = D - j - 1;
-      const int np = m * (m + 1) / 2;
-      int a = 0, off = tid;
-      while (a < m && off >= m - a) off -= m - a++;
-      for (int q = tid; q < np; q += 2 * NT) {
-        int a2 = a, off2 = off + NT;
-        while (a2 < m && off2 >= m - a2) off2 -= m - a2++;
-        const bool two = q + NT < np;
-        const int l = j + 1 + a, i = l + off;
-        const int l2 = two ? j + 1 + a2 : l, i2 = two ? l2 + off2 : i;
-        const LT lij = Lc[cj + i - j], alj = colb[l];
-        const LT lij2 = Lc[cj + i2 - j], alj2 = colb[l2];
-        LT acc = Lc[colstart(l, D) + i - l], acc2 = Lc[colstart(l2, D) + i2 - l2];
-        // acc -= lij * conj(alj)
-        acc.x = fma(-lij.x, alj.x, acc.x);
-        acc2.x = fma(-lij2.x, alj2.x, acc2.x);
-        acc.y = fma(-lij.y, alj.x, acc.y);
-        acc2.y = fma(-lij2.y, alj2.x, acc2.y);
-        acc.x = fma(-lij.y, alj.y, acc.x);
-        acc2.x = fma(-lij2.y, alj2.y, acc2.x);
-        acc.y = fma(lij.x, alj.y, acc.y);
-        acc2.y = fma(lij2.x, alj2.y, acc2.y);
-        Lc[colstart(l, D) + i - l] = acc;
-        if (two) Lc[colstart(l2, D) + i2 - l2] = acc2;
-        if (q == 0) rd[j + 1] = pivot(acc.x);
-        a = a2;
-        off = off2 + NT;
+      // read only columns j, j+1, colb and colb2, which this loop does not
+      // write)
+      const int m = D - j - 2;
+      if (m > 0) {
+        const int np = m * (m + 1) / 2;
+        int a = 0, off = tid;
         while (a < m && off >= m - a) off -= m - a++;
+        for (int q = tid; q < np; q += 2 * NT) {
+          int a2 = a, off2 = off + NT;
+          while (a2 < m && off2 >= m - a2) off2 -= m - a2++;
+          const bool two = q + NT < np;
+          const int l = j + 2 + a, i = l + off;
+          const int l2 = two ? j + 2 + a2 : l, i2 = two ? l2 + off2 : i;
+          const LT lij = Lc[cj + i - j], alj = colb[l], mij = Lc[c1 + i - j1], blj = colb2[l];
+          const LT lij2 = Lc[cj + i2 - j], alj2 = colb[l2], mij2 = Lc[c1 + i2 - j1], blj2 = colb2[l2];
+          LT acc = Lc[colstart(l, D) + i - l], acc2 = Lc[colstart(l2, D) + i2 - l2];
+          // acc -= lij conj(alj) + mij conj(blj)
+          acc.x = fma(-lij.x, alj.x, acc.x);
+          acc2.x = fma(-lij2.x, alj2.x, acc2.x);
+          acc.y = fma(-lij.y, alj.x, acc.y);
+          acc2.y = fma(-lij2.y, alj2.x, acc2.y);
+          acc.x = fma(-lij.y, alj.y, acc.x);
+          acc2.x = fma(-lij2.y, alj2.y, acc2.x);
+          acc.y = fma(lij.x, alj.y, acc.y);
+          acc2.y = fma(lij2.x, alj2.y, acc2.y);
+          acc.x = fma(-mij.x, blj.x, acc.x);
+          acc2.x = fma(-mij2.x, blj2.x, acc2.x);
+          acc.y = fma(-mij.y, blj.x, acc.y);
+          acc2.y = fma(-mij2.y, blj2.x, acc2.y);
+          acc.x = fma(-mij.y, blj.y, acc.x);
+          acc2.x = fma(-mij2.y, blj2.y, acc2.x);
+          acc.y = fma(mij.x, blj.y, acc.y);
+          acc2.y = fma(mij2.x, blj2.y, acc2.y);
+          Lc[colstart(l, D) + i - l] = acc;
+          if (two) Lc[colstart(l2, D) + i2 - l2] = acc2;
+          a = a2;
+          off = off2 + NT;
+          while (a < m && off >= m - a) off -= m - a++;
+        }
       }
       __syncthreads();
     }
@@ -1178,18 +1257,19 @@ __device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, lo
       for (int it = 0; it < refine_steps; ++it) {
         if constexpr (F32F) {
           // r = b - Rl u in double-float arithmetic (about 2^-48) on the FP32
-          // pipe: Rl read in FP64 from the input (the lower triangle, the
-          // conjugate above it by a sign flip) and split on the integer pipe,
-          // u split once per step and broadcast by shuffles; the load is
-          // applied after the sweep.  The FP64 pipe only splits the few values
-          // outside the fast split's range.
+          // pipe, from the double-float Rl in shared memory (the lower
+          // triangle, the conjugate above it by a sign flip, the load
+          // included); u split once per step and broadcast by shuffles
           ff::F2 rre[RPL], rim[RPL];
           float4 uf[RPL];
+          int csi[RPL];                                   // start of column i (the upper part's reads)
 #pragma unroll
           for (int q = 0; q < RPL; ++q) {
-            uf[q] = to_ff4(u[q]);
-            rre[q] = ff::from_double(b[q].x);
-            rim[q] = ff::from_double(b[q].y);
+            uf[q] = to_ff4_cvt(u[q]);
+            rre[q] = ff::from_double_cvt(b[q].x);
+            rim[q] = ff::from_double_cvt(b[q].y);
+            const int i = li + LR * q;
+            csi[q] = colstart(i < D ? i : D - 1, D);
           }
 #pragma unroll
           for (int ql = 0; ql < RPL; ++ql) {
@@ -1201,19 +1281,21 @@ __device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, lo
             const int src = grp * LR + lo;
             const ff::F2 ur{__shfl_sync(0xffffffffu, uf[ql].x, src), __shfl_sync(0xffffffffu, uf[ql].y, src)};
             const ff::F2 ui{__shfl_sync(0xffffffffu, uf[ql].z, src), __shfl_sync(0xffffffffu, uf[ql].w, src)};
+            const int cl = colstart(l, D);
 #pragma unroll
             for (int q = 0; q < RPL; ++q) {
               if (LR * q < D) {
                 const int i = li + LR * q;
                 const int ic = i < D ? i : D - 1;
-                const bool low = ic >= l;
-                const long long ao = low ? (long long)ic * D + l : (long long)l * D + ic;
-                const double2 a = in_bounds((long long)(A - cov) + ao, (long long)nsys * D * D, kSiteSolveIn)
-                                      ? __ldg(A + ao) : make_double2(0.0, 0.0);
-                const ff::F2 ar = ff::from_double(a.x);
-                ff::F2 ai = ic == l ? ff::F2{0.f, 0.f} : ff::from_double(a.y);
-                if (!low) ai = ff::F2{-ai.hi, -ai.lo};           // conj above the diagonal
-                const ff::F2 nar{-ar.hi, -ar.lo}, nai{-ai.hi, -ai.lo};
+                // row block q against column block ql: below it every entry is
+                // in the lower triangle, above it in the upper (compile-time);
+                // only the diagonal block decides per lane
+                const bool low = q > ql ? true : (q < ql ? false : ic >= l);
+                const int ao = low ? cl + ic - l : csi[q] + l - ic;
+                const float4 e = in_bounds(ao, Dp, kSiteSolveIn) ? Adf[ao] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const ff::F2 nar{-e.x, -e.y};
+                const ff::F2 ai = low ? ff::F2{e.z, e.w} : ff::F2{-e.z, -e.w};   // conj above the diagonal
+                const ff::F2 nai{-ai.hi, -ai.lo};
                 // r -= R[i][l] u_l:  re -= ar ur - ai ui,  im -= ar ui + ai ur
                 rre[q] = ff::fma(ff::fma(rre[q], nar, ur), ai, ui);
                 rim[q] = ff::fma(ff::fma(rim[q], nar, ui), nai, ur);
@@ -1221,15 +1303,9 @@ __device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, lo
             }
             }
           }
-          const ff::F2 nd = ff::from_double(-delta);
 #pragma unroll
-          for (int q = 0; q < RPL; ++q) {
-            if (LR * q < D) {
-              rre[q] = ff::fma(rre[q], nd, ff::F2{uf[q].x, uf[q].y});
-              rim[q] = ff::fma(rim[q], nd, ff::F2{uf[q].z, uf[q].w});
-            }
+          for (int q = 0; q < RPL; ++q)
             xf[q] = make_float2(__fadd_rn(rre[q].hi, rre[q].lo), __fadd_rn(rim[q].hi, rim[q].lo));
-          }
         } else {
         // r = b - R u - delta u  (R Hermitian: A[i][l] for i >= l, conj(A[l][i])
         // above, real diagonal; the load is applied after the sweep)
@@ -1294,9 +1370,21 @@ __device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, lo
       if (SEP) {
         if (live)
 #pragma unroll
-          for (int q = 0; q < RPL; ++q)
-            if (li + LR * q < D)
-              Ubf[(size_t)rhs * D + li + LR * q] = F32F ? to_ff4_cvt(u[q]) : to_ff4(u[q]);
+          for (int q = 0; q < RPL; ++q) {
+            const int i = li + LR * q;
+            if (i < D) {
+              if constexpr (F32F) {   // parked in the system's weight rows as two float2
+                const float4 f = to_ff4_cvt(u[q]);
+                float2* park = wts + (size_t)sys * S * D + 2 * ((size_t)rhs * D + i);
+                if (in_bounds((long long)(park - wts) + 1, (long long)nsys * S * D, kSiteSolveOut)) {
+                  park[0] = make_float2(f.x, f.y);
+                  park[1] = make_float2(f.z, f.w);
+                }
+              } else {
+                Ubf[(size_t)rhs * D + i] = to_ff4(u[q]);
+              }
+            }
+          }
       } else {
         emit(rsafe, u, live);
       }
@@ -1305,6 +1393,18 @@ __device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, lo
       // u_s = sum_c a_s[c] U_c and its normalisation in double-float on the
       // FP32 pipe; the group's partial Re v^H u is summed in FP64
       __syncthreads();
+      if constexpr (F32F) {   // the parked basis solutions over the matrix copy
+        const float2* park = wts + (size_t)sys * S * D;
+        for (int e = tid; e < C * D; e += NT) {
+          float2 h = make_float2(0.f, 0.f), l2 = make_float2(0.f, 0.f);
+          if (in_bounds((long long)(park - wts) + 2 * e + 1, (long long)nsys * S * D, kSiteSolveIn)) {
+            h = park[2 * e];        // written by this CTA before the barrier: plain loads
+            l2 = park[2 * e + 1];
+          }
+          Ubf[e] = make_float4(h.x, h.y, l2.x, l2.y);
+        }
+        __syncthreads();
+      }
       for (int s0 = 0; s0 < S; s0 += NG) {
         const int s = s0 + g;
         const int ssafe = s < S ? s : 0;
@@ -1737,16 +1837,15 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
   if (D < 1 || D > kMaxD || S < 1) return cudaErrorInvalidValue;
   const bool sep = sep_g != nullptr && sep_a != nullptr && steer_ff != nullptr && sep_a_ff != nullptr &&
                    C >= 1 && C <= 32 && D % C == 0;
-  if (solver == 1 && D > 64) {   // refinement with an FP32 factor and FP64 residuals
+  if (solver == 1 && D > 64) {   // refinement with an FP32 factor, double-float residuals
     if (!mir_supported(D) || steer_ff == nullptr) return cudaErrorNotSupported;
     const int LR = tn.solve_lr == 16 ? 16 : 32;    // 16 lanes x 8 rows or 32 x 4, 8 warps
     const size_t Dp = (size_t)D * (D + 1) / 2;
-    auto bytes = [&](bool with_u) {
-      return ((Dp + D) * sizeof(float2) + 15) / 16 * 16 + (with_u ? (size_t)C * D : 0) * 16 +
-             D * sizeof(float) + 16;
-    };
-    const bool sep_big = sep && bytes(true) <= 227 * 1024;
-    const size_t smem = bytes(sep_big);
+    // FP32 factor and the two pivot columns, the double-float Rl (the basis
+    // solutions' place in the combination), pivot reciprocals, pivot flag;
+    // separable steering parks the C basis solutions in the S weight rows
+    const size_t smem = ((Dp + 2 * D) * sizeof(float2) + 15) / 16 * 16 + Dp * 16 + D * sizeof(float) + 16;
+    const bool sep_big = sep && S >= 2 * C;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
 #define STAP_BIGF(lr, rpl)                                                                           \
   return sep_big ? launch_big<true, lr, 256, rpl, true>(cov, wts, steer, sep_g, steer_ff, sep_a_ff, \
@@ -1813,17 +1912,17 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
     // LR lanes per right-hand side, each holding RPL rows (D <= LR * RPL):
     //   LR = 8:  RPL 8, 4 warps (D <= 64)
     //   LR = 16: RPL 4, 4 warps (D <= 64) or RPL 8, 8 warps (D <= 128)
-    //   LR = 32: RPL 4, 8 warps
+    //   LR = 32: RPL 4, 8 warps (or 16, D > 64, when the tuning's warps per CTA is 16)
     // default: 16 up to D = 64 (several CTAs per SM), 32 above
     int LR = D <= 64 ? 16 : 32;
     if (tn.solve_lr == 32 || tn.solve_lr == 16 || (tn.solve_lr == 8 && D <= 64)) LR = tn.solve_lr;
     if (D <= kSmallMaxD) LR = 8;
     const int NT = (LR == 8 || (LR == 16 && D <= 64)) ? 128 : 256;
     const size_t Dp = (size_t)D * (D + 1) / 2;
-    // Lu, pivot column, (SEP) basis solutions; pivot reciprocals and the
+    // Lu, the two pivot columns, (SEP) basis solutions; pivot reciprocals and the
     // pivot flag
     auto bytes = [&](bool with_u) {
-      return (Dp + D) * sizeof(double2) + (with_u ? (size_t)C * D : 0) * 16 + D * sizeof(double) + 16;
+      return (Dp + 2 * D) * sizeof(double2) + (with_u ? (size_t)C * D : 0) * 16 + D * sizeof(double) + 16;
     };
     const bool sep_big = sep && bytes(true) <= 227 * 1024;
     const size_t smem = bytes(sep_big);
@@ -1836,6 +1935,7 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
     if (LR == 8) STAP_BIG(8, 128, 8);
     if (LR == 16 && NT == 128) STAP_BIG(16, 128, 4);
     if (LR == 16) STAP_BIG(16, 256, 8);
+    if (D > 64 && tn.solve_nw == 16) STAP_BIG(32, 512, 4);   // 16 warps, 16 right-hand sides at once
     STAP_BIG(32, 256, 4);
 #undef STAP_BIG
   }

@@ -30,7 +30,7 @@ struct Tune {
   int dop_tr = 0;      // range cells per Doppler CTA: 8, 16 or 32
   int cov_kt = 0;      // Doppler bins per covariance CTA (bin-pair kernel), a divisor of K
   int solve_ts = 0;    // D <= 32 solve: lanes per system (power of two, >= one per RHS)
-  int solve_nw = 0;    // D <= 32 solve: warps per CTA, 1..4
+  int solve_nw = 0;    // D <= 32 solve: warps per CTA, 1..4; D > 64 FP64 solve: 16 for 512-thread CTAs
   int solve_lr = 0;    // D > 32 solve: lanes per right-hand side, 8 (D <= 64), 16 or 32
   int apply_kind = 0;  // apply: 1 FP32 register-resident, 2 FP32 general, 3 tensor cores
   int slabs = 0;       // single-CPI run: range slabs pipelined on prioritised streams, 1..8

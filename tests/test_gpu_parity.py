@@ -287,6 +287,63 @@ def test_per_cta_solve_with_idle_lane_groups(lr, separable):
     plan.close()
 
 
+# D > 64 systems for the one-system-per-CTA kernels: an odd D (the two-column
+# factorisation rounds end with a single column) whose steering count leaves
+# idle lane groups and is below 2 C (the refinement option then solves the S
+# vectors directly), and D = 128 with S = 2 C (the refinement option parks the
+# basis solutions in the weight rows).
+LARGE_SPECS = {
+    "D75": synth.CPISpec(25, 16, 16, 192, 3, 96, 7, cnr_db=35.0, seed=61),
+    "D128": synth.CPISpec(32, 16, 16, 512, 4, 256, 64, cnr_db=40.0, seed=62),
+}
+
+
+@pytest.mark.parametrize("separable", [True, False], ids=["sep", "explicit"])
+@pytest.mark.parametrize("variant", [(16, 0), (32, 0), (32, 16)], ids=["lr16", "lr32", "lr32x16warps"])
+@pytest.mark.parametrize("refine", [0, 1])
+@pytest.mark.parametrize("name", list(LARGE_SPECS))
+def test_large_per_cta_solve_variants(name, refine, variant, separable):
+    """Every launch shape of the D > 64 FP64 solve (16 lanes x 8 rows, 32 x 4
+    with 8 or 16 warps) against the oracle's weights."""
+    spec = LARGE_SPECS[name]
+    d = oracle.Dims(*spec.dims())
+    cov = oracle.covariance(d, oracle.doppler(d, _cube(spec)))
+    ref, _, nf = oracle.weights(d, cov)
+    assert nf == 0
+    plan = _plan(spec, refine_steps=refine)
+    if not separable:
+        plan.set_steering(oracle.default_steering(d))
+    choices = stap.stap_plan_get_tuning(plan.handle, 0)
+    choices[4], choices[3] = variant
+    stap.stap_plan_set_tuning(plan.handle, 0, choices)
+    wts = to_np(plan.solve_weights(_dev(cov, torch.complex128)))
+    assert plan.status() == (stap.STAP_OK, 0)
+    err = np.linalg.norm(wts - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+    assert np.max(err) <= 2 * EPS32 * np.sqrt(2), np.max(err)
+    plan.close()
+
+
+@pytest.mark.parametrize("lr", [16, 32])
+@pytest.mark.parametrize("name", list(LARGE_SPECS))
+def test_large_refinement_solve_variants(name, lr):
+    """The refinement option's D > 64 form (FP32 factor in shared memory with
+    the double-float Rl) at both launch shapes, 2 steps."""
+    spec = LARGE_SPECS[name]
+    d = oracle.Dims(*spec.dims())
+    cov = oracle.covariance(d, oracle.doppler(d, _cube(spec)))
+    ref, _, nf = oracle.weights(d, cov)
+    assert nf == 0
+    plan = _plan(spec, refine_steps=2, solver=stap.STAP_SOLVE_MIXED_IR)
+    choices = stap.stap_plan_get_tuning(plan.handle, 0)
+    choices[4] = lr
+    stap.stap_plan_set_tuning(plan.handle, 0, choices)
+    wts = to_np(plan.solve_weights(_dev(cov, torch.complex128)))
+    assert plan.status() == (stap.STAP_OK, 0)
+    err = np.linalg.norm(wts - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+    assert np.max(err) <= 4 * EPS32, np.max(err)
+    plan.close()
+
+
 # Snapshot lengths with a register-resident solve kernel (D = 8, 12, 16), each
 # with a steering count that leaves idle lanes in the last pass.
 REG_SPECS = {
