@@ -45,8 +45,11 @@ L2_FLUSH_BYTES = 256 << 20
 # summarised in profiles/), keyed by a hash of the kernel source, the solve
 # kernel the tuning chose (1 register-resident, 2 shared-memory teams, 3 one
 # system per CTA) and the workload, so that a changed or different kernel
-# reports null until re-measured.
-SOLVE_TRAFFIC = {}
+# reports null until re-measured.  The large CPI's entry is an eighth of it
+# (8192 of its 65536 systems, same kernel and launch shape: 1151412224 bytes
+# read + 510120448 written, the capture summarised in profiles/) scaled by 8, the
+# traffic being per system (its lower triangle read, its weights written).
+SOLVE_TRAFFIC = {("ece189e7f5967c5d", 3, "large"): 8 * (1151412224 + 510120448)}
 SOLVE_KERNELS = {1: "solve_reg_kernel (register-resident FP64 LDL^H, solves, refinement)",
                  2: "solve_kernel (shared-memory FP64 Cholesky teams, solves, refinement)",
                  3: "solve_big_kernel (one system per CTA: FP64 LDL^H, solves, refinement)"}

@@ -460,6 +460,16 @@ stap_status stap_get_status(stap_plan plan, int64_t* n_failed_systems);
 /* Static description of a status code. */
 const char* stap_status_string(stap_status status);
 
+/* Test support: out[i] = the reciprocal 1/in[i] exactly as the FP64
+ * factorisation of the one-system-per-CTA solve forms its pivots' reciprocals
+ * (Newton-Raphson iteration from the hardware's approximate reciprocal), so
+ * that a test can compare it with IEEE division.  in, out: n device doubles
+ * (in[i] positive, finite and normal; other values give unspecified results);
+ * runs on cuda_stream (NULL = legacy default stream) and waits for it.
+ * Errors: STAP_ERR_INVALID_ARG for n < 0 or NULL pointers with n > 0;
+ * STAP_ERR_CUDA.  No counterpart in the paper. */
+stap_status stap_test_pivot_reciprocal(const double* in, double* out, int64_t n, void* cuda_stream);
+
 /* 1 if this library is the checked build (compiled with -DSTAP_CHECKED),
  * else 0.  No counterpart in the paper: a debugging aid. */
 int32_t stap_checked_build(void);

@@ -42,6 +42,13 @@ __device__ __forceinline__ F2 fma(F2 acc, F2 a, F2 b) {
 // acc - a * b
 __device__ __forceinline__ F2 fms(F2 acc, F2 a, F2 b) { return fma(acc, {-a.hi, -a.lo}, b); }
 
+// a + b and a - b with a, b double-floats (the sloppy sum: about 2^-48 of |a| + |b|)
+__device__ __forceinline__ F2 add2(F2 a, F2 b) {
+  const F2 s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) { return add2(a, {-b.hi, -b.lo}); }
+
 // a + b with a a double-float and b a float
 __device__ __forceinline__ F2 add(F2 a, float b) {
   const F2 s = two_sum(a.hi, b);

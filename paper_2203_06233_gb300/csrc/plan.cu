@@ -48,6 +48,7 @@ struct Cpi {
   // steer[s] = g (x) a_s for the default table: temporal factor g [T][2] and
   // spatial factors a [S][C][2]; cleared when the caller replaces the table
   bool separable = false;
+  bool sep_sym = false;   // sep_a_ff[S-1-s] is conj(sep_a_ff[s]) bit for bit
   std::vector<double> sep_g, sep_a;
   std::vector<float> steer_ff, sep_a_ff, g_ff;   // the tables as double-floats [..][4]
   size_t steer_ff_off = 0, a_ff_off = 0, g_ff_off = 0;
@@ -86,6 +87,27 @@ void to_ff(const std::vector<double>& src, std::vector<float>& dst) {
     dst[2 * i] = hi;
     dst[2 * i + 1] = (float)(src[i] - (double)hi);
   }
+}
+
+// Look angle of steering vector s of S, in radians: uniform in angle over
+// (-90, 90) degrees at s + 1/2 (the default steering's reading).  The upper
+// half is the negated lower half, so the spatial factors of s and S-1-s are
+// conjugates bit for bit (the solve combines such pairs in one pass).
+double steer_theta(int s, int S) {
+  if (2 * s + 1 > S) return -steer_theta(S - 1 - s, S);
+  return (-90.0 + 180.0 * (s + 0.5) / S) * kPi / 180.0;
+}
+
+// Whether the double-float spatial factors [S][C] (re hi, re lo, im hi, im lo)
+// satisfy a[S-1-s][c] = conj(a[s][c]) exactly.
+bool conj_symmetric(const std::vector<float>& a_ff, int S, int C) {
+  for (int s = 0; s < S; ++s)
+    for (int c = 0; c < C; ++c) {
+      const float* x = &a_ff[4 * ((size_t)s * C + c)];
+      const float* y = &a_ff[4 * ((size_t)(S - 1 - s) * C + c)];
+      if (!(x[0] == y[0] && x[1] == y[1] && x[2] == -y[2] && x[3] == -y[3])) return false;
+    }
+  return true;
 }
 
 void make_tables(Cpi& c) {
@@ -128,7 +150,7 @@ void make_tables(Cpi& c) {
     c.sep_g[2 * t + 1] = gi[t];
   }
   for (int s = 0; s < S; ++s) {
-    const double th = (-90.0 + 180.0 * (s + 0.5) / S) * kPi / 180.0;
+    const double th = steer_theta(s, S);
     const double fs = 0.5 * std::sin(th);
     for (int ch = 0; ch < C; ++ch) {
       const double a = 2.0 * kPi * fs * ch;
@@ -147,6 +169,7 @@ void make_tables(Cpi& c) {
   to_ff(c.steer, c.steer_ff);
   to_ff(c.sep_a, c.sep_a_ff);
   to_ff(c.sep_g, c.g_ff);
+  c.sep_sym = conj_symmetric(c.sep_a_ff, S, C);
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -308,7 +331,7 @@ stap_status do_solve(stap_plan p, const Cpi& c, const void* cov, void* wts, cuda
       c.separable ? p->at<const float4>(c.a_ff_off) : nullptr,
       c.separable ? p->at<const float4>(c.g_ff_off) : nullptr, (long long)d.n_dop * nb, c.D,
       d.n_steering, d.n_chan, p->opt.load_factor, p->opt.refine_steps, p->opt.solver, p->status(),
-      st, c.tune));
+      st, c.tune, c.separable && c.sep_sym));
 }
 
 stap_status do_apply(stap_plan p, const Cpi& c, const void* dop, const void* wts, float* out,
@@ -769,6 +792,14 @@ void stap_options_default(stap_options* opt) {
 
 int32_t stap_abi_version(void) { return STAP_ABI_VERSION; }
 
+stap_status stap_test_pivot_reciprocal(const double* in, double* out, int64_t n, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!in || !out))) return STAP_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (stap::launch_pivot_reciprocal(static_cast<const double*>(in), out, (long long)n, s) != cudaSuccess)
+    return STAP_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? STAP_OK : STAP_ERR_CUDA;
+}
+
 int32_t stap_checked_build(void) {
 #ifdef STAP_CHECKED
   return 1;
@@ -1136,7 +1167,7 @@ stap_status stap_plan_set_front_end(stap_plan p, int32_t n_elem, const double* W
   // spatial gains b_s[c] = sum_n conj(W[c][n]) exp(j 2 pi f_s n): the separable
   // steering's spatial factors, and v_s = g (x) b_s
   for (int s = 0; s < S; ++s) {
-    const double th = (-90.0 + 180.0 * (s + 0.5) / S) * kPi / 180.0;
+    const double th = steer_theta(s, S);
     const double fs = 0.5 * std::sin(th);
     for (int ch = 0; ch < C; ++ch) {
       double br = 0, bi = 0;
@@ -1162,6 +1193,7 @@ stap_status stap_plan_set_front_end(stap_plan p, int32_t n_elem, const double* W
   c.separable = true;
   to_ff(c.steer, c.steer_ff);
   to_ff(c.sep_a, c.sep_a_ff);
+  c.sep_sym = conj_symmetric(c.sep_a_ff, S, C);
   p->fe_w.resize(2 * (size_t)C * N);
   for (size_t i = 0; i < p->fe_w.size(); ++i) p->fe_w[i] = (float)W[i];
   p->fe_N = N;

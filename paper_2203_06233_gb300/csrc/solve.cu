@@ -199,6 +199,7 @@ struct SolveParams {
   int refine_steps;
   DeviceStatus* status;
   int gx;
+  int sym;   // the separable spatial factors are conjugate-symmetric: a_{S-1-s} = conj(a_s)
 };
 
 template <bool SEP>
@@ -1405,6 +1406,73 @@ __device__ __forceinline__ void solve_big_kernel_body(const SolveParams& prm, lo
         }
         __syncthreads();
       }
+      if (prm.sym) {
+        // conjugate-symmetric spatial factors (a_{S-1-s} = conj(a_s), as the
+        // default steering's mirrored angles give): one pass over the basis
+        // per row forms both u_s and u_{S-1-s} from four real sums,
+        // P = sum ar Ur, Q = sum ai Ui, R = sum ar Ui, T = sum ai Ur:
+        // u_s = (P - Q) + j (R + T), u_{S-1-s} = (P + Q) + j (R - T)
+        const int npair = (S + 1) / 2;
+        for (int p0 = 0; p0 < npair; p0 += NG) {
+          const int pidx = p0 + g;
+          const int s1 = pidx < npair ? pidx : 0;
+          const int s2 = S - 1 - s1;
+          const float4* as = sep_a_ff + (size_t)s1 * C;
+          const float4* v1 = steer_ff + (size_t)s1 * D;
+          const float4* v2 = steer_ff + (size_t)s2 * D;
+          float wr1[RPL], wi1[RPL], wr2[RPL], wi2[RPL];
+          ff::F2 qp1{0.f, 0.f}, qp2{0.f, 0.f};
+#pragma unroll
+          for (int q = 0; q < RPL; ++q) {
+            wr1[q] = wi1[q] = wr2[q] = wi2[q] = 0.f;
+            if (LR * q < D) {
+              const int i = li + LR * q;
+              const int ic = i < D ? i : D - 1;
+              ff::F2 P{0.f, 0.f}, Q{0.f, 0.f}, R{0.f, 0.f}, T{0.f, 0.f};
+              for (int c = 0; c < C; ++c) {
+                const float4 a = __ldg(as + c);
+                const float4 x = Ubf[(size_t)c * D + ic];
+                const ff::F2 ar{a.x, a.y}, ai{a.z, a.w}, xr{x.x, x.y}, xi{x.z, x.w};
+                P = ff::fma(P, ar, xr);
+                Q = ff::fma(Q, ai, xi);
+                R = ff::fma(R, ar, xi);
+                T = ff::fma(T, ai, xr);
+              }
+              const ff::F2 ur1 = ff::sub2(P, Q), ui1 = ff::add2(R, T);
+              const ff::F2 ur2 = ff::add2(P, Q), ui2 = ff::sub2(R, T);
+              if (i < D) {
+                const float4 a1 = __ldg(v1 + i), a2 = __ldg(v2 + i);
+                qp1 = ff::fma(ff::fma(qp1, {a1.x, a1.y}, ur1), {a1.z, a1.w}, ui1);
+                qp2 = ff::fma(ff::fma(qp2, {a2.x, a2.y}, ur2), {a2.z, a2.w}, ui2);
+              }
+              wr1[q] = __fadd_rn(ur1.hi, ur1.lo);
+              wi1[q] = __fadd_rn(ui1.hi, ui1.lo);
+              wr2[q] = __fadd_rn(ur2.hi, ur2.lo);
+              wi2[q] = __fadd_rn(ui2.hi, ui2.lo);
+            }
+          }
+          const double qs1 = group_sum<LR>(ff::to_double(qp1));
+          const double qs2 = group_sum<LR>(ff::to_double(qp2));
+          const bool good1 = ok && qs1 > 0.0 && isfinite(qs1);
+          const bool good2 = ok && qs2 > 0.0 && isfinite(qs2);
+          const float sf1 = good1 ? (float)rsqrt(qs1) : 0.f;
+          const float sf2 = good2 ? (float)rsqrt(qs2) : 0.f;
+          if (pidx < npair) {
+            float2* w1 = wts + ((size_t)sys * S + s1) * D;
+            float2* w2 = wts + ((size_t)sys * S + s2) * D;
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+              const int i = li + LR * q;
+              if (i < D) {
+                if (in_bounds((long long)(w1 - wts) + i, (long long)nsys * S * D, kSiteSolveOut))
+                  w1[i] = good1 ? make_float2(wr1[q] * sf1, wi1[q] * sf1) : make_float2(0.f, 0.f);
+                if (s2 != s1 && in_bounds((long long)(w2 - wts) + i, (long long)nsys * S * D, kSiteSolveOut))
+                  w2[i] = good2 ? make_float2(wr2[q] * sf2, wi2[q] * sf2) : make_float2(0.f, 0.f);
+              }
+            }
+          }
+        }
+      } else
       for (int s0 = 0; s0 < S; s0 += NG) {
         const int s = s0 + g;
         const int ssafe = s < S ? s : 0;
@@ -1762,7 +1830,7 @@ template <bool SEP, int LR, int NT, int RPL, bool F32F = false>
 cudaError_t launch_big(const double2* cov, float2* wts, const double2* steer, const double2* sep_g,
                        const float4* steer_ff, const float4* sep_a_ff, long long nsys, int D, int S,
                        int C, double lf, int refine, DeviceStatus* status, size_t smem,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool sym = false) {
   static int set_bytes[64] = {0}, set_bytes_b[64] = {0};
   cudaError_t e = ensure_smem(solve_big_kernel<SEP, LR, NT, RPL, F32F>, smem, set_bytes);
   if (e == cudaSuccess) e = ensure_smem(solve_big_kernel_batched<SEP, LR, NT, RPL, F32F>, smem, set_bytes_b);
@@ -1772,7 +1840,7 @@ cudaError_t launch_big(const double2* cov, float2* wts, const double2* steer, co
   if (blocks > nsys) blocks = nsys;
   // one system per virtual block of the persistent twin
   const SolveParams p{cov, wts, steer, sep_g, nullptr, steer_ff, sep_a_ff, nsys, D, S, C, 0, lf,
-                      refine, status, (int)nsys};
+                      refine, status, (int)nsys, SEP && sym ? 1 : 0};
   return launch_params(reinterpret_cast<const void*>(solve_big_kernel<SEP, LR, NT, RPL, F32F>),
                        reinterpret_cast<const void*>(solve_big_kernel_batched<SEP, LR, NT, RPL, F32F>),
                        dim3((unsigned)blocks), NT, smem, s, p, nsys);
@@ -1816,6 +1884,21 @@ cudaError_t launch_mir(const double2* cov, float2* wts, const float4* steer_ff, 
 
 }  // namespace
 
+namespace {
+__global__ void pivot_reciprocal_kernel(const double* __restrict__ in, double* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = recip_newton(in[i]);
+}
+}  // namespace
+
+cudaError_t launch_pivot_reciprocal(const double* in, double* out, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152LL * 8) blocks = 152LL * 8;
+  pivot_reciprocal_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
 bool mir_supported(int D) { return D >= 1 && D <= kMaxD; }
 
 namespace {
@@ -1832,7 +1915,7 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
                          const double2* sep_g, const double2* sep_a, const float4* steer_ff,
                          const float4* sep_a_ff, const float4* g_ff, long long nsys, int D, int S,
                          int C, double load_factor, int refine_steps, int solver,
-                         DeviceStatus* status, cudaStream_t s, const Tune& tn) {
+                         DeviceStatus* status, cudaStream_t s, const Tune& tn, bool sep_sym) {
   if (nsys <= 0) return cudaSuccess;
   if (D < 1 || D > kMaxD || S < 1) return cudaErrorInvalidValue;
   const bool sep = sep_g != nullptr && sep_a != nullptr && steer_ff != nullptr && sep_a_ff != nullptr &&
@@ -1850,7 +1933,7 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
 #define STAP_BIGF(lr, rpl)                                                                           \
   return sep_big ? launch_big<true, lr, 256, rpl, true>(cov, wts, steer, sep_g, steer_ff, sep_a_ff, \
                                                         nsys, D, S, C, load_factor, refine_steps,   \
-                                                        status, smem, s)                             \
+                                                        status, smem, s, sep_sym)                    \
                  : launch_big<false, lr, 256, rpl, true>(cov, wts, steer, nullptr, nullptr, nullptr,\
                                                          nsys, D, S, C, load_factor, refine_steps,  \
                                                          status, smem, s)
@@ -1929,7 +2012,8 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
 #define STAP_BIG(lr, nt, rpl)                                                                     \
   return sep_big ? launch_big<true, lr, nt, rpl>(cov, wts, steer, sep_g, steer_ff, sep_a_ff, nsys, D,  \
-                                                 S, C, load_factor, refine_steps, status, smem, s)   \
+                                                 S, C, load_factor, refine_steps, status, smem, s,   \
+                                                 sep_sym)                                            \
                  : launch_big<false, lr, nt, rpl>(cov, wts, steer, nullptr, nullptr, nullptr, nsys, D, \
                                                   S, C, load_factor, refine_steps, status, smem, s)
     if (LR == 8) STAP_BIG(8, 128, 8);

@@ -39,6 +39,10 @@ struct Tune {
   int cov_kind = 0;    // covariance: 1 FP32 error-free, 2 tensor cores (mixed-precision plans)
 };
 
+// The FP64 pivot reciprocal of the one-system-per-CTA factorisation on n
+// device doubles (test support).
+cudaError_t launch_pivot_reciprocal(const double* in, double* out, long long n, cudaStream_t s);
+
 // Training with guard cells: out[k][b] = mean of in[k][b-1] and in[k][b+1]
 // (the one that exists at either end); NB >= 2.
 cudaError_t launch_train_neighbours(const double2* in, double2* out, int K, int NB, int D,
@@ -124,7 +128,8 @@ cudaError_t launch_solve(const double2* cov, float2* wts, const double2* steer,
                          const double2* sep_g, const double2* sep_a, const float4* steer_ff,
                          const float4* sep_a_ff, const float4* g_ff, long long nsys, int D, int S,
                          int C, double load_factor, int refine_steps, int solver,
-                         DeviceStatus* status, cudaStream_t s, const Tune& t = Tune());
+                         DeviceStatus* status, cudaStream_t s, const Tune& t = Tune(),
+                         bool sep_sym = false);
 
 // out[s][k][r] = |w^H x|^2; dop [C][K][R] c64, wts [K][NB][S][D] c64, out [S][K][R] f32.
 cudaError_t launch_apply(const float2* dop, const float2* wts, float* out, int C, int K, int R,

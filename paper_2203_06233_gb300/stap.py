@@ -52,6 +52,7 @@ EXPORTED = (
     "stap_plan_set_tuning", "stap_train_neighbours", "stap_plan_stream_bytes", "stap_run_stream",
     "stap_plan_set_front_end", "stap_reduce_channels", "stap_plan_set_wait_limit",
     "stap_train_window", "stap_checked_build", "stap_check_report", "stap_plan_set_batch_schedule",
+    "stap_test_pivot_reciprocal",
     "stap_plan_get_batch_schedule",
 )
 
@@ -150,6 +151,7 @@ def lib():
             L.stap_plan_get_tuning.argtypes = [vp, i32, ctypes.POINTER(i32)]
             L.stap_plan_set_tuning.argtypes = [vp, i32, ctypes.POINTER(i32)]
             L.stap_checked_build.argtypes = []
+            L.stap_test_pivot_reciprocal.argtypes = [vp, vp, ctypes.c_int64, vp]
             L.stap_plan_set_batch_schedule.argtypes = [vp, i32]
             L.stap_plan_get_batch_schedule.argtypes = [vp, ctypes.POINTER(i32)]
             L.stap_check_report.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i32),
@@ -397,6 +399,18 @@ def default_tune_cache() -> str:
 
 def stap_abi_version() -> int:
     return lib().stap_abi_version()
+
+
+def stap_test_pivot_reciprocal(x: torch.Tensor) -> torch.Tensor:
+    """The factorisation's pivot reciprocal on a CUDA float64 tensor (test support)."""
+    if x.dtype != torch.float64 or not x.is_cuda:
+        raise StapError(STAP_ERR_INVALID_ARG, "stap_test_pivot_reciprocal: a CUDA float64 tensor")
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    _check(lib().stap_test_pivot_reciprocal(x.data_ptr(), out.data_ptr(), x.numel(),
+                                            torch.cuda.current_stream(x.device).cuda_stream),
+           "stap_test_pivot_reciprocal")
+    return out
 
 
 def stap_checked_build() -> bool:

@@ -332,3 +332,9 @@ def test_batch_schedule_values_without_cuda():
     stap.stap_plan_set_batch_schedule(h, stap.STAP_BATCH_STREAMS)
     assert stap.stap_plan_get_batch_schedule(h) == stap.STAP_BATCH_STREAMS
     stap.stap_plan_destroy(h)
+
+
+def test_pivot_reciprocal_test_call_validates_before_any_cuda_call():
+    L = stap.lib()
+    assert L.stap_test_pivot_reciprocal(None, None, -1, None) == stap.STAP_ERR_INVALID_ARG
+    assert L.stap_test_pivot_reciprocal(None, None, 4, None) == stap.STAP_ERR_INVALID_ARG

@@ -287,6 +287,20 @@ def test_per_cta_solve_with_idle_lane_groups(lr, separable):
     plan.close()
 
 
+def test_pivot_reciprocal_is_within_one_ulp_of_ieee_division():
+    """The FP64 factorisation's pivot reciprocal (Newton-Raphson steps from the
+    hardware's approximate reciprocal) against IEEE division, over normal
+    positive doubles of every magnitude whose reciprocal is normal too."""
+    rng = np.random.default_rng(71)
+    x = np.concatenate([2.0 ** rng.uniform(-1000.0, 1000.0, 200000), rng.uniform(1e-3, 1e3, 200000),
+                        [1.0, 2.0, 3.0, 0.1, 1e-300, 1e300, np.nextafter(1.0, 2.0), np.nextafter(2.0, 1.0)]])
+    got = stap.stap_test_pivot_reciprocal(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = 1.0 / x
+    ulps = np.abs(got - ref) / np.spacing(ref)
+    print(f"pivot reciprocal: max {np.max(ulps):.2f} ulp, {np.mean(ulps > 0):.3%} not correctly rounded")
+    assert np.max(ulps) <= 1.0
+
+
 # D > 64 systems for the one-system-per-CTA kernels: an odd D (the two-column
 # factorisation rounds end with a single column) whose steering count leaves
 # idle lane groups and is below 2 C (the refinement option then solves the S
