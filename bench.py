@@ -713,9 +713,25 @@ def batch_legs(args, dev, stream, flush):
             raise RuntimeError(f"batch {PREC_NAMES[prec]}: device status {code} ({failed} failed)")
         outs_pick[prec] = {i: outs[i][:, :, b * 64:(b + 1) * 64].cpu().numpy() for i, b in picks}
         ms = sum(times) / steps
+        # the autotuner's schedule, and the other one timed beside it (2 steps)
+        chosen = stap.stap_plan_get_batch_schedule(plan.handle)
+        other = stap.STAP_BATCH_STREAMS if chosen == stap.STAP_BATCH_PERSISTENT else stap.STAP_BATCH_PERSISTENT
+        sched_names = {stap.STAP_BATCH_PERSISTENT: "persistent", stap.STAP_BATCH_STREAMS: "streams"}
+        schedules = {sched_names[chosen]: ms}
+        try:
+            plan.set_batch_schedule(other)
+            plan.run_cpi(cubes, outs)
+            torch.cuda.synchronize()
+            t_other = time_steps(lambda: plan.run_cpi(cubes, outs), 2, flush, stream)
+            schedules[sched_names[other]] = sum(t_other) / 2
+            plan.set_batch_schedule(chosen)
+        except Exception as exc:   # a side measurement must not lose the leg
+            schedules[sched_names[other]] = f"{type(exc).__name__}: {exc}"[:200]
+        log(f"batch {PREC_NAMES[prec]}: {ms:.1f} ms/step ({sched_names[chosen]}), schedules {schedules}")
         res["mixed" if prec else "fp32"] = {
             "precision": PREC_NAMES[prec], "arithmetic": PREC_TEXT[prec] + "; " + SOLVE_TEXT,
             "value": cells / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "autotune_s": tune_s,
+            "schedule": sched_names[chosen], "ms_per_step_by_schedule": schedules,
             "gpu_launches_per_step": 4 * len(specs),
             "fp64_solve_frac_of_step": sum(solve_flops(s) for s in specs) / (ms * 1e-3) / 1e12 /
             peaks()["fp64_tflops"]}
