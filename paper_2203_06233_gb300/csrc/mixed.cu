@@ -20,20 +20,31 @@
 //
 // Covariance.  R = (1/B) X X^H per (Doppler bin, range block) with X the
 // D x B snapshot tile, X = Xr + j Xi.  The operand rows are stacked as
-// Y = [Xr ; Xi] for G = floor(128 / D8) systems at once (D8 = D rounded up
+// Y = [Xr ; Xi] for G systems at once (D8 = D rounded up
 // to 8; rows of entries a >= D are zero): rows 0 .. G D8 - 1 hold Xr of the
-// G systems, rows G D8 .. 2 G D8 - 1 their Xi.  Two MMAs per product and K
-// step, both with M = 128 and N = 2 G D8 (<= 256), B = Y:
-//   top = Xr Y^T  (A = rows 0 .. 127)       -> [Xr Xr^T | Xr Xi^T]
-//   bot = Xi Y^T  (A = rows G D8 .. +127)    -> [Xi Xr^T | Xi Xi^T]
-// so TMEM lane i (entry a of system g) holds everything its row of R needs:
-//   Re R[a][l] = XrXr[a][l] + XiXi[a][l],  Im R[a][l] = XiXr[a][l] - XrXi[a][l].
-// Only the blocks between different systems (G > 1) are computed and not
-// used.  Each snapshot element is loaded once, split once and stored once
-// per piece (the B operand is the A operand's own rows).  Thread a writes
-// R[a][l] for l >= a as conj into row l, column a, so a warp's stores of one
-// output row are contiguous; the full Hermitian form (the ABI call) mirrors
-// the same value into row a, so it is Hermitian bit for bit.
+// G systems, rows G D8 .. 2 G D8 - 1 their Xi.  Accumulators of NA = G D8
+// rounded up to 16 columns, M = 128, in one of two forms:
+//   stacked (D8 <= 64, G = floor(64 / D8)): A is all 128 rows [Xr ; Xi], and
+//     two MMAs per product and K step give every block of the tile:
+//       Xr-rows x Xr -> [XrXr^T ; XiXr^T],   Xr-rows x Xi -> [XrXi^T ; XiXi^T]
+//     in 2 NA <= 128 TMEM columns (two CTAs per SM).  TMEM lane GD + i holds
+//     the Xi row of the entry whose Xr row is lane i; the epilogue hands the
+//     Xi rows to the Xr lanes through shared memory;
+//   split (D8 > 64, G = 1): four MMAs per product and K step into four
+//     accumulators XrXr, XiXi, XiXr, XrXi (512 columns, one CTA per SM).
+//   Re R = XrXr + XiXi and Im R = XiXr - XrXi are formed in the epilogue.
+//   Each accumulator holds one product, so it takes one MMA step per K step
+//   and product: the tensor cores' FP32 accumulation loses up to about an
+//   ulp of the running sum per step, and summing Re R in one accumulator
+//   (twice the steps) measurably doubled the covariance error.
+// TMEM lane i (entry a of system g) holds its row of each block in columns
+// g D8 + l.  Only the blocks between different systems (G > 1) are
+// computed and not used.  Each snapshot element is loaded once, split once
+// and stored once per piece (the B operand is the A operand's own rows).
+// Thread a writes R[a][l] for l >= a as conj into row l, column a, so a
+// warp's stores of one output row are contiguous; the full Hermitian form
+// (the ABI call) mirrors the same value into row a, so it is Hermitian bit
+// for bit.
 //
 // Apply.  out[s][k][r] = |w_{k,b(r),s}^H x_{k,r}|^2 per tile of 128 range
 // cells of one bin: M = 128 cells, K = 2 D (the snapshot's re/im pairs in
@@ -149,21 +160,34 @@ __host__ __device__ constexpr uint32_t idesc_for(int N) {
 
 // ---- covariance -----------------------------------------------------------------
 
-constexpr int kCovRB = 128;                   // bytes of one operand row per chunk (8 core matrices)
-constexpr int kCovU = 16;                     // staging units per warp and chunk (G D8 / 8 <= 16)
-constexpr int kCovPiece = 256 * kCovRB;       // 256 rows of one piece (32 KB)
+// Two forms (see the file header): stacked (STK, D8 <= 64: M spans [Xr ; Xi]
+// of G = floor(64 / D8) systems, two accumulators of NA <= 64 columns) and
+// split (D8 > 64: four accumulators, 512 columns).  A piece of a stage holds
+// ROWS operand rows of RB bytes (16 KB either way).
+constexpr int kCovU = 8;                      // staging units per warp and chunk (<= 64 units / 8 warps)
+constexpr int kCovPiece = 16384;              // bytes of one piece of one stage
+
+template <bool STK>
+struct CovForm {
+  static constexpr int RB = STK ? 128 : 64;   // bytes of one operand row per chunk
+  static constexpr int ROWS = kCovPiece / RB; // 128 (stacked) or 256 (split) rows
+  static constexpr int NCM = RB / 16;         // core matrices along K per chunk
+  static constexpr int COLS = STK ? 128 : 512;   // TMEM columns of a tile
+  static constexpr int GROWS = STK ? 64 : 128;   // rows of Xr a tile takes (G D8 <= GROWS)
+};
 
 template <int PREC>
 constexpr size_t cov_smem() { return 2 * (size_t)Fmt<PREC>::NPC * kCovPiece; }
 
-template <int PREC>
-__global__ void __launch_bounds__(kThreads)
+template <int PREC, bool STK>
+__global__ void __launch_bounds__(kThreads, 2)
 covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov, int C, int K,
                       int ldr, int T, int B, int NB, int D8, int G, long long ntiles, int lower_only,
                       DeviceStatus* __restrict__ status, int wait_polls) {
   using F = Fmt<PREC>;
-  constexpr int KC = kCovRB / F::ESZ;        // cells per chunk: 32 (tf32) or 64 (16-bit)
-  constexpr int SBO = 8 * kCovRB;            // bytes between 8-row groups
+  using Fm = CovForm<STK>;
+  constexpr int KC = Fm::RB / F::ESZ;        // cells per chunk
+  constexpr int SBO = 8 * Fm::RB;            // bytes between 8-row groups
   constexpr int STAGE = F::NPC * kCovPiece;
   constexpr int CPW = 16 / F::ESZ;           // cells per core-matrix row
   constexpr int CPL = CPW / 4;               // cells per lane in a staging unit
@@ -175,13 +199,14 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
   __shared__ int smax[128];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int D = C * T;
-  const int GD = G * D8;
+  const int GD = G * D8;                     // Xr rows of the tile (Xi rows follow)
+  const int NA = (GD + 15) / 16 * 16;        // columns of one accumulator
   const long long nsys = (long long)K * NB;
   const int nchunks = (B + KC - 1) / KC;
-  const int units = GD;                      // (GD / 8) row groups x 8 core matrices along K
+  const int units = (GD / 8) * Fm::NCM;      // row groups x core matrices along K
 
   for (int i = tid; i < 2 * STAGE / 4; i += kThreads) reinterpret_cast<uint32_t*>(sm)[i] = 0u;
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, Fm::COLS);
   if (tid == 0) {
     tc::mbar_init(&mbar[0], 1);
     tc::mbar_init(&mbar[1], 1);
@@ -190,7 +215,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = idesc_for<PREC>(2 * GD);
+  const uint32_t idesc = idesc_for<PREC>(NA);
   uint32_t parity[2] = {0u, 0u};
   bool pending[2] = {false, false};
   bool ok = true;
@@ -251,8 +276,8 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
 #pragma unroll
       for (int uu = 0; uu < kCovU; ++uu) {
         const int unit = warp + uu * (kThreads / 32);
-        const int p = (unit >> 3) * 8 + (lane >> 2);
-        const int j = c0 + (unit & 7) * CPW + (lane & 3) * CPL;
+        const int p = (unit / Fm::NCM) * 8 + (lane >> 2);
+        const int j = c0 + (unit % Fm::NCM) * CPW + (lane & 3) * CPL;
         const long long base = unit < units ? rowbase[p] : -1;
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc)
@@ -278,7 +303,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
       for (int uu = 0; uu < kCovU; ++uu) {
         const int unit = warp + uu * (kThreads / 32);
         if (unit >= units) continue;
-        const int rg = unit >> 3, cmk = unit & 7;
+        const int rg = unit / Fm::NCM, cmk = unit % Fm::NCM;
         const int off = rg * SBO + cmk * 128 + (lane >> 2) * 16 + (lane & 3) * 4;
         const int offi = off + (GD / 8) * SBO;
         if (!in_bounds(offi + 3, kCovPiece, kSiteTcSmem)) continue;   // the word's last byte
@@ -319,7 +344,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
       tc::fence_after_sync();
       if (tid == 0) {
         const uint32_t base = tc::smem_u32(stage);
-        const uint32_t bot = (uint32_t)(GD / 8) * SBO;
+        const uint32_t bot = (uint32_t)(GD / 8) * SBO;   // the Xi rows
 #pragma unroll
         for (int ks = 0; ks < KC / F::KI; ++ks) {
           const uint32_t o = ks * 256;
@@ -328,9 +353,18 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
             const uint32_t pa = base + prod_a(pr) * kCovPiece + o;
             const uint32_t pb = base + prod_b(pr) * kCovPiece + o;
             const bool acc = !(ch == 0 && ks == 0 && pr == 0);
-            const uint64_t db = tc::smem_desc(pb, 128, SBO);
-            issue_mma<PREC>(tmem, tc::smem_desc(pa, 128, SBO), db, idesc, acc);
-            issue_mma<PREC>(tmem + 256, tc::smem_desc(pa + bot, 128, SBO), db, idesc, acc);
+            const uint64_t ar = tc::smem_desc(pa, 128, SBO);
+            const uint64_t br = tc::smem_desc(pb, 128, SBO), bi = tc::smem_desc(pb + bot, 128, SBO);
+            if constexpr (STK) {   // A = [Xr ; Xi] (all 128 rows)
+              issue_mma<PREC>(tmem, ar, br, idesc, acc);                // [XrXr^T ; XiXr^T]
+              issue_mma<PREC>(tmem + NA, ar, bi, idesc, acc);           // [XrXi^T ; XiXi^T]
+            } else {
+              const uint64_t ai = tc::smem_desc(pa + bot, 128, SBO);
+              issue_mma<PREC>(tmem, ar, br, idesc, acc);                // Xr Xr^T
+              issue_mma<PREC>(tmem + NA, ai, bi, idesc, acc);           // Xi Xi^T
+              issue_mma<PREC>(tmem + 2 * NA, ai, br, idesc, acc);       // Xi Xr^T
+              issue_mma<PREC>(tmem + 3 * NA, ar, bi, idesc, acc);       // Xr Xi^T
+            }
           }
         }
         tc::mma_commit(&mbar[st]);
@@ -352,36 +386,85 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
     tc::fence_after_sync();
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows i of the
     // tile); warps w and w + 4 take alternate column blocks of 8
-    {
-      const int q4 = warp & 3, hf = warp >> 2;
+    const int q4 = warp & 3, hf = warp >> 2;
+    const uint32_t lb = (uint32_t)(q4 * 32) << 16;
+    const float invB = 1.f / (float)B;
+    const int LDX = D8 + 1;                    // exchange row pitch (floats; odd: no bank conflicts)
+    float* xir = reinterpret_cast<float*>(sm);  // stacked: XiXr rows (the stages are idle now)
+    float* xii = xir + GD * LDX;                //          XiXi rows
+    if constexpr (STK) {
+      // lanes GD .. 2 GD - 1 hold the Xi rows: [XiXr | XiXi] of entry a of
+      // system g in columns g D8 + l; hand them to the Xr lanes through
+      // shared memory
+      if (q4 * 32 < 2 * GD && q4 * 32 + 32 > GD) {   // warp-uniform
+        const int ii = q4 * 32 + lane - GD;
+        const bool xi = ii >= 0 && ii < GD;
+        const int g = xi ? ii / D8 : 0, a = ii - g * D8;
+        for (int cb = hf * 8; cb < NA; cb += 16) {
+          float x0[8], x1[8];
+          in_bounds(NA + cb + 7, Fm::COLS, kSiteTcTmem);   // recorded only
+          tc::tmem_ld8x2(tmem + lb + cb, tmem + lb + NA + cb, x0, x1);
+          if (xi && a < D) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int l = cb + u - g * D8;
+              if (l >= 0 && l < D && in_bounds(ii * LDX + l, GD * LDX, kSiteTcSmem)) {
+                xir[ii * LDX + l] = x0[u];
+                xii[ii * LDX + l] = x1[u];
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (q4 * 32 < GD) {   // warps holding Xr rows (warp-uniform)
       const int i = q4 * 32 + lane;
       const int g = i / D8, a = i - g * D8;
       const long long sys = sys0 + g;
       const bool mine = i < GD && a < D && sys < nsys;
       const float sc = (PREC == kFP16S && i < GD) ? 1.f / sscale[g] : 1.f;   // exact
-      const float invB = 1.f / (float)B;
       double2* out = cov + (size_t)(mine ? sys : 0) * D * D;
       const int gw0 = (q4 * 32) / D8;
       const int gw1 = min(G - 1, (q4 * 32 + 31) / D8);
-      const uint32_t lb = (uint32_t)(q4 * 32) << 16;
       for (int gg = gw0; gg <= gw1; ++gg) {
         for (int cb = hf * 8; cb < D8; cb += 16) {   // warp-uniform bounds
           // one system per tile: a block of columns left of the warp's first
           // row has no l >= a entry
           if (G == 1 && cb + 8 <= q4 * 32) continue;
-          float rr[8], ri[8], ir[8], ii[8];
-          in_bounds(256 + GD + gg * D8 + cb + 7, 512, kSiteTcTmem);   // recorded only
-          tc::tmem_ld8(tmem + lb + gg * D8 + cb, rr);
-          tc::tmem_ld8(tmem + lb + GD + gg * D8 + cb, ri);
-          tc::tmem_ld8(tmem + 256 + lb + gg * D8 + cb, ir);
-          tc::tmem_ld8(tmem + 256 + lb + GD + gg * D8 + cb, ii);
+          float re8[8], im8[8];
+          const uint32_t tcol = tmem + lb + gg * D8 + cb;
+          if constexpr (STK) {
+            float xrxi[8];
+            in_bounds(NA + gg * D8 + cb + 7, Fm::COLS, kSiteTcTmem);   // recorded only
+            tc::tmem_ld8x2(tcol, tcol + NA, re8, xrxi);
+            if (mine && g == gg) {
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int l = cb + u;
+                const int xo = (l >= a && l < D) ? i * LDX + l : 0;
+                re8[u] += xii[xo];             // XrXr + XiXi
+                im8[u] = xir[xo] - xrxi[u];    // XiXr - XrXi
+              }
+            }
+          } else {
+            in_bounds(3 * NA + gg * D8 + cb + 7, Fm::COLS, kSiteTcTmem);   // recorded only
+            float ii8[8], ri8[8];
+            tc::tmem_ld8x2(tcol, tcol + NA, re8, ii8);
+            tc::tmem_ld8x2(tcol + 2 * NA, tcol + 3 * NA, im8, ri8);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              re8[u] += ii8[u];
+              im8[u] -= ri8[u];
+            }
+          }
           if (mine && g == gg) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
               const int l = cb + u;
               if (l >= a && l < D) {   // R[a][l], stored conjugated at [l][a]
-                const float re = (rr[u] + ii[u]) * sc * sc * invB;
-                const float im = l == a ? 0.f : (ir[u] - ri[u]) * sc * sc * invB;
+                const float re = re8[u] * sc * sc * invB;
+                const float im = l == a ? 0.f : im8[u] * sc * sc * invB;
                 const double dre = ff::f2d_exact(re), dim = ff::f2d_exact(im);
                 const long long ext = nsys * D * D, o = sys * D * D;
                 if (in_bounds(o + (long long)l * D + a, ext, kSiteTcOut))
@@ -395,7 +478,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
       }
     }
     tc::fence_before_sync();
-    __syncthreads();  // TMEM reads done before the next tile's MMAs overwrite it
+    __syncthreads();  // TMEM and exchange reads done before the next tile overwrites them
     tc::fence_after_sync();
   }
   if (!ok) {
@@ -405,7 +488,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+  if (warp == 0) tc::tmem_dealloc(tmem, Fm::COLS);
 }
 
 // ---- apply ------------------------------------------------------------------------
@@ -413,7 +496,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
 constexpr int kAppRB = 64;                    // bytes of one operand row per chunk (4 core matrices)
 constexpr int kAppA = 128 * kAppRB;           // A piece: 128 cells (8 KB)
 constexpr int kAppB = 256 * kAppRB;           // B piece: at most 256 weight rows (16 KB)
-constexpr int kAppU = 24;                     // staging units per warp and chunk ((16 + 32) x 4 / 8)
+constexpr int kAppU = 16;                     // staging units per warp and chunk ((16 + 32 x 2 / 4) x 4 / 8)
 
 // two stages of the pieces of 128 cell rows and NP weight rows
 template <int PREC>
@@ -447,7 +530,10 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
   const int nbt = B < 128 ? 128 / B : 1;
   const int Nq = nbt * S;                     // weight vectors per tile
   const int nchunks = (K2 + KC - 1) / KC;
-  const int unitsA = 16 * NCM, units = unitsA + (NP / 8) * NCM;
+  // A units: one core matrix of 8 cell rows; B units: a pair of core
+  // matrices along K of one 8-row group (4 weight vectors), each lane one
+  // weight element written to the vector's two rows
+  const int unitsA = 16 * NCM, units = unitsA + (NP / 8) * (NCM / 2);
 
   for (int i = tid; i < 2 * STAGE / 4; i += kThreads) reinterpret_cast<uint32_t*>(sm)[i] = 0u;
   if (warp == 0) tc::tmem_alloc(&tmem_base, tmem_cols);
@@ -510,10 +596,14 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
       __syncthreads();
     }
     // K elements kap0 .. kap0 + KC - 1 of the A rows (cells) and of the B
-    // rows (weights); a unit is one core matrix, lane l takes row 8 rg + l/4
-    // and K elements 4 cm + (l & 3) (tf32) or one re/im pair (16-bit).  Warp
-    // w takes units w, w + 8, ... (at most kAppU); the next chunk's loads are
-    // issued before this chunk's barrier and MMAs.
+    // rows (weights).  An A unit is one core matrix: lane l takes row
+    // 8 rg + l/4 and K elements 4 cm + (l & 3) (tf32) or one re/im pair
+    // (16-bit).  A B unit is two core matrices cm = 2 j + h (h = l / 16) of
+    // one 8-row group: lane l takes weight vector 4 rg + (l / 4) % 4 and word
+    // l & 3 of both its rows, [wr, wi] (even) and [-wi, wr] (odd), from one
+    // load and one split (pieces of -x are minus those of x).  Warp w takes
+    // units w, w + 8, ... (at most kAppU); the next chunk's loads are issued
+    // before this chunk's barrier and MMAs.
     float2 v[kAppU];
     auto load_chunk = [&](int ch) {
       const int kap0 = ch * KC;
@@ -522,20 +612,22 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
         const int unit = warp + uu * (kThreads / 32);
         v[uu] = make_float2(0.f, 0.f);
         if (unit < units) {
-          const bool isA = unit < unitsA;
-          const int ul = isA ? unit : unit - unitsA;
-          const int row = (ul / NCM) * 8 + (lane >> 2), cmk = ul % NCM;
-          const int d = PREC == kTF32X3 ? (kap0 + cmk * 4 + (lane & 3)) >> 1
-                                        : (kap0 + cmk * 8 + (lane & 3) * 2) >> 1;
-          if (d < D) {
-            if (isA) {
-              if (r0 + row < R &&
-                  in_bounds(colbase[d] + r0 + row, ((long long)C * K - 1) * ldr + R, kSiteTcIn))
-                v[uu] = __ldg(dop + colbase[d] + r0 + row);
-            } else {
-              const long long wb = wbase[row];
-              if (wb >= 0 && in_bounds(wb + d, (long long)K * NB * S * D, kSiteTcIn)) v[uu] = __ldg(wts + wb + d);
-            }
+          if (unit < unitsA) {
+            const int row = (unit / NCM) * 8 + (lane >> 2), cmk = unit % NCM;
+            const int d = PREC == kTF32X3 ? (kap0 + cmk * 4 + (lane & 3)) >> 1
+                                          : (kap0 + cmk * 8 + (lane & 3) * 2) >> 1;
+            if (d < D && r0 + row < R &&
+                in_bounds(colbase[d] + r0 + row, ((long long)C * K - 1) * ldr + R, kSiteTcIn))
+              v[uu] = __ldg(dop + colbase[d] + r0 + row);
+          } else {
+            const int ub = unit - unitsA;
+            const int q = (ub / (NCM / 2)) * 4 + ((lane >> 2) & 3);
+            const int cm = 2 * (ub % (NCM / 2)) + (lane >> 4);
+            const int d = PREC == kTF32X3 ? (kap0 + cm * 4 + (lane & 3)) >> 1
+                                          : (kap0 + cm * 8 + (lane & 3) * 2) >> 1;
+            const long long wb = wbase[2 * q];
+            if (d < D && wb >= 0 && in_bounds(wb + d, (long long)K * NB * S * D, kSiteTcIn))
+              v[uu] = __ldg(wts + wb + d);
           }
         }
       }
@@ -558,33 +650,70 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
       for (int uu = 0; uu < kAppU; ++uu) {
         const int unit = warp + uu * (kThreads / 32);
         if (unit >= units) continue;
-        const bool isA = unit < unitsA;
-        const int ul = isA ? unit : unit - unitsA;
-        const int row = (ul / NCM) * 8 + (lane >> 2), cmk = ul % NCM;
-        const int off = (isA ? 0 : kAppA) + (ul / NCM) * SBO + cmk * 128 + (lane >> 2) * 16 +
-                        (lane & 3) * 4;
-        if (!in_bounds(off + 3, isA ? kAppA : PIECE, kSiteTcSmem)) continue;   // the word's last byte
-        // the pair this row holds at (re, im) positions: x, or the weight
-        // rows (wr, wi) and (-wi, wr)
-        float2 e = v[uu];
-        if (!isA && (row & 1)) e = make_float2(-e.y, e.x);
-        if constexpr (PREC == kTF32X3) {
-          const int kap = kap0 + cmk * 4 + (lane & 3);
-          uint32_t w[2];
-          split_tf32((kap & 1) ? e.y : e.x, w);
-          *reinterpret_cast<uint32_t*>(stage + off) = w[0];
-          *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
-        } else if constexpr (PREC == kBF16X3) {
-          uint32_t w[3];
-          split_bf16(e.x, e.y, w);
+        const float2 e = v[uu];
+        if (unit < unitsA) {
+          const int rg = unit / NCM, cmk = unit % NCM;
+          const int off = rg * SBO + cmk * 128 + (lane >> 2) * 16 + (lane & 3) * 4;
+          if (!in_bounds(off + 3, kAppA, kSiteTcSmem)) continue;   // the word's last byte
+          if constexpr (PREC == kTF32X3) {
+            const int kap = kap0 + cmk * 4 + (lane & 3);
+            uint32_t w[2];
+            split_tf32((kap & 1) ? e.y : e.x, w);
+            *reinterpret_cast<uint32_t*>(stage + off) = w[0];
+            *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
+          } else if constexpr (PREC == kBF16X3) {
+            uint32_t w[3];
+            split_bf16(e.x, e.y, w);
 #pragma unroll
-          for (int pc = 0; pc < 3; ++pc) *reinterpret_cast<uint32_t*>(stage + pc * PIECE + off) = w[pc];
+            for (int pc = 0; pc < 3; ++pc) *reinterpret_cast<uint32_t*>(stage + pc * PIECE + off) = w[pc];
+          } else {
+            uint32_t w[2];
+            split_f16(e.x * xsc_s, e.y * xsc_s, w);
+            *reinterpret_cast<uint32_t*>(stage + off) = w[0];
+            *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
+          }
         } else {
-          const float sc = isA ? xsc_s : ((row >> 1) < Nq ? wsc[row >> 1] : 1.f);
-          uint32_t w[2];
-          split_f16(e.x * sc, e.y * sc, w);
-          *reinterpret_cast<uint32_t*>(stage + off) = w[0];
-          *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
+          const int ub = unit - unitsA;
+          const int rg = ub / (NCM / 2), q4 = (lane >> 2) & 3, h = lane >> 4;
+          const int cm = 2 * (ub % (NCM / 2)) + h;
+          const int offE = kAppA + rg * SBO + cm * 128 + (2 * q4) * 16 + (lane & 3) * 4;
+          const int offO = offE + 16;   // the odd row of the same vector
+          if (!in_bounds(offO + 3, PIECE, kSiteTcSmem)) continue;
+          // the first store takes even rows in lanes 0-15 and odd rows in
+          // lanes 16-31 (and the second the other way round), so each store
+          // covers all 32 banks
+          const int o1 = h ? offO : offE, o2 = h ? offE : offO;
+          constexpr int NPC = F::NPC;
+          uint32_t we[NPC], wo[NPC];
+          if constexpr (PREC == kTF32X3) {
+            // word l & 3 of a row is K element 2 d + (l & 1): even row wr, wi;
+            // odd row -wi, wr
+            uint32_t pr_[2], pi_[2];
+            split_tf32(e.x, pr_);
+            split_tf32(e.y, pi_);
+            const bool im_word = (lane & 1) != 0;
+#pragma unroll
+            for (int pc = 0; pc < 2; ++pc) {
+              we[pc] = im_word ? pi_[pc] : pr_[pc];
+              wo[pc] = im_word ? pr_[pc] : (pi_[pc] ^ 0x80000000u);
+            }
+          } else {
+            // 16-bit pairs (re in the low half): odd word = (-im, re)
+            if constexpr (PREC == kBF16X3) {
+              split_bf16(e.x, e.y, we);
+            } else {
+              const int q = rg * 4 + q4;
+              const float sc = q < Nq ? wsc[q] : 1.f;
+              split_f16(e.x * sc, e.y * sc, we);
+            }
+#pragma unroll
+            for (int pc = 0; pc < NPC; ++pc) wo[pc] = ((we[pc] >> 16) ^ 0x8000u) | (we[pc] << 16);
+          }
+#pragma unroll
+          for (int pc = 0; pc < NPC; ++pc) {
+            *reinterpret_cast<uint32_t*>(stage + pc * PIECE + o1) = h ? wo[pc] : we[pc];
+            *reinterpret_cast<uint32_t*>(stage + pc * PIECE + o2) = h ? we[pc] : wo[pc];
+          }
         }
       }
       if (ch + 1 < nchunks) load_chunk(ch + 1);
@@ -673,25 +802,39 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
   if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
 }
 
-template <int PREC>
-cudaError_t launch_cov(const float2* dop, double2* cov, int C, int K, int R, int ldr, int T, int B,
-                       bool lower_only, DeviceStatus* status, cudaStream_t s, int wait_polls) {
+template <int PREC, bool STK>
+cudaError_t launch_cov_form(const float2* dop, double2* cov, int C, int K, int R, int ldr, int T, int B,
+                            bool lower_only, DeviceStatus* status, cudaStream_t s, int wait_polls) {
   const int D = C * T;
   const int NB = R / B;
   const int D8 = (D + 7) / 8 * 8;
-  const int G = 128 / D8;
+  const int G = CovForm<STK>::GROWS / D8;
   const long long nsys = (long long)K * NB;
   const long long ntiles = (nsys + G - 1) / G;
   const size_t smem = cov_smem<PREC>();
   static int set_bytes[64] = {0};
-  cudaError_t e = ensure_smem(covariance_tcx_kernel<PREC>, smem, set_bytes);
+  cudaError_t e = ensure_smem(covariance_tcx_kernel<PREC, STK>, smem, set_bytes);
   if (e != cudaSuccess) return e;
-  const long long blocks = ntiles < 152 ? ntiles : 152;   // one CTA per SM (TMEM: 512 columns)
+  // resident CTAs per SM: registers and shared memory (occupancy query),
+  // and no more than the SM's 512 TMEM columns hold
+  int per_sm = resident_ctas(covariance_tcx_kernel<PREC, STK>, kThreads, smem);
+  if (per_sm > 512 / CovForm<STK>::COLS) per_sm = 512 / CovForm<STK>::COLS;
+  const long long cap = 152LL * per_sm;
+  const long long blocks = ntiles < cap ? ntiles : cap;
   return launch_or_defer(s, [=](cudaStream_t st) {
-    covariance_tcx_kernel<PREC><<<(unsigned)blocks, kThreads, smem, st>>>(
+    covariance_tcx_kernel<PREC, STK><<<(unsigned)blocks, kThreads, smem, st>>>(
         dop, cov, C, K, ldr, T, B, NB, D8, G, ntiles, lower_only ? 1 : 0, status, wait_polls);
     return cudaGetLastError();
   });
+}
+
+template <int PREC>
+cudaError_t launch_cov(const float2* dop, double2* cov, int C, int K, int R, int ldr, int T, int B,
+                       bool lower_only, DeviceStatus* status, cudaStream_t s, int wait_polls) {
+  const int D8 = (C * T + 7) / 8 * 8;
+  if (D8 <= 64)   // the stacked form: [Xr ; Xi] fill the 128 rows of M
+    return launch_cov_form<PREC, true>(dop, cov, C, K, R, ldr, T, B, lower_only, status, s, wait_polls);
+  return launch_cov_form<PREC, false>(dop, cov, C, K, R, ldr, T, B, lower_only, status, s, wait_polls);
 }
 
 template <int PREC>

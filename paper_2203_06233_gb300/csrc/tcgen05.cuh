@@ -48,6 +48,10 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction-descriptor bit that negates the A operand (bit 13, for
+// kind::f16 and kind::tf32): D (+)= (-A) * B^T.
+constexpr uint32_t kIdescNegateA = 1u << 13;
+
 __device__ __forceinline__ uint32_t to_tf32(float v) {  // round to nearest, ties away
   uint32_t t;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
@@ -115,16 +119,36 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;"); }
 
-// 8 consecutive FP32 columns of this thread's TMEM lane.
+// 8 consecutive FP32 columns of this thread's TMEM lane (the load and its
+// wait in one asm statement, so no use of a result comes before the wait).
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               "tcgen05.wait::ld.sync.aligned;"
                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
                : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
   v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1); v[2] = __uint_as_float(r2);
   v[3] = __uint_as_float(r3); v[4] = __uint_as_float(r4); v[5] = __uint_as_float(r5);
   v[6] = __uint_as_float(r6); v[7] = __uint_as_float(r7);
+}
+
+// 8 consecutive FP32 columns at each of two TMEM addresses of this thread's
+// lane, with one wait for both loads (inside the same asm statement, so no
+// use of a result can be scheduled before the wait).
+__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, uint32_t tb, float (&a)[8], float (&b)[8]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta), "r"(tb));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    a[i] = __uint_as_float(r[i]);
+    b[i] = __uint_as_float(r[8 + i]);
+  }
 }
 
 }  // namespace tc
