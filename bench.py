@@ -281,8 +281,11 @@ def block_errors(outs_blocks, refs):
     return {"normwise": (num / den) ** 0.5, "max_cell": worst, "blocks": len(refs)}
 
 
-def kernel_figures(spec, prec, kt, pk, refine=1, solver=0):
-    """Each step against its own bound: achieved rate and fraction."""
+def kernel_figures(spec, prec, kt, pk, refine=1, solver=0, used=None):
+    """Each step against its own bound: achieved rate and fraction.  `used`
+    (the leg's kernels_used) says which kernel ran the covariance and the
+    apply: a mixed plan keeps the FP32 kernel of a step where the autotuner
+    found it faster."""
     if not kt:
         return {}
     C, P, K, R, T, B, S = spec.dims()
@@ -305,32 +308,45 @@ def kernel_figures(spec, prec, kt, pk, refine=1, solver=0):
     # covariance through the step call (full Hermitian c128 output)
     cov_bytes = 8.0 * C * K * R + 16.0 * K * NB * D * D
     apply_bytes = 8.0 * C * K * R + 8.0 * K * NB * S * D + 4.0 * S * K * R
-    if prec == 0:
+    used = used or {}
+    fp32_cov = prec == 0 or used.get("covariance", "").startswith("FP32")
+    fp32_app = prec == 0 or used.get("apply", "").startswith("FP32")
+    if fp32_cov:
         cplx = 1.0 * K * NB * B * (T * C * C - C * (C - 1) // 2)
         out["covariance"] = {"ms": kt["covariance"], "bound": "alu", "fp32_instr": 20.0 * cplx,
                              "frac": 20.0 * cplx / kt["covariance"] / 1e9 / (pk["fp32_tflops"] / 2),
                              "hbm_frac": cov_bytes / kt["covariance"] / 1e6 / pk["hbm_gbs"]}
+    if fp32_app:
         af = 8.0 * K * R * S * D
         out["apply"] = {"ms": kt["apply"], "bound": "alu", "fp32_flops": af,
                         "frac": af / kt["apply"] / 1e9 / pk["fp32_tflops"],
                         "hbm_frac": apply_bytes / kt["apply"] / 1e6 / pk["hbm_gbs"]}
-    else:
+    if prec != 0:
         nprod = 6 if prec == 1 else 3
         peak = pk["bf16_tflops"] / (2.0 if prec == 2 else 1.0)
-        # tensor work the kernels issue: covariance 2 x (2 G D8) x 128 x B real
-        # MACs per G systems (D8 = D rounded up to 8, G = 128 // D8); apply
-        # 128 x N x 2D per 128-cell tile (N = 2 S per block in the tile)
+        # tensor work the kernels issue (real MACs), D8 = D rounded up to 8 and
+        # NA = G D8 rounded up to 16:
+        #   covariance, D8 <= 64 (stacked [Xr ; Xi] rows, G = 64 // D8 systems
+        #   per tile): 2 MMAs of 128 x NA per K step; D8 > 64 (G = 1): 4 of
+        #   128 x NA; K = B cells, nprod products;
+        #   apply: 128 x NP x 2D per 128-cell tile (NP = 2 S per block in the
+        #   tile, rounded up to 16)
         D8 = (D + 7) // 8 * 8
-        G = 128 // D8
-        cov_mac = 2.0 * (2 * G * D8) * 128 * B * np.ceil(K * NB / G) * nprod
+        G, nmma = (64 // D8, 2) if D8 <= 64 else (1, 4)
+        NA = -(-G * D8 // 16) * 16
+        cov_mac = nmma * 128.0 * NA * B * np.ceil(K * NB / G) * nprod
         nbt = 128 // B if B < 128 else 1
         NP = -(-2 * nbt * S // 16) * 16
         app_mac = 128.0 * NP * 2 * D * K * np.ceil(R / 128) * nprod
-        # useful work: Hermitian half not exploited; every computed entry of a
-        # system's own block is used
+        # useful work: the four real blocks of each system's own D x D
+        # covariance (the Hermitian half is not exploited), the apply's
+        # 4 real products per complex one
         cov_useful = 2.0 * 4 * D * D * B * K * NB * nprod
-        for name, mac, useful, byts in (("covariance", cov_mac, cov_useful, cov_bytes),
-                                        ("apply", app_mac, 2.0 * 4 * D * S * K * R * nprod, apply_bytes)):
+        for name, mac, useful, byts, skip in (
+                ("covariance", cov_mac, cov_useful, cov_bytes, fp32_cov),
+                ("apply", app_mac, 2.0 * 4 * D * S * K * R * nprod, apply_bytes, fp32_app)):
+            if skip:
+                continue
             out[name] = {"ms": kt[name], "bound": "tensor", "issued_tflops": 2 * mac / kt[name] / 1e9,
                          "useful_tflops": useful / kt[name] / 1e9,
                          "frac": 2 * mac / kt[name] / 1e9 / peak,
@@ -499,7 +515,7 @@ def run_gpu(args):
         # ---- headline: the mixed leg's timed region ----
         total_ms, value = aggregate(mleg["ms_per_step"] * sub.steps, cells * sub.steps, world, dev)
         ms_per_step = total_ms / sub.steps
-        kern = kernel_figures(spec, mprec, mleg["kernels_ms"], pk)
+        kern = kernel_figures(spec, mprec, mleg["kernels_ms"], pk, used=mleg["kernels_used"])
         solve_kind = 3 if C * T > 32 else list(mleg["tuning"].values())[0][7]
         roofline = {"kernel": SOLVE_KERNELS.get(solve_kind, "solve"),
                     "bound": "alu", "achieved": kern["solve"]["achieved_tflops"],
@@ -560,7 +576,8 @@ def run_gpu(args):
         if ilabel in legs:
             ileg = legs[ilabel]
             line["mixed_ir"] = dict(ileg, value=world * cells / (ileg["ms_per_step"] * 1e-3),
-                                    kernels=kernel_figures(spec, mprec, ileg["kernels_ms"], pk, solver=1))
+                                    kernels=kernel_figures(spec, mprec, ileg["kernels_ms"], pk, solver=1,
+                                                           used=ileg["kernels_used"]))
         if errors:
             line["errors_vs_oracle"] = errors
         if cpu is not None:
@@ -616,11 +633,13 @@ def workload_keys(args, name, rank, dev, stream, flush, pk):
     value = {lb: cells / (legs[lb]["ms_per_step"] * 1e-3) for lb in legs}
     res = {"config": workload_config(spec, name),
            "mixed": dict(legs[mlabel], value=value[mlabel],
-                         kernels=kernel_figures(spec, mprec, legs[mlabel]["kernels_ms"], pk)),
+                         kernels=kernel_figures(spec, mprec, legs[mlabel]["kernels_ms"], pk,
+                                                used=legs[mlabel]["kernels_used"])),
            "fp32": dict(legs[flabel], value=value[flabel],
                         kernels=kernel_figures(spec, 0, legs[flabel]["kernels_ms"], pk)),
            "mixed_ir": dict(legs[ilabel], value=value[ilabel],
-                            kernels=kernel_figures(spec, mprec, legs[ilabel]["kernels_ms"], pk, solver=1)),
+                            kernels=kernel_figures(spec, mprec, legs[ilabel]["kernels_ms"], pk, solver=1,
+                                                   used=legs[ilabel]["kernels_used"])),
            "mixed_vs_fp32": value[mlabel] / value[flabel], "errors_vs_oracle": errors,
            "cpu_baseline": cpu}
     if name == "standard":
