@@ -41,6 +41,14 @@ namespace {
 
 __device__ __forceinline__ int pidx(int i, int l) { return i * (i + 1) / 2 + l; }
 
+// Per-team strides of the refinement kernel's shared-memory arrays, rounded
+// up to an odd number of elements: the 32 / TS teams of a warp then read the
+// same offset of their own arrays from distinct banks.  (Dp = D (D + 1) / 2
+// is even for D = 8, 12 and 16: entries at an even stride put two, four or
+// eight teams on the same banks.  The FP64 kernels keep the even strides:
+// bound by the FP64 pipe, they measured no faster with odd ones.)
+__host__ __device__ constexpr int odd_up(int n) { return n | 1; }
+
 // acc -= a * b
 __device__ __forceinline__ void cfms(double2& acc, double2 a, double2 b) {
   acc.x = fma(-a.x, b.x, acc.x);
@@ -622,11 +630,12 @@ __host__ __device__ constexpr size_t mir_warp_bytes(int D, int G, bool sep) {
   // G double-float matrices [Dp] (the SEP exchange area [D][32] float4
   // overlays them when they are large enough, else follows), G FP32 factors
   // [Dp], the per-lane residual columns [D][32] float2, G pivot columns [D]
-  // float2, G pivot reciprocals [D] float
-  return ((size_t)G * (D * (D + 1) / 2) +
-          (sep && G * (D * (D + 1) / 2) < 32 * D ? (size_t)D * 32 : 0)) * 16 +
-         (size_t)G * (D * (D + 1) / 2) * 8 + (size_t)D * 32 * 8 + (size_t)G * D * 8 +
-         ((size_t)G * D * 4 + 15) / 16 * 16;
+  // float2, G pivot reciprocals [D] float; per-team strides odd_up(Dp) and
+  // odd_up(D)
+  return ((size_t)G * odd_up(D * (D + 1) / 2) +
+          (sep && G * odd_up(D * (D + 1) / 2) < 32 * D ? (size_t)D * 32 : 0)) * 16 +
+         ((size_t)G * odd_up(D * (D + 1) / 2) * 8 + 15) / 16 * 16 + (size_t)D * 32 * 8 +
+         ((size_t)G * odd_up(D) * 8 + 15) / 16 * 16 + ((size_t)G * odd_up(D) * 4 + 15) / 16 * 16;
 }
 
 // A compensated sum of double-float products (Dot2 of Ogita, Rump and Oishi,
@@ -668,16 +677,18 @@ solve_mir_kernel(const double2* __restrict__ cov, float2* __restrict__ wts,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   const int G = 32 / TS, team = lane / TS, tl = lane - team * TS;
-  const bool alias = G * Dp >= 32 * D;
+  constexpr int LS = odd_up(Dp), CS = odd_up(D);   // per-team strides
+  const bool alias = G * LS >= 32 * D;
   char* wb = reinterpret_cast<char*>(smf) + warp * mir_warp_bytes(D, G, SEP);
-  float4* Ad = reinterpret_cast<float4*>(wb) + (size_t)team * Dp;
-  float4* Wf = reinterpret_cast<float4*>(wb) + (alias ? 0 : (size_t)G * Dp);
-  char* fb = wb + ((size_t)G * Dp + (SEP && !alias ? (size_t)D * 32 : 0)) * 16;
-  float2* Lf = reinterpret_cast<float2*>(fb) + (size_t)team * Dp;
-  float2* Rs = reinterpret_cast<float2*>(fb + (size_t)G * Dp * 8) + lane;     // [D][32]
-  char* pb = fb + (size_t)G * Dp * 8 + (size_t)D * 32 * 8;
-  float2* colf = reinterpret_cast<float2*>(pb) + (size_t)team * D;
-  float* rdf = reinterpret_cast<float*>(pb + (size_t)G * D * 8) + (size_t)team * D;
+  float4* Ad = reinterpret_cast<float4*>(wb) + (size_t)team * LS;
+  float4* Wf = reinterpret_cast<float4*>(wb) + (alias ? 0 : (size_t)G * LS);
+  char* fb = wb + ((size_t)G * LS + (SEP && !alias ? (size_t)D * 32 : 0)) * 16;
+  float2* Lf = reinterpret_cast<float2*>(fb) + (size_t)team * LS;
+  char* rb = fb + ((size_t)G * LS * 8 + 15) / 16 * 16;
+  float2* Rs = reinterpret_cast<float2*>(rb) + lane;     // [D][32]
+  char* pb = rb + (size_t)D * 32 * 8;
+  float2* colf = reinterpret_cast<float2*>(pb) + (size_t)team * CS;
+  float* rdf = reinterpret_cast<float*>(pb + ((size_t)G * CS * 8 + 15) / 16 * 16) + (size_t)team * CS;
 
   for (long long base = ((long long)blockIdx.x * nw + warp) * G; base < nsys;
        base += (long long)gridDim.x * nw * G) {
