@@ -270,15 +270,26 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
     // w, w + 8, ... (at most kCovU of them).  The next chunk's loads are
     // issued before this chunk's barrier and MMAs, so their latency overlaps
     // both.
+    // Per tile, each lane's unit uu covers row (warp + 8 uu) / NCM * 8 + l/4
+    // (its dop offset and, for FP16S, its system's scale fetched here once)
+    // and the same cells of every chunk ((warp % NCM) CPW + (l & 3) CPL on).
+    long long rbase[kCovU];
+    float rsc[kCovU];
+#pragma unroll
+    for (int uu = 0; uu < kCovU; ++uu) {
+      const int unit = warp + uu * (kThreads / 32);
+      const int p = (unit / Fm::NCM) * 8 + (lane >> 2);
+      rbase[uu] = unit < units ? rowbase[p] : -1;
+      rsc[uu] = (PREC == kFP16S && unit < units) ? sscale[p / D8] : 1.f;
+    }
+    const int jl = (warp % Fm::NCM) * CPW + (lane & 3) * CPL;
     float2 v[kCovU][CPL];
     auto load_chunk = [&](int ch) {
       const int c0 = ch * KC;
 #pragma unroll
       for (int uu = 0; uu < kCovU; ++uu) {
-        const int unit = warp + uu * (kThreads / 32);
-        const int p = (unit / Fm::NCM) * 8 + (lane >> 2);
-        const int j = c0 + (unit % Fm::NCM) * CPW + (lane & 3) * CPL;
-        const long long base = unit < units ? rowbase[p] : -1;
+        const int j = c0 + jl;
+        const long long base = rbase[uu];
 #pragma unroll
         for (int cc = 0; cc < CPL; ++cc)
           v[uu][cc] = (base >= 0 && j + cc < B &&
@@ -326,7 +337,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
             *reinterpret_cast<uint32_t*>(stage + pc * kCovPiece + offi) = wi[pc];
           }
         } else {
-          const float sc = sscale[(rg * 8 + (lane >> 2)) / D8];
+          const float sc = rsc[uu];
           uint32_t wr[2], wi[2];
           split_f16(v[uu][0].x * sc, v[uu][1].x * sc, wr);
           split_f16(v[uu][0].y * sc, v[uu][1].y * sc, wi);
@@ -604,32 +615,43 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
     // load and one split (pieces of -x are minus those of x).  Warp w takes
     // units w, w + 8, ... (at most kAppU); the next chunk's loads are issued
     // before this chunk's barrier and MMAs.
+    // With NCM = 4 the 64 A units are units 0-63: warp w's unit uu < 8 is
+    // row group (w >> 2) + 2 uu, core matrix w & 3.  Its B unit vb (unit
+    // 64 + w + 8 vb) is row group (w >> 1) + 4 vb, core matrices 2 (w & 1) + h.
+    // Row offsets, weight-vector offsets and scales are fixed per tile; the
+    // snapshot entry and the weight element per chunk.
+    static_assert(NCM == 4 && kAppU == 16, "unit layout");
+    constexpr int kAU = 8, kBU = kAppU - kAU;
+    const int unitsB = units - unitsA;
+    const int cmA = warp & 3, h = lane >> 4, q4 = (lane >> 2) & 3;
+    const int cmB = 2 * (warp & 1) + h;
+    long long wbq[kBU];
+    float wscq[kBU];
+#pragma unroll
+    for (int vb = 0; vb < kBU; ++vb) {
+      const int ub = warp + 8 * vb;
+      const int q = ((warp >> 1) + 4 * vb) * 4 + q4;
+      wbq[vb] = ub < unitsB ? wbase[2 * q] : -1;
+      wscq[vb] = (PREC == kFP16S && ub < unitsB && q < Nq) ? wsc[q] : 1.f;
+    }
     float2 v[kAppU];
     auto load_chunk = [&](int ch) {
       const int kap0 = ch * KC;
+      const int dA = PREC == kTF32X3 ? (kap0 + cmA * 4 + (lane & 3)) >> 1 : (kap0 + cmA * 8 + (lane & 3) * 2) >> 1;
+      const int dB = PREC == kTF32X3 ? (kap0 + cmB * 4 + (lane & 3)) >> 1 : (kap0 + cmB * 8 + (lane & 3) * 2) >> 1;
+      const long long baseA = dA < D ? colbase[dA] + r0 : -1;
 #pragma unroll
-      for (int uu = 0; uu < kAppU; ++uu) {
-        const int unit = warp + uu * (kThreads / 32);
-        v[uu] = make_float2(0.f, 0.f);
-        if (unit < units) {
-          if (unit < unitsA) {
-            const int row = (unit / NCM) * 8 + (lane >> 2), cmk = unit % NCM;
-            const int d = PREC == kTF32X3 ? (kap0 + cmk * 4 + (lane & 3)) >> 1
-                                          : (kap0 + cmk * 8 + (lane & 3) * 2) >> 1;
-            if (d < D && r0 + row < R &&
-                in_bounds(colbase[d] + r0 + row, ((long long)C * K - 1) * ldr + R, kSiteTcIn))
-              v[uu] = __ldg(dop + colbase[d] + r0 + row);
-          } else {
-            const int ub = unit - unitsA;
-            const int q = (ub / (NCM / 2)) * 4 + ((lane >> 2) & 3);
-            const int cm = 2 * (ub % (NCM / 2)) + (lane >> 4);
-            const int d = PREC == kTF32X3 ? (kap0 + cm * 4 + (lane & 3)) >> 1
-                                          : (kap0 + cm * 8 + (lane & 3) * 2) >> 1;
-            const long long wb = wbase[2 * q];
-            if (d < D && wb >= 0 && in_bounds(wb + d, (long long)K * NB * S * D, kSiteTcIn))
-              v[uu] = __ldg(wts + wb + d);
-          }
-        }
+      for (int uu = 0; uu < kAU; ++uu) {
+        const int row = (warp >> 2) * 8 + 16 * uu + (lane >> 2);
+        v[uu] = (baseA >= 0 && r0 + row < R &&
+                 in_bounds(baseA + row, ((long long)C * K - 1) * ldr + R, kSiteTcIn))
+                    ? __ldg(dop + baseA + row) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int vb = 0; vb < kBU; ++vb) {
+        const long long wb = wbq[vb];
+        v[kAU + vb] = (dB < D && wb >= 0 && in_bounds(wb + dB, (long long)K * NB * S * D, kSiteTcIn))
+                          ? __ldg(wts + wb + dB) : make_float2(0.f, 0.f);
       }
     };
     if (ok) load_chunk(0);
@@ -647,73 +669,69 @@ apply_tcx_kernel(const float2* __restrict__ dop, const float2* __restrict__ wts,
       if (!ok) break;
       const int kap0 = ch * KC;
 #pragma unroll
-      for (int uu = 0; uu < kAppU; ++uu) {
-        const int unit = warp + uu * (kThreads / 32);
-        if (unit >= units) continue;
+      for (int uu = 0; uu < kAU; ++uu) {   // A: cell rows
         const float2 e = v[uu];
-        if (unit < unitsA) {
-          const int rg = unit / NCM, cmk = unit % NCM;
-          const int off = rg * SBO + cmk * 128 + (lane >> 2) * 16 + (lane & 3) * 4;
-          if (!in_bounds(off + 3, kAppA, kSiteTcSmem)) continue;   // the word's last byte
-          if constexpr (PREC == kTF32X3) {
-            const int kap = kap0 + cmk * 4 + (lane & 3);
-            uint32_t w[2];
-            split_tf32((kap & 1) ? e.y : e.x, w);
-            *reinterpret_cast<uint32_t*>(stage + off) = w[0];
-            *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
-          } else if constexpr (PREC == kBF16X3) {
-            uint32_t w[3];
-            split_bf16(e.x, e.y, w);
+        const int off = ((warp >> 2) + 2 * uu) * SBO + cmA * 128 + (lane >> 2) * 16 + (lane & 3) * 4;
+        if (!in_bounds(off + 3, kAppA, kSiteTcSmem)) continue;   // the word's last byte
+        if constexpr (PREC == kTF32X3) {
+          const int kap = kap0 + cmA * 4 + (lane & 3);
+          uint32_t w[2];
+          split_tf32((kap & 1) ? e.y : e.x, w);
+          *reinterpret_cast<uint32_t*>(stage + off) = w[0];
+          *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
+        } else if constexpr (PREC == kBF16X3) {
+          uint32_t w[3];
+          split_bf16(e.x, e.y, w);
 #pragma unroll
-            for (int pc = 0; pc < 3; ++pc) *reinterpret_cast<uint32_t*>(stage + pc * PIECE + off) = w[pc];
-          } else {
-            uint32_t w[2];
-            split_f16(e.x * xsc_s, e.y * xsc_s, w);
-            *reinterpret_cast<uint32_t*>(stage + off) = w[0];
-            *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
+          for (int pc = 0; pc < 3; ++pc) *reinterpret_cast<uint32_t*>(stage + pc * PIECE + off) = w[pc];
+        } else {
+          uint32_t w[2];
+          split_f16(e.x * xsc_s, e.y * xsc_s, w);
+          *reinterpret_cast<uint32_t*>(stage + off) = w[0];
+          *reinterpret_cast<uint32_t*>(stage + PIECE + off) = w[1];
+        }
+      }
+#pragma unroll
+      for (int vb = 0; vb < kBU; ++vb) {   // B: weight rows
+        if (warp + 8 * vb >= unitsB) continue;
+        const float2 e = v[kAU + vb];
+        const int rg = (warp >> 1) + 4 * vb;
+        const int offE = kAppA + rg * SBO + cmB * 128 + (2 * q4) * 16 + (lane & 3) * 4;
+        const int offO = offE + 16;   // the odd row of the same vector
+        if (!in_bounds(offO + 3, PIECE, kSiteTcSmem)) continue;
+        // the first store takes even rows in lanes 0-15 and odd rows in
+        // lanes 16-31 (and the second the other way round), so each store
+        // covers all 32 banks
+        const int o1 = h ? offO : offE, o2 = h ? offE : offO;
+        constexpr int NPC = F::NPC;
+        uint32_t we[NPC], wo[NPC];
+        if constexpr (PREC == kTF32X3) {
+          // word l & 3 of a row is K element 2 d + (l & 1): even row wr, wi;
+          // odd row -wi, wr
+          uint32_t pr_[2], pi_[2];
+          split_tf32(e.x, pr_);
+          split_tf32(e.y, pi_);
+          const bool im_word = (lane & 1) != 0;
+#pragma unroll
+          for (int pc = 0; pc < 2; ++pc) {
+            we[pc] = im_word ? pi_[pc] : pr_[pc];
+            wo[pc] = im_word ? pr_[pc] : (pi_[pc] ^ 0x80000000u);
           }
         } else {
-          const int ub = unit - unitsA;
-          const int rg = ub / (NCM / 2), q4 = (lane >> 2) & 3, h = lane >> 4;
-          const int cm = 2 * (ub % (NCM / 2)) + h;
-          const int offE = kAppA + rg * SBO + cm * 128 + (2 * q4) * 16 + (lane & 3) * 4;
-          const int offO = offE + 16;   // the odd row of the same vector
-          if (!in_bounds(offO + 3, PIECE, kSiteTcSmem)) continue;
-          // the first store takes even rows in lanes 0-15 and odd rows in
-          // lanes 16-31 (and the second the other way round), so each store
-          // covers all 32 banks
-          const int o1 = h ? offO : offE, o2 = h ? offE : offO;
-          constexpr int NPC = F::NPC;
-          uint32_t we[NPC], wo[NPC];
-          if constexpr (PREC == kTF32X3) {
-            // word l & 3 of a row is K element 2 d + (l & 1): even row wr, wi;
-            // odd row -wi, wr
-            uint32_t pr_[2], pi_[2];
-            split_tf32(e.x, pr_);
-            split_tf32(e.y, pi_);
-            const bool im_word = (lane & 1) != 0;
-#pragma unroll
-            for (int pc = 0; pc < 2; ++pc) {
-              we[pc] = im_word ? pi_[pc] : pr_[pc];
-              wo[pc] = im_word ? pr_[pc] : (pi_[pc] ^ 0x80000000u);
-            }
+          // 16-bit pairs (re in the low half): odd word = (-im, re)
+          if constexpr (PREC == kBF16X3) {
+            split_bf16(e.x, e.y, we);
           } else {
-            // 16-bit pairs (re in the low half): odd word = (-im, re)
-            if constexpr (PREC == kBF16X3) {
-              split_bf16(e.x, e.y, we);
-            } else {
-              const int q = rg * 4 + q4;
-              const float sc = q < Nq ? wsc[q] : 1.f;
-              split_f16(e.x * sc, e.y * sc, we);
-            }
-#pragma unroll
-            for (int pc = 0; pc < NPC; ++pc) wo[pc] = ((we[pc] >> 16) ^ 0x8000u) | (we[pc] << 16);
+            const float sc = wscq[vb];
+            split_f16(e.x * sc, e.y * sc, we);
           }
 #pragma unroll
-          for (int pc = 0; pc < NPC; ++pc) {
-            *reinterpret_cast<uint32_t*>(stage + pc * PIECE + o1) = h ? wo[pc] : we[pc];
-            *reinterpret_cast<uint32_t*>(stage + pc * PIECE + o2) = h ? we[pc] : wo[pc];
-          }
+          for (int pc = 0; pc < NPC; ++pc) wo[pc] = ((we[pc] >> 16) ^ 0x8000u) | (we[pc] << 16);
+        }
+#pragma unroll
+        for (int pc = 0; pc < NPC; ++pc) {
+          *reinterpret_cast<uint32_t*>(stage + pc * PIECE + o1) = h ? wo[pc] : we[pc];
+          *reinterpret_cast<uint32_t*>(stage + pc * PIECE + o2) = h ? we[pc] : wo[pc];
         }
       }
       if (ch + 1 < nchunks) load_chunk(ch + 1);
