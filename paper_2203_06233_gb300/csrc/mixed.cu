@@ -507,7 +507,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
 constexpr int kAppRB = 64;                    // bytes of one operand row per chunk (4 core matrices)
 constexpr int kAppA = 128 * kAppRB;           // A piece: 128 cells (8 KB)
 constexpr int kAppB = 256 * kAppRB;           // B piece: at most 256 weight rows (16 KB)
-constexpr int kAppU = 16;                     // staging units per warp and chunk ((16 + 32 x 2 / 4) x 4 / 8)
+constexpr int kAppU = 16;                     // staging units per warp and chunk: (64 A + at most 64 B units) / 8 warps
 
 // two stages of the pieces of 128 cell rows and NP weight rows
 template <int PREC>
