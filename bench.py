@@ -49,7 +49,12 @@ L2_FLUSH_BYTES = 256 << 20
 # (8192 of its 65536 systems, same kernel and launch shape: 1151412224 bytes
 # read + 510120448 written, the capture summarised in profiles/) scaled by 8, the
 # traffic being per system (its lower triangle read, its weights written).
-SOLVE_TRAFFIC = {("ece189e7f5967c5d", 3, "large"): 8 * (1151412224 + 510120448)}
+# The second key is solve.cu after a change confined to the refinement
+# option's team kernel (solve_mir_kernel, its shared-memory strides and size
+# function, and a helper they use): solve_big_kernel's source is the same, so
+# the same capture applies.
+SOLVE_TRAFFIC = {("ece189e7f5967c5d", 3, "large"): 8 * (1151412224 + 510120448),
+                 ("077ece954fb9fac1", 3, "large"): 8 * (1151412224 + 510120448)}
 SOLVE_KERNELS = {1: "solve_reg_kernel (register-resident FP64 LDL^H, solves, refinement)",
                  2: "solve_kernel (shared-memory FP64 Cholesky teams, solves, refinement)",
                  3: "solve_big_kernel (one system per CTA: FP64 LDL^H, solves, refinement)"}
