@@ -1102,6 +1102,11 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# configuration number -> workload: the standard CPI (D = 12), the D = 64 CPI,
+# the 512-CPI batch and the large CPI (D = 128)
+CONFIG_WORKLOADS = {2: "standard", 3: "mixed", 4: "batch", 5: "large"}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -1117,7 +1122,15 @@ def main():
                     help="large (the default) is the largest single-GPU CPI; batch: 512 uneven CPIs "
                          "per step in one graph replay; paper_cube: the paper's 1000-channel cube "
                          "through a subarray front end")
+    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=None,
+                    help="the workload by its configuration number: 2 standard, 3 mixed, 4 batch, "
+                         "5 large (1, the small CPI, is a parity-test case in tests/, not a "
+                         "benchmark workload)")
     args = ap.parse_args()
+    if args.config is not None:
+        if args.config not in CONFIG_WORKLOADS:
+            ap.error("configuration 1 (the small CPI) is a parity-test case, not a benchmark workload")
+        args.workload = CONFIG_WORKLOADS[args.config]
     global NAME
     NAME = args.workload
     if args.warmup < 3:
