@@ -55,6 +55,28 @@ def _plan(spec, prec):
 @pytest.mark.parametrize("prec", PRECS, ids=PIDS)
 @pytest.mark.parametrize("spec", SPECS, ids=IDS)
 def test_mixed_covariance_parity(spec, prec):
+    _check_covariance(spec, prec)
+
+
+# Snapshot lengths whose tensor-core tile is wider than its systems' rows:
+# D8 = D rounded up to 8 is 40 or 56, so the accumulator (G D8 rounded up to
+# 16 columns) also takes rows of the Xi block or zero rows as columns that
+# the epilogue must ignore; D = 24 packs two systems per tile, and D = 72
+# runs the four-accumulator form with 80 columns per accumulator.
+WIDTH_SPECS = [synth.CPISpec(10, 16, 16, 256, 4, 64, 4, cnr_db=30.0, seed=31),   # D = 40
+               synth.CPISpec(12, 16, 16, 256, 3, 64, 4, cnr_db=30.0, seed=32),   # D = 36
+               synth.CPISpec(14, 16, 16, 256, 4, 64, 4, cnr_db=30.0, seed=33),   # D = 56
+               synth.CPISpec(8, 16, 16, 256, 3, 64, 4, cnr_db=30.0, seed=34),    # D = 24
+               synth.CPISpec(18, 16, 16, 256, 4, 128, 4, cnr_db=30.0, seed=35)]  # D = 72
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PIDS)
+@pytest.mark.parametrize("spec", WIDTH_SPECS, ids=[f"D{s.D}" for s in WIDTH_SPECS])
+def test_mixed_covariance_tile_widths(spec, prec):
+    _check_covariance(spec, prec)
+
+
+def _check_covariance(spec, prec):
     from _parity import gather
     d = oracle.Dims(*spec.dims())
     dop64 = oracle.doppler(d, synth.make_cube(spec)).astype(np.complex64)
