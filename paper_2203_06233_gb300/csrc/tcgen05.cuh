@@ -48,18 +48,10 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
          ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// Instruction-descriptor bit that negates the A operand (bit 13, for
-// kind::f16 and kind::tf32): D (+)= (-A) * B^T.
-constexpr uint32_t kIdescNegateA = 1u << 13;
-
 __device__ __forceinline__ uint32_t to_tf32(float v) {  // round to nearest, ties away
   uint32_t t;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
   return t;
-}
-
-__device__ __forceinline__ int cm_offset(int m, int k, int K) {
-  return (m >> 3) * (128 * (K >> 2)) + (k >> 2) * 128 + (m & 7) * 16 + (k & 3) * 4;
 }
 
 // Warp-collective TMEM allocation (ncols a power of two in [32, 512]).
