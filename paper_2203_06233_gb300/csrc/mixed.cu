@@ -453,7 +453,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
 #pragma unroll
               for (int u = 0; u < 8; ++u) {
                 const int l = cb + u;
-                const int xo = (l >= a && l < D) ? i * LDX + l : 0;
+                const int xo = i * LDX + l;   // this lane's own row (entries l < a or l >= D unused)
                 re8[u] += xii[xo];             // XrXr + XiXi
                 im8[u] = xir[xo] - xrxi[u];    // XiXr - XrXi
               }
@@ -479,7 +479,7 @@ covariance_tcx_kernel(const float2* __restrict__ dop, double2* __restrict__ cov,
                 const double dre = ff::f2d_exact(re), dim = ff::f2d_exact(im);
                 const long long ext = nsys * D * D, o = sys * D * D;
                 if (in_bounds(o + (long long)l * D + a, ext, kSiteTcOut))
-                  out[(size_t)l * D + a] = make_double2(dre, -dim);
+                  out[(size_t)l * D + a] = make_double2(dre, ff::dneg(dim));   // sign bit: no FP64 op
                 if (!lower_only && l != a && in_bounds(o + (long long)a * D + l, ext, kSiteTcOut))
                   out[(size_t)a * D + l] = make_double2(dre, dim);
               }
